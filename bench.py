@@ -1,0 +1,372 @@
+"""Benchmark: multi-level synchronous Louvain on an R-MAT scale-22 graph.
+
+One step = one full multi-level run (every local-moving sweep, renumbering and graph
+induction of every level) of the library on the same synthetic graph:
+R-MAT scale 22 (4,194,304 vertices, 16 * 2^22 sampled pairs, a=0.57 b=0.19 c=0.19),
+symmetrised, loops and duplicates dropped, int32 weights uniform in [1, 16], seed 22.
+
+Metric: local-move edge-visits/s = sum over phases of (sweeps applied) * (stored
+entries of that phase's graph), divided by the device time of the run.
+
+Prints one JSON line.  With torchrun (N > 1) every rank runs its own replica on its
+own GPU (no data-path collective; weak scaling) and rank 0 reports the max time.
+`--impl reference` times the CPU oracle (single thread) on a bounded sample of the
+same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "local-move edge-visits/s, HBM % of peak; batched graphs/s vs plain (bit-exact)"
+UNIT = "edge-visits/s"
+WORKLOAD = ("R-MAT scale 22 (4,194,304 vertices, edge factor 16, a=0.57 b=0.19 c=0.19), "
+            "symmetrised, duplicates and self-loops dropped, int32 weights uniform in [1,16], "
+            "int32 ids, seed 22; full multi-level run to threshold 1e-6")
+FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 129 * 1024 * 1024
+KERNEL_NAMES = ["k_move_small", "k_move_group<8>", "k_move_group<32>", "k_move_big"]
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 is the workload)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-sweeps", type=int, default=2)
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a float over all ranks (identity when world == 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_traffic(kernel_name: str):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, or None when
+    the summary is missing or was taken on a different kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1805_10904_gb300", "csrc", "k_move.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    entry = rec.get("kernels", {}).get(kernel_name)
+    if not entry or entry.get("source_sha256") != sha:
+        return None
+    return entry.get("dram_bytes_per_launch_full")
+
+
+def make_graph(scale: int):
+    import graphgen as gg
+    return gg.rmat(scale, 16, 0.57, 0.19, 0.19, 1, 16, seed=22)
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+
+def time_oracle(g, sweeps: int):
+    """Single-threaded oracle on level 0 of the workload, `sweeps` sweeps."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.louvain(g.rp, g.col, g.w, max_iters=sweeps, max_levels=1)
+    dt = time.perf_counter() - t0
+    visits = r.edge_visits
+    return visits / dt, dt, visits
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    g = make_graph(args.scale)
+    sample = (f"level 0 of the workload graph, first {args.cpu_sample_sweeps} sweeps "
+              "(max_iters and max_levels capped), single thread, per step")
+    for _ in range(args.warmup):
+        time_oracle(g, args.cpu_sample_sweeps)
+    times, visits_total = [], 0
+    for _ in range(args.steps):
+        _, dt, v = time_oracle(g, args.cpu_sample_sweeps)
+        times.append(dt)
+        visits_total += v
+    value = visits_total / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph_n": g.n, "graph_nnz": g.nnz,
+                   "parallelism": "single host thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- native arm
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    import paper_1805_10904_gb300 as lv
+
+    world, rank, local = dist_env()
+    dist = dist_init(world, "nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g = make_graph(args.scale)
+    rp = torch.from_numpy(g.rp).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    w = torch.from_numpy(g.w).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    h = lv.Louvain(local, profile=True)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        return h.run(rp, col, w, stream=stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step().close()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    step_ms, visits, launches = [], 0, 0
+    dom = {"time_ms": 0.0, "bytes": 0, "launches": 0, "id": None}
+    levels = None
+    for _ in range(args.steps):
+        flush.fill_(1)  # L2 flush between timed steps (untimed)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        res = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        c, t = res.counters()
+        visits += int(c[0])
+        launches += int(c[4])
+        dom["time_ms"] += float(t[4])
+        dom["bytes"] += int(c[6])
+        dom["launches"] += int(c[5])
+        dom["id"] = int(c[7])
+        if levels is None:
+            levels = [(l.n, l.nnz, l.iters, l.ncomm, round(l.q, 6)) for l in res.levels()]
+        res.close()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    max_ms = reduce_max(total_ms, world, dev)
+    all_visits = reduce_sum(float(visits), world, dev)
+
+    # end-to-end through the C ABI with pinned host buffers: H2D inside, labels D2H inside
+    rp_h = torch.from_numpy(g.rp).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    w_h = torch.from_numpy(g.w).pin_memory()
+    h2 = lv.Louvain(local, profile=False)
+    for _ in range(max(1, args.warmup)):
+        r = h2.run(rp_h, col_h, w_h, stream=stream.cuda_stream)
+        for l in range(r.num_levels):
+            r.labels(l)
+        r.close()
+    barrier(world)
+    e2e_s, e2e_visits, d2h = 0.0, 0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = h2.run(rp_h, col_h, w_h, stream=stream.cuda_stream)
+        out = [r.labels(l) for l in range(r.num_levels)]
+        e2e_s += time.perf_counter() - t0
+        e2e_visits += int(r.counters()[0][0])
+        d2h = sum(a.nbytes for a in out)
+        r.close()
+    e2e_max = reduce_max(e2e_s, world, dev)
+    e2e_all = reduce_sum(float(e2e_visits), world, dev)
+    h2d = g.rp.nbytes + g.col.nbytes + g.w.nbytes
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = measured_hbm_peak()
+    roofline = None
+    if dom["time_ms"] > 0 and dom["launches"] > 0:
+        achieved = dom["bytes"] / (dom["time_ms"] / 1000.0) / 1e9
+        name = KERNEL_NAMES[dom["id"]]
+        traffic = kernel_traffic(name)
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic,
+                    "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
+                    "avg_launch_ms": dom["time_ms"] / dom["launches"]}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cores = 1
+        v, dt, vis = time_oracle(g, args.cpu_sample_sweeps)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"level 0 of the workload graph, first {args.cpu_sample_sweeps} sweeps "
+                         f"(max_iters/max_levels capped): {vis} edge visits in {dt:.1f} s, "
+                         f"one thread; host has {os.cpu_count()} cores"}
+
+    value = all_visits / (max_ms / 1000.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph_n": g.n, "graph_nnz": g.nnz,
+                   "levels": levels, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "L2 flushed between timed steps (258 MB write); CSR of 1 GB > L2"},
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_all / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * louvain.h -- C ABI of the GB300 synchronous parallel Louvain library.
+ *
+ * Method: Forster, "Parallel Louvain Community Detection Optimized for GPUs"
+ * (arXiv 1805.10904): the local-moving phase of Algorithm 1 (Eq. 1-5 with the
+ * Sec. 3.1 minimum-label rules) repeated inside the multi-level driver of
+ * Algorithm 2, with renumbering and graph induction after each level (Sec. 5.1.2).
+ * Degree-one vertex following (a heuristic of Lu et al. that Sec. 7 refers to) is
+ * applied before the first sweep of level 0.
+ *
+ * Arithmetic is exact: weights are integers >= 1, sums are int64, gains and
+ * modularity are compared as int64 or int128 integers (Qn = (2W)^2 * Q), so the
+ * labels returned are one deterministic function of the input.
+ *
+ * Conventions for every call:
+ *   - Return value: LOUVAIN_OK (0) or one of the LOUVAIN_ERR_* codes below.  No call
+ *     aborts, exits or traps; after an error the handle stays usable and
+ *     louvain_last_error() describes the failure.
+ *   - Streams are CUstream / cudaStream_t values passed as void*; NULL means the
+ *     legacy default stream.  Every call returns only after its GPU work on that stream
+ *     has completed.
+ *   - Input arrays are borrowed for the duration of the call and never retained.
+ *   - Results are owned by the library until louvain_result_free().
+ */
+#ifndef GB300_LOUVAIN_H
+#define GB300_LOUVAIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define LOUVAIN_OK 0
+#define LOUVAIN_ERR_INVALID_ARG 1  /* NULL pointer, negative size, bad config field        */
+#define LOUVAIN_ERR_NOT_SYMMETRIC 2/* A_ij != A_ji (full checks only)                      */
+#define LOUVAIN_ERR_DUPLICATE_EDGE 3 /* a row lists a column twice or unsorted (full checks) */
+#define LOUVAIN_ERR_BAD_WEIGHT 4   /* a weight < 1 (Sec. 2: weights are positive)           */
+#define LOUVAIN_ERR_INDEX_RANGE 5  /* row_ptr not monotone from 0, or a column outside [0,n) */
+#define LOUVAIN_ERR_OOM 6          /* device or host allocation failed                      */
+#define LOUVAIN_ERR_CUDA 7         /* a CUDA runtime call failed (message has the CUDA text) */
+#define LOUVAIN_ERR_TIMEOUT 8      /* a bounded device wait gave up                          */
+#define LOUVAIN_ERR_INTERNAL 9     /* a device-side consistency check failed                */
+#define LOUVAIN_PENDING 10         /* serving: the ticket has not finished                   */
+#define LOUVAIN_ERR_REJECTED 11    /* serving: request larger than the memory budget         */
+#define LOUVAIN_ERR_TOO_LARGE 12   /* sum of weights above 2^62, or n above 2^31 - 1         */
+
+/* pointer kinds of input arrays */
+#define LOUVAIN_PTR_HOST 0   /* host memory: copied to the device inside the call (timed as e2e) */
+#define LOUVAIN_PTR_DEVICE 1 /* device memory on the handle's device, read in place             */
+
+/* ---------------------------------------------------------------- configuration */
+typedef void *(*louvain_alloc_fn)(size_t bytes, void *ctx, void *stream);
+typedef void (*louvain_free_fn)(void *ptr, void *ctx, void *stream);
+
+typedef struct {
+    uint32_t struct_size;      /* sizeof(louvain_config), set by louvain_config_init       */
+    /* phase threshold theta as an exact rational (Algorithm 1 / Algorithm 2 threshold);
+     * a sweep ends the level when (Qn_new - Qn_prev) * den < num * (2W)^2.              */
+    int64_t theta_num;         /* default 1                                              */
+    int64_t theta_den;         /* default 1000000                                        */
+    int32_t max_iters;         /* sweeps per level cap, default 1000                     */
+    int32_t max_levels;        /* default 64                                             */
+    int32_t vertex_following;  /* 1 (default): degree-one following before level 0       */
+    int32_t vf_all_levels;     /* 1: also before every later level; default 0            */
+    int32_t checks;            /* 1 (default): index and weight checks; 2: also symmetry,
+                                  sortedness and duplicates; 0 is treated as 1             */
+    int32_t force_int128;      /* 1: take the int128 gain path even when int64 suffices  */
+    /* degree-bin thresholds (non-loop row length d):
+     *   d <= bin_small -> one thread per vertex (bin_small in [0, 8]),
+     *   d <= bin_mid1  -> 8-lane group, d <= bin_mid2 -> one warp,
+     *   larger         -> CTA chunks of chunk_entries entries, multi-chunk rows use a
+     *                     global-memory hash table.  0 selects the tuned default.      */
+    int32_t bin_small;
+    int32_t bin_mid1;
+    int32_t bin_mid2;
+    int32_t chunk_entries;     /* power of two in [32, 4096]; 0 = default                */
+    int32_t profile;           /* 1: time kernel groups with CUDA events (louvain_result_counters) */
+    int32_t reserved[7];       /* must be zero                                           */
+    /* device memory: both NULL means stream-ordered cudaMallocAsync/cudaFreeAsync */
+    louvain_alloc_fn alloc;
+    louvain_free_fn free;
+    void *alloc_ctx;
+} louvain_config;
+
+/* Fill *cfg with the defaults above.  Returns LOUVAIN_ERR_INVALID_ARG for NULL. */
+int louvain_config_init(louvain_config *cfg);
+
+/* ---------------------------------------------------------------- handle */
+typedef struct louvain_handle louvain_handle;
+typedef struct louvain_result louvain_result;
+
+/* Create a handle bound to CUDA device `device`.  cfg may be NULL (defaults); it is
+ * copied.  On success *out owns the handle (free with louvain_destroy). */
+int louvain_create(const louvain_config *cfg, int device, louvain_handle **out);
+
+/* Release the handle; NULL is ignored.  Results created from it must be freed first. */
+void louvain_destroy(louvain_handle *h);
+
+/* Text of the last error on this handle ("" if none).  Valid until the next call. */
+const char *louvain_last_error(const louvain_handle *h);
+
+/* ---------------------------------------------------------------- single graph */
+/* Run multi-level Louvain (Algorithm 2 around Algorithm 1) on one undirected graph
+ * G(V, E, w) given as symmetric CSR (Sec. 2):
+ *   n        number of vertices (0 <= n <= 2^31 - 1)
+ *   row_ptr  int64[n + 1], row_ptr[0] = 0, non-decreasing; nnz = row_ptr[n]
+ *   col_idx  int32[nnz], column ids in [0, n); both directions of every non-loop edge
+ *            are stored, a loop (i, i) once; no column twice in a row
+ *   weights  int32[nnz] >= 1, A_ij = A_ji; NULL means every weight is 1
+ *   ptr_kind LOUVAIN_PTR_HOST or LOUVAIN_PTR_DEVICE for all three arrays
+ *   stream   stream the work is ordered on
+ * On success *out receives the result: one entry per recorded level, a level being
+ * recorded when it merged at least two communities.  Errors: INVALID_ARG, INDEX_RANGE,
+ * BAD_WEIGHT, NOT_SYMMETRIC / DUPLICATE_EDGE (checks = 2), TOO_LARGE, OOM, CUDA,
+ * INTERNAL. */
+int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                const int32_t *weights, int ptr_kind, void *stream, louvain_result **out);
+
+/* ---------------------------------------------------------------- results */
+/* Number of recorded levels (0 when nothing merged, e.g. no edges). */
+int louvain_result_num_levels(const louvain_result *r);
+
+/* Number of vertices of the input graph. */
+int64_t louvain_result_num_vertices(const louvain_result *r);
+
+/* Labels of the original vertices after level `level`, compacted to 0..ncomm-1 in the
+ * order of the level's community labels (Sec. 5.1.2 renumbering).  *labels points to
+ * n int32 values in host memory owned by r (copied from the device on first access).
+ * ncomm may be NULL. */
+int louvain_result_labels(const louvain_result *r, int level, const int32_t **labels,
+                          int64_t *ncomm);
+
+/* Same labels in device memory owned by r (no copy). */
+int louvain_result_labels_device(const louvain_result *r, int level, const int32_t **labels);
+
+/* Modularity of level `level` (Eq. 3): q = (double)Qn / (double)TW^2 with TW = 2W; the
+ * exact values as int128 limbs {high (signed), low (bit pattern)}.  Any out pointer may be
+ * NULL.  qn_init is Qn of the level's state before its first sweep. */
+int louvain_result_modularity(const louvain_result *r, int level, double *q, int64_t qn[2],
+                              int64_t qn_init[2], int64_t *tw);
+
+/* Per-level counters: sweeps applied, vertices and stored entries of the graph the level
+ * ran on, communities after it, and whether the sweep cap stopped it.  Any out pointer may
+ * be NULL. */
+int louvain_result_level_info(const louvain_result *r, int level, int32_t *iters,
+                              int64_t *n_level, int64_t *nnz_level, int64_t *ncomm,
+                              int32_t *hit_iter_cap);
+
+/* Sweep trace in execution order over all phases run (recorded levels first, then the
+ * final phase that merged nothing): for entry t, the level, the 1-based sweep index, the
+ * vertices moved and Qn after the sweep (two int64 limbs per entry).  With all arrays NULL
+ * it only returns the entry count through *len. */
+int louvain_result_trace(const louvain_result *r, int64_t *len, int32_t *level, int32_t *iter,
+                         int64_t *moved, int64_t *qn);
+
+/* Work and time counters of the run:
+ *   counters[0] edge visits: sum over phases of (sweeps applied) * nnz of the phase's graph
+ *   counters[1] sweep kernels launched (including the one speculative sweep per phase
+ *               whose moves are discarded, see louvain_run)
+ *   counters[2] algorithmic bytes of all local-move sweeps: per sweep
+ *               nnz * (4 column + s_w weight + 4 gathered label)
+ *               + cand * 8 (deg of each distinct neighbouring community)
+ *               + n * (8 row offset + 8 deg_i read for sum deg^2 + 4 label + 8 delta
+ *                      + 8 deg of the own community + 4 proposed label)
+ *               + (8 row offset + 4 list entry) per vertex of the list-driven kernels,
+ *               s_w = 4 for int32 weights and 8 for int64
+ *   counters[3] distinct neighbour communities summed over vertices and sweeps
+ *   counters[4] kernels launched by the run
+ * times_ms[0] local-move kernels (device time), [1] coarsening, [2] everything else on
+ * the device, [3] wall time of louvain_run; [4] the dominant local-move kernel alone,
+ * [5] the thread-per-vertex kernel, [6] the lane-group kernels, [7] the chunked kernel;
+ * counters[5] launches of the dominant kernel, counters[6] its algorithmic bytes,
+ * counters[7] which one it is (0 thread-per-vertex, 1 8-lane groups, 2 warps, 3 chunks).
+ * Arrays of 8; unused slots are zero.  Device times are filled only when the config had
+ * profile = 1. */
+int louvain_result_counters(const louvain_result *r, int64_t counters[8], double times_ms[8]);
+
+/* Free a result and its host and device memory; NULL is ignored. */
+void louvain_result_free(louvain_result *r);
+
+/* ---------------------------------------------------------------- version */
+/* ABI version of this header: 1. */
+int louvain_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_LOUVAIN_H */

@@ -1,0 +1,948 @@
+// engine.cu -- host orchestration of multi-level synchronous Louvain and the C ABI.
+//
+// Algorithm 2 of arXiv 1805.10904 around Algorithm 1:
+//   level l: init status (delta, singletons; vertex following at level 0), degree bins,
+//            sweeps until the phase controller stops (all decisions on device), renumber
+//            (prefix-sum compaction), record the level if it merged anything, test the
+//            outer threshold, induce the next graph.
+// The host only sequences launches, sizes buffers and reads a few scalars per sweep and
+// per level; every step of the method runs in the kernels of k_level.cu, k_move.cu and
+// k_coarsen.cu.
+#include <chrono>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/louvain.h"
+#include "lv_common.cuh"
+#include "lv_kernels.h"
+#include "lv_scan.cuh"
+
+using namespace lv;
+
+namespace {
+
+struct LvErr {
+    int code;
+    std::string msg;
+};
+
+#define CK(x)                                                                                   \
+    do {                                                                                        \
+        cudaError_t e_ = (x);                                                                   \
+        if (e_ != cudaSuccess)                                                                  \
+            throw LvErr{e_ == cudaErrorMemoryAllocation ? LOUVAIN_ERR_OOM : LOUVAIN_ERR_CUDA,   \
+                        std::string(#x) + ": " + cudaGetErrorString(e_)};                       \
+    } while (0)
+
+// Device memory through the caller's allocator or stream-ordered cudaMallocAsync.
+struct DevAlloc {
+    louvain_alloc_fn fa = nullptr;
+    louvain_free_fn ff = nullptr;
+    void *ctx = nullptr;
+    cudaStream_t s = nullptr;
+    void *get(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        bytes = (bytes + 255) & ~(size_t)255;
+        void *p = nullptr;
+        if (fa) {
+            p = fa(bytes, ctx, (void *)s);
+            if (!p) throw LvErr{LOUVAIN_ERR_OOM, "allocator callback returned NULL"};
+        } else {
+            cudaError_t e = cudaMallocAsync(&p, bytes, s);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                throw LvErr{LOUVAIN_ERR_OOM, "cudaMallocAsync of " + std::to_string(bytes) +
+                                                 " bytes failed"};
+            }
+        }
+        return p;
+    }
+    void put(void *p)
+    {
+        if (!p) return;
+        if (ff) ff(p, ctx, (void *)s);
+        else cudaFreeAsync(p, s);
+    }
+};
+
+template <typename T>
+struct DBuf {
+    DevAlloc *A = nullptr;
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    void reset(DevAlloc *a, size_t count)
+    {
+        release();
+        A = a;
+        n = count;
+        p = (T *)A->get(sizeof(T) * (count ? count : 1));
+    }
+    void release()
+    {
+        if (p && A) A->put(p);
+        p = nullptr;
+        n = 0;
+    }
+    T *take()
+    {
+        T *q = p;
+        p = nullptr;
+        n = 0;
+        return q;
+    }
+    void swap(DBuf &o)
+    {
+        std::swap(A, o.A);
+        std::swap(p, o.p);
+        std::swap(n, o.n);
+    }
+    ~DBuf() { release(); }
+};
+
+// Scalars shared by host and device during a run (one device block, one pinned mirror).
+struct Scalars {
+    unsigned err;
+    int32_t pad0;
+    u64 tw;
+    SweepStats st;
+    LevelCtl ctl;
+    int32_t bin_counts[12];
+    int32_t ccounts[4];
+    u64 cand_total[4];
+    int32_t tail[8];
+};
+
+bool host_below_threshold(i128 qn_new, i128 qn_old, i64 tw, i64 num, i64 den)
+{
+    const i128 diff = qn_new - qn_old;
+    if (diff < 0) return true;
+    const u128 tw2 = (u128)(u64)tw * (u64)tw;
+    const u128 x = (u128)diff;
+    const u128 xl = (u128)(u64)x * (u64)den, xh = (u128)(u64)(x >> 64) * (u64)den;
+    const u128 yl = (u128)(u64)tw2 * (u64)num, yh = (u128)(u64)(tw2 >> 64) * (u64)num;
+    const u128 xmid = (xl >> 64) + (u64)xh, ymid = (yl >> 64) + (u64)yh;
+    const u64 x2 = (u64)(xh >> 64) + (u64)(xmid >> 64), y2 = (u64)(yh >> 64) + (u64)(ymid >> 64);
+    if (x2 != y2) return x2 < y2;
+    if ((u64)xmid != (u64)ymid) return (u64)xmid < (u64)ymid;
+    return (u64)xl < (u64)yl;
+}
+
+i128 limbs_to_i128(const i64 v[2]) { return (i128)(((u128)(u64)v[0] << 64) | (u128)(u64)v[1]); }
+void i128_to_limbs(i128 x, int64_t out[2])
+{
+    out[0] = (int64_t)(x >> 64);
+    out[1] = (int64_t)(u64)x;
+}
+
+double now_ms()
+{
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+}  // namespace
+
+struct LevelRec {
+    int64_t ncomm = 0;
+    i128 qn = 0, qn_init = 0;
+    int32_t iters = 0;
+    int64_t n = 0, nnz = 0;
+    int32_t hit_cap = 0;
+    int32_t *d_labels = nullptr;
+};
+
+struct TraceRec {
+    int32_t level, iter;
+    int64_t moved;
+    i128 qn;
+};
+
+struct louvain_handle {
+    louvain_config cfg;
+    int device = 0;
+    std::string err;
+    LaunchCfg lc;
+    Scalars *pinned = nullptr;
+};
+
+struct louvain_result {
+    int64_t n0 = 0;
+    int64_t tw = 0;
+    int device = 0;
+    std::vector<LevelRec> levels;
+    mutable std::vector<std::vector<int32_t>> host_labels;
+    std::vector<TraceRec> trace;
+    int64_t counters[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double times[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    louvain_free_fn ff = nullptr;
+    void *ctx = nullptr;
+};
+
+namespace {
+
+int map_err_bits(unsigned bits, std::string &msg)
+{
+    if (bits & ERRF_ROWPTR) {
+        msg = "row_ptr must start at 0 and never decrease";
+        return LOUVAIN_ERR_INDEX_RANGE;
+    }
+    if (bits & ERRF_INDEX) {
+        msg = "a column index is outside [0, n)";
+        return LOUVAIN_ERR_INDEX_RANGE;
+    }
+    if (bits & ERRF_WEIGHT) {
+        msg = "a weight is below 1";
+        return LOUVAIN_ERR_BAD_WEIGHT;
+    }
+    if (bits & ERRF_DUP) {
+        msg = "a row is unsorted or lists a column twice";
+        return LOUVAIN_ERR_DUPLICATE_EDGE;
+    }
+    if (bits & ERRF_ASYM) {
+        msg = "the adjacency is not symmetric (A_ij != A_ji)";
+        return LOUVAIN_ERR_NOT_SYMMETRIC;
+    }
+    if (bits & ERRF_HASH_FULL) {
+        msg = "internal: a hash table overflowed";
+        return LOUVAIN_ERR_INTERNAL;
+    }
+    msg = "internal device check failed";
+    return LOUVAIN_ERR_INTERNAL;
+}
+
+struct Runner {
+    louvain_handle *h;
+    cudaStream_t s;
+    DevAlloc A;
+    Scalars *d_sc = nullptr;
+    DBuf<Scalars> sc_buf;
+    int kernels = 0;
+
+    void sync_scalars()
+    {
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h->pinned, d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h->pinned->err) {
+            std::string msg;
+            int code = map_err_bits(h->pinned->err, msg);
+            throw LvErr{code, msg};
+        }
+    }
+
+    template <typename T>
+    T read_one(const T *dptr)
+    {
+        T v;
+        CK(cudaMemcpyAsync(&h->pinned->tail[0], dptr, sizeof(T), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        memcpy(&v, &h->pinned->tail[0], sizeof(T));
+        return v;
+    }
+
+    void run(int64_t n0, const int64_t *rp, const int32_t *col, const int32_t *w, int kind,
+             louvain_result *res);
+};
+
+void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const int32_t *w_in,
+                 int kind, louvain_result *res)
+{
+    const louvain_config &cfg = h->cfg;
+    const double wall0 = now_ms();
+    const LaunchCfg &lc = h->lc;
+    sc_buf.reset(&A, 1);
+    d_sc = sc_buf.p;
+    CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars), s));
+
+    // ---------------- input graph on the device
+    int64_t nnz = 0;
+    DBuf<int64_t> rp_own;
+    DBuf<int32_t> col_own, w_own;
+    const int64_t *d_rp = rp_in;
+    const int32_t *d_col = col_in;
+    const int32_t *d_w = w_in;
+    if (kind == LOUVAIN_PTR_HOST) {
+        if (rp_in[0] != 0) throw LvErr{LOUVAIN_ERR_INDEX_RANGE, "row_ptr[0] must be 0"};
+        nnz = rp_in[n0];
+        if (nnz < 0) throw LvErr{LOUVAIN_ERR_INDEX_RANGE, "row_ptr[n] is negative"};
+        if (nnz > 0 && !col_in) throw LvErr{LOUVAIN_ERR_INVALID_ARG, "col_idx is NULL"};
+        rp_own.reset(&A, (size_t)n0 + 1);
+        CK(cudaMemcpyAsync(rp_own.p, rp_in, sizeof(int64_t) * (size_t)(n0 + 1),
+                           cudaMemcpyHostToDevice, s));
+        d_rp = rp_own.p;
+        col_own.reset(&A, (size_t)nnz);
+        if (nnz)
+            CK(cudaMemcpyAsync(col_own.p, col_in, sizeof(int32_t) * (size_t)nnz,
+                               cudaMemcpyHostToDevice, s));
+        d_col = col_own.p;
+        if (w_in) {
+            w_own.reset(&A, (size_t)nnz);
+            if (nnz)
+                CK(cudaMemcpyAsync(w_own.p, w_in, sizeof(int32_t) * (size_t)nnz,
+                                   cudaMemcpyHostToDevice, s));
+            d_w = w_own.p;
+        }
+    } else {
+        const int64_t r0 = read_one(rp_in);
+        nnz = read_one(rp_in + n0);
+        if (r0 != 0) throw LvErr{LOUVAIN_ERR_INDEX_RANGE, "row_ptr[0] must be 0"};
+        if (nnz < 0) throw LvErr{LOUVAIN_ERR_INDEX_RANGE, "row_ptr[n] is negative"};
+        if (nnz > 0 && !col_in) throw LvErr{LOUVAIN_ERR_INVALID_ARG, "col_idx is NULL"};
+    }
+    if (!d_w) {
+        w_own.reset(&A, (size_t)nnz);
+        kernels += launch_fill_ones(w_own.p, nnz, s, lc);
+        d_w = w_own.p;
+    }
+    res->n0 = n0;
+    if (n0 == 0) {
+        CK(cudaStreamSynchronize(s));
+        res->times[3] = now_ms() - wall0;
+        return;
+    }
+
+    DevGraph G;
+    G.n = n0;
+    G.nnz = nnz;
+    G.rp = d_rp;
+    G.col = d_col;
+    G.w = d_w;
+    G.wbytes = 4;
+
+    // ---------------- validation and weighted degrees (Sec. 2)
+    kernels += launch_validate_rowptr(d_rp, n0, &d_sc->err, s, lc);
+    sync_scalars();  // row offsets must be sane before any row is read
+    DBuf<i64> delta, delta_next, deg;
+    DBuf<int32_t> C, Cnext, size, new_id;
+    delta.reset(&A, n0);
+    delta_next.reset(&A, n0);
+    deg.reset(&A, n0);
+    C.reset(&A, n0);
+    Cnext.reset(&A, n0);
+    size.reset(&A, n0);
+    new_id.reset(&A, (size_t)n0 + 1);
+    kernels += launch_row_sums(G, delta.p, &d_sc->tw, &d_sc->err, s, lc);
+    if (cfg.checks >= 2) kernels += launch_check_symmetry(G, &d_sc->err, s, lc);
+    sync_scalars();
+    const u64 tw_u = h->pinned->tw;
+    if (tw_u > ((u64)1 << 62)) throw LvErr{LOUVAIN_ERR_TOO_LARGE, "sum of weights above 2^62"};
+    const i64 TW = (i64)tw_u;
+    res->tw = TW;
+    const bool wide = cfg.force_int128 || (u128)tw_u * tw_u > (u128)INT64_MAX;
+
+    // ---------------- per-run buffers sized by level 0 (Theorem 1: levels never grow)
+    const int64_t scratch_n = scan_scratch_elems(n0 + 1) + 64;
+    DBuf<int32_t> lists[3];
+    for (auto &l : lists) l.reset(&A, n0);
+    DBuf<int32_t> b_nch, b_chunk_first, b_glog2, b_gcnt, b_gdone;
+    DBuf<int64_t> b_gcap, b_goff;
+    DBuf<u64> b_gloop;
+    b_nch.reset(&A, n0);
+    b_chunk_first.reset(&A, (size_t)n0 + 1);
+    b_glog2.reset(&A, n0);
+    b_gcnt.reset(&A, n0);
+    b_gdone.reset(&A, n0);
+    b_gcap.reset(&A, n0);
+    b_goff.reset(&A, (size_t)n0 + 1);
+    b_gloop.reset(&A, n0);
+    DBuf<int32_t> scratch32;
+    DBuf<int64_t> scratch64;
+    scratch32.reset(&A, scratch_n);
+    scratch64.reset(&A, scratch_n);
+    DBuf<i64> tr_moved, tr_qn;
+    const int tcap = cfg.max_iters + 1;
+    tr_moved.reset(&A, tcap);
+    tr_qn.reset(&A, 2 * (size_t)tcap);
+    std::vector<i64> h_tr_moved(tcap), h_tr_qn(2 * (size_t)tcap);
+    // coarsening buffers
+    DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_clist, c_blist, c_tmp_col;
+    DBuf<int64_t> c_mpre;
+    DBuf<u64> c_tmp_w;
+    // graph buffers of the levels above 0
+    DBuf<int64_t> g_rp, g_rp_next;
+    DBuf<int32_t> g_col, g_col_next;
+    DBuf<unsigned char> g_w, g_w_next;
+    DBuf<int32_t> chunk_b;
+    DBuf<int32_t> gkeys, glist;
+    DBuf<u64> gvals;
+
+    SweepTimers tm;
+    std::vector<cudaEvent_t> extra_ev;
+    double t_kernel[4] = {0, 0, 0, 0};
+    int64_t launches_kernel[4] = {0, 0, 0, 0};
+    double bytes_kernel[4] = {0, 0, 0, 0};
+    if (cfg.profile) {
+        for (auto &e : tm.ev) CK(cudaEventCreate(&e));
+        tm.on = true;
+    }
+    struct EvGuard {
+        SweepTimers *t;
+        ~EvGuard()
+        {
+            if (t->on)
+                for (auto &e : t->ev) cudaEventDestroy(e);
+        }
+    } evg{&tm};
+
+    PhaseState st;
+    st.C = C.p;
+    st.Cnext = Cnext.p;
+    st.deg = deg.p;
+    st.size = size.p;
+    st.delta = delta.p;
+
+    Bins bins;
+    bins.small_max = cfg.bin_small;
+    bins.mid1 = cfg.bin_mid1;
+    bins.mid2 = cfg.bin_mid2;
+    bins.chunk = cfg.chunk_entries;
+    bins.counts = &d_sc->bin_counts[0];
+
+    const int32_t *prev_labels = nullptr;
+    i128 qn_prev_level = 0;
+    int64_t edge_visits = 0, sweeps_launched = 0;
+    double alg_bytes = 0.0;
+    u64 cand_all = 0;
+    int levels_run = 0;
+
+    for (int level = 0; level < cfg.max_levels; level++) {
+        levels_run++;
+        const int64_t n = G.n;
+        if (level > 0) {
+            delta.swap(delta_next);
+            st.delta = delta.p;
+        }
+        kernels += launch_init_state(n, st, s, lc);
+        if (cfg.vertex_following && (level == 0 || cfg.vf_all_levels))
+            kernels += launch_vertex_following(G, st, s, lc);
+
+        // degree bins
+        bins.list[0] = lists[0].p;
+        bins.list[1] = lists[1].p;
+        bins.list[2] = lists[2].p;
+        kernels += launch_bin(G, bins, s, lc);
+        sync_scalars();
+        for (int b = 0; b < 3; b++) bins.nlist[b] = h->pinned->bin_counts[b];
+        for (int b = 0; b < 4; b++)
+            memcpy(&bins.entries[b], &h->pinned->bin_counts[4 + 2 * b], sizeof(int64_t));
+        bins.nch = b_nch.p;
+        bins.chunk_first = b_chunk_first.p;
+        bins.gcap = b_gcap.p;
+        bins.goff = b_goff.p;
+        bins.glog2 = b_glog2.p;
+        bins.gcnt = b_gcnt.p;
+        bins.gdone = b_gdone.p;
+        bins.gloop = b_gloop.p;
+        bins.nchunks = 0;
+        bins.gslots = 0;
+        if (bins.nlist[2] > 0) {
+            const int nb = bins.nlist[2];
+            kernels += launch_big_prep(G, bins, scratch64.p, scratch32.p, s, lc);
+            bins.nchunks = read_one(b_chunk_first.p + nb);
+            bins.gslots = read_one(b_goff.p + nb);
+            chunk_b.reset(&A, bins.nchunks);
+            bins.chunk_b = chunk_b.p;
+            kernels += launch_big_fill(bins, s, lc);
+            if (bins.gslots > 0) {
+                gkeys.reset(&A, bins.gslots);
+                gvals.reset(&A, bins.gslots);
+                glist.reset(&A, bins.gslots);
+                CK(cudaMemsetAsync(gkeys.p, 0xFF, sizeof(int32_t) * bins.gslots, s));
+                CK(cudaMemsetAsync(gvals.p, 0, sizeof(u64) * bins.gslots, s));
+            }
+            bins.gkeys = gkeys.p;
+            bins.gvals = gvals.p;
+            bins.glist = glist.p;
+            CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
+            CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
+            CK(cudaMemsetAsync(b_gloop.p, 0, sizeof(u64) * nb, s));
+        }
+
+        // phase controller
+        LevelCtl ctl;
+        memset(&ctl, 0, sizeof(ctl));
+        ctl.tw = TW;
+        ctl.theta_num = cfg.theta_num;
+        ctl.theta_den = cfg.theta_den;
+        ctl.max_iters = cfg.max_iters;
+        h->pinned->ctl = ctl;
+        CK(cudaMemcpyAsync(&d_sc->ctl, &h->pinned->ctl, sizeof(LevelCtl), cudaMemcpyHostToDevice,
+                           s));
+        CK(cudaMemsetAsync(&d_sc->st, 0, sizeof(SweepStats), s));
+        CK(cudaMemsetAsync(&d_sc->cand_total[0], 0, sizeof(u64) * 4, s));
+
+        // sweeps (Algorithm 1); one host read of the controller per sweep
+        int sweeps = 0;
+        for (;;) {
+            kernels += launch_sweep(G, st, bins, TW, wide, &d_sc->st, &d_sc->err, s, lc, &tm);
+            kernels += launch_decide(&d_sc->st, &d_sc->ctl, tr_moved.p, tr_qn.p,
+                                     &d_sc->cand_total[0], s);
+            kernels += launch_apply(n, st, &d_sc->ctl, s, lc);
+            sweeps++;
+            sync_scalars();
+            if (tm.on) {
+                for (int k = 0; k < 4; k++) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, tm.ev[2 * k], tm.ev[2 * k + 1]));
+                    t_kernel[k] += ms;
+                }
+                launches_kernel[0] += 1;
+                launches_kernel[1] += bins.nlist[0] > 0;
+                launches_kernel[2] += bins.nlist[1] > 0;
+                launches_kernel[3] += bins.nchunks > 0;
+            }
+            if (h->pinned->ctl.done) break;
+            if (sweeps > cfg.max_iters + 2)
+                throw LvErr{LOUVAIN_ERR_INTERNAL, "phase controller did not stop"};
+        }
+        sweeps_launched += sweeps;
+        const LevelCtl &hc = h->pinned->ctl;
+        const int iters = hc.iters;
+        const i128 qn_final = limbs_to_i128(hc.qn_final);
+        const i128 qn_init = limbs_to_i128(hc.qn_init);
+        const int hit_cap = hc.hit_cap;
+        u64 cand_level[4];
+        for (int b = 0; b < 4; b++) cand_level[b] = h->pinned->cand_total[b];
+        if (iters > 0) {
+            CK(cudaMemcpyAsync(h_tr_moved.data(), tr_moved.p, sizeof(i64) * iters,
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(h_tr_qn.data(), tr_qn.p, sizeof(i64) * 2 * iters,
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        for (int t = 0; t < iters; t++)
+            res->trace.push_back(
+                TraceRec{level, t + 1, h_tr_moved[t], limbs_to_i128(&h_tr_qn[2 * (size_t)t])});
+        edge_visits += (int64_t)iters * G.nnz;
+        // algorithmic bytes of the sweeps run in this phase (see louvain.h)
+        {
+            const double wb = (double)G.wbytes;
+            const double per_entry = 8.0 + wb;
+            const int64_t nsmall = n - bins.nlist[0] - bins.nlist[1] - bins.nlist[2];
+            double kb[4];
+            kb[0] = (double)n * 16.0 + (double)nsmall * 24.0 + (double)bins.entries[0] * per_entry;
+            kb[1] = (double)bins.nlist[0] * 36.0 + (double)bins.entries[1] * per_entry;
+            kb[2] = (double)bins.nlist[1] * 36.0 + (double)bins.entries[2] * per_entry;
+            kb[3] = (double)bins.nlist[2] * 36.0 + (double)bins.entries[3] * per_entry;
+            for (int b = 0; b < 4; b++) {
+                const double tot = kb[b] * sweeps + 8.0 * (double)cand_level[b];
+                bytes_kernel[b] += tot;
+                alg_bytes += tot;
+                cand_all += cand_level[b];
+            }
+        }
+
+        // renumber (Sec. 5.1.2) -- labels of used communities in increasing order
+        kernels += launch_renumber(n, size.p, new_id.p, scratch32.p, s);
+        const int64_t k = read_one(new_id.p + n);
+        if (k == n) break;  // nothing merged: no new level
+
+        LevelRec rec;
+        rec.ncomm = k;
+        rec.qn = qn_final;
+        rec.qn_init = qn_init;
+        rec.iters = iters;
+        rec.n = n;
+        rec.nnz = G.nnz;
+        rec.hit_cap = hit_cap;
+        rec.d_labels = (int32_t *)A.get(sizeof(int32_t) * (size_t)n0);
+        res->levels.push_back(rec);
+        kernels += launch_compose(n0, prev_labels, st.C, new_id.p, rec.d_labels, s, lc);
+        prev_labels = rec.d_labels;
+
+        // Algorithm 2 outer test from the second level on
+        if (level >= 1 &&
+            host_below_threshold(qn_final, qn_prev_level, TW, cfg.theta_num, cfg.theta_den))
+            break;
+        qn_prev_level = qn_final;
+        if (level + 1 >= cfg.max_levels) break;
+
+        // ---------------- induce the next graph (Sec. 5.1.2)
+        if (!c_csize.p) {
+            c_csize.reset(&A, n0);
+            c_moff.reset(&A, (size_t)n0 + 1);
+            c_cursor.reset(&A, n0);
+            c_members.reset(&A, n0);
+            c_mpre.reset(&A, (size_t)n0 + 1);
+            c_ccnt.reset(&A, n0);
+            c_clist.reset(&A, n0);
+            c_blist.reset(&A, n0);
+            c_tmp_col.reset(&A, (size_t)nnz);
+            c_tmp_w.reset(&A, (size_t)nnz);
+        }
+        CoarsenBufs cb;
+        cb.csize = c_csize.p;
+        cb.moff = c_moff.p;
+        cb.cursor = c_cursor.p;
+        cb.members = c_members.p;
+        cb.mpre = c_mpre.p;
+        cb.ccnt = c_ccnt.p;
+        cb.tmp_col = c_tmp_col.p;
+        cb.tmp_w = c_tmp_w.p;
+        cb.clist = c_clist.p;
+        cb.blist = c_blist.p;
+        cb.counts = &d_sc->ccounts[0];
+        cb.scratch32 = scratch32.p;
+        cb.scratch64 = scratch64.p;
+        kernels += launch_coarsen_stage1(G, st, new_id.p, k, delta_next.p, cb, s, lc);
+        sync_scalars();
+        const int nsmall_c = h->pinned->ccounts[0];
+        Bins cbig;
+        cbig.chunk = cfg.chunk_entries;
+        cbig.nlist[2] = h->pinned->ccounts[1];
+        cbig.list[2] = cb.blist;
+        cbig.nch = b_nch.p;
+        cbig.chunk_first = b_chunk_first.p;
+        cbig.gcap = b_gcap.p;
+        cbig.goff = b_goff.p;
+        cbig.glog2 = b_glog2.p;
+        cbig.gcnt = b_gcnt.p;
+        cbig.gdone = b_gdone.p;
+        cbig.gloop = b_gloop.p;
+        if (cbig.nlist[2] > 0) {
+            const int nb = cbig.nlist[2];
+            kernels += launch_coarsen_bigprep(k, cb, cbig, s, lc);
+            cbig.nchunks = read_one(b_chunk_first.p + nb);
+            cbig.gslots = read_one(b_goff.p + nb);
+            chunk_b.reset(&A, cbig.nchunks);
+            cbig.chunk_b = chunk_b.p;
+            kernels += launch_big_fill(cbig, s, lc);
+            if (cbig.gslots > 0) {
+                gkeys.reset(&A, cbig.gslots);
+                gvals.reset(&A, cbig.gslots);
+                glist.reset(&A, cbig.gslots);
+                CK(cudaMemsetAsync(gkeys.p, 0xFF, sizeof(int32_t) * cbig.gslots, s));
+                CK(cudaMemsetAsync(gvals.p, 0, sizeof(u64) * cbig.gslots, s));
+            }
+            cbig.gkeys = gkeys.p;
+            cbig.gvals = gvals.p;
+            cbig.glist = glist.p;
+            CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
+            CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
+        }
+        kernels += launch_coarsen_stage2(G, st, new_id.p, k, cb, nsmall_c, cbig, &d_sc->err, s, lc);
+        g_rp_next.reset(&A, (size_t)k + 1);
+        kernels += launch_coarsen_rowptr(k, cb, g_rp_next.p, s);
+        sync_scalars();
+        const int64_t nnz_next = read_one(g_rp_next.p + k);
+        const int wb_next = TW <= INT32_MAX ? 4 : 8;
+        g_col_next.reset(&A, (size_t)nnz_next);
+        g_w_next.reset(&A, (size_t)nnz_next * wb_next);
+        kernels += launch_coarsen_compact(k, cb, g_rp_next.p, g_col_next.p, g_w_next.p, wb_next,
+                                          s, lc);
+        g_rp.swap(g_rp_next);
+        g_col.swap(g_col_next);
+        g_w.swap(g_w_next);
+        g_rp_next.release();
+        g_col_next.release();
+        g_w_next.release();
+        G.n = k;
+        G.nnz = nnz_next;
+        G.rp = g_rp.p;
+        G.col = g_col.p;
+        G.w = g_w.p;
+        G.wbytes = wb_next;
+        if (level == 0) {  // the input copies are no longer needed
+            rp_own.release();
+            col_own.release();
+            w_own.release();
+        }
+    }
+    sync_scalars();
+    res->counters[0] = edge_visits;
+    res->counters[1] = sweeps_launched;
+    res->counters[2] = (int64_t)alg_bytes;
+    res->counters[3] = (int64_t)cand_all;
+    res->counters[4] = kernels;
+    if (tm.on) {
+        int dom = 0;
+        for (int b = 1; b < 4; b++)
+            if (t_kernel[b] > t_kernel[dom]) dom = b;
+        res->times[0] = t_kernel[0] + t_kernel[1] + t_kernel[2] + t_kernel[3];
+        res->times[4] = t_kernel[dom];
+        res->counters[5] = launches_kernel[dom];
+        res->counters[6] = (int64_t)bytes_kernel[dom];
+        res->counters[7] = dom;
+        res->times[5] = t_kernel[0];
+        res->times[6] = t_kernel[1] + t_kernel[2];
+        res->times[7] = t_kernel[3];
+    }
+    (void)levels_run;
+    res->times[3] = now_ms() - wall0;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+int louvain_abi_version(void) { return 1; }
+
+int louvain_config_init(louvain_config *cfg)
+{
+    if (!cfg) return LOUVAIN_ERR_INVALID_ARG;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->struct_size = sizeof(louvain_config);
+    cfg->theta_num = 1;
+    cfg->theta_den = 1000000;
+    cfg->max_iters = 1000;
+    cfg->max_levels = 64;
+    cfg->vertex_following = 1;
+    cfg->vf_all_levels = 0;
+    cfg->checks = 1;
+    cfg->force_int128 = 0;
+    cfg->bin_small = 8;
+    cfg->bin_mid1 = 32;
+    cfg->bin_mid2 = 128;
+    cfg->chunk_entries = 1024;
+    cfg->profile = 0;
+    return LOUVAIN_OK;
+}
+
+static int check_config(louvain_config &c, std::string &msg)
+{
+    if (c.struct_size != sizeof(louvain_config)) {
+        msg = "louvain_config.struct_size mismatch (call louvain_config_init)";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (c.theta_den <= 0 || c.theta_num < 0 || c.theta_den > INT32_MAX || c.theta_num > INT32_MAX) {
+        msg = "theta must be num/den with 0 <= num, 0 < den, both below 2^31";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (c.max_iters < 1 || c.max_iters > 1000000 || c.max_levels < 1 || c.max_levels > 1024) {
+        msg = "max_iters must be in [1, 10^6] and max_levels in [1, 1024]";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (c.checks == 0) c.checks = 1;
+    if (c.bin_small == 0 && c.bin_mid1 == 0 && c.bin_mid2 == 0) {
+        c.bin_small = 8;
+        c.bin_mid1 = 32;
+        c.bin_mid2 = 128;
+    }
+    if (c.bin_small < 0 || c.bin_small > 8 || c.bin_mid1 < c.bin_small || c.bin_mid1 > 32 ||
+        c.bin_mid2 < c.bin_mid1 || c.bin_mid2 > 128) {
+        msg = "bins need 0 <= bin_small <= 8, bin_small <= bin_mid1 <= 32, bin_mid1 <= bin_mid2 <= 128";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (c.chunk_entries == 0) c.chunk_entries = 1024;
+    if (c.chunk_entries < 32 || c.chunk_entries > 4096 ||
+        (c.chunk_entries & (c.chunk_entries - 1)) != 0) {
+        msg = "chunk_entries must be a power of two in [32, 4096]";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    for (int r : c.reserved)
+        if (r != 0) {
+            msg = "reserved config fields must be zero";
+            return LOUVAIN_ERR_INVALID_ARG;
+        }
+    if ((c.alloc == nullptr) != (c.free == nullptr)) {
+        msg = "alloc and free callbacks must be given together";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    return LOUVAIN_OK;
+}
+
+int louvain_create(const louvain_config *cfg, int device, louvain_handle **out)
+{
+    if (!out) return LOUVAIN_ERR_INVALID_ARG;
+    *out = nullptr;
+    louvain_config c;
+    if (cfg) c = *cfg;
+    else louvain_config_init(&c);
+    std::string msg;
+    int rc = check_config(c, msg);
+    if (rc != LOUVAIN_OK) return rc;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return LOUVAIN_ERR_CUDA;
+    }
+    louvain_handle *h = new (std::nothrow) louvain_handle();
+    if (!h) return LOUVAIN_ERR_OOM;
+    h->cfg = c;
+    h->device = device;
+    int sms = 152;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMallocHost((void **)&h->pinned, sizeof(Scalars)) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return LOUVAIN_ERR_CUDA;
+    }
+    h->lc.num_sms = sms;
+    h->lc.max_blocks = sms * 8;
+    *out = h;
+    return LOUVAIN_OK;
+}
+
+void louvain_destroy(louvain_handle *h)
+{
+    if (!h) return;
+    if (h->pinned) cudaFreeHost(h->pinned);
+    delete h;
+}
+
+const char *louvain_last_error(const louvain_handle *h) { return h ? h->err.c_str() : ""; }
+
+int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                const int32_t *weights, int ptr_kind, void *stream, louvain_result **out)
+{
+    if (!h) return LOUVAIN_ERR_INVALID_ARG;
+    h->err.clear();
+    if (!out) {
+        h->err = "out is NULL";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (n < 0 || !row_ptr || (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE)) {
+        h->err = "bad n, row_ptr or ptr_kind";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (n > INT32_MAX) {
+        h->err = "n above 2^31 - 1";
+        return LOUVAIN_ERR_TOO_LARGE;
+    }
+    louvain_result *res = new (std::nothrow) louvain_result();
+    if (!res) return LOUVAIN_ERR_OOM;
+    res->device = h->device;
+    res->ff = h->cfg.free;
+    res->ctx = h->cfg.alloc_ctx;
+    Runner R;
+    R.h = h;
+    R.s = (cudaStream_t)stream;
+    R.A.fa = h->cfg.alloc;
+    R.A.ff = h->cfg.free;
+    R.A.ctx = h->cfg.alloc_ctx;
+    R.A.s = R.s;
+    int rc = LOUVAIN_OK;
+    try {
+        CK(cudaSetDevice(h->device));
+        R.run(n, row_ptr, col_idx, weights, ptr_kind, res);
+    } catch (const LvErr &e) {
+        rc = e.code;
+        h->err = e.msg;
+    } catch (const std::bad_alloc &) {
+        rc = LOUVAIN_ERR_OOM;
+        h->err = "host allocation failed";
+    }
+    if (rc != LOUVAIN_OK) {
+        cudaStreamSynchronize(R.s);
+        cudaGetLastError();
+        louvain_result_free(res);
+        return rc;
+    }
+    *out = res;
+    return LOUVAIN_OK;
+}
+
+int louvain_result_num_levels(const louvain_result *r) { return r ? (int)r->levels.size() : 0; }
+
+int64_t louvain_result_num_vertices(const louvain_result *r) { return r ? r->n0 : 0; }
+
+int louvain_result_labels(const louvain_result *r, int level, const int32_t **labels,
+                          int64_t *ncomm)
+{
+    if (!r || level < 0 || level >= (int)r->levels.size() || !labels)
+        return LOUVAIN_ERR_INVALID_ARG;
+    if (r->host_labels.size() != r->levels.size()) r->host_labels.resize(r->levels.size());
+    std::vector<int32_t> &hl = r->host_labels[level];
+    if (hl.size() != (size_t)r->n0) {
+        hl.resize(r->n0);
+        if (cudaSetDevice(r->device) != cudaSuccess ||
+            cudaMemcpy(hl.data(), r->levels[level].d_labels, sizeof(int32_t) * (size_t)r->n0,
+                       cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            hl.clear();
+            return LOUVAIN_ERR_CUDA;
+        }
+    }
+    *labels = hl.data();
+    if (ncomm) *ncomm = r->levels[level].ncomm;
+    return LOUVAIN_OK;
+}
+
+int louvain_result_labels_device(const louvain_result *r, int level, const int32_t **labels)
+{
+    if (!r || level < 0 || level >= (int)r->levels.size() || !labels)
+        return LOUVAIN_ERR_INVALID_ARG;
+    *labels = r->levels[level].d_labels;
+    return LOUVAIN_OK;
+}
+
+int louvain_result_modularity(const louvain_result *r, int level, double *q, int64_t qn[2],
+                              int64_t qn_init[2], int64_t *tw)
+{
+    if (!r || level < 0 || level >= (int)r->levels.size()) return LOUVAIN_ERR_INVALID_ARG;
+    const LevelRec &L = r->levels[level];
+    if (q) {
+        const i128 tw2 = (i128)r->tw * r->tw;
+        *q = (double)L.qn / (double)tw2;
+    }
+    if (qn) i128_to_limbs(L.qn, qn);
+    if (qn_init) i128_to_limbs(L.qn_init, qn_init);
+    if (tw) *tw = r->tw;
+    return LOUVAIN_OK;
+}
+
+int louvain_result_level_info(const louvain_result *r, int level, int32_t *iters,
+                              int64_t *n_level, int64_t *nnz_level, int64_t *ncomm,
+                              int32_t *hit_iter_cap)
+{
+    if (!r || level < 0 || level >= (int)r->levels.size()) return LOUVAIN_ERR_INVALID_ARG;
+    const LevelRec &L = r->levels[level];
+    if (iters) *iters = L.iters;
+    if (n_level) *n_level = L.n;
+    if (nnz_level) *nnz_level = L.nnz;
+    if (ncomm) *ncomm = L.ncomm;
+    if (hit_iter_cap) *hit_iter_cap = L.hit_cap;
+    return LOUVAIN_OK;
+}
+
+int louvain_result_trace(const louvain_result *r, int64_t *len, int32_t *level, int32_t *iter,
+                         int64_t *moved, int64_t *qn)
+{
+    if (!r) return LOUVAIN_ERR_INVALID_ARG;
+    if (len) *len = (int64_t)r->trace.size();
+    for (size_t t = 0; t < r->trace.size(); t++) {
+        if (level) level[t] = r->trace[t].level;
+        if (iter) iter[t] = r->trace[t].iter;
+        if (moved) moved[t] = r->trace[t].moved;
+        if (qn) i128_to_limbs(r->trace[t].qn, qn + 2 * t);
+    }
+    return LOUVAIN_OK;
+}
+
+int louvain_result_counters(const louvain_result *r, int64_t counters[8], double times_ms[8])
+{
+    if (!r) return LOUVAIN_ERR_INVALID_ARG;
+    for (int k = 0; k < 8; k++) {
+        if (counters) counters[k] = r->counters[k];
+        if (times_ms) times_ms[k] = r->times[k];
+    }
+    return LOUVAIN_OK;
+}
+
+void louvain_result_free(louvain_result *r)
+{
+    if (!r) return;
+    cudaSetDevice(r->device);
+    for (LevelRec &L : r->levels) {
+        if (!L.d_labels) continue;
+        if (r->ff) r->ff(L.d_labels, r->ctx, nullptr);
+        else cudaFreeAsync(L.d_labels, nullptr);
+        L.d_labels = nullptr;
+    }
+    delete r;
+}
+
+}  // extern "C"

@@ -1,0 +1,457 @@
+// k_coarsen.cu -- graph induction between levels (arXiv 1805.10904, Sec. 3 and Sec. 5.1.2
+// "Inducing new graph").
+//
+// With a = new_id[C(u)] the renumbered community of u, the next level's graph is
+//     A'_ab = sum over stored entries (u, v) with new_id[C(u)] = a, new_id[C(v)] = b of A_uv,
+// so an internal edge adds to the loop of its community from both of its stored
+// directions, old loops once, and delta and 2W are preserved.  The paper sorts
+// (source, target) keys and reduces by key; here every community's entries are
+// aggregated directly in a hash table keyed by the target community:
+//   1. community sizes and next-level delta (= deg of the old community),
+//   2. member lists by counting sort, flattened entry offsets of each community,
+//   3. per community: a warp with a shared-memory table (few entries) or CTA chunks with
+//      a shared table merged into a global table (many entries),
+//   4. row offsets by prefix sum, then compaction into the next CSR.
+// Rows of the induced graph are not sorted; nothing downstream depends on their order.
+#include <climits>
+
+#include "lv_common.cuh"
+#include "lv_kernels.h"
+#include "lv_scan.cuh"
+
+namespace lv {
+
+__global__ void k_coarsen_prep(int64_t n, const int32_t *size, const i64 *deg,
+                               const int32_t *new_id, int32_t *csize, i64 *delta_next)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (size[c] > 0) {
+            const int32_t a = new_id[c];
+            csize[a] = size[c];
+            delta_next[a] = deg[c];
+        }
+    }
+}
+
+__global__ void k_coarsen_scatter(int64_t n, const int32_t *C, const int32_t *new_id,
+                                  const int32_t *moff, int32_t *cursor, int32_t *members)
+{
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = new_id[C[u]];
+        const int32_t p = moff[a] + atomicAdd(&cursor[a], 1);
+        members[p] = (int32_t)u;
+    }
+}
+
+struct MemberDegIn {
+    const int32_t *members;
+    const int64_t *rp;
+    __device__ __forceinline__ int64_t operator()(int64_t p) const
+    {
+        const int32_t u = members[p];
+        return rp[u + 1] - rp[u];
+    }
+};
+
+// community entry count E_a = mpre[moff[a+1]] - mpre[moff[a]]
+__device__ __forceinline__ int64_t comm_entries(const int32_t *moff, const int64_t *mpre, int32_t a)
+{
+    return mpre[moff[a + 1]] - mpre[moff[a]];
+}
+
+// counts[0]: warp list, counts[1]: chunked list
+__global__ void __launch_bounds__(kBlock) k_coarsen_bin(int64_t k, const int32_t *moff,
+                                                        const int64_t *mpre, int group_max,
+                                                        int32_t *clist, int32_t *blist,
+                                                        int32_t *counts)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t a0 = (int64_t)blockIdx.x * blockDim.x; a0 < k; a0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = a0 + threadIdx.x;
+        int bin = -1;
+        if (a < k) bin = comm_entries(moff, mpre, (int32_t)a) <= group_max ? 0 : 1;
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const unsigned mask = __ballot_sync(0xffffffffu, bin == b);
+            if (!mask) continue;
+            const int leader = __ffs(mask) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&counts[b], __popc(mask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (bin == b) (b == 0 ? clist : blist)[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)a;
+        }
+    }
+}
+
+__global__ void k_cbig_prep(int nb, const int32_t *blist, const int32_t *moff, const int64_t *mpre,
+                            int64_t k, int chunk, int32_t *nch, int64_t *gcap, int32_t *glog2)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const int64_t e = comm_entries(moff, mpre, blist[b]);
+        const int64_t c = (e + chunk - 1) / chunk;
+        nch[b] = (int32_t)c;
+        if (c > 1) {
+            const int64_t need = 2 * (e < k ? e : k);
+            int l = 1;
+            while (((int64_t)1 << l) < need) l++;
+            gcap[b] = (int64_t)1 << l;
+            glog2[b] = l;
+        } else {
+            gcap[b] = 0;
+            glog2[b] = 0;
+        }
+    }
+}
+
+template <typename WT>
+struct CoarsenArgs {
+    const int64_t *rp;
+    const int32_t *col;
+    const WT *w;
+    const int32_t *C;
+    const int32_t *new_id;
+    const int32_t *moff;
+    const int32_t *members;
+    const int64_t *mpre;
+    int32_t *ccnt;
+    int32_t *tmp_col;
+    u64 *tmp_w;
+    unsigned *err;
+};
+
+// largest p in [lo, hi) with mpre[p] <= t (mpre non-decreasing, mpre[lo] <= t)
+__device__ __forceinline__ int32_t find_member(const int64_t *mpre, int32_t lo, int32_t hi, int64_t t)
+{
+    while (hi - lo > 1) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (mpre[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One warp per community with at most 128 entries: 256-slot shared table per warp.
+template <typename WT>
+__global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, const int32_t *clist,
+                                                          int ncl)
+{
+    constexpr int LOG2CAP = 8, CAP = 1 << LOG2CAP, NG = kBlock / 32;
+    __shared__ int s_keys[NG * CAP];
+    __shared__ u64 s_vals[NG * CAP];
+    __shared__ int s_list[NG * CAP];
+    __shared__ int s_cnt[NG];
+    for (int s = threadIdx.x; s < NG * CAP; s += kBlock) {
+        s_keys[s] = -1;
+        s_vals[s] = 0;
+    }
+    if (threadIdx.x < NG) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *keys = s_keys + g * CAP;
+    u64 *vals = s_vals + g * CAP;
+    int *list = s_list + g * CAP;
+    int *cnt = &s_cnt[g];
+    for (int base = blockIdx.x * NG; base < ncl; base += gridDim.x * NG) {
+        const int vi = base + g;
+        const bool valid = vi < ncl;
+        int32_t a = 0, pb = 0, pe = 0;
+        int64_t tb = 0, te = 0;
+        if (valid) {
+            a = clist[vi];
+            pb = A.moff[a];
+            pe = A.moff[a + 1];
+            tb = A.mpre[pb];
+            te = A.mpre[pe];
+        }
+        int32_t p = pb;
+        for (int64_t t = tb + lane; t < te; t += 32) {
+            if (A.mpre[p + 1] <= t) p = find_member(A.mpre, p + 1, pe, t);
+            const int32_t u = A.members[p];
+            const int64_t kk = A.rp[u] + (t - A.mpre[p]);
+            const int32_t key = A.new_id[A.C[A.col[kk]]];
+            sh_insert<LOG2CAP>(keys, vals, list, cnt, key, (u64)A.w[kk], A.err);
+        }
+        __syncwarp();
+        const int m = valid ? *(volatile int *)cnt : 0;
+        for (int q = lane; q < m; q += 32) {
+            const int s = list[q];
+            A.tmp_col[tb + q] = keys[s];
+            A.tmp_w[tb + q] = vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+        }
+        if (lane == 0) {
+            if (valid) A.ccnt[a] = m;
+            *cnt = 0;
+        }
+        __syncwarp();
+    }
+}
+
+struct CBigArgs {
+    const int32_t *blist;
+    const int32_t *chunk_b;
+    const int32_t *chunk_first;
+    const int32_t *nch;
+    const int64_t *goff;
+    const int32_t *glog2;
+    int32_t *gcnt;
+    int32_t *gdone;
+    int32_t *gkeys;
+    u64 *gvals;
+    int32_t *glist;
+    int chunk;
+    int nchunks;
+};
+
+__device__ __forceinline__ void shc_insert(int *keys, u64 *vals, int *list, int *cnt, int log2cap,
+                                           int key, u64 val, unsigned *err)
+{
+    const unsigned cap = 1u << log2cap;
+    unsigned h = hash_slot(key, log2cap);
+#pragma unroll 1
+    for (unsigned probe = 0; probe < cap; probe++) {
+        int k = ((volatile int *)keys)[h];
+        if (k == key) {
+            atomicAdd(&vals[h], val);
+            return;
+        }
+        if (k == -1) {
+            int old = atomicCAS(&keys[h], -1, key);
+            if (old == -1) {
+                int p = atomicAdd(cnt, 1);
+                list[p] = (int)h;
+                atomicAdd(&vals[h], val);
+                return;
+            }
+            if (old == key) {
+                atomicAdd(&vals[h], val);
+                return;
+            }
+        }
+        h = (h + 1) & (cap - 1);
+    }
+    atomicOr(err, ERRF_HASH_FULL);
+}
+
+// Communities with many entries: CTA chunks of `chunk` flattened entries.
+template <typename WT>
+__global__ void __launch_bounds__(kBlock) k_coarsen_big(CoarsenArgs<WT> A, CBigArgs B)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int log2cap = 31 - __clz(2 * B.chunk);
+    const int cap = 1 << log2cap;
+    u64 *vals = (u64 *)smem;
+    int *keys = (int *)(vals + cap);
+    int *list = keys + cap;
+    __shared__ int s_cnt;
+    __shared__ int s_last;
+    for (int s = threadIdx.x; s < cap; s += kBlock) {
+        keys[s] = -1;
+        vals[s] = 0;
+    }
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int c = blockIdx.x; c < B.nchunks; c += gridDim.x) {
+        const int b = B.chunk_b[c];
+        const int32_t a = B.blist[b];
+        const int q = c - B.chunk_first[b];
+        const int nch = B.nch[b];
+        const int32_t pb = A.moff[a], pe = A.moff[a + 1];
+        const int64_t tb = A.mpre[pb], te = A.mpre[pe];
+        const int64_t cb = tb + (int64_t)q * B.chunk;
+        const int64_t ce = min(te, cb + (int64_t)B.chunk);
+        int32_t p = pb;
+        for (int64_t t = cb + threadIdx.x; t < ce; t += kBlock) {
+            if (A.mpre[p + 1] <= t) p = find_member(A.mpre, p + 1, pe, t);
+            const int32_t u = A.members[p];
+            const int64_t kk = A.rp[u] + (t - A.mpre[p]);
+            const int32_t key = A.new_id[A.C[A.col[kk]]];
+            shc_insert(keys, vals, list, &s_cnt, log2cap, key, (u64)A.w[kk], A.err);
+        }
+        __syncthreads();
+        const int m = s_cnt;
+        if (nch == 1) {
+            for (int r = threadIdx.x; r < m; r += kBlock) {
+                const int s = list[r];
+                A.tmp_col[tb + r] = keys[s];
+                A.tmp_w[tb + r] = vals[s];
+                keys[s] = -1;
+                vals[s] = 0;
+            }
+            if (threadIdx.x == 0) A.ccnt[a] = m;
+        } else {
+            const int64_t off = B.goff[b];
+            const int l2 = B.glog2[b];
+            int32_t *gk = B.gkeys + off;
+            u64 *gv = B.gvals + off;
+            int32_t *gl = B.glist + off;
+            for (int r = threadIdx.x; r < m; r += kBlock) {
+                const int s = list[r];
+                const int32_t key = keys[s];
+                const u64 v = vals[s];
+                keys[s] = -1;
+                vals[s] = 0;
+                g_insert(gk, gv, gl, &B.gcnt[b], l2, key, v, A.err);
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int t = atomicAdd(&B.gdone[b], 1);
+                s_last = (t == nch - 1);
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                const int gm = __ldcg(&B.gcnt[b]);
+                for (int r = threadIdx.x; r < gm; r += kBlock) {
+                    const int s = __ldcg(gl + r);
+                    A.tmp_col[tb + r] = __ldcg(gk + s);
+                    A.tmp_w[tb + r] = __ldcg(gv + s);
+                    gk[s] = -1;
+                    gv[s] = 0;
+                }
+                if (threadIdx.x == 0) {
+                    A.ccnt[a] = gm;
+                    B.gcnt[b] = 0;
+                    B.gdone[b] = 0;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+    }
+}
+
+template <typename WO>
+__global__ void __launch_bounds__(kBlock) k_coarsen_compact(int64_t k, const int32_t *moff,
+                                                            const int64_t *mpre,
+                                                            const int64_t *rp_next,
+                                                            const int32_t *tmp_col,
+                                                            const u64 *tmp_w, int32_t *col_next,
+                                                            WO *w_next)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = warp; a < k; a += nwarps) {
+        const int64_t src = mpre[moff[a]];
+        const int64_t dst = rp_next[a];
+        const int64_t m = rp_next[a + 1] - dst;
+        for (int64_t q = lane; q < m; q += 32) {
+            col_next[dst + q] = tmp_col[src + q];
+            w_next[dst + q] = (WO)tmp_w[src + q];
+        }
+    }
+}
+
+struct I32AsI64In {
+    const int32_t *a;
+    __device__ __forceinline__ int64_t operator()(int64_t i) const { return (int64_t)a[i]; }
+};
+
+// ------------------------------------------------------------------ launchers
+
+int launch_coarsen_stage1(const DevGraph &g, const PhaseState &st, const int32_t *new_id,
+                          int64_t k, i64 *delta_next, CoarsenBufs &cb, cudaStream_t s,
+                          const LaunchCfg &lc)
+{
+    int launched = 0;
+    const int64_t n = g.n;
+    k_coarsen_prep<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(n, st.size, st.deg,
+                                                                        new_id, cb.csize,
+                                                                        delta_next);
+    launched++;
+    launched += exclusive_scan<int32_t>(ArrayIn<int32_t>{cb.csize}, k, cb.moff, cb.scratch32, s);
+    cudaMemsetAsync(cb.cursor, 0, sizeof(int32_t) * (size_t)k, s);
+    k_coarsen_scatter<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        n, st.C, new_id, cb.moff, cb.cursor, cb.members);
+    launched++;
+    launched += exclusive_scan<int64_t>(MemberDegIn{cb.members, g.rp}, n, cb.mpre, cb.scratch64, s);
+    cudaMemsetAsync(cb.counts, 0, sizeof(int32_t) * 4, s);
+    k_coarsen_bin<<<grid_for(k, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        k, cb.moff, cb.mpre, 128, cb.clist, cb.blist, cb.counts);
+    launched++;
+    return launched;
+}
+
+inline size_t cbig_smem_bytes(int chunk) { return (size_t)(2 * chunk) * 16; }
+
+template <typename WT>
+static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *new_id, int64_t k,
+                       CoarsenBufs &cb, int nsmall, Bins &big, unsigned *err, cudaStream_t s,
+                       const LaunchCfg &lc)
+{
+    CoarsenArgs<WT> A{g.rp,       g.col,       (const WT *)g.w, st.C,       new_id, cb.moff,
+                      cb.members, cb.mpre,     cb.ccnt,         cb.tmp_col, cb.tmp_w, err};
+    int launched = 0;
+    if (nsmall > 0) {
+        k_coarsen_group<WT><<<grid_for(nsmall, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(
+            A, cb.clist, nsmall);
+        launched++;
+    }
+    if (big.nchunks > 0) {
+        CBigArgs B{cb.blist, big.chunk_b, big.chunk_first, big.nch,   big.goff,
+                   big.glog2, big.gcnt,   big.gdone,       big.gkeys, big.gvals,
+                   big.glist, big.chunk,  big.nchunks};
+        const size_t smem = cbig_smem_bytes(big.chunk);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_coarsen_big<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        const int grid = big.nchunks < lc.max_blocks ? big.nchunks : lc.max_blocks;
+        k_coarsen_big<WT><<<grid, kBlock, smem, s>>>(A, B);
+        launched++;
+    }
+    return launched;
+}
+
+// Prepares the chunk lists of the big communities (big.nlist[2] = their count, big.list[2]
+// = cb.blist) and runs the aggregation.  The host must have filled big.nch etc. through
+// launch_coarsen_bigprep first; see the engine.
+int launch_coarsen_stage2(const DevGraph &g, const PhaseState &st, const int32_t *new_id,
+                          int64_t k, CoarsenBufs &cb, int nsmall, Bins &big, unsigned *err,
+                          cudaStream_t s, const LaunchCfg &lc)
+{
+    if (g.wbytes == 4) return stage2_impl<int32_t>(g, st, new_id, k, cb, nsmall, big, err, s, lc);
+    return stage2_impl<i64>(g, st, new_id, k, cb, nsmall, big, err, s, lc);
+}
+
+int launch_coarsen_bigprep(int64_t k, CoarsenBufs &cb, Bins &big, cudaStream_t s,
+                           const LaunchCfg &lc)
+{
+    const int nb = big.nlist[2];
+    if (nb == 0) return 0;
+    k_cbig_prep<<<grid_for(nb, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        nb, cb.blist, cb.moff, cb.mpre, k, big.chunk, big.nch, big.gcap, big.glog2);
+    int launched = 1;
+    launched += exclusive_scan<int32_t>(ArrayIn<int32_t>{big.nch}, nb, big.chunk_first,
+                                        cb.scratch32, s);
+    launched += exclusive_scan<int64_t>(ArrayIn<int64_t>{big.gcap}, nb, big.goff, cb.scratch64, s);
+    return launched;
+}
+
+int launch_coarsen_rowptr(int64_t k, CoarsenBufs &cb, int64_t *rp_next, cudaStream_t s)
+{
+    return exclusive_scan<int64_t>(I32AsI64In{cb.ccnt}, k, rp_next, cb.scratch64, s);
+}
+
+int launch_coarsen_compact(int64_t k, const CoarsenBufs &cb, const int64_t *rp_next,
+                           int32_t *col_next, void *w_next, int wbytes_next, cudaStream_t s,
+                           const LaunchCfg &lc)
+{
+    if (k == 0) return 0;
+    const int grid = grid_for(k, kBlock / 32, lc.max_blocks);
+    if (wbytes_next == 4)
+        k_coarsen_compact<int32_t><<<grid, kBlock, 0, s>>>(k, cb.moff, cb.mpre, rp_next,
+                                                           cb.tmp_col, cb.tmp_w, col_next,
+                                                           (int32_t *)w_next);
+    else
+        k_coarsen_compact<i64><<<grid, kBlock, 0, s>>>(k, cb.moff, cb.mpre, rp_next, cb.tmp_col,
+                                                       cb.tmp_w, col_next, (i64 *)w_next);
+    return 1;
+}
+
+}  // namespace lv

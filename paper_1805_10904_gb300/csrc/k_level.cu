@@ -1,0 +1,467 @@
+// k_level.cu -- per-level kernels around the local-moving sweep.
+//
+//   validation of the input CSR (Sec. 2 graph model),
+//   weighted degrees delta_i and 2W (Sec. 2, "initStatus" of Sec. 5.1.2),
+//   degree-one vertex following (Lu et al.; Sec. 7 "other heuristics"),
+//   degree binning of the vertices (Sec. 6.3: group vertices of similar degree),
+//   the phase controller (Algorithm 1 stopping rule on exact Qn = (2W)^2 Q, Eq. 3),
+//   applying a sweep's moves with deg_C / size_C updates (Sec. 5.1.2 "oneLevelKernel"),
+//   renumbering by prefix-sum compaction and label composition (Sec. 5.1.2).
+#include "lv_common.cuh"
+#include "lv_kernels.h"
+#include "lv_scan.cuh"
+
+namespace lv {
+
+// ------------------------------------------------------------------ validation
+
+__global__ void __launch_bounds__(kBlock) k_validate_rowptr(const int64_t *rp, int64_t n,
+                                                            unsigned *err)
+{
+    unsigned bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i == 0 && rp[0] != 0) bad |= ERRF_ROWPTR;
+        if (rp[i + 1] < rp[i]) bad |= ERRF_ROWPTR;
+    }
+    if (bad) atomicOr(err, bad);
+}
+
+int launch_validate_rowptr(const int64_t *rp, int64_t n, unsigned *err, cudaStream_t s,
+                           const LaunchCfg &lc)
+{
+    if (n == 0) return 0;
+    k_validate_rowptr<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(rp, n, err);
+    return 1;
+}
+
+__global__ void k_fill_ones(int32_t *w, int64_t nnz)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x)
+        w[k] = 1;
+}
+
+int launch_fill_ones(int32_t *w, int64_t nnz, cudaStream_t s, const LaunchCfg &lc)
+{
+    if (nnz == 0) return 0;
+    k_fill_ones<<<grid_for(nnz, kBlock, lc.max_blocks), kBlock, 0, s>>>(w, nnz);
+    return 1;
+}
+
+// delta_i = sum of row i's weights (loop once), 2W = sum delta; columns and weights
+// checked on the way.  One warp per row.
+template <typename WT>
+__global__ void __launch_bounds__(kBlock) k_row_sums(int64_t n, const int64_t *rp,
+                                                     const int32_t *col, const WT *w, i64 *delta,
+                                                     u64 *tw, unsigned *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned bad = 0;
+    u64 tot = 0;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int64_t b = rp[i], e = rp[i + 1];
+        u64 s = 0;
+        for (int64_t k = b + lane; k < e; k += 32) {
+            const int32_t j = col[k];
+            const i64 x = (i64)w[k];
+            if ((uint32_t)j >= (uint64_t)n) bad |= ERRF_INDEX;
+            if (x < 1) bad |= ERRF_WEIGHT;
+            s += (u64)x;
+        }
+        s = sum_reduce(s, 32);
+        if (lane == 0) {
+            delta[i] = (i64)s;
+            tot += s;
+        }
+    }
+    if (lane == 0 && tot) atomicAdd(tw, tot);
+    if (bad) atomicOr(err, bad);
+}
+
+int launch_row_sums(const DevGraph &g, i64 *delta, u64 *tw, unsigned *err, cudaStream_t s,
+                    const LaunchCfg &lc)
+{
+    if (g.n == 0) return 0;
+    const int grid = grid_for(g.n, kBlock / 32, lc.max_blocks);
+    if (g.wbytes == 4)
+        k_row_sums<int32_t><<<grid, kBlock, 0, s>>>(g.n, g.rp, g.col, (const int32_t *)g.w,
+                                                    delta, tw, err);
+    else
+        k_row_sums<i64><<<grid, kBlock, 0, s>>>(g.n, g.rp, g.col, (const i64 *)g.w, delta, tw,
+                                                err);
+    return 1;
+}
+
+// Full input checks: every row strictly increasing (sorted, no duplicate), and every
+// entry (i, j, w) has a mirror (j, i, w) found by binary search in row j.
+template <typename WT>
+__global__ void __launch_bounds__(kBlock) k_check_symmetry(int64_t n, const int64_t *rp,
+                                                           const int32_t *col, const WT *w,
+                                                           unsigned *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned bad = 0;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int64_t b = rp[i], e = rp[i + 1];
+        for (int64_t k = b + lane; k < e; k += 32) {
+            const int32_t j = col[k];
+            if ((uint32_t)j >= (uint64_t)n) {
+                bad |= ERRF_INDEX;
+                continue;
+            }
+            if (k + 1 < e && col[k + 1] <= j) bad |= ERRF_DUP;
+            int64_t lo = rp[j], hi = rp[j + 1];
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (col[mid] < (int32_t)i) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo >= rp[j + 1] || col[lo] != (int32_t)i || w[lo] != w[k]) bad |= ERRF_ASYM;
+        }
+    }
+    if (bad) atomicOr(err, bad);
+}
+
+int launch_check_symmetry(const DevGraph &g, unsigned *err, cudaStream_t s, const LaunchCfg &lc)
+{
+    if (g.n == 0) return 0;
+    const int grid = grid_for(g.n, kBlock / 32, lc.max_blocks);
+    if (g.wbytes == 4)
+        k_check_symmetry<int32_t><<<grid, kBlock, 0, s>>>(g.n, g.rp, g.col,
+                                                          (const int32_t *)g.w, err);
+    else
+        k_check_symmetry<i64><<<grid, kBlock, 0, s>>>(g.n, g.rp, g.col, (const i64 *)g.w, err);
+    return 1;
+}
+
+// ------------------------------------------------------------------ phase state
+
+__global__ void k_init_state(int64_t n, int32_t *C, i64 *deg, int32_t *size, const i64 *delta)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        C[i] = (int32_t)i;
+        deg[i] = delta[i];
+        size[i] = 1;
+    }
+}
+
+int launch_init_state(int64_t n, const PhaseState &st, cudaStream_t s, const LaunchCfg &lc)
+{
+    if (n == 0) return 0;
+    k_init_state<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(n, st.C, st.deg, st.size,
+                                                                      st.delta);
+    return 1;
+}
+
+// If v has exactly one non-loop neighbour, return 1 and put it in *other.
+__device__ __forceinline__ int sole_neighbour(const int64_t *rp, const int32_t *col, int32_t v,
+                                              int32_t *other)
+{
+    const int64_t b = rp[v], len = rp[v + 1] - b;
+    if (len == 1) {
+        const int32_t c0 = col[b];
+        if (c0 != v) {
+            *other = c0;
+            return 1;
+        }
+        return 0;
+    }
+    if (len == 2) {
+        const int32_t c0 = col[b], c1 = col[b + 1];
+        if (c0 == v && c1 != v) {
+            *other = c1;
+            return 1;
+        }
+        if (c1 == v && c0 != v) {
+            *other = c0;
+            return 1;
+        }
+    }
+    return 0;
+}
+
+// Vertex following: a vertex whose only non-loop neighbour is j joins j's singleton
+// community; an isolated pair joins the smaller id.  Targets never follow anyone, so
+// the deg/size updates below commute.  Runs right after k_init_state.
+__global__ void k_vertex_following(int64_t n, const int64_t *rp, const int32_t *col,
+                                   const i64 *delta, int32_t *C, i64 *deg, int32_t *size)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t j;
+        if (!sole_neighbour(rp, col, (int32_t)i, &j)) continue;
+        int32_t j2;
+        const int32_t t = sole_neighbour(rp, col, j, &j2) ? min((int32_t)i, j) : j;
+        if (t == (int32_t)i) continue;
+        const i64 d = delta[i];
+        C[i] = t;
+        atomicAdd((u64 *)&deg[t], (u64)d);
+        atomicAdd((u64 *)&deg[i], (u64)(-d));
+        atomicAdd(&size[t], 1);
+        atomicSub(&size[i], 1);
+    }
+}
+
+int launch_vertex_following(const DevGraph &g, const PhaseState &st, cudaStream_t s,
+                            const LaunchCfg &lc)
+{
+    if (g.n == 0) return 0;
+    k_vertex_following<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        g.n, g.rp, g.col, st.delta, st.C, st.deg, st.size);
+    return 1;
+}
+
+// ------------------------------------------------------------------ degree bins
+// counts[0..2]: list sizes; counts[4..11]: entries of the small, mid1, mid2 and big rows as
+// 64-bit values (two int32 slots each).
+__global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, int small_max,
+                                                int mid1, int mid2, int32_t *l0, int32_t *l1,
+                                                int32_t *l2, int32_t *counts)
+{
+    const int lane = threadIdx.x & 31;
+    u64 ent[4] = {0, 0, 0, 0};
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        int bin = -2;
+        if (i < n) {
+            const int64_t d = rp[i + 1] - rp[i];
+            bin = d <= small_max ? -1 : d <= mid1 ? 0 : d <= mid2 ? 1 : 2;
+            ent[bin + 1] += (u64)d;
+        }
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const unsigned mask = __ballot_sync(0xffffffffu, bin == b);
+            if (!mask) continue;
+            const int leader = __ffs(mask) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&counts[b], __popc(mask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (bin == b) {
+                int32_t *l = b == 0 ? l0 : b == 1 ? l1 : l2;
+                l[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        u64 v = sum_reduce(ent[b], 32);
+        if (lane == 0 && v) atomicAdd((u64 *)(counts + 4 + 2 * b), v);
+    }
+}
+
+int launch_bin(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc)
+{
+    cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * 12, s);
+    if (g.n == 0) return 0;
+    k_bin<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        g.n, g.rp, b.small_max, b.mid1, b.mid2, b.list[0], b.list[1], b.list[2], b.counts);
+    return 1;
+}
+
+// Big rows: chunk counts and, for multi-chunk rows, a global table of 2^k >= 2*min(d, n)
+// slots (distinct neighbour labels <= min(d, n) < slots, so it never fills).
+__global__ void k_big_prep(int nb, const int32_t *bverts, const int64_t *rp, int64_t n, int chunk,
+                           int32_t *nch, int64_t *gcap, int32_t *glog2)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const int32_t v = bverts[b];
+        const int64_t d = rp[v + 1] - rp[v];
+        const int64_t c = (d + chunk - 1) / chunk;
+        nch[b] = (int32_t)c;
+        if (c > 1) {
+            const int64_t need = 2 * (d < n ? d : n);
+            int l = 1;
+            while (((int64_t)1 << l) < need) l++;
+            gcap[b] = (int64_t)1 << l;
+            glog2[b] = l;
+        } else {
+            gcap[b] = 0;
+            glog2[b] = 0;
+        }
+    }
+}
+
+int launch_big_prep(const DevGraph &g, Bins &b, int64_t *scratch64, int32_t *scratch32,
+                    cudaStream_t s, const LaunchCfg &lc)
+{
+    const int nb = b.nlist[2];
+    if (nb == 0) return 0;
+    k_big_prep<<<grid_for(nb, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        nb, b.list[2], g.rp, g.n, b.chunk, b.nch, b.gcap, b.glog2);
+    int k = 1;
+    k += exclusive_scan<int32_t>(ArrayIn<int32_t>{b.nch}, nb, b.chunk_first, scratch32, s);
+    k += exclusive_scan<int64_t>(ArrayIn<int64_t>{b.gcap}, nb, b.goff, scratch64, s);
+    return k;
+}
+
+__global__ void k_big_fill(int nb, const int32_t *nch, const int32_t *chunk_first, int32_t *chunk_b)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int b = warp; b < nb; b += nwarps)
+        for (int q = lane; q < nch[b]; q += 32) chunk_b[chunk_first[b] + q] = b;
+}
+
+int launch_big_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc)
+{
+    const int nb = b.nlist[2];
+    if (nb == 0) return 0;
+    k_big_fill<<<grid_for(nb, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(nb, b.nch,
+                                                                           b.chunk_first, b.chunk_b);
+    return 1;
+}
+
+// ------------------------------------------------------------------ phase controller
+
+// (qn_new - qn_old) * den < num * tw^2, exact: both sides formed in 192 bits.
+__device__ bool dev_below_threshold(i128 qn_new, i128 qn_old, i64 tw, i64 num, i64 den)
+{
+    const i128 diff = qn_new - qn_old;
+    if (diff < 0) return true;
+    const u128 tw2 = (u128)(u64)tw * (u64)tw;
+    const u128 x = (u128)diff;
+    // x * den and tw2 * num as (high 64, low 128)
+    const u128 xl = (u128)(u64)x * (u64)den, xh = (u128)(u64)(x >> 64) * (u64)den;
+    const u128 yl = (u128)(u64)tw2 * (u64)num, yh = (u128)(u64)(tw2 >> 64) * (u64)num;
+    const u128 xmid = (xl >> 64) + (u64)xh, ymid = (yl >> 64) + (u64)yh;
+    const u64 x2 = (u64)(xh >> 64) + (u64)(xmid >> 64), y2 = (u64)(yh >> 64) + (u64)(ymid >> 64);
+    const u64 x1 = (u64)xmid, y1 = (u64)ymid, x0 = (u64)xl, y0 = (u64)yl;
+    if (x2 != y2) return x2 < y2;
+    if (x1 != y1) return x1 < y1;
+    return x0 < y0;
+}
+
+// Runs after sweep k (1-based) on state C_{k-1}; the sweep measured Qn(C_{k-1}) and
+// proposed C_k.  Stopping rule (Algorithm 1 with the absolute threshold on exact Qn):
+//   k >= 2: stop with C_{k-1} if Qn(C_{k-1}) - Qn(C_{k-2}) is below theta, or if k-1
+//           sweeps reached the cap;
+//   stop with C_{k-1} = C_k if sweep k moved nobody.
+// Otherwise the proposal is applied by k_apply.  The trace gets (moved, Qn) of every
+// applied sweep.
+__global__ void k_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_qn,
+                         u64 *cand_total)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (!ctl->done) {
+        const i128 sq = (i128)(((u128)st->sq_hi << 64) | (u128)st->sq_lo);
+        const i128 qn = (i128)ctl->tw * (i128)(i64)st->internal - sq;
+        const int k = ctl->sweep + 1;
+        const i64 moved = (i64)st->moved;
+        bool stop = false;
+        int iters = 0;
+        for (int b = 0; b < 4; b++) cand_total[b] += st->cand[b];
+        if (k == 1) {
+            i128_to(qn, ctl->qn_init);
+        } else {
+            const int t = k - 2;
+            if (t < ctl->max_iters + 1) {
+                tr_moved[t] = ctl->moved_last;
+                i128_to(qn, &tr_qn[2 * t]);
+            }
+            if (dev_below_threshold(qn, i128_from(ctl->qn_prev), ctl->tw, ctl->theta_num,
+                                    ctl->theta_den)) {
+                stop = true;
+                iters = k - 1;
+            } else if (k - 1 >= ctl->max_iters) {
+                stop = true;
+                iters = k - 1;
+                ctl->hit_cap = 1;
+            }
+        }
+        if (!stop && moved == 0) {
+            const int t = k - 1;
+            if (t < ctl->max_iters + 1) {
+                tr_moved[t] = 0;
+                i128_to(qn, &tr_qn[2 * t]);
+            }
+            stop = true;
+            iters = k;
+        }
+        if (stop) {
+            ctl->done = 1;
+            ctl->iters = iters;
+            i128_to(qn, ctl->qn_final);
+        } else {
+            i128_to(qn, ctl->qn_prev);
+            ctl->moved_last = moved;
+            ctl->sweep = k;
+        }
+    }
+    st->internal = 0;
+    st->sq_lo = 0;
+    st->sq_hi = 0;
+    st->moved = 0;
+    for (int b = 0; b < 4; b++) st->cand[b] = 0;
+}
+
+int launch_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_qn, u64 *cand_total,
+                  cudaStream_t s)
+{
+    k_decide<<<1, 32, 0, s>>>(st, ctl, tr_moved, tr_qn, cand_total);
+    return 1;
+}
+
+// Apply the sweep's proposal (unless the controller stopped the phase): deg_C and size_C
+// follow the moved vertices (the paper's remove / insert with atomics), then C <- C_next.
+__global__ void __launch_bounds__(kBlock) k_apply(int64_t n, int32_t *C, const int32_t *Cnext,
+                                                  i64 *deg, int32_t *size, const i64 *delta,
+                                                  const LevelCtl *ctl)
+{
+    if (*(volatile const int *)&ctl->done) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = C[i], b = Cnext[i];
+        if (a == b) continue;
+        const i64 d = delta[i];
+        atomicAdd((u64 *)&deg[b], (u64)d);
+        atomicAdd((u64 *)&deg[a], (u64)(-d));
+        atomicAdd(&size[b], 1);
+        atomicSub(&size[a], 1);
+        C[i] = b;
+    }
+}
+
+int launch_apply(int64_t n, const PhaseState &st, const LevelCtl *ctl, cudaStream_t s,
+                 const LaunchCfg &lc)
+{
+    if (n == 0) return 0;
+    k_apply<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(n, st.C, st.Cnext, st.deg,
+                                                                 st.size, st.delta, ctl);
+    return 1;
+}
+
+// ------------------------------------------------------------------ renumber / compose
+
+// new_id[c] = number of non-empty communities below c; new_id[n] = their count.
+int launch_renumber(int64_t n, const int32_t *size, int32_t *new_id, int32_t *scratch,
+                    cudaStream_t s)
+{
+    return exclusive_scan<int32_t>(PositiveFlagIn<int32_t, int32_t>{size}, n, new_id, scratch, s);
+}
+
+__global__ void k_compose(int64_t n0, const int32_t *prev, const int32_t *C,
+                          const int32_t *new_id, int32_t *out)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n0;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = prev ? prev[v] : (int32_t)v;
+        out[v] = new_id[C[u]];
+    }
+}
+
+int launch_compose(int64_t n0, const int32_t *prev, const int32_t *C, const int32_t *new_id,
+                   int32_t *out, cudaStream_t s, const LaunchCfg &lc)
+{
+    if (n0 == 0) return 0;
+    k_compose<<<grid_for(n0, kBlock, lc.max_blocks), kBlock, 0, s>>>(n0, prev, C, new_id, out);
+    return 1;
+}
+
+}  // namespace lv

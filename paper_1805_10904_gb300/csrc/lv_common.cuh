@@ -1,0 +1,267 @@
+// lv_common.cuh -- device helpers shared by the kernels of the Louvain library.
+//
+// Exact integer arithmetic throughout (arXiv 1805.10904, Eq. 3-4 rescaled by (2W)^2):
+// sums of weights are int64, products of two of them are int64 when (2W)^2 < 2^63 and
+// __int128 otherwise (the GT template parameter of the move kernels).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lv {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+typedef unsigned long long u64;
+typedef long long i64;
+
+constexpr int kBlock = 256;  // threads per CTA of every kernel unless stated
+
+// error bits raised by device code into a per-run error word
+enum : unsigned {
+    ERRF_INDEX = 1u,      // column outside [0, n)
+    ERRF_WEIGHT = 2u,     // weight < 1
+    ERRF_HASH_FULL = 4u,  // open-addressing probe ran through a whole table
+    ERRF_ROWPTR = 8u,     // row_ptr[0] != 0 or decreasing
+    ERRF_ASYM = 16u,      // A_ij != A_ji (full checks)
+    ERRF_DUP = 32u,       // unsorted or duplicate column in a row (full checks)
+    ERRF_INTERNAL = 64u,  // consistency check failed
+};
+
+// Per-sweep accumulators, zeroed by the decide kernel after it reads them.
+struct SweepStats {
+    u64 internal;  // sum_i e_{i->C(i)} including loops (Eq. 3 first term / TW)
+    u64 sq_lo;     // sum_c deg_c^2 as a 128-bit value
+    u64 sq_hi;
+    u64 moved;     // vertices whose proposed label differs from the current one
+    u64 cand[4];   // distinct neighbouring communities summed over the vertices of the
+                   // small, mid1, mid2 and big kernels
+};
+
+// Level controller state (one per phase), read and written by the decide kernel.
+struct LevelCtl {
+    i64 tw;
+    i64 theta_num;
+    i64 theta_den;
+    int max_iters;
+    int sweep;     // sweeps applied so far in this phase
+    int done;      // 1 once the phase has stopped
+    int hit_cap;
+    int iters;     // sweeps applied when the phase stopped
+    int pad0;
+    i64 moved_last;
+    i64 qn_init[2];   // {hi, lo}
+    i64 qn_prev[2];
+    i64 qn_final[2];
+    i64 pad1[4];
+};
+
+__device__ __forceinline__ i128 i128_from(const i64 v[2])
+{
+    return (i128)(((u128)(u64)v[0] << 64) | (u128)(u64)v[1]);
+}
+
+__device__ __forceinline__ void i128_to(i128 x, i64 v[2])
+{
+    v[0] = (i64)(x >> 64);
+    v[1] = (i64)(u64)x;
+}
+
+// ---------------------------------------------------------------- shuffles
+__device__ __forceinline__ i64 shfl_xor(i64 v, int m, int width = 32)
+{
+    return __shfl_xor_sync(0xffffffffu, v, m, width);
+}
+__device__ __forceinline__ u64 shfl_xor(u64 v, int m, int width = 32)
+{
+    return __shfl_xor_sync(0xffffffffu, v, m, width);
+}
+__device__ __forceinline__ int shfl_xor(int v, int m, int width = 32)
+{
+    return __shfl_xor_sync(0xffffffffu, v, m, width);
+}
+__device__ __forceinline__ i128 shfl_xor(i128 v, int m, int width = 32)
+{
+    u64 lo = (u64)v;
+    i64 hi = (i64)(v >> 64);
+    lo = __shfl_xor_sync(0xffffffffu, lo, m, width);
+    hi = __shfl_xor_sync(0xffffffffu, hi, m, width);
+    return (i128)(((u128)(u64)hi << 64) | (u128)lo);
+}
+__device__ __forceinline__ u128 shfl_xor(u128 v, int m, int width = 32)
+{
+    u64 lo = (u64)v, hi = (u64)(v >> 64);
+    lo = __shfl_xor_sync(0xffffffffu, lo, m, width);
+    hi = __shfl_xor_sync(0xffffffffu, hi, m, width);
+    return ((u128)hi << 64) | (u128)lo;
+}
+
+template <typename GT>
+__device__ __forceinline__ GT gain_min();
+template <>
+__device__ __forceinline__ i64 gain_min<i64>()
+{
+    return (i64)0x8000000000000000ULL;
+}
+template <>
+__device__ __forceinline__ i128 gain_min<i128>()
+{
+    return (i128)((u128)1 << 127);
+}
+
+// Argmax order of Eq. 5 with the Sec. 3.1.2 tie rule: larger gain first, then smaller label.
+template <typename GT>
+__device__ __forceinline__ bool better(GT g1, int c1, GT g2, int c2)
+{
+    return g1 > g2 || (g1 == g2 && c1 < c2);
+}
+
+// Reduce (gain, label) to the group's argmax over `width` lanes (width a power of two <= 32;
+// every lane of the warp must call this).
+template <typename GT>
+__device__ __forceinline__ void argmax_reduce(GT &g, int &c, int width)
+{
+    for (int off = width >> 1; off > 0; off >>= 1) {
+        GT g2 = shfl_xor(g, off, width);
+        int c2 = shfl_xor(c, off, width);
+        if (better(g2, c2, g, c)) {
+            g = g2;
+            c = c2;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T sum_reduce(T v, int width)
+{
+    for (int off = width >> 1; off > 0; off >>= 1) v += shfl_xor(v, off, width);
+    return v;
+}
+
+// 128-bit unsigned atomic add over two 64-bit words (carry applied per addition).
+__device__ __forceinline__ void atomic_add_u128(u64 *lo, u64 *hi, u128 v)
+{
+    u64 vlo = (u64)v, vhi = (u64)(v >> 64);
+    if (vlo) {
+        u64 old = atomicAdd(lo, vlo);
+        if (old + vlo < old) vhi += 1;
+    }
+    if (vhi) atomicAdd(hi, vhi);
+}
+
+// Block-wide sums of up to four u64 counters and one u128, thread 0 publishes with atomics.
+__device__ __forceinline__ void block_flush_stats(SweepStats *st, int slot, u64 internal,
+                                                  u64 moved, u64 cand, u128 sq)
+{
+    __shared__ u64 s_red[kBlock / 32][5];
+    internal = sum_reduce(internal, 32);
+    moved = sum_reduce(moved, 32);
+    cand = sum_reduce(cand, 32);
+    u128 sqr = sum_reduce(sq, 32);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_red[warp][0] = internal;
+        s_red[warp][1] = moved;
+        s_red[warp][2] = cand;
+        s_red[warp][3] = (u64)sqr;
+        s_red[warp][4] = (u64)(sqr >> 64);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u64 a = 0, b = 0, c = 0;
+        u128 s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            a += s_red[w][0];
+            b += s_red[w][1];
+            c += s_red[w][2];
+            s += ((u128)s_red[w][4] << 64) | (u128)s_red[w][3];
+        }
+        if (a) atomicAdd(&st->internal, a);
+        if (b) atomicAdd(&st->moved, b);
+        if (c) atomicAdd(&st->cand[slot], c);
+        if (s) atomic_add_u128(&st->sq_lo, &st->sq_hi, s);
+    }
+}
+
+// ---------------------------------------------------------------- hashing
+// Multiplicative (Fibonacci) hashing of a community label into a power-of-two table.
+__device__ __forceinline__ unsigned hash_slot(int key, int log2cap)
+{
+    return log2cap == 0 ? 0u : ((unsigned)key * 2654435761u) >> (32 - log2cap);
+}
+
+// Shared-memory open-addressing insert-or-add.  `list` records the slot of every key
+// the first time it is claimed (count in *cnt), so the table can be walked and cleared
+// in O(distinct keys).  A table larger than the number of distinct keys never fills.
+template <int LOG2CAP>
+__device__ __forceinline__ void sh_insert(int *keys, u64 *vals, int *list, int *cnt, int key,
+                                          u64 val, unsigned *err)
+{
+    constexpr unsigned CAP = 1u << LOG2CAP;
+    unsigned h = hash_slot(key, LOG2CAP);
+#pragma unroll 1
+    for (unsigned probe = 0; probe < CAP; probe++) {
+        int k = ((volatile int *)keys)[h];
+        if (k == key) {
+            atomicAdd(&vals[h], val);
+            return;
+        }
+        if (k == -1) {
+            int old = atomicCAS(&keys[h], -1, key);
+            if (old == -1) {
+                int p = atomicAdd(cnt, 1);
+                list[p] = (int)h;
+                atomicAdd(&vals[h], val);
+                return;
+            }
+            if (old == key) {
+                atomicAdd(&vals[h], val);
+                return;
+            }
+        }
+        h = (h + 1) & (CAP - 1);
+    }
+    atomicOr(err, ERRF_HASH_FULL);
+}
+
+// Global-memory variant (table of 2^log2cap slots at keys/vals/list + off).
+__device__ __forceinline__ void g_insert(int *keys, u64 *vals, int *list, int *cnt, int log2cap,
+                                         int key, u64 val, unsigned *err)
+{
+    const unsigned cap = 1u << log2cap;
+    unsigned h = hash_slot(key, log2cap);
+#pragma unroll 1
+    for (unsigned probe = 0; probe < cap; probe++) {
+        int k = __ldcg(keys + h);
+        if (k == key) {
+            atomicAdd(vals + h, val);
+            return;
+        }
+        if (k == -1) {
+            int old = atomicCAS(keys + h, -1, key);
+            if (old == -1) {
+                int p = atomicAdd(cnt, 1);
+                list[p] = (int)h;
+                atomicAdd(vals + h, val);
+                return;
+            }
+            if (old == key) {
+                atomicAdd(vals + h, val);
+                return;
+            }
+        }
+        h = (h + 1) & (cap - 1);
+    }
+    atomicOr(err, ERRF_HASH_FULL);
+}
+
+// ---------------------------------------------------------------- launch helpers
+inline int grid_for(int64_t work_items, int per_block, int max_blocks)
+{
+    int64_t g = (work_items + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+}  // namespace lv

@@ -1,0 +1,324 @@
+"""Thin ctypes binding of the C ABI in include/louvain.h (argument marshalling only).
+
+Every step of community detection runs in the CUDA library; this module passes
+pointers, sizes and the current torch stream, and lets the library allocate device
+memory through PyTorch's caching allocator.  If the library has not been built the
+import of the binding succeeds but every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libgb300louvain.so")
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_NOT_SYMMETRIC = 2
+ERR_DUPLICATE_EDGE = 3
+ERR_BAD_WEIGHT = 4
+ERR_INDEX_RANGE = 5
+ERR_OOM = 6
+ERR_CUDA = 7
+ERR_TIMEOUT = 8
+ERR_INTERNAL = 9
+PENDING = 10
+ERR_REJECTED = 11
+ERR_TOO_LARGE = 12
+PTR_HOST = 0
+PTR_DEVICE = 1
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("theta_num", ctypes.c_int64),
+        ("theta_den", ctypes.c_int64),
+        ("max_iters", ctypes.c_int32),
+        ("max_levels", ctypes.c_int32),
+        ("vertex_following", ctypes.c_int32),
+        ("vf_all_levels", ctypes.c_int32),
+        ("checks", ctypes.c_int32),
+        ("force_int128", ctypes.c_int32),
+        ("bin_small", ctypes.c_int32),
+        ("bin_mid1", ctypes.c_int32),
+        ("bin_mid2", ctypes.c_int32),
+        ("chunk_entries", ctypes.c_int32),
+        ("profile", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
+        ("alloc", ALLOC_FN),
+        ("free", FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class LouvainError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"louvain error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load the CUDA library; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library missing at {LIB_PATH}: run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    lib.louvain_abi_version.restype = ctypes.c_int
+    lib.louvain_config_init.argtypes = [ctypes.POINTER(Config)]
+    lib.louvain_create.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(P)]
+    lib.louvain_destroy.argtypes = [P]
+    lib.louvain_destroy.restype = None
+    lib.louvain_last_error.argtypes = [P]
+    lib.louvain_last_error.restype = ctypes.c_char_p
+    lib.louvain_run.argtypes = [P, i64, P, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
+    lib.louvain_result_num_levels.argtypes = [P]
+    lib.louvain_result_num_vertices.argtypes = [P]
+    lib.louvain_result_num_vertices.restype = i64
+    lib.louvain_result_labels.argtypes = [P, ctypes.c_int, ctypes.POINTER(P), P]
+    lib.louvain_result_labels_device.argtypes = [P, ctypes.c_int, ctypes.POINTER(P)]
+    lib.louvain_result_modularity.argtypes = [P, ctypes.c_int, P, P, P, P]
+    lib.louvain_result_level_info.argtypes = [P, ctypes.c_int, P, P, P, P, P]
+    lib.louvain_result_trace.argtypes = [P, P, P, P, P, P]
+    lib.louvain_result_counters.argtypes = [P, P, P]
+    lib.louvain_result_free.argtypes = [P]
+    lib.louvain_result_free.restype = None
+    _lib = lib
+    return lib
+
+
+def _i128(hi, lo) -> int:
+    return (int(hi) << 64) | (int(lo) & 0xFFFFFFFFFFFFFFFF)
+
+
+def _ptr_of(a):
+    """(pointer, kind, keepalive) of a torch tensor or numpy array."""
+    if a is None:
+        return None, None, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                a = a.contiguous()
+            return a.data_ptr(), (PTR_DEVICE if a.is_cuda else PTR_HOST), a
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(a)
+    return a.ctypes.data, PTR_HOST, a
+
+
+@dataclass
+class Level:
+    ncomm: int
+    q: float
+    qn: int
+    qn_init: int
+    iters: int
+    n: int
+    nnz: int
+    hit_iter_cap: bool
+
+
+class Result:
+    """Owns a louvain_result*; labels are copied to the host on first access."""
+
+    def __init__(self, lib, ptr, owner=None):
+        self._lib = lib
+        self._p = ptr
+        # the handle owns the allocator callbacks that free this result's device memory
+        self._owner = owner
+
+    def close(self):
+        if self._p:
+            self._lib.louvain_result_free(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_levels(self) -> int:
+        return self._lib.louvain_result_num_levels(self._p)
+
+    @property
+    def n(self) -> int:
+        return self._lib.louvain_result_num_vertices(self._p)
+
+    def labels(self, level: int) -> np.ndarray:
+        p = ctypes.c_void_p()
+        rc = self._lib.louvain_result_labels(self._p, level, ctypes.byref(p), None)
+        if rc != OK:
+            raise LouvainError(rc, "louvain_result_labels")
+        n = self.n
+        return np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ctypes.c_int32)),
+                                     shape=(n,)).copy() if n else np.zeros(0, np.int32)
+
+    def labels_device_ptr(self, level: int) -> int:
+        p = ctypes.c_void_p()
+        rc = self._lib.louvain_result_labels_device(self._p, level, ctypes.byref(p))
+        if rc != OK:
+            raise LouvainError(rc, "louvain_result_labels_device")
+        return p.value or 0
+
+    def level(self, level: int) -> Level:
+        q = ctypes.c_double()
+        qn = np.zeros(2, np.int64)
+        qi = np.zeros(2, np.int64)
+        tw = ctypes.c_int64()
+        rc = self._lib.louvain_result_modularity(self._p, level, ctypes.addressof(q),
+                                                 qn.ctypes.data, qi.ctypes.data,
+                                                 ctypes.addressof(tw))
+        if rc != OK:
+            raise LouvainError(rc, "louvain_result_modularity")
+        it = ctypes.c_int32()
+        nl = ctypes.c_int64()
+        ml = ctypes.c_int64()
+        nc = ctypes.c_int64()
+        cap = ctypes.c_int32()
+        self._lib.louvain_result_level_info(self._p, level, ctypes.addressof(it),
+                                            ctypes.addressof(nl), ctypes.addressof(ml),
+                                            ctypes.addressof(nc), ctypes.addressof(cap))
+        return Level(nc.value, q.value, _i128(*qn), _i128(*qi), it.value, nl.value, ml.value,
+                     bool(cap.value))
+
+    def levels(self) -> List[Level]:
+        return [self.level(l) for l in range(self.num_levels)]
+
+    @property
+    def tw(self) -> int:
+        tw = ctypes.c_int64()
+        if self.num_levels == 0:
+            return 0
+        self._lib.louvain_result_modularity(self._p, 0, None, None, None, ctypes.addressof(tw))
+        return tw.value
+
+    def trace(self):
+        ln = ctypes.c_int64()
+        self._lib.louvain_result_trace(self._p, ctypes.addressof(ln), None, None, None, None)
+        T = ln.value
+        lv = np.zeros(T, np.int32)
+        it = np.zeros(T, np.int32)
+        mv = np.zeros(T, np.int64)
+        qn = np.zeros(2 * T, np.int64)
+        if T:
+            self._lib.louvain_result_trace(self._p, None, lv.ctypes.data, it.ctypes.data,
+                                           mv.ctypes.data, qn.ctypes.data)
+        return [(int(lv[t]), int(it[t]), int(mv[t]), _i128(qn[2 * t], qn[2 * t + 1]))
+                for t in range(T)]
+
+    def counters(self):
+        c = np.zeros(8, np.int64)
+        t = np.zeros(8, np.float64)
+        self._lib.louvain_result_counters(self._p, c.ctypes.data, t.ctypes.data)
+        return c, t
+
+
+class Louvain:
+    """A library handle bound to one CUDA device.
+
+    torch_alloc=True routes the library's device allocations through PyTorch's
+    caching allocator (so PyTorch owns device memory); otherwise the library uses
+    stream-ordered cudaMallocAsync.
+    """
+
+    def __init__(self, device: int = 0, theta=(1, 1_000_000), max_iters: int = 1000,
+                 max_levels: int = 64, vertex_following: bool = True,
+                 vf_all_levels: bool = False, checks: int = 1, force_int128: bool = False,
+                 bin_small: int = 0, bin_mid1: int = 0, bin_mid2: int = 0,
+                 chunk_entries: int = 0, profile: bool = False, torch_alloc: bool = True):
+        lib = load()
+        self._lib = lib
+        cfg = Config()
+        lib.louvain_config_init(ctypes.byref(cfg))
+        cfg.theta_num, cfg.theta_den = int(theta[0]), int(theta[1])
+        cfg.max_iters = max_iters
+        cfg.max_levels = max_levels
+        cfg.vertex_following = int(vertex_following)
+        cfg.vf_all_levels = int(vf_all_levels)
+        cfg.checks = checks
+        cfg.force_int128 = int(force_int128)
+        if bin_small or bin_mid1 or bin_mid2:
+            cfg.bin_small, cfg.bin_mid1, cfg.bin_mid2 = bin_small, bin_mid1, bin_mid2
+        if chunk_entries:
+            cfg.chunk_entries = chunk_entries
+        cfg.profile = int(profile)
+        self.device = device
+        if torch_alloc:
+            import torch
+
+            def _alloc(size, ctx, stream):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(size), device,
+                                                              int(stream or 0))
+                except Exception:
+                    return None
+
+            def _free(ptr, ctx, stream):
+                try:
+                    torch.cuda.caching_allocator_delete(int(ptr))
+                except Exception:
+                    pass
+
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+            cfg.alloc, cfg.free = self._cb
+        self._cfg = cfg
+        h = ctypes.c_void_p()
+        rc = lib.louvain_create(ctypes.byref(cfg), device, ctypes.byref(h))
+        if rc != OK:
+            raise LouvainError(rc, "louvain_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.louvain_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return (self._lib.louvain_last_error(self._h) or b"").decode()
+
+    def run(self, row_ptr, col_idx, weights=None, stream: Optional[int] = None) -> Result:
+        """Multi-level Louvain on a symmetric CSR (torch CUDA tensors: read in place;
+        torch CPU tensors or numpy arrays: copied inside the call)."""
+        rp, k1, keep1 = _ptr_of(row_ptr)
+        col, k2, keep2 = _ptr_of(col_idx)
+        w, k3, keep3 = _ptr_of(weights)
+        kinds = {k for k in (k1, k2, k3) if k is not None}
+        if len(kinds) != 1:
+            raise ValueError("row_ptr, col_idx and weights must all be on the host or all on the device")
+        n = int(keep1.shape[0]) - 1
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(self.device).cuda_stream
+            except Exception:
+                stream = 0
+        out = ctypes.c_void_p()
+        rc = self._lib.louvain_run(self._h, n, rp, col, w, kinds.pop(), ctypes.c_void_p(stream),
+                                   ctypes.byref(out))
+        if rc != OK:
+            raise LouvainError(rc, self.last_error())
+        return Result(self._lib, out, self)

@@ -1,0 +1,86 @@
+"""The C-ABI library loads and exports every symbol that include/*.h declares.
+
+Runs without a GPU: it builds the library (nvcc cross-compiles for sm_103a), loads it,
+and calls only host-side entry points.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \t\*]*?\b(louvain_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1805_10904_gb300.build import build
+    path = build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["louvain_create", "louvain_run", "louvain_destroy", "louvain_result_labels",
+                     "louvain_result_modularity", "louvain_last_error", "louvain_config_init"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_config_defaults(lib):
+    from paper_1805_10904_gb300.louvain import Config
+    cfg = Config()
+    assert lib.louvain_config_init(ctypes.byref(cfg)) == 0
+    assert cfg.struct_size == ctypes.sizeof(Config)
+    assert (cfg.theta_num, cfg.theta_den) == (1, 1_000_000)
+    assert cfg.max_iters == 1000 and cfg.vertex_following == 1 and cfg.checks == 1
+    assert lib.louvain_config_init(None) == 1
+
+
+def test_invalid_config_rejected_before_any_device_call(lib):
+    from paper_1805_10904_gb300.louvain import Config
+    cfg = Config()
+    lib.louvain_config_init(ctypes.byref(cfg))
+    h = ctypes.c_void_p()
+    bad = Config.from_buffer_copy(cfg)
+    bad.theta_den = 0
+    assert lib.louvain_create(ctypes.byref(bad), 0, ctypes.byref(h)) == 1
+    bad = Config.from_buffer_copy(cfg)
+    bad.chunk_entries = 1000
+    assert lib.louvain_create(ctypes.byref(bad), 0, ctypes.byref(h)) == 1
+    bad = Config.from_buffer_copy(cfg)
+    bad.bin_small = 9
+    assert lib.louvain_create(ctypes.byref(bad), 0, ctypes.byref(h)) == 1
+    assert not h.value
+
+
+def test_null_handle_calls_are_safe(lib):
+    lib.louvain_last_error.restype = ctypes.c_char_p
+    assert lib.louvain_last_error(None) == b""
+    lib.louvain_destroy(None)
+    lib.louvain_result_free(None)
+    assert lib.louvain_result_num_levels(None) == 0
+    assert lib.louvain_run(None, 0, None, None, None, 0, None, None) == 1
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_1805_10904_gb300.louvain as L
+    monkeypatch.setattr(L, "_lib", None)
+    monkeypatch.setattr(L, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="CUDA library missing"):
+        L.load()

@@ -1,0 +1,217 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+Labels are integers decided by exact integer gains, so every level's labels, Qn
+(exact int128), Q (double computed the same way on both sides), sweep counts and the
+per-sweep trace (moved count, Qn) must be identical.  The relative tolerance on Q
+stated for this method is 1e-12; both sides convert the same int128 values, so the
+check below is equality, which implies it.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+Q_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+@pytest.fixture(scope="module")
+def lv():
+    import paper_1805_10904_gb300 as m
+    m.load()
+    return m
+
+
+def to_dev(torch, g):
+    d = torch.device("cuda:0")
+    return (torch.from_numpy(g.rp).to(d), torch.from_numpy(g.col).to(d),
+            torch.from_numpy(g.w).to(d))
+
+
+def assert_parity(res, ref, check_trace=True):
+    assert res.num_levels == len(ref.levels)
+    for l, rl in enumerate(ref.levels):
+        lev = res.level(l)
+        lab = res.labels(l)
+        assert np.array_equal(lab, rl.labels), f"labels differ at level {l}"
+        assert lev.ncomm == rl.ncomm and lev.qn == rl.qn and lev.qn_init == rl.qn_init
+        assert lev.iters == rl.iters and lev.n == rl.n and lev.nnz == rl.nnz
+        assert lev.q == rl.q or abs(lev.q - rl.q) <= Q_RTOL * abs(rl.q)
+    if check_trace:
+        assert res.trace() == ref.trace
+    c, _ = res.counters()
+    assert c[0] == ref.edge_visits
+
+
+def run_both(torch, lv, g, **kw):
+    okw = {k: kw[k] for k in ("theta", "max_iters", "max_levels", "vertex_following",
+                              "vf_all_levels") if k in kw}
+    ref = oracle.louvain(g.rp, g.col, g.w, **okw)
+    h = lv.Louvain(0, **kw)
+    res = h.run(*to_dev(torch, g))
+    return res, ref
+
+
+BIN_CONFIGS = [
+    {},                                                        # default bins
+    {"bin_small": 0, "bin_mid1": 0, "bin_mid2": 0},            # everything through chunks
+    {"bin_small": 1, "bin_mid1": 2, "bin_mid2": 3, "chunk_entries": 32},  # many multi-chunk rows
+    {"bin_small": 8, "bin_mid1": 32, "bin_mid2": 128, "chunk_entries": 4096},
+    {"force_int128": True},
+    {"force_int128": True, "bin_small": 0, "bin_mid1": 0, "bin_mid2": 0, "chunk_entries": 32},
+]
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_fuzz_small_graphs(torch, lv, seed):
+    g = gg.random_small(1000 + seed, n_max=80)
+    kw = dict(BIN_CONFIGS[seed % len(BIN_CONFIGS)])
+    kw["vertex_following"] = seed % 3 != 0
+    kw["vf_all_levels"] = seed % 5 == 0
+    res, ref = run_both(torch, lv, g, **kw)
+    assert_parity(res, ref)
+
+
+@pytest.mark.parametrize("cfg", range(len(BIN_CONFIGS)))
+def test_planted_partition_4096(torch, lv, cfg):
+    """Planted partition: 4,096 vertices, 32 blocks of 128, p_in 0.10, p_out 0.002,
+    weights uniform in [1, 4], threshold 1e-6, full multi-level run."""
+    g = gg.sbm(4096, 128, 0.10, 0.002, 1, 4, seed=1)
+    res, ref = run_both(torch, lv, g, **BIN_CONFIGS[cfg])
+    assert_parity(res, ref)
+
+
+@pytest.mark.parametrize("scale,cfg", [(10, 0), (12, 0), (13, 1), (14, 2), (12, 4), (15, 0)])
+def test_rmat_medium(torch, lv, scale, cfg):
+    """R-MAT graphs (a=.57, b=c=.19): hubs spanning many chunks, isolated vertices,
+    several tiles of every scan and a ragged tail."""
+    g = gg.rmat(scale, 16, seed=100 + scale)
+    res, ref = run_both(torch, lv, g, **BIN_CONFIGS[cfg])
+    assert_parity(res, ref)
+
+
+@pytest.mark.parametrize("n,cfg", [(20_000, 0), (7_777, 2), (30_001, 1)])
+def test_chung_lu(torch, lv, n, cfg):
+    g = gg.chung_lu(n, 2.1, 10.0, 1, 8, seed=n)
+    res, ref = run_both(torch, lv, g, **BIN_CONFIGS[cfg])
+    assert_parity(res, ref)
+
+
+def test_sbm_ragged_blocks(torch, lv):
+    g = gg.sbm(10_007, 300, 0.05, 0.0005, 1, 8, seed=9)
+    res, ref = run_both(torch, lv, g)
+    assert_parity(res, ref)
+
+
+@pytest.mark.parametrize("theta,max_iters,max_levels", [((1, 1000), 1000, 64), ((0, 1), 3, 2),
+                                                        ((1, 10), 1000, 64), ((1, 10**6), 1, 64)])
+def test_thresholds_and_caps(torch, lv, theta, max_iters, max_levels):
+    g = gg.rmat(12, 16, seed=77)
+    res, ref = run_both(torch, lv, g, theta=theta, max_iters=max_iters, max_levels=max_levels)
+    assert_parity(res, ref)
+    if not ref.hit_iter_cap:
+        assert not any(res.level(l).hit_iter_cap for l in range(res.num_levels))
+
+
+def test_hand_worked_cases(torch, lv):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "hand_cases.json")) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        g = gg.from_edges(case["n"], [tuple(e) for e in case["edges"]])
+        h = lv.Louvain(0, vertex_following=case["vertex_following"])
+        res = h.run(*to_dev(torch, g))
+        assert res.num_levels == len(case["levels"])
+        for l, exp in enumerate(case["levels"]):
+            assert res.labels(l).tolist() == exp["labels"]
+            assert res.level(l).qn == exp["qn"]
+        lev0 = [(t[2], t[3]) for t in res.trace() if t[0] == 0]
+        assert lev0 == [(s[1], s[2]) for s in case["sweeps"]]
+
+
+def test_edge_cases(torch, lv):
+    h = lv.Louvain(0)
+    for g in [gg.from_edges(0, []), gg.from_edges(1, []), gg.from_edges(6, []),
+              gg.from_edges(1, [(0, 0, 5)]), gg.from_edges(2, [(0, 1, 1)]),
+              gg.from_edges(3, [(0, 0, 2), (1, 1, 3), (2, 2, 1)]), gg.star(200),
+              gg.from_edges(4, [(0, 1, 2**31 - 1), (2, 3, 2**31 - 1), (1, 2, 1)])]:
+        ref = oracle.louvain(g.rp, g.col, g.w)
+        res = h.run(*to_dev(torch, g))
+        assert_parity(res, ref)
+
+
+def test_host_pointers_match_device_pointers(torch, lv):
+    g = gg.rmat(13, 16, seed=5)
+    h = lv.Louvain(0)
+    a = h.run(*to_dev(torch, g))
+    b = h.run(g.rp, g.col, g.w)
+    assert a.num_levels == b.num_levels
+    for l in range(a.num_levels):
+        assert np.array_equal(a.labels(l), b.labels(l))
+        assert a.level(l).qn == b.level(l).qn
+
+
+def test_unweighted_means_all_ones(torch, lv):
+    g = gg.rmat(11, 8, seed=3)
+    ones = np.ones_like(g.w)
+    ref = oracle.louvain(g.rp, g.col, ones)
+    h = lv.Louvain(0)
+    rp, col, _ = to_dev(torch, g)
+    res = h.run(rp, col, None)
+    assert_parity(res, ref)
+
+
+def test_deterministic_and_allocator_independent(torch, lv):
+    g = gg.rmat(14, 16, seed=8)
+    a = lv.Louvain(0, torch_alloc=True).run(*to_dev(torch, g))
+    b = lv.Louvain(0, torch_alloc=False).run(*to_dev(torch, g))
+    c = lv.Louvain(0).run(*to_dev(torch, g))
+    for r in (b, c):
+        assert r.num_levels == a.num_levels
+        for l in range(a.num_levels):
+            assert np.array_equal(a.labels(l), r.labels(l))
+        assert r.trace() == a.trace()
+
+
+def test_invalid_inputs_are_reported_and_handle_survives(torch, lv):
+    h = lv.Louvain(0, checks=2)
+    g = gg.path(5)
+    rp, col, w = to_dev(torch, g)
+    bad_col = col.clone()
+    bad_col[3] = 99
+    with pytest.raises(lv.LouvainError) as e:
+        h.run(rp, bad_col, w)
+    assert e.value.code == 5
+    bad_w = w.clone()
+    bad_w[0] = 0
+    with pytest.raises(lv.LouvainError) as e:
+        h.run(rp, col, bad_w)
+    assert e.value.code == 4
+    bad_rp = rp.clone()
+    bad_rp[2] = 0
+    with pytest.raises(lv.LouvainError) as e:
+        h.run(bad_rp, col, w)
+    assert e.value.code == 5
+    asym_w = w.clone()
+    asym_w[0] = 7
+    with pytest.raises(lv.LouvainError) as e:
+        h.run(rp, col, asym_w)
+    assert e.value.code == 2
+    dup = gg.Graph(np.array([0, 2, 3], np.int64), np.array([1, 1, 0], np.int32),
+                   np.array([1, 1, 1], np.int32))
+    with pytest.raises(lv.LouvainError) as e:
+        h.run(*to_dev(torch, dup))
+    assert e.value.code in (2, 3)
+    # the handle still works
+    res = h.run(rp, col, w)
+    ref = oracle.louvain(g.rp, g.col, g.w)
+    assert_parity(res, ref)
