@@ -217,11 +217,11 @@ static void vertex_following(const og_graph *g, int32_t *C)
 /* ------------------------------------------------------------------------- */
 
 /* Reads only the snapshot (C, deg, size); writes Cnext.  Returns the number of vertices
- * whose label changed.  e, stamp and touched are n-sized scratch arrays; stamp must hold
- * values < 0 on entry. */
+ * whose label changed.  e, seen and touched are n-sized scratch arrays; seen must be all
+ * zero on entry and is all zero again on return. */
 static int64_t local_move_sweep(const og_graph *g, const int32_t *C, const int64_t *deg,
                                 const int32_t *size, const int64_t *delta, int64_t TW,
-                                int32_t *Cnext, int64_t *e, int64_t *stamp, int32_t *touched)
+                                int32_t *Cnext, int64_t *e, int64_t *seen, int32_t *touched)
 {
     int64_t moved = 0;
     for (int64_t i = 0; i < g->n; i++) {
@@ -232,17 +232,18 @@ static int64_t local_move_sweep(const og_graph *g, const int32_t *C, const int64
             int32_t j = g->col[k];
             if (j == i) continue;
             int32_t c = C[j];
-            if (stamp[c] != i) {
-                stamp[c] = i;
+            if (!seen[c]) {
+                seen[c] = 1;
                 e[c] = 0;
                 touched[m++] = c;
             }
             e[c] += g->w[k];
         }
+        int64_t e_a = seen[a] ? e[a] : 0; /* e_{i -> C(i)\{i}} */
+        for (int64_t t = 0; t < m; t++) seen[touched[t]] = 0; /* e[] stays readable */
         Cnext[i] = a;
         if (m == 0) continue; /* no non-loop neighbour: i stays */
 
-        int64_t e_a = (stamp[a] == i) ? e[a] : 0; /* e_{i -> C(i)\{i}} */
         i128 g_stay = (i128)TW * e_a - (i128)delta[i] * (deg[a] - delta[i]);
 
         int have = 0;
@@ -471,9 +472,9 @@ static int louvain_run_impl(const og_graph *g0, int64_t theta_num, int64_t theta
     int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
     int64_t *deg_tmp = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
     int64_t *e = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
-    int64_t *stamp = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *seen = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
     if (!map0 || !C || !Cnext || !new_id || !size || !size_tmp || !touched || !delta || !deg ||
-        !deg_tmp || !e || !stamp) {
+        !deg_tmp || !e || !seen) {
         rc = ORACLE_ERR_OOM;
         goto done;
     }
@@ -506,13 +507,13 @@ static int louvain_run_impl(const og_graph *g0, int64_t theta_num, int64_t theta
         for (int64_t i = 0; i < n; i++) C[i] = (int32_t)i;
         if (vf && (level == 0 || vf_all)) vertex_following(&g, C);
         community_degrees(n, C, delta, deg, size);
-        for (int64_t i = 0; i < n; i++) stamp[i] = -1;
+        for (int64_t i = 0; i < n; i++) seen[i] = 0;
 
         i128 qn_init = modularity_qn(&g, C, delta, TW, deg_tmp, size_tmp);
         i128 qn_prev = qn_init, qn_new = qn_init;
         int32_t iters = 0;
         for (;;) {
-            int64_t moved = local_move_sweep(&g, C, deg, size, delta, TW, Cnext, e, stamp, touched);
+            int64_t moved = local_move_sweep(&g, C, deg, size, delta, TW, Cnext, e, seen, touched);
             iters += 1;
             r->edge_visits += g.nnz;
             r->sweeps_total += 1;
@@ -575,7 +576,7 @@ done:
     free(deg);
     free(deg_tmp);
     free(e);
-    free(stamp);
+    free(seen);
     return rc;
 }
 
@@ -753,19 +754,19 @@ int64_t oracle_sweep(int64_t n, const int64_t *rp, const int32_t *col, const int
     int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
     int32_t *size = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
     int64_t *e = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
-    int64_t *stamp = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *seen = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
     int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
     weighted_degrees(&g, delta);
     community_degrees(n, C, delta, deg, size);
     int64_t TW = 0;
     for (int64_t v = 0; v < n; v++) TW += delta[v];
-    for (int64_t v = 0; v < n; v++) stamp[v] = -1;
-    int64_t moved = local_move_sweep(&g, C, deg, size, delta, TW, Cnext, e, stamp, touched);
+    for (int64_t v = 0; v < n; v++) seen[v] = 0;
+    int64_t moved = local_move_sweep(&g, C, deg, size, delta, TW, Cnext, e, seen, touched);
     free(delta);
     free(deg);
     free(size);
     free(e);
-    free(stamp);
+    free(seen);
     free(touched);
     graph_free(&g);
     return moved;

@@ -311,3 +311,68 @@ def test_invalid_inputs_rejected():
         oracle.louvain(g.rp, np.array([0, 5, 1, 1], np.int32), g.w)
     with pytest.raises(oracle.OracleError):
         oracle.louvain(g.rp, g.col, np.zeros_like(g.w))
+
+
+# ------------------------------------------- sweep rule and driver consistency ----
+
+def reference_sweep(g, C):
+    """Algorithm 1 body written from the rules, with gains from the pinned oracle.gain:
+    candidates are the communities of non-loop neighbours other than C(i); target = argmax
+    gain, ties to the smaller label (Sec. 3.1.2); move iff gain > 0 (strict) unless both
+    communities are singletons and target > C(i) (Sec. 3.1.1)."""
+    w = g.w.astype(np.int64)
+    size = np.bincount(C, minlength=g.n)
+    out = C.copy()
+    for i in range(g.n):
+        cands = sorted({int(C[j]) for j in g.col[g.rp[i]:g.rp[i + 1]] if j != i} - {int(C[i])})
+        best, best_gain = None, None
+        for b in cands:
+            gain = oracle.gain(g.rp, g.col, w, C, i, b)
+            if best is None or gain > best_gain:
+                best, best_gain = b, gain
+        if best is None or best_gain <= 0:
+            continue
+        if size[C[i]] == 1 and size[best] == 1 and best > C[i]:
+            continue
+        out[i] = best
+    return out
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_sweep_matches_reference_rule(seed):
+    g = gg.random_small(800 + seed, n_max=40)
+    rng = np.random.default_rng(seed)
+    for trial in range(3):
+        C = rng.integers(0, max(1, g.n), size=g.n).astype(np.int32) if trial else \
+            np.arange(g.n, dtype=np.int32)
+        Cn, moved = oracle.sweep(g.rp, g.col, g.w.astype(np.int64), C)
+        ref = reference_sweep(g, C)
+        assert np.array_equal(Cn, ref)
+        assert moved == int((ref != C).sum())
+
+
+@pytest.mark.parametrize("seed,kind", [(s, k) for s in range(4) for k in ("small", "rmat")])
+def test_run_trace_equals_repeated_sweeps(seed, kind):
+    """The multi-sweep driver must equal single sweeps applied one after another, each
+    followed by Eq. 3; this is the phase loop of Algorithm 1 with the stopping rule."""
+    if kind == "small":
+        g = gg.random_small(900 + seed, n_max=60)
+    else:
+        g = gg.rmat(9 + seed % 3, 8, seed=seed)
+    vf = bool(seed % 2)
+    r = oracle.louvain(g.rp, g.col, g.w, max_levels=1, vertex_following=vf)
+    w = g.w.astype(np.int64)
+    C = oracle.vertex_following(g.rp, g.col) if vf else np.arange(g.n, dtype=np.int32)
+    qn_prev, tw = oracle.modularity(g.rp, g.col, w, C)
+    trace = []
+    for it in range(1, 1001):
+        C, moved = oracle.sweep(g.rp, g.col, w, C)
+        qn, _ = oracle.modularity(g.rp, g.col, w, C)
+        trace.append((0, it, moved, qn))
+        if moved == 0 or (qn - qn_prev) * 1_000_000 < tw * tw:
+            break
+        qn_prev = qn
+    assert r.trace == trace
+    if r.levels:
+        new_id, _ = oracle.renumber(C)
+        assert np.array_equal(r.levels[0].labels, new_id[C])
