@@ -54,6 +54,7 @@
  *       neighbour is j joins j's community (j keeps its own singleton label); an isolated
  *       pair (each the other's only neighbour) joins min(i, j).
  *   R12 zero-degree vertices stay singletons at every level.
+ *   R13 a graph without vertices runs no phase (no sweep, no level).
  *
  * Arithmetic: weights, degrees and sums in int64; every product of two of them in
  * __int128.  Nothing here is floating point except the reported Q = (double)Qn / (double)TW^2
@@ -500,7 +501,8 @@ static int louvain_run_impl(const og_graph *g0, int64_t theta_num, int64_t theta
     r->tw = TW;
 
     i128 qn_prev_level = 0;
-    for (int32_t level = 0; level < max_levels; level++) {
+    /* an empty vertex set gives Algorithm 1 nothing to evaluate: no phase is run (R13) */
+    for (int32_t level = 0; level < max_levels && n0 > 0; level++) {
         int64_t n = g.n;
         /* initStatus: singletons, delta from the level's graph (Sec. 5.1.2) */
         weighted_degrees(&g, delta);

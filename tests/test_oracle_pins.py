@@ -303,6 +303,7 @@ def test_trivial_inputs():
     for g in [gg.from_edges(0, []), gg.from_edges(5, []), gg.from_edges(1, [(0, 0, 3)])]:
         r = oracle.louvain(g.rp, g.col, g.w)
         assert r.levels == []
+        assert r.trace == ([] if g.n == 0 else [(0, 1, 0, r.trace[0][3])])
 
 
 def test_invalid_inputs_rejected():
