@@ -47,6 +47,7 @@ def parse_args(argv=None):
     p.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 is the workload)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-sweeps", type=int, default=2)
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer arm (profiling)")
     return p.parse_args(argv)
 
 
@@ -234,6 +235,36 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- native arm
 
+def run_e2e(args, g, lv, local, stream, world, dev):
+    """Same metric through the C ABI with pinned host buffers: the H2D copy of the graph
+    and the D2H copy of every level's labels are inside the timed region."""
+    import torch
+    rp_h = torch.from_numpy(g.rp).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    w_h = torch.from_numpy(g.w).pin_memory()
+    h2 = lv.Louvain(local, profile=False)
+    for _ in range(max(1, args.warmup)):
+        r = h2.run(rp_h, col_h, w_h, stream=stream.cuda_stream)
+        for l in range(r.num_levels):
+            r.labels(l)
+        r.close()
+    barrier(world)
+    e2e_s, e2e_visits, d2h = 0.0, 0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = h2.run(rp_h, col_h, w_h, stream=stream.cuda_stream)
+        out = [r.labels(l) for l in range(r.num_levels)]
+        e2e_s += time.perf_counter() - t0
+        e2e_visits += int(r.counters()[0][0])
+        d2h = sum(a.nbytes for a in out)
+        r.close()
+    e2e_max = reduce_max(e2e_s, world, dev)
+    e2e_all = reduce_sum(float(e2e_visits), world, dev)
+    h2d = g.rp.nbytes + g.col.nbytes + g.w.nbytes
+    return {"value": e2e_all / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -293,28 +324,7 @@ def run_native(args):
     all_visits = reduce_sum(float(visits), world, dev)
 
     # end-to-end through the C ABI with pinned host buffers: H2D inside, labels D2H inside
-    rp_h = torch.from_numpy(g.rp).pin_memory()
-    col_h = torch.from_numpy(g.col).pin_memory()
-    w_h = torch.from_numpy(g.w).pin_memory()
-    h2 = lv.Louvain(local, profile=False)
-    for _ in range(max(1, args.warmup)):
-        r = h2.run(rp_h, col_h, w_h, stream=stream.cuda_stream)
-        for l in range(r.num_levels):
-            r.labels(l)
-        r.close()
-    barrier(world)
-    e2e_s, e2e_visits, d2h = 0.0, 0, 0
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        r = h2.run(rp_h, col_h, w_h, stream=stream.cuda_stream)
-        out = [r.labels(l) for l in range(r.num_levels)]
-        e2e_s += time.perf_counter() - t0
-        e2e_visits += int(r.counters()[0][0])
-        d2h = sum(a.nbytes for a in out)
-        r.close()
-    e2e_max = reduce_max(e2e_s, world, dev)
-    e2e_all = reduce_sum(float(e2e_visits), world, dev)
-    h2d = g.rp.nbytes + g.col.nbytes + g.w.nbytes
+    e2e = run_e2e(args, g, lv, local, stream, world, dev) if not args.no_e2e else None
 
     if rank != 0:
         if world > 1:
@@ -351,8 +361,7 @@ def run_native(args):
                    "levels": levels, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "L2 flushed between timed steps (258 MB write); CSR of 1 GB > L2"},
         "roofline": roofline, "cpu_baseline": cpu,
-        "e2e": {"value": e2e_all / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -68,17 +68,26 @@ typedef struct {
     int32_t checks;            /* 1 (default): index and weight checks; 2: also symmetry,
                                   sortedness and duplicates; 0 is treated as 1             */
     int32_t force_int128;      /* 1: take the int128 gain path even when int64 suffices  */
-    /* degree-bin thresholds (non-loop row length d):
-     *   d <= bin_small -> one thread per vertex (bin_small in [0, 8]),
-     *   d <= bin_mid1  -> 8-lane group, d <= bin_mid2 -> one warp,
-     *   larger         -> CTA chunks of chunk_entries entries, multi-chunk rows use a
-     *                     global-memory hash table.  0 selects the tuned default.      */
+    int32_t wide_sums;         /* 1: 64-bit hash-table sums even when 2W < 2^32 allows 32 */
+    /* degree-bin thresholds on the row length d (entries stored in the row):
+     *   d <= bin_small -> one thread per vertex            (0 <= bin_small <= 8)
+     *   d <= bin_mid1  -> 8 lanes per vertex               (bin_mid1 <= 32)
+     *   d <= bin_mid2  -> one warp per vertex              (bin_mid2 <= 128)
+     *   d <= bin_cta1 / bin_cta2 / bin_cta3 -> one CTA of 128 / 256 / 1024 threads per
+     *                     vertex with a shared-memory table of at least 4/3 d slots
+     *                     (bin_cta3 <= 12288; lowered to 6144 when sums are 64-bit)
+     *   larger         -> CTA chunks of chunk_entries entries merged in a global table.
+     * Thresholds must not decrease.  All zero selects the defaults 8, 32, 128, 512, 2048,
+     * 12288.  The same thresholds bin the communities (by entries) when coarsening. */
     int32_t bin_small;
     int32_t bin_mid1;
     int32_t bin_mid2;
-    int32_t chunk_entries;     /* power of two in [32, 4096]; 0 = default                */
+    int32_t bin_cta1;
+    int32_t bin_cta2;
+    int32_t bin_cta3;
+    int32_t chunk_entries;     /* power of two in [32, 4096]; 0 = default 4096           */
     int32_t profile;           /* 1: time kernel groups with CUDA events (louvain_result_counters) */
-    int32_t reserved[7];       /* must be zero                                           */
+    int32_t reserved[4];       /* must be zero                                           */
     /* device memory: both NULL means stream-ordered cudaMallocAsync/cudaFreeAsync */
     louvain_alloc_fn alloc;
     louvain_free_fn free;
@@ -171,9 +180,9 @@ int louvain_result_trace(const louvain_result *r, int64_t *len, int32_t *level, 
  *   counters[4] kernels launched by the run
  * times_ms[0] local-move kernels (device time), [1] coarsening, [2] everything else on
  * the device, [3] wall time of louvain_run; [4] the dominant local-move kernel alone,
- * [5] the thread-per-vertex kernel, [6] the lane-group kernels, [7] the chunked kernel;
- * counters[5] launches of the dominant kernel, counters[6] its algorithmic bytes,
- * counters[7] which one it is (0 thread-per-vertex, 1 8-lane groups, 2 warps, 3 chunks).
+ * [5] the thread-per-vertex kernel, [6] the lane-group kernels, [7] the CTA and chunk
+ * kernels; counters[5] launches of the dominant kernel, counters[6] its algorithmic bytes,
+ * counters[7] which degree bin it serves (0 thread, 1 8-lane, 2 warp, 3-5 CTA, 6 chunks).
  * Arrays of 8; unused slots are zero.  Device times are filled only when the config had
  * profile = 1. */
 int louvain_result_counters(const louvain_result *r, int64_t counters[8], double times_ms[8]);

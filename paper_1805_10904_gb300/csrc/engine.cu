@@ -114,9 +114,9 @@ struct Scalars {
     u64 tw;
     SweepStats st;
     LevelCtl ctl;
-    int32_t bin_counts[12];
-    int32_t ccounts[4];
-    u64 cand_total[4];
+    int32_t bin_counts[24];
+    int32_t ccounts[8];
+    u64 cand_total[8];
     int32_t tail[8];
 };
 
@@ -338,11 +338,12 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     const i64 TW = (i64)tw_u;
     res->tw = TW;
     const bool wide = cfg.force_int128 || (u128)tw_u * tw_u > (u128)INT64_MAX;
+    const bool narrow = !cfg.wide_sums && tw_u < ((u64)1 << 32);
 
     // ---------------- per-run buffers sized by level 0 (Theorem 1: levels never grow)
     const int64_t scratch_n = scan_scratch_elems(n0 + 1) + 64;
-    DBuf<int32_t> lists[3];
-    for (auto &l : lists) l.reset(&A, n0);
+    DBuf<int32_t> lists;  // bins 1..6, n0 entries each
+    lists.reset(&A, (size_t)n0 * (kNumBins - 1));
     DBuf<int32_t> b_nch, b_chunk_first, b_glog2, b_gcnt, b_gdone;
     DBuf<int64_t> b_gcap, b_goff;
     DBuf<u64> b_gloop;
@@ -364,7 +365,7 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     tr_qn.reset(&A, 2 * (size_t)tcap);
     std::vector<i64> h_tr_moved(tcap), h_tr_qn(2 * (size_t)tcap);
     // coarsening buffers
-    DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_clist, c_blist, c_tmp_col;
+    DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_clist, c_tmp_col;
     DBuf<int64_t> c_mpre;
     DBuf<u64> c_tmp_w;
     // graph buffers of the levels above 0
@@ -376,10 +377,9 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     DBuf<u64> gvals;
 
     SweepTimers tm;
-    std::vector<cudaEvent_t> extra_ev;
-    double t_kernel[4] = {0, 0, 0, 0};
-    int64_t launches_kernel[4] = {0, 0, 0, 0};
-    double bytes_kernel[4] = {0, 0, 0, 0};
+    double t_kernel[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
+    int64_t launches_kernel[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
+    double bytes_kernel[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
     if (cfg.profile) {
         for (auto &e : tm.ev) CK(cudaEventCreate(&e));
         tm.on = true;
@@ -400,22 +400,61 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     st.size = size.p;
     st.delta = delta.p;
 
-    Bins bins;
-    bins.small_max = cfg.bin_small;
-    bins.mid1 = cfg.bin_mid1;
-    bins.mid2 = cfg.bin_mid2;
-    bins.chunk = cfg.chunk_entries;
-    bins.counts = &d_sc->bin_counts[0];
+    // bin thresholds: every table must fit shared memory with the chosen sum width
+    Bins proto;
+    const int32_t thr[kNumBins - 1] = {cfg.bin_small, cfg.bin_mid1, cfg.bin_mid2,
+                                       cfg.bin_cta1,  cfg.bin_cta2, cfg.bin_cta3};
+    for (int t = 0; t < kNumBins - 1; t++) proto.upper[t] = thr[t];
+    if (!narrow && proto.upper[5] > 6144) {
+        proto.upper[5] = 6144;
+        for (int t = 4; t >= 0; t--)
+            if (proto.upper[t] > proto.upper[t + 1]) proto.upper[t] = proto.upper[t + 1];
+    }
+    proto.chunk = cfg.chunk_entries;
+    proto.nch = b_nch.p;
+    proto.chunk_first = b_chunk_first.p;
+    proto.gcap = b_gcap.p;
+    proto.goff = b_goff.p;
+    proto.glog2 = b_glog2.p;
+    proto.gcnt = b_gcnt.p;
+    proto.gdone = b_gdone.p;
+    proto.gloop = b_gloop.p;
+
+    // sets up chunk lists and global tables of bin 6 (after nlist[6] is known)
+    auto prep_huge = [&](Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *cbp) {
+        b.nchunks = 0;
+        b.gslots = 0;
+        const int nb = b.nlist[6];
+        if (nb == 0) return;
+        if (coarsen_side) kernels += launch_coarsen_bigprep(k_comm, *cbp, b, s, lc);
+        else kernels += launch_big_prep(G, b, scratch64.p, scratch32.p, s, lc);
+        b.nchunks = read_one(b_chunk_first.p + nb);
+        b.gslots = read_one(b_goff.p + nb);
+        chunk_b.reset(&A, b.nchunks);
+        b.chunk_b = chunk_b.p;
+        kernels += launch_big_fill(b, s, lc);
+        if (b.gslots > 0) {
+            gkeys.reset(&A, b.gslots);
+            gvals.reset(&A, b.gslots);  // 8 bytes per slot covers both sum widths
+            glist.reset(&A, b.gslots);
+            CK(cudaMemsetAsync(gkeys.p, 0xFF, sizeof(int32_t) * b.gslots, s));
+            CK(cudaMemsetAsync(gvals.p, 0, sizeof(u64) * b.gslots, s));
+        }
+        b.gkeys = gkeys.p;
+        b.gvals = gvals.p;
+        b.glist = glist.p;
+        CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
+        CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
+        CK(cudaMemsetAsync(b_gloop.p, 0, sizeof(u64) * nb, s));
+    };
 
     const int32_t *prev_labels = nullptr;
     i128 qn_prev_level = 0;
     int64_t edge_visits = 0, sweeps_launched = 0;
     double alg_bytes = 0.0;
     u64 cand_all = 0;
-    int levels_run = 0;
 
     for (int level = 0; level < cfg.max_levels; level++) {
-        levels_run++;
         const int64_t n = G.n;
         if (level > 0) {
             delta.swap(delta_next);
@@ -426,46 +465,17 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
             kernels += launch_vertex_following(G, st, s, lc);
 
         // degree bins
-        bins.list[0] = lists[0].p;
-        bins.list[1] = lists[1].p;
-        bins.list[2] = lists[2].p;
+        Bins bins = proto;
+        for (int b = 1; b < kNumBins; b++) bins.list[b] = lists.p + (size_t)(b - 1) * n0;
+        bins.counts = &d_sc->bin_counts[0];
         kernels += launch_bin(G, bins, s, lc);
         sync_scalars();
-        for (int b = 0; b < 3; b++) bins.nlist[b] = h->pinned->bin_counts[b];
-        for (int b = 0; b < 4; b++)
-            memcpy(&bins.entries[b], &h->pinned->bin_counts[4 + 2 * b], sizeof(int64_t));
-        bins.nch = b_nch.p;
-        bins.chunk_first = b_chunk_first.p;
-        bins.gcap = b_gcap.p;
-        bins.goff = b_goff.p;
-        bins.glog2 = b_glog2.p;
-        bins.gcnt = b_gcnt.p;
-        bins.gdone = b_gdone.p;
-        bins.gloop = b_gloop.p;
-        bins.nchunks = 0;
-        bins.gslots = 0;
-        if (bins.nlist[2] > 0) {
-            const int nb = bins.nlist[2];
-            kernels += launch_big_prep(G, bins, scratch64.p, scratch32.p, s, lc);
-            bins.nchunks = read_one(b_chunk_first.p + nb);
-            bins.gslots = read_one(b_goff.p + nb);
-            chunk_b.reset(&A, bins.nchunks);
-            bins.chunk_b = chunk_b.p;
-            kernels += launch_big_fill(bins, s, lc);
-            if (bins.gslots > 0) {
-                gkeys.reset(&A, bins.gslots);
-                gvals.reset(&A, bins.gslots);
-                glist.reset(&A, bins.gslots);
-                CK(cudaMemsetAsync(gkeys.p, 0xFF, sizeof(int32_t) * bins.gslots, s));
-                CK(cudaMemsetAsync(gvals.p, 0, sizeof(u64) * bins.gslots, s));
-            }
-            bins.gkeys = gkeys.p;
-            bins.gvals = gvals.p;
-            bins.glist = glist.p;
-            CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
-            CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
-            CK(cudaMemsetAsync(b_gloop.p, 0, sizeof(u64) * nb, s));
-        }
+        for (int b = 1; b < kNumBins; b++) bins.nlist[b] = h->pinned->bin_counts[b];
+        for (int b = 0; b < kNumBins; b++)
+            memcpy(&bins.entries[b], &h->pinned->bin_counts[8 + 2 * b], sizeof(int64_t));
+        bins.nlist[0] = (int)(n - bins.nlist[1] - bins.nlist[2] - bins.nlist[3] - bins.nlist[4] -
+                              bins.nlist[5] - bins.nlist[6]);
+        prep_huge(bins, false, 0, nullptr);
 
         // phase controller
         LevelCtl ctl;
@@ -478,27 +488,25 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         CK(cudaMemcpyAsync(&d_sc->ctl, &h->pinned->ctl, sizeof(LevelCtl), cudaMemcpyHostToDevice,
                            s));
         CK(cudaMemsetAsync(&d_sc->st, 0, sizeof(SweepStats), s));
-        CK(cudaMemsetAsync(&d_sc->cand_total[0], 0, sizeof(u64) * 4, s));
+        CK(cudaMemsetAsync(&d_sc->cand_total[0], 0, sizeof(u64) * 8, s));
 
         // sweeps (Algorithm 1); one host read of the controller per sweep
         int sweeps = 0;
         for (;;) {
-            kernels += launch_sweep(G, st, bins, TW, wide, &d_sc->st, &d_sc->err, s, lc, &tm);
+            kernels += launch_sweep(G, st, bins, TW, wide, narrow, &d_sc->st, &d_sc->err, s, lc,
+                                    &tm);
             kernels += launch_decide(&d_sc->st, &d_sc->ctl, tr_moved.p, tr_qn.p,
                                      &d_sc->cand_total[0], s);
             kernels += launch_apply(n, st, &d_sc->ctl, s, lc);
             sweeps++;
             sync_scalars();
             if (tm.on) {
-                for (int k = 0; k < 4; k++) {
+                for (int b = 0; b < kNumBins; b++) {
                     float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, tm.ev[2 * k], tm.ev[2 * k + 1]));
-                    t_kernel[k] += ms;
+                    CK(cudaEventElapsedTime(&ms, tm.ev[2 * b], tm.ev[2 * b + 1]));
+                    t_kernel[b] += ms;
+                    launches_kernel[b] += b == 0 ? 1 : (b == 6 ? bins.nchunks > 0 : bins.nlist[b] > 0);
                 }
-                launches_kernel[0] += 1;
-                launches_kernel[1] += bins.nlist[0] > 0;
-                launches_kernel[2] += bins.nlist[1] > 0;
-                launches_kernel[3] += bins.nchunks > 0;
             }
             if (h->pinned->ctl.done) break;
             if (sweeps > cfg.max_iters + 2)
@@ -510,8 +518,8 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         const i128 qn_final = limbs_to_i128(hc.qn_final);
         const i128 qn_init = limbs_to_i128(hc.qn_init);
         const int hit_cap = hc.hit_cap;
-        u64 cand_level[4];
-        for (int b = 0; b < 4; b++) cand_level[b] = h->pinned->cand_total[b];
+        u64 cand_level[8];
+        for (int b = 0; b < 8; b++) cand_level[b] = h->pinned->cand_total[b];
         if (iters > 0) {
             CK(cudaMemcpyAsync(h_tr_moved.data(), tr_moved.p, sizeof(i64) * iters,
                                cudaMemcpyDeviceToHost, s));
@@ -523,18 +531,14 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
             res->trace.push_back(
                 TraceRec{level, t + 1, h_tr_moved[t], limbs_to_i128(&h_tr_qn[2 * (size_t)t])});
         edge_visits += (int64_t)iters * G.nnz;
-        // algorithmic bytes of the sweeps run in this phase (see louvain.h)
+        // algorithmic bytes of the sweeps run in this phase (formula in louvain.h)
         {
-            const double wb = (double)G.wbytes;
-            const double per_entry = 8.0 + wb;
-            const int64_t nsmall = n - bins.nlist[0] - bins.nlist[1] - bins.nlist[2];
-            double kb[4];
-            kb[0] = (double)n * 16.0 + (double)nsmall * 24.0 + (double)bins.entries[0] * per_entry;
-            kb[1] = (double)bins.nlist[0] * 36.0 + (double)bins.entries[1] * per_entry;
-            kb[2] = (double)bins.nlist[1] * 36.0 + (double)bins.entries[2] * per_entry;
-            kb[3] = (double)bins.nlist[2] * 36.0 + (double)bins.entries[3] * per_entry;
-            for (int b = 0; b < 4; b++) {
-                const double tot = kb[b] * sweeps + 8.0 * (double)cand_level[b];
+            const double per_entry = 8.0 + (double)G.wbytes;
+            for (int b = 0; b < kNumBins; b++) {
+                double kb = (double)bins.entries[b] * per_entry;
+                kb += b == 0 ? (double)n * 16.0 + (double)bins.nlist[0] * 24.0
+                             : (double)bins.nlist[b] * 36.0;
+                const double tot = kb * sweeps + 8.0 * (double)cand_level[b];
                 bytes_kernel[b] += tot;
                 alg_bytes += tot;
                 cand_all += cand_level[b];
@@ -574,8 +578,7 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
             c_members.reset(&A, n0);
             c_mpre.reset(&A, (size_t)n0 + 1);
             c_ccnt.reset(&A, n0);
-            c_clist.reset(&A, n0);
-            c_blist.reset(&A, n0);
+            c_clist.reset(&A, (size_t)n0 * 5);
             c_tmp_col.reset(&A, (size_t)nnz);
             c_tmp_w.reset(&A, (size_t)nnz);
         }
@@ -589,47 +592,18 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         cb.tmp_col = c_tmp_col.p;
         cb.tmp_w = c_tmp_w.p;
         cb.clist = c_clist.p;
-        cb.blist = c_blist.p;
         cb.counts = &d_sc->ccounts[0];
         cb.scratch32 = scratch32.p;
         cb.scratch64 = scratch64.p;
-        kernels += launch_coarsen_stage1(G, st, new_id.p, k, delta_next.p, cb, s, lc);
+        kernels += launch_coarsen_stage1(G, st, new_id.p, k, delta_next.p, cb, proto, s, lc);
         sync_scalars();
-        const int nsmall_c = h->pinned->ccounts[0];
-        Bins cbig;
-        cbig.chunk = cfg.chunk_entries;
-        cbig.nlist[2] = h->pinned->ccounts[1];
-        cbig.list[2] = cb.blist;
-        cbig.nch = b_nch.p;
-        cbig.chunk_first = b_chunk_first.p;
-        cbig.gcap = b_gcap.p;
-        cbig.goff = b_goff.p;
-        cbig.glog2 = b_glog2.p;
-        cbig.gcnt = b_gcnt.p;
-        cbig.gdone = b_gdone.p;
-        cbig.gloop = b_gloop.p;
-        if (cbig.nlist[2] > 0) {
-            const int nb = cbig.nlist[2];
-            kernels += launch_coarsen_bigprep(k, cb, cbig, s, lc);
-            cbig.nchunks = read_one(b_chunk_first.p + nb);
-            cbig.gslots = read_one(b_goff.p + nb);
-            chunk_b.reset(&A, cbig.nchunks);
-            cbig.chunk_b = chunk_b.p;
-            kernels += launch_big_fill(cbig, s, lc);
-            if (cbig.gslots > 0) {
-                gkeys.reset(&A, cbig.gslots);
-                gvals.reset(&A, cbig.gslots);
-                glist.reset(&A, cbig.gslots);
-                CK(cudaMemsetAsync(gkeys.p, 0xFF, sizeof(int32_t) * cbig.gslots, s));
-                CK(cudaMemsetAsync(gvals.p, 0, sizeof(u64) * cbig.gslots, s));
-            }
-            cbig.gkeys = gkeys.p;
-            cbig.gvals = gvals.p;
-            cbig.glist = glist.p;
-            CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
-            CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
+        Bins cbins = proto;
+        for (int r = 0; r < 5; r++) {
+            cbins.list[2 + r] = c_clist.p + (size_t)r * k;
+            cbins.nlist[2 + r] = h->pinned->ccounts[r];
         }
-        kernels += launch_coarsen_stage2(G, st, new_id.p, k, cb, nsmall_c, cbig, &d_sc->err, s, lc);
+        prep_huge(cbins, true, k, &cb);
+        kernels += launch_coarsen_stage2(G, st, new_id.p, k, cb, cbins, narrow, &d_sc->err, s, lc);
         g_rp_next.reset(&A, (size_t)k + 1);
         kernels += launch_coarsen_rowptr(k, cb, g_rp_next.p, s);
         sync_scalars();
@@ -665,18 +639,19 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     res->counters[4] = kernels;
     if (tm.on) {
         int dom = 0;
-        for (int b = 1; b < 4; b++)
+        for (int b = 1; b < kNumBins; b++)
             if (t_kernel[b] > t_kernel[dom]) dom = b;
-        res->times[0] = t_kernel[0] + t_kernel[1] + t_kernel[2] + t_kernel[3];
+        double tot = 0;
+        for (int b = 0; b < kNumBins; b++) tot += t_kernel[b];
+        res->times[0] = tot;
         res->times[4] = t_kernel[dom];
+        res->times[5] = t_kernel[0];
+        res->times[6] = t_kernel[1] + t_kernel[2];
+        res->times[7] = t_kernel[3] + t_kernel[4] + t_kernel[5] + t_kernel[6];
         res->counters[5] = launches_kernel[dom];
         res->counters[6] = (int64_t)bytes_kernel[dom];
         res->counters[7] = dom;
-        res->times[5] = t_kernel[0];
-        res->times[6] = t_kernel[1] + t_kernel[2];
-        res->times[7] = t_kernel[3];
     }
-    (void)levels_run;
     res->times[3] = now_ms() - wall0;
 }
 
@@ -701,10 +676,14 @@ int louvain_config_init(louvain_config *cfg)
     cfg->vf_all_levels = 0;
     cfg->checks = 1;
     cfg->force_int128 = 0;
+    cfg->wide_sums = 0;
     cfg->bin_small = 8;
     cfg->bin_mid1 = 32;
     cfg->bin_mid2 = 128;
-    cfg->chunk_entries = 1024;
+    cfg->bin_cta1 = 512;
+    cfg->bin_cta2 = 2048;
+    cfg->bin_cta3 = 12288;
+    cfg->chunk_entries = 4096;
     cfg->profile = 0;
     return LOUVAIN_OK;
 }
@@ -724,17 +703,23 @@ static int check_config(louvain_config &c, std::string &msg)
         return LOUVAIN_ERR_INVALID_ARG;
     }
     if (c.checks == 0) c.checks = 1;
-    if (c.bin_small == 0 && c.bin_mid1 == 0 && c.bin_mid2 == 0) {
+    if (c.bin_small == 0 && c.bin_mid1 == 0 && c.bin_mid2 == 0 && c.bin_cta1 == 0 &&
+        c.bin_cta2 == 0 && c.bin_cta3 == 0) {
         c.bin_small = 8;
         c.bin_mid1 = 32;
         c.bin_mid2 = 128;
+        c.bin_cta1 = 512;
+        c.bin_cta2 = 2048;
+        c.bin_cta3 = 12288;
     }
     if (c.bin_small < 0 || c.bin_small > 8 || c.bin_mid1 < c.bin_small || c.bin_mid1 > 32 ||
-        c.bin_mid2 < c.bin_mid1 || c.bin_mid2 > 128) {
-        msg = "bins need 0 <= bin_small <= 8, bin_small <= bin_mid1 <= 32, bin_mid1 <= bin_mid2 <= 128";
+        c.bin_mid2 < c.bin_mid1 || c.bin_mid2 > 128 || c.bin_cta1 < c.bin_mid2 ||
+        c.bin_cta2 < c.bin_cta1 || c.bin_cta3 < c.bin_cta2 || c.bin_cta3 > 12288) {
+        msg = "bins need 0 <= small <= 8 <= ..., small <= mid1 <= 32, mid1 <= mid2 <= 128, "
+              "mid2 <= cta1 <= cta2 <= cta3 <= 12288";
         return LOUVAIN_ERR_INVALID_ARG;
     }
-    if (c.chunk_entries == 0) c.chunk_entries = 1024;
+    if (c.chunk_entries == 0) c.chunk_entries = 4096;
     if (c.chunk_entries < 32 || c.chunk_entries > 4096 ||
         (c.chunk_entries & (c.chunk_entries - 1)) != 0) {
         msg = "chunk_entries must be a power of two in [32, 4096]";

@@ -61,26 +61,36 @@ __device__ __forceinline__ int64_t comm_entries(const int32_t *moff, const int64
     return mpre[moff[a + 1]] - mpre[moff[a]];
 }
 
-// counts[0]: warp list, counts[1]: chunked list
+// Communities binned by entry count with the sweep's thresholds; bins 0..2 all go to the
+// warp kernel.  clist holds 5 regions of k entries (bins 2..6), counts[r] their sizes.
+struct CBinArgs {
+    int64_t upper[kNumBins - 1];
+};
+
 __global__ void __launch_bounds__(kBlock) k_coarsen_bin(int64_t k, const int32_t *moff,
-                                                        const int64_t *mpre, int group_max,
-                                                        int32_t *clist, int32_t *blist,
-                                                        int32_t *counts)
+                                                        const int64_t *mpre, CBinArgs ba,
+                                                        int32_t *clist, int32_t *counts)
 {
     const int lane = threadIdx.x & 31;
     for (int64_t a0 = (int64_t)blockIdx.x * blockDim.x; a0 < k; a0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = a0 + threadIdx.x;
-        int bin = -1;
-        if (a < k) bin = comm_entries(moff, mpre, (int32_t)a) <= group_max ? 0 : 1;
+        int r = -1;
+        if (a < k) {
+            const int64_t e = comm_entries(moff, mpre, (int32_t)a);
+            int b = 0;
 #pragma unroll
-        for (int b = 0; b < 2; b++) {
-            const unsigned mask = __ballot_sync(0xffffffffu, bin == b);
+            for (int t = 0; t < kNumBins - 1; t++) b += e > ba.upper[t];
+            r = b < 2 ? 0 : b - 2;
+        }
+#pragma unroll
+        for (int b = 0; b < 5; b++) {
+            const unsigned mask = __ballot_sync(0xffffffffu, r == b);
             if (!mask) continue;
             const int leader = __ffs(mask) - 1;
             int base = 0;
             if (lane == leader) base = atomicAdd(&counts[b], __popc(mask));
             base = __shfl_sync(0xffffffffu, base, leader);
-            if (bin == b) (b == 0 ? clist : blist)[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)a;
+            if (r == b) clist[(int64_t)b * k + base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)a;
         }
     }
 }
@@ -132,14 +142,27 @@ __device__ __forceinline__ int32_t find_member(const int64_t *mpre, int32_t lo, 
     return lo;
 }
 
-// One warp per community with at most 128 entries: 256-slot shared table per warp.
+// Entry t of community a's flattened member rows: returns (target community, weight); p is
+// the member index of the previous call (advanced monotonically).
 template <typename WT>
+__device__ __forceinline__ void flat_entry(const CoarsenArgs<WT> &A, int32_t &p, int32_t pe,
+                                           int64_t t, int32_t &key, i64 &wv)
+{
+    if (A.mpre[p + 1] <= t) p = find_member(A.mpre, p + 1, pe, t);
+    const int32_t u = A.members[p];
+    const int64_t kk = A.rp[u] + (t - A.mpre[p]);
+    key = A.new_id[A.C[A.col[kk]]];
+    wv = (i64)A.w[kk];
+}
+
+// One warp per community with few entries: 256-slot shared table per warp.
+template <typename WT, typename VT>
 __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, const int32_t *clist,
                                                           int ncl)
 {
     constexpr int LOG2CAP = 8, CAP = 1 << LOG2CAP, NG = kBlock / 32;
     __shared__ int s_keys[NG * CAP];
-    __shared__ u64 s_vals[NG * CAP];
+    __shared__ VT s_vals[NG * CAP];
     __shared__ int s_list[NG * CAP];
     __shared__ int s_cnt[NG];
     for (int s = threadIdx.x; s < NG * CAP; s += kBlock) {
@@ -150,7 +173,7 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
     __syncthreads();
     const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *keys = s_keys + g * CAP;
-    u64 *vals = s_vals + g * CAP;
+    VT *vals = s_vals + g * CAP;
     int *list = s_list + g * CAP;
     int *cnt = &s_cnt[g];
     for (int base = blockIdx.x * NG; base < ncl; base += gridDim.x * NG) {
@@ -167,18 +190,17 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
         }
         int32_t p = pb;
         for (int64_t t = tb + lane; t < te; t += 32) {
-            if (A.mpre[p + 1] <= t) p = find_member(A.mpre, p + 1, pe, t);
-            const int32_t u = A.members[p];
-            const int64_t kk = A.rp[u] + (t - A.mpre[p]);
-            const int32_t key = A.new_id[A.C[A.col[kk]]];
-            sh_insert<LOG2CAP>(keys, vals, list, cnt, key, (u64)A.w[kk], A.err);
+            int32_t key;
+            i64 wv;
+            flat_entry(A, p, pe, t, key, wv);
+            tbl_insert<false, VT>(keys, vals, list, cnt, LOG2CAP, key, (VT)wv, A.err);
         }
         __syncwarp();
         const int m = valid ? *(volatile int *)cnt : 0;
         for (int q = lane; q < m; q += 32) {
             const int s = list[q];
             A.tmp_col[tb + q] = keys[s];
-            A.tmp_w[tb + q] = vals[s];
+            A.tmp_w[tb + q] = (u64)vals[s];
             keys[s] = -1;
             vals[s] = 0;
         }
@@ -187,6 +209,52 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
             *cnt = 0;
         }
         __syncwarp();
+    }
+}
+
+// One CTA per community with a 2^log2cap-slot table in dynamic shared memory.
+template <int BLOCK, typename WT, typename VT>
+__global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const int32_t *clist,
+                                                       int ncl, int log2cap)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int cap = 1 << log2cap;
+    VT *vals = (VT *)smem;
+    int *keys = (int *)(vals + cap);
+    int *list = keys + cap;
+    __shared__ int s_cnt;
+    for (int s = threadIdx.x; s < cap; s += BLOCK) {
+        keys[s] = -1;
+        vals[s] = 0;
+    }
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int v = blockIdx.x; v < ncl; v += gridDim.x) {
+        const int32_t a = clist[v];
+        const int32_t pb = A.moff[a], pe = A.moff[a + 1];
+        const int64_t tb = A.mpre[pb], te = A.mpre[pe];
+        int32_t p = pb;
+        for (int64_t t = tb + threadIdx.x; t < te; t += BLOCK) {
+            int32_t key;
+            i64 wv;
+            flat_entry(A, p, pe, t, key, wv);
+            tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, (VT)wv, A.err);
+        }
+        __syncthreads();
+        const int m = s_cnt;
+        for (int q = threadIdx.x; q < m; q += BLOCK) {
+            const int s = list[q];
+            A.tmp_col[tb + q] = keys[s];
+            A.tmp_w[tb + q] = (u64)vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            A.ccnt[a] = m;
+            s_cnt = 0;
+        }
+        __syncthreads();
     }
 }
 
@@ -200,55 +268,28 @@ struct CBigArgs {
     int32_t *gcnt;
     int32_t *gdone;
     int32_t *gkeys;
-    u64 *gvals;
+    void *gvals;
     int32_t *glist;
     int chunk;
     int nchunks;
 };
 
-__device__ __forceinline__ void shc_insert(int *keys, u64 *vals, int *list, int *cnt, int log2cap,
-                                           int key, u64 val, unsigned *err)
-{
-    const unsigned cap = 1u << log2cap;
-    unsigned h = hash_slot(key, log2cap);
-#pragma unroll 1
-    for (unsigned probe = 0; probe < cap; probe++) {
-        int k = ((volatile int *)keys)[h];
-        if (k == key) {
-            atomicAdd(&vals[h], val);
-            return;
-        }
-        if (k == -1) {
-            int old = atomicCAS(&keys[h], -1, key);
-            if (old == -1) {
-                int p = atomicAdd(cnt, 1);
-                list[p] = (int)h;
-                atomicAdd(&vals[h], val);
-                return;
-            }
-            if (old == key) {
-                atomicAdd(&vals[h], val);
-                return;
-            }
-        }
-        h = (h + 1) & (cap - 1);
-    }
-    atomicOr(err, ERRF_HASH_FULL);
-}
+constexpr int kCHugeBlock = 512;
 
-// Communities with many entries: CTA chunks of `chunk` flattened entries.
-template <typename WT>
-__global__ void __launch_bounds__(kBlock) k_coarsen_big(CoarsenArgs<WT> A, CBigArgs B)
+// Communities with the most entries: CTA chunks of `chunk` flattened entries merged in a
+// global table; the last chunk to finish writes the community's row.
+template <typename WT, typename VT>
+__global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A, CBigArgs B)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int log2cap = 31 - __clz(2 * B.chunk);
     const int cap = 1 << log2cap;
-    u64 *vals = (u64 *)smem;
+    VT *vals = (VT *)smem;
     int *keys = (int *)(vals + cap);
     int *list = keys + cap;
     __shared__ int s_cnt;
     __shared__ int s_last;
-    for (int s = threadIdx.x; s < cap; s += kBlock) {
+    for (int s = threadIdx.x; s < cap; s += kCHugeBlock) {
         keys[s] = -1;
         vals[s] = 0;
     }
@@ -264,20 +305,19 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_big(CoarsenArgs<WT> A, CBigA
         const int64_t cb = tb + (int64_t)q * B.chunk;
         const int64_t ce = min(te, cb + (int64_t)B.chunk);
         int32_t p = pb;
-        for (int64_t t = cb + threadIdx.x; t < ce; t += kBlock) {
-            if (A.mpre[p + 1] <= t) p = find_member(A.mpre, p + 1, pe, t);
-            const int32_t u = A.members[p];
-            const int64_t kk = A.rp[u] + (t - A.mpre[p]);
-            const int32_t key = A.new_id[A.C[A.col[kk]]];
-            shc_insert(keys, vals, list, &s_cnt, log2cap, key, (u64)A.w[kk], A.err);
+        for (int64_t t = cb + threadIdx.x; t < ce; t += kCHugeBlock) {
+            int32_t key;
+            i64 wv;
+            flat_entry(A, p, pe, t, key, wv);
+            tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, (VT)wv, A.err);
         }
         __syncthreads();
         const int m = s_cnt;
         if (nch == 1) {
-            for (int r = threadIdx.x; r < m; r += kBlock) {
+            for (int r = threadIdx.x; r < m; r += kCHugeBlock) {
                 const int s = list[r];
                 A.tmp_col[tb + r] = keys[s];
-                A.tmp_w[tb + r] = vals[s];
+                A.tmp_w[tb + r] = (u64)vals[s];
                 keys[s] = -1;
                 vals[s] = 0;
             }
@@ -286,15 +326,15 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_big(CoarsenArgs<WT> A, CBigA
             const int64_t off = B.goff[b];
             const int l2 = B.glog2[b];
             int32_t *gk = B.gkeys + off;
-            u64 *gv = B.gvals + off;
+            VT *gv = (VT *)B.gvals + off;
             int32_t *gl = B.glist + off;
-            for (int r = threadIdx.x; r < m; r += kBlock) {
+            for (int r = threadIdx.x; r < m; r += kCHugeBlock) {
                 const int s = list[r];
                 const int32_t key = keys[s];
-                const u64 v = vals[s];
+                const VT v = vals[s];
                 keys[s] = -1;
                 vals[s] = 0;
-                g_insert(gk, gv, gl, &B.gcnt[b], l2, key, v, A.err);
+                tbl_insert<true, VT>(gk, gv, gl, &B.gcnt[b], l2, key, v, A.err);
             }
             __threadfence();
             __syncthreads();
@@ -306,10 +346,10 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_big(CoarsenArgs<WT> A, CBigA
             if (s_last) {
                 __threadfence();
                 const int gm = __ldcg(&B.gcnt[b]);
-                for (int r = threadIdx.x; r < gm; r += kBlock) {
+                for (int r = threadIdx.x; r < gm; r += kCHugeBlock) {
                     const int s = __ldcg(gl + r);
                     A.tmp_col[tb + r] = __ldcg(gk + s);
-                    A.tmp_w[tb + r] = __ldcg(gv + s);
+                    A.tmp_w[tb + r] = (u64)__ldcg(gv + s);
                     gk[s] = -1;
                     gv[s] = 0;
                 }
@@ -356,8 +396,8 @@ struct I32AsI64In {
 // ------------------------------------------------------------------ launchers
 
 int launch_coarsen_stage1(const DevGraph &g, const PhaseState &st, const int32_t *new_id,
-                          int64_t k, i64 *delta_next, CoarsenBufs &cb, cudaStream_t s,
-                          const LaunchCfg &lc)
+                          int64_t k, i64 *delta_next, CoarsenBufs &cb, const Bins &bins,
+                          cudaStream_t s, const LaunchCfg &lc)
 {
     int launched = 0;
     const int64_t n = g.n;
@@ -371,65 +411,95 @@ int launch_coarsen_stage1(const DevGraph &g, const PhaseState &st, const int32_t
         n, st.C, new_id, cb.moff, cb.cursor, cb.members);
     launched++;
     launched += exclusive_scan<int64_t>(MemberDegIn{cb.members, g.rp}, n, cb.mpre, cb.scratch64, s);
-    cudaMemsetAsync(cb.counts, 0, sizeof(int32_t) * 4, s);
-    k_coarsen_bin<<<grid_for(k, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        k, cb.moff, cb.mpre, 128, cb.clist, cb.blist, cb.counts);
+    cudaMemsetAsync(cb.counts, 0, sizeof(int32_t) * 8, s);
+    CBinArgs ba;
+    for (int t = 0; t < kNumBins - 1; t++) ba.upper[t] = bins.upper[t];
+    k_coarsen_bin<<<grid_for(k, kBlock, lc.max_blocks), kBlock, 0, s>>>(k, cb.moff, cb.mpre, ba,
+                                                                        cb.clist, cb.counts);
     launched++;
     return launched;
 }
 
-inline size_t cbig_smem_bytes(int chunk) { return (size_t)(2 * chunk) * 16; }
+template <typename VT>
+inline size_t ctable_bytes(int log2cap)
+{
+    return ((size_t)1 << log2cap) * (sizeof(VT) + 8);
+}
 
-template <typename WT>
+template <int BLOCK, typename WT, typename VT>
+static void launch_cta(const CoarsenArgs<WT> &A, const int32_t *list, int nl, int l2,
+                       cudaStream_t s, const LaunchCfg &lc)
+{
+    const size_t smem = ctable_bytes<VT>(l2);
+    cudaFuncSetAttribute(k_coarsen_cta<BLOCK, WT, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    const int per_sm = (int)((227 * 1024) / (smem + 1024));
+    const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
+    k_coarsen_cta<BLOCK, WT, VT><<<nl < maxg ? nl : maxg, BLOCK, smem, s>>>(A, list, nl, l2);
+}
+
+template <typename WT, typename VT>
 static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *new_id, int64_t k,
-                       CoarsenBufs &cb, int nsmall, Bins &big, unsigned *err, cudaStream_t s,
+                       CoarsenBufs &cb, Bins &bins, unsigned *err, cudaStream_t s,
                        const LaunchCfg &lc)
 {
     CoarsenArgs<WT> A{g.rp,       g.col,       (const WT *)g.w, st.C,       new_id, cb.moff,
                       cb.members, cb.mpre,     cb.ccnt,         cb.tmp_col, cb.tmp_w, err};
     int launched = 0;
-    if (nsmall > 0) {
-        k_coarsen_group<WT><<<grid_for(nsmall, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(
-            A, cb.clist, nsmall);
+    if (bins.nlist[2] > 0) {
+        k_coarsen_group<WT, VT><<<grid_for(bins.nlist[2], kBlock / 32, lc.max_blocks), kBlock, 0,
+                                  s>>>(A, bins.list[2], bins.nlist[2]);
         launched++;
     }
-    if (big.nchunks > 0) {
-        CBigArgs B{cb.blist, big.chunk_b, big.chunk_first, big.nch,   big.goff,
-                   big.glog2, big.gcnt,   big.gdone,       big.gkeys, big.gvals,
-                   big.glist, big.chunk,  big.nchunks};
-        const size_t smem = cbig_smem_bytes(big.chunk);
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_coarsen_big<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        const int grid = big.nchunks < lc.max_blocks ? big.nchunks : lc.max_blocks;
-        k_coarsen_big<WT><<<grid, kBlock, smem, s>>>(A, B);
+    for (int cbn = 0; cbn < kCtaBins; cbn++) {
+        const int bin = 3 + cbn;
+        if (bins.nlist[bin] == 0) continue;
+        const int l2 = cta_log2cap(bins, bin);
+        if (kCtaBlock[cbn] == 128) launch_cta<128, WT, VT>(A, bins.list[bin], bins.nlist[bin], l2, s, lc);
+        else if (kCtaBlock[cbn] == 256) launch_cta<256, WT, VT>(A, bins.list[bin], bins.nlist[bin], l2, s, lc);
+        else launch_cta<1024, WT, VT>(A, bins.list[bin], bins.nlist[bin], l2, s, lc);
+        launched++;
+    }
+    if (bins.nchunks > 0) {
+        CBigArgs B{bins.list[6], bins.chunk_b, bins.chunk_first, bins.nch,   bins.goff,
+                   bins.glog2,   bins.gcnt,    bins.gdone,       bins.gkeys, bins.gvals,
+                   bins.glist,   bins.chunk,   bins.nchunks};
+        const int l2 = 31 - __builtin_clz(2 * bins.chunk);
+        const size_t smem = ctable_bytes<VT>(l2);
+        cudaFuncSetAttribute(k_coarsen_huge<WT, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        const int per_sm = (int)((227 * 1024) / (smem + 1024));
+        const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
+        k_coarsen_huge<WT, VT><<<bins.nchunks < maxg ? bins.nchunks : maxg, kCHugeBlock, smem, s>>>(
+            A, B);
         launched++;
     }
     return launched;
 }
 
-// Prepares the chunk lists of the big communities (big.nlist[2] = their count, big.list[2]
-// = cb.blist) and runs the aggregation.  The host must have filled big.nch etc. through
-// launch_coarsen_bigprep first; see the engine.
 int launch_coarsen_stage2(const DevGraph &g, const PhaseState &st, const int32_t *new_id,
-                          int64_t k, CoarsenBufs &cb, int nsmall, Bins &big, unsigned *err,
+                          int64_t k, CoarsenBufs &cb, Bins &bins, bool narrow, unsigned *err,
                           cudaStream_t s, const LaunchCfg &lc)
 {
-    if (g.wbytes == 4) return stage2_impl<int32_t>(g, st, new_id, k, cb, nsmall, big, err, s, lc);
-    return stage2_impl<i64>(g, st, new_id, k, cb, nsmall, big, err, s, lc);
+    typedef unsigned int u32;
+    if (g.wbytes == 4)
+        return narrow ? stage2_impl<int32_t, u32>(g, st, new_id, k, cb, bins, err, s, lc)
+                      : stage2_impl<int32_t, u64>(g, st, new_id, k, cb, bins, err, s, lc);
+    return narrow ? stage2_impl<i64, u32>(g, st, new_id, k, cb, bins, err, s, lc)
+                  : stage2_impl<i64, u64>(g, st, new_id, k, cb, bins, err, s, lc);
 }
 
-int launch_coarsen_bigprep(int64_t k, CoarsenBufs &cb, Bins &big, cudaStream_t s,
+int launch_coarsen_bigprep(int64_t k, CoarsenBufs &cb, Bins &bins, cudaStream_t s,
                            const LaunchCfg &lc)
 {
-    const int nb = big.nlist[2];
+    const int nb = bins.nlist[6];
     if (nb == 0) return 0;
     k_cbig_prep<<<grid_for(nb, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        nb, cb.blist, cb.moff, cb.mpre, k, big.chunk, big.nch, big.gcap, big.glog2);
+        nb, bins.list[6], cb.moff, cb.mpre, k, bins.chunk, bins.nch, bins.gcap, bins.glog2);
     int launched = 1;
-    launched += exclusive_scan<int32_t>(ArrayIn<int32_t>{big.nch}, nb, big.chunk_first,
+    launched += exclusive_scan<int32_t>(ArrayIn<int32_t>{bins.nch}, nb, bins.chunk_first,
                                         cb.scratch32, s);
-    launched += exclusive_scan<int64_t>(ArrayIn<int64_t>{big.gcap}, nb, big.goff, cb.scratch64, s);
+    launched += exclusive_scan<int64_t>(ArrayIn<int64_t>{bins.gcap}, nb, bins.goff, cb.scratch64, s);
     return launched;
 }
 

@@ -218,53 +218,66 @@ int launch_vertex_following(const DevGraph &g, const PhaseState &st, cudaStream_
 }
 
 // ------------------------------------------------------------------ degree bins
-// counts[0..2]: list sizes; counts[4..11]: entries of the small, mid1, mid2 and big rows as
-// 64-bit values (two int32 slots each).
-__global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, int small_max,
-                                                int mid1, int mid2, int32_t *l0, int32_t *l1,
-                                                int32_t *l2, int32_t *counts)
+// counts[b] (b = 1..6): list sizes; counts + 8 + 2b: entries of bin b as a 64-bit value.
+struct BinArgs {
+    int64_t upper[kNumBins - 1];
+    int32_t *list[kNumBins];
+};
+
+__device__ __forceinline__ int bin_of(int64_t d, const int64_t *upper)
+{
+    int b = 0;
+#pragma unroll
+    for (int t = 0; t < kNumBins - 1; t++) b += d > upper[t];
+    return b;
+}
+
+__global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, BinArgs ba,
+                                                int32_t *counts)
 {
     const int lane = threadIdx.x & 31;
-    u64 ent[4] = {0, 0, 0, 0};
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+    u64 ent[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n;
+         i0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = i0 + threadIdx.x;
-        int bin = -2;
+        int bin = -1;
         if (i < n) {
             const int64_t d = rp[i + 1] - rp[i];
-            bin = d <= small_max ? -1 : d <= mid1 ? 0 : d <= mid2 ? 1 : 2;
-            ent[bin + 1] += (u64)d;
+            bin = bin_of(d, ba.upper);
+#pragma unroll
+            for (int b = 0; b < kNumBins; b++)
+                if (b == bin) ent[b] += (u64)d;
         }
 #pragma unroll
-        for (int b = 0; b < 3; b++) {
+        for (int b = 1; b < kNumBins; b++) {
             const unsigned mask = __ballot_sync(0xffffffffu, bin == b);
             if (!mask) continue;
             const int leader = __ffs(mask) - 1;
             int base = 0;
             if (lane == leader) base = atomicAdd(&counts[b], __popc(mask));
             base = __shfl_sync(0xffffffffu, base, leader);
-            if (bin == b) {
-                int32_t *l = b == 0 ? l0 : b == 1 ? l1 : l2;
-                l[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
-            }
+            if (bin == b) ba.list[b][base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
         }
     }
 #pragma unroll
-    for (int b = 0; b < 4; b++) {
+    for (int b = 0; b < kNumBins; b++) {
         u64 v = sum_reduce(ent[b], 32);
-        if (lane == 0 && v) atomicAdd((u64 *)(counts + 4 + 2 * b), v);
+        if (lane == 0 && v) atomicAdd((u64 *)(counts + 8 + 2 * b), v);
     }
 }
 
 int launch_bin(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc)
 {
-    cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * 12, s);
+    cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * 24, s);
     if (g.n == 0) return 0;
-    k_bin<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        g.n, g.rp, b.small_max, b.mid1, b.mid2, b.list[0], b.list[1], b.list[2], b.counts);
+    BinArgs ba;
+    for (int t = 0; t < kNumBins - 1; t++) ba.upper[t] = b.upper[t];
+    for (int t = 0; t < kNumBins; t++) ba.list[t] = b.list[t];
+    k_bin<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(g.n, g.rp, ba, b.counts);
     return 1;
 }
 
-// Big rows: chunk counts and, for multi-chunk rows, a global table of 2^k >= 2*min(d, n)
+// Bin-6 rows: chunk counts and, for multi-chunk rows, a global table of 2^k >= 2*min(d, n)
 // slots (distinct neighbour labels <= min(d, n) < slots, so it never fills).
 __global__ void k_big_prep(int nb, const int32_t *bverts, const int64_t *rp, int64_t n, int chunk,
                            int32_t *nch, int64_t *gcap, int32_t *glog2)
@@ -290,10 +303,10 @@ __global__ void k_big_prep(int nb, const int32_t *bverts, const int64_t *rp, int
 int launch_big_prep(const DevGraph &g, Bins &b, int64_t *scratch64, int32_t *scratch32,
                     cudaStream_t s, const LaunchCfg &lc)
 {
-    const int nb = b.nlist[2];
+    const int nb = b.nlist[6];
     if (nb == 0) return 0;
     k_big_prep<<<grid_for(nb, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        nb, b.list[2], g.rp, g.n, b.chunk, b.nch, b.gcap, b.glog2);
+        nb, b.list[6], g.rp, g.n, b.chunk, b.nch, b.gcap, b.glog2);
     int k = 1;
     k += exclusive_scan<int32_t>(ArrayIn<int32_t>{b.nch}, nb, b.chunk_first, scratch32, s);
     k += exclusive_scan<int64_t>(ArrayIn<int64_t>{b.gcap}, nb, b.goff, scratch64, s);
@@ -311,7 +324,7 @@ __global__ void k_big_fill(int nb, const int32_t *nch, const int32_t *chunk_firs
 
 int launch_big_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc)
 {
-    const int nb = b.nlist[2];
+    const int nb = b.nlist[6];
     if (nb == 0) return 0;
     k_big_fill<<<grid_for(nb, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(nb, b.nch,
                                                                            b.chunk_first, b.chunk_b);
@@ -356,7 +369,7 @@ __global__ void k_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_q
         const i64 moved = (i64)st->moved;
         bool stop = false;
         int iters = 0;
-        for (int b = 0; b < 4; b++) cand_total[b] += st->cand[b];
+        for (int b = 0; b < 8; b++) cand_total[b] += st->cand[b];
         if (k == 1) {
             i128_to(qn, ctl->qn_init);
         } else {
@@ -398,7 +411,7 @@ __global__ void k_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_q
     st->sq_lo = 0;
     st->sq_hi = 0;
     st->moved = 0;
-    for (int b = 0; b < 4; b++) st->cand[b] = 0;
+    for (int b = 0; b < 8; b++) st->cand[b] = 0;
 }
 
 int launch_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_qn, u64 *cand_total,

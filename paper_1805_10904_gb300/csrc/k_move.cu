@@ -15,11 +15,12 @@
 // Qn = (2W)^2 Q of that state without a separate pass over the edges.
 //
 // Work is binned by row length (Sec. 6.3 suggests grouping vertices by degree):
-//   short rows   -> one thread per vertex, neighbours aggregated in registers,
-//   medium rows  -> 8-lane groups or whole warps with a shared-memory hash table each,
-//   long rows    -> CTA-sized chunks with a shared-memory hash table; a row spanning
-//                   several chunks merges its chunks into a global-memory hash table and
-//                   the last chunk to finish takes the decision.
+//   bin 0    one thread per vertex, neighbours aggregated in registers (dense over all i),
+//   bin 1-2  8-lane groups / whole warps, one shared-memory hash table per group,
+//   bin 3-5  one CTA per row with a shared-memory table sized for the bin (up to 16K slots),
+//   bin 6    CTA-sized chunks of a row; a row spanning several chunks merges its chunk
+//            tables into a global-memory table and the last chunk to finish decides.
+// Table values are 32-bit when 2W < 2^32 (every e_{i->c} <= delta_i <= 2W fits), else 64-bit.
 #include <climits>
 
 #include "lv_common.cuh"
@@ -28,6 +29,7 @@
 namespace lv {
 
 constexpr int kSmallMax = 8;  // register slots of the thread-per-vertex kernel
+constexpr int kUnroll = 4;    // independent row entries in flight per thread
 
 template <typename WT>
 struct MoveArgs {
@@ -58,7 +60,55 @@ __device__ __forceinline__ int32_t choose_target(int32_t a, int32_t best, GT gbe
     return best;
 }
 
-// ------------------------------------------------------------------ short rows
+// One candidate community c with weight e from vertex (a, dl): updates the running argmax
+// or records e_{i->a}.
+template <typename GT>
+__device__ __forceinline__ void consider(int32_t c, i64 e, int32_t a, i64 dl, i64 tw,
+                                         const i64 *deg, GT &gbest, int32_t &best, i64 &e_a)
+{
+    if (c == a) {
+        e_a = e;
+        return;
+    }
+    const GT g = (GT)tw * (GT)e - (GT)dl * (GT)deg[c];
+    if (better(g, c, gbest, best)) {
+        gbest = g;
+        best = c;
+    }
+}
+
+// CTA-wide argmax and sums; results valid in thread 0.  Ends with a barrier.
+template <typename GT>
+__device__ __forceinline__ void block_argmax(GT &g, int32_t &c, i64 &e_a, i64 &loop)
+{
+    __shared__ GT s_g[32];
+    __shared__ int32_t s_c[32];
+    __shared__ i64 s_e[32], s_l[32];
+    argmax_reduce(g, c, 32);
+    e_a = sum_reduce(e_a, 32);
+    loop = sum_reduce(loop, 32);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_g[warp] = g;
+        s_c[warp] = c;
+        s_e[warp] = e_a;
+        s_l[warp] = loop;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            if (better(s_g[w], s_c[w], g, c)) {
+                g = s_g[w];
+                c = s_c[w];
+            }
+            e_a += s_e[w];
+            loop += s_l[w];
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ bin 0
 // Dense over every vertex: also adds deg[i]^2 of label i to sum_c deg_c^2.
 template <typename WT, typename GT>
 __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small_max)
@@ -112,15 +162,7 @@ __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small
 #pragma unroll
                 for (int u = t; u < kSmallMax; u++) e += (lab[u] == c) ? wt[u] : 0;
                 m++;
-                if (c == a) {
-                    e_a = e;
-                } else {
-                    const GT g = (GT)A.tw * (GT)e - (GT)dl * (GT)A.deg[c];
-                    if (better(g, c, gbest, best)) {
-                        gbest = g;
-                        best = c;
-                    }
-                }
+                consider<GT>(c, e, a, dl, A.tw, A.deg, gbest, best, e_a);
             }
         }
         const int32_t target = choose_target<GT>(a, best, gbest, e_a, dl, A.tw, A.deg, A.size);
@@ -132,17 +174,17 @@ __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small
     block_flush_stats(A.st, 0, internal, moved, cand, sq);
 }
 
-// ------------------------------------------------------------------ medium rows
+// ------------------------------------------------------------------ bins 1-2
 // G lanes per vertex (G <= 32), each group with a 2^LOG2CAP-slot shared table.  The
 // outer loop is uniform across the block so every lane reaches the shuffles.
-template <int G, int LOG2CAP, typename WT, typename GT>
+template <int G, int LOG2CAP, typename WT, typename GT, typename VT>
 __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int32_t *verts,
                                                        int nverts, int slot)
 {
     constexpr int CAP = 1 << LOG2CAP;
     constexpr int NG = kBlock / G;
     __shared__ int s_keys[NG * CAP];
-    __shared__ u64 s_vals[NG * CAP];
+    __shared__ VT s_vals[NG * CAP];
     __shared__ int s_list[NG * CAP];
     __shared__ int s_cnt[NG];
     for (int s = threadIdx.x; s < NG * CAP; s += kBlock) {
@@ -153,7 +195,7 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
     __syncthreads();
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     int *keys = s_keys + g * CAP;
-    u64 *vals = s_vals + g * CAP;
+    VT *vals = s_vals + g * CAP;
     int *list = s_list + g * CAP;
     int *cnt = &s_cnt[g];
     u64 internal = 0, moved = 0, cand = 0;
@@ -175,7 +217,7 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
             const int32_t j = A.col[k];
             const i64 x = (i64)A.w[k];
             if (j == i) loop += x;
-            else sh_insert<LOG2CAP>(keys, vals, list, cnt, A.C[j], (u64)x, A.err);
+            else tbl_insert<false, VT>(keys, vals, list, cnt, LOG2CAP, A.C[j], (VT)x, A.err);
         }
         __syncwarp();
         const int m = valid ? *(volatile int *)cnt : 0;
@@ -188,15 +230,7 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
             const i64 e = (i64)vals[s];
             keys[s] = -1;
             vals[s] = 0;
-            if (c == a) {
-                e_a = e;
-            } else {
-                const GT gc = (GT)A.tw * (GT)e - (GT)dl * (GT)A.deg[c];
-                if (better(gc, c, gbest, best)) {
-                    gbest = gc;
-                    best = c;
-                }
-            }
+            consider<GT>(c, e, a, dl, A.tw, A.deg, gbest, best, e_a);
         }
         argmax_reduce(gbest, best, G);
         e_a = sum_reduce(e_a, G);
@@ -217,7 +251,84 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
     block_flush_stats(A.st, slot, internal, moved, cand, 0);
 }
 
-// ------------------------------------------------------------------ long rows
+// ------------------------------------------------------------------ bins 3-5
+// One CTA per row, table of 2^log2cap slots in dynamic shared memory (vals, keys, list).
+template <int BLOCK, typename WT, typename GT, typename VT>
+__global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_t *verts,
+                                                    int nverts, int log2cap, int slot)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int cap = 1 << log2cap;
+    VT *vals = (VT *)smem;
+    int *keys = (int *)(vals + cap);
+    int *list = keys + cap;
+    __shared__ int s_cnt;
+    for (int s = threadIdx.x; s < cap; s += BLOCK) {
+        keys[s] = -1;
+        vals[s] = 0;
+    }
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    u64 internal = 0, moved = 0, cand = 0;
+    for (int v = blockIdx.x; v < nverts; v += gridDim.x) {
+        const int32_t i = verts[v];
+        const int64_t rb = A.rp[i], re = A.rp[i + 1];
+        const int32_t a = A.C[i];
+        const i64 dl = A.delta[i];
+        i64 loop = 0;
+        for (int64_t k0 = rb + threadIdx.x; k0 < re; k0 += (int64_t)kUnroll * BLOCK) {
+            int32_t j[kUnroll];
+            i64 x[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const int64_t k = k0 + (int64_t)u * BLOCK;
+                j[u] = -1;
+                x[u] = 0;
+                if (k < re) {
+                    j[u] = A.col[k];
+                    x[u] = (i64)A.w[k];
+                }
+            }
+            int32_t c[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (j[u] == i) loop += x[u];
+                else if (c[u] >= 0)
+                    tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, c[u], (VT)x[u], A.err);
+            }
+        }
+        __syncthreads();
+        const int m = s_cnt;
+        GT gbest = gain_min<GT>();
+        int32_t best = INT_MAX;
+        i64 e_a = 0;
+        for (int p = threadIdx.x; p < m; p += BLOCK) {
+            const int s = list[p];
+            const int32_t cc = keys[s];
+            const i64 e = (i64)vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+            consider<GT>(cc, e, a, dl, A.tw, A.deg, gbest, best, e_a);
+        }
+        block_argmax(gbest, best, e_a, loop);
+        if (threadIdx.x == 0) {
+            const int32_t target = choose_target<GT>(a, best, gbest, e_a, dl, A.tw, A.deg, A.size);
+            A.Cnext[i] = target;
+            moved += target != a;
+            internal += (u64)(e_a + loop);
+            cand += (u64)m;
+            s_cnt = 0;
+        }
+        __syncthreads();
+    }
+    block_flush_stats(A.st, slot, internal, moved, cand, 0);
+}
+
+// ------------------------------------------------------------------ bin 6
+constexpr int kHugeBlock = 512;
+
 struct BigArgs {
     const int32_t *bverts;
     const int32_t *chunk_b;
@@ -229,86 +340,24 @@ struct BigArgs {
     int32_t *gdone;
     u64 *gloop;
     int32_t *gkeys;
-    u64 *gvals;
+    void *gvals;
     int32_t *glist;
     int chunk;
     int nchunks;
 };
 
-// Shared table with a run-time power-of-two size.
-__device__ __forceinline__ void shr_insert(int *keys, u64 *vals, int *list, int *cnt, int log2cap,
-                                           int key, u64 val, unsigned *err)
-{
-    const unsigned cap = 1u << log2cap;
-    unsigned h = hash_slot(key, log2cap);
-#pragma unroll 1
-    for (unsigned probe = 0; probe < cap; probe++) {
-        int k = ((volatile int *)keys)[h];
-        if (k == key) {
-            atomicAdd(&vals[h], val);
-            return;
-        }
-        if (k == -1) {
-            int old = atomicCAS(&keys[h], -1, key);
-            if (old == -1) {
-                int p = atomicAdd(cnt, 1);
-                list[p] = (int)h;
-                atomicAdd(&vals[h], val);
-                return;
-            }
-            if (old == key) {
-                atomicAdd(&vals[h], val);
-                return;
-            }
-        }
-        h = (h + 1) & (cap - 1);
-    }
-    atomicOr(err, ERRF_HASH_FULL);
-}
-
-// CTA argmax / sums; results valid in thread 0.
-template <typename GT>
-__device__ __forceinline__ void block_argmax(GT &g, int32_t &c, i64 &e_a, i64 &loop)
-{
-    __shared__ GT s_g[kBlock / 32];
-    __shared__ int32_t s_c[kBlock / 32];
-    __shared__ i64 s_e[kBlock / 32], s_l[kBlock / 32];
-    argmax_reduce(g, c, 32);
-    e_a = sum_reduce(e_a, 32);
-    loop = sum_reduce(loop, 32);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        s_g[warp] = g;
-        s_c[warp] = c;
-        s_e[warp] = e_a;
-        s_l[warp] = loop;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < kBlock / 32; w++) {
-            if (better(s_g[w], s_c[w], g, c)) {
-                g = s_g[w];
-                c = s_c[w];
-            }
-            e_a += s_e[w];
-            loop += s_l[w];
-        }
-    }
-    __syncthreads();
-}
-
-template <typename WT, typename GT>
-__global__ void __launch_bounds__(kBlock) k_move_big(MoveArgs<WT> A, BigArgs B)
+template <typename WT, typename GT, typename VT>
+__global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArgs B)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int log2cap = 31 - __clz(2 * B.chunk);  // 2 * chunk slots
     const int cap = 1 << log2cap;
-    u64 *vals = (u64 *)smem;
+    VT *vals = (VT *)smem;
     int *keys = (int *)(vals + cap);
     int *list = keys + cap;
     __shared__ int s_cnt;
     __shared__ int s_last;
-    for (int s = threadIdx.x; s < cap; s += kBlock) {
+    for (int s = threadIdx.x; s < cap; s += kHugeBlock) {
         keys[s] = -1;
         vals[s] = 0;
     }
@@ -326,11 +375,28 @@ __global__ void __launch_bounds__(kBlock) k_move_big(MoveArgs<WT> A, BigArgs B)
         const int32_t a = A.C[i];
         const i64 dl = A.delta[i];
         i64 loop = 0;
-        for (int64_t k = cb + threadIdx.x; k < ce; k += kBlock) {
-            const int32_t j = A.col[k];
-            const i64 x = (i64)A.w[k];
-            if (j == i) loop += x;
-            else shr_insert(keys, vals, list, &s_cnt, log2cap, A.C[j], (u64)x, A.err);
+        for (int64_t k0 = cb + threadIdx.x; k0 < ce; k0 += (int64_t)kUnroll * kHugeBlock) {
+            int32_t j[kUnroll];
+            i64 x[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const int64_t k = k0 + (int64_t)u * kHugeBlock;
+                j[u] = -1;
+                x[u] = 0;
+                if (k < ce) {
+                    j[u] = A.col[k];
+                    x[u] = (i64)A.w[k];
+                }
+            }
+            int32_t cc[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) cc[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (j[u] == i) loop += x[u];
+                else if (cc[u] >= 0)
+                    tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, cc[u], (VT)x[u], A.err);
+            }
         }
         __syncthreads();
         const int m = s_cnt;
@@ -338,21 +404,13 @@ __global__ void __launch_bounds__(kBlock) k_move_big(MoveArgs<WT> A, BigArgs B)
             GT gbest = gain_min<GT>();
             int32_t best = INT_MAX;
             i64 e_a = 0;
-            for (int p = threadIdx.x; p < m; p += kBlock) {
+            for (int p = threadIdx.x; p < m; p += kHugeBlock) {
                 const int s = list[p];
-                const int32_t cc = keys[s];
+                const int32_t k2 = keys[s];
                 const i64 e = (i64)vals[s];
                 keys[s] = -1;
                 vals[s] = 0;
-                if (cc == a) {
-                    e_a = e;
-                } else {
-                    const GT g = (GT)A.tw * (GT)e - (GT)dl * (GT)A.deg[cc];
-                    if (better(g, cc, gbest, best)) {
-                        gbest = g;
-                        best = cc;
-                    }
-                }
+                consider<GT>(k2, e, a, dl, A.tw, A.deg, gbest, best, e_a);
             }
             block_argmax(gbest, best, e_a, loop);
             if (threadIdx.x == 0) {
@@ -367,15 +425,15 @@ __global__ void __launch_bounds__(kBlock) k_move_big(MoveArgs<WT> A, BigArgs B)
             const int64_t off = B.goff[b];
             const int l2 = B.glog2[b];
             int32_t *gk = B.gkeys + off;
-            u64 *gv = B.gvals + off;
+            VT *gv = (VT *)B.gvals + off;
             int32_t *gl = B.glist + off;
-            for (int p = threadIdx.x; p < m; p += kBlock) {
+            for (int p = threadIdx.x; p < m; p += kHugeBlock) {
                 const int s = list[p];
-                const int32_t cc = keys[s];
-                const u64 e = vals[s];
+                const int32_t k2 = keys[s];
+                const VT e = vals[s];
                 keys[s] = -1;
                 vals[s] = 0;
-                g_insert(gk, gv, gl, &B.gcnt[b], l2, cc, e, A.err);
+                tbl_insert<true, VT>(gk, gv, gl, &B.gcnt[b], l2, k2, e, A.err);
             }
             loop = sum_reduce(loop, 32);
             if ((threadIdx.x & 31) == 0 && loop) atomicAdd(&B.gloop[b], (u64)loop);
@@ -392,21 +450,13 @@ __global__ void __launch_bounds__(kBlock) k_move_big(MoveArgs<WT> A, BigArgs B)
                 GT gbest = gain_min<GT>();
                 int32_t best = INT_MAX;
                 i64 e_a = 0, lz = 0;
-                for (int p = threadIdx.x; p < gm; p += kBlock) {
+                for (int p = threadIdx.x; p < gm; p += kHugeBlock) {
                     const int s = __ldcg(gl + p);
-                    const int32_t cc = __ldcg(gk + s);
+                    const int32_t k2 = __ldcg(gk + s);
                     const i64 e = (i64)__ldcg(gv + s);
                     gk[s] = -1;
                     gv[s] = 0;
-                    if (cc == a) {
-                        e_a = e;
-                    } else {
-                        const GT g = (GT)A.tw * (GT)e - (GT)dl * (GT)A.deg[cc];
-                        if (better(g, cc, gbest, best)) {
-                            gbest = g;
-                            best = cc;
-                        }
-                    }
+                    consider<GT>(k2, e, a, dl, A.tw, A.deg, gbest, best, e_a);
                 }
                 block_argmax(gbest, best, e_a, lz);
                 if (threadIdx.x == 0) {
@@ -427,14 +477,18 @@ __global__ void __launch_bounds__(kBlock) k_move_big(MoveArgs<WT> A, BigArgs B)
         if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
     }
-    block_flush_stats(A.st, 3, internal, moved, cand, 0);
+    block_flush_stats(A.st, 6, internal, moved, cand, 0);
 }
 
 // ------------------------------------------------------------------ launch
 
-inline size_t big_smem_bytes(int chunk) { return (size_t)(2 * chunk) * 16; }
+template <typename VT>
+inline size_t table_bytes(int log2cap)
+{
+    return ((size_t)1 << log2cap) * (sizeof(VT) + 8);
+}
 
-template <typename WT, typename GT>
+template <typename WT, typename GT, typename VT>
 static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw,
                       SweepStats *stats, unsigned *err, cudaStream_t s, const LaunchCfg &lc,
                       SweepTimers *tm)
@@ -443,65 +497,94 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
                    tw, st.Cnext, stats, err};
     const bool timed = tm && tm->on;
     int launched = 0;
-    if (timed) cudaEventRecord(tm->ev[0], s);
+    auto mark = [&](int e) {
+        if (timed) cudaEventRecord(tm->ev[e], s);
+    };
+    mark(0);
     if (g.n > 0) {
         k_move_small<WT, GT><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-            A, b.small_max);
+            A, (int)b.upper[0]);
         launched++;
     }
-    if (timed) cudaEventRecord(tm->ev[1], s);
-    if (timed) cudaEventRecord(tm->ev[2], s);
-    if (b.nlist[0] > 0) {
-        k_move_group<8, 6, WT, GT><<<grid_for(b.nlist[0], kBlock / 8, lc.max_blocks), kBlock, 0,
-                                     s>>>(A, b.list[0], b.nlist[0], 1);
-        launched++;
-    }
-    if (timed) cudaEventRecord(tm->ev[3], s);
-    if (timed) cudaEventRecord(tm->ev[4], s);
+    mark(1);
+    mark(2);
     if (b.nlist[1] > 0) {
-        k_move_group<32, 8, WT, GT><<<grid_for(b.nlist[1], kBlock / 32, lc.max_blocks), kBlock,
-                                      0, s>>>(A, b.list[1], b.nlist[1], 2);
+        k_move_group<8, 6, WT, GT, VT><<<grid_for(b.nlist[1], kBlock / 8, lc.max_blocks), kBlock,
+                                         0, s>>>(A, b.list[1], b.nlist[1], 1);
         launched++;
     }
-    if (timed) cudaEventRecord(tm->ev[5], s);
-    if (timed) cudaEventRecord(tm->ev[6], s);
+    mark(3);
+    mark(4);
+    if (b.nlist[2] > 0) {
+        k_move_group<32, 8, WT, GT, VT><<<grid_for(b.nlist[2], kBlock / 32, lc.max_blocks),
+                                          kBlock, 0, s>>>(A, b.list[2], b.nlist[2], 2);
+        launched++;
+    }
+    mark(5);
+    for (int cb = 0; cb < kCtaBins; cb++) {
+        const int bin = 3 + cb;
+        mark(2 * bin);
+        if (b.nlist[bin] > 0) {
+            const int l2 = cta_log2cap(b, bin);
+            const size_t smem = table_bytes<VT>(l2);
+            const int per_sm = (int)((227 * 1024) / (smem + 1024));
+            const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
+            const int grid = b.nlist[bin] < maxg ? b.nlist[bin] : maxg;
+            if (kCtaBlock[cb] == 128) {
+                cudaFuncSetAttribute(k_move_cta<128, WT, GT, VT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_move_cta<128, WT, GT, VT><<<grid, 128, smem, s>>>(A, b.list[bin], b.nlist[bin],
+                                                                    l2, bin);
+            } else if (kCtaBlock[cb] == 256) {
+                cudaFuncSetAttribute(k_move_cta<256, WT, GT, VT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_move_cta<256, WT, GT, VT><<<grid, 256, smem, s>>>(A, b.list[bin], b.nlist[bin],
+                                                                    l2, bin);
+            } else {
+                cudaFuncSetAttribute(k_move_cta<1024, WT, GT, VT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_move_cta<1024, WT, GT, VT><<<grid, 1024, smem, s>>>(A, b.list[bin],
+                                                                      b.nlist[bin], l2, bin);
+            }
+            launched++;
+        }
+        mark(2 * bin + 1);
+    }
+    mark(12);
     if (b.nchunks > 0) {
-        BigArgs B{b.list[2], b.chunk_b, b.chunk_first, b.nch,   b.goff,  b.glog2, b.gcnt,
+        BigArgs B{b.list[6], b.chunk_b, b.chunk_first, b.nch,   b.goff,  b.glog2, b.gcnt,
                   b.gdone,   b.gloop,   b.gkeys,       b.gvals, b.glist, b.chunk, b.nchunks};
-        const size_t smem = big_smem_bytes(b.chunk);
-        const int grid = b.nchunks < lc.max_blocks ? b.nchunks : lc.max_blocks;
-        k_move_big<WT, GT><<<grid, kBlock, smem, s>>>(A, B);
+        const int l2 = 31 - __builtin_clz(2 * b.chunk);
+        const size_t smem = table_bytes<VT>(l2);
+        cudaFuncSetAttribute(k_move_huge<WT, GT, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        const int per_sm = (int)((227 * 1024) / (smem + 1024));
+        const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
+        const int grid = b.nchunks < maxg ? b.nchunks : maxg;
+        k_move_huge<WT, GT, VT><<<grid, kHugeBlock, smem, s>>>(A, B);
         launched++;
     }
-    if (timed) cudaEventRecord(tm->ev[7], s);
+    mark(13);
     return launched;
 }
 
-template <typename WT, typename GT>
-static void set_big_smem(int chunk)
-{
-    cudaFuncSetAttribute(k_move_big<WT, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)big_smem_bytes(chunk));
-}
-
 int launch_sweep(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, bool wide,
-                 SweepStats *stats, unsigned *err, cudaStream_t s, const LaunchCfg &lc,
-                 SweepTimers *tm)
+                 bool narrow, SweepStats *stats, unsigned *err, cudaStream_t s,
+                 const LaunchCfg &lc, SweepTimers *tm)
 {
-    if (b.nchunks > 0 && big_smem_bytes(b.chunk) > 48 * 1024) {
-        if (g.wbytes == 4) {
-            if (wide) set_big_smem<int32_t, i128>(b.chunk);
-            else set_big_smem<int32_t, i64>(b.chunk);
-        } else {
-            if (wide) set_big_smem<i64, i128>(b.chunk);
-            else set_big_smem<i64, i64>(b.chunk);
-        }
+    typedef unsigned int u32;
+    if (g.wbytes == 4) {
+        if (wide)
+            return narrow ? sweep_impl<int32_t, i128, u32>(g, st, b, tw, stats, err, s, lc, tm)
+                          : sweep_impl<int32_t, i128, u64>(g, st, b, tw, stats, err, s, lc, tm);
+        return narrow ? sweep_impl<int32_t, i64, u32>(g, st, b, tw, stats, err, s, lc, tm)
+                      : sweep_impl<int32_t, i64, u64>(g, st, b, tw, stats, err, s, lc, tm);
     }
-    if (g.wbytes == 4)
-        return wide ? sweep_impl<int32_t, i128>(g, st, b, tw, stats, err, s, lc, tm)
-                    : sweep_impl<int32_t, i64>(g, st, b, tw, stats, err, s, lc, tm);
-    return wide ? sweep_impl<i64, i128>(g, st, b, tw, stats, err, s, lc, tm)
-                : sweep_impl<i64, i64>(g, st, b, tw, stats, err, s, lc, tm);
+    if (wide)
+        return narrow ? sweep_impl<i64, i128, u32>(g, st, b, tw, stats, err, s, lc, tm)
+                      : sweep_impl<i64, i128, u64>(g, st, b, tw, stats, err, s, lc, tm);
+    return narrow ? sweep_impl<i64, i64, u32>(g, st, b, tw, stats, err, s, lc, tm)
+                  : sweep_impl<i64, i64, u64>(g, st, b, tw, stats, err, s, lc, tm);
 }
 
 }  // namespace lv

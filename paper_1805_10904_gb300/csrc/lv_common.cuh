@@ -34,8 +34,8 @@ struct SweepStats {
     u64 sq_lo;     // sum_c deg_c^2 as a 128-bit value
     u64 sq_hi;
     u64 moved;     // vertices whose proposed label differs from the current one
-    u64 cand[4];   // distinct neighbouring communities summed over the vertices of the
-                   // small, mid1, mid2 and big kernels
+    u64 cand[8];   // distinct neighbouring communities summed over the vertices of each
+                   // degree bin (index = bin)
 };
 
 // Level controller state (one per phase), read and written by the decide kernel.
@@ -153,7 +153,7 @@ __device__ __forceinline__ void atomic_add_u128(u64 *lo, u64 *hi, u128 v)
 __device__ __forceinline__ void block_flush_stats(SweepStats *st, int slot, u64 internal,
                                                   u64 moved, u64 cand, u128 sq)
 {
-    __shared__ u64 s_red[kBlock / 32][5];
+    __shared__ u64 s_red[32][5];
     internal = sum_reduce(internal, 32);
     moved = sum_reduce(moved, 32);
     cand = sum_reduce(cand, 32);
@@ -190,26 +190,35 @@ __device__ __forceinline__ unsigned hash_slot(int key, int log2cap)
     return log2cap == 0 ? 0u : ((unsigned)key * 2654435761u) >> (32 - log2cap);
 }
 
-// Shared-memory open-addressing insert-or-add.  `list` records the slot of every key
-// the first time it is claimed (count in *cnt), so the table can be walked and cleared
-// in O(distinct keys).  A table larger than the number of distinct keys never fills.
-template <int LOG2CAP>
-__device__ __forceinline__ void sh_insert(int *keys, u64 *vals, int *list, int *cnt, int key,
-                                          u64 val, unsigned *err)
+// Open-addressing insert-or-add of (key, val) into a table of 2^log2cap slots.  `list`
+// records the slot of every key the first time it is claimed (count in *cnt), so the table
+// can be walked and cleared in O(distinct keys).  A table with more slots than distinct
+// keys never fills; if it does anyway the error word is flagged and the value dropped.
+// GLOBAL selects L2 reads (tables shared by several CTAs) instead of shared memory.
+template <bool GLOBAL>
+__device__ __forceinline__ int tbl_key(const int *keys, unsigned h)
 {
-    constexpr unsigned CAP = 1u << LOG2CAP;
-    unsigned h = hash_slot(key, LOG2CAP);
+    if (GLOBAL) return __ldcg(keys + h);
+    return ((volatile const int *)keys)[h];
+}
+
+template <bool GLOBAL, typename VT>
+__device__ __forceinline__ void tbl_insert(int *keys, VT *vals, int *list, int *cnt, int log2cap,
+                                           int key, VT val, unsigned *err)
+{
+    const unsigned mask = (1u << log2cap) - 1u;
+    unsigned h = hash_slot(key, log2cap);
 #pragma unroll 1
-    for (unsigned probe = 0; probe < CAP; probe++) {
-        int k = ((volatile int *)keys)[h];
+    for (unsigned probe = 0; probe <= mask; probe++) {
+        const int k = tbl_key<GLOBAL>(keys, h);
         if (k == key) {
             atomicAdd(&vals[h], val);
             return;
         }
         if (k == -1) {
-            int old = atomicCAS(&keys[h], -1, key);
+            const int old = atomicCAS(&keys[h], -1, key);
             if (old == -1) {
-                int p = atomicAdd(cnt, 1);
+                const int p = atomicAdd(cnt, 1);
                 list[p] = (int)h;
                 atomicAdd(&vals[h], val);
                 return;
@@ -219,38 +228,7 @@ __device__ __forceinline__ void sh_insert(int *keys, u64 *vals, int *list, int *
                 return;
             }
         }
-        h = (h + 1) & (CAP - 1);
-    }
-    atomicOr(err, ERRF_HASH_FULL);
-}
-
-// Global-memory variant (table of 2^log2cap slots at keys/vals/list + off).
-__device__ __forceinline__ void g_insert(int *keys, u64 *vals, int *list, int *cnt, int log2cap,
-                                         int key, u64 val, unsigned *err)
-{
-    const unsigned cap = 1u << log2cap;
-    unsigned h = hash_slot(key, log2cap);
-#pragma unroll 1
-    for (unsigned probe = 0; probe < cap; probe++) {
-        int k = __ldcg(keys + h);
-        if (k == key) {
-            atomicAdd(vals + h, val);
-            return;
-        }
-        if (k == -1) {
-            int old = atomicCAS(keys + h, -1, key);
-            if (old == -1) {
-                int p = atomicAdd(cnt, 1);
-                list[p] = (int)h;
-                atomicAdd(vals + h, val);
-                return;
-            }
-            if (old == key) {
-                atomicAdd(vals + h, val);
-                return;
-            }
-        }
-        h = (h + 1) & (cap - 1);
+        h = (h + 1) & mask;
     }
     atomicOr(err, ERRF_HASH_FULL);
 }

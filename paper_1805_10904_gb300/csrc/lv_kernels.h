@@ -31,20 +31,26 @@ struct PhaseState {
     i64 *delta = nullptr;      // weighted degree of each vertex
 };
 
-// Degree bins of one phase.
+// Degree bins of one phase.  Bin b holds the vertices (or communities) whose entry count
+// d satisfies upper[b-1] < d <= upper[b]; the last bin holds the rest.
+//   0: one thread per vertex (dense kernel, no list)   3..5: one CTA per row, shared table
+//   1: 8-lane groups, 64-slot tables                   6:    CTA chunks, global table
+//   2: one warp, 256-slot tables
+constexpr int kNumBins = 7;
+constexpr int kCtaBins = 3;                       // bins 3, 4, 5
+constexpr int kCtaBlock[kCtaBins] = {128, 256, 1024};
+
 struct Bins {
-    int small_max = 8;  // row length <= small_max: thread per vertex (dense kernel)
-    int mid1 = 32;      // <= mid1: 8-lane groups
-    int mid2 = 128;     // <= mid2: one warp
-    int chunk = 1024;   // CTA chunk of a longer row
-    int32_t *list[3] = {nullptr, nullptr, nullptr};  // mid1, mid2, big vertex lists
-    int32_t *counts = nullptr;  // device int32[8]: list sizes [0..2], entries per bin [4..7] as int64 pair
-    int nlist[3] = {0, 0, 0};
-    int64_t entries[4] = {0, 0, 0, 0};  // stored entries in small, mid1, mid2, big rows
-    // big rows, split in chunks
-    int32_t *nch = nullptr;          // chunks per big row
+    int64_t upper[kNumBins - 1] = {8, 32, 128, 512, 2048, 12288};
+    int chunk = 4096;   // entries per CTA chunk of a bin-6 row
+    int32_t *list[kNumBins] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int nlist[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
+    int64_t entries[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
+    int32_t *counts = nullptr;  // device: [0..7] list sizes, then 8 int64 entry totals
+    // bin-6 rows, split in chunks
+    int32_t *nch = nullptr;          // chunks per row
     int32_t *chunk_first = nullptr;  // exclusive scan of nch (nb + 1)
-    int32_t *chunk_b = nullptr;      // big-list index of every chunk
+    int32_t *chunk_b = nullptr;      // bin-6 list index of every chunk
     int nchunks = 0;
     // global hash tables of multi-chunk rows
     int64_t *gcap = nullptr;   // slots (0 for single-chunk rows)
@@ -54,10 +60,19 @@ struct Bins {
     int32_t *gdone = nullptr;
     u64 *gloop = nullptr;
     int32_t *gkeys = nullptr;
-    u64 *gvals = nullptr;
+    void *gvals = nullptr;     // u32 or u64 per slot
     int32_t *glist = nullptr;
     int64_t gslots = 0;
 };
+
+// log2 of the shared table of CTA bin b (3..5): at least 4/3 of the bin's upper bound.
+inline int cta_log2cap(const Bins &b, int bin)
+{
+    const int64_t need = b.upper[bin] + b.upper[bin] / 3 + 1;
+    int l = 5;
+    while (((int64_t)1 << l) < need) l++;
+    return l;
+}
 
 struct LaunchCfg {
     int num_sms = 152;
@@ -89,12 +104,13 @@ int launch_compose(int64_t n0, const int32_t *prev, const int32_t *C, const int3
 
 // ---- k_move.cu: one synchronous sweep (Algorithm 1 body) over all bins
 struct SweepTimers {
-    cudaEvent_t ev[8];  // start/stop pairs for small, mid1, mid2, big
+    cudaEvent_t ev[2 * kNumBins];  // start/stop pair around each bin's kernel
     bool on = false;
 };
+// narrow: tables hold 32-bit sums (valid when 2W < 2^32); wide: int128 gains.
 int launch_sweep(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, bool wide,
-                 SweepStats *stats, unsigned *err, cudaStream_t s, const LaunchCfg &lc,
-                 SweepTimers *tm);
+                 bool narrow, SweepStats *stats, unsigned *err, cudaStream_t s,
+                 const LaunchCfg &lc, SweepTimers *tm);
 
 // ---- k_coarsen.cu: graph induction (Sec. 5.1.2), renumbered labels new_id[C[u]]
 struct CoarsenBufs {
@@ -106,22 +122,22 @@ struct CoarsenBufs {
     int32_t *ccnt = nullptr;      // k (distinct neighbours of each community)
     int32_t *tmp_col = nullptr;   // nnz
     u64 *tmp_w = nullptr;         // nnz
-    int32_t *clist = nullptr;     // small communities
-    int32_t *blist = nullptr;     // big communities
-    int32_t *counts = nullptr;    // device int32[4]
+    int32_t *clist = nullptr;     // community lists of bins 2..6 (5 regions of k entries)
+    int32_t *counts = nullptr;    // device int32[8]: list sizes of bins 2..6
     int64_t *scratch64 = nullptr;
     int32_t *scratch32 = nullptr;
 };
-// Stage 1: community sizes, next-level delta, member lists, flattened offsets, bins.
+// Stage 1: community sizes, next-level delta, member lists, flattened offsets, bins
+// (communities binned by entry count with the thresholds of `bins`, bins 2..6 used).
 int launch_coarsen_stage1(const DevGraph &g, const PhaseState &st, const int32_t *new_id,
-                          int64_t k, i64 *delta_next, CoarsenBufs &cb, cudaStream_t s,
-                          const LaunchCfg &lc);
-// Chunk counts and global-table sizes of the communities in cb.blist (big.nlist[2] of them).
-int launch_coarsen_bigprep(int64_t k, CoarsenBufs &cb, Bins &big, cudaStream_t s,
+                          int64_t k, i64 *delta_next, CoarsenBufs &cb, const Bins &bins,
+                          cudaStream_t s, const LaunchCfg &lc);
+// Chunk counts and global-table sizes of the bin-6 communities (bins.list[6]).
+int launch_coarsen_bigprep(int64_t k, CoarsenBufs &cb, Bins &bins, cudaStream_t s,
                            const LaunchCfg &lc);
 // Stage 2 (after the host read the bin counts): aggregate every community's entries.
 int launch_coarsen_stage2(const DevGraph &g, const PhaseState &st, const int32_t *new_id,
-                          int64_t k, CoarsenBufs &cb, int nsmall, Bins &big, unsigned *err,
+                          int64_t k, CoarsenBufs &cb, Bins &bins, bool narrow, unsigned *err,
                           cudaStream_t s, const LaunchCfg &lc);
 // Stage 3 (after the host allocated the next graph): row offsets and compaction.
 int launch_coarsen_rowptr(int64_t k, CoarsenBufs &cb, int64_t *rp_next, cudaStream_t s);

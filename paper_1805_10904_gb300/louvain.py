@@ -48,12 +48,16 @@ class Config(ctypes.Structure):
         ("vf_all_levels", ctypes.c_int32),
         ("checks", ctypes.c_int32),
         ("force_int128", ctypes.c_int32),
+        ("wide_sums", ctypes.c_int32),
         ("bin_small", ctypes.c_int32),
         ("bin_mid1", ctypes.c_int32),
         ("bin_mid2", ctypes.c_int32),
+        ("bin_cta1", ctypes.c_int32),
+        ("bin_cta2", ctypes.c_int32),
+        ("bin_cta3", ctypes.c_int32),
         ("chunk_entries", ctypes.c_int32),
         ("profile", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("reserved", ctypes.c_int32 * 4),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
@@ -242,8 +246,8 @@ class Louvain:
     def __init__(self, device: int = 0, theta=(1, 1_000_000), max_iters: int = 1000,
                  max_levels: int = 64, vertex_following: bool = True,
                  vf_all_levels: bool = False, checks: int = 1, force_int128: bool = False,
-                 bin_small: int = 0, bin_mid1: int = 0, bin_mid2: int = 0,
-                 chunk_entries: int = 0, profile: bool = False, torch_alloc: bool = True):
+                 wide_sums: bool = False, bins=None, chunk_entries: int = 0,
+                 profile: bool = False, torch_alloc: bool = True):
         lib = load()
         self._lib = lib
         cfg = Config()
@@ -255,8 +259,10 @@ class Louvain:
         cfg.vf_all_levels = int(vf_all_levels)
         cfg.checks = checks
         cfg.force_int128 = int(force_int128)
-        if bin_small or bin_mid1 or bin_mid2:
-            cfg.bin_small, cfg.bin_mid1, cfg.bin_mid2 = bin_small, bin_mid1, bin_mid2
+        cfg.wide_sums = int(wide_sums)
+        if bins is not None:  # (small, mid1, mid2, cta1, cta2, cta3)
+            (cfg.bin_small, cfg.bin_mid1, cfg.bin_mid2, cfg.bin_cta1, cfg.bin_cta2,
+             cfg.bin_cta3) = [int(x) for x in bins]
         if chunk_entries:
             cfg.chunk_entries = chunk_entries
         cfg.profile = int(profile)

@@ -61,12 +61,14 @@ def run_both(torch, lv, g, **kw):
 
 
 BIN_CONFIGS = [
-    {},                                                        # default bins
-    {"bin_small": 0, "bin_mid1": 0, "bin_mid2": 0},            # everything through chunks
-    {"bin_small": 1, "bin_mid1": 2, "bin_mid2": 3, "chunk_entries": 32},  # many multi-chunk rows
-    {"bin_small": 8, "bin_mid1": 32, "bin_mid2": 128, "chunk_entries": 4096},
+    {},                                                          # default bins
+    {"bins": (0, 0, 0, 0, 0, 12288)},                            # every row in one CTA
+    {"bins": (1, 2, 3, 4, 5, 6), "chunk_entries": 32},           # every bin, many chunked rows
+    {"bins": (0, 0, 0, 0, 0, 0), "chunk_entries": 32},           # every row chunked
     {"force_int128": True},
-    {"force_int128": True, "bin_small": 0, "bin_mid1": 0, "bin_mid2": 0, "chunk_entries": 32},
+    {"wide_sums": True, "bins": (2, 4, 8, 16, 32, 64), "chunk_entries": 64},
+    {"force_int128": True, "wide_sums": True, "bins": (0, 0, 0, 0, 0, 0), "chunk_entries": 32},
+    {"bins": (8, 32, 128, 512, 2048, 12288), "chunk_entries": 128},
 ]
 
 
@@ -89,7 +91,8 @@ def test_planted_partition_4096(torch, lv, cfg):
     assert_parity(res, ref)
 
 
-@pytest.mark.parametrize("scale,cfg", [(10, 0), (12, 0), (13, 1), (14, 2), (12, 4), (15, 0)])
+@pytest.mark.parametrize("scale,cfg", [(10, 0), (12, 0), (13, 1), (14, 2), (12, 4), (15, 0),
+                                       (14, 3), (13, 5), (12, 6), (15, 7), (16, 0)])
 def test_rmat_medium(torch, lv, scale, cfg):
     """R-MAT graphs (a=.57, b=c=.19): hubs spanning many chunks, isolated vertices,
     several tiles of every scan and a ragged tail."""
@@ -98,7 +101,7 @@ def test_rmat_medium(torch, lv, scale, cfg):
     assert_parity(res, ref)
 
 
-@pytest.mark.parametrize("n,cfg", [(20_000, 0), (7_777, 2), (30_001, 1)])
+@pytest.mark.parametrize("n,cfg", [(20_000, 0), (7_777, 2), (30_001, 1), (12_345, 5)])
 def test_chung_lu(torch, lv, n, cfg):
     g = gg.chung_lu(n, 2.1, 10.0, 1, 8, seed=n)
     res, ref = run_both(torch, lv, g, **BIN_CONFIGS[cfg])
