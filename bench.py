@@ -35,7 +35,8 @@ WORKLOAD = ("R-MAT scale 22 (4,194,304 vertices, edge factor 16, a=0.57 b=0.19 c
             "int32 ids, seed 22; full multi-level run to threshold 1e-6")
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129 * 1024 * 1024
-KERNEL_NAMES = ["k_move_small", "k_move_group<8>", "k_move_group<32>", "k_move_big"]
+KERNEL_NAMES = ["k_move_small", "k_move_group<8>", "k_move_group<32>", "k_move_cta<128>",
+                "k_move_cta<256>", "k_move_cta<1024>", "k_move_huge"]
 
 
 def parse_args(argv=None):

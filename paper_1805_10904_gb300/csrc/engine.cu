@@ -227,9 +227,21 @@ struct Runner {
     DBuf<Scalars> sc_buf;
     int kernels = 0;
 
+    void check_launches()
+    {
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && launch_site()) e = cudaErrorInvalidValue;
+        if (e != cudaSuccess) {
+            std::string where = launch_site() ? launch_site() : "a launch";
+            launch_site() = nullptr;
+            throw LvErr{e == cudaErrorMemoryAllocation ? LOUVAIN_ERR_OOM : LOUVAIN_ERR_CUDA,
+                        where + ": " + cudaGetErrorString(e)};
+        }
+    }
+
     void sync_scalars()
     {
-        CK(cudaGetLastError());
+        check_launches();
         CK(cudaMemcpyAsync(h->pinned, d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (h->pinned->err) {
@@ -810,6 +822,7 @@ int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int3
     R.A.ctx = h->cfg.alloc_ctx;
     R.A.s = R.s;
     int rc = LOUVAIN_OK;
+    launch_site() = nullptr;
     try {
         CK(cudaSetDevice(h->device));
         R.run(n, row_ptr, col_idx, weights, ptr_kind, res);

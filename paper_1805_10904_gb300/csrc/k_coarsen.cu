@@ -431,11 +431,11 @@ static void launch_cta(const CoarsenArgs<WT> &A, const int32_t *list, int nl, in
                        cudaStream_t s, const LaunchCfg &lc)
 {
     const size_t smem = ctable_bytes<VT>(l2);
-    cudaFuncSetAttribute(k_coarsen_cta<BLOCK, WT, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    set_dyn_smem(k_coarsen_cta<BLOCK, WT, VT>, smem, "k_coarsen_cta");
     const int per_sm = (int)((227 * 1024) / (smem + 1024));
     const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
     k_coarsen_cta<BLOCK, WT, VT><<<nl < maxg ? nl : maxg, BLOCK, smem, s>>>(A, list, nl, l2);
+    note_launch("k_coarsen_cta");
 }
 
 template <typename WT, typename VT>
@@ -466,12 +466,12 @@ static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *n
                    bins.glist,   bins.chunk,   bins.nchunks};
         const int l2 = 31 - __builtin_clz(2 * bins.chunk);
         const size_t smem = ctable_bytes<VT>(l2);
-        cudaFuncSetAttribute(k_coarsen_huge<WT, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        set_dyn_smem(k_coarsen_huge<WT, VT>, smem, "k_coarsen_huge");
         const int per_sm = (int)((227 * 1024) / (smem + 1024));
         const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
         k_coarsen_huge<WT, VT><<<bins.nchunks < maxg ? bins.nchunks : maxg, kCHugeBlock, smem, s>>>(
             A, B);
+        note_launch("k_coarsen_huge");
         launched++;
     }
     return launched;

@@ -504,6 +504,7 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
     if (g.n > 0) {
         k_move_small<WT, GT><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
             A, (int)b.upper[0]);
+        note_launch("k_move_small");
         launched++;
     }
     mark(1);
@@ -511,6 +512,7 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
     if (b.nlist[1] > 0) {
         k_move_group<8, 6, WT, GT, VT><<<grid_for(b.nlist[1], kBlock / 8, lc.max_blocks), kBlock,
                                          0, s>>>(A, b.list[1], b.nlist[1], 1);
+        note_launch("k_move_group<8>");
         launched++;
     }
     mark(3);
@@ -518,6 +520,7 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
     if (b.nlist[2] > 0) {
         k_move_group<32, 8, WT, GT, VT><<<grid_for(b.nlist[2], kBlock / 32, lc.max_blocks),
                                           kBlock, 0, s>>>(A, b.list[2], b.nlist[2], 2);
+        note_launch("k_move_group<32>");
         launched++;
     }
     mark(5);
@@ -531,21 +534,19 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
             const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
             const int grid = b.nlist[bin] < maxg ? b.nlist[bin] : maxg;
             if (kCtaBlock[cb] == 128) {
-                cudaFuncSetAttribute(k_move_cta<128, WT, GT, VT>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                set_dyn_smem(k_move_cta<128, WT, GT, VT>, smem, "k_move_cta<128>");
                 k_move_cta<128, WT, GT, VT><<<grid, 128, smem, s>>>(A, b.list[bin], b.nlist[bin],
                                                                     l2, bin);
             } else if (kCtaBlock[cb] == 256) {
-                cudaFuncSetAttribute(k_move_cta<256, WT, GT, VT>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                set_dyn_smem(k_move_cta<256, WT, GT, VT>, smem, "k_move_cta<256>");
                 k_move_cta<256, WT, GT, VT><<<grid, 256, smem, s>>>(A, b.list[bin], b.nlist[bin],
                                                                     l2, bin);
             } else {
-                cudaFuncSetAttribute(k_move_cta<1024, WT, GT, VT>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                set_dyn_smem(k_move_cta<1024, WT, GT, VT>, smem, "k_move_cta<1024>");
                 k_move_cta<1024, WT, GT, VT><<<grid, 1024, smem, s>>>(A, b.list[bin],
                                                                       b.nlist[bin], l2, bin);
             }
+            note_launch("k_move_cta");
             launched++;
         }
         mark(2 * bin + 1);
@@ -556,12 +557,12 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
                   b.gdone,   b.gloop,   b.gkeys,       b.gvals, b.glist, b.chunk, b.nchunks};
         const int l2 = 31 - __builtin_clz(2 * b.chunk);
         const size_t smem = table_bytes<VT>(l2);
-        cudaFuncSetAttribute(k_move_huge<WT, GT, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        set_dyn_smem(k_move_huge<WT, GT, VT>, smem, "k_move_huge");
         const int per_sm = (int)((227 * 1024) / (smem + 1024));
         const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
         const int grid = b.nchunks < maxg ? b.nchunks : maxg;
         k_move_huge<WT, GT, VT><<<grid, kHugeBlock, smem, s>>>(A, B);
+        note_launch("k_move_huge");
         launched++;
     }
     mark(13);

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 
 namespace lv {
 
@@ -234,6 +235,37 @@ __device__ __forceinline__ void tbl_insert(int *keys, VT *vals, int *list, int *
 }
 
 // ---------------------------------------------------------------- launch helpers
+// Name of the first launch site that left a CUDA error pending (for error messages).
+inline const char *&launch_site()
+{
+    static thread_local const char *site = nullptr;
+    return site;
+}
+inline void note_launch(const char *name)
+{
+    if (!launch_site() && cudaPeekAtLastError() != cudaSuccess) launch_site() = name;
+}
+
+// Raise a kernel's dynamic shared memory limit; on failure records the kernel's own
+// attributes in the launch-site message.
+template <typename K>
+inline void set_dyn_smem(K kernel, size_t bytes, const char *name)
+{
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+        cudaSuccess)
+        return;
+    if (launch_site()) return;
+    static thread_local char msg[256];
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    snprintf(msg, sizeof(msg),
+             "%s: dynamic smem %zu rejected (attr query %d: static %zu, max threads %d, regs %d, "
+             "max dyn %d)",
+             name, bytes, (int)e, a.sharedSizeBytes, a.maxThreadsPerBlock, a.numRegs,
+             a.maxDynamicSharedSizeBytes);
+    launch_site() = msg;
+}
+
 inline int grid_for(int64_t work_items, int per_block, int max_blocks)
 {
     int64_t g = (work_items + per_block - 1) / per_block;

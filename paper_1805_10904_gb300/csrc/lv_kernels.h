@@ -65,10 +65,11 @@ struct Bins {
     int64_t gslots = 0;
 };
 
-// log2 of the shared table of CTA bin b (3..5): at least 4/3 of the bin's upper bound.
+// log2 of the shared table of CTA bin b (3..5): at least 4/3 of the bin's upper bound, so
+// the load factor stays <= 0.75 and there are always more slots than distinct keys.
 inline int cta_log2cap(const Bins &b, int bin)
 {
-    const int64_t need = b.upper[bin] + b.upper[bin] / 3 + 1;
+    const int64_t need = b.upper[bin] + b.upper[bin] / 3;
     int l = 5;
     while (((int64_t)1 << l) < need) l++;
     return l;
