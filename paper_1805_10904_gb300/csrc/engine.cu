@@ -114,9 +114,9 @@ struct Scalars {
     u64 tw;
     SweepStats st;
     LevelCtl ctl;
-    int32_t bin_counts[24];
-    int32_t ccounts[8];
-    u64 cand_total[8];
+    int32_t bin_counts[40];
+    int32_t ccounts[16];
+    u64 cand_total[kNumBins + 1];
     int32_t tail[8];
 };
 
@@ -354,8 +354,8 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
 
     // ---------------- per-run buffers sized by level 0 (Theorem 1: levels never grow)
     const int64_t scratch_n = scan_scratch_elems(n0 + 1) + 64;
-    DBuf<int32_t> lists;  // bins 1..6, n0 entries each
-    lists.reset(&A, (size_t)n0 * (kNumBins - 1));
+    DBuf<int32_t> lists;  // rows of bins 1.., grouped by bin
+    lists.reset(&A, (size_t)n0);
     DBuf<int32_t> b_nch, b_chunk_first, b_glog2, b_gcnt, b_gdone;
     DBuf<int64_t> b_gcap, b_goff;
     DBuf<u64> b_gloop;
@@ -377,7 +377,7 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     tr_qn.reset(&A, 2 * (size_t)tcap);
     std::vector<i64> h_tr_moved(tcap), h_tr_qn(2 * (size_t)tcap);
     // coarsening buffers
-    DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_clist, c_tmp_col;
+    DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_tmp_col;
     DBuf<int64_t> c_mpre;
     DBuf<u64> c_tmp_w;
     // graph buffers of the levels above 0
@@ -389,9 +389,9 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     DBuf<u64> gvals;
 
     SweepTimers tm;
-    double t_kernel[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
-    int64_t launches_kernel[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
-    double bytes_kernel[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
+    double t_kernel[kNumBins] = {};
+    int64_t launches_kernel[kNumBins] = {};
+    double bytes_kernel[kNumBins] = {};
     if (cfg.profile) {
         for (auto &e : tm.ev) CK(cudaEventCreate(&e));
         tm.on = true;
@@ -412,15 +412,21 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     st.size = size.p;
     st.delta = delta.p;
 
-    // bin thresholds: every table must fit shared memory with the chosen sum width
+    // bin thresholds: every table must fit shared memory with the chosen sum width; the
+    // cluster bins hold rows up to CL times the bin-5 bound (CL CTAs, bin-5 table each);
+    // cluster sizes that cannot be resident are left empty.
     Bins proto;
-    const int32_t thr[kNumBins - 1] = {cfg.bin_small, cfg.bin_mid1, cfg.bin_mid2,
-                                       cfg.bin_cta1,  cfg.bin_cta2, cfg.bin_cta3};
-    for (int t = 0; t < kNumBins - 1; t++) proto.upper[t] = thr[t];
+    const int32_t thr[6] = {cfg.bin_small, cfg.bin_mid1, cfg.bin_mid2,
+                            cfg.bin_cta1,  cfg.bin_cta2, cfg.bin_cta3};
+    for (int t = 0; t < 6; t++) proto.upper[t] = thr[t];
     if (!narrow && proto.upper[5] > 6144) {
         proto.upper[5] = 6144;
         for (int t = 4; t >= 0; t--)
             if (proto.upper[t] > proto.upper[t + 1]) proto.upper[t] = proto.upper[t + 1];
+    }
+    for (int t = 0; t < 4; t++) {
+        const int64_t cl = (int64_t)kBinSpec[6 + t].cluster;
+        proto.upper[6 + t] = lc.cluster_ok[t] ? proto.upper[5] * cl : proto.upper[5 + t];
     }
     proto.chunk = cfg.chunk_entries;
     proto.nch = b_nch.p;
@@ -432,11 +438,11 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     proto.gdone = b_gdone.p;
     proto.gloop = b_gloop.p;
 
-    // sets up chunk lists and global tables of bin 6 (after nlist[6] is known)
+    // sets up chunk lists and global tables of the chunked bin (after its size is known)
     auto prep_huge = [&](Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *cbp) {
         b.nchunks = 0;
         b.gslots = 0;
-        const int nb = b.nlist[6];
+        const int nb = b.nlist[kChunkedBin];
         if (nb == 0) return;
         if (coarsen_side) kernels += launch_coarsen_bigprep(k_comm, *cbp, b, s, lc);
         else kernels += launch_big_prep(G, b, scratch64.p, scratch32.p, s, lc);
@@ -476,17 +482,19 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         if (cfg.vertex_following && (level == 0 || cfg.vf_all_levels))
             kernels += launch_vertex_following(G, st, s, lc);
 
-        // degree bins
+        // degree bins: count, then fill the list grouped by bin
         Bins bins = proto;
-        for (int b = 1; b < kNumBins; b++) bins.list[b] = lists.p + (size_t)(b - 1) * n0;
+        bins.list = lists.p;
         bins.counts = &d_sc->bin_counts[0];
-        kernels += launch_bin(G, bins, s, lc);
+        kernels += launch_bin_count(G, bins, s, lc);
         sync_scalars();
-        for (int b = 1; b < kNumBins; b++) bins.nlist[b] = h->pinned->bin_counts[b];
-        for (int b = 0; b < kNumBins; b++)
-            memcpy(&bins.entries[b], &h->pinned->bin_counts[8 + 2 * b], sizeof(int64_t));
-        bins.nlist[0] = (int)(n - bins.nlist[1] - bins.nlist[2] - bins.nlist[3] - bins.nlist[4] -
-                              bins.nlist[5] - bins.nlist[6]);
+        bins.off[0] = bins.off[1] = 0;
+        for (int b = 0; b < kNumBins; b++) {
+            bins.nlist[b] = h->pinned->bin_counts[b];
+            memcpy(&bins.entries[b], &h->pinned->bin_counts[16 + 2 * b], sizeof(int64_t));
+            if (b >= 1) bins.off[b + 1] = bins.off[b] + bins.nlist[b];
+        }
+        kernels += launch_bin_fill(G, bins, s, lc);
         prep_huge(bins, false, 0, nullptr);
 
         // phase controller
@@ -500,7 +508,7 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         CK(cudaMemcpyAsync(&d_sc->ctl, &h->pinned->ctl, sizeof(LevelCtl), cudaMemcpyHostToDevice,
                            s));
         CK(cudaMemsetAsync(&d_sc->st, 0, sizeof(SweepStats), s));
-        CK(cudaMemsetAsync(&d_sc->cand_total[0], 0, sizeof(u64) * 8, s));
+        CK(cudaMemsetAsync(&d_sc->cand_total[0], 0, sizeof(u64) * (kNumBins + 1), s));
 
         // sweeps (Algorithm 1); one host read of the controller per sweep
         int sweeps = 0;
@@ -517,7 +525,8 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
                     float ms = 0.f;
                     CK(cudaEventElapsedTime(&ms, tm.ev[2 * b], tm.ev[2 * b + 1]));
                     t_kernel[b] += ms;
-                    launches_kernel[b] += b == 0 ? 1 : (b == 6 ? bins.nchunks > 0 : bins.nlist[b] > 0);
+                    launches_kernel[b] +=
+                        b == 0 ? 1 : (b == kChunkedBin ? bins.nchunks > 0 : bins.nlist[b] > 0);
                 }
             }
             if (h->pinned->ctl.done) break;
@@ -530,8 +539,8 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         const i128 qn_final = limbs_to_i128(hc.qn_final);
         const i128 qn_init = limbs_to_i128(hc.qn_init);
         const int hit_cap = hc.hit_cap;
-        u64 cand_level[8];
-        for (int b = 0; b < 8; b++) cand_level[b] = h->pinned->cand_total[b];
+        u64 cand_level[kNumBins];
+        for (int b = 0; b < kNumBins; b++) cand_level[b] = h->pinned->cand_total[b];
         if (iters > 0) {
             CK(cudaMemcpyAsync(h_tr_moved.data(), tr_moved.p, sizeof(i64) * iters,
                                cudaMemcpyDeviceToHost, s));
@@ -590,7 +599,6 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
             c_members.reset(&A, n0);
             c_mpre.reset(&A, (size_t)n0 + 1);
             c_ccnt.reset(&A, n0);
-            c_clist.reset(&A, (size_t)n0 * 5);
             c_tmp_col.reset(&A, (size_t)nnz);
             c_tmp_w.reset(&A, (size_t)nnz);
         }
@@ -603,17 +611,19 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         cb.ccnt = c_ccnt.p;
         cb.tmp_col = c_tmp_col.p;
         cb.tmp_w = c_tmp_w.p;
-        cb.clist = c_clist.p;
         cb.counts = &d_sc->ccounts[0];
         cb.scratch32 = scratch32.p;
         cb.scratch64 = scratch64.p;
-        kernels += launch_coarsen_stage1(G, st, new_id.p, k, delta_next.p, cb, proto, s, lc);
-        sync_scalars();
         Bins cbins = proto;
-        for (int r = 0; r < 5; r++) {
-            cbins.list[2 + r] = c_clist.p + (size_t)r * k;
-            cbins.nlist[2 + r] = h->pinned->ccounts[r];
+        kernels += launch_coarsen_stage1(G, st, new_id.p, k, delta_next.p, cb, cbins, s, lc);
+        sync_scalars();
+        cbins.list = lists.p;  // the sweep's lists are free again
+        cbins.off[0] = cbins.off[1] = cbins.off[2] = 0;
+        for (int b = 0; b < kNumBins; b++) {
+            cbins.nlist[b] = b < 2 ? 0 : h->pinned->ccounts[b];
+            if (b >= 2) cbins.off[b + 1] = cbins.off[b] + cbins.nlist[b];
         }
+        kernels += launch_coarsen_binfill(k, cb, cbins, s, lc);
         prep_huge(cbins, true, k, &cb);
         kernels += launch_coarsen_stage2(G, st, new_id.p, k, cb, cbins, narrow, &d_sc->err, s, lc);
         g_rp_next.reset(&A, (size_t)k + 1);
@@ -778,6 +788,12 @@ int louvain_create(const louvain_config *cfg, int device, louvain_handle **out)
     }
     h->lc.num_sms = sms;
     h->lc.max_blocks = sms * 8;
+    {
+        Bins b;
+        b.upper[5] = c.bin_cta3;
+        probe_cluster_support(shared_table_bytes(cta_log2cap(b, 5), true), h->lc.cluster_ok);
+        cudaGetLastError();
+    }
     *out = h;
     return LOUVAIN_OK;
 }

@@ -15,6 +15,8 @@
 // Rows of the induced graph are not sorted; nothing downstream depends on their order.
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "lv_common.cuh"
 #include "lv_kernels.h"
 #include "lv_scan.cuh"
@@ -61,36 +63,40 @@ __device__ __forceinline__ int64_t comm_entries(const int32_t *moff, const int64
     return mpre[moff[a + 1]] - mpre[moff[a]];
 }
 
-// Communities binned by entry count with the sweep's thresholds; bins 0..2 all go to the
-// warp kernel.  clist holds 5 regions of k entries (bins 2..6), counts[r] their sizes.
+// Communities binned by entry count with the sweep's thresholds (rows of bins 0..2 all go
+// to the warp kernel of bin 2).  Count pass: counts[b] and entries; fill pass: list regions.
 struct CBinArgs {
     int64_t upper[kNumBins - 1];
+    int64_t off[kNumBins + 1];
+    int32_t *list;
 };
 
+template <bool FILL>
 __global__ void __launch_bounds__(kBlock) k_coarsen_bin(int64_t k, const int32_t *moff,
                                                         const int64_t *mpre, CBinArgs ba,
-                                                        int32_t *clist, int32_t *counts)
+                                                        int32_t *counts)
 {
     const int lane = threadIdx.x & 31;
     for (int64_t a0 = (int64_t)blockIdx.x * blockDim.x; a0 < k; a0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = a0 + threadIdx.x;
-        int r = -1;
+        int bin = -1;
         if (a < k) {
             const int64_t e = comm_entries(moff, mpre, (int32_t)a);
             int b = 0;
 #pragma unroll
             for (int t = 0; t < kNumBins - 1; t++) b += e > ba.upper[t];
-            r = b < 2 ? 0 : b - 2;
+            bin = b < 2 ? 2 : b;
         }
 #pragma unroll
-        for (int b = 0; b < 5; b++) {
-            const unsigned mask = __ballot_sync(0xffffffffu, r == b);
+        for (int b = 2; b < kNumBins; b++) {
+            const unsigned mask = __ballot_sync(0xffffffffu, bin == b);
             if (!mask) continue;
             const int leader = __ffs(mask) - 1;
             int base = 0;
             if (lane == leader) base = atomicAdd(&counts[b], __popc(mask));
+            if (!FILL) continue;
             base = __shfl_sync(0xffffffffu, base, leader);
-            if (r == b) clist[(int64_t)b * k + base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)a;
+            if (bin == b) ba.list[ba.off[b] + base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)a;
         }
     }
 }
@@ -258,6 +264,84 @@ __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const 
     }
 }
 
+namespace cg = cooperative_groups;
+
+template <int CL>
+struct CLog2 {
+    static constexpr int v = CL <= 1 ? 0 : 1 + CLog2<CL / 2>::v;
+};
+template <>
+struct CLog2<1> {
+    static constexpr int v = 0;
+};
+
+// Large communities: one thread-block cluster per community, the table partitioned over
+// the cluster's distributed shared memory by key hash; each CTA writes its part of the row.
+template <int CL, typename WT, typename VT>
+__global__ void __launch_bounds__(1024) k_coarsen_cluster(CoarsenArgs<WT> A, const int32_t *clist,
+                                                          int ncl, int log2cap)
+{
+    constexpr int BLOCK = 1024;
+    constexpr int LOG2CL = CLog2<CL>::v;
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int cap = 1 << log2cap;
+    VT *vals = (VT *)smem;
+    int *keys = (int *)(vals + cap);
+    int *list = keys + cap;
+    __shared__ int s_cnt;
+    __shared__ int s_off, s_tot;
+    for (int s = threadIdx.x; s < cap; s += BLOCK) {
+        keys[s] = -1;
+        vals[s] = 0;
+    }
+    if (threadIdx.x == 0) s_cnt = 0;
+    cluster.sync();
+    const int cid = blockIdx.x / CL, nclu = gridDim.x / CL;
+    const int64_t stride = (int64_t)CL * BLOCK;
+    for (int v = cid; v < ncl; v += nclu) {
+        const int32_t a = clist[v];
+        const int32_t pb = A.moff[a], pe = A.moff[a + 1];
+        const int64_t tb = A.mpre[pb], te = A.mpre[pe];
+        int32_t p = pb;
+        for (int64_t t = tb + (int64_t)rank * BLOCK + threadIdx.x; t < te; t += stride) {
+            int32_t key;
+            i64 wv;
+            flat_entry(A, p, pe, t, key, wv);
+            cluster_insert<VT>(cluster, keys, vals, list, &s_cnt, LOG2CL, log2cap, key, (VT)wv,
+                               A.err);
+        }
+        cluster.sync();  // every insert has landed
+        if (threadIdx.x == 0) {
+            int off = 0, tot = 0;
+            for (int r = 0; r < CL; r++) {
+                const int c = *cluster.map_shared_rank(&s_cnt, r);
+                if (r < (int)rank) off += c;
+                tot += c;
+            }
+            s_off = off;
+            s_tot = tot;
+        }
+        cluster.sync();  // every CTA has read every count
+        const int m = s_cnt;
+        const int off = s_off;
+        for (int q = threadIdx.x; q < m; q += BLOCK) {
+            const int s = list[q];
+            A.tmp_col[tb + off + q] = keys[s];
+            A.tmp_w[tb + off + q] = (u64)vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (rank == 0) A.ccnt[a] = s_tot;
+            s_cnt = 0;
+        }
+        cluster.sync();  // tables cleared before the next community's inserts
+    }
+}
+
 struct CBigArgs {
     const int32_t *blist;
     const int32_t *chunk_b;
@@ -395,8 +479,17 @@ struct I32AsI64In {
 
 // ------------------------------------------------------------------ launchers
 
+static CBinArgs cbin_args(const Bins &b)
+{
+    CBinArgs ba;
+    for (int t = 0; t < kNumBins - 1; t++) ba.upper[t] = b.upper[t];
+    for (int t = 0; t <= kNumBins; t++) ba.off[t] = b.off[t];
+    ba.list = b.list;
+    return ba;
+}
+
 int launch_coarsen_stage1(const DevGraph &g, const PhaseState &st, const int32_t *new_id,
-                          int64_t k, i64 *delta_next, CoarsenBufs &cb, const Bins &bins,
+                          int64_t k, i64 *delta_next, CoarsenBufs &cb, Bins &bins,
                           cudaStream_t s, const LaunchCfg &lc)
 {
     int launched = 0;
@@ -411,13 +504,20 @@ int launch_coarsen_stage1(const DevGraph &g, const PhaseState &st, const int32_t
         n, st.C, new_id, cb.moff, cb.cursor, cb.members);
     launched++;
     launched += exclusive_scan<int64_t>(MemberDegIn{cb.members, g.rp}, n, cb.mpre, cb.scratch64, s);
-    cudaMemsetAsync(cb.counts, 0, sizeof(int32_t) * 8, s);
-    CBinArgs ba;
-    for (int t = 0; t < kNumBins - 1; t++) ba.upper[t] = bins.upper[t];
-    k_coarsen_bin<<<grid_for(k, kBlock, lc.max_blocks), kBlock, 0, s>>>(k, cb.moff, cb.mpre, ba,
-                                                                        cb.clist, cb.counts);
+    cudaMemsetAsync(cb.counts, 0, sizeof(int32_t) * 16, s);
+    k_coarsen_bin<false><<<grid_for(k, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        k, cb.moff, cb.mpre, cbin_args(bins), cb.counts);
     launched++;
     return launched;
+}
+
+int launch_coarsen_binfill(int64_t k, CoarsenBufs &cb, Bins &bins, cudaStream_t s,
+                           const LaunchCfg &lc)
+{
+    cudaMemsetAsync(cb.counts, 0, sizeof(int32_t) * 16, s);
+    k_coarsen_bin<true><<<grid_for(k, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        k, cb.moff, cb.mpre, cbin_args(bins), cb.counts);
+    return 1;
 }
 
 template <typename VT>
@@ -426,16 +526,48 @@ inline size_t ctable_bytes(int log2cap)
     return ((size_t)1 << log2cap) * (sizeof(VT) + 8);
 }
 
-template <int BLOCK, typename WT, typename VT>
-static void launch_cta(const CoarsenArgs<WT> &A, const int32_t *list, int nl, int l2,
-                       cudaStream_t s, const LaunchCfg &lc)
+template <typename K>
+static int cta_grid(K kernel, int block, size_t smem, int nrows, const LaunchCfg &lc,
+                    const char *name)
 {
-    const size_t smem = ctable_bytes<VT>(l2);
-    set_dyn_smem(k_coarsen_cta<BLOCK, WT, VT>, smem, "k_coarsen_cta");
-    const int per_sm = (int)((227 * 1024) / (smem + 1024));
-    const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
-    k_coarsen_cta<BLOCK, WT, VT><<<nl < maxg ? nl : maxg, BLOCK, smem, s>>>(A, list, nl, l2);
-    note_launch("k_coarsen_cta");
+    set_dyn_smem(kernel, smem, name);
+    const int per_sm_smem = (int)((227 * 1024) / (smem + 1024));
+    const int per_sm_thr = 2048 / block;
+    int per_sm = per_sm_smem < per_sm_thr ? per_sm_smem : per_sm_thr;
+    if (per_sm < 1) per_sm = 1;
+    const int maxg = lc.num_sms * per_sm;
+    return nrows < maxg ? nrows : maxg;
+}
+
+template <int CL, typename K, typename... Args>
+static int cluster_launch(K kernel, size_t smem, int nrows, cudaStream_t s, const char *name,
+                          Args... args)
+{
+    set_dyn_smem(kernel, smem, name);
+    if (CL > 8) cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(CL, 1, 1);
+    int maxc = 0;
+    if (cudaOccupancyMaxActiveClusters(&maxc, kernel, &cfg) != cudaSuccess || maxc < 1) {
+        cudaGetLastError();
+        if (!launch_site()) launch_site() = name;
+        return 0;
+    }
+    const int nclusters = nrows < maxc ? nrows : maxc;
+    cfg.gridDim = dim3((unsigned)(nclusters * CL), 1, 1);
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+    note_launch(name);
+    return 1;
 }
 
 template <typename WT, typename VT>
@@ -446,33 +578,64 @@ static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *n
     CoarsenArgs<WT> A{g.rp,       g.col,       (const WT *)g.w, st.C,       new_id, cb.moff,
                       cb.members, cb.mpre,     cb.ccnt,         cb.tmp_col, cb.tmp_w, err};
     int launched = 0;
-    if (bins.nlist[2] > 0) {
-        k_coarsen_group<WT, VT><<<grid_for(bins.nlist[2], kBlock / 32, lc.max_blocks), kBlock, 0,
-                                  s>>>(A, bins.list[2], bins.nlist[2]);
-        launched++;
-    }
-    for (int cbn = 0; cbn < kCtaBins; cbn++) {
-        const int bin = 3 + cbn;
-        if (bins.nlist[bin] == 0) continue;
-        const int l2 = cta_log2cap(bins, bin);
-        if (kCtaBlock[cbn] == 128) launch_cta<128, WT, VT>(A, bins.list[bin], bins.nlist[bin], l2, s, lc);
-        else if (kCtaBlock[cbn] == 256) launch_cta<256, WT, VT>(A, bins.list[bin], bins.nlist[bin], l2, s, lc);
-        else launch_cta<1024, WT, VT>(A, bins.list[bin], bins.nlist[bin], l2, s, lc);
-        launched++;
-    }
-    if (bins.nchunks > 0) {
-        CBigArgs B{bins.list[6], bins.chunk_b, bins.chunk_first, bins.nch,   bins.goff,
-                   bins.glog2,   bins.gcnt,    bins.gdone,       bins.gkeys, bins.gvals,
-                   bins.glist,   bins.chunk,   bins.nchunks};
-        const int l2 = 31 - __builtin_clz(2 * bins.chunk);
-        const size_t smem = ctable_bytes<VT>(l2);
-        set_dyn_smem(k_coarsen_huge<WT, VT>, smem, "k_coarsen_huge");
-        const int per_sm = (int)((227 * 1024) / (smem + 1024));
-        const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
-        k_coarsen_huge<WT, VT><<<bins.nchunks < maxg ? bins.nchunks : maxg, kCHugeBlock, smem, s>>>(
-            A, B);
-        note_launch("k_coarsen_huge");
-        launched++;
+    for (int bin = 2; bin < kNumBins; bin++) {
+        const BinSpec sp = kBinSpec[bin];
+        const int nr = bins.nlist[bin];
+        const int32_t *rows = bins.rows(bin);
+        if (nr == 0 && sp.kind != BIN_CHUNKED) continue;
+        if (sp.kind == BIN_WARP) {
+            k_coarsen_group<WT, VT><<<grid_for(nr, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(
+                A, rows, nr);
+            note_launch("k_coarsen_group");
+            launched++;
+        } else if (sp.kind == BIN_CTA) {
+            const int l2 = cta_log2cap(bins, bin);
+            const size_t smem = ctable_bytes<VT>(l2);
+            if (sp.block == 128) {
+                const int grid = cta_grid(k_coarsen_cta<128, WT, VT>, 128, smem, nr, lc, "k_coarsen_cta");
+                k_coarsen_cta<128, WT, VT><<<grid, 128, smem, s>>>(A, rows, nr, l2);
+            } else if (sp.block == 256) {
+                const int grid = cta_grid(k_coarsen_cta<256, WT, VT>, 256, smem, nr, lc, "k_coarsen_cta");
+                k_coarsen_cta<256, WT, VT><<<grid, 256, smem, s>>>(A, rows, nr, l2);
+            } else {
+                const int grid = cta_grid(k_coarsen_cta<1024, WT, VT>, 1024, smem, nr, lc, "k_coarsen_cta");
+                k_coarsen_cta<1024, WT, VT><<<grid, 1024, smem, s>>>(A, rows, nr, l2);
+            }
+            note_launch("k_coarsen_cta");
+            launched++;
+        } else if (sp.kind == BIN_CLUSTER) {
+            const int l2 = cta_log2cap(bins, bin);
+            const size_t smem = ctable_bytes<VT>(l2);
+            switch (sp.cluster) {
+            case 2:
+                launched += cluster_launch<2>(k_coarsen_cluster<2, WT, VT>, smem, nr, s,
+                                              "k_coarsen_cluster<2>", A, rows, nr, l2);
+                break;
+            case 4:
+                launched += cluster_launch<4>(k_coarsen_cluster<4, WT, VT>, smem, nr, s,
+                                              "k_coarsen_cluster<4>", A, rows, nr, l2);
+                break;
+            case 8:
+                launched += cluster_launch<8>(k_coarsen_cluster<8, WT, VT>, smem, nr, s,
+                                              "k_coarsen_cluster<8>", A, rows, nr, l2);
+                break;
+            default:
+                launched += cluster_launch<16>(k_coarsen_cluster<16, WT, VT>, smem, nr, s,
+                                               "k_coarsen_cluster<16>", A, rows, nr, l2);
+                break;
+            }
+        } else if (sp.kind == BIN_CHUNKED && bins.nchunks > 0) {
+            CBigArgs B{rows,       bins.chunk_b, bins.chunk_first, bins.nch,   bins.goff,
+                       bins.glog2, bins.gcnt,    bins.gdone,       bins.gkeys, bins.gvals,
+                       bins.glist, bins.chunk,   bins.nchunks};
+            const int l2 = 31 - __builtin_clz(2 * bins.chunk);
+            const size_t smem = ctable_bytes<VT>(l2);
+            const int grid = cta_grid(k_coarsen_huge<WT, VT>, kCHugeBlock, smem, bins.nchunks, lc,
+                                      "k_coarsen_huge");
+            k_coarsen_huge<WT, VT><<<grid, kCHugeBlock, smem, s>>>(A, B);
+            note_launch("k_coarsen_huge");
+            launched++;
+        }
     }
     return launched;
 }
@@ -492,10 +655,11 @@ int launch_coarsen_stage2(const DevGraph &g, const PhaseState &st, const int32_t
 int launch_coarsen_bigprep(int64_t k, CoarsenBufs &cb, Bins &bins, cudaStream_t s,
                            const LaunchCfg &lc)
 {
-    const int nb = bins.nlist[6];
+    const int nb = bins.nlist[kChunkedBin];
     if (nb == 0) return 0;
     k_cbig_prep<<<grid_for(nb, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        nb, bins.list[6], cb.moff, cb.mpre, k, bins.chunk, bins.nch, bins.gcap, bins.glog2);
+        nb, bins.rows(kChunkedBin), cb.moff, cb.mpre, k, bins.chunk, bins.nch, bins.gcap,
+        bins.glog2);
     int launched = 1;
     launched += exclusive_scan<int32_t>(ArrayIn<int32_t>{bins.nch}, nb, bins.chunk_first,
                                         cb.scratch32, s);

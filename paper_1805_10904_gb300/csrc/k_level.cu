@@ -218,10 +218,13 @@ int launch_vertex_following(const DevGraph &g, const PhaseState &st, cudaStream_
 }
 
 // ------------------------------------------------------------------ degree bins
-// counts[b] (b = 1..6): list sizes; counts + 8 + 2b: entries of bin b as a 64-bit value.
+// Pass 1 counts rows (counts[b]) and entries (int64 at counts + 16 + 2b) per bin; pass 2
+// writes each row of bins 1.. into its bin's region of the list (order within a bin is
+// not specified).  counts[b] is reused as the fill cursor of bin b.
 struct BinArgs {
     int64_t upper[kNumBins - 1];
-    int32_t *list[kNumBins];
+    int64_t off[kNumBins + 1];
+    int32_t *list;
 };
 
 __device__ __forceinline__ int bin_of(int64_t d, const int64_t *upper)
@@ -232,52 +235,76 @@ __device__ __forceinline__ int bin_of(int64_t d, const int64_t *upper)
     return b;
 }
 
+template <bool FILL>
 __global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, BinArgs ba,
                                                 int32_t *counts)
 {
     const int lane = threadIdx.x & 31;
-    u64 ent[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
+    u64 ent[kNumBins] = {};
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n;
          i0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = i0 + threadIdx.x;
         int bin = -1;
+        int64_t d = 0;
         if (i < n) {
-            const int64_t d = rp[i + 1] - rp[i];
+            d = rp[i + 1] - rp[i];
             bin = bin_of(d, ba.upper);
-#pragma unroll
-            for (int b = 0; b < kNumBins; b++)
-                if (b == bin) ent[b] += (u64)d;
         }
 #pragma unroll
-        for (int b = 1; b < kNumBins; b++) {
+        for (int b = 0; b < kNumBins; b++) {
             const unsigned mask = __ballot_sync(0xffffffffu, bin == b);
             if (!mask) continue;
+            if (!FILL) {
+                if (bin == b) ent[b] += (u64)d;
+                if (lane == __ffs(mask) - 1) atomicAdd(&counts[b], __popc(mask));
+                continue;
+            }
+            if (b == 0) continue;
             const int leader = __ffs(mask) - 1;
             int base = 0;
             if (lane == leader) base = atomicAdd(&counts[b], __popc(mask));
             base = __shfl_sync(0xffffffffu, base, leader);
-            if (bin == b) ba.list[b][base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
+            if (bin == b)
+                ba.list[ba.off[b] + base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
         }
     }
+    if (!FILL) {
 #pragma unroll
-    for (int b = 0; b < kNumBins; b++) {
-        u64 v = sum_reduce(ent[b], 32);
-        if (lane == 0 && v) atomicAdd((u64 *)(counts + 8 + 2 * b), v);
+        for (int b = 0; b < kNumBins; b++) {
+            u64 v = sum_reduce(ent[b], 32);
+            if (lane == 0 && v) atomicAdd((u64 *)(counts + 16 + 2 * b), v);
+        }
     }
 }
 
-int launch_bin(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc)
+static BinArgs bin_args(const Bins &b)
 {
-    cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * 24, s);
-    if (g.n == 0) return 0;
     BinArgs ba;
     for (int t = 0; t < kNumBins - 1; t++) ba.upper[t] = b.upper[t];
-    for (int t = 0; t < kNumBins; t++) ba.list[t] = b.list[t];
-    k_bin<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(g.n, g.rp, ba, b.counts);
+    for (int t = 0; t <= kNumBins; t++) ba.off[t] = b.off[t];
+    ba.list = b.list;
+    return ba;
+}
+
+int launch_bin_count(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc)
+{
+    cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * (16 + 2 * kNumBins), s);
+    if (g.n == 0) return 0;
+    k_bin<false><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(g.n, g.rp, bin_args(b),
+                                                                        b.counts);
     return 1;
 }
 
-// Bin-6 rows: chunk counts and, for multi-chunk rows, a global table of 2^k >= 2*min(d, n)
+int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc)
+{
+    cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * 16, s);
+    if (g.n == 0) return 0;
+    k_bin<true><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(g.n, g.rp, bin_args(b),
+                                                                       b.counts);
+    return 1;
+}
+
+// Chunked rows: chunk counts and, for multi-chunk rows, a global table of 2^k >= 2*min(d, n)
 // slots (distinct neighbour labels <= min(d, n) < slots, so it never fills).
 __global__ void k_big_prep(int nb, const int32_t *bverts, const int64_t *rp, int64_t n, int chunk,
                            int32_t *nch, int64_t *gcap, int32_t *glog2)
@@ -303,10 +330,10 @@ __global__ void k_big_prep(int nb, const int32_t *bverts, const int64_t *rp, int
 int launch_big_prep(const DevGraph &g, Bins &b, int64_t *scratch64, int32_t *scratch32,
                     cudaStream_t s, const LaunchCfg &lc)
 {
-    const int nb = b.nlist[6];
+    const int nb = b.nlist[kChunkedBin];
     if (nb == 0) return 0;
     k_big_prep<<<grid_for(nb, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        nb, b.list[6], g.rp, g.n, b.chunk, b.nch, b.gcap, b.glog2);
+        nb, b.rows(kChunkedBin), g.rp, g.n, b.chunk, b.nch, b.gcap, b.glog2);
     int k = 1;
     k += exclusive_scan<int32_t>(ArrayIn<int32_t>{b.nch}, nb, b.chunk_first, scratch32, s);
     k += exclusive_scan<int64_t>(ArrayIn<int64_t>{b.gcap}, nb, b.goff, scratch64, s);
@@ -324,7 +351,7 @@ __global__ void k_big_fill(int nb, const int32_t *nch, const int32_t *chunk_firs
 
 int launch_big_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc)
 {
-    const int nb = b.nlist[6];
+    const int nb = b.nlist[kChunkedBin];
     if (nb == 0) return 0;
     k_big_fill<<<grid_for(nb, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(nb, b.nch,
                                                                            b.chunk_first, b.chunk_b);

@@ -18,10 +18,15 @@
 //   bin 0    one thread per vertex, neighbours aggregated in registers (dense over all i),
 //   bin 1-2  8-lane groups / whole warps, one shared-memory hash table per group,
 //   bin 3-5  one CTA per row with a shared-memory table sized for the bin (up to 16K slots),
-//   bin 6    CTA-sized chunks of a row; a row spanning several chunks merges its chunk
+//   bin 6-9  a thread-block cluster of 2-16 CTAs per row; the table is partitioned over the
+//            cluster's distributed shared memory by key hash (inserts are DSMEM atomics),
+//            each CTA scans its own part, and rank 0 combines the partial argmaxes,
+//   bin 10   CTA-sized chunks of a row; a row spanning several chunks merges its chunk
 //            tables into a global-memory table and the last chunk to finish decides.
 // Table values are 32-bit when 2W < 2^32 (every e_{i->c} <= delta_i <= 2W fits), else 64-bit.
 #include <climits>
+
+#include <cooperative_groups.h>
 
 #include "lv_common.cuh"
 #include "lv_kernels.h"
@@ -326,7 +331,127 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
     block_flush_stats(A.st, slot, internal, moved, cand, 0);
 }
 
-// ------------------------------------------------------------------ bin 6
+// ------------------------------------------------------------------ bins 6-9
+namespace cg = cooperative_groups;
+
+template <int CL>
+struct Log2Of {
+    static constexpr int v = CL <= 1 ? 0 : 1 + Log2Of<CL / 2>::v;
+};
+template <>
+struct Log2Of<1> {
+    static constexpr int v = 0;
+};
+
+template <int CL, typename WT, typename GT, typename VT>
+__global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int32_t *verts,
+                                                       int nverts, int log2cap, int slot)
+{
+    constexpr int BLOCK = 1024;
+    constexpr int LOG2CL = Log2Of<CL>::v;
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int cap = 1 << log2cap;
+    VT *vals = (VT *)smem;
+    int *keys = (int *)(vals + cap);
+    int *list = keys + cap;
+    __shared__ int s_cnt;
+    __shared__ GT p_g;
+    __shared__ int32_t p_c;
+    __shared__ i64 p_e, p_l, p_m;
+    for (int s = threadIdx.x; s < cap; s += BLOCK) {
+        keys[s] = -1;
+        vals[s] = 0;
+    }
+    if (threadIdx.x == 0) s_cnt = 0;
+    cluster.sync();
+    const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
+    const int64_t stride = (int64_t)CL * BLOCK;
+    u64 internal = 0, moved = 0, cand = 0;
+    for (int v = cid; v < nverts; v += ncl) {
+        const int32_t i = verts[v];
+        const int64_t rb = A.rp[i], re = A.rp[i + 1];
+        i64 loop = 0;
+        for (int64_t k0 = rb + (int64_t)rank * BLOCK + threadIdx.x; k0 < re;
+             k0 += (int64_t)kUnroll * stride) {
+            int32_t j[kUnroll];
+            i64 x[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const int64_t k = k0 + (int64_t)u * stride;
+                j[u] = -1;
+                x[u] = 0;
+                if (k < re) {
+                    j[u] = A.col[k];
+                    x[u] = (i64)A.w[k];
+                }
+            }
+            int32_t c[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (j[u] == i) {
+                    loop += x[u];
+                } else if (c[u] >= 0) {
+                    cluster_insert<VT>(cluster, keys, vals, list, &s_cnt, LOG2CL, log2cap, c[u],
+                                       (VT)x[u], A.err);
+                }
+            }
+        }
+        cluster.sync();  // every insert of this row has landed
+        const int32_t a = A.C[i];
+        const i64 dl = A.delta[i];
+        const int m = s_cnt;
+        GT gbest = gain_min<GT>();
+        int32_t best = INT_MAX;
+        i64 e_a = 0;
+        for (int p = threadIdx.x; p < m; p += BLOCK) {
+            const int s = list[p];
+            const int32_t cc = keys[s];
+            const i64 e = (i64)vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+            consider<GT>(cc, e, a, dl, A.tw, A.deg, gbest, best, e_a);
+        }
+        block_argmax(gbest, best, e_a, loop);
+        if (threadIdx.x == 0) {
+            p_g = gbest;
+            p_c = best;
+            p_e = e_a;
+            p_l = loop;
+            p_m = m;
+            s_cnt = 0;
+        }
+        cluster.sync();  // partial results of every CTA published
+        if (rank == 0 && threadIdx.x == 0) {
+            GT g = p_g;
+            int32_t c = p_c;
+            i64 ea = p_e, lp = p_l, mm = p_m;
+            for (int r = 1; r < CL; r++) {
+                const GT g2 = *cluster.map_shared_rank(&p_g, r);
+                const int32_t c2 = *cluster.map_shared_rank(&p_c, r);
+                if (better(g2, c2, g, c)) {
+                    g = g2;
+                    c = c2;
+                }
+                ea += *cluster.map_shared_rank(&p_e, r);
+                lp += *cluster.map_shared_rank(&p_l, r);
+                mm += *cluster.map_shared_rank(&p_m, r);
+            }
+            const int32_t target = choose_target<GT>(a, c, g, ea, dl, A.tw, A.deg, A.size);
+            A.Cnext[i] = target;
+            moved += target != a;
+            internal += (u64)(ea + lp);
+            cand += (u64)mm;
+        }
+        cluster.sync();  // partials read before the next row overwrites them
+    }
+    block_flush_stats(A.st, slot, internal, moved, cand, 0);
+}
+
+// ------------------------------------------------------------------ bin 10
 constexpr int kHugeBlock = 512;
 
 struct BigArgs {
@@ -477,7 +602,7 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
         if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
     }
-    block_flush_stats(A.st, 6, internal, moved, cand, 0);
+    block_flush_stats(A.st, kChunkedBin, internal, moved, cand, 0);
 }
 
 // ------------------------------------------------------------------ launch
@@ -486,6 +611,52 @@ template <typename VT>
 inline size_t table_bytes(int log2cap)
 {
     return ((size_t)1 << log2cap) * (sizeof(VT) + 8);
+}
+
+template <typename K>
+static int launch_cta_kernel(K kernel, int block, size_t smem, int nrows, cudaStream_t s,
+                             const LaunchCfg &lc, const char *name)
+{
+    set_dyn_smem(kernel, smem, name);
+    const int per_sm_smem = (int)((227 * 1024) / (smem + 1024));
+    const int per_sm_thr = 2048 / block;
+    int per_sm = per_sm_smem < per_sm_thr ? per_sm_smem : per_sm_thr;
+    if (per_sm < 1) per_sm = 1;
+    const int maxg = lc.num_sms * per_sm;
+    return nrows < maxg ? nrows : maxg;
+}
+
+// Launch a cluster kernel with CL CTAs per cluster over nrows rows.  Returns 0 if no
+// cluster of that size can be resident (then the caller reports an error).
+template <int CL, typename K, typename... Args>
+static int launch_cluster_kernel(K kernel, size_t smem, int nrows, cudaStream_t s,
+                                 const char *name, Args... args)
+{
+    set_dyn_smem(kernel, smem, name);
+    if (CL > 8) cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(CL, 1, 1);
+    int maxc = 0;
+    if (cudaOccupancyMaxActiveClusters(&maxc, kernel, &cfg) != cudaSuccess || maxc < 1) {
+        cudaGetLastError();
+        if (!launch_site()) launch_site() = name;
+        return 0;
+    }
+    const int nclusters = nrows < maxc ? nrows : maxc;
+    cfg.gridDim = dim3((unsigned)(nclusters * CL), 1, 1);
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+    note_launch(name);
+    return 1;
 }
 
 template <typename WT, typename GT, typename VT>
@@ -497,76 +668,121 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
                    tw, st.Cnext, stats, err};
     const bool timed = tm && tm->on;
     int launched = 0;
-    auto mark = [&](int e) {
-        if (timed) cudaEventRecord(tm->ev[e], s);
-    };
-    mark(0);
-    if (g.n > 0) {
-        k_move_small<WT, GT><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-            A, (int)b.upper[0]);
-        note_launch("k_move_small");
-        launched++;
-    }
-    mark(1);
-    mark(2);
-    if (b.nlist[1] > 0) {
-        k_move_group<8, 6, WT, GT, VT><<<grid_for(b.nlist[1], kBlock / 8, lc.max_blocks), kBlock,
-                                         0, s>>>(A, b.list[1], b.nlist[1], 1);
-        note_launch("k_move_group<8>");
-        launched++;
-    }
-    mark(3);
-    mark(4);
-    if (b.nlist[2] > 0) {
-        k_move_group<32, 8, WT, GT, VT><<<grid_for(b.nlist[2], kBlock / 32, lc.max_blocks),
-                                          kBlock, 0, s>>>(A, b.list[2], b.nlist[2], 2);
-        note_launch("k_move_group<32>");
-        launched++;
-    }
-    mark(5);
-    for (int cb = 0; cb < kCtaBins; cb++) {
-        const int bin = 3 + cb;
-        mark(2 * bin);
-        if (b.nlist[bin] > 0) {
+    for (int bin = 0; bin < kNumBins; bin++) {
+        if (timed) cudaEventRecord(tm->ev[2 * bin], s);
+        const BinSpec sp = kBinSpec[bin];
+        const int nr = b.nlist[bin];
+        const int32_t *rows = b.rows(bin);
+        if (sp.kind == BIN_THREAD) {
+            if (g.n > 0) {  // dense over every vertex: also sums deg_c^2 over all labels
+                k_move_small<WT, GT><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+                    A, (int)b.upper[0]);
+                note_launch("k_move_small");
+                launched++;
+            }
+        } else if (nr > 0 && sp.kind == BIN_GROUP8) {
+            k_move_group<8, 6, WT, GT, VT><<<grid_for(nr, kBlock / 8, lc.max_blocks), kBlock, 0,
+                                             s>>>(A, rows, nr, bin);
+            note_launch("k_move_group<8>");
+            launched++;
+        } else if (nr > 0 && sp.kind == BIN_WARP) {
+            k_move_group<32, 8, WT, GT, VT><<<grid_for(nr, kBlock / 32, lc.max_blocks), kBlock,
+                                              0, s>>>(A, rows, nr, bin);
+            note_launch("k_move_group<32>");
+            launched++;
+        } else if (nr > 0 && sp.kind == BIN_CTA) {
             const int l2 = cta_log2cap(b, bin);
             const size_t smem = table_bytes<VT>(l2);
-            const int per_sm = (int)((227 * 1024) / (smem + 1024));
-            const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
-            const int grid = b.nlist[bin] < maxg ? b.nlist[bin] : maxg;
-            if (kCtaBlock[cb] == 128) {
-                set_dyn_smem(k_move_cta<128, WT, GT, VT>, smem, "k_move_cta<128>");
-                k_move_cta<128, WT, GT, VT><<<grid, 128, smem, s>>>(A, b.list[bin], b.nlist[bin],
-                                                                    l2, bin);
-            } else if (kCtaBlock[cb] == 256) {
-                set_dyn_smem(k_move_cta<256, WT, GT, VT>, smem, "k_move_cta<256>");
-                k_move_cta<256, WT, GT, VT><<<grid, 256, smem, s>>>(A, b.list[bin], b.nlist[bin],
-                                                                    l2, bin);
+            if (sp.block == 128) {
+                const int grid = launch_cta_kernel(k_move_cta<128, WT, GT, VT>, 128, smem, nr, s,
+                                                   lc, "k_move_cta<128>");
+                k_move_cta<128, WT, GT, VT><<<grid, 128, smem, s>>>(A, rows, nr, l2, bin);
+            } else if (sp.block == 256) {
+                const int grid = launch_cta_kernel(k_move_cta<256, WT, GT, VT>, 256, smem, nr, s,
+                                                   lc, "k_move_cta<256>");
+                k_move_cta<256, WT, GT, VT><<<grid, 256, smem, s>>>(A, rows, nr, l2, bin);
             } else {
-                set_dyn_smem(k_move_cta<1024, WT, GT, VT>, smem, "k_move_cta<1024>");
-                k_move_cta<1024, WT, GT, VT><<<grid, 1024, smem, s>>>(A, b.list[bin],
-                                                                      b.nlist[bin], l2, bin);
+                const int grid = launch_cta_kernel(k_move_cta<1024, WT, GT, VT>, 1024, smem, nr,
+                                                   s, lc, "k_move_cta<1024>");
+                k_move_cta<1024, WT, GT, VT><<<grid, 1024, smem, s>>>(A, rows, nr, l2, bin);
             }
             note_launch("k_move_cta");
             launched++;
+        } else if (nr > 0 && sp.kind == BIN_CLUSTER) {
+            const int l2 = cta_log2cap(b, bin);
+            const size_t smem = table_bytes<VT>(l2);
+            switch (sp.cluster) {
+            case 2:
+                launched += launch_cluster_kernel<2>(k_move_cluster<2, WT, GT, VT>, smem, nr, s,
+                                                     "k_move_cluster<2>", A, rows, nr, l2, bin);
+                break;
+            case 4:
+                launched += launch_cluster_kernel<4>(k_move_cluster<4, WT, GT, VT>, smem, nr, s,
+                                                     "k_move_cluster<4>", A, rows, nr, l2, bin);
+                break;
+            case 8:
+                launched += launch_cluster_kernel<8>(k_move_cluster<8, WT, GT, VT>, smem, nr, s,
+                                                     "k_move_cluster<8>", A, rows, nr, l2, bin);
+                break;
+            default:
+                launched += launch_cluster_kernel<16>(k_move_cluster<16, WT, GT, VT>, smem, nr, s,
+                                                      "k_move_cluster<16>", A, rows, nr, l2, bin);
+                break;
+            }
+        } else if (sp.kind == BIN_CHUNKED && b.nchunks > 0) {
+            BigArgs B{rows,    b.chunk_b, b.chunk_first, b.nch,   b.goff,  b.glog2, b.gcnt,
+                      b.gdone, b.gloop,   b.gkeys,       b.gvals, b.glist, b.chunk, b.nchunks};
+            const int l2 = 31 - __builtin_clz(2 * b.chunk);
+            const size_t smem = table_bytes<VT>(l2);
+            const int grid = launch_cta_kernel(k_move_huge<WT, GT, VT>, kHugeBlock, smem,
+                                               b.nchunks, s, lc, "k_move_huge");
+            k_move_huge<WT, GT, VT><<<grid, kHugeBlock, smem, s>>>(A, B);
+            note_launch("k_move_huge");
+            launched++;
         }
-        mark(2 * bin + 1);
+        if (timed) cudaEventRecord(tm->ev[2 * bin + 1], s);
     }
-    mark(12);
-    if (b.nchunks > 0) {
-        BigArgs B{b.list[6], b.chunk_b, b.chunk_first, b.nch,   b.goff,  b.glog2, b.gcnt,
-                  b.gdone,   b.gloop,   b.gkeys,       b.gvals, b.glist, b.chunk, b.nchunks};
-        const int l2 = 31 - __builtin_clz(2 * b.chunk);
-        const size_t smem = table_bytes<VT>(l2);
-        set_dyn_smem(k_move_huge<WT, GT, VT>, smem, "k_move_huge");
-        const int per_sm = (int)((227 * 1024) / (smem + 1024));
-        const int maxg = lc.num_sms * (per_sm > 0 ? per_sm : 1);
-        const int grid = b.nchunks < maxg ? b.nchunks : maxg;
-        k_move_huge<WT, GT, VT><<<grid, kHugeBlock, smem, s>>>(A, B);
-        note_launch("k_move_huge");
-        launched++;
-    }
-    mark(13);
     return launched;
+}
+
+template <int CL>
+static bool cluster_fits(size_t smem)
+{
+    auto kernel = k_move_cluster<CL, int32_t, i64, unsigned int>;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (CL > 8) cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CL, 1, 1);
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int maxc = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&maxc, kernel, &cfg);
+    cudaGetLastError();
+    return e == cudaSuccess && maxc >= 1;
+}
+
+void probe_cluster_support(size_t smem, bool ok[4])
+{
+    ok[0] = cluster_fits<2>(smem);
+    ok[1] = cluster_fits<4>(smem);
+    ok[2] = cluster_fits<8>(smem);
+    ok[3] = cluster_fits<16>(smem);
+}
+
+size_t shared_table_bytes(int log2cap, bool narrow)
+{
+    return narrow ? table_bytes<unsigned int>(log2cap) : table_bytes<u64>(log2cap);
 }
 
 int launch_sweep(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, bool wide,

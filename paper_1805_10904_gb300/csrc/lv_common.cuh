@@ -204,11 +204,11 @@ __device__ __forceinline__ int tbl_key(const int *keys, unsigned h)
 }
 
 template <bool GLOBAL, typename VT>
-__device__ __forceinline__ void tbl_insert(int *keys, VT *vals, int *list, int *cnt, int log2cap,
-                                           int key, VT val, unsigned *err)
+__device__ __forceinline__ void tbl_insert_at(int *keys, VT *vals, int *list, int *cnt,
+                                              int log2cap, unsigned h, int key, VT val,
+                                              unsigned *err)
 {
     const unsigned mask = (1u << log2cap) - 1u;
-    unsigned h = hash_slot(key, log2cap);
 #pragma unroll 1
     for (unsigned probe = 0; probe <= mask; probe++) {
         const int k = tbl_key<GLOBAL>(keys, h);
@@ -230,6 +230,60 @@ __device__ __forceinline__ void tbl_insert(int *keys, VT *vals, int *list, int *
             }
         }
         h = (h + 1) & mask;
+    }
+    atomicOr(err, ERRF_HASH_FULL);
+}
+
+template <bool GLOBAL, typename VT>
+__device__ __forceinline__ void tbl_insert(int *keys, VT *vals, int *list, int *cnt, int log2cap,
+                                           int key, VT val, unsigned *err)
+{
+    tbl_insert_at<GLOBAL, VT>(keys, vals, list, cnt, log2cap, hash_slot(key, log2cap), key, val,
+                              err);
+}
+
+// Table spread over the CTAs of a thread-block cluster: one linear-probing table of
+// 2^(log2cl + log2cap) slots whose segment r lives in the shared memory of CTA r (virtual
+// slot v -> CTA v >> log2cap, local slot v & (cap - 1)).  The key's hash picks the first
+// virtual slot, so keys spread over the CTAs, and probing crosses into the next CTA's
+// segment instead of overflowing.  `keys`, `vals`, `list`, `cnt` are this CTA's own
+// arrays; each segment's list records the local slots claimed in it.
+template <typename VT, typename Cluster>
+__device__ __forceinline__ void cluster_insert(Cluster &cluster, int *keys, VT *vals, int *list,
+                                               int *cnt, int log2cl, int log2cap, int key,
+                                               VT val, unsigned *err)
+{
+    const unsigned total_mask = (1u << (log2cl + log2cap)) - 1u;
+    const unsigned local_mask = (1u << log2cap) - 1u;
+    unsigned v = ((unsigned)key * 2654435761u) >> (32 - (log2cl + log2cap));
+    unsigned owner = v >> log2cap;
+    int *rk = cluster.map_shared_rank(keys, owner);
+#pragma unroll 1
+    for (unsigned probe = 0; probe <= total_mask; probe++) {
+        const unsigned h = v & local_mask;
+        const int k = ((volatile const int *)rk)[h];
+        if (k == key) {
+            atomicAdd(cluster.map_shared_rank(vals, owner) + h, val);
+            return;
+        }
+        if (k == -1) {
+            const int old = atomicCAS(rk + h, -1, key);
+            if (old == -1) {
+                const int p = atomicAdd(cluster.map_shared_rank(cnt, owner), 1);
+                cluster.map_shared_rank(list, owner)[p] = (int)h;
+                atomicAdd(cluster.map_shared_rank(vals, owner) + h, val);
+                return;
+            }
+            if (old == key) {
+                atomicAdd(cluster.map_shared_rank(vals, owner) + h, val);
+                return;
+            }
+        }
+        v = (v + 1) & total_mask;
+        if ((v & local_mask) == 0) {
+            owner = v >> log2cap;
+            rk = cluster.map_shared_rank(keys, owner);
+        }
     }
     atomicOr(err, ERRF_HASH_FULL);
 }

@@ -31,26 +31,42 @@ struct PhaseState {
     i64 *delta = nullptr;      // weighted degree of each vertex
 };
 
-// Degree bins of one phase.  Bin b holds the vertices (or communities) whose entry count
-// d satisfies upper[b-1] < d <= upper[b]; the last bin holds the rest.
-//   0: one thread per vertex (dense kernel, no list)   3..5: one CTA per row, shared table
-//   1: 8-lane groups, 64-slot tables                   6:    CTA chunks, global table
-//   2: one warp, 256-slot tables
-constexpr int kNumBins = 7;
-constexpr int kCtaBins = 3;                       // bins 3, 4, 5
-constexpr int kCtaBlock[kCtaBins] = {128, 256, 1024};
+// Degree bins of one phase.  Bin b holds the rows (vertices, or communities when coarsening)
+// whose entry count d satisfies upper[b-1] < d <= upper[b]; the last bin holds the rest.
+enum BinKind { BIN_THREAD, BIN_GROUP8, BIN_WARP, BIN_CTA, BIN_CLUSTER, BIN_CHUNKED };
+struct BinSpec {
+    BinKind kind;
+    int block;    // threads per CTA
+    int cluster;  // CTAs per thread-block cluster (distributed shared-memory table)
+};
+constexpr int kNumBins = 11;
+constexpr BinSpec kBinSpec[kNumBins] = {
+    {BIN_THREAD, 256, 1},    // 0: one thread per row, registers
+    {BIN_GROUP8, 256, 1},    // 1: 8 lanes per row, 64-slot shared table
+    {BIN_WARP, 256, 1},      // 2: one warp per row, 256-slot shared table
+    {BIN_CTA, 128, 1},       // 3-5: one CTA per row, shared table of >= 4/3 d slots
+    {BIN_CTA, 256, 1},
+    {BIN_CTA, 1024, 1},
+    {BIN_CLUSTER, 1024, 2},  // 6-9: a cluster per row, table spread over the cluster's
+    {BIN_CLUSTER, 1024, 4},  //      distributed shared memory (bin-5 table per CTA)
+    {BIN_CLUSTER, 1024, 8},
+    {BIN_CLUSTER, 1024, 16},
+    {BIN_CHUNKED, 512, 1},   // 10: CTA chunks merged in a global-memory table
+};
+constexpr int kChunkedBin = kNumBins - 1;
 
 struct Bins {
-    int64_t upper[kNumBins - 1] = {8, 32, 128, 512, 2048, 12288};
-    int chunk = 4096;   // entries per CTA chunk of a bin-6 row
-    int32_t *list[kNumBins] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    int nlist[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
-    int64_t entries[kNumBins] = {0, 0, 0, 0, 0, 0, 0};
-    int32_t *counts = nullptr;  // device: [0..7] list sizes, then 8 int64 entry totals
-    // bin-6 rows, split in chunks
+    int64_t upper[kNumBins - 1] = {8, 32, 128, 512, 2048, 12288, 24576, 49152, 98304, 196608};
+    int chunk = 4096;               // entries per CTA chunk of a chunked row
+    int32_t *list = nullptr;        // rows of bins 1.., grouped by bin
+    int64_t off[kNumBins + 1] = {}; // bin b's rows are list[off[b] .. off[b+1])
+    int nlist[kNumBins] = {};
+    int64_t entries[kNumBins] = {};
+    int32_t *counts = nullptr;      // device: [0..15] list sizes / cursors, then int64 entries
+    // chunked rows
     int32_t *nch = nullptr;          // chunks per row
     int32_t *chunk_first = nullptr;  // exclusive scan of nch (nb + 1)
-    int32_t *chunk_b = nullptr;      // bin-6 list index of every chunk
+    int32_t *chunk_b = nullptr;      // chunked-list index of every chunk
     int nchunks = 0;
     // global hash tables of multi-chunk rows
     int64_t *gcap = nullptr;   // slots (0 for single-chunk rows)
@@ -63,12 +79,15 @@ struct Bins {
     void *gvals = nullptr;     // u32 or u64 per slot
     int32_t *glist = nullptr;
     int64_t gslots = 0;
+    const int32_t *rows(int b) const { return list + off[b]; }
 };
 
-// log2 of the shared table of CTA bin b (3..5): at least 4/3 of the bin's upper bound, so
+// log2 of the shared table of CTA bins (3..5): at least 4/3 of the bin's upper bound, so
 // the load factor stays <= 0.75 and there are always more slots than distinct keys.
+// Cluster bins use the bin-5 table in each of their CTAs.
 inline int cta_log2cap(const Bins &b, int bin)
 {
+    if (bin > 5) bin = 5;
     const int64_t need = b.upper[bin] + b.upper[bin] / 3;
     int l = 5;
     while (((int64_t)1 << l) < need) l++;
@@ -78,7 +97,14 @@ inline int cta_log2cap(const Bins &b, int bin)
 struct LaunchCfg {
     int num_sms = 152;
     int max_blocks = 152 * 8;  // persistent grid cap for grid-stride kernels
+    bool cluster_ok[4] = {false, false, false, false};  // clusters of 2, 4, 8, 16 resident
 };
+
+// Which cluster sizes (2, 4, 8, 16 CTAs of 1024 threads with `smem` bytes of dynamic shared
+// memory each) can be resident on the current device.
+void probe_cluster_support(size_t smem, bool ok[4]);
+// Bytes of a CTA's shared table of 2^log2cap slots with 32-bit (narrow) or 64-bit sums.
+size_t shared_table_bytes(int log2cap, bool narrow);
 
 // ---- k_level.cu
 int launch_validate_rowptr(const int64_t *rp, int64_t n, unsigned *err, cudaStream_t s,
@@ -90,7 +116,10 @@ int launch_check_symmetry(const DevGraph &g, unsigned *err, cudaStream_t s, cons
 int launch_init_state(int64_t n, const PhaseState &st, cudaStream_t s, const LaunchCfg &lc);
 int launch_vertex_following(const DevGraph &g, const PhaseState &st, cudaStream_t s,
                             const LaunchCfg &lc);
-int launch_bin(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc);
+// Two passes: count rows and entries per bin (then the host reads counts and sets off[]),
+// fill the list grouped by bin.
+int launch_bin_count(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc);
+int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc);
 int launch_big_prep(const DevGraph &g, Bins &b, int64_t *scratch64, int32_t *scratch32,
                     cudaStream_t s, const LaunchCfg &lc);
 int launch_big_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc);
@@ -123,17 +152,19 @@ struct CoarsenBufs {
     int32_t *ccnt = nullptr;      // k (distinct neighbours of each community)
     int32_t *tmp_col = nullptr;   // nnz
     u64 *tmp_w = nullptr;         // nnz
-    int32_t *clist = nullptr;     // community lists of bins 2..6 (5 regions of k entries)
-    int32_t *counts = nullptr;    // device int32[8]: list sizes of bins 2..6
+    int32_t *counts = nullptr;    // device counters of the community bins
     int64_t *scratch64 = nullptr;
     int32_t *scratch32 = nullptr;
 };
-// Stage 1: community sizes, next-level delta, member lists, flattened offsets, bins
-// (communities binned by entry count with the thresholds of `bins`, bins 2..6 used).
+// Stage 1: community sizes, next-level delta, member lists, flattened offsets, and the
+// count pass of the community bins (by entries; rows of bins 0..2 all go to bin 2).
 int launch_coarsen_stage1(const DevGraph &g, const PhaseState &st, const int32_t *new_id,
-                          int64_t k, i64 *delta_next, CoarsenBufs &cb, const Bins &bins,
+                          int64_t k, i64 *delta_next, CoarsenBufs &cb, Bins &bins,
                           cudaStream_t s, const LaunchCfg &lc);
-// Chunk counts and global-table sizes of the bin-6 communities (bins.list[6]).
+// Fill pass of the community bins (after the host set bins.off from the counts).
+int launch_coarsen_binfill(int64_t k, CoarsenBufs &cb, Bins &bins, cudaStream_t s,
+                           const LaunchCfg &lc);
+// Chunk counts and global-table sizes of the communities of the chunked bin.
 int launch_coarsen_bigprep(int64_t k, CoarsenBufs &cb, Bins &bins, cudaStream_t s,
                            const LaunchCfg &lc);
 // Stage 2 (after the host read the bin counts): aggregate every community's entries.

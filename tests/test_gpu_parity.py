@@ -69,6 +69,8 @@ BIN_CONFIGS = [
     {"wide_sums": True, "bins": (2, 4, 8, 16, 32, 64), "chunk_entries": 64},
     {"force_int128": True, "wide_sums": True, "bins": (0, 0, 0, 0, 0, 0), "chunk_entries": 32},
     {"bins": (8, 32, 128, 512, 2048, 12288), "chunk_entries": 128},
+    {"bins": (0, 0, 0, 0, 0, 2)},                                # clusters of 2..16 CTAs
+    {"bins": (1, 2, 3, 4, 5, 6), "wide_sums": True, "force_int128": True, "chunk_entries": 64},
 ]
 
 
@@ -92,7 +94,8 @@ def test_planted_partition_4096(torch, lv, cfg):
 
 
 @pytest.mark.parametrize("scale,cfg", [(10, 0), (12, 0), (13, 1), (14, 2), (12, 4), (15, 0),
-                                       (14, 3), (13, 5), (12, 6), (15, 7), (16, 0)])
+                                       (14, 3), (13, 5), (12, 6), (15, 7), (16, 0), (13, 8),
+                                       (14, 9), (17, 0)])
 def test_rmat_medium(torch, lv, scale, cfg):
     """R-MAT graphs (a=.57, b=c=.19): hubs spanning many chunks, isolated vertices,
     several tiles of every scan and a ragged tail."""
