@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(1024) k_coarsen_cluster(CoarsenArgs<WT> A, con
         cluster.sync();  // every insert has landed
         if (threadIdx.x == 0) {
             int off = 0, tot = 0;
+#pragma unroll 1
             for (int r = 0; r < CL; r++) {
                 const int c = *cluster.map_shared_rank(&s_cnt, r);
                 if (r < (int)rank) off += c;

@@ -429,6 +429,7 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
             GT g = p_g;
             int32_t c = p_c;
             i64 ea = p_e, lp = p_l, mm = p_m;
+#pragma unroll 1
             for (int r = 1; r < CL; r++) {
                 const GT g2 = *cluster.map_shared_rank(&p_g, r);
                 const int32_t c2 = *cluster.map_shared_rank(&p_c, r);
