@@ -116,7 +116,7 @@ struct Scalars {
     LevelCtl ctl;
     int32_t bin_counts[40];
     int32_t ccounts[16];
-    u64 cand_total[kNumBins + 1];
+    u64 cand_total[16];
     int32_t tail[8];
 };
 
@@ -508,7 +508,7 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         CK(cudaMemcpyAsync(&d_sc->ctl, &h->pinned->ctl, sizeof(LevelCtl), cudaMemcpyHostToDevice,
                            s));
         CK(cudaMemsetAsync(&d_sc->st, 0, sizeof(SweepStats), s));
-        CK(cudaMemsetAsync(&d_sc->cand_total[0], 0, sizeof(u64) * (kNumBins + 1), s));
+        CK(cudaMemsetAsync(&d_sc->cand_total[0], 0, sizeof(u64) * 16, s));
 
         // sweeps (Algorithm 1); one host read of the controller per sweep
         int sweeps = 0;

@@ -396,7 +396,7 @@ __global__ void k_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_q
         const i64 moved = (i64)st->moved;
         bool stop = false;
         int iters = 0;
-        for (int b = 0; b < 8; b++) cand_total[b] += st->cand[b];
+        for (int b = 0; b < 16; b++) cand_total[b] += st->cand[b];
         if (k == 1) {
             i128_to(qn, ctl->qn_init);
         } else {
@@ -438,7 +438,7 @@ __global__ void k_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_q
     st->sq_lo = 0;
     st->sq_hi = 0;
     st->moved = 0;
-    for (int b = 0; b < 8; b++) st->cand[b] = 0;
+    for (int b = 0; b < 16; b++) st->cand[b] = 0;
 }
 
 int launch_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_qn, u64 *cand_total,

@@ -35,8 +35,8 @@ struct SweepStats {
     u64 sq_lo;     // sum_c deg_c^2 as a 128-bit value
     u64 sq_hi;
     u64 moved;     // vertices whose proposed label differs from the current one
-    u64 cand[8];   // distinct neighbouring communities summed over the vertices of each
-                   // degree bin (index = bin)
+    u64 cand[16];  // distinct neighbouring communities summed over the vertices of each
+                   // degree bin (index = bin, fewer than 16 bins)
 };
 
 // Level controller state (one per phase), read and written by the decide kernel.

@@ -54,6 +54,7 @@ constexpr BinSpec kBinSpec[kNumBins] = {
     {BIN_CHUNKED, 512, 1},   // 10: CTA chunks merged in a global-memory table
 };
 constexpr int kChunkedBin = kNumBins - 1;
+static_assert(kNumBins <= 16, "per-bin counters of SweepStats hold 16 bins");
 
 struct Bins {
     int64_t upper[kNumBins - 1] = {8, 32, 128, 512, 2048, 12288, 24576, 49152, 98304, 196608};
