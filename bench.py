@@ -36,7 +36,8 @@ WORKLOAD = ("R-MAT scale 22 (4,194,304 vertices, edge factor 16, a=0.57 b=0.19 c
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129 * 1024 * 1024
 KERNEL_NAMES = ["k_move_small", "k_move_group<8>", "k_move_group<32>", "k_move_cta<128>",
-                "k_move_cta<256>", "k_move_cta<1024>", "k_move_huge"]
+                "k_move_cta<256>", "k_move_cta<1024>", "k_move_cluster<2>", "k_move_cluster<4>",
+                "k_move_cluster<8>", "k_move_cluster<16>", "k_move_huge"]
 
 
 def parse_args(argv=None):
@@ -297,6 +298,7 @@ def run_native(args):
     torch.cuda.synchronize(dev)
     step_ms, visits, launches = [], 0, 0
     dom = {"time_ms": 0.0, "bytes": 0, "launches": 0, "id": None}
+    bins_acc, coarsen_ms = {}, 0.0
     levels = None
     for _ in range(args.steps):
         flush.fill_(1)  # L2 flush between timed steps (untimed)
@@ -314,6 +316,11 @@ def run_native(args):
         dom["bytes"] += int(c[6])
         dom["launches"] += int(c[5])
         dom["id"] = int(c[7])
+        coarsen_ms += float(t[1])
+        for b, st in enumerate(res.bin_stats()):
+            agg = bins_acc.setdefault(b, {"time_ms": 0.0, "launches": 0, "alg_bytes": 0})
+            for key in agg:
+                agg[key] += st[key]
         if levels is None:
             levels = [(l.n, l.nnz, l.iters, l.ncomm, round(l.q, 6)) for l in res.levels()]
         res.close()
@@ -362,6 +369,13 @@ def run_native(args):
                    "levels": levels, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "L2 flushed between timed steps (258 MB write); CSR of 1 GB > L2"},
         "roofline": roofline, "cpu_baseline": cpu,
+        "kernels_ms_per_step": {
+            KERNEL_NAMES[b]: {"ms": round(a["time_ms"] / args.steps, 4),
+                              "launches": a["launches"] // args.steps,
+                              "GB/s": round(a["alg_bytes"] / (a["time_ms"] / 1000.0) / 1e9, 1)
+                              if a["time_ms"] > 0 else None}
+            for b, a in sorted(bins_acc.items()) if a["launches"]},
+        "coarsen_ms_per_step": round(coarsen_ms / args.steps, 4),
         "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,
     }

@@ -178,14 +178,25 @@ int louvain_result_trace(const louvain_result *r, int64_t *len, int32_t *level, 
  *               s_w = 4 for int32 weights and 8 for int64
  *   counters[3] distinct neighbour communities summed over vertices and sweeps
  *   counters[4] kernels launched by the run
- * times_ms[0] local-move kernels (device time), [1] coarsening, [2] everything else on
- * the device, [3] wall time of louvain_run; [4] the dominant local-move kernel alone,
+ * times_ms[0] local-move kernels (device time), [1] graph induction from its first to its
+ * last kernel, [2] reserved, [3] wall time of louvain_run; [4] the dominant local-move kernel alone,
  * [5] the thread-per-vertex kernel, [6] the lane-group kernels, [7] the CTA and chunk
  * kernels; counters[5] launches of the dominant kernel, counters[6] its algorithmic bytes,
  * counters[7] which degree bin it serves (0 thread, 1 8-lane, 2 warp, 3-5 CTA, 6 chunks).
  * Arrays of 8; unused slots are zero.  Device times are filled only when the config had
  * profile = 1. */
 int louvain_result_counters(const louvain_result *r, int64_t counters[8], double times_ms[8]);
+
+/* Number of degree bins of the local-move sweep (see louvain_config's bin thresholds). */
+int louvain_num_bins(void);
+
+/* Statistics of degree bin `bin` summed over every sweep of the run: device time of its
+ * kernel (profile = 1 only, else 0), kernel launches, algorithmic bytes (formula of
+ * louvain_result_counters), rows handled and stored entries of those rows.  Any out pointer
+ * may be NULL. */
+int louvain_result_bin_stats(const louvain_result *r, int bin, double *time_ms,
+                             int64_t *launches, int64_t *alg_bytes, int64_t *rows,
+                             int64_t *entries);
 
 /* Free a result and its host and device memory; NULL is ignored. */
 void louvain_result_free(louvain_result *r);

@@ -183,6 +183,11 @@ struct louvain_result {
     std::vector<TraceRec> trace;
     int64_t counters[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double times[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double bin_time[kNumBins] = {};
+    int64_t bin_launches[kNumBins] = {};
+    double bin_bytes[kNumBins] = {};
+    int64_t bin_rows[kNumBins] = {};
+    int64_t bin_entries[kNumBins] = {};
     louvain_free_fn ff = nullptr;
     void *ctx = nullptr;
 };
@@ -392,18 +397,26 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     double t_kernel[kNumBins] = {};
     int64_t launches_kernel[kNumBins] = {};
     double bytes_kernel[kNumBins] = {};
+    cudaEvent_t coarsen_ev[2] = {nullptr, nullptr};
+    double t_coarsen = 0.0;
     if (cfg.profile) {
         for (auto &e : tm.ev) CK(cudaEventCreate(&e));
+        CK(cudaEventCreate(&coarsen_ev[0]));
+        CK(cudaEventCreate(&coarsen_ev[1]));
         tm.on = true;
     }
     struct EvGuard {
         SweepTimers *t;
+        cudaEvent_t *ce;
         ~EvGuard()
         {
-            if (t->on)
+            if (t->on) {
                 for (auto &e : t->ev) cudaEventDestroy(e);
+                cudaEventDestroy(ce[0]);
+                cudaEventDestroy(ce[1]);
+            }
         }
-    } evg{&tm};
+    } evg{&tm, coarsen_ev};
 
     PhaseState st;
     st.C = C.p;
@@ -520,14 +533,14 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
             kernels += launch_apply(n, st, &d_sc->ctl, s, lc);
             sweeps++;
             sync_scalars();
-            if (tm.on) {
-                for (int b = 0; b < kNumBins; b++) {
+            for (int b = 0; b < kNumBins; b++) {
+                if (tm.on) {
                     float ms = 0.f;
                     CK(cudaEventElapsedTime(&ms, tm.ev[2 * b], tm.ev[2 * b + 1]));
                     t_kernel[b] += ms;
-                    launches_kernel[b] +=
-                        b == 0 ? 1 : (b == kChunkedBin ? bins.nchunks > 0 : bins.nlist[b] > 0);
                 }
+                launches_kernel[b] +=
+                    b == 0 ? 1 : (b == kChunkedBin ? bins.nchunks > 0 : bins.nlist[b] > 0);
             }
             if (h->pinned->ctl.done) break;
             if (sweeps > cfg.max_iters + 2)
@@ -561,6 +574,8 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
                              : (double)bins.nlist[b] * 36.0;
                 const double tot = kb * sweeps + 8.0 * (double)cand_level[b];
                 bytes_kernel[b] += tot;
+                res->bin_rows[b] += (int64_t)(b == 0 ? n : bins.nlist[b]) * sweeps;
+                res->bin_entries[b] += bins.entries[b] * sweeps;
                 alg_bytes += tot;
                 cand_all += cand_level[b];
             }
@@ -614,6 +629,7 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         cb.counts = &d_sc->ccounts[0];
         cb.scratch32 = scratch32.p;
         cb.scratch64 = scratch64.p;
+        if (tm.on) CK(cudaEventRecord(coarsen_ev[0], s));
         Bins cbins = proto;
         kernels += launch_coarsen_stage1(G, st, new_id.p, k, delta_next.p, cb, cbins, s, lc);
         sync_scalars();
@@ -635,6 +651,13 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         g_w_next.reset(&A, (size_t)nnz_next * wb_next);
         kernels += launch_coarsen_compact(k, cb, g_rp_next.p, g_col_next.p, g_w_next.p, wb_next,
                                           s, lc);
+        if (tm.on) {
+            CK(cudaEventRecord(coarsen_ev[1], s));
+            CK(cudaEventSynchronize(coarsen_ev[1]));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, coarsen_ev[0], coarsen_ev[1]));
+            t_coarsen += ms;
+        }
         g_rp.swap(g_rp_next);
         g_col.swap(g_col_next);
         g_w.swap(g_w_next);
@@ -673,6 +696,12 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         res->counters[5] = launches_kernel[dom];
         res->counters[6] = (int64_t)bytes_kernel[dom];
         res->counters[7] = dom;
+        res->times[1] = t_coarsen;
+    }
+    for (int b = 0; b < kNumBins; b++) {
+        res->bin_time[b] = t_kernel[b];
+        res->bin_launches[b] = launches_kernel[b];
+        res->bin_bytes[b] = bytes_kernel[b];
     }
     res->times[3] = now_ms() - wall0;
 }
@@ -943,6 +972,21 @@ int louvain_result_counters(const louvain_result *r, int64_t counters[8], double
         if (counters) counters[k] = r->counters[k];
         if (times_ms) times_ms[k] = r->times[k];
     }
+    return LOUVAIN_OK;
+}
+
+int louvain_num_bins(void) { return kNumBins; }
+
+int louvain_result_bin_stats(const louvain_result *r, int bin, double *time_ms,
+                             int64_t *launches, int64_t *alg_bytes, int64_t *rows,
+                             int64_t *entries)
+{
+    if (!r || bin < 0 || bin >= kNumBins) return LOUVAIN_ERR_INVALID_ARG;
+    if (time_ms) *time_ms = r->bin_time[bin];
+    if (launches) *launches = r->bin_launches[bin];
+    if (alg_bytes) *alg_bytes = (int64_t)r->bin_bytes[bin];
+    if (rows) *rows = r->bin_rows[bin];
+    if (entries) *entries = r->bin_entries[bin];
     return LOUVAIN_OK;
 }
 

@@ -100,6 +100,8 @@ def load():
     lib.louvain_result_level_info.argtypes = [P, ctypes.c_int, P, P, P, P, P]
     lib.louvain_result_trace.argtypes = [P, P, P, P, P, P]
     lib.louvain_result_counters.argtypes = [P, P, P]
+    lib.louvain_num_bins.restype = ctypes.c_int
+    lib.louvain_result_bin_stats.argtypes = [P, ctypes.c_int, P, P, P, P, P]
     lib.louvain_result_free.argtypes = [P]
     lib.louvain_result_free.restype = None
     _lib = lib
@@ -227,6 +229,18 @@ class Result:
                                            mv.ctypes.data, qn.ctypes.data)
         return [(int(lv[t]), int(it[t]), int(mv[t]), _i128(qn[2 * t], qn[2 * t + 1]))
                 for t in range(T)]
+
+    def bin_stats(self):
+        """Per degree bin: dict(time_ms, launches, alg_bytes, rows, entries) over all sweeps."""
+        out = []
+        for b in range(self._lib.louvain_num_bins()):
+            t = ctypes.c_double()
+            v = [ctypes.c_int64() for _ in range(4)]
+            self._lib.louvain_result_bin_stats(self._p, b, ctypes.addressof(t),
+                                               *[ctypes.addressof(x) for x in v])
+            out.append({"time_ms": t.value, "launches": v[0].value, "alg_bytes": v[1].value,
+                        "rows": v[2].value, "entries": v[3].value})
+        return out
 
     def counters(self):
         c = np.zeros(8, np.int64)
