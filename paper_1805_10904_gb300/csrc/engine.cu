@@ -347,7 +347,47 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     Cnext.reset(&A, n0);
     size.reset(&A, n0);
     new_id.reset(&A, (size_t)n0 + 1);
-    kernels += launch_row_sums(G, delta.p, &d_sc->tw, &d_sc->err, s, lc);
+    DBuf<int32_t> lists;  // rows of bins 1.., grouped by bin
+    lists.reset(&A, (size_t)n0);
+    // bin thresholds: every table must fit shared memory with the chosen sum width; the
+    // cluster bins hold rows up to CL times the bin-5 bound (CL CTAs, bin-5 table each);
+    // cluster sizes that cannot be resident are left empty.
+    auto make_proto = [&](bool narrow_sums) {
+        Bins pr;
+        const int32_t thr[6] = {cfg.bin_small, cfg.bin_mid1, cfg.bin_mid2,
+                                cfg.bin_cta1,  cfg.bin_cta2, cfg.bin_cta3};
+        for (int t = 0; t < 6; t++) pr.upper[t] = thr[t];
+        if (!narrow_sums && pr.upper[5] > 6144) {
+            pr.upper[5] = 6144;
+            for (int t = 4; t >= 0; t--)
+                if (pr.upper[t] > pr.upper[t + 1]) pr.upper[t] = pr.upper[t + 1];
+        }
+        for (int t = 0; t < 4; t++) {
+            const int64_t cl = (int64_t)kBinSpec[6 + t].cluster;
+            pr.upper[6 + t] = lc.cluster_ok[t] ? pr.upper[5] * cl : pr.upper[5 + t];
+        }
+        pr.chunk = cfg.chunk_entries;
+        return pr;
+    };
+    // degree bins of graph G: count, then fill the list grouped by bin
+    auto make_bins = [&](const DevGraph &gr, const Bins &pr) {
+        Bins bins = pr;
+        bins.list = lists.p;
+        bins.counts = &d_sc->bin_counts[0];
+        kernels += launch_bin_count(gr, bins, s, lc);
+        sync_scalars();
+        bins.off[0] = bins.off[1] = 0;
+        for (int b = 0; b < kNumBins; b++) {
+            bins.nlist[b] = h->pinned->bin_counts[b];
+            memcpy(&bins.entries[b], &h->pinned->bin_counts[16 + 2 * b], sizeof(int64_t));
+            if (b >= 1) bins.off[b + 1] = bins.off[b] + bins.nlist[b];
+        }
+        kernels += launch_bin_fill(gr, bins, s, lc);
+        return bins;
+    };
+    const Bins proto_narrow = make_proto(true);
+    Bins bins0 = make_bins(G, proto_narrow);
+    kernels += launch_row_sums(G, bins0, delta.p, &d_sc->tw, &d_sc->err, s, lc);
     if (cfg.checks >= 2) kernels += launch_check_symmetry(G, &d_sc->err, s, lc);
     sync_scalars();
     const u64 tw_u = h->pinned->tw;
@@ -359,8 +399,6 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
 
     // ---------------- per-run buffers sized by level 0 (Theorem 1: levels never grow)
     const int64_t scratch_n = scan_scratch_elems(n0 + 1) + 64;
-    DBuf<int32_t> lists;  // rows of bins 1.., grouped by bin
-    lists.reset(&A, (size_t)n0);
     DBuf<int32_t> b_nch, b_chunk_first, b_glog2, b_gcnt, b_gdone;
     DBuf<int64_t> b_gcap, b_goff;
     DBuf<u64> b_gloop;
@@ -425,23 +463,8 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     st.size = size.p;
     st.delta = delta.p;
 
-    // bin thresholds: every table must fit shared memory with the chosen sum width; the
-    // cluster bins hold rows up to CL times the bin-5 bound (CL CTAs, bin-5 table each);
-    // cluster sizes that cannot be resident are left empty.
-    Bins proto;
-    const int32_t thr[6] = {cfg.bin_small, cfg.bin_mid1, cfg.bin_mid2,
-                            cfg.bin_cta1,  cfg.bin_cta2, cfg.bin_cta3};
-    for (int t = 0; t < 6; t++) proto.upper[t] = thr[t];
-    if (!narrow && proto.upper[5] > 6144) {
-        proto.upper[5] = 6144;
-        for (int t = 4; t >= 0; t--)
-            if (proto.upper[t] > proto.upper[t + 1]) proto.upper[t] = proto.upper[t + 1];
-    }
-    for (int t = 0; t < 4; t++) {
-        const int64_t cl = (int64_t)kBinSpec[6 + t].cluster;
-        proto.upper[6 + t] = lc.cluster_ok[t] ? proto.upper[5] * cl : proto.upper[5 + t];
-    }
-    proto.chunk = cfg.chunk_entries;
+    Bins proto = make_proto(narrow);
+    const bool reuse_bins0 = narrow;  // level-0 bins were made with these thresholds
     proto.nch = b_nch.p;
     proto.chunk_first = b_chunk_first.p;
     proto.gcap = b_gcap.p;
@@ -495,19 +518,20 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         if (cfg.vertex_following && (level == 0 || cfg.vf_all_levels))
             kernels += launch_vertex_following(G, st, s, lc);
 
-        // degree bins: count, then fill the list grouped by bin
-        Bins bins = proto;
-        bins.list = lists.p;
-        bins.counts = &d_sc->bin_counts[0];
-        kernels += launch_bin_count(G, bins, s, lc);
-        sync_scalars();
-        bins.off[0] = bins.off[1] = 0;
-        for (int b = 0; b < kNumBins; b++) {
-            bins.nlist[b] = h->pinned->bin_counts[b];
-            memcpy(&bins.entries[b], &h->pinned->bin_counts[16 + 2 * b], sizeof(int64_t));
-            if (b >= 1) bins.off[b + 1] = bins.off[b] + bins.nlist[b];
+        // degree bins (level 0 reuses the bins made for the row sums)
+        Bins bins;
+        if (level == 0 && reuse_bins0) {
+            bins = proto;
+            bins.list = bins0.list;
+            bins.counts = bins0.counts;
+            for (int b = 0; b <= kNumBins; b++) bins.off[b] = bins0.off[b];
+            for (int b = 0; b < kNumBins; b++) {
+                bins.nlist[b] = bins0.nlist[b];
+                bins.entries[b] = bins0.entries[b];
+            }
+        } else {
+            bins = make_bins(G, proto);
         }
-        kernels += launch_bin_fill(G, bins, s, lc);
         prep_huge(bins, false, 0, nullptr);
 
         // phase controller
@@ -649,8 +673,8 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         const int wb_next = TW <= INT32_MAX ? 4 : 8;
         g_col_next.reset(&A, (size_t)nnz_next);
         g_w_next.reset(&A, (size_t)nnz_next * wb_next);
-        kernels += launch_coarsen_compact(k, cb, g_rp_next.p, g_col_next.p, g_w_next.p, wb_next,
-                                          s, lc);
+        kernels += launch_coarsen_compact(k, nnz_next, cb, g_rp_next.p, g_col_next.p,
+                                          g_w_next.p, wb_next, s, lc);
         if (tm.on) {
             CK(cudaEventRecord(coarsen_ev[1], s));
             CK(cudaEventSynchronize(coarsen_ev[1]));

@@ -362,7 +362,8 @@ struct CBigArgs {
 constexpr int kCHugeBlock = 512;
 
 // Communities with the most entries: CTA chunks of `chunk` flattened entries merged in a
-// global table; the last chunk to finish writes the community's row.
+// global table (a single-chunk community writes its row directly); k_coarsen_huge_extract
+// then writes the rows of multi-chunk communities, every chunk CTA taking a slice.
 template <typename WT, typename VT>
 __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A, CBigArgs B)
 {
@@ -373,7 +374,6 @@ __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A,
     int *keys = (int *)(vals + cap);
     int *list = keys + cap;
     __shared__ int s_cnt;
-    __shared__ int s_last;
     for (int s = threadIdx.x; s < cap; s += kCHugeBlock) {
         keys[s] = -1;
         vals[s] = 0;
@@ -421,29 +421,6 @@ __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A,
                 vals[s] = 0;
                 tbl_insert<true, VT>(gk, gv, gl, &B.gcnt[b], l2, key, v, A.err);
             }
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const int t = atomicAdd(&B.gdone[b], 1);
-                s_last = (t == nch - 1);
-            }
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-                const int gm = __ldcg(&B.gcnt[b]);
-                for (int r = threadIdx.x; r < gm; r += kCHugeBlock) {
-                    const int s = __ldcg(gl + r);
-                    A.tmp_col[tb + r] = __ldcg(gk + s);
-                    A.tmp_w[tb + r] = (u64)__ldcg(gv + s);
-                    gk[s] = -1;
-                    gv[s] = 0;
-                }
-                if (threadIdx.x == 0) {
-                    A.ccnt[a] = gm;
-                    B.gcnt[b] = 0;
-                    B.gdone[b] = 0;
-                }
-            }
         }
         __syncthreads();
         if (threadIdx.x == 0) s_cnt = 0;
@@ -451,8 +428,51 @@ __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A,
     }
 }
 
+// Rows of multi-chunk communities: chunk q of community b writes list positions
+// [q * chunk, (q + 1) * chunk) of its global table (the list order is the row order).
+template <typename VT>
+__global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge_extract(
+    CBigArgs B, const int32_t *moff, const int64_t *mpre, int32_t *ccnt, int32_t *tmp_col,
+    u64 *tmp_w)
+{
+    for (int c = blockIdx.x; c < B.nchunks; c += gridDim.x) {
+        const int b = B.chunk_b[c];
+        if (B.nch[b] == 1) continue;
+        const int32_t a = B.blist[b];
+        const int q = c - B.chunk_first[b];
+        const int64_t tb = mpre[moff[a]];
+        const int64_t off = B.goff[b];
+        const int gm = B.gcnt[b];
+        const int64_t pb = (int64_t)q * B.chunk;
+        const int64_t pe = min((int64_t)gm, pb + B.chunk);
+        for (int64_t p = pb + threadIdx.x; p < pe; p += kCHugeBlock) {
+            const int s = B.glist[off + p];
+            tmp_col[tb + p] = B.gkeys[off + s];
+            tmp_w[tb + p] = (u64)((const VT *)B.gvals)[off + s];
+        }
+        if (q == 0 && threadIdx.x == 0) ccnt[a] = gm;
+    }
+}
+
+// Compaction into the next CSR, balanced by output entries: each warp copies a slice of
+// kCompactSlice consecutive output entries; the community of an entry is found by a
+// binary search over the new row offsets and then advanced monotonically.
+constexpr int kCompactSlice = 1024;
+
+__device__ __forceinline__ int64_t row_of(const int64_t *rp, int64_t lo, int64_t hi, int64_t o)
+{
+    // largest a in [lo, hi) with rp[a] <= o
+    while (hi - lo > 1) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (rp[mid] <= o) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 template <typename WO>
-__global__ void __launch_bounds__(kBlock) k_coarsen_compact(int64_t k, const int32_t *moff,
+__global__ void __launch_bounds__(kBlock) k_coarsen_compact(int64_t k, int64_t nnz_next,
+                                                            const int32_t *moff,
                                                             const int64_t *mpre,
                                                             const int64_t *rp_next,
                                                             const int32_t *tmp_col,
@@ -462,13 +482,14 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_compact(int64_t k, const int
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t a = warp; a < k; a += nwarps) {
-        const int64_t src = mpre[moff[a]];
-        const int64_t dst = rp_next[a];
-        const int64_t m = rp_next[a + 1] - dst;
-        for (int64_t q = lane; q < m; q += 32) {
-            col_next[dst + q] = tmp_col[src + q];
-            w_next[dst + q] = (WO)tmp_w[src + q];
+    for (int64_t o0 = warp * kCompactSlice; o0 < nnz_next; o0 += nwarps * kCompactSlice) {
+        const int64_t o1 = min(nnz_next, o0 + kCompactSlice);
+        int64_t a = row_of(rp_next, 0, k, o0);
+        for (int64_t o = o0 + lane; o < o1; o += 32) {
+            if (rp_next[a + 1] <= o) a = row_of(rp_next, a + 1, k, o);
+            const int64_t src = mpre[moff[a]] + (o - rp_next[a]);
+            col_next[o] = tmp_col[src];
+            w_next[o] = (WO)tmp_w[src];
         }
     }
 }
@@ -635,7 +656,10 @@ static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *n
                                       "k_coarsen_huge");
             k_coarsen_huge<WT, VT><<<grid, kCHugeBlock, smem, s>>>(A, B);
             note_launch("k_coarsen_huge");
-            launched++;
+            k_coarsen_huge_extract<VT><<<grid, kCHugeBlock, 0, s>>>(B, cb.moff, cb.mpre, cb.ccnt,
+                                                                   cb.tmp_col, cb.tmp_w);
+            note_launch("k_coarsen_huge_extract");
+            launched += 2;
         }
     }
     return launched;
@@ -673,19 +697,21 @@ int launch_coarsen_rowptr(int64_t k, CoarsenBufs &cb, int64_t *rp_next, cudaStre
     return exclusive_scan<int64_t>(I32AsI64In{cb.ccnt}, k, rp_next, cb.scratch64, s);
 }
 
-int launch_coarsen_compact(int64_t k, const CoarsenBufs &cb, const int64_t *rp_next,
-                           int32_t *col_next, void *w_next, int wbytes_next, cudaStream_t s,
-                           const LaunchCfg &lc)
+int launch_coarsen_compact(int64_t k, int64_t nnz_next, const CoarsenBufs &cb,
+                           const int64_t *rp_next, int32_t *col_next, void *w_next,
+                           int wbytes_next, cudaStream_t s, const LaunchCfg &lc)
 {
-    if (k == 0) return 0;
-    const int grid = grid_for(k, kBlock / 32, lc.max_blocks);
+    if (k == 0 || nnz_next == 0) return 0;
+    const int grid = grid_for((nnz_next + kCompactSlice - 1) / kCompactSlice, kBlock / 32,
+                              lc.max_blocks);
     if (wbytes_next == 4)
-        k_coarsen_compact<int32_t><<<grid, kBlock, 0, s>>>(k, cb.moff, cb.mpre, rp_next,
-                                                           cb.tmp_col, cb.tmp_w, col_next,
-                                                           (int32_t *)w_next);
+        k_coarsen_compact<int32_t><<<grid, kBlock, 0, s>>>(k, nnz_next, cb.moff, cb.mpre,
+                                                           rp_next, cb.tmp_col, cb.tmp_w,
+                                                           col_next, (int32_t *)w_next);
     else
-        k_coarsen_compact<i64><<<grid, kBlock, 0, s>>>(k, cb.moff, cb.mpre, rp_next, cb.tmp_col,
-                                                       cb.tmp_w, col_next, (i64 *)w_next);
+        k_coarsen_compact<i64><<<grid, kBlock, 0, s>>>(k, nnz_next, cb.moff, cb.mpre, rp_next,
+                                                       cb.tmp_col, cb.tmp_w, col_next,
+                                                       (i64 *)w_next);
     return 1;
 }
 

@@ -49,50 +49,131 @@ int launch_fill_ones(int32_t *w, int64_t nnz, cudaStream_t s, const LaunchCfg &l
     return 1;
 }
 
-// delta_i = sum of row i's weights (loop once), 2W = sum delta; columns and weights
-// checked on the way.  One warp per row.
+// delta_i = sum of row i's weights (loop once), 2W = sum delta; columns and weights are
+// checked on the way.  Rows of bin 0 take one thread each (dense kernel), rows of bins 1-2
+// one warp each, longer rows one CTA each, so a hub row never serialises on one warp.
+__device__ __forceinline__ void check_entry(int32_t j, i64 x, int64_t n, unsigned &bad)
+{
+    if ((uint32_t)j >= (uint64_t)n) bad |= ERRF_INDEX;
+    if (x < 1) bad |= ERRF_WEIGHT;
+}
+
 template <typename WT>
-__global__ void __launch_bounds__(kBlock) k_row_sums(int64_t n, const int64_t *rp,
-                                                     const int32_t *col, const WT *w, i64 *delta,
-                                                     u64 *tw, unsigned *err)
+__global__ void __launch_bounds__(kBlock) k_row_sums_thread(int64_t n, const int64_t *rp,
+                                                            const int32_t *col, const WT *w,
+                                                            int64_t dmax, i64 *delta, u64 *tw,
+                                                            unsigned *err)
+{
+    unsigned bad = 0;
+    u64 tot = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = rp[i], e = rp[i + 1];
+        if (e - b > dmax) continue;
+        u64 sum = 0;
+        for (int64_t k = b; k < e; k++) {
+            const i64 x = (i64)w[k];
+            check_entry(col[k], x, n, bad);
+            sum += (u64)x;
+        }
+        delta[i] = (i64)sum;
+        tot += sum;
+    }
+    tot = sum_reduce(tot, 32);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(tw, tot);
+    if (bad) atomicOr(err, bad);
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(kBlock) k_row_sums_warp(int64_t n, const int64_t *rp,
+                                                          const int32_t *col, const WT *w,
+                                                          const int32_t *rows, int64_t nrows,
+                                                          i64 *delta, u64 *tw, unsigned *err)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned bad = 0;
     u64 tot = 0;
-    for (int64_t i = warp; i < n; i += nwarps) {
+    for (int64_t r = warp; r < nrows; r += nwarps) {
+        const int32_t i = rows[r];
         const int64_t b = rp[i], e = rp[i + 1];
-        u64 s = 0;
+        u64 sum = 0;
         for (int64_t k = b + lane; k < e; k += 32) {
-            const int32_t j = col[k];
             const i64 x = (i64)w[k];
-            if ((uint32_t)j >= (uint64_t)n) bad |= ERRF_INDEX;
-            if (x < 1) bad |= ERRF_WEIGHT;
-            s += (u64)x;
+            check_entry(col[k], x, n, bad);
+            sum += (u64)x;
         }
-        s = sum_reduce(s, 32);
+        sum = sum_reduce(sum, 32);
         if (lane == 0) {
-            delta[i] = (i64)s;
-            tot += s;
+            delta[i] = (i64)sum;
+            tot += sum;
         }
     }
     if (lane == 0 && tot) atomicAdd(tw, tot);
     if (bad) atomicOr(err, bad);
 }
 
-int launch_row_sums(const DevGraph &g, i64 *delta, u64 *tw, unsigned *err, cudaStream_t s,
-                    const LaunchCfg &lc)
+template <typename WT>
+__global__ void __launch_bounds__(kBlock) k_row_sums_cta(int64_t n, const int64_t *rp,
+                                                         const int32_t *col, const WT *w,
+                                                         const int32_t *rows, int64_t nrows,
+                                                         i64 *delta, u64 *tw, unsigned *err)
+{
+    __shared__ u64 s_part[kBlock / 32];
+    unsigned bad = 0;
+    for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int32_t i = rows[r];
+        const int64_t b = rp[i], e = rp[i + 1];
+        u64 sum = 0;
+        for (int64_t k = b + threadIdx.x; k < e; k += kBlock) {
+            const i64 x = (i64)w[k];
+            check_entry(col[k], x, n, bad);
+            sum += (u64)x;
+        }
+        sum = sum_reduce(sum, 32);
+        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            u64 t = 0;
+            for (int q = 0; q < kBlock / 32; q++) t += s_part[q];
+            delta[i] = (i64)t;
+            atomicAdd(tw, t);
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(err, bad);
+}
+
+template <typename WT>
+static int row_sums_impl(const DevGraph &g, const Bins &b, i64 *delta, u64 *tw, unsigned *err,
+                         cudaStream_t s, const LaunchCfg &lc)
+{
+    const WT *w = (const WT *)g.w;
+    int launched = 1;
+    k_row_sums_thread<WT><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        g.n, g.rp, g.col, w, b.upper[0], delta, tw, err);
+    const int64_t nwarp = b.off[3] - b.off[1];
+    if (nwarp > 0) {
+        k_row_sums_warp<WT><<<grid_for(nwarp, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(
+            g.n, g.rp, g.col, w, b.list + b.off[1], nwarp, delta, tw, err);
+        launched++;
+    }
+    const int64_t ncta = b.off[kNumBins] - b.off[3];
+    if (ncta > 0) {
+        k_row_sums_cta<WT><<<grid_for(ncta, 1, lc.max_blocks), kBlock, 0, s>>>(
+            g.n, g.rp, g.col, w, b.list + b.off[3], ncta, delta, tw, err);
+        launched++;
+    }
+    return launched;
+}
+
+int launch_row_sums(const DevGraph &g, const Bins &b, i64 *delta, u64 *tw, unsigned *err,
+                    cudaStream_t s, const LaunchCfg &lc)
 {
     if (g.n == 0) return 0;
-    const int grid = grid_for(g.n, kBlock / 32, lc.max_blocks);
-    if (g.wbytes == 4)
-        k_row_sums<int32_t><<<grid, kBlock, 0, s>>>(g.n, g.rp, g.col, (const int32_t *)g.w,
-                                                    delta, tw, err);
-    else
-        k_row_sums<i64><<<grid, kBlock, 0, s>>>(g.n, g.rp, g.col, (const i64 *)g.w, delta, tw,
-                                                err);
-    return 1;
+    if (g.wbytes == 4) return row_sums_impl<int32_t>(g, b, delta, tw, err, s, lc);
+    return row_sums_impl<i64>(g, b, delta, tw, err, s, lc);
 }
 
 // Full input checks: every row strictly increasing (sorted, no duplicate), and every

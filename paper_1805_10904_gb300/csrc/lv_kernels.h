@@ -111,8 +111,10 @@ size_t shared_table_bytes(int log2cap, bool narrow);
 int launch_validate_rowptr(const int64_t *rp, int64_t n, unsigned *err, cudaStream_t s,
                            const LaunchCfg &lc);
 int launch_fill_ones(int32_t *w, int64_t nnz, cudaStream_t s, const LaunchCfg &lc);
-int launch_row_sums(const DevGraph &g, i64 *delta, u64 *tw, unsigned *err, cudaStream_t s,
-                    const LaunchCfg &lc);
+// Weighted degrees and 2W with column / weight checks, one thread, warp or CTA per row
+// according to the row's degree bin (bins must have been filled for g).
+int launch_row_sums(const DevGraph &g, const Bins &b, i64 *delta, u64 *tw, unsigned *err,
+                    cudaStream_t s, const LaunchCfg &lc);
 int launch_check_symmetry(const DevGraph &g, unsigned *err, cudaStream_t s, const LaunchCfg &lc);
 int launch_init_state(int64_t n, const PhaseState &st, cudaStream_t s, const LaunchCfg &lc);
 int launch_vertex_following(const DevGraph &g, const PhaseState &st, cudaStream_t s,
@@ -174,8 +176,8 @@ int launch_coarsen_stage2(const DevGraph &g, const PhaseState &st, const int32_t
                           cudaStream_t s, const LaunchCfg &lc);
 // Stage 3 (after the host allocated the next graph): row offsets and compaction.
 int launch_coarsen_rowptr(int64_t k, CoarsenBufs &cb, int64_t *rp_next, cudaStream_t s);
-int launch_coarsen_compact(int64_t k, const CoarsenBufs &cb, const int64_t *rp_next,
-                           int32_t *col_next, void *w_next, int wbytes_next, cudaStream_t s,
-                           const LaunchCfg &lc);
+int launch_coarsen_compact(int64_t k, int64_t nnz_next, const CoarsenBufs &cb,
+                           const int64_t *rp_next, int32_t *col_next, void *w_next,
+                           int wbytes_next, cudaStream_t s, const LaunchCfg &lc);
 
 }  // namespace lv
