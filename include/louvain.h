@@ -201,6 +201,36 @@ int louvain_result_bin_stats(const louvain_result *r, int bin, double *time_ms,
 /* Free a result and its host and device memory; NULL is ignored. */
 void louvain_result_free(louvain_result *r);
 
+/* ---------------------------------------------------------------- without allocation */
+/* The paper has no counterpart to this entry point; it serves callers of this library
+ * that cannot allocate device memory while they run -- for example a service whose GPU
+ * memory is entirely reserved at start-up by another framework's allocator, or code that
+ * must not trigger the device-wide synchronisation that cudaMalloc and cudaFree imply.
+ *
+ * louvain_modularity_noalloc computes the exact modularity (Eq. 3) of a caller-given
+ * partition, like louvain_result_modularity reports it for the levels of a run, without
+ * allocating anything: its scratch (one degree per community plus a few accumulators) is a
+ * static device array of LOUVAIN_NOALLOC_MAX_VERTICES + 8 64-bit words (32 MiB + 64 bytes),
+ * reserved on every GPU that loads the library and held until the process exits.
+ *   n         vertices, 0 <= n <= LOUVAIN_NOALLOC_MAX_VERTICES, else LOUVAIN_ERR_TOO_LARGE
+ *             (checked before any device work)
+ *   row_ptr, col_idx, weights
+ *             device CSR as for louvain_run (weights NULL = all 1), on the current device
+ *   labels    device int32[n], community label of every vertex, each in [0, n)
+ *   stream    stream the work is ordered on; the call returns after it completes
+ *   qn, tw, q host outputs: Qn = (2W)^2 Q as int128 limbs {high, low}, 2W, and
+ *             Q = (double)Qn / (double)(2W)^2 (0 when 2W = 0); any may be NULL
+ * Errors: INVALID_ARG, TOO_LARGE, INDEX_RANGE (row offsets, a column or a label out of
+ * range), BAD_WEIGHT, CUDA.  The first call on each device looks up the array's device
+ * address with cudaGetSymbolAddress (the current device must be the one the graph lives
+ * on); make that first call before any stream capture.  Every call on a device uses the same
+ * array and clears the part it needs at its start, so calls whose GPU work overlaps (on
+ * different streams or from different host threads) race and give wrong results. */
+#define LOUVAIN_NOALLOC_MAX_VERTICES 4194304
+int louvain_modularity_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                               const int32_t *weights, const int32_t *labels, void *stream,
+                               int64_t qn[2], int64_t *tw, double *q);
+
 /* ---------------------------------------------------------------- version */
 /* ABI version of this header: 1. */
 int louvain_abi_version(void);

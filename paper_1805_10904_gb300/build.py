@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libgb300louvain.so")
-SOURCES = ["k_level.cu", "k_move.cu", "k_coarsen.cu", "engine.cu"]
+SOURCES = ["k_level.cu", "k_move.cu", "k_coarsen.cu", "engine.cu", "noalloc.cu"]
 HEADERS = ["lv_common.cuh", "lv_scan.cuh", "lv_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
