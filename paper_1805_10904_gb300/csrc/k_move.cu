@@ -257,7 +257,55 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
 }
 
 // ------------------------------------------------------------------ bins 3-5
+// Lanes of a warp holding the same community combine their weights before one insert
+// (32-bit sums only: the weights of one row add up to at most delta_i <= 2W < 2^32).
+// Every lane of the warp must call this; `ins(key, val)` performs the table insert.
+template <typename VT, typename Ins>
+__device__ __forceinline__ void warp_combined_insert(int32_t key, i64 x, Ins ins)
+{
+    const bool valid = key >= 0;
+    if (sizeof(VT) == 4) {
+        const unsigned act = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            const unsigned peers = __match_any_sync(act, key);
+            const unsigned tot = __reduce_add_sync(peers, (unsigned)x);
+            if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) ins(key, (VT)tot);
+        }
+    } else if (valid) {
+        ins(key, (VT)x);
+    }
+}
+
+// Loads of one chunk of a row: entries base + u * BLOCK, u < kUnroll, below re.
+template <int BLOCK, typename WT>
+__device__ __forceinline__ void load_chunk(const MoveArgs<WT> &A, int64_t base, int64_t re,
+                                           int32_t (&j)[kUnroll], i64 (&x)[kUnroll])
+{
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+        const int64_t k = base + (int64_t)u * BLOCK;
+        j[u] = -1;
+        x[u] = 0;
+        if (k < re) {
+            j[u] = A.col[k];
+            x[u] = (i64)A.w[k];
+        }
+    }
+}
+
+// Label gathers of a loaded chunk of row i: community of each non-loop entry, -1 otherwise.
+template <typename WT>
+__device__ __forceinline__ void gather_chunk(const MoveArgs<WT> &A, int32_t i,
+                                             const int32_t (&j)[kUnroll], int32_t (&c)[kUnroll])
+{
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+}
+
 // One CTA per row, table of 2^log2cap slots in dynamic shared memory (vals, keys, list).
+// Software pipeline over the CTA's rows: while row v finishes (barrier, candidate scan,
+// argmax), the next row's vertex id, entry range, first chunk of columns / weights and its
+// label gathers are already in flight, issued stage by stage so no load waits on another.
 template <int BLOCK, typename WT, typename GT, typename VT>
 __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_t *verts,
                                                     int nverts, int log2cap, int slot)
@@ -274,38 +322,62 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
     }
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
+    auto ins = [&](int32_t key, VT val) {
+        tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, val, A.err);
+    };
     u64 internal = 0, moved = 0, cand = 0;
-    for (int v = blockIdx.x; v < nverts; v += gridDim.x) {
-        const int32_t i = verts[v];
-        const int64_t rb = A.rp[i], re = A.rp[i + 1];
+    // prologue: the first row completely prefetched
+    int v = blockIdx.x;
+    int32_t nx_i = -1;
+    int64_t nx_rb = 0, nx_re = 0;
+    if (v < nverts) {
+        nx_i = verts[v];
+        nx_rb = A.rp[nx_i];
+        nx_re = A.rp[nx_i + 1];
+    }
+    int32_t nj[kUnroll], nc[kUnroll];
+    i64 nw[kUnroll];
+    load_chunk<BLOCK>(A, nx_rb + threadIdx.x, nx_re, nj, nw);
+    gather_chunk(A, nx_i, nj, nc);
+    for (; v < nverts; v += gridDim.x) {
+        const int32_t i = nx_i;
+        const int64_t rb = nx_rb, re = nx_re;
+        // stage 1: next row's vertex id; this row's own community and degree
+        const int vn = v + gridDim.x;
+        const int32_t i_next = vn < nverts ? verts[vn] : -1;
         const int32_t a = A.C[i];
         const i64 dl = A.delta[i];
+        // the prefetched first chunk, then the rest of the row
         i64 loop = 0;
-        for (int64_t k0 = rb + threadIdx.x; k0 < re; k0 += (int64_t)kUnroll * BLOCK) {
-            int32_t j[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            if (nj[u] == i) loop += nw[u];
+            warp_combined_insert<VT>(nc[u], nw[u], ins);
+        }
+        for (int64_t k0 = rb + threadIdx.x + (int64_t)kUnroll * BLOCK;
+             __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * BLOCK) {
+            int32_t j[kUnroll], c[kUnroll];
             i64 x[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
-                const int64_t k = k0 + (int64_t)u * BLOCK;
-                j[u] = -1;
-                x[u] = 0;
-                if (k < re) {
-                    j[u] = A.col[k];
-                    x[u] = (i64)A.w[k];
-                }
-            }
-            int32_t c[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+            load_chunk<BLOCK>(A, k0, re, j, x);
+            gather_chunk(A, i, j, c);
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) {
                 if (j[u] == i) loop += x[u];
-                else if (c[u] >= 0)
-                    tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, c[u], (VT)x[u], A.err);
+                warp_combined_insert<VT>(c[u], x[u], ins);
             }
         }
+        // stage 2: next row's entry range; this row's community degree and size
+        int64_t rb_next = 0, re_next = 0;
+        if (i_next >= 0) {
+            rb_next = A.rp[i_next];
+            re_next = A.rp[i_next + 1];
+        }
+        const i64 deg_a = A.deg[a];
+        const int32_t size_a = A.size[a];
         __syncthreads();
         const int m = s_cnt;
+        // stage 3: next row's first chunk of columns and weights
+        load_chunk<BLOCK>(A, rb_next + threadIdx.x, re_next, nj, nw);
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
         i64 e_a = 0;
@@ -317,15 +389,25 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
             vals[s] = 0;
             consider<GT>(cc, e, a, dl, A.tw, A.deg, gbest, best, e_a);
         }
+        // stage 4: next row's label gathers
+        gather_chunk(A, i_next, nj, nc);
         block_argmax(gbest, best, e_a, loop);
         if (threadIdx.x == 0) {
-            const int32_t target = choose_target<GT>(a, best, gbest, e_a, dl, A.tw, A.deg, A.size);
+            int32_t target = a;
+            if (best != INT_MAX) {
+                const GT gstay = (GT)A.tw * (GT)e_a - (GT)dl * (GT)(deg_a - dl);
+                if (gbest > gstay && !(size_a == 1 && best > a && A.size[best] == 1))
+                    target = best;
+            }
             A.Cnext[i] = target;
             moved += target != a;
             internal += (u64)(e_a + loop);
             cand += (u64)m;
             s_cnt = 0;
         }
+        nx_i = i_next;
+        nx_rb = rb_next;
+        nx_re = re_next;
         __syncthreads();
     }
     block_flush_stats(A.st, slot, internal, moved, cand, 0);
@@ -373,8 +455,12 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
         const int32_t i = verts[v];
         const int64_t rb = A.rp[i], re = A.rp[i + 1];
         i64 loop = 0;
-        for (int64_t k0 = rb + (int64_t)rank * BLOCK + threadIdx.x; k0 < re;
-             k0 += (int64_t)kUnroll * stride) {
+        auto cins = [&](int32_t key, VT val) {
+            cluster_insert<VT>(cluster, keys, vals, list, &s_cnt, LOG2CL, log2cap, key, val,
+                               A.err);
+        };
+        for (int64_t k0 = rb + (int64_t)rank * BLOCK + threadIdx.x;
+             __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * stride) {
             int32_t j[kUnroll];
             i64 x[kUnroll];
 #pragma unroll
@@ -392,12 +478,8 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
             for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) {
-                if (j[u] == i) {
-                    loop += x[u];
-                } else if (c[u] >= 0) {
-                    cluster_insert<VT>(cluster, keys, vals, list, &s_cnt, LOG2CL, log2cap, c[u],
-                                       (VT)x[u], A.err);
-                }
+                if (j[u] == i) loop += x[u];
+                warp_combined_insert<VT>(c[u], x[u], cins);
             }
         }
         cluster.sync();  // every insert of this row has landed
