@@ -257,23 +257,11 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
 }
 
 // ------------------------------------------------------------------ bins 3-5
-// Lanes of a warp holding the same community combine their weights before one insert
-// (32-bit sums only: the weights of one row add up to at most delta_i <= 2W < 2^32).
-// Every lane of the warp must call this; `ins(key, val)` performs the table insert.
+// Table insert of one chunk entry (key -1 = loop or absent entry: nothing to insert).
 template <typename VT, typename Ins>
-__device__ __forceinline__ void warp_combined_insert(int32_t key, i64 x, Ins ins)
+__device__ __forceinline__ void chunk_insert(int32_t key, i64 x, Ins ins)
 {
-    const bool valid = key >= 0;
-    if (sizeof(VT) == 4) {
-        const unsigned act = __ballot_sync(0xffffffffu, valid);
-        if (valid) {
-            const unsigned peers = __match_any_sync(act, key);
-            const unsigned tot = __reduce_add_sync(peers, (unsigned)x);
-            if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) ins(key, (VT)tot);
-        }
-    } else if (valid) {
-        ins(key, (VT)x);
-    }
+    if (key >= 0) ins(key, (VT)x);
 }
 
 // Loads of one chunk of a row: entries base + u * BLOCK, u < kUnroll, below re.
@@ -352,7 +340,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
 #pragma unroll
         for (int u = 0; u < kUnroll; u++) {
             if (nj[u] == i) loop += nw[u];
-            warp_combined_insert<VT>(nc[u], nw[u], ins);
+            chunk_insert<VT>(nc[u], nw[u], ins);
         }
         for (int64_t k0 = rb + threadIdx.x + (int64_t)kUnroll * BLOCK;
              __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * BLOCK) {
@@ -363,7 +351,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) {
                 if (j[u] == i) loop += x[u];
-                warp_combined_insert<VT>(c[u], x[u], ins);
+                chunk_insert<VT>(c[u], x[u], ins);
             }
         }
         // stage 2: next row's entry range; this row's community degree and size
@@ -479,7 +467,7 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) {
                 if (j[u] == i) loop += x[u];
-                warp_combined_insert<VT>(c[u], x[u], cins);
+                chunk_insert<VT>(c[u], x[u], cins);
             }
         }
         cluster.sync();  // every insert of this row has landed
