@@ -290,8 +290,9 @@ __device__ __forceinline__ void gather_chunk(const MoveArgs<WT> &A, int32_t i,
     for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
 }
 
-// One CTA per row, table of 2^log2cap slots in dynamic shared memory (vals, keys, list).
-// Software pipeline over the CTA's rows: while row v finishes (barrier, candidate scan,
+// One CTA per row, table of 2^log2cap slots in dynamic shared memory (vals, keys); the
+// finalize scans every slot (no claim list, so claiming a slot is a single CAS and no
+// shared counter serialises the inserts).  Software pipeline over the CTA's rows: while row v finishes (barrier, candidate scan,
 // argmax), the next row's vertex id, entry range, first chunk of columns / weights and its
 // label gathers are already in flight, issued stage by stage so no load waits on another.
 template <int BLOCK, typename WT, typename GT, typename VT>
@@ -302,16 +303,13 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
     const int cap = 1 << log2cap;
     VT *vals = (VT *)smem;
     int *keys = (int *)(vals + cap);
-    int *list = keys + cap;
-    __shared__ int s_cnt;
     for (int s = threadIdx.x; s < cap; s += BLOCK) {
         keys[s] = -1;
         vals[s] = 0;
     }
-    if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     auto ins = [&](int32_t key, VT val) {
-        tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, val, A.err);
+        tbl_insert_scan<VT>(keys, vals, log2cap, key, val, A.err);
     };
     u64 internal = 0, moved = 0, cand = 0;
     // prologue: the first row completely prefetched
@@ -363,18 +361,18 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
         const i64 deg_a = A.deg[a];
         const int32_t size_a = A.size[a];
         __syncthreads();
-        const int m = s_cnt;
         // stage 3: next row's first chunk of columns and weights
         load_chunk<BLOCK>(A, rb_next + threadIdx.x, re_next, nj, nw);
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
         i64 e_a = 0;
-        for (int p = threadIdx.x; p < m; p += BLOCK) {
-            const int s = list[p];
+        for (int s = threadIdx.x; s < cap; s += BLOCK) {
             const int32_t cc = keys[s];
+            if (cc < 0) continue;
             const i64 e = (i64)vals[s];
             keys[s] = -1;
             vals[s] = 0;
+            cand++;
             consider<GT>(cc, e, a, dl, A.tw, A.deg, gbest, best, e_a);
         }
         // stage 4: next row's label gathers
@@ -390,8 +388,6 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
             A.Cnext[i] = target;
             moved += target != a;
             internal += (u64)(e_a + loop);
-            cand += (u64)m;
-            s_cnt = 0;
         }
         nx_i = i_next;
         nx_rb = rb_next;
@@ -425,8 +421,6 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
     const int cap = 1 << log2cap;
     VT *vals = (VT *)smem;
     int *keys = (int *)(vals + cap);
-    int *list = keys + cap;
-    __shared__ int s_cnt;
     __shared__ GT p_g;
     __shared__ int32_t p_c;
     __shared__ i64 p_e, p_l, p_m;
@@ -434,7 +428,6 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
         keys[s] = -1;
         vals[s] = 0;
     }
-    if (threadIdx.x == 0) s_cnt = 0;
     cluster.sync();
     const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
     const int64_t stride = (int64_t)CL * BLOCK;
@@ -444,8 +437,7 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
         const int64_t rb = A.rp[i], re = A.rp[i + 1];
         i64 loop = 0;
         auto cins = [&](int32_t key, VT val) {
-            cluster_insert<VT>(cluster, keys, vals, list, &s_cnt, LOG2CL, log2cap, key, val,
-                               A.err);
+            cluster_insert<VT>(cluster, keys, vals, LOG2CL, log2cap, key, val, A.err);
         };
         for (int64_t k0 = rb + (int64_t)rank * BLOCK + threadIdx.x;
              __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * stride) {
@@ -473,26 +465,31 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
         cluster.sync();  // every insert of this row has landed
         const int32_t a = A.C[i];
         const i64 dl = A.delta[i];
-        const int m = s_cnt;
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
-        i64 e_a = 0;
-        for (int p = threadIdx.x; p < m; p += BLOCK) {
-            const int s = list[p];
+        i64 e_a = 0, mloc = 0;
+        for (int s = threadIdx.x; s < cap; s += BLOCK) {
             const int32_t cc = keys[s];
+            if (cc < 0) continue;
             const i64 e = (i64)vals[s];
             keys[s] = -1;
             vals[s] = 0;
+            mloc++;
             consider<GT>(cc, e, a, dl, A.tw, A.deg, gbest, best, e_a);
         }
+        mloc = sum_reduce(mloc, 32);  // per-warp count, folded into the CTA sum below
         block_argmax(gbest, best, e_a, loop);
+        __shared__ i64 s_mw[32];
+        if ((threadIdx.x & 31) == 0) s_mw[threadIdx.x >> 5] = mloc;
+        __syncthreads();
         if (threadIdx.x == 0) {
+            i64 m = 0;
+            for (int w = 0; w < BLOCK / 32; w++) m += s_mw[w];
             p_g = gbest;
             p_c = best;
             p_e = e_a;
             p_l = loop;
             p_m = m;
-            s_cnt = 0;
         }
         cluster.sync();  // partial results of every CTA published
         if (rank == 0 && threadIdx.x == 0) {
@@ -678,10 +675,11 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
 
 // ------------------------------------------------------------------ launch
 
+// shared table bytes: keys + values, plus a claim list when `with_list`
 template <typename VT>
-inline size_t table_bytes(int log2cap)
+inline size_t table_bytes(int log2cap, bool with_list = false)
 {
-    return ((size_t)1 << log2cap) * (sizeof(VT) + 8);
+    return ((size_t)1 << log2cap) * (sizeof(VT) + (with_list ? 8 : 4));
 }
 
 template <typename K>
@@ -804,7 +802,7 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
             BigArgs B{rows,    b.chunk_b, b.chunk_first, b.nch,   b.goff,  b.glog2, b.gcnt,
                       b.gdone, b.gloop,   b.gkeys,       b.gvals, b.glist, b.chunk, b.nchunks};
             const int l2 = 31 - __builtin_clz(2 * b.chunk);
-            const size_t smem = table_bytes<VT>(l2);
+            const size_t smem = table_bytes<VT>(l2, true);
             const int grid = launch_cta_kernel(k_move_huge<WT, GT, VT>, kHugeBlock, smem,
                                                b.nchunks, s, lc, "k_move_huge");
             k_move_huge<WT, GT, VT><<<grid, kHugeBlock, smem, s>>>(A, B);

@@ -242,6 +242,33 @@ __device__ __forceinline__ void tbl_insert(int *keys, VT *vals, int *list, int *
                               err);
 }
 
+// Insert-or-add without a claim list (the owner scans the whole table afterwards): one CAS
+// to claim a slot, no shared counter.
+template <typename VT>
+__device__ __forceinline__ void tbl_insert_scan(int *keys, VT *vals, int log2cap, int key, VT val,
+                                                unsigned *err)
+{
+    const unsigned mask = (1u << log2cap) - 1u;
+    unsigned h = hash_slot(key, log2cap);
+#pragma unroll 1
+    for (unsigned probe = 0; probe <= mask; probe++) {
+        const int k = ((volatile const int *)keys)[h];
+        if (k == key) {
+            atomicAdd(&vals[h], val);
+            return;
+        }
+        if (k == -1) {
+            const int old = atomicCAS(&keys[h], -1, key);
+            if (old == -1 || old == key) {
+                atomicAdd(&vals[h], val);
+                return;
+            }
+        }
+        h = (h + 1) & mask;
+    }
+    atomicOr(err, ERRF_HASH_FULL);
+}
+
 // Table spread over the CTAs of a thread-block cluster: one linear-probing table of
 // 2^(log2cl + log2cap) slots whose segment r lives in the shared memory of CTA r (virtual
 // slot v -> CTA v >> log2cap, local slot v & (cap - 1)).  The key's hash picks the first
@@ -249,9 +276,8 @@ __device__ __forceinline__ void tbl_insert(int *keys, VT *vals, int *list, int *
 // segment instead of overflowing.  `keys`, `vals`, `list`, `cnt` are this CTA's own
 // arrays; each segment's list records the local slots claimed in it.
 template <typename VT, typename Cluster>
-__device__ __forceinline__ void cluster_insert(Cluster &cluster, int *keys, VT *vals, int *list,
-                                               int *cnt, int log2cl, int log2cap, int key,
-                                               VT val, unsigned *err)
+__device__ __forceinline__ void cluster_insert(Cluster &cluster, int *keys, VT *vals, int log2cl,
+                                               int log2cap, int key, VT val, unsigned *err)
 {
     const unsigned total_mask = (1u << (log2cl + log2cap)) - 1u;
     const unsigned local_mask = (1u << log2cap) - 1u;
@@ -268,13 +294,7 @@ __device__ __forceinline__ void cluster_insert(Cluster &cluster, int *keys, VT *
         }
         if (k == -1) {
             const int old = atomicCAS(rk + h, -1, key);
-            if (old == -1) {
-                const int p = atomicAdd(cluster.map_shared_rank(cnt, owner), 1);
-                cluster.map_shared_rank(list, owner)[p] = (int)h;
-                atomicAdd(cluster.map_shared_rank(vals, owner) + h, val);
-                return;
-            }
-            if (old == key) {
+            if (old == -1 || old == key) {
                 atomicAdd(cluster.map_shared_rank(vals, owner) + h, val);
                 return;
             }
