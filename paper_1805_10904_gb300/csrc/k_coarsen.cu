@@ -218,7 +218,60 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
     }
 }
 
-// One CTA per community with a 2^log2cap-slot table in dynamic shared memory.
+// Exclusive prefix sum over the threads of a CTA of BLOCK threads; *total gets the sum.
+template <int BLOCK>
+__device__ __forceinline__ int cta_excl_scan(int v, int *total)
+{
+    __shared__ int s_w[32];
+    __shared__ int s_total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += u;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int x = lane < BLOCK / 32 ? s_w[lane] : 0;
+        int xi = x;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, xi, off);
+            if (lane >= off) xi += u;
+        }
+        if (lane < BLOCK / 32) s_w[lane] = xi - x;
+        if (lane == 31) s_total = xi;  // lanes >= BLOCK/32 add nothing
+    }
+    __syncthreads();
+    const int res = s_w[warp] + incl - v;
+    *total = s_total;
+    __syncthreads();
+    return res;
+}
+
+// Write the occupied slots of a table of `cap` slots to out[base + ...] in slot order of a
+// CTA-strided walk, clearing them; returns this CTA's count (valid in every thread).
+template <int BLOCK, typename VT>
+__device__ __forceinline__ int drain_table(int *keys, VT *vals, int cap, int32_t *out_col,
+                                           u64 *out_w, int64_t base, int rank_off)
+{
+    int mine = 0;
+    for (int s = threadIdx.x; s < cap; s += BLOCK) mine += keys[s] >= 0;
+    int total;
+    int off = cta_excl_scan<BLOCK>(mine, &total) + rank_off;
+    for (int s = threadIdx.x; s < cap; s += BLOCK) {
+        const int key = keys[s];
+        if (key < 0) continue;
+        out_col[base + off] = key;
+        out_w[base + off] = (u64)vals[s];
+        off++;
+        keys[s] = -1;
+        vals[s] = 0;
+    }
+    return total;
+}
+
+// One CTA per community with a 2^log2cap-slot table (keys, sums) in dynamic shared memory.
 template <int BLOCK, typename WT, typename VT>
 __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const int32_t *clist,
                                                        int ncl, int log2cap)
@@ -227,13 +280,10 @@ __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const 
     const int cap = 1 << log2cap;
     VT *vals = (VT *)smem;
     int *keys = (int *)(vals + cap);
-    int *list = keys + cap;
-    __shared__ int s_cnt;
     for (int s = threadIdx.x; s < cap; s += BLOCK) {
         keys[s] = -1;
         vals[s] = 0;
     }
-    if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     for (int v = blockIdx.x; v < ncl; v += gridDim.x) {
         const int32_t a = clist[v];
@@ -244,22 +294,11 @@ __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const 
             int32_t key;
             i64 wv;
             flat_entry(A, p, pe, t, key, wv);
-            tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, (VT)wv, A.err);
+            tbl_insert_scan<VT>(keys, vals, log2cap, key, (VT)wv, A.err);
         }
         __syncthreads();
-        const int m = s_cnt;
-        for (int q = threadIdx.x; q < m; q += BLOCK) {
-            const int s = list[q];
-            A.tmp_col[tb + q] = keys[s];
-            A.tmp_w[tb + q] = (u64)vals[s];
-            keys[s] = -1;
-            vals[s] = 0;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            A.ccnt[a] = m;
-            s_cnt = 0;
-        }
+        const int m = drain_table<BLOCK, VT>(keys, vals, cap, A.tmp_col, A.tmp_w, tb, 0);
+        if (threadIdx.x == 0) A.ccnt[a] = m;
         __syncthreads();
     }
 }
@@ -276,7 +315,8 @@ struct CLog2<1> {
 };
 
 // Large communities: one thread-block cluster per community, the table partitioned over
-// the cluster's distributed shared memory by key hash; each CTA writes its part of the row.
+// the cluster's distributed shared memory; each CTA writes the occupied slots of its segment
+// after the segments of lower ranks.
 template <int CL, typename WT, typename VT>
 __global__ void __launch_bounds__(1024) k_coarsen_cluster(CoarsenArgs<WT> A, const int32_t *clist,
                                                           int ncl, int log2cap)
@@ -289,14 +329,12 @@ __global__ void __launch_bounds__(1024) k_coarsen_cluster(CoarsenArgs<WT> A, con
     const int cap = 1 << log2cap;
     VT *vals = (VT *)smem;
     int *keys = (int *)(vals + cap);
-    int *list = keys + cap;
     __shared__ int s_cnt;
     __shared__ int s_off, s_tot;
     for (int s = threadIdx.x; s < cap; s += BLOCK) {
         keys[s] = -1;
         vals[s] = 0;
     }
-    if (threadIdx.x == 0) s_cnt = 0;
     cluster.sync();
     const int cid = blockIdx.x / CL, nclu = gridDim.x / CL;
     const int64_t stride = (int64_t)CL * BLOCK;
@@ -309,10 +347,15 @@ __global__ void __launch_bounds__(1024) k_coarsen_cluster(CoarsenArgs<WT> A, con
             int32_t key;
             i64 wv;
             flat_entry(A, p, pe, t, key, wv);
-            cluster_insert<VT>(cluster, keys, vals, list, &s_cnt, LOG2CL, log2cap, key, (VT)wv,
-                               A.err);
+            cluster_insert<VT>(cluster, keys, vals, LOG2CL, log2cap, key, (VT)wv, A.err);
         }
         cluster.sync();  // every insert has landed
+        int mine = 0;
+        for (int s = threadIdx.x; s < cap; s += BLOCK) mine += keys[s] >= 0;
+        int total;
+        cta_excl_scan<BLOCK>(mine, &total);
+        if (threadIdx.x == 0) s_cnt = total;
+        cluster.sync();  // every segment's count published
         if (threadIdx.x == 0) {
             int off = 0, tot = 0;
 #pragma unroll 1
@@ -324,22 +367,10 @@ __global__ void __launch_bounds__(1024) k_coarsen_cluster(CoarsenArgs<WT> A, con
             s_off = off;
             s_tot = tot;
         }
-        cluster.sync();  // every CTA has read every count
-        const int m = s_cnt;
-        const int off = s_off;
-        for (int q = threadIdx.x; q < m; q += BLOCK) {
-            const int s = list[q];
-            A.tmp_col[tb + off + q] = keys[s];
-            A.tmp_w[tb + off + q] = (u64)vals[s];
-            keys[s] = -1;
-            vals[s] = 0;
-        }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            if (rank == 0) A.ccnt[a] = s_tot;
-            s_cnt = 0;
-        }
-        cluster.sync();  // tables cleared before the next community's inserts
+        drain_table<BLOCK, VT>(keys, vals, cap, A.tmp_col, A.tmp_w, tb, s_off);
+        if (threadIdx.x == 0 && rank == 0) A.ccnt[a] = s_tot;
+        cluster.sync();  // counts read and tables cleared before the next community
     }
 }
 
@@ -542,10 +573,11 @@ int launch_coarsen_binfill(int64_t k, CoarsenBufs &cb, Bins &bins, cudaStream_t 
     return 1;
 }
 
+// shared table bytes: keys + values, plus a claim list when `with_list`
 template <typename VT>
-inline size_t ctable_bytes(int log2cap)
+inline size_t ctable_bytes(int log2cap, bool with_list = false)
 {
-    return ((size_t)1 << log2cap) * (sizeof(VT) + 8);
+    return ((size_t)1 << log2cap) * (sizeof(VT) + (with_list ? 8 : 4));
 }
 
 template <typename K>
@@ -651,7 +683,7 @@ static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *n
                        bins.glog2, bins.gcnt,    bins.gdone,       bins.gkeys, bins.gvals,
                        bins.glist, bins.chunk,   bins.nchunks};
             const int l2 = 31 - __builtin_clz(2 * bins.chunk);
-            const size_t smem = ctable_bytes<VT>(l2);
+            const size_t smem = ctable_bytes<VT>(l2, true);
             const int grid = cta_grid(k_coarsen_huge<WT, VT>, kCHugeBlock, smem, bins.nchunks, lc,
                                       "k_coarsen_huge");
             k_coarsen_huge<WT, VT><<<grid, kCHugeBlock, smem, s>>>(A, B);
