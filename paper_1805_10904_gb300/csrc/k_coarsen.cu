@@ -271,7 +271,7 @@ __device__ __forceinline__ int drain_table(int *keys, VT *vals, int cap, int32_t
     return total;
 }
 
-// One CTA per community with a 2^log2cap-slot table (keys, sums) in dynamic shared memory.
+// One CTA per community with a 2^log2cap-slot table in dynamic shared memory.
 template <int BLOCK, typename WT, typename VT>
 __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const int32_t *clist,
                                                        int ncl, int log2cap)
@@ -280,10 +280,13 @@ __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const 
     const int cap = 1 << log2cap;
     VT *vals = (VT *)smem;
     int *keys = (int *)(vals + cap);
+    int *list = keys + cap;
+    __shared__ int s_cnt;
     for (int s = threadIdx.x; s < cap; s += BLOCK) {
         keys[s] = -1;
         vals[s] = 0;
     }
+    if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     for (int v = blockIdx.x; v < ncl; v += gridDim.x) {
         const int32_t a = clist[v];
@@ -294,11 +297,22 @@ __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const 
             int32_t key;
             i64 wv;
             flat_entry(A, p, pe, t, key, wv);
-            tbl_insert_scan<VT>(keys, vals, log2cap, key, (VT)wv, A.err);
+            tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, (VT)wv, A.err);
         }
         __syncthreads();
-        const int m = drain_table<BLOCK, VT>(keys, vals, cap, A.tmp_col, A.tmp_w, tb, 0);
-        if (threadIdx.x == 0) A.ccnt[a] = m;
+        const int m = s_cnt;
+        for (int q = threadIdx.x; q < m; q += BLOCK) {
+            const int s = list[q];
+            A.tmp_col[tb + q] = keys[s];
+            A.tmp_w[tb + q] = (u64)vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            A.ccnt[a] = m;
+            s_cnt = 0;
+        }
         __syncthreads();
     }
 }
@@ -644,7 +658,7 @@ static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *n
             launched++;
         } else if (sp.kind == BIN_CTA) {
             const int l2 = cta_log2cap(bins, bin);
-            const size_t smem = ctable_bytes<VT>(l2);
+            const size_t smem = ctable_bytes<VT>(l2, true);
             if (sp.block == 128) {
                 const int grid = cta_grid(k_coarsen_cta<128, WT, VT>, 128, smem, nr, lc, "k_coarsen_cta");
                 k_coarsen_cta<128, WT, VT><<<grid, 128, smem, s>>>(A, rows, nr, l2);

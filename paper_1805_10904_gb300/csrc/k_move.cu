@@ -290,9 +290,8 @@ __device__ __forceinline__ void gather_chunk(const MoveArgs<WT> &A, int32_t i,
     for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
 }
 
-// One CTA per row, table of 2^log2cap slots in dynamic shared memory (vals, keys); the
-// finalize scans every slot (no claim list, so claiming a slot is a single CAS and no
-// shared counter serialises the inserts).  Software pipeline over the CTA's rows: while row v finishes (barrier, candidate scan,
+// One CTA per row, table of 2^log2cap slots in dynamic shared memory (vals, keys, list).
+// Software pipeline over the CTA's rows: while row v finishes (barrier, candidate scan,
 // argmax), the next row's vertex id, entry range, first chunk of columns / weights and its
 // label gathers are already in flight, issued stage by stage so no load waits on another.
 template <int BLOCK, typename WT, typename GT, typename VT>
@@ -303,13 +302,16 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
     const int cap = 1 << log2cap;
     VT *vals = (VT *)smem;
     int *keys = (int *)(vals + cap);
+    int *list = keys + cap;
+    __shared__ int s_cnt;
     for (int s = threadIdx.x; s < cap; s += BLOCK) {
         keys[s] = -1;
         vals[s] = 0;
     }
+    if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     auto ins = [&](int32_t key, VT val) {
-        tbl_insert_scan<VT>(keys, vals, log2cap, key, val, A.err);
+        tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, val, A.err);
     };
     u64 internal = 0, moved = 0, cand = 0;
     // prologue: the first row completely prefetched
@@ -361,18 +363,18 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
         const i64 deg_a = A.deg[a];
         const int32_t size_a = A.size[a];
         __syncthreads();
+        const int m = s_cnt;
         // stage 3: next row's first chunk of columns and weights
         load_chunk<BLOCK>(A, rb_next + threadIdx.x, re_next, nj, nw);
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
         i64 e_a = 0;
-        for (int s = threadIdx.x; s < cap; s += BLOCK) {
+        for (int p = threadIdx.x; p < m; p += BLOCK) {
+            const int s = list[p];
             const int32_t cc = keys[s];
-            if (cc < 0) continue;
             const i64 e = (i64)vals[s];
             keys[s] = -1;
             vals[s] = 0;
-            cand++;
             consider<GT>(cc, e, a, dl, A.tw, A.deg, gbest, best, e_a);
         }
         // stage 4: next row's label gathers
@@ -388,6 +390,8 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
             A.Cnext[i] = target;
             moved += target != a;
             internal += (u64)(e_a + loop);
+            cand += (u64)m;
+            s_cnt = 0;
         }
         nx_i = i_next;
         nx_rb = rb_next;
@@ -761,7 +765,7 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
             launched++;
         } else if (nr > 0 && sp.kind == BIN_CTA) {
             const int l2 = cta_log2cap(b, bin);
-            const size_t smem = table_bytes<VT>(l2);
+            const size_t smem = table_bytes<VT>(l2, true);
             if (sp.block == 128) {
                 const int grid = launch_cta_kernel(k_move_cta<128, WT, GT, VT>, 128, smem, nr, s,
                                                    lc, "k_move_cta<128>");
