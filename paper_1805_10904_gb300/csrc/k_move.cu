@@ -82,7 +82,8 @@ __device__ __forceinline__ void consider(int32_t c, i64 e, int32_t a, i64 dl, i6
     }
 }
 
-// CTA-wide argmax and sums; results valid in thread 0.  Ends with a barrier.
+// CTA-wide argmax and sums; results valid in thread 0.  Warp 0 combines the per-warp
+// partials with shuffles.  Ends with a barrier.
 template <typename GT>
 __device__ __forceinline__ void block_argmax(GT &g, int32_t &c, i64 &e_a, i64 &loop)
 {
@@ -100,15 +101,15 @@ __device__ __forceinline__ void block_argmax(GT &g, int32_t &c, i64 &e_a, i64 &l
         s_l[warp] = loop;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
-            if (better(s_g[w], s_c[w], g, c)) {
-                g = s_g[w];
-                c = s_c[w];
-            }
-            e_a += s_e[w];
-            loop += s_l[w];
-        }
+    if (warp == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        g = lane < nw ? s_g[lane] : gain_min<GT>();
+        c = lane < nw ? s_c[lane] : INT_MAX;
+        e_a = lane < nw ? s_e[lane] : 0;
+        loop = lane < nw ? s_l[lane] : 0;
+        argmax_reduce(g, c, 32);
+        e_a = sum_reduce(e_a, 32);
+        loop = sum_reduce(loop, 32);
     }
     __syncthreads();
 }
@@ -310,8 +311,19 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
     }
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    auto ins = [&](int32_t key, VT val) {
-        tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, val, A.err);
+    // one chunk: inserts, then the claimed slots appended to the list once per warp
+    auto insert_chunk = [&](const int32_t(&c)[kUnroll], const i64(&x)[kUnroll]) {
+        int slot[kUnroll];
+        bool cl[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            cl[u] = false;
+            slot[u] = 0;
+            if (c[u] >= 0)
+                cl[u] = tbl_insert_claim<VT>(keys, vals, log2cap, c[u], (VT)x[u], A.err, slot[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) warp_append(cl[u], slot[u], list, &s_cnt);
     };
     u64 internal = 0, moved = 0, cand = 0;
     // prologue: the first row completely prefetched
@@ -338,10 +350,9 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
         // the prefetched first chunk, then the rest of the row
         i64 loop = 0;
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
+        for (int u = 0; u < kUnroll; u++)
             if (nj[u] == i) loop += nw[u];
-            chunk_insert<VT>(nc[u], nw[u], ins);
-        }
+        insert_chunk(nc, nw);
         for (int64_t k0 = rb + threadIdx.x + (int64_t)kUnroll * BLOCK;
              __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * BLOCK) {
             int32_t j[kUnroll], c[kUnroll];
@@ -349,10 +360,9 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
             load_chunk<BLOCK>(A, k0, re, j, x);
             gather_chunk(A, i, j, c);
 #pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
+            for (int u = 0; u < kUnroll; u++)
                 if (j[u] == i) loop += x[u];
-                chunk_insert<VT>(c[u], x[u], ins);
-            }
+            insert_chunk(c, x);
         }
         // stage 2: next row's entry range; this row's community degree and size
         int64_t rb_next = 0, re_next = 0;
@@ -369,13 +379,37 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
         i64 e_a = 0;
-        for (int p = threadIdx.x; p < m; p += BLOCK) {
-            const int s = list[p];
-            const int32_t cc = keys[s];
-            const i64 e = (i64)vals[s];
-            keys[s] = -1;
-            vals[s] = 0;
-            consider<GT>(cc, e, a, dl, A.tw, A.deg, gbest, best, e_a);
+        for (int p0 = threadIdx.x; p0 < m; p0 += kUnroll * BLOCK) {
+            int32_t cc[kUnroll];
+            i64 e[kUnroll], dg[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const int p = p0 + u * BLOCK;
+                cc[u] = -1;
+                e[u] = 0;
+                if (p < m) {
+                    const int sl = list[p];
+                    cc[u] = keys[sl];
+                    e[u] = (i64)vals[sl];
+                    keys[sl] = -1;
+                    vals[sl] = 0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) dg[u] = (cc[u] >= 0 && cc[u] != a) ? A.deg[cc[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (cc[u] < 0) continue;
+                if (cc[u] == a) {
+                    e_a = e[u];
+                    continue;
+                }
+                const GT gc = (GT)A.tw * (GT)e[u] - (GT)dl * (GT)dg[u];
+                if (better(gc, cc[u], gbest, best)) {
+                    gbest = gc;
+                    best = cc[u];
+                }
+            }
         }
         // stage 4: next row's label gathers
         gather_chunk(A, i_next, nj, nc);

@@ -269,6 +269,49 @@ __device__ __forceinline__ void tbl_insert_scan(int *keys, VT *vals, int log2cap
     atomicOr(err, ERRF_HASH_FULL);
 }
 
+// Insert-or-add that reports a newly claimed slot instead of appending it to a list, so
+// the caller can append claims of a whole warp with one counter update.  Returns true
+// (and the slot) only for the call that claimed the slot.
+template <typename VT>
+__device__ __forceinline__ bool tbl_insert_claim(int *keys, VT *vals, int log2cap, int key, VT val,
+                                                 unsigned *err, int &slot)
+{
+    const unsigned mask = (1u << log2cap) - 1u;
+    unsigned h = hash_slot(key, log2cap);
+#pragma unroll 1
+    for (unsigned probe = 0; probe <= mask; probe++) {
+        const int k = ((volatile const int *)keys)[h];
+        if (k == key) {
+            atomicAdd(&vals[h], val);
+            return false;
+        }
+        if (k == -1) {
+            const int old = atomicCAS(&keys[h], -1, key);
+            if (old == -1 || old == key) {
+                atomicAdd(&vals[h], val);
+                slot = (int)h;
+                return old == -1;
+            }
+        }
+        h = (h + 1) & mask;
+    }
+    atomicOr(err, ERRF_HASH_FULL);
+    return false;
+}
+
+// Append the slots claimed by the lanes of a warp to `list` with one counter update
+// (every lane of the warp must call this).
+__device__ __forceinline__ void warp_append(bool claimed, int slot, int *list, int *cnt)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, claimed);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (claimed) list[base + __popc(m & ((1u << lane) - 1u))] = slot;
+}
+
 // Table spread over the CTAs of a thread-block cluster: one linear-probing table of
 // 2^(log2cl + log2cap) slots whose segment r lives in the shared memory of CTA r (virtual
 // slot v -> CTA v >> log2cap, local slot v & (cap - 1)).  The key's hash picks the first
