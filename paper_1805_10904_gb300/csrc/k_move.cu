@@ -311,19 +311,8 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
     }
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    // one chunk: inserts, then the claimed slots appended to the list once per warp
-    auto insert_chunk = [&](const int32_t(&c)[kUnroll], const i64(&x)[kUnroll]) {
-        int slot[kUnroll];
-        bool cl[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
-            cl[u] = false;
-            slot[u] = 0;
-            if (c[u] >= 0)
-                cl[u] = tbl_insert_claim<VT>(keys, vals, log2cap, c[u], (VT)x[u], A.err, slot[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; u++) warp_append(cl[u], slot[u], list, &s_cnt);
+    auto ins = [&](int32_t key, VT val) {
+        tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, val, A.err);
     };
     u64 internal = 0, moved = 0, cand = 0;
     // prologue: the first row completely prefetched
@@ -350,9 +339,10 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
         // the prefetched first chunk, then the rest of the row
         i64 loop = 0;
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++)
+        for (int u = 0; u < kUnroll; u++) {
             if (nj[u] == i) loop += nw[u];
-        insert_chunk(nc, nw);
+            chunk_insert<VT>(nc[u], nw[u], ins);
+        }
         for (int64_t k0 = rb + threadIdx.x + (int64_t)kUnroll * BLOCK;
              __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * BLOCK) {
             int32_t j[kUnroll], c[kUnroll];
@@ -360,9 +350,10 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
             load_chunk<BLOCK>(A, k0, re, j, x);
             gather_chunk(A, i, j, c);
 #pragma unroll
-            for (int u = 0; u < kUnroll; u++)
+            for (int u = 0; u < kUnroll; u++) {
                 if (j[u] == i) loop += x[u];
-            insert_chunk(c, x);
+                chunk_insert<VT>(c[u], x[u], ins);
+            }
         }
         // stage 2: next row's entry range; this row's community degree and size
         int64_t rb_next = 0, re_next = 0;
@@ -379,37 +370,13 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
         i64 e_a = 0;
-        for (int p0 = threadIdx.x; p0 < m; p0 += kUnroll * BLOCK) {
-            int32_t cc[kUnroll];
-            i64 e[kUnroll], dg[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
-                const int p = p0 + u * BLOCK;
-                cc[u] = -1;
-                e[u] = 0;
-                if (p < m) {
-                    const int sl = list[p];
-                    cc[u] = keys[sl];
-                    e[u] = (i64)vals[sl];
-                    keys[sl] = -1;
-                    vals[sl] = 0;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; u++) dg[u] = (cc[u] >= 0 && cc[u] != a) ? A.deg[cc[u]] : 0;
-#pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
-                if (cc[u] < 0) continue;
-                if (cc[u] == a) {
-                    e_a = e[u];
-                    continue;
-                }
-                const GT gc = (GT)A.tw * (GT)e[u] - (GT)dl * (GT)dg[u];
-                if (better(gc, cc[u], gbest, best)) {
-                    gbest = gc;
-                    best = cc[u];
-                }
-            }
+        for (int p = threadIdx.x; p < m; p += BLOCK) {
+            const int s = list[p];
+            const int32_t cc = keys[s];
+            const i64 e = (i64)vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+            consider<GT>(cc, e, a, dl, A.tw, A.deg, gbest, best, e_a);
         }
         // stage 4: next row's label gathers
         gather_chunk(A, i_next, nj, nc);
