@@ -50,6 +50,11 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-sweeps", type=int, default=2)
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer arm (profiling)")
+    p.add_argument("--batch-graphs", type=int, default=0,
+                   help="also time the mixed batch workload of this many graphs, batched vs "
+                        "one graph at a time (0: skip)")
+    p.add_argument("--batch-only", action="store_true",
+                   help="time only the batch workload (its own JSON line)")
     return p.parse_args(argv)
 
 
@@ -267,6 +272,79 @@ def run_e2e(args, g, lv, local, stream, world, dev):
             "d2h_bytes_per_step": d2h}
 
 
+BATCH_WORKLOAD = ("mixed batch: graph sizes log-uniform in [1K, 200K] vertices; even graphs "
+                  "planted partition (block size log-uniform 32-512, average degree 8-40, "
+                  "80% inside blocks), odd graphs Chung-Lu power law (exponent 2.1, average "
+                  "degree 10); int32 weights uniform in [1, 8]; seed 512; stacked "
+                  "block-diagonal CSR; full multi-level run per graph to threshold 1e-6")
+
+
+def run_batch_workload(args, lv, dev, stream, steps, warmup):
+    """Graphs/s of louvain_run_batch over the mixed workload against louvain_run on the
+    same graphs one at a time (inputs resident in HBM for both), and whether every
+    graph's result is identical in both forms."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    graphs = gg.batch_mix(args.batch_graphs, seed=512)
+    vptr, eptr, rp, col, w = lv.stack_graphs([(g.rp, g.col, g.w) for g in graphs])
+    d_rp, d_col, d_w = (torch.from_numpy(a).to(dev) for a in (rp, col, w))
+    singles = [tuple(torch.from_numpy(a).to(dev) for a in (g.rp, g.col, g.w)) for g in graphs]
+    h = lv.Louvain(dev.index, profile=False)
+
+    def batched():
+        return h.run_batch(vptr, d_rp, d_col, d_w, graph_eptr=eptr, stream=stream.cuda_stream)
+
+    def plain():
+        return [h.run(*t, stream=stream.cuda_stream) for t in singles]
+
+    def timed(fn):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        out = fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1), out
+
+    for _ in range(warmup):
+        for r in batched():
+            r.close()
+        for r in plain():
+            r.close()
+    t_b, t_p, kernels = [], [], 0
+    identical = True
+    for k in range(steps):
+        ms, rb = timed(batched)
+        t_b.append(ms)
+        kernels += int(rb[0].counters()[0][4]) if rb else 0
+        ms, rp_ = timed(plain)
+        t_p.append(ms)
+        if k == 0:  # compare every graph's levels, labels and trace in both forms
+            for a, b in zip(rb, rp_):
+                if a.num_levels != b.num_levels or a.trace() != b.trace():
+                    identical = False
+                    break
+                for l in range(a.num_levels):
+                    if a.level(l) != b.level(l) or not np.array_equal(a.labels(l), b.labels(l)):
+                        identical = False
+                        break
+        for r in rb + rp_:
+            r.close()
+    nb = sum(t_b) / len(t_b)
+    npl = sum(t_p) / len(t_p)
+    return {
+        "workload": BATCH_WORKLOAD, "graphs": len(graphs), "total_vertices": int(vptr[-1]),
+        "total_entries": int(eptr[-1]), "steps": steps,
+        "batched_ms_per_step": nb, "plain_ms_per_step": npl,
+        "graphs_per_s_batched": len(graphs) / (nb / 1000.0),
+        "graphs_per_s_plain": len(graphs) / (npl / 1000.0),
+        "speedup": npl / nb, "identical_to_plain": identical,
+        "gpu_launches_per_batched_step": kernels // max(1, steps),
+    }
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -277,6 +355,12 @@ def run_native(args):
     dist = dist_init(world, "nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.batch_only:
+        stream = torch.cuda.current_stream(dev)
+        b = run_batch_workload(args, lv, dev, stream, args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"batch": b}), flush=True)
+        return 0
     g = make_graph(args.scale)
     rp = torch.from_numpy(g.rp).to(dev)
     col = torch.from_numpy(g.col).to(dev)
@@ -333,6 +417,8 @@ def run_native(args):
 
     # end-to-end through the C ABI with pinned host buffers: H2D inside, labels D2H inside
     e2e = run_e2e(args, g, lv, local, stream, world, dev) if not args.no_e2e else None
+    batch = (run_batch_workload(args, lv, dev, stream, 2, 1) if args.batch_graphs > 0
+             else None)
 
     if rank != 0:
         if world > 1:
@@ -377,6 +463,7 @@ def run_native(args):
             for b, a in sorted(bins_acc.items()) if a["launches"]},
         "coarsen_ms_per_step": round(coarsen_ms / args.steps, 4),
         "e2e": e2e,
+        "batch": batch,
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

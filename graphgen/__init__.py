@@ -141,6 +141,44 @@ def chung_lu(n: int, gamma: float = 2.1, avg_deg: float = 10.0, wmin: int = 1, w
     return _take(h, f"chunglu{n}")
 
 
+def batch_mix_params(num_graphs: int, seed: int = 512, n_min: int = 1000,
+                     n_max: int = 200_000):
+    """Parameters of the mixed batch workload: graph k has a log-uniform size in
+    [n_min, n_max]; even k are planted partitions (block size log-uniform in [32, 512],
+    average degree uniform in [8, 40], 80% of it inside the block), odd k Chung-Lu
+    power-law graphs (exponent 2.1, average degree 10); weights uniform in [1, 8].
+    Every draw comes from the counter-based stream of graph_seed(seed, k)."""
+    out = []
+    for k in range(num_graphs):
+        gs = graph_seed(seed, k)
+        rng = np.random.Generator(np.random.PCG64(gs))
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        if k % 2 == 0:
+            b = int(round(np.exp(rng.uniform(np.log(32), np.log(512)))))
+            b = max(2, min(b, n))
+            d = float(rng.uniform(8.0, 40.0))
+            p_in = min(1.0, 0.8 * d / max(b - 1, 1))
+            p_out = 0.2 * d / max(n - b, 1)
+            out.append(("sbm", n, b, p_in, p_out, gs))
+        else:
+            out.append(("chung_lu", n, 2.1, 10.0, gs))
+    return out
+
+
+def batch_mix_graph(params) -> Graph:
+    if params[0] == "sbm":
+        _, n, b, p_in, p_out, gs = params
+        return sbm(n, b, p_in, p_out, 1, 8, gs)
+    _, n, gamma, avg, gs = params
+    return chung_lu(n, gamma, avg, 1, 8, gs)
+
+
+def batch_mix(num_graphs: int, seed: int = 512, n_min: int = 1000,
+              n_max: int = 200_000):
+    """The graphs of batch_mix_params (see there)."""
+    return [batch_mix_graph(p) for p in batch_mix_params(num_graphs, seed, n_min, n_max)]
+
+
 def from_pairs(n: int, pairs: Iterable[Tuple[int, int]], wmin: int = 1, wmax: int = 1,
                seed: int = 0) -> Graph:
     p = np.asarray(list(pairs), dtype=np.int32).reshape(-1, 2)

@@ -128,6 +128,36 @@ const char *louvain_last_error(const louvain_handle *h);
 int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                 const int32_t *weights, int ptr_kind, void *stream, louvain_result **out);
 
+/* ---------------------------------------------------------------- batch of graphs */
+/* Largest number of graphs in one louvain_run_batch call. */
+#define LOUVAIN_MAX_BATCH_GRAPHS 1048576
+
+/* Run louvain_run on each of num_graphs independent graphs in one pass over the device:
+ * every phase step (degree bins, sweeps, controller, renumbering, coarsening) is launched
+ * once for all graphs that still have a phase at that level, and each graph's controller
+ * (Algorithm 1 stopping rule) and outer test (Algorithm 2) run independently, so graph g's
+ * result is identical -- labels, Qn, iterations, trace -- to louvain_run on graph g alone.
+ * The method itself is defined for one graph; batching is this library's addition.
+ *   graph_vptr  HOST int64[num_graphs + 1]: graph g owns vertices [graph_vptr[g],
+ *               graph_vptr[g+1]) of the stacked CSR; graph_vptr[0] = 0, non-decreasing
+ *               (empty graphs allowed), n = graph_vptr[num_graphs] <= 2^31 - 1
+ *   graph_eptr  HOST int64[num_graphs + 1] or NULL: if given, must equal
+ *               row_ptr[graph_vptr[g]] for every g (checked)
+ *   row_ptr, col_idx, weights, ptr_kind, stream: one CSR over all n vertices exactly as in
+ *               louvain_run (block-diagonal: column ids are global and must lie in the
+ *               row's own graph range, else INDEX_RANGE)
+ *   out         array of num_graphs result pointers; out[g] gets graph g's result, its
+ *               labels numbered for graph g's own vertices 0..n_g-1.  Each result is
+ *               freed with louvain_result_free (in any order).  Per-graph counters: [0]
+ *               edge visits of that graph; the other counters and times describe the
+ *               whole batch.
+ * Device memory: as louvain_run for the stacked graph, plus (max_iters + 1) * num_graphs
+ * * 24 bytes of trace and O(num_graphs) controller state.  Errors as louvain_run, plus
+ * TOO_LARGE for num_graphs > LOUVAIN_MAX_BATCH_GRAPHS.  On error no result is returned. */
+int louvain_run_batch(louvain_handle *h, int32_t num_graphs, const int64_t *graph_vptr,
+                      const int64_t *graph_eptr, const int64_t *row_ptr, const int32_t *col_idx,
+                      const int32_t *weights, int ptr_kind, void *stream, louvain_result **out);
+
 /* ---------------------------------------------------------------- results */
 /* Number of recorded levels (0 when nothing merged, e.g. no edges). */
 int louvain_result_num_levels(const louvain_result *r);

@@ -7,10 +7,10 @@ All of it runs in the CUDA library built from ``csrc/`` (C ABI in
 ``include/louvain.h``); this package is its Python binding.
 """
 from .louvain import (Config, Level, Louvain, LouvainError, Result, load, LIB_PATH,
-                      PTR_DEVICE, PTR_HOST)
+                      PTR_DEVICE, PTR_HOST, stack_graphs)
 
 __all__ = ["Config", "Level", "Louvain", "LouvainError", "Result", "load", "LIB_PATH",
-           "PTR_DEVICE", "PTR_HOST", "build"]
+           "PTR_DEVICE", "PTR_HOST", "build", "stack_graphs"]
 
 
 def build(force: bool = False) -> str:

@@ -10,6 +10,7 @@
 // k_coarsen.cu.
 #include <chrono>
 #include <climits>
+#include <memory>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -110,7 +111,7 @@ struct DBuf {
 // Scalars shared by host and device during a run (one device block, one pinned mirror).
 struct Scalars {
     unsigned err;
-    int32_t pad0;
+    int32_t ndone;  // phase controllers that have stopped
     u64 tw;
     SweepStats st;
     LevelCtl ctl;
@@ -174,8 +175,26 @@ struct louvain_handle {
     Scalars *pinned = nullptr;
 };
 
+// Label arrays of a batch, shared by the results of its graphs; freed with the last one.
+struct LabelStore {
+    std::vector<int32_t *> arrays;
+    louvain_free_fn ff = nullptr;
+    void *ctx = nullptr;
+    int device = 0;
+    ~LabelStore()
+    {
+        cudaSetDevice(device);
+        for (int32_t *p : arrays) {
+            if (ff) ff(p, ctx, nullptr);
+            else cudaFreeAsync(p, nullptr);
+        }
+    }
+};
+
 struct louvain_result {
     int64_t n0 = 0;
+    int batch_index = -1;  // graph index in its batch, -1 for a plain run
+    std::shared_ptr<LabelStore> store;  // set for the results of a batch
     int64_t tw = 0;
     int device = 0;
     std::vector<LevelRec> levels;
@@ -266,16 +285,21 @@ struct Runner {
         return v;
     }
 
+    // One graph (gvptr null, NG = 1) or a batch of NG graphs stored as one CSR whose graph g
+    // owns vertices [gvptr[g], gvptr[g+1]); out holds one result per graph.
     void run(int64_t n0, const int64_t *rp, const int32_t *col, const int32_t *w, int kind,
-             louvain_result *res);
+             int NG, const int64_t *gvptr, const int64_t *geptr,
+             std::vector<louvain_result *> &out);
 };
 
 void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const int32_t *w_in,
-                 int kind, louvain_result *res)
+                 int kind, int NG, const int64_t *gvptr, const int64_t *geptr,
+                 std::vector<louvain_result *> &out)
 {
     const louvain_config &cfg = h->cfg;
     const double wall0 = now_ms();
     const LaunchCfg &lc = h->lc;
+    const bool batch = gvptr != nullptr;  // a batch of NG graphs, else one graph (NG = 1)
     sc_buf.reset(&A, 1);
     d_sc = sc_buf.p;
     CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars), s));
@@ -320,10 +344,13 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         kernels += launch_fill_ones(w_own.p, nnz, s, lc);
         d_w = w_own.p;
     }
-    res->n0 = n0;
+    for (int g = 0; g < NG; g++) {
+        out[g]->n0 = batch ? gvptr[g + 1] - gvptr[g] : n0;
+        out[g]->batch_index = batch ? g : -1;
+    }
     if (n0 == 0) {
         CK(cudaStreamSynchronize(s));
-        res->times[3] = now_ms() - wall0;
+        for (int g = 0; g < NG; g++) out[g]->times[3] = now_ms() - wall0;
         return;
     }
 
@@ -338,8 +365,52 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     // ---------------- validation and weighted degrees (Sec. 2)
     kernels += launch_validate_rowptr(d_rp, n0, &d_sc->err, s, lc);
     sync_scalars();  // row offsets must be sane before any row is read
+    // batch bookkeeping: vertex offsets of every graph at the current level, the graph of
+    // every vertex (current level and level 0), per-graph 2W, controllers and statistics
+    DBuf<int64_t> d_gptr, d_gptr_next, d_base1, d_gnnz;
+    DBuf<int32_t> d_vg, d_vg_next, d_vg0, d_rec, d_keep, map0;
+    DBuf<u64> d_gtw;
+    DBuf<SweepStats> d_stats;
+    DBuf<LevelCtl> d_ctls;
+    std::vector<int64_t> h_gptr(NG + 1), h_gnnz(NG + 1), h_base1(NG + 1);
+    if (batch) {
+        for (int g = 0; g <= NG; g++) h_gptr[g] = gvptr[g];
+        d_gptr.reset(&A, NG + 1);
+        d_gptr_next.reset(&A, NG + 1);
+        d_base1.reset(&A, NG + 1);
+        d_gnnz.reset(&A, NG + 1);
+        CK(cudaMemcpyAsync(d_gptr.p, h_gptr.data(), sizeof(int64_t) * (NG + 1),
+                           cudaMemcpyHostToDevice, s));
+        kernels += launch_gather64(d_rp, d_gptr.p, NG + 1, d_gnnz.p, s);
+        CK(cudaMemcpyAsync(h_gnnz.data(), d_gnnz.p, sizeof(int64_t) * (NG + 1),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (geptr)
+            for (int g = 0; g <= NG; g++)
+                if (geptr[g] != h_gnnz[g])
+                    throw LvErr{LOUVAIN_ERR_INDEX_RANGE,
+                                "graph_eptr[" + std::to_string(g) + "] != row_ptr[graph_vptr[g]]"};
+        d_vg.reset(&A, n0);
+        d_vg_next.reset(&A, n0);
+        d_vg0.reset(&A, n0);
+        d_rec.reset(&A, NG);
+        d_keep.reset(&A, NG);
+        map0.reset(&A, n0);
+        d_gtw.reset(&A, NG);
+        d_stats.reset(&A, NG);
+        d_ctls.reset(&A, NG);
+        CK(cudaMemsetAsync(d_gtw.p, 0, sizeof(u64) * NG, s));
+        CK(cudaMemsetAsync(d_stats.p, 0, sizeof(SweepStats) * NG, s));
+        kernels += launch_graph_ids(n0, d_gptr.p, NG, d_vg0.p, s, lc);
+        CK(cudaMemcpyAsync(d_vg.p, d_vg0.p, sizeof(int32_t) * n0, cudaMemcpyDeviceToDevice, s));
+    } else {
+        h_gptr[0] = 0;
+        h_gptr[1] = n0;
+        h_gnnz[0] = 0;
+        h_gnnz[1] = nnz;
+    }
     DBuf<i64> delta, delta_next, deg;
-    DBuf<int32_t> C, Cnext, size, new_id;
+    DBuf<int32_t> C, Cnext, size, new_id, new_id2;
     delta.reset(&A, n0);
     delta_next.reset(&A, n0);
     deg.reset(&A, n0);
@@ -387,15 +458,29 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     };
     const Bins proto_narrow = make_proto(true);
     Bins bins0 = make_bins(G, proto_narrow);
-    kernels += launch_row_sums(G, bins0, delta.p, &d_sc->tw, &d_sc->err, s, lc);
+    kernels += launch_row_sums(G, bins0, batch ? d_vg.p : nullptr, batch ? d_gptr.p : nullptr,
+                               delta.p, batch ? d_gtw.p : &d_sc->tw, &d_sc->err, s, lc);
     if (cfg.checks >= 2) kernels += launch_check_symmetry(G, &d_sc->err, s, lc);
     sync_scalars();
-    const u64 tw_u = h->pinned->tw;
-    if (tw_u > ((u64)1 << 62)) throw LvErr{LOUVAIN_ERR_TOO_LARGE, "sum of weights above 2^62"};
-    const i64 TW = (i64)tw_u;
-    res->tw = TW;
-    const bool wide = cfg.force_int128 || (u128)tw_u * tw_u > (u128)INT64_MAX;
-    const bool narrow = !cfg.wide_sums && tw_u < ((u64)1 << 32);
+    std::vector<i64> h_tw(NG);
+    if (batch) {
+        CK(cudaMemcpyAsync(h_tw.data(), d_gtw.p, sizeof(u64) * NG, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        h_tw[0] = (i64)h->pinned->tw;
+    }
+    u64 tw_max = 0;
+    for (int g = 0; g < NG; g++) {
+        const u64 t = (u64)h_tw[g];
+        if (t > ((u64)1 << 62)) throw LvErr{LOUVAIN_ERR_TOO_LARGE, "sum of weights above 2^62"};
+        if (t > tw_max) tw_max = t;
+        out[g]->tw = h_tw[g];
+    }
+    const i64 TW = h_tw[0];  // one graph: its 2W (a batch reads 2W per graph on the device)
+    // gains in int128 when some graph's (2W)^2 leaves int64; 32-bit table sums when every
+    // graph's 2W fits (a table sum never exceeds its graph's 2W)
+    const bool wide = cfg.force_int128 || (u128)tw_max * tw_max > (u128)INT64_MAX;
+    const bool narrow = !cfg.wide_sums && tw_max < ((u64)1 << 32);
 
     // ---------------- per-run buffers sized by level 0 (Theorem 1: levels never grow)
     const int64_t scratch_n = scan_scratch_elems(n0 + 1) + 64;
@@ -416,9 +501,9 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
     scratch64.reset(&A, scratch_n);
     DBuf<i64> tr_moved, tr_qn;
     const int tcap = cfg.max_iters + 1;
-    tr_moved.reset(&A, tcap);
-    tr_qn.reset(&A, 2 * (size_t)tcap);
-    std::vector<i64> h_tr_moved(tcap), h_tr_qn(2 * (size_t)tcap);
+    tr_moved.reset(&A, (size_t)tcap * NG);
+    tr_qn.reset(&A, 2 * (size_t)tcap * NG);
+    std::vector<i64> h_tr_moved, h_tr_qn;
     // coarsening buffers
     DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_tmp_col;
     DBuf<int64_t> c_mpre;
@@ -502,11 +587,34 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         CK(cudaMemsetAsync(b_gloop.p, 0, sizeof(u64) * nb, s));
     };
 
+    // labels of the original vertices, one array of n0 per level; in a batch, the arrays
+    // are shared by the graphs' results (graph g's labels start at gvptr[g])
+    std::shared_ptr<LabelStore> store;
+    if (batch) {
+        store = std::make_shared<LabelStore>();
+        store->ff = cfg.free;
+        store->ctx = cfg.alloc_ctx;
+        store->device = h->device;
+        for (int g = 0; g < NG; g++) out[g]->store = store;
+    }
     const int32_t *prev_labels = nullptr;
-    i128 qn_prev_level = 0;
+    // per-graph state: in the current level's graph, finished, previous level's Qn
+    std::vector<char> active(NG, 1), rec(NG, 0), keep(NG, 0);
+    std::vector<i128> qn_prev_level(NG, 0);
+    std::vector<int64_t> visits(NG, 0);
+    for (int g = 0; g < NG; g++)
+        if (h_gptr[g + 1] == h_gptr[g]) active[g] = 0;  // an empty graph has no phase
+    std::vector<LevelCtl> h_ctl(NG);
     int64_t edge_visits = 0, sweeps_launched = 0;
     double alg_bytes = 0.0;
     u64 cand_all = 0;
+    LevelCtl *ctl_dev = batch ? d_ctls.p : &d_sc->ctl;
+    SweepStats *st_dev = batch ? d_stats.p : &d_sc->st;
+    BatchCtx bc;
+    if (batch) {
+        bc.gtw = (const i64 *)d_gtw.p;
+        bc.gctl = d_ctls.p;
+    }
 
     for (int level = 0; level < cfg.max_levels; level++) {
         const int64_t n = G.n;
@@ -514,6 +622,7 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
             delta.swap(delta_next);
             st.delta = delta.p;
         }
+        bc.vg = batch ? d_vg.p : nullptr;
         kernels += launch_init_state(n, st, s, lc);
         if (cfg.vertex_following && (level == 0 || cfg.vf_all_levels))
             kernels += launch_vertex_following(G, st, s, lc);
@@ -534,27 +643,40 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         }
         prep_huge(bins, false, 0, nullptr);
 
-        // phase controller
-        LevelCtl ctl;
-        memset(&ctl, 0, sizeof(ctl));
-        ctl.tw = TW;
-        ctl.theta_num = cfg.theta_num;
-        ctl.theta_den = cfg.theta_den;
-        ctl.max_iters = cfg.max_iters;
-        h->pinned->ctl = ctl;
-        CK(cudaMemcpyAsync(&d_sc->ctl, &h->pinned->ctl, sizeof(LevelCtl), cudaMemcpyHostToDevice,
-                           s));
-        CK(cudaMemsetAsync(&d_sc->st, 0, sizeof(SweepStats), s));
+        // phase controllers (graphs without a phase at this level start stopped)
+        int ninactive = 0;
+        for (int g = 0; g < NG; g++) {
+            LevelCtl &c = h_ctl[g];
+            memset(&c, 0, sizeof(c));
+            c.tw = h_tw[g];
+            c.theta_num = cfg.theta_num;
+            c.theta_den = cfg.theta_den;
+            c.max_iters = cfg.max_iters;
+            c.done = active[g] ? 0 : 1;
+            ninactive += !active[g];
+        }
+        if (batch) {
+            CK(cudaMemcpyAsync(d_ctls.p, h_ctl.data(), sizeof(LevelCtl) * NG,
+                               cudaMemcpyHostToDevice, s));
+        } else {
+            h->pinned->ctl = h_ctl[0];
+            CK(cudaMemcpyAsync(&d_sc->ctl, &h->pinned->ctl, sizeof(LevelCtl),
+                               cudaMemcpyHostToDevice, s));
+            CK(cudaMemsetAsync(&d_sc->st, 0, sizeof(SweepStats), s));
+        }
+        h->pinned->ndone = ninactive;
+        CK(cudaMemcpyAsync(&d_sc->ndone, &h->pinned->ndone, sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(&d_sc->cand_total[0], 0, sizeof(u64) * 16, s));
 
-        // sweeps (Algorithm 1); one host read of the controller per sweep
+        // sweeps (Algorithm 1); one host read of the controllers' count per sweep
         int sweeps = 0;
         for (;;) {
-            kernels += launch_sweep(G, st, bins, TW, wide, narrow, &d_sc->st, &d_sc->err, s, lc,
-                                    &tm);
-            kernels += launch_decide(&d_sc->st, &d_sc->ctl, tr_moved.p, tr_qn.p,
-                                     &d_sc->cand_total[0], s);
-            kernels += launch_apply(n, st, &d_sc->ctl, s, lc);
+            kernels += launch_sweep(G, st, bins, TW, wide, narrow, st_dev, &d_sc->err, s, lc,
+                                    &tm, bc);
+            kernels += launch_decide(st_dev, ctl_dev, NG, tr_moved.p, tr_qn.p,
+                                     &d_sc->cand_total[0], &d_sc->ndone, s);
+            kernels += launch_apply(n, st, ctl_dev, bc.vg, s, lc);
             sweeps++;
             sync_scalars();
             for (int b = 0; b < kNumBins; b++) {
@@ -566,29 +688,45 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
                 launches_kernel[b] +=
                     b == 0 ? 1 : (b == kChunkedBin ? bins.nchunks > 0 : bins.nlist[b] > 0);
             }
-            if (h->pinned->ctl.done) break;
+            if (h->pinned->ndone >= NG) break;
             if (sweeps > cfg.max_iters + 2)
                 throw LvErr{LOUVAIN_ERR_INTERNAL, "phase controller did not stop"};
         }
         sweeps_launched += sweeps;
-        const LevelCtl &hc = h->pinned->ctl;
-        const int iters = hc.iters;
-        const i128 qn_final = limbs_to_i128(hc.qn_final);
-        const i128 qn_init = limbs_to_i128(hc.qn_init);
-        const int hit_cap = hc.hit_cap;
+        if (batch) {
+            CK(cudaMemcpyAsync(h_ctl.data(), d_ctls.p, sizeof(LevelCtl) * NG,
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        } else {
+            h_ctl[0] = h->pinned->ctl;
+        }
         u64 cand_level[kNumBins];
         for (int b = 0; b < kNumBins; b++) cand_level[b] = h->pinned->cand_total[b];
-        if (iters > 0) {
-            CK(cudaMemcpyAsync(h_tr_moved.data(), tr_moved.p, sizeof(i64) * iters,
+        int max_iters_run = 0;
+        for (int g = 0; g < NG; g++)
+            if (active[g] && h_ctl[g].iters > max_iters_run) max_iters_run = h_ctl[g].iters;
+        if (max_iters_run > 0) {
+            const size_t cnt = (size_t)max_iters_run * NG;
+            h_tr_moved.resize(cnt);
+            h_tr_qn.resize(2 * cnt);
+            CK(cudaMemcpyAsync(h_tr_moved.data(), tr_moved.p, sizeof(i64) * cnt,
                                cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(h_tr_qn.data(), tr_qn.p, sizeof(i64) * 2 * iters,
+            CK(cudaMemcpyAsync(h_tr_qn.data(), tr_qn.p, sizeof(i64) * 2 * cnt,
                                cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
         }
-        for (int t = 0; t < iters; t++)
-            res->trace.push_back(
-                TraceRec{level, t + 1, h_tr_moved[t], limbs_to_i128(&h_tr_qn[2 * (size_t)t])});
-        edge_visits += (int64_t)iters * G.nnz;
+        for (int g = 0; g < NG; g++) {
+            if (!active[g]) continue;
+            const int it = h_ctl[g].iters;
+            for (int t = 0; t < it; t++) {
+                const size_t e = (size_t)t * NG + g;
+                out[g]->trace.push_back(
+                    TraceRec{level, t + 1, h_tr_moved[e], limbs_to_i128(&h_tr_qn[2 * e])});
+            }
+            const int64_t nnz_g = h_gnnz[g + 1] - h_gnnz[g];
+            visits[g] += (int64_t)it * nnz_g;
+            edge_visits += (int64_t)it * nnz_g;
+        }
         // algorithmic bytes of the sweeps run in this phase (formula in louvain.h)
         {
             const double per_entry = 8.0 + (double)G.wbytes;
@@ -598,37 +736,103 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
                              : (double)bins.nlist[b] * 36.0;
                 const double tot = kb * sweeps + 8.0 * (double)cand_level[b];
                 bytes_kernel[b] += tot;
-                res->bin_rows[b] += (int64_t)(b == 0 ? n : bins.nlist[b]) * sweeps;
-                res->bin_entries[b] += bins.entries[b] * sweeps;
+                for (int g = 0; g < NG; g++) {
+                    out[g]->bin_rows[b] += (int64_t)(b == 0 ? n : bins.nlist[b]) * sweeps;
+                    out[g]->bin_entries[b] += bins.entries[b] * sweeps;
+                }
                 alg_bytes += tot;
                 cand_all += cand_level[b];
             }
         }
 
-        // renumber (Sec. 5.1.2) -- labels of used communities in increasing order
-        kernels += launch_renumber(n, size.p, new_id.p, scratch32.p, s);
-        const int64_t k = read_one(new_id.p + n);
-        if (k == n) break;  // nothing merged: no new level
-
-        LevelRec rec;
-        rec.ncomm = k;
-        rec.qn = qn_final;
-        rec.qn_init = qn_init;
-        rec.iters = iters;
-        rec.n = n;
-        rec.nnz = G.nnz;
-        rec.hit_cap = hit_cap;
-        rec.d_labels = (int32_t *)A.get(sizeof(int32_t) * (size_t)n0);
-        res->levels.push_back(rec);
-        kernels += launch_compose(n0, prev_labels, st.C, new_id.p, rec.d_labels, s, lc);
-        prev_labels = rec.d_labels;
-
-        // Algorithm 2 outer test from the second level on
-        if (level >= 1 &&
-            host_below_threshold(qn_final, qn_prev_level, TW, cfg.theta_num, cfg.theta_den))
-            break;
-        qn_prev_level = qn_final;
-        if (level + 1 >= cfg.max_levels) break;
+        // renumber (Sec. 5.1.2) -- labels of used communities in increasing order; labels
+        // of one graph are contiguous, so the scan also numbers each graph's communities
+        kernels += launch_renumber(n, size.p, nullptr, nullptr, new_id.p, scratch32.p, s);
+        std::vector<int64_t> kg(NG, 0);
+        if (batch) {
+            kernels += launch_gather_ids(new_id.p, d_gptr.p, NG + 1, d_base1.p, s);
+            CK(cudaMemcpyAsync(h_base1.data(), d_base1.p, sizeof(int64_t) * (NG + 1),
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int g = 0; g < NG; g++) kg[g] = h_base1[g + 1] - h_base1[g];
+        } else {
+            kg[0] = read_one(new_id.p + n);
+        }
+        // record the level for every graph that merged something (a graph whose phase
+        // merged nothing is finished: no new level), then the outer test of Algorithm 2
+        int nrec = 0, nkeep = 0;
+        int64_t k_next = 0, n_keep = 0;
+        bool all_active_kept = true;
+        for (int g = 0; g < NG; g++) {
+            const int64_t ng = h_gptr[g + 1] - h_gptr[g];
+            rec[g] = active[g] && kg[g] < ng;
+            keep[g] = 0;
+            if (!rec[g]) {
+                if (active[g]) all_active_kept = false;
+                active[g] = 0;
+                continue;
+            }
+            nrec++;
+            const LevelCtl &hc = h_ctl[g];
+            LevelRec r;
+            r.ncomm = kg[g];
+            r.qn = limbs_to_i128(hc.qn_final);
+            r.qn_init = limbs_to_i128(hc.qn_init);
+            r.iters = hc.iters;
+            r.n = ng;
+            r.nnz = h_gnnz[g + 1] - h_gnnz[g];
+            r.hit_cap = hc.hit_cap;
+            out[g]->levels.push_back(r);
+            const bool stop =
+                (level >= 1 && host_below_threshold(r.qn, qn_prev_level[g], h_tw[g],
+                                                    cfg.theta_num, cfg.theta_den)) ||
+                level + 1 >= cfg.max_levels;
+            qn_prev_level[g] = r.qn;
+            if (stop) {
+                all_active_kept = false;
+                active[g] = 0;
+            } else {
+                keep[g] = 1;
+                nkeep++;
+                k_next += kg[g];
+                n_keep += ng;
+            }
+        }
+        if (nrec == 0) break;
+        int32_t *d_labels = (int32_t *)A.get(sizeof(int32_t) * (size_t)n0);
+        if (batch) {
+            store->arrays.push_back(d_labels);
+            for (int g = 0; g < NG; g++)
+                if (rec[g]) out[g]->levels.back().d_labels = d_labels + gvptr[g];
+        } else {
+            out[0]->levels.back().d_labels = d_labels;
+        }
+        // next-level numbering: the kept graphs' communities only
+        const int32_t *nid2 = new_id.p;
+        if (batch) {
+            std::vector<int32_t> hk(NG), hr(NG);
+            for (int g = 0; g < NG; g++) {
+                hr[g] = rec[g];
+                hk[g] = keep[g];
+            }
+            CK(cudaMemcpyAsync(d_rec.p, hr.data(), sizeof(int32_t) * NG, cudaMemcpyHostToDevice,
+                               s));
+            CK(cudaMemcpyAsync(d_keep.p, hk.data(), sizeof(int32_t) * NG,
+                               cudaMemcpyHostToDevice, s));
+            if (nkeep > 0 && !all_active_kept) {
+                if (!new_id2.p) new_id2.reset(&A, (size_t)n0 + 1);
+                kernels += launch_renumber(n, size.p, d_vg.p, d_keep.p, new_id2.p, scratch32.p, s);
+                nid2 = new_id2.p;
+            }
+            kernels += launch_compose(n0, d_vg0.p, d_rec.p, d_keep.p, level == 0 ? nullptr : map0.p,
+                                      map0.p, st.C, new_id.p, d_base1.p, nid2, d_labels, s, lc);
+            CK(cudaStreamSynchronize(s));  // host vectors above are copied before they go
+        } else {
+            kernels += launch_compose(n0, nullptr, nullptr, nullptr, prev_labels, nullptr, st.C,
+                                      new_id.p, nullptr, nullptr, d_labels, s, lc);
+            prev_labels = d_labels;
+        }
+        if (nkeep == 0) break;
 
         // ---------------- induce the next graph (Sec. 5.1.2)
         if (!c_csize.p) {
@@ -655,7 +859,11 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         cb.scratch64 = scratch64.p;
         if (tm.on) CK(cudaEventRecord(coarsen_ev[0], s));
         Bins cbins = proto;
-        kernels += launch_coarsen_stage1(G, st, new_id.p, k, delta_next.p, cb, cbins, s, lc);
+        const int64_t k = k_next;
+        kernels += launch_coarsen_stage1(G, st, nid2, k, batch ? n_keep : n,
+                                         batch ? d_vg.p : nullptr, batch ? d_keep.p : nullptr,
+                                         batch ? d_vg_next.p : nullptr, delta_next.p, cb, cbins,
+                                         s, lc);
         sync_scalars();
         cbins.list = lists.p;  // the sweep's lists are free again
         cbins.off[0] = cbins.off[1] = cbins.off[2] = 0;
@@ -665,12 +873,12 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         }
         kernels += launch_coarsen_binfill(k, cb, cbins, s, lc);
         prep_huge(cbins, true, k, &cb);
-        kernels += launch_coarsen_stage2(G, st, new_id.p, k, cb, cbins, narrow, &d_sc->err, s, lc);
+        kernels += launch_coarsen_stage2(G, st, nid2, k, cb, cbins, narrow, &d_sc->err, s, lc);
         g_rp_next.reset(&A, (size_t)k + 1);
         kernels += launch_coarsen_rowptr(k, cb, g_rp_next.p, s);
         sync_scalars();
         const int64_t nnz_next = read_one(g_rp_next.p + k);
-        const int wb_next = TW <= INT32_MAX ? 4 : 8;
+        const int wb_next = tw_max <= (u64)INT32_MAX ? 4 : 8;
         g_col_next.reset(&A, (size_t)nnz_next);
         g_w_next.reset(&A, (size_t)nnz_next * wb_next);
         kernels += launch_coarsen_compact(k, nnz_next, cb, g_rp_next.p, g_col_next.p,
@@ -694,6 +902,21 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         G.col = g_col.p;
         G.w = g_w.p;
         G.wbytes = wb_next;
+        if (batch) {
+            // vertex and entry offsets of every graph in the next level's graph
+            d_vg.swap(d_vg_next);
+            kernels += launch_gather_ids(nid2, d_gptr.p, NG + 1, d_gptr_next.p, s);
+            d_gptr.swap(d_gptr_next);
+            kernels += launch_gather64(G.rp, d_gptr.p, NG + 1, d_gnnz.p, s);
+            CK(cudaMemcpyAsync(h_gptr.data(), d_gptr.p, sizeof(int64_t) * (NG + 1),
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(h_gnnz.data(), d_gnnz.p, sizeof(int64_t) * (NG + 1),
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        } else {
+            h_gptr[1] = k;
+            h_gnnz[1] = nnz_next;
+        }
         if (level == 0) {  // the input copies are no longer needed
             rp_own.release();
             col_own.release();
@@ -701,33 +924,37 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         }
     }
     sync_scalars();
-    res->counters[0] = edge_visits;
-    res->counters[1] = sweeps_launched;
-    res->counters[2] = (int64_t)alg_bytes;
-    res->counters[3] = (int64_t)cand_all;
-    res->counters[4] = kernels;
-    if (tm.on) {
-        int dom = 0;
-        for (int b = 1; b < kNumBins; b++)
-            if (t_kernel[b] > t_kernel[dom]) dom = b;
-        double tot = 0;
-        for (int b = 0; b < kNumBins; b++) tot += t_kernel[b];
-        res->times[0] = tot;
-        res->times[4] = t_kernel[dom];
-        res->times[5] = t_kernel[0];
-        res->times[6] = t_kernel[1] + t_kernel[2];
-        res->times[7] = t_kernel[3] + t_kernel[4] + t_kernel[5] + t_kernel[6];
-        res->counters[5] = launches_kernel[dom];
-        res->counters[6] = (int64_t)bytes_kernel[dom];
-        res->counters[7] = dom;
-        res->times[1] = t_coarsen;
+    const double wall = now_ms() - wall0;
+    for (int g = 0; g < NG; g++) {
+        louvain_result *res = out[g];
+        res->counters[0] = batch ? visits[g] : edge_visits;
+        res->counters[1] = sweeps_launched;
+        res->counters[2] = (int64_t)alg_bytes;
+        res->counters[3] = (int64_t)cand_all;
+        res->counters[4] = kernels;
+        if (tm.on) {
+            int dom = 0;
+            for (int b = 1; b < kNumBins; b++)
+                if (t_kernel[b] > t_kernel[dom]) dom = b;
+            double tot = 0;
+            for (int b = 0; b < kNumBins; b++) tot += t_kernel[b];
+            res->times[0] = tot;
+            res->times[4] = t_kernel[dom];
+            res->times[5] = t_kernel[0];
+            res->times[6] = t_kernel[1] + t_kernel[2];
+            res->times[7] = t_kernel[3] + t_kernel[4] + t_kernel[5] + t_kernel[6];
+            res->counters[5] = launches_kernel[dom];
+            res->counters[6] = (int64_t)bytes_kernel[dom];
+            res->counters[7] = dom;
+            res->times[1] = t_coarsen;
+        }
+        for (int b = 0; b < kNumBins; b++) {
+            res->bin_time[b] = t_kernel[b];
+            res->bin_launches[b] = launches_kernel[b];
+            res->bin_bytes[b] = bytes_kernel[b];
+        }
+        res->times[3] = wall;
     }
-    for (int b = 0; b < kNumBins; b++) {
-        res->bin_time[b] = t_kernel[b];
-        res->bin_launches[b] = launches_kernel[b];
-        res->bin_bytes[b] = bytes_kernel[b];
-    }
-    res->times[3] = now_ms() - wall0;
 }
 
 }  // namespace
@@ -894,7 +1121,8 @@ int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int3
     launch_site() = nullptr;
     try {
         CK(cudaSetDevice(h->device));
-        R.run(n, row_ptr, col_idx, weights, ptr_kind, res);
+        std::vector<louvain_result *> outs{res};
+        R.run(n, row_ptr, col_idx, weights, ptr_kind, 1, nullptr, nullptr, outs);
     } catch (const LvErr &e) {
         rc = e.code;
         h->err = e.msg;
@@ -909,6 +1137,76 @@ int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int3
         return rc;
     }
     *out = res;
+    return LOUVAIN_OK;
+}
+
+int louvain_run_batch(louvain_handle *h, int32_t num_graphs, const int64_t *graph_vptr,
+                      const int64_t *graph_eptr, const int64_t *row_ptr, const int32_t *col_idx,
+                      const int32_t *weights, int ptr_kind, void *stream, louvain_result **out)
+{
+    if (!h) return LOUVAIN_ERR_INVALID_ARG;
+    h->err.clear();
+    if (!out || num_graphs < 1 || !graph_vptr || !row_ptr ||
+        (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE)) {
+        h->err = "bad out, num_graphs, graph_vptr, row_ptr or ptr_kind";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    for (int g = 0; g < num_graphs; g++) out[g] = nullptr;
+    if (num_graphs > LOUVAIN_MAX_BATCH_GRAPHS) {
+        h->err = "more graphs than LOUVAIN_MAX_BATCH_GRAPHS";
+        return LOUVAIN_ERR_TOO_LARGE;
+    }
+    if (graph_vptr[0] != 0) {
+        h->err = "graph_vptr[0] must be 0";
+        return LOUVAIN_ERR_INDEX_RANGE;
+    }
+    for (int g = 0; g < num_graphs; g++)
+        if (graph_vptr[g + 1] < graph_vptr[g]) {
+            h->err = "graph_vptr must not decrease";
+            return LOUVAIN_ERR_INDEX_RANGE;
+        }
+    const int64_t n = graph_vptr[num_graphs];
+    if (n > INT32_MAX) {
+        h->err = "total vertex count above 2^31 - 1";
+        return LOUVAIN_ERR_TOO_LARGE;
+    }
+    std::vector<louvain_result *> outs(num_graphs, nullptr);
+    for (int g = 0; g < num_graphs; g++) {
+        outs[g] = new (std::nothrow) louvain_result();
+        if (!outs[g]) {
+            for (int q = 0; q < g; q++) delete outs[q];
+            return LOUVAIN_ERR_OOM;
+        }
+        outs[g]->device = h->device;
+        outs[g]->ff = h->cfg.free;
+        outs[g]->ctx = h->cfg.alloc_ctx;
+    }
+    Runner R;
+    R.h = h;
+    R.s = (cudaStream_t)stream;
+    R.A.fa = h->cfg.alloc;
+    R.A.ff = h->cfg.free;
+    R.A.ctx = h->cfg.alloc_ctx;
+    R.A.s = R.s;
+    int rc = LOUVAIN_OK;
+    launch_site() = nullptr;
+    try {
+        CK(cudaSetDevice(h->device));
+        R.run(n, row_ptr, col_idx, weights, ptr_kind, num_graphs, graph_vptr, graph_eptr, outs);
+    } catch (const LvErr &e) {
+        rc = e.code;
+        h->err = e.msg;
+    } catch (const std::bad_alloc &) {
+        rc = LOUVAIN_ERR_OOM;
+        h->err = "host allocation failed";
+    }
+    if (rc != LOUVAIN_OK) {
+        cudaStreamSynchronize(R.s);
+        cudaGetLastError();
+        for (louvain_result *r : outs) louvain_result_free(r);
+        return rc;
+    }
+    for (int g = 0; g < num_graphs; g++) out[g] = outs[g];
     return LOUVAIN_OK;
 }
 
@@ -1017,6 +1315,11 @@ int louvain_result_bin_stats(const louvain_result *r, int bin, double *time_ms,
 void louvain_result_free(louvain_result *r)
 {
     if (!r) return;
+    if (r->store) {  // a batch's label arrays go with the last of its results
+        r->store.reset();
+        delete r;
+        return;
+    }
     cudaSetDevice(r->device);
     for (LevelRec &L : r->levels) {
         if (!L.d_labels) continue;

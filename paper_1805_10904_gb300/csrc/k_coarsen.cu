@@ -23,24 +23,35 @@
 
 namespace lv {
 
+// A community c of a kept graph (keep[vg[c]], or every community for one graph) becomes
+// vertex a = new_id[c] of the next level.
+__device__ __forceinline__ bool kept(const int32_t *vg, const int32_t *keep, int64_t v)
+{
+    return !vg || keep[vg[v]];
+}
+
 __global__ void k_coarsen_prep(int64_t n, const int32_t *size, const i64 *deg,
-                               const int32_t *new_id, int32_t *csize, i64 *delta_next)
+                               const int32_t *new_id, const int32_t *vg, const int32_t *keep,
+                               int32_t *csize, i64 *delta_next, int32_t *vg_next)
 {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x) {
-        if (size[c] > 0) {
+        if (size[c] > 0 && kept(vg, keep, c)) {
             const int32_t a = new_id[c];
             csize[a] = size[c];
             delta_next[a] = deg[c];
+            if (vg) vg_next[a] = vg[c];
         }
     }
 }
 
 __global__ void k_coarsen_scatter(int64_t n, const int32_t *C, const int32_t *new_id,
-                                  const int32_t *moff, int32_t *cursor, int32_t *members)
+                                  const int32_t *vg, const int32_t *keep, const int32_t *moff,
+                                  int32_t *cursor, int32_t *members)
 {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
          u += (int64_t)gridDim.x * blockDim.x) {
+        if (!kept(vg, keep, u)) continue;
         const int32_t a = new_id[C[u]];
         const int32_t p = moff[a] + atomicAdd(&cursor[a], 1);
         members[p] = (int32_t)u;
@@ -556,21 +567,22 @@ static CBinArgs cbin_args(const Bins &b)
 }
 
 int launch_coarsen_stage1(const DevGraph &g, const PhaseState &st, const int32_t *new_id,
-                          int64_t k, i64 *delta_next, CoarsenBufs &cb, Bins &bins,
+                          int64_t k, int64_t n_keep, const int32_t *vg, const int32_t *keep,
+                          int32_t *vg_next, i64 *delta_next, CoarsenBufs &cb, Bins &bins,
                           cudaStream_t s, const LaunchCfg &lc)
 {
     int launched = 0;
     const int64_t n = g.n;
-    k_coarsen_prep<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(n, st.size, st.deg,
-                                                                        new_id, cb.csize,
-                                                                        delta_next);
+    k_coarsen_prep<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        n, st.size, st.deg, new_id, vg, keep, cb.csize, delta_next, vg_next);
     launched++;
     launched += exclusive_scan<int32_t>(ArrayIn<int32_t>{cb.csize}, k, cb.moff, cb.scratch32, s);
     cudaMemsetAsync(cb.cursor, 0, sizeof(int32_t) * (size_t)k, s);
     k_coarsen_scatter<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        n, st.C, new_id, cb.moff, cb.cursor, cb.members);
+        n, st.C, new_id, vg, keep, cb.moff, cb.cursor, cb.members);
     launched++;
-    launched += exclusive_scan<int64_t>(MemberDegIn{cb.members, g.rp}, n, cb.mpre, cb.scratch64, s);
+    launched += exclusive_scan<int64_t>(MemberDegIn{cb.members, g.rp}, n_keep, cb.mpre,
+                                        cb.scratch64, s);
     cudaMemsetAsync(cb.counts, 0, sizeof(int32_t) * 16, s);
     k_coarsen_bin<false><<<grid_for(k, kBlock, lc.max_blocks), kBlock, 0, s>>>(
         k, cb.moff, cb.mpre, cbin_args(bins), cb.counts);

@@ -52,83 +52,113 @@ int launch_fill_ones(int32_t *w, int64_t nnz, cudaStream_t s, const LaunchCfg &l
 // delta_i = sum of row i's weights (loop once), 2W = sum delta; columns and weights are
 // checked on the way.  Rows of bin 0 take one thread each (dense kernel), rows of bins 1-2
 // one warp each, longer rows one CTA each, so a hub row never serialises on one warp.
-__device__ __forceinline__ void check_entry(int32_t j, i64 x, int64_t n, unsigned &bad)
+// In a batch (vg set) 2W is per graph and a column must stay inside its row's graph.
+struct RowCtx {
+    int64_t n;
+    const int32_t *vg;
+    const int64_t *gptr;
+    u64 *tw;
+    __device__ __forceinline__ int graph(int64_t i) const { return vg ? vg[i] : 0; }
+    __device__ __forceinline__ void range(int g, int64_t &lo, int64_t &hi) const
+    {
+        lo = vg ? gptr[g] : 0;
+        hi = vg ? gptr[g + 1] : n;
+    }
+};
+
+__device__ __forceinline__ void check_entry(int32_t j, i64 x, int64_t lo, int64_t hi, unsigned &bad)
 {
-    if ((uint32_t)j >= (uint64_t)n) bad |= ERRF_INDEX;
+    if ((int64_t)j < lo || (int64_t)j >= hi) bad |= ERRF_INDEX;
     if (x < 1) bad |= ERRF_WEIGHT;
 }
 
 template <typename WT>
-__global__ void __launch_bounds__(kBlock) k_row_sums_thread(int64_t n, const int64_t *rp,
+__global__ void __launch_bounds__(kBlock) k_row_sums_thread(RowCtx R, const int64_t *rp,
                                                             const int32_t *col, const WT *w,
-                                                            int64_t dmax, i64 *delta, u64 *tw,
+                                                            int64_t dmax, i64 *delta,
                                                             unsigned *err)
 {
     unsigned bad = 0;
-    u64 tot = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = rp[i], e = rp[i + 1];
-        if (e - b > dmax) continue;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < R.n;
+         i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
         u64 sum = 0;
-        for (int64_t k = b; k < e; k++) {
-            const i64 x = (i64)w[k];
-            check_entry(col[k], x, n, bad);
-            sum += (u64)x;
+        int g = -1;
+        if (i < R.n) {
+            const int64_t b = rp[i], e = rp[i + 1];
+            if (e - b <= dmax) {
+                g = R.graph(i);
+                int64_t lo, hi;
+                R.range(g, lo, hi);
+                for (int64_t k = b; k < e; k++) {
+                    const i64 x = (i64)w[k];
+                    check_entry(col[k], x, lo, hi, bad);
+                    sum += (u64)x;
+                }
+                delta[i] = (i64)sum;
+            }
         }
-        delta[i] = (i64)sum;
-        tot += sum;
+        // one atomic per warp when its rows share a graph
+        const int g0 = __shfl_sync(0xffffffffu, g, 0);
+        if (__all_sync(0xffffffffu, g == g0 || g < 0)) {
+            const u64 ws = sum_reduce(sum, 32);
+            if ((threadIdx.x & 31) == 0 && g0 >= 0 && ws) atomicAdd(&R.tw[g0], ws);
+        } else if (g >= 0 && sum) {
+            atomicAdd(&R.tw[g], sum);
+        }
     }
-    tot = sum_reduce(tot, 32);
-    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(tw, tot);
     if (bad) atomicOr(err, bad);
 }
 
 template <typename WT>
-__global__ void __launch_bounds__(kBlock) k_row_sums_warp(int64_t n, const int64_t *rp,
+__global__ void __launch_bounds__(kBlock) k_row_sums_warp(RowCtx R, const int64_t *rp,
                                                           const int32_t *col, const WT *w,
                                                           const int32_t *rows, int64_t nrows,
-                                                          i64 *delta, u64 *tw, unsigned *err)
+                                                          i64 *delta, unsigned *err)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned bad = 0;
-    u64 tot = 0;
     for (int64_t r = warp; r < nrows; r += nwarps) {
         const int32_t i = rows[r];
+        const int g = R.graph(i);
+        int64_t lo, hi;
+        R.range(g, lo, hi);
         const int64_t b = rp[i], e = rp[i + 1];
         u64 sum = 0;
         for (int64_t k = b + lane; k < e; k += 32) {
             const i64 x = (i64)w[k];
-            check_entry(col[k], x, n, bad);
+            check_entry(col[k], x, lo, hi, bad);
             sum += (u64)x;
         }
         sum = sum_reduce(sum, 32);
         if (lane == 0) {
             delta[i] = (i64)sum;
-            tot += sum;
+            atomicAdd(&R.tw[g], sum);
         }
     }
-    if (lane == 0 && tot) atomicAdd(tw, tot);
     if (bad) atomicOr(err, bad);
 }
 
 template <typename WT>
-__global__ void __launch_bounds__(kBlock) k_row_sums_cta(int64_t n, const int64_t *rp,
+__global__ void __launch_bounds__(kBlock) k_row_sums_cta(RowCtx R, const int64_t *rp,
                                                          const int32_t *col, const WT *w,
                                                          const int32_t *rows, int64_t nrows,
-                                                         i64 *delta, u64 *tw, unsigned *err)
+                                                         i64 *delta, unsigned *err)
 {
     __shared__ u64 s_part[kBlock / 32];
     unsigned bad = 0;
     for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
         const int32_t i = rows[r];
+        const int g = R.graph(i);
+        int64_t lo, hi;
+        R.range(g, lo, hi);
         const int64_t b = rp[i], e = rp[i + 1];
         u64 sum = 0;
         for (int64_t k = b + threadIdx.x; k < e; k += kBlock) {
             const i64 x = (i64)w[k];
-            check_entry(col[k], x, n, bad);
+            check_entry(col[k], x, lo, hi, bad);
             sum += (u64)x;
         }
         sum = sum_reduce(sum, 32);
@@ -138,7 +168,7 @@ __global__ void __launch_bounds__(kBlock) k_row_sums_cta(int64_t n, const int64_
             u64 t = 0;
             for (int q = 0; q < kBlock / 32; q++) t += s_part[q];
             delta[i] = (i64)t;
-            atomicAdd(tw, t);
+            atomicAdd(&R.tw[g], t);
         }
         __syncthreads();
     }
@@ -146,34 +176,35 @@ __global__ void __launch_bounds__(kBlock) k_row_sums_cta(int64_t n, const int64_
 }
 
 template <typename WT>
-static int row_sums_impl(const DevGraph &g, const Bins &b, i64 *delta, u64 *tw, unsigned *err,
-                         cudaStream_t s, const LaunchCfg &lc)
+static int row_sums_impl(const DevGraph &g, const Bins &b, const RowCtx &R, i64 *delta,
+                         unsigned *err, cudaStream_t s, const LaunchCfg &lc)
 {
     const WT *w = (const WT *)g.w;
     int launched = 1;
     k_row_sums_thread<WT><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        g.n, g.rp, g.col, w, b.upper[0], delta, tw, err);
+        R, g.rp, g.col, w, b.upper[0], delta, err);
     const int64_t nwarp = b.off[3] - b.off[1];
     if (nwarp > 0) {
         k_row_sums_warp<WT><<<grid_for(nwarp, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(
-            g.n, g.rp, g.col, w, b.list + b.off[1], nwarp, delta, tw, err);
+            R, g.rp, g.col, w, b.list + b.off[1], nwarp, delta, err);
         launched++;
     }
     const int64_t ncta = b.off[kNumBins] - b.off[3];
     if (ncta > 0) {
         k_row_sums_cta<WT><<<grid_for(ncta, 1, lc.max_blocks), kBlock, 0, s>>>(
-            g.n, g.rp, g.col, w, b.list + b.off[3], ncta, delta, tw, err);
+            R, g.rp, g.col, w, b.list + b.off[3], ncta, delta, err);
         launched++;
     }
     return launched;
 }
 
-int launch_row_sums(const DevGraph &g, const Bins &b, i64 *delta, u64 *tw, unsigned *err,
-                    cudaStream_t s, const LaunchCfg &lc)
+int launch_row_sums(const DevGraph &g, const Bins &b, const int32_t *vg, const int64_t *gptr,
+                    i64 *delta, u64 *tw, unsigned *err, cudaStream_t s, const LaunchCfg &lc)
 {
     if (g.n == 0) return 0;
-    if (g.wbytes == 4) return row_sums_impl<int32_t>(g, b, delta, tw, err, s, lc);
-    return row_sums_impl<i64>(g, b, delta, tw, err, s, lc);
+    RowCtx R{g.n, vg, gptr, tw};
+    if (g.wbytes == 4) return row_sums_impl<int32_t>(g, b, R, delta, err, s, lc);
+    return row_sums_impl<i64>(g, b, R, delta, err, s, lc);
 }
 
 // Full input checks: every row strictly increasing (sorted, no duplicate), and every
@@ -465,11 +496,14 @@ __device__ bool dev_below_threshold(i128 qn_new, i128 qn_old, i64 tw, i64 num, i
 //           sweeps reached the cap;
 //   stop with C_{k-1} = C_k if sweep k moved nobody.
 // Otherwise the proposal is applied by k_apply.  The trace gets (moved, Qn) of every
-// applied sweep.
-__global__ void k_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_qn,
-                         u64 *cand_total)
+// applied sweep.  Thread g runs the controller of graph g of a batch (G = 1: one graph).
+__global__ void k_decide(SweepStats *sts, LevelCtl *ctls, int G, i64 *tr_moved, i64 *tr_qn,
+                         u64 *cand_total, int *ndone)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    SweepStats *st = sts + g;
+    LevelCtl *ctl = ctls + g;
     if (!ctl->done) {
         const i128 sq = (i128)(((u128)st->sq_hi << 64) | (u128)st->sq_lo);
         const i128 qn = (i128)ctl->tw * (i128)(i64)st->internal - sq;
@@ -477,14 +511,13 @@ __global__ void k_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_q
         const i64 moved = (i64)st->moved;
         bool stop = false;
         int iters = 0;
-        for (int b = 0; b < 16; b++) cand_total[b] += st->cand[b];
         if (k == 1) {
             i128_to(qn, ctl->qn_init);
         } else {
             const int t = k - 2;
             if (t < ctl->max_iters + 1) {
-                tr_moved[t] = ctl->moved_last;
-                i128_to(qn, &tr_qn[2 * t]);
+                tr_moved[(size_t)t * G + g] = ctl->moved_last;
+                i128_to(qn, &tr_qn[2 * ((size_t)t * G + g)]);
             }
             if (dev_below_threshold(qn, i128_from(ctl->qn_prev), ctl->tw, ctl->theta_num,
                                     ctl->theta_den)) {
@@ -499,8 +532,8 @@ __global__ void k_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_q
         if (!stop && moved == 0) {
             const int t = k - 1;
             if (t < ctl->max_iters + 1) {
-                tr_moved[t] = 0;
-                i128_to(qn, &tr_qn[2 * t]);
+                tr_moved[(size_t)t * G + g] = 0;
+                i128_to(qn, &tr_qn[2 * ((size_t)t * G + g)]);
             }
             stop = true;
             iters = k;
@@ -509,6 +542,7 @@ __global__ void k_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_q
             ctl->done = 1;
             ctl->iters = iters;
             i128_to(qn, ctl->qn_final);
+            atomicAdd(ndone, 1);
         } else {
             i128_to(qn, ctl->qn_prev);
             ctl->moved_last = moved;
@@ -519,27 +553,34 @@ __global__ void k_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_q
     st->sq_lo = 0;
     st->sq_hi = 0;
     st->moved = 0;
-    for (int b = 0; b < 16; b++) st->cand[b] = 0;
+    if (g == 0) {
+        for (int b = 0; b < 16; b++) {
+            cand_total[b] += st->cand[b];
+            st->cand[b] = 0;
+        }
+    }
 }
 
-int launch_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_qn, u64 *cand_total,
-                  cudaStream_t s)
+int launch_decide(SweepStats *st, LevelCtl *ctl, int G, i64 *tr_moved, i64 *tr_qn,
+                  u64 *cand_total, int *ndone, cudaStream_t s)
 {
-    k_decide<<<1, 32, 0, s>>>(st, ctl, tr_moved, tr_qn, cand_total);
+    k_decide<<<(G + 127) / 128, 128, 0, s>>>(st, ctl, G, tr_moved, tr_qn, cand_total, ndone);
     return 1;
 }
 
-// Apply the sweep's proposal (unless the controller stopped the phase): deg_C and size_C
-// follow the moved vertices (the paper's remove / insert with atomics), then C <- C_next.
+// Apply the sweep's proposal (unless the controller of the vertex's graph stopped the
+// phase): deg_C and size_C follow the moved vertices (the paper's remove / insert with
+// atomics), then C <- C_next.
 __global__ void __launch_bounds__(kBlock) k_apply(int64_t n, int32_t *C, const int32_t *Cnext,
                                                   i64 *deg, int32_t *size, const i64 *delta,
-                                                  const LevelCtl *ctl)
+                                                  const LevelCtl *ctl, const int32_t *vg)
 {
-    if (*(volatile const int *)&ctl->done) return;
+    if (!vg && *(volatile const int *)&ctl->done) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = C[i], b = Cnext[i];
         if (a == b) continue;
+        if (vg && ctl[vg[i]].done) continue;
         const i64 d = delta[i];
         atomicAdd((u64 *)&deg[b], (u64)d);
         atomicAdd((u64 *)&deg[a], (u64)(-d));
@@ -549,39 +590,110 @@ __global__ void __launch_bounds__(kBlock) k_apply(int64_t n, int32_t *C, const i
     }
 }
 
-int launch_apply(int64_t n, const PhaseState &st, const LevelCtl *ctl, cudaStream_t s,
-                 const LaunchCfg &lc)
+int launch_apply(int64_t n, const PhaseState &st, const LevelCtl *ctl, const int32_t *vg,
+                 cudaStream_t s, const LaunchCfg &lc)
 {
     if (n == 0) return 0;
     k_apply<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(n, st.C, st.Cnext, st.deg,
-                                                                 st.size, st.delta, ctl);
+                                                                 st.size, st.delta, ctl, vg);
     return 1;
 }
 
 // ------------------------------------------------------------------ renumber / compose
 
-// new_id[c] = number of non-empty communities below c; new_id[n] = their count.
-int launch_renumber(int64_t n, const int32_t *size, int32_t *new_id, int32_t *scratch,
-                    cudaStream_t s)
+struct UsedIn {  // 1 for a used label whose graph is kept
+    const int32_t *size;
+    const int32_t *vg;
+    const int32_t *keep;
+    __device__ __forceinline__ int32_t operator()(int64_t c) const
+    {
+        return size[c] > 0 && (!keep || keep[vg ? vg[c] : 0]) ? 1 : 0;
+    }
+};
+
+// new_id[c] = number of used labels below c; new_id[n] = their count.  Labels of one graph
+// are contiguous, so a batch's labels are renumbered graph by graph by the same scan.
+int launch_renumber(int64_t n, const int32_t *size, const int32_t *vg, const int32_t *keep,
+                    int32_t *new_id, int32_t *scratch, cudaStream_t s)
 {
-    return exclusive_scan<int32_t>(PositiveFlagIn<int32_t, int32_t>{size}, n, new_id, scratch, s);
+    return exclusive_scan<int32_t>(UsedIn{size, vg, keep}, n, new_id, scratch, s);
 }
 
-__global__ void k_compose(int64_t n0, const int32_t *prev, const int32_t *C,
-                          const int32_t *new_id, int32_t *out)
+__global__ void k_gather64(const int64_t *a, const int64_t *idx, int cnt, int64_t *out)
 {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+        out[i] = a[idx[i]];
+}
+
+__global__ void k_gather_ids(const int32_t *a, const int64_t *idx, int cnt, int64_t *out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+        out[i] = (int64_t)a[idx[i]];
+}
+
+int launch_gather64(const int64_t *a, const int64_t *idx, int cnt, int64_t *out, cudaStream_t s)
+{
+    if (cnt <= 0) return 0;
+    k_gather64<<<(cnt + 255) / 256, 256, 0, s>>>(a, idx, cnt, out);
+    return 1;
+}
+
+int launch_gather_ids(const int32_t *a, const int64_t *idx, int cnt, int64_t *out, cudaStream_t s)
+{
+    if (cnt <= 0) return 0;
+    k_gather_ids<<<(cnt + 255) / 256, 256, 0, s>>>(a, idx, cnt, out);
+    return 1;
+}
+
+// vg[v] = the graph g with gptr[g] <= v < gptr[g+1] (empty graphs own no vertex).
+__global__ void k_graph_ids(int64_t n, const int64_t *gptr, int G, int32_t *vg)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t u = prev ? prev[v] : (int32_t)v;
-        out[v] = new_id[C[u]];
+        int lo = 0, hi = G;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (gptr[mid] <= v) lo = mid;
+            else hi = mid;
+        }
+        vg[v] = lo;
     }
 }
 
-int launch_compose(int64_t n0, const int32_t *prev, const int32_t *C, const int32_t *new_id,
+int launch_graph_ids(int64_t n, const int64_t *gptr, int G, int32_t *vg, cudaStream_t s,
+                     const LaunchCfg &lc)
+{
+    if (n == 0) return 0;
+    k_graph_ids<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(n, gptr, G, vg);
+    return 1;
+}
+
+// Labels of the original vertices (Sec. 5.1.2: a vertex's community at level l is the
+// community of the level-l vertex it was merged into).  m = map_in[v] (v itself when
+// map_in is null) is v's vertex at this level; out[v] = new_id1[C[m]] - base1[g].
+__global__ void k_compose(int64_t n0, const int32_t *vg0, const int32_t *rec, const int32_t *keep,
+                          const int32_t *map_in, int32_t *map_out, const int32_t *C,
+                          const int32_t *new_id1, const int64_t *base1, const int32_t *new_id2,
+                          int32_t *out)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n0;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int g = vg0 ? vg0[v] : 0;
+        if (rec && !rec[g]) continue;
+        const int32_t c = C[map_in ? map_in[v] : (int32_t)v];
+        out[v] = new_id1[c] - (base1 ? (int32_t)base1[g] : 0);
+        if (map_out && (!keep || keep[g])) map_out[v] = new_id2[c];
+    }
+}
+
+int launch_compose(int64_t n0, const int32_t *vg0, const int32_t *rec, const int32_t *keep,
+                   const int32_t *map_in, int32_t *map_out, const int32_t *C,
+                   const int32_t *new_id1, const int64_t *base1, const int32_t *new_id2,
                    int32_t *out, cudaStream_t s, const LaunchCfg &lc)
 {
     if (n0 == 0) return 0;
-    k_compose<<<grid_for(n0, kBlock, lc.max_blocks), kBlock, 0, s>>>(n0, prev, C, new_id, out);
+    k_compose<<<grid_for(n0, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        n0, vg0, rec, keep, map_in, map_out, C, new_id1, base1, new_id2, out);
     return 1;
 }
 

@@ -46,11 +46,38 @@ struct MoveArgs {
     const i64 *deg;
     const int32_t *size;
     const i64 *delta;
-    i64 tw;
+    i64 tw;               // 2W of the graph (one graph)
     int32_t *Cnext;
-    SweepStats *st;
+    SweepStats *st;       // per graph (one entry for one graph)
     unsigned *err;
+    const int32_t *vg;    // graph of every vertex in a batch of graphs, nullptr for one graph
+    const i64 *gtw;       // 2W of every graph of the batch
+    const LevelCtl *gctl; // phase controller of every graph; rows of finished graphs are frozen
 };
+
+// Graph context of vertex i: its graph, that graph's 2W, and whether its phase has stopped.
+template <typename WT>
+__device__ __forceinline__ int graph_of(const MoveArgs<WT> &A, int64_t i)
+{
+    return A.vg ? A.vg[i] : 0;
+}
+template <typename WT>
+__device__ __forceinline__ i64 tw_of(const MoveArgs<WT> &A, int g)
+{
+    return A.vg ? A.gtw[g] : A.tw;
+}
+template <typename WT>
+__device__ __forceinline__ bool frozen(const MoveArgs<WT> &A, int g)
+{
+    return A.vg && *(volatile const int *)&A.gctl[g].done;
+}
+
+// Per-row statistics of a batch of graphs go straight to the row's graph.
+__device__ __forceinline__ void row_stats(SweepStats *st, int g, i64 internal, bool moved)
+{
+    if (internal) atomicAdd(&st[g].internal, (u64)internal);
+    if (moved) atomicAdd(&st[g].moved, 1ull);
+}
 
 // Decision of Algorithm 1 for vertex i in community a (Eq. 4-5, Sec. 3.1).
 template <typename GT>
@@ -115,67 +142,102 @@ __device__ __forceinline__ void block_argmax(GT &g, int32_t &c, i64 &e_a, i64 &l
 }
 
 // ------------------------------------------------------------------ bin 0
-// Dense over every vertex: also adds deg[i]^2 of label i to sum_c deg_c^2.
+// Dense over every vertex: also adds deg[i]^2 of label i to sum_c deg_c^2.  The loop is
+// uniform across each warp so a batch of graphs can combine a warp's statistics when all
+// its vertices belong to one graph.
 template <typename WT, typename GT>
 __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small_max)
 {
     u64 internal = 0, moved = 0, cand = 0;
     u128 sq = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const i64 dg = A.deg[i];
-        sq += (u128)(u64)dg * (u64)dg;
-        const int64_t rb = A.rp[i];
-        const int64_t d = A.rp[i + 1] - rb;
-        if (d > small_max) continue;
-        const int32_t a = A.C[i];
-        int32_t lab[kSmallMax];
-        i64 wt[kSmallMax];
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < A.n;
+         i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        u64 v_int = 0, v_mov = 0;
+        u128 v_sq = 0;
+        int g = -1;
+        if (i < A.n) {
+            g = graph_of(A, i);
+            const i64 dg = A.deg[i];
+            v_sq = (u128)(u64)dg * (u64)dg;
+            const int64_t rb = A.rp[i];
+            const int64_t d = A.rp[i + 1] - rb;
+            const bool fz = frozen(A, g);
+            if (d <= small_max && !fz) {
+                const i64 tw = tw_of(A, g);
+                const int32_t a = A.C[i];
+                int32_t lab[kSmallMax];
+                i64 wt[kSmallMax];
 #pragma unroll
-        for (int t = 0; t < kSmallMax; t++) {
-            lab[t] = -1;
-            wt[t] = 0;
-            if (t < d) {
-                lab[t] = A.col[rb + t];
-                wt[t] = (i64)A.w[rb + t];
-            }
-        }
-        i64 loop = 0;
-#pragma unroll
-        for (int t = 0; t < kSmallMax; t++) {
-            if (t < d) {
-                if (lab[t] == (int32_t)i) {
-                    loop += wt[t];
+                for (int t = 0; t < kSmallMax; t++) {
                     lab[t] = -1;
-                } else {
-                    lab[t] = A.C[lab[t]];
+                    wt[t] = 0;
+                    if (t < d) {
+                        lab[t] = A.col[rb + t];
+                        wt[t] = (i64)A.w[rb + t];
+                    }
                 }
+                i64 loop = 0;
+#pragma unroll
+                for (int t = 0; t < kSmallMax; t++) {
+                    if (t < d) {
+                        if (lab[t] == (int32_t)i) {
+                            loop += wt[t];
+                            lab[t] = -1;
+                        } else {
+                            lab[t] = A.C[lab[t]];
+                        }
+                    }
+                }
+                const i64 dl = A.delta[i];
+                i64 e_a = 0;
+                GT gbest = gain_min<GT>();
+                int32_t best = INT_MAX;
+                int m = 0;
+#pragma unroll
+                for (int t = 0; t < kSmallMax; t++) {
+                    const int32_t c = lab[t];
+                    bool first = c >= 0;
+#pragma unroll
+                    for (int u = 0; u < t; u++) first = first && (lab[u] != c);
+                    if (first) {
+                        i64 e = 0;
+#pragma unroll
+                        for (int u = t; u < kSmallMax; u++) e += (lab[u] == c) ? wt[u] : 0;
+                        m++;
+                        consider<GT>(c, e, a, dl, tw, A.deg, gbest, best, e_a);
+                    }
+                }
+                const int32_t target = choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
+                A.Cnext[i] = target;
+                v_mov = target != a;
+                v_int = (u64)(e_a + loop);
+                cand += (u64)m;
+            } else if (d <= small_max) {
+                A.Cnext[i] = A.C[i];  // frozen graph: nothing moves
             }
         }
-        const i64 dl = A.delta[i];
-        i64 e_a = 0;
-        GT gbest = gain_min<GT>();
-        int32_t best = INT_MAX;
-        int m = 0;
-#pragma unroll
-        for (int t = 0; t < kSmallMax; t++) {
-            const int32_t c = lab[t];
-            bool first = c >= 0;
-#pragma unroll
-            for (int u = 0; u < t; u++) first = first && (lab[u] != c);
-            if (first) {
-                i64 e = 0;
-#pragma unroll
-                for (int u = t; u < kSmallMax; u++) e += (lab[u] == c) ? wt[u] : 0;
-                m++;
-                consider<GT>(c, e, a, dl, A.tw, A.deg, gbest, best, e_a);
-            }
+        if (!A.vg) {
+            internal += v_int;
+            moved += v_mov;
+            sq += v_sq;
+            continue;
         }
-        const int32_t target = choose_target<GT>(a, best, gbest, e_a, dl, A.tw, A.deg, A.size);
-        A.Cnext[i] = target;
-        moved += target != a;
-        internal += (u64)(e_a + loop);
-        cand += (u64)m;
+        // batch of graphs: one atomic per warp when the warp's vertices share a graph
+        const int g0 = __shfl_sync(0xffffffffu, g, 0);
+        if (__all_sync(0xffffffffu, g == g0 || g < 0)) {
+            const u64 wi = sum_reduce(v_int, 32), wm = sum_reduce(v_mov, 32);
+            const u128 ws = sum_reduce(v_sq, 32);
+            if ((threadIdx.x & 31) == 0 && g0 >= 0) {
+                if (wi) atomicAdd(&A.st[g0].internal, wi);
+                if (wm) atomicAdd(&A.st[g0].moved, wm);
+                if (ws) atomic_add_u128(&A.st[g0].sq_lo, &A.st[g0].sq_hi, ws);
+            }
+        } else if (g >= 0) {
+            if (v_int) atomicAdd(&A.st[g].internal, v_int);
+            if (v_mov) atomicAdd(&A.st[g].moved, v_mov);
+            if (v_sq) atomic_add_u128(&A.st[g].sq_lo, &A.st[g].sq_hi, v_sq);
+        }
     }
     block_flush_stats(A.st, 0, internal, moved, cand, sq);
 }
@@ -210,11 +272,16 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
         const bool valid = vi < nverts;
         int32_t i = 0, a = 0;
         int64_t rb = 0, re = 0;
-        i64 dl = 0;
+        i64 dl = 0, tw = 0;
+        int gr = 0;
+        bool fz = false;
         if (valid) {
             i = verts[vi];
+            gr = graph_of(A, i);
+            tw = tw_of(A, gr);
+            fz = frozen(A, gr);
             rb = A.rp[i];
-            re = A.rp[i + 1];
+            re = fz ? rb : A.rp[i + 1];  // a frozen row inserts nothing and stays
             a = A.C[i];
             dl = A.delta[i];
         }
@@ -236,7 +303,7 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
             const i64 e = (i64)vals[s];
             keys[s] = -1;
             vals[s] = 0;
-            consider<GT>(c, e, a, dl, A.tw, A.deg, gbest, best, e_a);
+            consider<GT>(c, e, a, dl, tw, A.deg, gbest, best, e_a);
         }
         argmax_reduce(gbest, best, G);
         e_a = sum_reduce(e_a, G);
@@ -244,10 +311,14 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
         if (lane == 0) {
             if (valid) {
                 const int32_t target =
-                    choose_target<GT>(a, best, gbest, e_a, dl, A.tw, A.deg, A.size);
+                    choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
                 A.Cnext[i] = target;
-                moved += target != a;
-                internal += (u64)(e_a + loop);
+                if (!A.vg) {
+                    moved += target != a;
+                    internal += (u64)(e_a + loop);
+                } else if (!fz) {
+                    row_stats(A.st, gr, e_a + loop, target != a);
+                }
                 cand += (u64)m;
             }
             *cnt = 0;
@@ -336,15 +407,20 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
         const int32_t i_next = vn < nverts ? verts[vn] : -1;
         const int32_t a = A.C[i];
         const i64 dl = A.delta[i];
+        const int gr = graph_of(A, i);
+        const i64 tw = tw_of(A, gr);
+        const bool fz = frozen(A, gr);  // a frozen row inserts nothing and stays
         // the prefetched first chunk, then the rest of the row
         i64 loop = 0;
+        if (!fz) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
-            if (nj[u] == i) loop += nw[u];
-            chunk_insert<VT>(nc[u], nw[u], ins);
+            for (int u = 0; u < kUnroll; u++) {
+                if (nj[u] == i) loop += nw[u];
+                chunk_insert<VT>(nc[u], nw[u], ins);
+            }
         }
         for (int64_t k0 = rb + threadIdx.x + (int64_t)kUnroll * BLOCK;
-             __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * BLOCK) {
+             !fz && __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * BLOCK) {
             int32_t j[kUnroll], c[kUnroll];
             i64 x[kUnroll];
             load_chunk<BLOCK>(A, k0, re, j, x);
@@ -376,7 +452,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
             const i64 e = (i64)vals[s];
             keys[s] = -1;
             vals[s] = 0;
-            consider<GT>(cc, e, a, dl, A.tw, A.deg, gbest, best, e_a);
+            consider<GT>(cc, e, a, dl, tw, A.deg, gbest, best, e_a);
         }
         // stage 4: next row's label gathers
         gather_chunk(A, i_next, nj, nc);
@@ -384,13 +460,17 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
         if (threadIdx.x == 0) {
             int32_t target = a;
             if (best != INT_MAX) {
-                const GT gstay = (GT)A.tw * (GT)e_a - (GT)dl * (GT)(deg_a - dl);
+                const GT gstay = (GT)tw * (GT)e_a - (GT)dl * (GT)(deg_a - dl);
                 if (gbest > gstay && !(size_a == 1 && best > a && A.size[best] == 1))
                     target = best;
             }
             A.Cnext[i] = target;
-            moved += target != a;
-            internal += (u64)(e_a + loop);
+            if (!A.vg) {
+                moved += target != a;
+                internal += (u64)(e_a + loop);
+            } else if (!fz) {
+                row_stats(A.st, gr, e_a + loop, target != a);
+            }
             cand += (u64)m;
             s_cnt = 0;
         }
@@ -439,7 +519,10 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
     u64 internal = 0, moved = 0, cand = 0;
     for (int v = cid; v < nverts; v += ncl) {
         const int32_t i = verts[v];
-        const int64_t rb = A.rp[i], re = A.rp[i + 1];
+        const int gr = graph_of(A, i);
+        const i64 tw = tw_of(A, gr);
+        const bool fz = frozen(A, gr);  // a frozen row inserts nothing and stays
+        const int64_t rb = A.rp[i], re = fz ? rb : A.rp[i + 1];
         i64 loop = 0;
         auto cins = [&](int32_t key, VT val) {
             cluster_insert<VT>(cluster, keys, vals, LOG2CL, log2cap, key, val, A.err);
@@ -480,7 +563,7 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
             keys[s] = -1;
             vals[s] = 0;
             mloc++;
-            consider<GT>(cc, e, a, dl, A.tw, A.deg, gbest, best, e_a);
+            consider<GT>(cc, e, a, dl, tw, A.deg, gbest, best, e_a);
         }
         mloc = sum_reduce(mloc, 32);  // per-warp count, folded into the CTA sum below
         block_argmax(gbest, best, e_a, loop);
@@ -513,10 +596,14 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
                 lp += *cluster.map_shared_rank(&p_l, r);
                 mm += *cluster.map_shared_rank(&p_m, r);
             }
-            const int32_t target = choose_target<GT>(a, c, g, ea, dl, A.tw, A.deg, A.size);
+            const int32_t target = choose_target<GT>(a, c, g, ea, dl, tw, A.deg, A.size);
             A.Cnext[i] = target;
-            moved += target != a;
-            internal += (u64)(ea + lp);
+            if (!A.vg) {
+                moved += target != a;
+                internal += (u64)(ea + lp);
+            } else if (!fz) {
+                row_stats(A.st, gr, ea + lp, target != a);
+            }
             cand += (u64)mm;
         }
         cluster.sync();  // partials read before the next row overwrites them
@@ -572,6 +659,12 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
         const int64_t ce = min(re, cb + (int64_t)B.chunk);
         const int32_t a = A.C[i];
         const i64 dl = A.delta[i];
+        const int gr = graph_of(A, i);
+        const i64 tw = tw_of(A, gr);
+        if (frozen(A, gr)) {  // a frozen row stays; its first chunk records that
+            if (q == 0 && threadIdx.x == 0) A.Cnext[i] = a;
+            continue;
+        }
         i64 loop = 0;
         for (int64_t k0 = cb + threadIdx.x; k0 < ce; k0 += (int64_t)kUnroll * kHugeBlock) {
             int32_t j[kUnroll];
@@ -608,15 +701,19 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
                 const i64 e = (i64)vals[s];
                 keys[s] = -1;
                 vals[s] = 0;
-                consider<GT>(k2, e, a, dl, A.tw, A.deg, gbest, best, e_a);
+                consider<GT>(k2, e, a, dl, tw, A.deg, gbest, best, e_a);
             }
             block_argmax(gbest, best, e_a, loop);
             if (threadIdx.x == 0) {
                 const int32_t target =
-                    choose_target<GT>(a, best, gbest, e_a, dl, A.tw, A.deg, A.size);
+                    choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
                 A.Cnext[i] = target;
-                moved += target != a;
-                internal += (u64)(e_a + loop);
+                if (!A.vg) {
+                    moved += target != a;
+                    internal += (u64)(e_a + loop);
+                } else {
+                    row_stats(A.st, gr, e_a + loop, target != a);
+                }
                 cand += (u64)m;
             }
         } else {
@@ -654,16 +751,20 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
                     const i64 e = (i64)__ldcg(gv + s);
                     gk[s] = -1;
                     gv[s] = 0;
-                    consider<GT>(k2, e, a, dl, A.tw, A.deg, gbest, best, e_a);
+                    consider<GT>(k2, e, a, dl, tw, A.deg, gbest, best, e_a);
                 }
                 block_argmax(gbest, best, e_a, lz);
                 if (threadIdx.x == 0) {
                     const i64 lp = (i64)__ldcg(&B.gloop[b]);
                     const int32_t target =
-                        choose_target<GT>(a, best, gbest, e_a, dl, A.tw, A.deg, A.size);
+                        choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
                     A.Cnext[i] = target;
-                    moved += target != a;
-                    internal += (u64)(e_a + lp);
+                    if (!A.vg) {
+                        moved += target != a;
+                        internal += (u64)(e_a + lp);
+                    } else {
+                        row_stats(A.st, gr, e_a + lp, target != a);
+                    }
                     cand += (u64)gm;
                     B.gcnt[b] = 0;
                     B.gdone[b] = 0;
@@ -736,10 +837,11 @@ static int launch_cluster_kernel(K kernel, size_t smem, int nrows, cudaStream_t 
 template <typename WT, typename GT, typename VT>
 static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw,
                       SweepStats *stats, unsigned *err, cudaStream_t s, const LaunchCfg &lc,
-                      SweepTimers *tm)
+                      SweepTimers *tm, const BatchCtx &bc)
 {
-    MoveArgs<WT> A{g.n, g.rp, g.col, (const WT *)g.w, st.C, st.deg, st.size, st.delta,
-                   tw, st.Cnext, stats, err};
+    MoveArgs<WT> A{g.n,   g.rp,     g.col,  (const WT *)g.w, st.C,  st.deg,  st.size,
+                   st.delta, tw,    st.Cnext, stats,         err,   bc.vg,   bc.gtw,
+                   bc.gctl};
     const bool timed = tm && tm->on;
     int launched = 0;
     for (int bin = 0; bin < kNumBins; bin++) {
@@ -861,21 +963,21 @@ size_t shared_table_bytes(int log2cap, bool narrow)
 
 int launch_sweep(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, bool wide,
                  bool narrow, SweepStats *stats, unsigned *err, cudaStream_t s,
-                 const LaunchCfg &lc, SweepTimers *tm)
+                 const LaunchCfg &lc, SweepTimers *tm, const BatchCtx &bc)
 {
     typedef unsigned int u32;
     if (g.wbytes == 4) {
         if (wide)
-            return narrow ? sweep_impl<int32_t, i128, u32>(g, st, b, tw, stats, err, s, lc, tm)
-                          : sweep_impl<int32_t, i128, u64>(g, st, b, tw, stats, err, s, lc, tm);
-        return narrow ? sweep_impl<int32_t, i64, u32>(g, st, b, tw, stats, err, s, lc, tm)
-                      : sweep_impl<int32_t, i64, u64>(g, st, b, tw, stats, err, s, lc, tm);
+            return narrow ? sweep_impl<int32_t, i128, u32>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                          : sweep_impl<int32_t, i128, u64>(g, st, b, tw, stats, err, s, lc, tm, bc);
+        return narrow ? sweep_impl<int32_t, i64, u32>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                      : sweep_impl<int32_t, i64, u64>(g, st, b, tw, stats, err, s, lc, tm, bc);
     }
     if (wide)
-        return narrow ? sweep_impl<i64, i128, u32>(g, st, b, tw, stats, err, s, lc, tm)
-                      : sweep_impl<i64, i128, u64>(g, st, b, tw, stats, err, s, lc, tm);
-    return narrow ? sweep_impl<i64, i64, u32>(g, st, b, tw, stats, err, s, lc, tm)
-                  : sweep_impl<i64, i64, u64>(g, st, b, tw, stats, err, s, lc, tm);
+        return narrow ? sweep_impl<i64, i128, u32>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                      : sweep_impl<i64, i128, u64>(g, st, b, tw, stats, err, s, lc, tm, bc);
+    return narrow ? sweep_impl<i64, i64, u32>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                  : sweep_impl<i64, i64, u64>(g, st, b, tw, stats, err, s, lc, tm, bc);
 }
 
 }  // namespace lv

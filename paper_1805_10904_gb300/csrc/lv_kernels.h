@@ -95,6 +95,14 @@ inline int cta_log2cap(const Bins &b, int bin)
     return l;
 }
 
+// Graph context of a batch of graphs stored as one disjoint union (nullptr pointers for a
+// single graph): the graph of every vertex, every graph's 2W and phase controller.
+struct BatchCtx {
+    const int32_t *vg = nullptr;
+    const i64 *gtw = nullptr;
+    const LevelCtl *gctl = nullptr;
+};
+
 struct LaunchCfg {
     int num_sms = 152;
     int max_blocks = 152 * 8;  // persistent grid cap for grid-stride kernels
@@ -112,9 +120,11 @@ int launch_validate_rowptr(const int64_t *rp, int64_t n, unsigned *err, cudaStre
                            const LaunchCfg &lc);
 int launch_fill_ones(int32_t *w, int64_t nnz, cudaStream_t s, const LaunchCfg &lc);
 // Weighted degrees and 2W with column / weight checks, one thread, warp or CTA per row
-// according to the row's degree bin (bins must have been filled for g).
-int launch_row_sums(const DevGraph &g, const Bins &b, i64 *delta, u64 *tw, unsigned *err,
-                    cudaStream_t s, const LaunchCfg &lc);
+// according to the row's degree bin (bins must have been filled for g).  With vg set (a
+// batch), 2W is summed per graph into tw[vg[i]] and a column must lie in its row's graph
+// [gptr[g], gptr[g+1]); otherwise tw[0] gets the total and columns lie in [0, n).
+int launch_row_sums(const DevGraph &g, const Bins &b, const int32_t *vg, const int64_t *gptr,
+                    i64 *delta, u64 *tw, unsigned *err, cudaStream_t s, const LaunchCfg &lc);
 int launch_check_symmetry(const DevGraph &g, unsigned *err, cudaStream_t s, const LaunchCfg &lc);
 int launch_init_state(int64_t n, const PhaseState &st, cudaStream_t s, const LaunchCfg &lc);
 int launch_vertex_following(const DevGraph &g, const PhaseState &st, cudaStream_t s,
@@ -126,13 +136,29 @@ int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg 
 int launch_big_prep(const DevGraph &g, Bins &b, int64_t *scratch64, int32_t *scratch32,
                     cudaStream_t s, const LaunchCfg &lc);
 int launch_big_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc);
-int launch_decide(SweepStats *st, LevelCtl *ctl, i64 *tr_moved, i64 *tr_qn, u64 *cand_total,
-                  cudaStream_t s);
-int launch_apply(int64_t n, const PhaseState &st, const LevelCtl *ctl, cudaStream_t s,
-                 const LaunchCfg &lc);
-int launch_renumber(int64_t n, const int32_t *size, int32_t *new_id, int32_t *scratch,
-                    cudaStream_t s);
-int launch_compose(int64_t n0, const int32_t *prev, const int32_t *C, const int32_t *new_id,
+// Phase controllers of G graphs (one thread each): trace entry t of graph g at t * G + g;
+// *ndone counts the graphs whose phase has stopped.
+int launch_decide(SweepStats *st, LevelCtl *ctl, int G, i64 *tr_moved, i64 *tr_qn,
+                  u64 *cand_total, int *ndone, cudaStream_t s);
+int launch_apply(int64_t n, const PhaseState &st, const LevelCtl *ctl, const int32_t *vg,
+                 cudaStream_t s, const LaunchCfg &lc);
+// new_id[c] = rank of c among used labels (size[c] > 0, and keep[vg[c]] when given).
+int launch_renumber(int64_t n, const int32_t *size, const int32_t *vg, const int32_t *keep,
+                    int32_t *new_id, int32_t *scratch, cudaStream_t s);
+// out[i] = a[idx[i]] for i < cnt (small gathers of per-graph offsets).
+int launch_gather64(const int64_t *a, const int64_t *idx, int cnt, int64_t *out, cudaStream_t s);
+int launch_gather_ids(const int32_t *a, const int64_t *idx, int cnt, int64_t *out, cudaStream_t s);
+// vg[v] = graph of vertex v from the vertex offsets gptr[0..G] of a batch.
+int launch_graph_ids(int64_t n, const int64_t *gptr, int G, int32_t *vg, cudaStream_t s,
+                     const LaunchCfg &lc);
+// Labels of the original vertices.  For every v (graph g = vg0[v], 0 when vg0 is null) with
+// rec[g] (all when rec is null): m = map_in[v] (v when map_in is null) is v's vertex at this
+// level, out[v] = new_id1[C[m]] - base1[g] (base1 null: 0), and, when map_out is given and
+// keep[g] (all when keep is null), map_out[v] = new_id2[C[m]] (v's vertex at the next level).
+// map_in and map_out may be the same array.
+int launch_compose(int64_t n0, const int32_t *vg0, const int32_t *rec, const int32_t *keep,
+                   const int32_t *map_in, int32_t *map_out, const int32_t *C,
+                   const int32_t *new_id1, const int64_t *base1, const int32_t *new_id2,
                    int32_t *out, cudaStream_t s, const LaunchCfg &lc);
 
 // ---- k_move.cu: one synchronous sweep (Algorithm 1 body) over all bins
@@ -143,7 +169,7 @@ struct SweepTimers {
 // narrow: tables hold 32-bit sums (valid when 2W < 2^32); wide: int128 gains.
 int launch_sweep(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, bool wide,
                  bool narrow, SweepStats *stats, unsigned *err, cudaStream_t s,
-                 const LaunchCfg &lc, SweepTimers *tm);
+                 const LaunchCfg &lc, SweepTimers *tm, const BatchCtx &bc);
 
 // ---- k_coarsen.cu: graph induction (Sec. 5.1.2), renumbered labels new_id[C[u]]
 struct CoarsenBufs {
@@ -161,8 +187,12 @@ struct CoarsenBufs {
 };
 // Stage 1: community sizes, next-level delta, member lists, flattened offsets, and the
 // count pass of the community bins (by entries; rows of bins 0..2 all go to bin 2).
+// Only communities of graphs with keep[vg[c]] (all when vg is nullptr) enter the next
+// level; vg_next receives the graph of every next-level vertex (when vg is set), and
+// n_keep is the number of vertices of the kept graphs.
 int launch_coarsen_stage1(const DevGraph &g, const PhaseState &st, const int32_t *new_id,
-                          int64_t k, i64 *delta_next, CoarsenBufs &cb, Bins &bins,
+                          int64_t k, int64_t n_keep, const int32_t *vg, const int32_t *keep,
+                          int32_t *vg_next, i64 *delta_next, CoarsenBufs &cb, Bins &bins,
                           cudaStream_t s, const LaunchCfg &lc);
 // Fill pass of the community bins (after the host set bins.off from the counts).
 int launch_coarsen_binfill(int64_t k, CoarsenBufs &cb, Bins &bins, cudaStream_t s,

@@ -91,6 +91,7 @@ def load():
     lib.louvain_last_error.argtypes = [P]
     lib.louvain_last_error.restype = ctypes.c_char_p
     lib.louvain_run.argtypes = [P, i64, P, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
+    lib.louvain_run_batch.argtypes = [P, i32, P, P, P, P, P, ctypes.c_int, P, P]
     lib.louvain_result_num_levels.argtypes = [P]
     lib.louvain_result_num_vertices.argtypes = [P]
     lib.louvain_result_num_vertices.restype = i64
@@ -342,3 +343,57 @@ class Louvain:
         if rc != OK:
             raise LouvainError(rc, self.last_error())
         return Result(self._lib, out, self)
+
+    def run_batch(self, graph_vptr, row_ptr, col_idx, weights=None, graph_eptr=None,
+                  stream: Optional[int] = None) -> List[Result]:
+        """louvain_run_batch: one result per graph of a stacked block-diagonal CSR (graph g
+        owns vertices graph_vptr[g] .. graph_vptr[g+1]-1; column ids are global).
+        graph_vptr / graph_eptr are host arrays; the CSR arrays as in run()."""
+        gv = np.ascontiguousarray(np.asarray(graph_vptr, dtype=np.int64))
+        ge = None if graph_eptr is None else np.ascontiguousarray(
+            np.asarray(graph_eptr, dtype=np.int64))
+        G = int(gv.shape[0]) - 1
+        if G < 1:
+            raise ValueError("graph_vptr needs at least two entries")
+        rp, k1, keep1 = _ptr_of(row_ptr)
+        col, k2, keep2 = _ptr_of(col_idx)
+        w, k3, keep3 = _ptr_of(weights)
+        kinds = {k for k in (k1, k2, k3) if k is not None}
+        if len(kinds) != 1:
+            raise ValueError("row_ptr, col_idx and weights must all be on the host or all on the device")
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(self.device).cuda_stream
+            except Exception:
+                stream = 0
+        outs = (ctypes.c_void_p * G)()
+        rc = self._lib.louvain_run_batch(self._h, G, gv.ctypes.data,
+                                         None if ge is None else ge.ctypes.data, rp, col, w,
+                                         kinds.pop(), ctypes.c_void_p(stream), outs)
+        if rc != OK:
+            raise LouvainError(rc, self.last_error())
+        return [Result(self._lib, ctypes.c_void_p(outs[g]), self) for g in range(G)]
+
+
+def stack_graphs(graphs):
+    """Stack graphs given as (row_ptr, col_idx, weights) numpy arrays into the block-diagonal
+    CSR of louvain_run_batch: returns (graph_vptr, graph_eptr, row_ptr, col_idx, weights).
+    Column ids are shifted to global ids; weights None means all 1."""
+    vptr = [0]
+    eptr = [0]
+    rps, cols, ws = [], [], []
+    for rp, col, w in graphs:
+        rp = np.asarray(rp, np.int64)
+        col = np.asarray(col, np.int32)
+        n = rp.shape[0] - 1
+        nnz = int(rp[-1])
+        rps.append(rp[1:] + eptr[-1])
+        cols.append(col[:nnz] + np.int32(vptr[-1]))
+        ws.append(np.ones(nnz, np.int32) if w is None else np.asarray(w, np.int32)[:nnz])
+        vptr.append(vptr[-1] + n)
+        eptr.append(eptr[-1] + nnz)
+    row_ptr = np.concatenate([np.zeros(1, np.int64)] + rps).astype(np.int64)
+    col_idx = np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32)
+    weights = np.concatenate(ws).astype(np.int32) if ws else np.zeros(0, np.int32)
+    return (np.asarray(vptr, np.int64), np.asarray(eptr, np.int64), row_ptr, col_idx, weights)

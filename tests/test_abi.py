@@ -76,6 +76,26 @@ def test_null_handle_calls_are_safe(lib):
     lib.louvain_result_free(None)
     assert lib.louvain_result_num_levels(None) == 0
     assert lib.louvain_run(None, 0, None, None, None, 0, None, None) == 1
+    assert lib.louvain_run_batch(None, 1, None, None, None, None, None, 0, None, None) == 1
+
+
+def test_stack_graphs_builds_block_diagonal_csr():
+    import numpy as np
+    import graphgen as gg
+    from paper_1805_10904_gb300 import stack_graphs
+    graphs = [gg.path(4, 2), gg.from_edges(0, []), gg.star(3), gg.from_edges(2, [(1, 1, 5)])]
+    vptr, eptr, rp, col, w = stack_graphs([(g.rp, g.col, g.w) for g in graphs])
+    assert list(vptr) == [0, 4, 4, 8, 10]
+    assert list(eptr) == [0, 6, 6, 12, 13]
+    assert rp.dtype == np.int64 and col.dtype == np.int32 and w.dtype == np.int32
+    whole = gg.Graph(rp, col, w, "stacked")
+    gg.check_csr(whole)
+    for k, g in enumerate(graphs):
+        v0, v1 = vptr[k], vptr[k + 1]
+        sub = rp[v0:v1 + 1] - rp[v0]
+        assert np.array_equal(sub, g.rp)
+        assert np.array_equal(col[rp[v0]:rp[v1]] - v0, g.col)
+        assert np.array_equal(w[rp[v0]:rp[v1]], g.w)
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
