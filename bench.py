@@ -184,7 +184,7 @@ def kernel_traffic(kernel_name: str):
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_1805_10904_gb300", "csrc", "k_move.cu")
+    src = os.path.join(ROOT, "paper_1805_10904_gb300", "csrc", "k_move_impl.cuh")
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
     entry = rec.get("kernels", {}).get(kernel_name)

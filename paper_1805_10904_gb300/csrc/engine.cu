@@ -441,11 +441,12 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         return pr;
     };
     // degree bins of graph G: count, then fill the list grouped by bin
-    auto make_bins = [&](const DevGraph &gr, const Bins &pr) {
+    auto make_bins = [&](const DevGraph &gr, const Bins &pr, const int32_t *vg = nullptr,
+                         const LevelCtl *gctl = nullptr) {
         Bins bins = pr;
         bins.list = lists.p;
         bins.counts = &d_sc->bin_counts[0];
-        kernels += launch_bin_count(gr, bins, s, lc);
+        kernels += launch_bin_count(gr, bins, s, lc, vg, gctl);
         sync_scalars();
         bins.off[0] = bins.off[1] = 0;
         for (int b = 0; b < kNumBins; b++) {
@@ -453,7 +454,7 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
             memcpy(&bins.entries[b], &h->pinned->bin_counts[16 + 2 * b], sizeof(int64_t));
             if (b >= 1) bins.off[b + 1] = bins.off[b] + bins.nlist[b];
         }
-        kernels += launch_bin_fill(gr, bins, s, lc);
+        kernels += launch_bin_fill(gr, bins, s, lc, vg, gctl);
         return bins;
     };
     const Bins proto_narrow = make_proto(true);
@@ -670,7 +671,24 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
         CK(cudaMemsetAsync(&d_sc->cand_total[0], 0, sizeof(u64) * 16, s));
 
         // sweeps (Algorithm 1); one host read of the controllers' count per sweep
+        // algorithmic bytes of one sweep over the current bins (formula in louvain.h)
+        auto account_sweep = [&](const Bins &bb) {
+            const double per_entry = 8.0 + (double)G.wbytes;
+            for (int b = 0; b < kNumBins; b++) {
+                double kb = (double)bb.entries[b] * per_entry;
+                kb += b == 0 ? (double)n * 16.0 + (double)bb.nlist[0] * 24.0
+                             : (double)bb.nlist[b] * 36.0;
+                bytes_kernel[b] += kb;
+                alg_bytes += kb;
+                const int64_t rows = b == 0 ? n : bb.nlist[b];
+                for (int g = 0; g < NG; g++) {
+                    out[g]->bin_rows[b] += rows;
+                    out[g]->bin_entries[b] += bb.entries[b];
+                }
+            }
+        };
         int sweeps = 0;
+        int ndone_binned = ninactive;
         for (;;) {
             kernels += launch_sweep(G, st, bins, TW, wide, narrow, st_dev, &d_sc->err, s, lc,
                                     &tm, bc);
@@ -678,6 +696,7 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
                                      &d_sc->cand_total[0], &d_sc->ndone, s);
             kernels += launch_apply(n, st, ctl_dev, bc.vg, s, lc);
             sweeps++;
+            account_sweep(bins);
             sync_scalars();
             for (int b = 0; b < kNumBins; b++) {
                 if (tm.on) {
@@ -688,9 +707,16 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
                 launches_kernel[b] +=
                     b == 0 ? 1 : (b == kChunkedBin ? bins.nchunks > 0 : bins.nlist[b] > 0);
             }
-            if (h->pinned->ndone >= NG) break;
+            const int ndone = h->pinned->ndone;
+            if (ndone >= NG) break;
             if (sweeps > cfg.max_iters + 2)
                 throw LvErr{LOUVAIN_ERR_INTERNAL, "phase controller did not stop"};
+            if (batch && ndone > ndone_binned) {
+                // some graphs stopped: bin again without their rows
+                bins = make_bins(G, proto, d_vg.p, d_ctls.p);
+                prep_huge(bins, false, 0, nullptr);
+                ndone_binned = ndone;
+            }
         }
         sweeps_launched += sweeps;
         if (batch) {
@@ -727,22 +753,11 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
             visits[g] += (int64_t)it * nnz_g;
             edge_visits += (int64_t)it * nnz_g;
         }
-        // algorithmic bytes of the sweeps run in this phase (formula in louvain.h)
-        {
-            const double per_entry = 8.0 + (double)G.wbytes;
-            for (int b = 0; b < kNumBins; b++) {
-                double kb = (double)bins.entries[b] * per_entry;
-                kb += b == 0 ? (double)n * 16.0 + (double)bins.nlist[0] * 24.0
-                             : (double)bins.nlist[b] * 36.0;
-                const double tot = kb * sweeps + 8.0 * (double)cand_level[b];
-                bytes_kernel[b] += tot;
-                for (int g = 0; g < NG; g++) {
-                    out[g]->bin_rows[b] += (int64_t)(b == 0 ? n : bins.nlist[b]) * sweeps;
-                    out[g]->bin_entries[b] += bins.entries[b] * sweeps;
-                }
-                alg_bytes += tot;
-                cand_all += cand_level[b];
-            }
+        // candidate reads (8 bytes each) of the sweeps of this phase
+        for (int b = 0; b < kNumBins; b++) {
+            bytes_kernel[b] += 8.0 * (double)cand_level[b];
+            alg_bytes += 8.0 * (double)cand_level[b];
+            cand_all += cand_level[b];
         }
 
         // renumber (Sec. 5.1.2) -- labels of used communities in increasing order; labels

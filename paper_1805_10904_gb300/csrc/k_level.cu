@@ -337,6 +337,8 @@ struct BinArgs {
     int64_t upper[kNumBins - 1];
     int64_t off[kNumBins + 1];
     int32_t *list;
+    const int32_t *vg;      // batch: graph of every vertex (nullptr for one graph)
+    const LevelCtl *gctl;   // batch: rows of graphs whose phase stopped are left out
 };
 
 __device__ __forceinline__ int bin_of(int64_t d, const int64_t *upper)
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, Bi
         const int64_t i = i0 + threadIdx.x;
         int bin = -1;
         int64_t d = 0;
-        if (i < n) {
+        if (i < n && !(ba.vg && ba.gctl[ba.vg[i]].done)) {
             d = rp[i + 1] - rp[i];
             bin = bin_of(d, ba.upper);
         }
@@ -389,30 +391,34 @@ __global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, Bi
     }
 }
 
-static BinArgs bin_args(const Bins &b)
+static BinArgs bin_args(const Bins &b, const int32_t *vg, const LevelCtl *gctl)
 {
     BinArgs ba;
+    ba.vg = vg;
+    ba.gctl = gctl;
     for (int t = 0; t < kNumBins - 1; t++) ba.upper[t] = b.upper[t];
     for (int t = 0; t <= kNumBins; t++) ba.off[t] = b.off[t];
     ba.list = b.list;
     return ba;
 }
 
-int launch_bin_count(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc)
+int launch_bin_count(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc,
+                     const int32_t *vg, const LevelCtl *gctl)
 {
     cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * (16 + 2 * kNumBins), s);
     if (g.n == 0) return 0;
-    k_bin<false><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(g.n, g.rp, bin_args(b),
-                                                                        b.counts);
+    k_bin<false><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        g.n, g.rp, bin_args(b, vg, gctl), b.counts);
     return 1;
 }
 
-int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc)
+int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc,
+                    const int32_t *vg, const LevelCtl *gctl)
 {
     cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * 16, s);
     if (g.n == 0) return 0;
-    k_bin<true><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(g.n, g.rp, bin_args(b),
-                                                                       b.counts);
+    k_bin<true><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        g.n, g.rp, bin_args(b, vg, gctl), b.counts);
     return 1;
 }
 

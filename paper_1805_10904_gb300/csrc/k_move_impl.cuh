@@ -1,0 +1,949 @@
+// k_move_impl.cuh -- one synchronous local-moving sweep (arXiv 1805.10904, Algorithm 1 body).
+//
+// For every vertex i, using only the previous iteration's state (C, deg_C, size_C):
+//   e_{i->c} = sum of the weights from i into community c over non-loop entries (Eq. 1;
+//              the loop is left out of the move decision as in Sec. 5.1.2),
+//   G_c      = 2W * e_{i->c} - delta_i * deg_c          for c != C(i),
+//   G_stay   = 2W * e_{i->C(i)} - delta_i * (deg_{C(i)} - delta_i),
+// which are the Eq. 4 gains scaled by (2W)^2 / 2 with the term dropped from Eq. 4 as
+// printed restored; target = argmax G_c with ties to the smaller label (Eq. 5,
+// Sec. 3.1.2); i moves iff G_target > G_stay, except that a singleton never moves into
+// a singleton community with a larger label (Sec. 3.1.1).
+//
+// The same pass also accumulates, for the state it reads, sum_i e_{i->C(i)} with loops
+// (the first term of Eq. 3) and sum_c deg_c^2, so the phase controller gets the exact
+// Qn = (2W)^2 Q of that state without a separate pass over the edges.
+//
+// Work is binned by row length (Sec. 6.3 suggests grouping vertices by degree):
+//   bin 0    one thread per vertex, neighbours aggregated in registers (dense over all i),
+//   bin 1-2  8-lane groups / whole warps, one shared-memory hash table per group,
+//   bin 3-5  one CTA per row with a shared-memory table sized for the bin (up to 16K slots),
+//   bin 6-9  a thread-block cluster of 2-16 CTAs per row; the table is partitioned over the
+//            cluster's distributed shared memory by key hash (inserts are DSMEM atomics),
+//            each CTA scans its own part, and rank 0 combines the partial argmaxes,
+//   bin 10   CTA-sized chunks of a row; a row spanning several chunks merges its chunk
+//            tables into a global-memory table and the last chunk to finish decides.
+// Table values are 32-bit when 2W < 2^32 (every e_{i->c} <= delta_i <= 2W fits), else 64-bit.
+#pragma once
+#include <climits>
+
+#include <cooperative_groups.h>
+
+#include "lv_common.cuh"
+#include "lv_kernels.h"
+
+namespace lv {
+
+constexpr int kSmallMax = 8;  // register slots of the thread-per-vertex kernel
+constexpr int kUnroll = 4;    // independent row entries in flight per thread
+
+template <typename WT>
+struct MoveArgs {
+    int64_t n;
+    const int64_t *rp;
+    const int32_t *col;
+    const WT *w;
+    const int32_t *C;
+    const i64 *deg;
+    const int32_t *size;
+    const i64 *delta;
+    i64 tw;               // 2W of the graph (one graph)
+    int32_t *Cnext;
+    SweepStats *st;       // per graph (one entry for one graph)
+    unsigned *err;
+    const int32_t *vg;    // graph of every vertex in a batch of graphs, nullptr for one graph
+    const i64 *gtw;       // 2W of every graph of the batch
+    const LevelCtl *gctl; // phase controller of every graph; rows of finished graphs are frozen
+};
+
+// Graph context of vertex i: its graph, that graph's 2W, and whether its phase has stopped.
+// BT (a batch) is a template flag, so the one-graph kernels carry none of this.
+template <bool BT, typename WT>
+__device__ __forceinline__ int graph_of(const MoveArgs<WT> &A, int64_t i)
+{
+    if constexpr (BT) return A.vg[i];
+    else return 0;
+}
+template <bool BT, typename WT>
+__device__ __forceinline__ i64 tw_of(const MoveArgs<WT> &A, int g)
+{
+    if constexpr (BT) return A.gtw[g];
+    else return A.tw;
+}
+template <bool BT, typename WT>
+__device__ __forceinline__ bool frozen(const MoveArgs<WT> &A, int g)
+{
+    if constexpr (BT) return *(volatile const int *)&A.gctl[g].done;
+    else return false;
+}
+
+// Per-row statistics of a batch of graphs go straight to the row's graph.
+__device__ __forceinline__ void row_stats(SweepStats *st, int g, i64 internal, bool moved)
+{
+    if (internal) atomicAdd(&st[g].internal, (u64)internal);
+    if (moved) atomicAdd(&st[g].moved, 1ull);
+}
+
+// Decision of Algorithm 1 for vertex i in community a (Eq. 4-5, Sec. 3.1).
+template <typename GT>
+__device__ __forceinline__ int32_t choose_target(int32_t a, int32_t best, GT gbest, i64 e_a,
+                                                 i64 dl, i64 tw, const i64 *deg,
+                                                 const int32_t *size)
+{
+    if (best == INT_MAX) return a;
+    const GT gstay = (GT)tw * (GT)e_a - (GT)dl * (GT)(deg[a] - dl);
+    if (!(gbest > gstay)) return a;
+    if (size[a] == 1 && size[best] == 1 && best > a) return a;  // singlet minimum-label rule
+    return best;
+}
+
+// One candidate community c with weight e from vertex (a, dl): updates the running argmax
+// or records e_{i->a}.
+template <typename GT>
+__device__ __forceinline__ void consider(int32_t c, i64 e, int32_t a, i64 dl, i64 tw,
+                                         const i64 *deg, GT &gbest, int32_t &best, i64 &e_a)
+{
+    if (c == a) {
+        e_a = e;
+        return;
+    }
+    const GT g = (GT)tw * (GT)e - (GT)dl * (GT)deg[c];
+    if (better(g, c, gbest, best)) {
+        gbest = g;
+        best = c;
+    }
+}
+
+// CTA-wide argmax and sums; results valid in thread 0.  Warp 0 combines the per-warp
+// partials with shuffles.  Ends with a barrier.
+template <typename GT>
+__device__ __forceinline__ void block_argmax(GT &g, int32_t &c, i64 &e_a, i64 &loop)
+{
+    __shared__ GT s_g[32];
+    __shared__ int32_t s_c[32];
+    __shared__ i64 s_e[32], s_l[32];
+    argmax_reduce(g, c, 32);
+    e_a = sum_reduce(e_a, 32);
+    loop = sum_reduce(loop, 32);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_g[warp] = g;
+        s_c[warp] = c;
+        s_e[warp] = e_a;
+        s_l[warp] = loop;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        g = lane < nw ? s_g[lane] : gain_min<GT>();
+        c = lane < nw ? s_c[lane] : INT_MAX;
+        e_a = lane < nw ? s_e[lane] : 0;
+        loop = lane < nw ? s_l[lane] : 0;
+        argmax_reduce(g, c, 32);
+        e_a = sum_reduce(e_a, 32);
+        loop = sum_reduce(loop, 32);
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ bin 0
+// Dense over every vertex: also adds deg[i]^2 of label i to sum_c deg_c^2.  The loop is
+// uniform across each warp so a batch of graphs can combine a warp's statistics when all
+// its vertices belong to one graph.
+template <typename WT, typename GT, bool BT>
+__global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small_max)
+{
+    u64 internal = 0, moved = 0, cand = 0;
+    u128 sq = 0;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < A.n;
+         i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        u64 v_int = 0, v_mov = 0;
+        u128 v_sq = 0;
+        int g = -1;
+        if (i < A.n) {
+            g = graph_of<BT>(A, i);
+            const i64 dg = A.deg[i];
+            v_sq = (u128)(u64)dg * (u64)dg;
+            const int64_t rb = A.rp[i];
+            const int64_t d = A.rp[i + 1] - rb;
+            const bool fz = frozen<BT>(A, g);
+            if (d <= small_max && !fz) {
+                const i64 tw = tw_of<BT>(A, g);
+                const int32_t a = A.C[i];
+                int32_t lab[kSmallMax];
+                i64 wt[kSmallMax];
+#pragma unroll
+                for (int t = 0; t < kSmallMax; t++) {
+                    lab[t] = -1;
+                    wt[t] = 0;
+                    if (t < d) {
+                        lab[t] = A.col[rb + t];
+                        wt[t] = (i64)A.w[rb + t];
+                    }
+                }
+                i64 loop = 0;
+#pragma unroll
+                for (int t = 0; t < kSmallMax; t++) {
+                    if (t < d) {
+                        if (lab[t] == (int32_t)i) {
+                            loop += wt[t];
+                            lab[t] = -1;
+                        } else {
+                            lab[t] = A.C[lab[t]];
+                        }
+                    }
+                }
+                const i64 dl = A.delta[i];
+                i64 e_a = 0;
+                GT gbest = gain_min<GT>();
+                int32_t best = INT_MAX;
+                int m = 0;
+#pragma unroll
+                for (int t = 0; t < kSmallMax; t++) {
+                    const int32_t c = lab[t];
+                    bool first = c >= 0;
+#pragma unroll
+                    for (int u = 0; u < t; u++) first = first && (lab[u] != c);
+                    if (first) {
+                        i64 e = 0;
+#pragma unroll
+                        for (int u = t; u < kSmallMax; u++) e += (lab[u] == c) ? wt[u] : 0;
+                        m++;
+                        consider<GT>(c, e, a, dl, tw, A.deg, gbest, best, e_a);
+                    }
+                }
+                const int32_t target = choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
+                A.Cnext[i] = target;
+                v_mov = target != a;
+                v_int = (u64)(e_a + loop);
+                cand += (u64)m;
+            } else if (d <= small_max) {
+                A.Cnext[i] = A.C[i];  // frozen graph: nothing moves
+            }
+        }
+        if constexpr (!BT) {
+            internal += v_int;
+            moved += v_mov;
+            sq += v_sq;
+            continue;
+        }
+        // batch of graphs: one atomic per warp when the warp's vertices share a graph
+        const int g0 = __shfl_sync(0xffffffffu, g, 0);
+        if (__all_sync(0xffffffffu, g == g0 || g < 0)) {
+            const u64 wi = sum_reduce(v_int, 32), wm = sum_reduce(v_mov, 32);
+            const u128 ws = sum_reduce(v_sq, 32);
+            if ((threadIdx.x & 31) == 0 && g0 >= 0) {
+                if (wi) atomicAdd(&A.st[g0].internal, wi);
+                if (wm) atomicAdd(&A.st[g0].moved, wm);
+                if (ws) atomic_add_u128(&A.st[g0].sq_lo, &A.st[g0].sq_hi, ws);
+            }
+        } else if (g >= 0) {
+            if (v_int) atomicAdd(&A.st[g].internal, v_int);
+            if (v_mov) atomicAdd(&A.st[g].moved, v_mov);
+            if (v_sq) atomic_add_u128(&A.st[g].sq_lo, &A.st[g].sq_hi, v_sq);
+        }
+    }
+    block_flush_stats(A.st, 0, internal, moved, cand, sq);
+}
+
+// ------------------------------------------------------------------ bins 1-2
+// G lanes per vertex (G <= 32), each group with a 2^LOG2CAP-slot shared table.  The
+// outer loop is uniform across the block so every lane reaches the shuffles.
+template <int G, int LOG2CAP, typename WT, typename GT, typename VT, bool BT>
+__global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int32_t *verts,
+                                                       int nverts, int slot)
+{
+    constexpr int CAP = 1 << LOG2CAP;
+    constexpr int NG = kBlock / G;
+    __shared__ int s_keys[NG * CAP];
+    __shared__ VT s_vals[NG * CAP];
+    __shared__ int s_list[NG * CAP];
+    __shared__ int s_cnt[NG];
+    for (int s = threadIdx.x; s < NG * CAP; s += kBlock) {
+        s_keys[s] = -1;
+        s_vals[s] = 0;
+    }
+    if (threadIdx.x < NG) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    int *keys = s_keys + g * CAP;
+    VT *vals = s_vals + g * CAP;
+    int *list = s_list + g * CAP;
+    int *cnt = &s_cnt[g];
+    u64 internal = 0, moved = 0, cand = 0;
+    for (int base = blockIdx.x * NG; base < nverts; base += gridDim.x * NG) {
+        const int vi = base + g;
+        const bool valid = vi < nverts;
+        int32_t i = 0, a = 0;
+        int64_t rb = 0, re = 0;
+        i64 dl = 0, tw = 0;
+        int gr = 0;
+        bool fz = false;
+        if (valid) {
+            i = verts[vi];
+            gr = graph_of<BT>(A, i);
+            tw = tw_of<BT>(A, gr);
+            fz = frozen<BT>(A, gr);
+            rb = A.rp[i];
+            re = fz ? rb : A.rp[i + 1];  // a frozen row inserts nothing and stays
+            a = A.C[i];
+            dl = A.delta[i];
+        }
+        i64 loop = 0;
+        for (int64_t k = rb + lane; k < re; k += G) {
+            const int32_t j = A.col[k];
+            const i64 x = (i64)A.w[k];
+            if (j == i) loop += x;
+            else tbl_insert<false, VT>(keys, vals, list, cnt, LOG2CAP, A.C[j], (VT)x, A.err);
+        }
+        __syncwarp();
+        const int m = valid ? *(volatile int *)cnt : 0;
+        GT gbest = gain_min<GT>();
+        int32_t best = INT_MAX;
+        i64 e_a = 0;
+        for (int p = lane; p < m; p += G) {
+            const int s = list[p];
+            const int32_t c = keys[s];
+            const i64 e = (i64)vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+            consider<GT>(c, e, a, dl, tw, A.deg, gbest, best, e_a);
+        }
+        argmax_reduce(gbest, best, G);
+        e_a = sum_reduce(e_a, G);
+        loop = sum_reduce(loop, G);
+        if (lane == 0) {
+            if (valid) {
+                const int32_t target =
+                    choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
+                A.Cnext[i] = target;
+                if constexpr (!BT) {
+                    moved += target != a;
+                    internal += (u64)(e_a + loop);
+                } else if (!fz) {
+                    row_stats(A.st, gr, e_a + loop, target != a);
+                }
+                cand += (u64)m;
+            }
+            *cnt = 0;
+        }
+        __syncwarp();
+    }
+    block_flush_stats(A.st, slot, internal, moved, cand, 0);
+}
+
+// ------------------------------------------------------------------ bins 3-5
+// Table insert of one chunk entry (key -1 = loop or absent entry: nothing to insert).
+template <typename VT, typename Ins>
+__device__ __forceinline__ void chunk_insert(int32_t key, i64 x, Ins ins)
+{
+    if (key >= 0) ins(key, (VT)x);
+}
+
+// Loads of one chunk of a row: entries base + u * BLOCK, u < kUnroll, below re.
+template <int BLOCK, typename WT>
+__device__ __forceinline__ void load_chunk(const MoveArgs<WT> &A, int64_t base, int64_t re,
+                                           int32_t (&j)[kUnroll], i64 (&x)[kUnroll])
+{
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+        const int64_t k = base + (int64_t)u * BLOCK;
+        j[u] = -1;
+        x[u] = 0;
+        if (k < re) {
+            j[u] = A.col[k];
+            x[u] = (i64)A.w[k];
+        }
+    }
+}
+
+// Label gathers of a loaded chunk of row i: community of each non-loop entry, -1 otherwise.
+template <typename WT>
+__device__ __forceinline__ void gather_chunk(const MoveArgs<WT> &A, int32_t i,
+                                             const int32_t (&j)[kUnroll], int32_t (&c)[kUnroll])
+{
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+}
+
+// One CTA per row, table of 2^log2cap slots in dynamic shared memory (vals, keys, list).
+// Software pipeline over the CTA's rows: while row v finishes (barrier, candidate scan,
+// argmax), the next row's vertex id, entry range, first chunk of columns / weights and its
+// label gathers are already in flight, issued stage by stage so no load waits on another.
+template <int BLOCK, typename WT, typename GT, typename VT, bool BT>
+__global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_t *verts,
+                                                    int nverts, int log2cap, int slot)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int cap = 1 << log2cap;
+    VT *vals = (VT *)smem;
+    int *keys = (int *)(vals + cap);
+    int *list = keys + cap;
+    __shared__ int s_cnt;
+    for (int s = threadIdx.x; s < cap; s += BLOCK) {
+        keys[s] = -1;
+        vals[s] = 0;
+    }
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    auto ins = [&](int32_t key, VT val) {
+        tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, val, A.err);
+    };
+    u64 internal = 0, moved = 0, cand = 0;
+    // prologue: the first row completely prefetched
+    int v = blockIdx.x;
+    int32_t nx_i = -1;
+    int64_t nx_rb = 0, nx_re = 0;
+    if (v < nverts) {
+        nx_i = verts[v];
+        nx_rb = A.rp[nx_i];
+        nx_re = A.rp[nx_i + 1];
+    }
+    int32_t nj[kUnroll], nc[kUnroll];
+    i64 nw[kUnroll];
+    load_chunk<BLOCK>(A, nx_rb + threadIdx.x, nx_re, nj, nw);
+    gather_chunk(A, nx_i, nj, nc);
+    for (; v < nverts; v += gridDim.x) {
+        const int32_t i = nx_i;
+        const int64_t rb = nx_rb, re = nx_re;
+        // stage 1: next row's vertex id; this row's own community and degree
+        const int vn = v + gridDim.x;
+        const int32_t i_next = vn < nverts ? verts[vn] : -1;
+        const int32_t a = A.C[i];
+        const i64 dl = A.delta[i];
+        const int gr = graph_of<BT>(A, i);
+        const i64 tw = tw_of<BT>(A, gr);
+        const bool fz = frozen<BT>(A, gr);  // a frozen row inserts nothing and stays
+        // the prefetched first chunk, then the rest of the row
+        i64 loop = 0;
+        if (!fz) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (nj[u] == i) loop += nw[u];
+                chunk_insert<VT>(nc[u], nw[u], ins);
+            }
+        }
+        for (int64_t k0 = rb + threadIdx.x + (int64_t)kUnroll * BLOCK;
+             !fz && __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * BLOCK) {
+            int32_t j[kUnroll], c[kUnroll];
+            i64 x[kUnroll];
+            load_chunk<BLOCK>(A, k0, re, j, x);
+            gather_chunk(A, i, j, c);
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (j[u] == i) loop += x[u];
+                chunk_insert<VT>(c[u], x[u], ins);
+            }
+        }
+        // stage 2: next row's entry range; this row's community degree and size
+        int64_t rb_next = 0, re_next = 0;
+        if (i_next >= 0) {
+            rb_next = A.rp[i_next];
+            re_next = A.rp[i_next + 1];
+        }
+        const i64 deg_a = A.deg[a];
+        const int32_t size_a = A.size[a];
+        __syncthreads();
+        const int m = s_cnt;
+        // stage 3: next row's first chunk of columns and weights
+        load_chunk<BLOCK>(A, rb_next + threadIdx.x, re_next, nj, nw);
+        GT gbest = gain_min<GT>();
+        int32_t best = INT_MAX;
+        i64 e_a = 0;
+        for (int p = threadIdx.x; p < m; p += BLOCK) {
+            const int s = list[p];
+            const int32_t cc = keys[s];
+            const i64 e = (i64)vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+            consider<GT>(cc, e, a, dl, tw, A.deg, gbest, best, e_a);
+        }
+        // stage 4: next row's label gathers
+        gather_chunk(A, i_next, nj, nc);
+        block_argmax(gbest, best, e_a, loop);
+        if (threadIdx.x == 0) {
+            int32_t target = a;
+            if (best != INT_MAX) {
+                const GT gstay = (GT)tw * (GT)e_a - (GT)dl * (GT)(deg_a - dl);
+                if (gbest > gstay && !(size_a == 1 && best > a && A.size[best] == 1))
+                    target = best;
+            }
+            A.Cnext[i] = target;
+            if constexpr (!BT) {
+                moved += target != a;
+                internal += (u64)(e_a + loop);
+            } else if (!fz) {
+                row_stats(A.st, gr, e_a + loop, target != a);
+            }
+            cand += (u64)m;
+            s_cnt = 0;
+        }
+        nx_i = i_next;
+        nx_rb = rb_next;
+        nx_re = re_next;
+        __syncthreads();
+    }
+    block_flush_stats(A.st, slot, internal, moved, cand, 0);
+}
+
+// ------------------------------------------------------------------ bins 6-9
+namespace cg = cooperative_groups;
+
+template <int CL>
+struct Log2Of {
+    static constexpr int v = CL <= 1 ? 0 : 1 + Log2Of<CL / 2>::v;
+};
+template <>
+struct Log2Of<1> {
+    static constexpr int v = 0;
+};
+
+template <int CL, typename WT, typename GT, typename VT, bool BT>
+__global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int32_t *verts,
+                                                       int nverts, int log2cap, int slot)
+{
+    constexpr int BLOCK = 1024;
+    constexpr int LOG2CL = Log2Of<CL>::v;
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int cap = 1 << log2cap;
+    VT *vals = (VT *)smem;
+    int *keys = (int *)(vals + cap);
+    __shared__ GT p_g;
+    __shared__ int32_t p_c;
+    __shared__ i64 p_e, p_l, p_m;
+    for (int s = threadIdx.x; s < cap; s += BLOCK) {
+        keys[s] = -1;
+        vals[s] = 0;
+    }
+    cluster.sync();
+    const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
+    const int64_t stride = (int64_t)CL * BLOCK;
+    u64 internal = 0, moved = 0, cand = 0;
+    for (int v = cid; v < nverts; v += ncl) {
+        const int32_t i = verts[v];
+        const int gr = graph_of<BT>(A, i);
+        const i64 tw = tw_of<BT>(A, gr);
+        const bool fz = frozen<BT>(A, gr);  // a frozen row inserts nothing and stays
+        const int64_t rb = A.rp[i], re = fz ? rb : A.rp[i + 1];
+        i64 loop = 0;
+        auto cins = [&](int32_t key, VT val) {
+            cluster_insert<VT>(cluster, keys, vals, LOG2CL, log2cap, key, val, A.err);
+        };
+        for (int64_t k0 = rb + (int64_t)rank * BLOCK + threadIdx.x;
+             __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * stride) {
+            int32_t j[kUnroll];
+            i64 x[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const int64_t k = k0 + (int64_t)u * stride;
+                j[u] = -1;
+                x[u] = 0;
+                if (k < re) {
+                    j[u] = A.col[k];
+                    x[u] = (i64)A.w[k];
+                }
+            }
+            int32_t c[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (j[u] == i) loop += x[u];
+                chunk_insert<VT>(c[u], x[u], cins);
+            }
+        }
+        cluster.sync();  // every insert of this row has landed
+        const int32_t a = A.C[i];
+        const i64 dl = A.delta[i];
+        GT gbest = gain_min<GT>();
+        int32_t best = INT_MAX;
+        i64 e_a = 0, mloc = 0;
+        for (int s = threadIdx.x; s < cap; s += BLOCK) {
+            const int32_t cc = keys[s];
+            if (cc < 0) continue;
+            const i64 e = (i64)vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+            mloc++;
+            consider<GT>(cc, e, a, dl, tw, A.deg, gbest, best, e_a);
+        }
+        mloc = sum_reduce(mloc, 32);  // per-warp count, folded into the CTA sum below
+        block_argmax(gbest, best, e_a, loop);
+        __shared__ i64 s_mw[32];
+        if ((threadIdx.x & 31) == 0) s_mw[threadIdx.x >> 5] = mloc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            i64 m = 0;
+            for (int w = 0; w < BLOCK / 32; w++) m += s_mw[w];
+            p_g = gbest;
+            p_c = best;
+            p_e = e_a;
+            p_l = loop;
+            p_m = m;
+        }
+        cluster.sync();  // partial results of every CTA published
+        if (rank == 0 && threadIdx.x == 0) {
+            GT g = p_g;
+            int32_t c = p_c;
+            i64 ea = p_e, lp = p_l, mm = p_m;
+#pragma unroll 1
+            for (int r = 1; r < CL; r++) {
+                const GT g2 = *cluster.map_shared_rank(&p_g, r);
+                const int32_t c2 = *cluster.map_shared_rank(&p_c, r);
+                if (better(g2, c2, g, c)) {
+                    g = g2;
+                    c = c2;
+                }
+                ea += *cluster.map_shared_rank(&p_e, r);
+                lp += *cluster.map_shared_rank(&p_l, r);
+                mm += *cluster.map_shared_rank(&p_m, r);
+            }
+            const int32_t target = choose_target<GT>(a, c, g, ea, dl, tw, A.deg, A.size);
+            A.Cnext[i] = target;
+            if constexpr (!BT) {
+                moved += target != a;
+                internal += (u64)(ea + lp);
+            } else if (!fz) {
+                row_stats(A.st, gr, ea + lp, target != a);
+            }
+            cand += (u64)mm;
+        }
+        cluster.sync();  // partials read before the next row overwrites them
+    }
+    block_flush_stats(A.st, slot, internal, moved, cand, 0);
+}
+
+// ------------------------------------------------------------------ bin 10
+constexpr int kHugeBlock = 512;
+
+struct BigArgs {
+    const int32_t *bverts;
+    const int32_t *chunk_b;
+    const int32_t *chunk_first;
+    const int32_t *nch;
+    const int64_t *goff;
+    const int32_t *glog2;
+    int32_t *gcnt;
+    int32_t *gdone;
+    u64 *gloop;
+    int32_t *gkeys;
+    void *gvals;
+    int32_t *glist;
+    int chunk;
+    int nchunks;
+};
+
+template <typename WT, typename GT, typename VT, bool BT>
+__global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArgs B)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int log2cap = 31 - __clz(2 * B.chunk);  // 2 * chunk slots
+    const int cap = 1 << log2cap;
+    VT *vals = (VT *)smem;
+    int *keys = (int *)(vals + cap);
+    int *list = keys + cap;
+    __shared__ int s_cnt;
+    __shared__ int s_last;
+    for (int s = threadIdx.x; s < cap; s += kHugeBlock) {
+        keys[s] = -1;
+        vals[s] = 0;
+    }
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    u64 internal = 0, moved = 0, cand = 0;
+    for (int c = blockIdx.x; c < B.nchunks; c += gridDim.x) {
+        const int b = B.chunk_b[c];
+        const int32_t i = B.bverts[b];
+        const int q = c - B.chunk_first[b];
+        const int nch = B.nch[b];
+        const int64_t rb = A.rp[i], re = A.rp[i + 1];
+        const int64_t cb = rb + (int64_t)q * B.chunk;
+        const int64_t ce = min(re, cb + (int64_t)B.chunk);
+        const int32_t a = A.C[i];
+        const i64 dl = A.delta[i];
+        const int gr = graph_of<BT>(A, i);
+        const i64 tw = tw_of<BT>(A, gr);
+        if (frozen<BT>(A, gr)) {  // a frozen row stays; its first chunk records that
+            if (q == 0 && threadIdx.x == 0) A.Cnext[i] = a;
+            continue;
+        }
+        i64 loop = 0;
+        for (int64_t k0 = cb + threadIdx.x; k0 < ce; k0 += (int64_t)kUnroll * kHugeBlock) {
+            int32_t j[kUnroll];
+            i64 x[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const int64_t k = k0 + (int64_t)u * kHugeBlock;
+                j[u] = -1;
+                x[u] = 0;
+                if (k < ce) {
+                    j[u] = A.col[k];
+                    x[u] = (i64)A.w[k];
+                }
+            }
+            int32_t cc[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) cc[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (j[u] == i) loop += x[u];
+                else if (cc[u] >= 0)
+                    tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, cc[u], (VT)x[u], A.err);
+            }
+        }
+        __syncthreads();
+        const int m = s_cnt;
+        if (nch == 1) {
+            GT gbest = gain_min<GT>();
+            int32_t best = INT_MAX;
+            i64 e_a = 0;
+            for (int p = threadIdx.x; p < m; p += kHugeBlock) {
+                const int s = list[p];
+                const int32_t k2 = keys[s];
+                const i64 e = (i64)vals[s];
+                keys[s] = -1;
+                vals[s] = 0;
+                consider<GT>(k2, e, a, dl, tw, A.deg, gbest, best, e_a);
+            }
+            block_argmax(gbest, best, e_a, loop);
+            if (threadIdx.x == 0) {
+                const int32_t target =
+                    choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
+                A.Cnext[i] = target;
+                if constexpr (!BT) {
+                    moved += target != a;
+                    internal += (u64)(e_a + loop);
+                } else {
+                    row_stats(A.st, gr, e_a + loop, target != a);
+                }
+                cand += (u64)m;
+            }
+        } else {
+            const int64_t off = B.goff[b];
+            const int l2 = B.glog2[b];
+            int32_t *gk = B.gkeys + off;
+            VT *gv = (VT *)B.gvals + off;
+            int32_t *gl = B.glist + off;
+            for (int p = threadIdx.x; p < m; p += kHugeBlock) {
+                const int s = list[p];
+                const int32_t k2 = keys[s];
+                const VT e = vals[s];
+                keys[s] = -1;
+                vals[s] = 0;
+                tbl_insert<true, VT>(gk, gv, gl, &B.gcnt[b], l2, k2, e, A.err);
+            }
+            loop = sum_reduce(loop, 32);
+            if ((threadIdx.x & 31) == 0 && loop) atomicAdd(&B.gloop[b], (u64)loop);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int t = atomicAdd(&B.gdone[b], 1);
+                s_last = (t == nch - 1);
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                const int gm = __ldcg(&B.gcnt[b]);
+                GT gbest = gain_min<GT>();
+                int32_t best = INT_MAX;
+                i64 e_a = 0, lz = 0;
+                for (int p = threadIdx.x; p < gm; p += kHugeBlock) {
+                    const int s = __ldcg(gl + p);
+                    const int32_t k2 = __ldcg(gk + s);
+                    const i64 e = (i64)__ldcg(gv + s);
+                    gk[s] = -1;
+                    gv[s] = 0;
+                    consider<GT>(k2, e, a, dl, tw, A.deg, gbest, best, e_a);
+                }
+                block_argmax(gbest, best, e_a, lz);
+                if (threadIdx.x == 0) {
+                    const i64 lp = (i64)__ldcg(&B.gloop[b]);
+                    const int32_t target =
+                        choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
+                    A.Cnext[i] = target;
+                    if constexpr (!BT) {
+                        moved += target != a;
+                        internal += (u64)(e_a + lp);
+                    } else {
+                        row_stats(A.st, gr, e_a + lp, target != a);
+                    }
+                    cand += (u64)gm;
+                    B.gcnt[b] = 0;
+                    B.gdone[b] = 0;
+                    B.gloop[b] = 0;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+    }
+    block_flush_stats(A.st, kChunkedBin, internal, moved, cand, 0);
+}
+
+// ------------------------------------------------------------------ launch
+
+// shared table bytes: keys + values, plus a claim list when `with_list`
+template <typename VT>
+inline size_t table_bytes(int log2cap, bool with_list = false)
+{
+    return ((size_t)1 << log2cap) * (sizeof(VT) + (with_list ? 8 : 4));
+}
+
+template <typename K>
+static int launch_cta_kernel(K kernel, int block, size_t smem, int nrows, cudaStream_t s,
+                             const LaunchCfg &lc, const char *name)
+{
+    set_dyn_smem(kernel, smem, name);
+    const int per_sm_smem = (int)((227 * 1024) / (smem + 1024));
+    const int per_sm_thr = 2048 / block;
+    int per_sm = per_sm_smem < per_sm_thr ? per_sm_smem : per_sm_thr;
+    if (per_sm < 1) per_sm = 1;
+    const int maxg = lc.num_sms * per_sm;
+    return nrows < maxg ? nrows : maxg;
+}
+
+// Launch a cluster kernel with CL CTAs per cluster over nrows rows.  Returns 0 if no
+// cluster of that size can be resident (then the caller reports an error).
+template <int CL, typename K, typename... Args>
+static int launch_cluster_kernel(K kernel, size_t smem, int nrows, cudaStream_t s,
+                                 const char *name, Args... args)
+{
+    set_dyn_smem(kernel, smem, name);
+    if (CL > 8) cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(CL, 1, 1);
+    int maxc = 0;
+    if (cudaOccupancyMaxActiveClusters(&maxc, kernel, &cfg) != cudaSuccess || maxc < 1) {
+        cudaGetLastError();
+        if (!launch_site()) launch_site() = name;
+        return 0;
+    }
+    const int nclusters = nrows < maxc ? nrows : maxc;
+    cfg.gridDim = dim3((unsigned)(nclusters * CL), 1, 1);
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+    note_launch(name);
+    return 1;
+}
+
+template <typename WT, typename GT, typename VT, bool BT>
+static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw,
+                      SweepStats *stats, unsigned *err, cudaStream_t s, const LaunchCfg &lc,
+                      SweepTimers *tm, const BatchCtx &bc)
+{
+    MoveArgs<WT> A{g.n,   g.rp,     g.col,  (const WT *)g.w, st.C,  st.deg,  st.size,
+                   st.delta, tw,    st.Cnext, stats,         err,   bc.vg,   bc.gtw,
+                   bc.gctl};
+    const bool timed = tm && tm->on;
+    int launched = 0;
+    for (int bin = 0; bin < kNumBins; bin++) {
+        if (timed) cudaEventRecord(tm->ev[2 * bin], s);
+        const BinSpec sp = kBinSpec[bin];
+        const int nr = b.nlist[bin];
+        const int32_t *rows = b.rows(bin);
+        if (sp.kind == BIN_THREAD) {
+            if (g.n > 0) {  // dense over every vertex: also sums deg_c^2 over all labels
+                k_move_small<WT, GT, BT><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+                    A, (int)b.upper[0]);
+                note_launch("k_move_small");
+                launched++;
+            }
+        } else if (nr > 0 && sp.kind == BIN_GROUP8) {
+            k_move_group<8, 6, WT, GT, VT, BT><<<grid_for(nr, kBlock / 8, lc.max_blocks), kBlock, 0,
+                                             s>>>(A, rows, nr, bin);
+            note_launch("k_move_group<8>");
+            launched++;
+        } else if (nr > 0 && sp.kind == BIN_WARP) {
+            k_move_group<32, 8, WT, GT, VT, BT><<<grid_for(nr, kBlock / 32, lc.max_blocks), kBlock,
+                                              0, s>>>(A, rows, nr, bin);
+            note_launch("k_move_group<32>");
+            launched++;
+        } else if (nr > 0 && sp.kind == BIN_CTA) {
+            const int l2 = cta_log2cap(b, bin);
+            const size_t smem = table_bytes<VT>(l2, true);
+            if (sp.block == 128) {
+                const int grid = launch_cta_kernel(k_move_cta<128, WT, GT, VT, BT>, 128, smem, nr, s,
+                                                   lc, "k_move_cta<128>");
+                k_move_cta<128, WT, GT, VT, BT><<<grid, 128, smem, s>>>(A, rows, nr, l2, bin);
+            } else if (sp.block == 256) {
+                const int grid = launch_cta_kernel(k_move_cta<256, WT, GT, VT, BT>, 256, smem, nr, s,
+                                                   lc, "k_move_cta<256>");
+                k_move_cta<256, WT, GT, VT, BT><<<grid, 256, smem, s>>>(A, rows, nr, l2, bin);
+            } else {
+                const int grid = launch_cta_kernel(k_move_cta<1024, WT, GT, VT, BT>, 1024, smem, nr,
+                                                   s, lc, "k_move_cta<1024>");
+                k_move_cta<1024, WT, GT, VT, BT><<<grid, 1024, smem, s>>>(A, rows, nr, l2, bin);
+            }
+            note_launch("k_move_cta");
+            launched++;
+        } else if (nr > 0 && sp.kind == BIN_CLUSTER) {
+            const int l2 = cta_log2cap(b, bin);
+            const size_t smem = table_bytes<VT>(l2);
+            switch (sp.cluster) {
+            case 2:
+                launched += launch_cluster_kernel<2>(k_move_cluster<2, WT, GT, VT, BT>, smem, nr, s,
+                                                     "k_move_cluster<2>", A, rows, nr, l2, bin);
+                break;
+            case 4:
+                launched += launch_cluster_kernel<4>(k_move_cluster<4, WT, GT, VT, BT>, smem, nr, s,
+                                                     "k_move_cluster<4>", A, rows, nr, l2, bin);
+                break;
+            case 8:
+                launched += launch_cluster_kernel<8>(k_move_cluster<8, WT, GT, VT, BT>, smem, nr, s,
+                                                     "k_move_cluster<8>", A, rows, nr, l2, bin);
+                break;
+            default:
+                launched += launch_cluster_kernel<16>(k_move_cluster<16, WT, GT, VT, BT>, smem, nr, s,
+                                                      "k_move_cluster<16>", A, rows, nr, l2, bin);
+                break;
+            }
+        } else if (sp.kind == BIN_CHUNKED && b.nchunks > 0) {
+            BigArgs B{rows,    b.chunk_b, b.chunk_first, b.nch,   b.goff,  b.glog2, b.gcnt,
+                      b.gdone, b.gloop,   b.gkeys,       b.gvals, b.glist, b.chunk, b.nchunks};
+            const int l2 = 31 - __builtin_clz(2 * b.chunk);
+            const size_t smem = table_bytes<VT>(l2, true);
+            const int grid = launch_cta_kernel(k_move_huge<WT, GT, VT, BT>, kHugeBlock, smem,
+                                               b.nchunks, s, lc, "k_move_huge");
+            k_move_huge<WT, GT, VT, BT><<<grid, kHugeBlock, smem, s>>>(A, B);
+            note_launch("k_move_huge");
+            launched++;
+        }
+        if (timed) cudaEventRecord(tm->ev[2 * bin + 1], s);
+    }
+    return launched;
+}
+
+template <bool BT>
+int sweep_typed(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, bool wide,
+                 bool narrow, SweepStats *stats, unsigned *err, cudaStream_t s,
+                 const LaunchCfg &lc, SweepTimers *tm, const BatchCtx &bc)
+{
+    typedef unsigned int u32;
+    if (g.wbytes == 4) {
+        if (wide)
+            return narrow ? sweep_impl<int32_t, i128, u32, BT>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                          : sweep_impl<int32_t, i128, u64, BT>(g, st, b, tw, stats, err, s, lc, tm, bc);
+        return narrow ? sweep_impl<int32_t, i64, u32, BT>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                      : sweep_impl<int32_t, i64, u64, BT>(g, st, b, tw, stats, err, s, lc, tm, bc);
+    }
+    if (wide)
+        return narrow ? sweep_impl<i64, i128, u32, BT>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                      : sweep_impl<i64, i128, u64, BT>(g, st, b, tw, stats, err, s, lc, tm, bc);
+    return narrow ? sweep_impl<i64, i64, u32, BT>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                  : sweep_impl<i64, i64, u64, BT>(g, st, b, tw, stats, err, s, lc, tm, bc);
+}
+
+}  // namespace lv

@@ -130,9 +130,12 @@ int launch_init_state(int64_t n, const PhaseState &st, cudaStream_t s, const Lau
 int launch_vertex_following(const DevGraph &g, const PhaseState &st, cudaStream_t s,
                             const LaunchCfg &lc);
 // Two passes: count rows and entries per bin (then the host reads counts and sets off[]),
-// fill the list grouped by bin.
-int launch_bin_count(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc);
-int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc);
+// fill the list grouped by bin.  In a batch (vg, gctl given) rows of graphs whose phase has
+// stopped are left out of every bin.
+int launch_bin_count(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc,
+                     const int32_t *vg = nullptr, const LevelCtl *gctl = nullptr);
+int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc,
+                    const int32_t *vg = nullptr, const LevelCtl *gctl = nullptr);
 int launch_big_prep(const DevGraph &g, Bins &b, int64_t *scratch64, int32_t *scratch32,
                     cudaStream_t s, const LaunchCfg &lc);
 int launch_big_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc);
