@@ -8,6 +8,7 @@
 // The host only sequences launches, sizes buffers and reads a few scalars per sweep and
 // per level; every step of the method runs in the kernels of k_level.cu, k_move.cu and
 // k_coarsen.cu.
+#include <algorithm>
 #include <chrono>
 #include <climits>
 #include <memory>
@@ -175,7 +176,8 @@ struct louvain_handle {
     Scalars *pinned = nullptr;
 };
 
-// Label arrays of a batch, shared by the results of its graphs; freed with the last one.
+// Label arrays of one engine step (every graph that recorded a level in it has its labels
+// there); freed with the last result that refers to it.
 struct LabelStore {
     std::vector<int32_t *> arrays;
     louvain_free_fn ff = nullptr;
@@ -194,7 +196,9 @@ struct LabelStore {
 struct louvain_result {
     int64_t n0 = 0;
     int batch_index = -1;  // graph index in its batch, -1 for a plain run
-    std::shared_ptr<LabelStore> store;  // set for the results of a batch
+    std::vector<std::shared_ptr<LabelStore>> stores;  // label arrays of its levels
+    int64_t acc_sweeps = 0, acc_cand = 0, acc_kernels = 0;
+    double acc_alg_bytes = 0.0, acc_coarsen_ms = 0.0, acc_step_ms = 0.0;
     int64_t tw = 0;
     int device = 0;
     std::vector<LevelRec> levels;
@@ -243,13 +247,116 @@ int map_err_bits(unsigned bits, std::string &msg)
     return LOUVAIN_ERR_INTERNAL;
 }
 
-struct Runner {
+// ---------------------------------------------------------------------- step engine
+//
+// The engine holds a set of resident graphs stacked into one block-diagonal CSR (their
+// current levels) and advances all of them by one level per step: Algorithm 1's phase for
+// every resident graph at once, then renumbering, recording, Algorithm 2's outer test and
+// the induction of the next level for the graphs that go on.  Graphs enter at a step
+// boundary (all at once for a batch, one by one as they arrive when serving) and leave when
+// their own run ends; every graph keeps its own 2W, controller and outer test, so its result
+// does not depend on the graphs it shared steps with.
+
+// A graph in the engine.
+struct Member {
+    louvain_result *res = nullptr;
+    int64_t n0 = 0;          // vertices of the input graph
+    i64 tw = 0;              // its 2W
+    int level = 0;           // index of the level its next phase computes
+    i128 qn_prev = 0;        // Qn of its last recorded level
+    int64_t nv = 0, nnz = 0; // vertices and entries in the current stacked graph
+    int32_t *map = nullptr;  // device int32[n0]: current-level vertex of each input vertex
+    int64_t visits = 0;
+    double t0 = 0.0;         // when it was handed to the engine (host ms)
+    void *tag = nullptr;     // owner of the member (a served request)
+};
+
+// Graphs waiting to enter: one CSR holding K graphs (block-diagonal, global column ids,
+// int32 weights).  The arrays belong to the caller and must live until the graphs leave.
+struct Source {
+    int64_t n = 0, nnz = 0;
+    const int64_t *rp = nullptr;
+    const int32_t *col = nullptr;
+    const int32_t *w = nullptr;
+    std::vector<int64_t> vptr, eptr;  // K + 1 each
+    std::vector<Member *> members;    // K
+};
+
+struct Engine {
     louvain_handle *h;
     cudaStream_t s;
-    DevAlloc A;
+    DevAlloc &A;
+    const louvain_config &cfg;
+    const LaunchCfg &lc;
+    bool batch;  // batch kernels (any number of graphs) or the one-graph kernels
     Scalars *d_sc = nullptr;
     DBuf<Scalars> sc_buf;
-    int kernels = 0;
+    int64_t kernels = 0;
+
+    std::vector<Member *> mem;  // resident graphs in slot order
+    std::vector<Source> pending;
+    bool need_row_sums = false;
+
+    // current stacked graph (n = 0: none)
+    DevGraph G;
+    DBuf<int64_t> g_rp;
+    DBuf<int32_t> g_col;
+    DBuf<unsigned char> g_w;
+
+    // per-vertex state, sized for the largest stacked graph so far
+    DBuf<i64> delta, delta_next, deg;
+    DBuf<int32_t> C, Cnext, size, new_id, new_id2, lists, vg;
+    DBuf<int32_t> b_nch, b_chunk_first, b_glog2, b_gcnt, b_gdone;
+    DBuf<int64_t> b_gcap, b_goff;
+    DBuf<u64> b_gloop;
+    DBuf<int32_t> scratch32;
+    DBuf<int64_t> scratch64;
+    DBuf<int32_t> chunk_b, gkeys, glist;
+    DBuf<u64> gvals;
+    DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_tmp_col;
+    DBuf<int64_t> c_mpre;
+    DBuf<u64> c_tmp_w;
+    // per-slot arrays
+    DBuf<int64_t> d_gptr, d_base1, d_gnnz, d_off, d_vbase;
+    DBuf<int32_t> d_rec, d_keep, d_vf;
+    DBuf<u64> d_tw;
+    DBuf<SweepStats> d_stats;
+    DBuf<LevelCtl> d_ctls;
+    DBuf<int32_t *> d_maps;
+    DBuf<i64> tr_moved, tr_qn;
+    std::vector<i64> h_tr_moved, h_tr_qn;
+
+    SweepTimers tm;
+    cudaEvent_t coarsen_ev[2] = {nullptr, nullptr};
+
+    Engine(louvain_handle *h_, cudaStream_t s_, DevAlloc &A_, bool batch_)
+        : h(h_), s(s_), A(A_), cfg(h_->cfg), lc(h_->lc), batch(batch_)
+    {
+        sc_buf.reset(&A, 1);
+        d_sc = sc_buf.p;
+        CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars), s));
+        G.n = 0;
+        G.nnz = 0;
+        if (cfg.profile) {
+            for (auto &e : tm.ev) CK(cudaEventCreate(&e));
+            CK(cudaEventCreate(&coarsen_ev[0]));
+            CK(cudaEventCreate(&coarsen_ev[1]));
+            tm.on = true;
+        }
+    }
+    ~Engine()
+    {
+        if (tm.on) {
+            for (auto &e : tm.ev) cudaEventDestroy(e);
+            cudaEventDestroy(coarsen_ev[0]);
+            cudaEventDestroy(coarsen_ev[1]);
+        }
+        for (Member *m : mem) release_map(m);
+    }
+    Engine(const Engine &) = delete;
+    Engine &operator=(const Engine &) = delete;
+
+    bool idle() const { return mem.empty() && pending.empty(); }
 
     void check_launches()
     {
@@ -285,24 +392,734 @@ struct Runner {
         return v;
     }
 
-    // One graph (gvptr null, NG = 1) or a batch of NG graphs stored as one CSR whose graph g
-    // owns vertices [gvptr[g], gvptr[g+1]); out holds one result per graph.
-    void run(int64_t n0, const int64_t *rp, const int32_t *col, const int32_t *w, int kind,
-             int NG, const int64_t *gvptr, const int64_t *geptr,
-             std::vector<louvain_result *> &out);
+    template <typename T>
+    void ensure(DBuf<T> &b, size_t count)
+    {
+        if (!b.p || b.n < count) b.reset(&A, count);
+    }
+
+    template <typename T>
+    void upload(DBuf<T> &b, const T *src, size_t count)
+    {
+        ensure(b, count);
+        if (count) CK(cudaMemcpyAsync(b.p, src, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+    }
+
+    void release_map(Member *m)
+    {
+        if (m->map) A.put(m->map);
+        m->map = nullptr;
+    }
+
+    // Adds the graphs of a source; they enter at the next step.  Empty graphs have no
+    // level to compute and are finished at once (returned in `done`).
+    void add(Source &&src, std::vector<Member *> &done)
+    {
+        const size_t K = src.members.size();
+        for (size_t k = 0; k < K; k++) {
+            Member *m = src.members[k];
+            m->n0 = src.vptr[k + 1] - src.vptr[k];
+            m->nv = m->n0;
+            m->nnz = src.eptr[k + 1] - src.eptr[k];
+            m->res->n0 = m->n0;
+            if (m->n0 == 0) done.push_back(m);
+        }
+        if (src.n > 0) pending.push_back(std::move(src));
+    }
+
+    Bins make_proto(bool narrow_sums) const;
+    Bins make_bins(const DevGraph &gr, const Bins &pr, const int32_t *vgp = nullptr,
+                   const LevelCtl *gctl = nullptr);
+    void prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *cbp);
+    void join();
+    void step(std::vector<Member *> &retired);
 };
 
-void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const int32_t *w_in,
-                 int kind, int NG, const int64_t *gvptr, const int64_t *geptr,
-                 std::vector<louvain_result *> &out)
+Bins Engine::make_proto(bool narrow_sums) const
 {
-    const louvain_config &cfg = h->cfg;
+    // bin thresholds: every table must fit shared memory with the chosen sum width; the
+    // cluster bins hold rows up to CL times the bin-5 bound (CL CTAs, bin-5 table each);
+    // cluster sizes that cannot be resident are left empty.
+    Bins pr;
+    const int32_t thr[6] = {cfg.bin_small, cfg.bin_mid1, cfg.bin_mid2,
+                            cfg.bin_cta1,  cfg.bin_cta2, cfg.bin_cta3};
+    for (int t = 0; t < 6; t++) pr.upper[t] = thr[t];
+    if (!narrow_sums && pr.upper[5] > 6144) {
+        pr.upper[5] = 6144;
+        for (int t = 4; t >= 0; t--)
+            if (pr.upper[t] > pr.upper[t + 1]) pr.upper[t] = pr.upper[t + 1];
+    }
+    for (int t = 0; t < 4; t++) {
+        const int64_t cl = (int64_t)kBinSpec[6 + t].cluster;
+        pr.upper[6 + t] = lc.cluster_ok[t] ? pr.upper[5] * cl : pr.upper[5 + t];
+    }
+    pr.chunk = cfg.chunk_entries;
+    return pr;
+}
+
+// degree bins of graph gr: count, then fill the list grouped by bin (rows of graphs whose
+// phase stopped are left out when gctl is given)
+Bins Engine::make_bins(const DevGraph &gr, const Bins &pr, const int32_t *vgp,
+                       const LevelCtl *gctl)
+{
+    Bins bins = pr;
+    bins.list = lists.p;
+    bins.counts = &d_sc->bin_counts[0];
+    bins.nch = b_nch.p;
+    bins.chunk_first = b_chunk_first.p;
+    bins.gcap = b_gcap.p;
+    bins.goff = b_goff.p;
+    bins.glog2 = b_glog2.p;
+    bins.gcnt = b_gcnt.p;
+    bins.gdone = b_gdone.p;
+    bins.gloop = b_gloop.p;
+    kernels += launch_bin_count(gr, bins, s, lc, vgp, gctl);
+    sync_scalars();
+    bins.off[0] = bins.off[1] = 0;
+    for (int b = 0; b < kNumBins; b++) {
+        bins.nlist[b] = h->pinned->bin_counts[b];
+        memcpy(&bins.entries[b], &h->pinned->bin_counts[16 + 2 * b], sizeof(int64_t));
+        if (b >= 1) bins.off[b + 1] = bins.off[b] + bins.nlist[b];
+    }
+    kernels += launch_bin_fill(gr, bins, s, lc, vgp, gctl);
+    return bins;
+}
+
+// chunk lists and global tables of the chunked bin (after its size is known)
+void Engine::prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *cbp)
+{
+    b.nchunks = 0;
+    b.gslots = 0;
+    const int nb = b.nlist[kChunkedBin];
+    if (nb == 0) return;
+    if (coarsen_side) kernels += launch_coarsen_bigprep(k_comm, *cbp, b, s, lc);
+    else kernels += launch_big_prep(G, b, scratch64.p, scratch32.p, s, lc);
+    b.nchunks = read_one(b_chunk_first.p + nb);
+    b.gslots = read_one(b_goff.p + nb);
+    chunk_b.reset(&A, b.nchunks);
+    b.chunk_b = chunk_b.p;
+    kernels += launch_big_fill(b, s, lc);
+    if (b.gslots > 0) {
+        gkeys.reset(&A, b.gslots);
+        gvals.reset(&A, b.gslots);  // 8 bytes per slot covers both sum widths
+        glist.reset(&A, b.gslots);
+        CK(cudaMemsetAsync(gkeys.p, 0xFF, sizeof(int32_t) * b.gslots, s));
+        CK(cudaMemsetAsync(gvals.p, 0, sizeof(u64) * b.gslots, s));
+    }
+    b.gkeys = gkeys.p;
+    b.gvals = gvals.p;
+    b.glist = glist.p;
+    CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
+    CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
+    CK(cudaMemsetAsync(b_gloop.p, 0, sizeof(u64) * nb, s));
+}
+
+// Stacks the waiting graphs after the resident ones: the current graph keeps its rows, each
+// source's rows follow with shifted columns; a lone source on an empty engine is used in
+// place.  New graphs start at level 0 with their own vertices as their map.
+void Engine::join()
+{
+    const int64_t n_cont = G.n, nnz_cont = G.nnz;
+    int64_t n_add = 0, nnz_add = 0;
+    for (const Source &src : pending) {
+        n_add += src.n;
+        nnz_add += src.nnz;
+    }
+    const int64_t n = n_cont + n_add, nnz = nnz_cont + nnz_add;
+    if (n > INT32_MAX) throw LvErr{LOUVAIN_ERR_TOO_LARGE, "stacked vertex count above 2^31 - 1"};
+    std::vector<Member *> fresh;
+    std::vector<int64_t> vbase;
+    if (n_cont == 0 && pending.size() == 1) {
+        const Source &src = pending[0];
+        g_rp.release();
+        g_col.release();
+        g_w.release();
+        G.n = src.n;
+        G.nnz = src.nnz;
+        G.rp = src.rp;
+        G.col = src.col;
+        G.w = src.w;
+        G.wbytes = 4;
+    } else {
+        const int wb = n_cont > 0 ? G.wbytes : 4;
+        DBuf<int64_t> j_rp;
+        DBuf<int32_t> j_col;
+        DBuf<unsigned char> j_w;
+        j_rp.reset(&A, (size_t)n + 1);
+        j_col.reset(&A, (size_t)nnz);
+        j_w.reset(&A, (size_t)nnz * wb);
+        if (n_cont > 0) {
+            CK(cudaMemcpyAsync(j_rp.p, G.rp, sizeof(int64_t) * n_cont, cudaMemcpyDeviceToDevice, s));
+            if (nnz_cont) {
+                CK(cudaMemcpyAsync(j_col.p, G.col, sizeof(int32_t) * nnz_cont,
+                                   cudaMemcpyDeviceToDevice, s));
+                CK(cudaMemcpyAsync(j_w.p, G.w, (size_t)wb * nnz_cont, cudaMemcpyDeviceToDevice, s));
+            }
+        }
+        int64_t v_base = n_cont, e_base = nnz_cont;
+        for (const Source &src : pending) {
+            kernels += launch_append_rows(src.n, src.nnz, src.rp, src.col, src.w, v_base, e_base,
+                                          j_rp.p, j_col.p, j_w.p, wb, s, lc);
+            v_base += src.n;
+            e_base += src.nnz;
+        }
+        h->pinned->tail[0] = 0;
+        memcpy(&h->pinned->tail[0], &nnz, sizeof(nnz));
+        CK(cudaMemcpyAsync(j_rp.p + n, &h->pinned->tail[0], sizeof(int64_t),
+                           cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));  // the pinned word is reused below
+        g_rp.swap(j_rp);
+        g_col.swap(j_col);
+        g_w.swap(j_w);
+        G.n = n;
+        G.nnz = nnz;
+        G.rp = g_rp.p;
+        G.col = g_col.p;
+        G.w = g_w.p;
+        G.wbytes = wb;
+    }
+    int64_t v_base = n_cont;
+    for (Source &src : pending) {
+        for (size_t k = 0; k < src.members.size(); k++) {
+            Member *m = src.members[k];
+            if (m->n0 == 0) continue;
+            m->map = (int32_t *)A.get(sizeof(int32_t) * (size_t)m->n0);
+            m->level = 0;
+            fresh.push_back(m);
+            vbase.push_back(v_base + src.vptr[k]);
+            mem.push_back(m);
+        }
+        v_base += src.n;
+    }
+    pending.clear();
+    // every input vertex of a new graph is its own level-0 vertex
+    const int F = (int)fresh.size();
+    std::vector<int64_t> off(F + 1, 0);
+    std::vector<int32_t *> maps(F);
+    for (int f = 0; f < F; f++) {
+        off[f + 1] = off[f] + fresh[f]->n0;
+        maps[f] = fresh[f]->map;
+    }
+    upload(d_off, off.data(), F + 1);
+    upload(d_vbase, vbase.data(), F);
+    upload(d_maps, maps.data(), F);
+    kernels += launch_map_init(off[F], F, d_off.p, d_maps.p, d_vbase.p, s, lc);
+    need_row_sums = true;
+
+    // per-vertex buffers for the stacked graph (Theorem 1: later levels never grow)
+    ensure(delta, n);
+    ensure(delta_next, n);
+    ensure(deg, n);
+    ensure(C, n);
+    ensure(Cnext, n);
+    ensure(size, n);
+    ensure(new_id, (size_t)n + 1);
+    ensure(lists, n);
+    ensure(b_nch, n);
+    ensure(b_chunk_first, (size_t)n + 1);
+    ensure(b_glog2, n);
+    ensure(b_gcnt, n);
+    ensure(b_gdone, n);
+    ensure(b_gcap, n);
+    ensure(b_goff, (size_t)n + 1);
+    ensure(b_gloop, n);
+    const int64_t scratch_n = scan_scratch_elems(n + 1) + 64;
+    ensure(scratch32, scratch_n);
+    ensure(scratch64, scratch_n);
+    if (batch) {
+        ensure(vg, n);
+        ensure(new_id2, (size_t)n + 1);
+    }
+    CK(cudaStreamSynchronize(s));  // host arrays above are uploaded before they go
+}
+
+void Engine::step(std::vector<Member *> &retired)
+{
     const double wall0 = now_ms();
+    const int64_t k_start = kernels;
+    if (!pending.empty()) join();
+    if (mem.empty()) return;
+    const int M = (int)mem.size();
+    const int64_t n = G.n;
+    if (!batch && M != 1) throw LvErr{LOUVAIN_ERR_INTERNAL, "one-graph engine with several graphs"};
+
+    // slot offsets of the stacked graph
+    std::vector<int64_t> h_gptr(M + 1, 0), h_gnnz(M + 1, 0);
+    for (int m = 0; m < M; m++) {
+        h_gptr[m + 1] = h_gptr[m] + mem[m]->nv;
+        h_gnnz[m + 1] = h_gnnz[m] + mem[m]->nnz;
+    }
+    if (h_gptr[M] != n || h_gnnz[M] != G.nnz)
+        throw LvErr{LOUVAIN_ERR_INTERNAL, "graph offsets out of step with the stacked graph"};
+    if (batch) {
+        upload(d_gptr, h_gptr.data(), M + 1);
+        kernels += launch_graph_ids(n, d_gptr.p, M, vg.p, s, lc);
+        ensure(d_tw, M);
+        ensure(d_stats, M);
+        ensure(d_ctls, M);
+        ensure(d_base1, M + 1);
+        ensure(d_gnnz, M + 1);
+        CK(cudaMemsetAsync(d_stats.p, 0, sizeof(SweepStats) * M, s));
+    }
+    const int32_t *vgp = batch ? vg.p : nullptr;
+
+    // weighted degrees and 2W of every graph (Sec. 2), with the input checks, when graphs
+    // joined; otherwise delta comes from the last induction (it is preserved)
+    Bins bins0;
+    bool have_bins0 = false;
+    if (need_row_sums) {
+        bins0 = make_bins(G, make_proto(true));
+        have_bins0 = true;
+        if (batch) CK(cudaMemsetAsync(d_tw.p, 0, sizeof(u64) * M, s));
+        else CK(cudaMemsetAsync(&d_sc->tw, 0, sizeof(u64), s));
+        kernels += launch_row_sums(G, bins0, vgp, batch ? d_gptr.p : nullptr, delta.p,
+                                   batch ? d_tw.p : &d_sc->tw, &d_sc->err, s, lc);
+        if (cfg.checks >= 2) kernels += launch_check_symmetry(G, &d_sc->err, s, lc);
+        sync_scalars();
+        std::vector<u64> tws(M);
+        if (batch) {
+            CK(cudaMemcpyAsync(tws.data(), d_tw.p, sizeof(u64) * M, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        } else {
+            tws[0] = h->pinned->tw;
+        }
+        for (int m = 0; m < M; m++) {
+            if (tws[m] > ((u64)1 << 62))
+                throw LvErr{LOUVAIN_ERR_TOO_LARGE, "sum of weights above 2^62"};
+            mem[m]->tw = (i64)tws[m];
+            mem[m]->res->tw = (i64)tws[m];
+        }
+        need_row_sums = false;
+    } else {
+        delta.swap(delta_next);
+    }
+    u64 tw_max = 0;
+    std::vector<i64> h_tw(M);
+    for (int m = 0; m < M; m++) {
+        h_tw[m] = mem[m]->tw;
+        if ((u64)h_tw[m] > tw_max) tw_max = (u64)h_tw[m];
+    }
+    if (batch) upload(d_tw, (const u64 *)h_tw.data(), M);
+    // gains in int128 when some graph's (2W)^2 leaves int64; 32-bit table sums when every
+    // graph's 2W fits (a table sum never exceeds its graph's 2W)
+    const bool wide = cfg.force_int128 || (u128)tw_max * tw_max > (u128)INT64_MAX;
+    const bool narrow = !cfg.wide_sums && tw_max < ((u64)1 << 32);
+    const i64 TW = h_tw[0];  // one graph: its 2W (a batch reads 2W per graph on the device)
+
+    PhaseState st;
+    st.C = C.p;
+    st.Cnext = Cnext.p;
+    st.deg = deg.p;
+    st.size = size.p;
+    st.delta = delta.p;
+    kernels += launch_init_state(n, st, s, lc);
+    // vertex following: level 0 of each graph (every level with vf_all_levels)
+    if (cfg.vertex_following) {
+        if (batch) {
+            std::vector<int32_t> vf(M);
+            bool any = false;
+            for (int m = 0; m < M; m++) {
+                vf[m] = mem[m]->level == 0 || cfg.vf_all_levels;
+                any = any || vf[m];
+            }
+            if (any) {
+                upload(d_vf, vf.data(), M);
+                kernels += launch_vertex_following(G, st, s, lc, vgp, d_vf.p);
+            }
+        } else if (mem[0]->level == 0 || cfg.vf_all_levels) {
+            kernels += launch_vertex_following(G, st, s, lc);
+        }
+    }
+
+    // degree bins (the row-sum bins are reused when they were made with these thresholds)
+    const Bins proto = make_proto(narrow);
+    Bins bins;
+    if (have_bins0 && narrow) {
+        bins = bins0;
+    } else {
+        bins = make_bins(G, proto);
+    }
+    prep_huge(bins, false, 0, nullptr);
+
+    // phase controllers
+    std::vector<LevelCtl> h_ctl(M);
+    for (int m = 0; m < M; m++) {
+        LevelCtl &c = h_ctl[m];
+        memset(&c, 0, sizeof(c));
+        c.tw = h_tw[m];
+        c.theta_num = cfg.theta_num;
+        c.theta_den = cfg.theta_den;
+        c.max_iters = cfg.max_iters;
+    }
+    LevelCtl *ctl_dev = batch ? d_ctls.p : &d_sc->ctl;
+    SweepStats *st_dev = batch ? d_stats.p : &d_sc->st;
+    if (batch) {
+        CK(cudaMemcpyAsync(d_ctls.p, h_ctl.data(), sizeof(LevelCtl) * M, cudaMemcpyHostToDevice,
+                           s));
+    } else {
+        h->pinned->ctl = h_ctl[0];
+        CK(cudaMemcpyAsync(&d_sc->ctl, &h->pinned->ctl, sizeof(LevelCtl), cudaMemcpyHostToDevice,
+                           s));
+        CK(cudaMemsetAsync(&d_sc->st, 0, sizeof(SweepStats), s));
+    }
+    h->pinned->ndone = 0;
+    CK(cudaMemcpyAsync(&d_sc->ndone, &h->pinned->ndone, sizeof(int32_t), cudaMemcpyHostToDevice,
+                       s));
+    CK(cudaMemsetAsync(&d_sc->cand_total[0], 0, sizeof(u64) * 16, s));
+    const int tcap = cfg.max_iters + 1;
+    ensure(tr_moved, (size_t)tcap * M);
+    ensure(tr_qn, 2 * (size_t)tcap * M);
+    BatchCtx bc;
+    if (batch) {
+        bc.vg = vg.p;
+        bc.gtw = (const i64 *)d_tw.p;
+        bc.gctl = d_ctls.p;
+    }
+
+    // sweeps (Algorithm 1); one host read of the controllers' count per sweep
+    double t_kernel[kNumBins] = {};
+    int64_t launches_kernel[kNumBins] = {};
+    double bytes_kernel[kNumBins] = {};
+    int64_t rows_kernel[kNumBins] = {}, entries_kernel[kNumBins] = {};
+    double alg_bytes = 0.0;
+    u64 cand_all = 0;
+    auto account_sweep = [&](const Bins &bb) {  // algorithmic bytes (formula in louvain.h)
+        const double per_entry = 8.0 + (double)G.wbytes;
+        for (int b = 0; b < kNumBins; b++) {
+            double kb = (double)bb.entries[b] * per_entry;
+            kb += b == 0 ? (double)n * 16.0 + (double)bb.nlist[0] * 24.0
+                         : (double)bb.nlist[b] * 36.0;
+            bytes_kernel[b] += kb;
+            alg_bytes += kb;
+            rows_kernel[b] += b == 0 ? n : bb.nlist[b];
+            entries_kernel[b] += bb.entries[b];
+        }
+    };
+    int sweeps = 0;
+    int ndone_binned = 0;
+    for (;;) {
+        kernels += launch_sweep(G, st, bins, TW, wide, narrow, st_dev, &d_sc->err, s, lc, &tm, bc);
+        kernels += launch_decide(st_dev, ctl_dev, M, tr_moved.p, tr_qn.p, &d_sc->cand_total[0],
+                                 &d_sc->ndone, s);
+        kernels += launch_apply(n, st, ctl_dev, bc.vg, s, lc);
+        sweeps++;
+        account_sweep(bins);
+        sync_scalars();
+        for (int b = 0; b < kNumBins; b++) {
+            if (tm.on) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, tm.ev[2 * b], tm.ev[2 * b + 1]));
+                t_kernel[b] += ms;
+            }
+            launches_kernel[b] +=
+                b == 0 ? 1 : (b == kChunkedBin ? bins.nchunks > 0 : bins.nlist[b] > 0);
+        }
+        const int ndone = h->pinned->ndone;
+        if (ndone >= M) break;
+        if (sweeps > cfg.max_iters + 2)
+            throw LvErr{LOUVAIN_ERR_INTERNAL, "phase controller did not stop"};
+        if (batch && ndone > ndone_binned) {
+            // some graphs stopped: bin again without their rows
+            bins = make_bins(G, proto, vg.p, d_ctls.p);
+            prep_huge(bins, false, 0, nullptr);
+            ndone_binned = ndone;
+        }
+    }
+    if (batch) {
+        CK(cudaMemcpyAsync(h_ctl.data(), d_ctls.p, sizeof(LevelCtl) * M, cudaMemcpyDeviceToHost,
+                           s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        h_ctl[0] = h->pinned->ctl;
+    }
+    for (int b = 0; b < kNumBins; b++) {  // candidate reads, 8 bytes each
+        const u64 cb = h->pinned->cand_total[b];
+        bytes_kernel[b] += 8.0 * (double)cb;
+        alg_bytes += 8.0 * (double)cb;
+        cand_all += cb;
+    }
+    int max_iters_run = 0;
+    for (int m = 0; m < M; m++) max_iters_run = std::max(max_iters_run, h_ctl[m].iters);
+    if (max_iters_run > 0) {
+        const size_t cnt = (size_t)max_iters_run * M;
+        h_tr_moved.resize(cnt);
+        h_tr_qn.resize(2 * cnt);
+        CK(cudaMemcpyAsync(h_tr_moved.data(), tr_moved.p, sizeof(i64) * cnt,
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h_tr_qn.data(), tr_qn.p, sizeof(i64) * 2 * cnt, cudaMemcpyDeviceToHost,
+                           s));
+        CK(cudaStreamSynchronize(s));
+    }
+    for (int m = 0; m < M; m++) {
+        Member *mb = mem[m];
+        const int it = h_ctl[m].iters;
+        for (int t = 0; t < it; t++) {
+            const size_t e = (size_t)t * M + m;
+            mb->res->trace.push_back(
+                TraceRec{mb->level, t + 1, h_tr_moved[e], limbs_to_i128(&h_tr_qn[2 * e])});
+        }
+        mb->visits += (int64_t)it * mb->nnz;
+    }
+
+    // renumber (Sec. 5.1.2) -- used labels in increasing order; labels of one graph are
+    // contiguous, so the scan also numbers each graph's communities
+    kernels += launch_renumber(n, size.p, nullptr, nullptr, new_id.p, scratch32.p, s);
+    std::vector<int64_t> h_base1(M + 1, 0);
+    if (batch) {
+        kernels += launch_gather_ids(new_id.p, d_gptr.p, M + 1, d_base1.p, s);
+        CK(cudaMemcpyAsync(h_base1.data(), d_base1.p, sizeof(int64_t) * (M + 1),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        h_base1[1] = read_one(new_id.p + n);
+        upload(d_base1, h_base1.data(), 2);
+    }
+    // record the level of every graph that merged something (one that merged nothing is
+    // finished: no new level), then the outer test of Algorithm 2
+    std::vector<int32_t> rec(M, 0), keep(M, 0);
+    int nrec = 0, nkeep = 0;
+    int64_t k_next = 0, n_keep = 0, n0_all = 0;
+    bool all_kept = true;
+    for (int m = 0; m < M; m++) {
+        Member *mb = mem[m];
+        n0_all += mb->n0;
+        const int64_t kg = h_base1[m + 1] - h_base1[m];
+        rec[m] = kg < mb->nv;
+        if (!rec[m]) {
+            all_kept = false;
+            continue;
+        }
+        nrec++;
+        const LevelCtl &hc = h_ctl[m];
+        LevelRec r;
+        r.ncomm = kg;
+        r.qn = limbs_to_i128(hc.qn_final);
+        r.qn_init = limbs_to_i128(hc.qn_init);
+        r.iters = hc.iters;
+        r.n = mb->nv;
+        r.nnz = mb->nnz;
+        r.hit_cap = hc.hit_cap;
+        mb->res->levels.push_back(r);
+        const bool stop = (mb->level >= 1 && host_below_threshold(r.qn, mb->qn_prev, mb->tw,
+                                                                  cfg.theta_num, cfg.theta_den)) ||
+                          mb->level + 1 >= cfg.max_levels;
+        mb->qn_prev = r.qn;
+        if (stop) {
+            all_kept = false;
+        } else {
+            keep[m] = 1;
+            nkeep++;
+            k_next += kg;
+            n_keep += mb->nv;
+        }
+    }
+    // labels of the input vertices of every recorded graph (one array for this step, shared
+    // by the results that recorded a level in it)
+    const int32_t *nid2 = new_id.p;
+    if (nrec > 0) {
+        auto store = std::make_shared<LabelStore>();
+        store->ff = cfg.free;
+        store->ctx = cfg.alloc_ctx;
+        store->device = h->device;
+        int32_t *out = (int32_t *)A.get(sizeof(int32_t) * (size_t)n0_all);
+        store->arrays.push_back(out);
+        std::vector<int64_t> off(M + 1, 0);
+        std::vector<int32_t *> maps(M);
+        for (int m = 0; m < M; m++) {
+            off[m + 1] = off[m] + mem[m]->n0;
+            maps[m] = mem[m]->map;
+            if (rec[m]) {
+                mem[m]->res->levels.back().d_labels = out + off[m];
+                mem[m]->res->stores.push_back(store);
+            }
+        }
+        upload(d_off, off.data(), M + 1);
+        upload(d_maps, maps.data(), M);
+        upload(d_rec, rec.data(), M);
+        upload(d_keep, keep.data(), M);
+        if (batch && nkeep > 0 && !all_kept) {
+            // next-level numbering: the kept graphs' communities only
+            kernels += launch_renumber(n, size.p, vg.p, d_keep.p, new_id2.p, scratch32.p, s);
+            nid2 = new_id2.p;
+        }
+        kernels += launch_compose(n0_all, M, d_off.p, d_maps.p, d_rec.p, d_keep.p, st.C, new_id.p,
+                                  d_base1.p, nid2, out, s, lc);
+        CK(cudaStreamSynchronize(s));  // host vectors above are uploaded before they go
+    }
+
+    // ---------------- induce the next graph of the kept graphs (Sec. 5.1.2)
+    double t_coarsen = 0.0;
+    std::vector<int64_t> gptr_next(M + 1, 0), gnnz_next(M + 1, 0);
+    if (nkeep > 0) {
+        ensure(c_csize, n);
+        ensure(c_moff, (size_t)n + 1);
+        ensure(c_cursor, n);
+        ensure(c_members, n);
+        ensure(c_mpre, (size_t)n + 1);
+        ensure(c_ccnt, n);
+        ensure(c_tmp_col, (size_t)G.nnz);
+        ensure(c_tmp_w, (size_t)G.nnz);
+        CoarsenBufs cb;
+        cb.csize = c_csize.p;
+        cb.moff = c_moff.p;
+        cb.cursor = c_cursor.p;
+        cb.members = c_members.p;
+        cb.mpre = c_mpre.p;
+        cb.ccnt = c_ccnt.p;
+        cb.tmp_col = c_tmp_col.p;
+        cb.tmp_w = c_tmp_w.p;
+        cb.counts = &d_sc->ccounts[0];
+        cb.scratch32 = scratch32.p;
+        cb.scratch64 = scratch64.p;
+        if (tm.on) CK(cudaEventRecord(coarsen_ev[0], s));
+        Bins cbins = proto;
+        cbins.nch = b_nch.p;
+        cbins.chunk_first = b_chunk_first.p;
+        cbins.gcap = b_gcap.p;
+        cbins.goff = b_goff.p;
+        cbins.glog2 = b_glog2.p;
+        cbins.gcnt = b_gcnt.p;
+        cbins.gdone = b_gdone.p;
+        cbins.gloop = b_gloop.p;
+        const int64_t k = k_next;
+        const bool masked = batch && !all_kept;
+        kernels += launch_coarsen_stage1(G, st, nid2, k, masked ? n_keep : n,
+                                         masked ? vg.p : nullptr, masked ? d_keep.p : nullptr,
+                                         nullptr, delta_next.p, cb, cbins, s, lc);
+        sync_scalars();
+        cbins.list = lists.p;  // the sweep's lists are free again
+        cbins.off[0] = cbins.off[1] = cbins.off[2] = 0;
+        for (int b = 0; b < kNumBins; b++) {
+            cbins.nlist[b] = b < 2 ? 0 : h->pinned->ccounts[b];
+            if (b >= 2) cbins.off[b + 1] = cbins.off[b] + cbins.nlist[b];
+        }
+        kernels += launch_coarsen_binfill(k, cb, cbins, s, lc);
+        prep_huge(cbins, true, k, &cb);
+        kernels += launch_coarsen_stage2(G, st, nid2, k, cb, cbins, narrow, &d_sc->err, s, lc);
+        DBuf<int64_t> rp_next;
+        rp_next.reset(&A, (size_t)k + 1);
+        kernels += launch_coarsen_rowptr(k, cb, rp_next.p, s);
+        sync_scalars();
+        const int64_t nnz_next = read_one(rp_next.p + k);
+        const int wb_next = tw_max <= (u64)INT32_MAX ? 4 : 8;
+        DBuf<int32_t> col_next;
+        DBuf<unsigned char> w_next;
+        col_next.reset(&A, (size_t)nnz_next);
+        w_next.reset(&A, (size_t)nnz_next * wb_next);
+        kernels += launch_coarsen_compact(k, nnz_next, cb, rp_next.p, col_next.p, w_next.p,
+                                          wb_next, s, lc);
+        if (tm.on) {
+            CK(cudaEventRecord(coarsen_ev[1], s));
+            CK(cudaEventSynchronize(coarsen_ev[1]));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, coarsen_ev[0], coarsen_ev[1]));
+            t_coarsen = ms;
+        }
+        // vertex and entry offsets of every kept graph in the next graph
+        if (batch) {
+            kernels += launch_gather_ids(nid2, d_gptr.p, M + 1, d_base1.p, s);
+            kernels += launch_gather64(rp_next.p, d_base1.p, M + 1, d_gnnz.p, s);
+            CK(cudaMemcpyAsync(gptr_next.data(), d_base1.p, sizeof(int64_t) * (M + 1),
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(gnnz_next.data(), d_gnnz.p, sizeof(int64_t) * (M + 1),
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        } else {
+            gptr_next[1] = k;
+            gnnz_next[1] = nnz_next;
+        }
+        g_rp.swap(rp_next);
+        g_col.swap(col_next);
+        g_w.swap(w_next);
+        G.n = k;
+        G.nnz = nnz_next;
+        G.rp = g_rp.p;
+        G.col = g_col.p;
+        G.w = g_w.p;
+        G.wbytes = wb_next;
+    } else {
+        g_rp.release();
+        g_col.release();
+        g_w.release();
+        G.n = 0;
+        G.nnz = 0;
+        G.rp = nullptr;
+        G.col = nullptr;
+        G.w = nullptr;
+    }
+
+    // step totals go to every graph of the step; the kept graphs move on, the rest leave
+    const double wall = now_ms() - wall0;
+    const int64_t step_kernels = kernels - k_start;
+    std::vector<Member *> next;
+    for (int m = 0; m < M; m++) {
+        Member *mb = mem[m];
+        louvain_result *r = mb->res;
+        r->acc_sweeps += sweeps;
+        r->acc_alg_bytes += alg_bytes;
+        r->acc_cand += (int64_t)cand_all;
+        r->acc_kernels += step_kernels;
+        r->acc_coarsen_ms += t_coarsen;
+        r->acc_step_ms += wall;
+        for (int b = 0; b < kNumBins; b++) {
+            r->bin_time[b] += t_kernel[b];
+            r->bin_launches[b] += launches_kernel[b];
+            r->bin_bytes[b] += bytes_kernel[b];
+            r->bin_rows[b] += rows_kernel[b];
+            r->bin_entries[b] += entries_kernel[b];
+        }
+        if (keep[m]) {
+            mb->level++;
+            mb->nv = gptr_next[m + 1] - gptr_next[m];
+            mb->nnz = gnnz_next[m + 1] - gnnz_next[m];
+            next.push_back(mb);
+        } else {
+            release_map(mb);
+            retired.push_back(mb);
+        }
+    }
+    mem.swap(next);
+}
+
+// Counters and times of a graph that left the engine (formulas in louvain.h).
+void finish_result(Member *m)
+{
+    louvain_result *r = m->res;
+    r->counters[0] = m->visits;
+    r->counters[1] = r->acc_sweeps;
+    r->counters[2] = (int64_t)r->acc_alg_bytes;
+    r->counters[3] = r->acc_cand;
+    r->counters[4] = r->acc_kernels;
+    int dom = 0;
+    for (int b = 1; b < kNumBins; b++)
+        if (r->bin_time[b] > r->bin_time[dom]) dom = b;
+    double tot = 0;
+    for (int b = 0; b < kNumBins; b++) tot += r->bin_time[b];
+    if (tot > 0) {
+        r->times[0] = tot;
+        r->times[4] = r->bin_time[dom];
+        r->times[5] = r->bin_time[0];
+        r->times[6] = r->bin_time[1] + r->bin_time[2];
+        r->times[7] = r->bin_time[3] + r->bin_time[4] + r->bin_time[5] + r->bin_time[6];
+        r->counters[5] = r->bin_launches[dom];
+        r->counters[6] = (int64_t)r->bin_bytes[dom];
+        r->counters[7] = dom;
+        r->times[1] = r->acc_coarsen_ms;
+    }
+    r->times[3] = now_ms() - m->t0;
+}
+
+// Runs louvain_run (gvptr null: one graph, one-graph kernels) or louvain_run_batch on the
+// engine: the input enters as one source and the engine steps until every graph has left.
+void run_engine(louvain_handle *h, cudaStream_t s, DevAlloc &A, int64_t n0, const int64_t *rp_in,
+                const int32_t *col_in, const int32_t *w_in, int kind, int NG,
+                const int64_t *gvptr, const int64_t *geptr, std::vector<louvain_result *> &out)
+{
+    const double t0 = now_ms();
+    const bool batch = gvptr != nullptr;
+    std::vector<std::unique_ptr<Member>> members(NG);  // outlives the engine
+    Engine E(h, s, A, batch);
     const LaunchCfg &lc = h->lc;
-    const bool batch = gvptr != nullptr;  // a batch of NG graphs, else one graph (NG = 1)
-    sc_buf.reset(&A, 1);
-    d_sc = sc_buf.p;
-    CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars), s));
 
     // ---------------- input graph on the device
     int64_t nnz = 0;
@@ -333,644 +1150,68 @@ void Runner::run(int64_t n0, const int64_t *rp_in, const int32_t *col_in, const 
             d_w = w_own.p;
         }
     } else {
-        const int64_t r0 = read_one(rp_in);
-        nnz = read_one(rp_in + n0);
+        const int64_t r0 = E.read_one(rp_in);
+        nnz = E.read_one(rp_in + n0);
         if (r0 != 0) throw LvErr{LOUVAIN_ERR_INDEX_RANGE, "row_ptr[0] must be 0"};
         if (nnz < 0) throw LvErr{LOUVAIN_ERR_INDEX_RANGE, "row_ptr[n] is negative"};
         if (nnz > 0 && !col_in) throw LvErr{LOUVAIN_ERR_INVALID_ARG, "col_idx is NULL"};
     }
     if (!d_w) {
         w_own.reset(&A, (size_t)nnz);
-        kernels += launch_fill_ones(w_own.p, nnz, s, lc);
+        E.kernels += launch_fill_ones(w_own.p, nnz, s, lc);
         d_w = w_own.p;
     }
+    Source src;
+    src.n = n0;
+    src.nnz = nnz;
+    src.rp = d_rp;
+    src.col = d_col;
+    src.w = d_w;
+    src.vptr.assign(NG + 1, 0);
+    src.eptr.assign(NG + 1, 0);
+    for (int g = 0; g <= NG; g++) src.vptr[g] = batch ? gvptr[g] : (g ? n0 : 0);
     for (int g = 0; g < NG; g++) {
-        out[g]->n0 = batch ? gvptr[g + 1] - gvptr[g] : n0;
+        members[g].reset(new Member());
+        members[g]->res = out[g];
+        members[g]->t0 = t0;
+        src.members.push_back(members[g].get());
+        out[g]->n0 = src.vptr[g + 1] - src.vptr[g];
         out[g]->batch_index = batch ? g : -1;
     }
-    if (n0 == 0) {
-        CK(cudaStreamSynchronize(s));
-        for (int g = 0; g < NG; g++) out[g]->times[3] = now_ms() - wall0;
-        return;
-    }
-
-    DevGraph G;
-    G.n = n0;
-    G.nnz = nnz;
-    G.rp = d_rp;
-    G.col = d_col;
-    G.w = d_w;
-    G.wbytes = 4;
-
-    // ---------------- validation and weighted degrees (Sec. 2)
-    kernels += launch_validate_rowptr(d_rp, n0, &d_sc->err, s, lc);
-    sync_scalars();  // row offsets must be sane before any row is read
-    // batch bookkeeping: vertex offsets of every graph at the current level, the graph of
-    // every vertex (current level and level 0), per-graph 2W, controllers and statistics
-    DBuf<int64_t> d_gptr, d_gptr_next, d_base1, d_gnnz;
-    DBuf<int32_t> d_vg, d_vg_next, d_vg0, d_rec, d_keep, map0;
-    DBuf<u64> d_gtw;
-    DBuf<SweepStats> d_stats;
-    DBuf<LevelCtl> d_ctls;
-    std::vector<int64_t> h_gptr(NG + 1), h_gnnz(NG + 1), h_base1(NG + 1);
-    if (batch) {
-        for (int g = 0; g <= NG; g++) h_gptr[g] = gvptr[g];
-        d_gptr.reset(&A, NG + 1);
-        d_gptr_next.reset(&A, NG + 1);
-        d_base1.reset(&A, NG + 1);
-        d_gnnz.reset(&A, NG + 1);
-        CK(cudaMemcpyAsync(d_gptr.p, h_gptr.data(), sizeof(int64_t) * (NG + 1),
-                           cudaMemcpyHostToDevice, s));
-        kernels += launch_gather64(d_rp, d_gptr.p, NG + 1, d_gnnz.p, s);
-        CK(cudaMemcpyAsync(h_gnnz.data(), d_gnnz.p, sizeof(int64_t) * (NG + 1),
-                           cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (geptr)
-            for (int g = 0; g <= NG; g++)
-                if (geptr[g] != h_gnnz[g])
-                    throw LvErr{LOUVAIN_ERR_INDEX_RANGE,
-                                "graph_eptr[" + std::to_string(g) + "] != row_ptr[graph_vptr[g]]"};
-        d_vg.reset(&A, n0);
-        d_vg_next.reset(&A, n0);
-        d_vg0.reset(&A, n0);
-        d_rec.reset(&A, NG);
-        d_keep.reset(&A, NG);
-        map0.reset(&A, n0);
-        d_gtw.reset(&A, NG);
-        d_stats.reset(&A, NG);
-        d_ctls.reset(&A, NG);
-        CK(cudaMemsetAsync(d_gtw.p, 0, sizeof(u64) * NG, s));
-        CK(cudaMemsetAsync(d_stats.p, 0, sizeof(SweepStats) * NG, s));
-        kernels += launch_graph_ids(n0, d_gptr.p, NG, d_vg0.p, s, lc);
-        CK(cudaMemcpyAsync(d_vg.p, d_vg0.p, sizeof(int32_t) * n0, cudaMemcpyDeviceToDevice, s));
-    } else {
-        h_gptr[0] = 0;
-        h_gptr[1] = n0;
-        h_gnnz[0] = 0;
-        h_gnnz[1] = nnz;
-    }
-    DBuf<i64> delta, delta_next, deg;
-    DBuf<int32_t> C, Cnext, size, new_id, new_id2;
-    delta.reset(&A, n0);
-    delta_next.reset(&A, n0);
-    deg.reset(&A, n0);
-    C.reset(&A, n0);
-    Cnext.reset(&A, n0);
-    size.reset(&A, n0);
-    new_id.reset(&A, (size_t)n0 + 1);
-    DBuf<int32_t> lists;  // rows of bins 1.., grouped by bin
-    lists.reset(&A, (size_t)n0);
-    // bin thresholds: every table must fit shared memory with the chosen sum width; the
-    // cluster bins hold rows up to CL times the bin-5 bound (CL CTAs, bin-5 table each);
-    // cluster sizes that cannot be resident are left empty.
-    auto make_proto = [&](bool narrow_sums) {
-        Bins pr;
-        const int32_t thr[6] = {cfg.bin_small, cfg.bin_mid1, cfg.bin_mid2,
-                                cfg.bin_cta1,  cfg.bin_cta2, cfg.bin_cta3};
-        for (int t = 0; t < 6; t++) pr.upper[t] = thr[t];
-        if (!narrow_sums && pr.upper[5] > 6144) {
-            pr.upper[5] = 6144;
-            for (int t = 4; t >= 0; t--)
-                if (pr.upper[t] > pr.upper[t + 1]) pr.upper[t] = pr.upper[t + 1];
-        }
-        for (int t = 0; t < 4; t++) {
-            const int64_t cl = (int64_t)kBinSpec[6 + t].cluster;
-            pr.upper[6 + t] = lc.cluster_ok[t] ? pr.upper[5] * cl : pr.upper[5 + t];
-        }
-        pr.chunk = cfg.chunk_entries;
-        return pr;
-    };
-    // degree bins of graph G: count, then fill the list grouped by bin
-    auto make_bins = [&](const DevGraph &gr, const Bins &pr, const int32_t *vg = nullptr,
-                         const LevelCtl *gctl = nullptr) {
-        Bins bins = pr;
-        bins.list = lists.p;
-        bins.counts = &d_sc->bin_counts[0];
-        kernels += launch_bin_count(gr, bins, s, lc, vg, gctl);
-        sync_scalars();
-        bins.off[0] = bins.off[1] = 0;
-        for (int b = 0; b < kNumBins; b++) {
-            bins.nlist[b] = h->pinned->bin_counts[b];
-            memcpy(&bins.entries[b], &h->pinned->bin_counts[16 + 2 * b], sizeof(int64_t));
-            if (b >= 1) bins.off[b + 1] = bins.off[b] + bins.nlist[b];
-        }
-        kernels += launch_bin_fill(gr, bins, s, lc, vg, gctl);
-        return bins;
-    };
-    const Bins proto_narrow = make_proto(true);
-    Bins bins0 = make_bins(G, proto_narrow);
-    kernels += launch_row_sums(G, bins0, batch ? d_vg.p : nullptr, batch ? d_gptr.p : nullptr,
-                               delta.p, batch ? d_gtw.p : &d_sc->tw, &d_sc->err, s, lc);
-    if (cfg.checks >= 2) kernels += launch_check_symmetry(G, &d_sc->err, s, lc);
-    sync_scalars();
-    std::vector<i64> h_tw(NG);
-    if (batch) {
-        CK(cudaMemcpyAsync(h_tw.data(), d_gtw.p, sizeof(u64) * NG, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-    } else {
-        h_tw[0] = (i64)h->pinned->tw;
-    }
-    u64 tw_max = 0;
-    for (int g = 0; g < NG; g++) {
-        const u64 t = (u64)h_tw[g];
-        if (t > ((u64)1 << 62)) throw LvErr{LOUVAIN_ERR_TOO_LARGE, "sum of weights above 2^62"};
-        if (t > tw_max) tw_max = t;
-        out[g]->tw = h_tw[g];
-    }
-    const i64 TW = h_tw[0];  // one graph: its 2W (a batch reads 2W per graph on the device)
-    // gains in int128 when some graph's (2W)^2 leaves int64; 32-bit table sums when every
-    // graph's 2W fits (a table sum never exceeds its graph's 2W)
-    const bool wide = cfg.force_int128 || (u128)tw_max * tw_max > (u128)INT64_MAX;
-    const bool narrow = !cfg.wide_sums && tw_max < ((u64)1 << 32);
-
-    // ---------------- per-run buffers sized by level 0 (Theorem 1: levels never grow)
-    const int64_t scratch_n = scan_scratch_elems(n0 + 1) + 64;
-    DBuf<int32_t> b_nch, b_chunk_first, b_glog2, b_gcnt, b_gdone;
-    DBuf<int64_t> b_gcap, b_goff;
-    DBuf<u64> b_gloop;
-    b_nch.reset(&A, n0);
-    b_chunk_first.reset(&A, (size_t)n0 + 1);
-    b_glog2.reset(&A, n0);
-    b_gcnt.reset(&A, n0);
-    b_gdone.reset(&A, n0);
-    b_gcap.reset(&A, n0);
-    b_goff.reset(&A, (size_t)n0 + 1);
-    b_gloop.reset(&A, n0);
-    DBuf<int32_t> scratch32;
-    DBuf<int64_t> scratch64;
-    scratch32.reset(&A, scratch_n);
-    scratch64.reset(&A, scratch_n);
-    DBuf<i64> tr_moved, tr_qn;
-    const int tcap = cfg.max_iters + 1;
-    tr_moved.reset(&A, (size_t)tcap * NG);
-    tr_qn.reset(&A, 2 * (size_t)tcap * NG);
-    std::vector<i64> h_tr_moved, h_tr_qn;
-    // coarsening buffers
-    DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_tmp_col;
-    DBuf<int64_t> c_mpre;
-    DBuf<u64> c_tmp_w;
-    // graph buffers of the levels above 0
-    DBuf<int64_t> g_rp, g_rp_next;
-    DBuf<int32_t> g_col, g_col_next;
-    DBuf<unsigned char> g_w, g_w_next;
-    DBuf<int32_t> chunk_b;
-    DBuf<int32_t> gkeys, glist;
-    DBuf<u64> gvals;
-
-    SweepTimers tm;
-    double t_kernel[kNumBins] = {};
-    int64_t launches_kernel[kNumBins] = {};
-    double bytes_kernel[kNumBins] = {};
-    cudaEvent_t coarsen_ev[2] = {nullptr, nullptr};
-    double t_coarsen = 0.0;
-    if (cfg.profile) {
-        for (auto &e : tm.ev) CK(cudaEventCreate(&e));
-        CK(cudaEventCreate(&coarsen_ev[0]));
-        CK(cudaEventCreate(&coarsen_ev[1]));
-        tm.on = true;
-    }
-    struct EvGuard {
-        SweepTimers *t;
-        cudaEvent_t *ce;
-        ~EvGuard()
-        {
-            if (t->on) {
-                for (auto &e : t->ev) cudaEventDestroy(e);
-                cudaEventDestroy(ce[0]);
-                cudaEventDestroy(ce[1]);
-            }
-        }
-    } evg{&tm, coarsen_ev};
-
-    PhaseState st;
-    st.C = C.p;
-    st.Cnext = Cnext.p;
-    st.deg = deg.p;
-    st.size = size.p;
-    st.delta = delta.p;
-
-    Bins proto = make_proto(narrow);
-    const bool reuse_bins0 = narrow;  // level-0 bins were made with these thresholds
-    proto.nch = b_nch.p;
-    proto.chunk_first = b_chunk_first.p;
-    proto.gcap = b_gcap.p;
-    proto.goff = b_goff.p;
-    proto.glog2 = b_glog2.p;
-    proto.gcnt = b_gcnt.p;
-    proto.gdone = b_gdone.p;
-    proto.gloop = b_gloop.p;
-
-    // sets up chunk lists and global tables of the chunked bin (after its size is known)
-    auto prep_huge = [&](Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *cbp) {
-        b.nchunks = 0;
-        b.gslots = 0;
-        const int nb = b.nlist[kChunkedBin];
-        if (nb == 0) return;
-        if (coarsen_side) kernels += launch_coarsen_bigprep(k_comm, *cbp, b, s, lc);
-        else kernels += launch_big_prep(G, b, scratch64.p, scratch32.p, s, lc);
-        b.nchunks = read_one(b_chunk_first.p + nb);
-        b.gslots = read_one(b_goff.p + nb);
-        chunk_b.reset(&A, b.nchunks);
-        b.chunk_b = chunk_b.p;
-        kernels += launch_big_fill(b, s, lc);
-        if (b.gslots > 0) {
-            gkeys.reset(&A, b.gslots);
-            gvals.reset(&A, b.gslots);  // 8 bytes per slot covers both sum widths
-            glist.reset(&A, b.gslots);
-            CK(cudaMemsetAsync(gkeys.p, 0xFF, sizeof(int32_t) * b.gslots, s));
-            CK(cudaMemsetAsync(gvals.p, 0, sizeof(u64) * b.gslots, s));
-        }
-        b.gkeys = gkeys.p;
-        b.gvals = gvals.p;
-        b.glist = glist.p;
-        CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
-        CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
-        CK(cudaMemsetAsync(b_gloop.p, 0, sizeof(u64) * nb, s));
-    };
-
-    // labels of the original vertices, one array of n0 per level; in a batch, the arrays
-    // are shared by the graphs' results (graph g's labels start at gvptr[g])
-    std::shared_ptr<LabelStore> store;
-    if (batch) {
-        store = std::make_shared<LabelStore>();
-        store->ff = cfg.free;
-        store->ctx = cfg.alloc_ctx;
-        store->device = h->device;
-        for (int g = 0; g < NG; g++) out[g]->store = store;
-    }
-    const int32_t *prev_labels = nullptr;
-    // per-graph state: in the current level's graph, finished, previous level's Qn
-    std::vector<char> active(NG, 1), rec(NG, 0), keep(NG, 0);
-    std::vector<i128> qn_prev_level(NG, 0);
-    std::vector<int64_t> visits(NG, 0);
-    for (int g = 0; g < NG; g++)
-        if (h_gptr[g + 1] == h_gptr[g]) active[g] = 0;  // an empty graph has no phase
-    std::vector<LevelCtl> h_ctl(NG);
-    int64_t edge_visits = 0, sweeps_launched = 0;
-    double alg_bytes = 0.0;
-    u64 cand_all = 0;
-    LevelCtl *ctl_dev = batch ? d_ctls.p : &d_sc->ctl;
-    SweepStats *st_dev = batch ? d_stats.p : &d_sc->st;
-    BatchCtx bc;
-    if (batch) {
-        bc.gtw = (const i64 *)d_gtw.p;
-        bc.gctl = d_ctls.p;
-    }
-
-    for (int level = 0; level < cfg.max_levels; level++) {
-        const int64_t n = G.n;
-        if (level > 0) {
-            delta.swap(delta_next);
-            st.delta = delta.p;
-        }
-        bc.vg = batch ? d_vg.p : nullptr;
-        kernels += launch_init_state(n, st, s, lc);
-        if (cfg.vertex_following && (level == 0 || cfg.vf_all_levels))
-            kernels += launch_vertex_following(G, st, s, lc);
-
-        // degree bins (level 0 reuses the bins made for the row sums)
-        Bins bins;
-        if (level == 0 && reuse_bins0) {
-            bins = proto;
-            bins.list = bins0.list;
-            bins.counts = bins0.counts;
-            for (int b = 0; b <= kNumBins; b++) bins.off[b] = bins0.off[b];
-            for (int b = 0; b < kNumBins; b++) {
-                bins.nlist[b] = bins0.nlist[b];
-                bins.entries[b] = bins0.entries[b];
-            }
-        } else {
-            bins = make_bins(G, proto);
-        }
-        prep_huge(bins, false, 0, nullptr);
-
-        // phase controllers (graphs without a phase at this level start stopped)
-        int ninactive = 0;
-        for (int g = 0; g < NG; g++) {
-            LevelCtl &c = h_ctl[g];
-            memset(&c, 0, sizeof(c));
-            c.tw = h_tw[g];
-            c.theta_num = cfg.theta_num;
-            c.theta_den = cfg.theta_den;
-            c.max_iters = cfg.max_iters;
-            c.done = active[g] ? 0 : 1;
-            ninactive += !active[g];
-        }
+    if (n0 > 0) {
+        // row offsets must be sane before any row is read
+        E.kernels += launch_validate_rowptr(d_rp, n0, &E.d_sc->err, s, lc);
+        E.sync_scalars();
         if (batch) {
-            CK(cudaMemcpyAsync(d_ctls.p, h_ctl.data(), sizeof(LevelCtl) * NG,
+            DBuf<int64_t> d_v, d_e;
+            d_v.reset(&A, NG + 1);
+            d_e.reset(&A, NG + 1);
+            CK(cudaMemcpyAsync(d_v.p, src.vptr.data(), sizeof(int64_t) * (NG + 1),
                                cudaMemcpyHostToDevice, s));
-        } else {
-            h->pinned->ctl = h_ctl[0];
-            CK(cudaMemcpyAsync(&d_sc->ctl, &h->pinned->ctl, sizeof(LevelCtl),
-                               cudaMemcpyHostToDevice, s));
-            CK(cudaMemsetAsync(&d_sc->st, 0, sizeof(SweepStats), s));
-        }
-        h->pinned->ndone = ninactive;
-        CK(cudaMemcpyAsync(&d_sc->ndone, &h->pinned->ndone, sizeof(int32_t),
-                           cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(&d_sc->cand_total[0], 0, sizeof(u64) * 16, s));
-
-        // sweeps (Algorithm 1); one host read of the controllers' count per sweep
-        // algorithmic bytes of one sweep over the current bins (formula in louvain.h)
-        auto account_sweep = [&](const Bins &bb) {
-            const double per_entry = 8.0 + (double)G.wbytes;
-            for (int b = 0; b < kNumBins; b++) {
-                double kb = (double)bb.entries[b] * per_entry;
-                kb += b == 0 ? (double)n * 16.0 + (double)bb.nlist[0] * 24.0
-                             : (double)bb.nlist[b] * 36.0;
-                bytes_kernel[b] += kb;
-                alg_bytes += kb;
-                const int64_t rows = b == 0 ? n : bb.nlist[b];
-                for (int g = 0; g < NG; g++) {
-                    out[g]->bin_rows[b] += rows;
-                    out[g]->bin_entries[b] += bb.entries[b];
-                }
-            }
-        };
-        int sweeps = 0;
-        int ndone_binned = ninactive;
-        for (;;) {
-            kernels += launch_sweep(G, st, bins, TW, wide, narrow, st_dev, &d_sc->err, s, lc,
-                                    &tm, bc);
-            kernels += launch_decide(st_dev, ctl_dev, NG, tr_moved.p, tr_qn.p,
-                                     &d_sc->cand_total[0], &d_sc->ndone, s);
-            kernels += launch_apply(n, st, ctl_dev, bc.vg, s, lc);
-            sweeps++;
-            account_sweep(bins);
-            sync_scalars();
-            for (int b = 0; b < kNumBins; b++) {
-                if (tm.on) {
-                    float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, tm.ev[2 * b], tm.ev[2 * b + 1]));
-                    t_kernel[b] += ms;
-                }
-                launches_kernel[b] +=
-                    b == 0 ? 1 : (b == kChunkedBin ? bins.nchunks > 0 : bins.nlist[b] > 0);
-            }
-            const int ndone = h->pinned->ndone;
-            if (ndone >= NG) break;
-            if (sweeps > cfg.max_iters + 2)
-                throw LvErr{LOUVAIN_ERR_INTERNAL, "phase controller did not stop"};
-            if (batch && ndone > ndone_binned) {
-                // some graphs stopped: bin again without their rows
-                bins = make_bins(G, proto, d_vg.p, d_ctls.p);
-                prep_huge(bins, false, 0, nullptr);
-                ndone_binned = ndone;
-            }
-        }
-        sweeps_launched += sweeps;
-        if (batch) {
-            CK(cudaMemcpyAsync(h_ctl.data(), d_ctls.p, sizeof(LevelCtl) * NG,
+            E.kernels += launch_gather64(d_rp, d_v.p, NG + 1, d_e.p, s);
+            CK(cudaMemcpyAsync(src.eptr.data(), d_e.p, sizeof(int64_t) * (NG + 1),
                                cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
+            if (geptr)
+                for (int g = 0; g <= NG; g++)
+                    if (geptr[g] != src.eptr[g])
+                        throw LvErr{LOUVAIN_ERR_INDEX_RANGE, "graph_eptr[" + std::to_string(g) +
+                                                                 "] != row_ptr[graph_vptr[g]]"};
         } else {
-            h_ctl[0] = h->pinned->ctl;
+            src.eptr[1] = nnz;
         }
-        u64 cand_level[kNumBins];
-        for (int b = 0; b < kNumBins; b++) cand_level[b] = h->pinned->cand_total[b];
-        int max_iters_run = 0;
-        for (int g = 0; g < NG; g++)
-            if (active[g] && h_ctl[g].iters > max_iters_run) max_iters_run = h_ctl[g].iters;
-        if (max_iters_run > 0) {
-            const size_t cnt = (size_t)max_iters_run * NG;
-            h_tr_moved.resize(cnt);
-            h_tr_qn.resize(2 * cnt);
-            CK(cudaMemcpyAsync(h_tr_moved.data(), tr_moved.p, sizeof(i64) * cnt,
-                               cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(h_tr_qn.data(), tr_qn.p, sizeof(i64) * 2 * cnt,
-                               cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-        }
-        for (int g = 0; g < NG; g++) {
-            if (!active[g]) continue;
-            const int it = h_ctl[g].iters;
-            for (int t = 0; t < it; t++) {
-                const size_t e = (size_t)t * NG + g;
-                out[g]->trace.push_back(
-                    TraceRec{level, t + 1, h_tr_moved[e], limbs_to_i128(&h_tr_qn[2 * e])});
-            }
-            const int64_t nnz_g = h_gnnz[g + 1] - h_gnnz[g];
-            visits[g] += (int64_t)it * nnz_g;
-            edge_visits += (int64_t)it * nnz_g;
-        }
-        // candidate reads (8 bytes each) of the sweeps of this phase
-        for (int b = 0; b < kNumBins; b++) {
-            bytes_kernel[b] += 8.0 * (double)cand_level[b];
-            alg_bytes += 8.0 * (double)cand_level[b];
-            cand_all += cand_level[b];
-        }
-
-        // renumber (Sec. 5.1.2) -- labels of used communities in increasing order; labels
-        // of one graph are contiguous, so the scan also numbers each graph's communities
-        kernels += launch_renumber(n, size.p, nullptr, nullptr, new_id.p, scratch32.p, s);
-        std::vector<int64_t> kg(NG, 0);
-        if (batch) {
-            kernels += launch_gather_ids(new_id.p, d_gptr.p, NG + 1, d_base1.p, s);
-            CK(cudaMemcpyAsync(h_base1.data(), d_base1.p, sizeof(int64_t) * (NG + 1),
-                               cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            for (int g = 0; g < NG; g++) kg[g] = h_base1[g + 1] - h_base1[g];
-        } else {
-            kg[0] = read_one(new_id.p + n);
-        }
-        // record the level for every graph that merged something (a graph whose phase
-        // merged nothing is finished: no new level), then the outer test of Algorithm 2
-        int nrec = 0, nkeep = 0;
-        int64_t k_next = 0, n_keep = 0;
-        bool all_active_kept = true;
-        for (int g = 0; g < NG; g++) {
-            const int64_t ng = h_gptr[g + 1] - h_gptr[g];
-            rec[g] = active[g] && kg[g] < ng;
-            keep[g] = 0;
-            if (!rec[g]) {
-                if (active[g]) all_active_kept = false;
-                active[g] = 0;
-                continue;
-            }
-            nrec++;
-            const LevelCtl &hc = h_ctl[g];
-            LevelRec r;
-            r.ncomm = kg[g];
-            r.qn = limbs_to_i128(hc.qn_final);
-            r.qn_init = limbs_to_i128(hc.qn_init);
-            r.iters = hc.iters;
-            r.n = ng;
-            r.nnz = h_gnnz[g + 1] - h_gnnz[g];
-            r.hit_cap = hc.hit_cap;
-            out[g]->levels.push_back(r);
-            const bool stop =
-                (level >= 1 && host_below_threshold(r.qn, qn_prev_level[g], h_tw[g],
-                                                    cfg.theta_num, cfg.theta_den)) ||
-                level + 1 >= cfg.max_levels;
-            qn_prev_level[g] = r.qn;
-            if (stop) {
-                all_active_kept = false;
-                active[g] = 0;
-            } else {
-                keep[g] = 1;
-                nkeep++;
-                k_next += kg[g];
-                n_keep += ng;
-            }
-        }
-        if (nrec == 0) break;
-        int32_t *d_labels = (int32_t *)A.get(sizeof(int32_t) * (size_t)n0);
-        if (batch) {
-            store->arrays.push_back(d_labels);
-            for (int g = 0; g < NG; g++)
-                if (rec[g]) out[g]->levels.back().d_labels = d_labels + gvptr[g];
-        } else {
-            out[0]->levels.back().d_labels = d_labels;
-        }
-        // next-level numbering: the kept graphs' communities only
-        const int32_t *nid2 = new_id.p;
-        if (batch) {
-            std::vector<int32_t> hk(NG), hr(NG);
-            for (int g = 0; g < NG; g++) {
-                hr[g] = rec[g];
-                hk[g] = keep[g];
-            }
-            CK(cudaMemcpyAsync(d_rec.p, hr.data(), sizeof(int32_t) * NG, cudaMemcpyHostToDevice,
-                               s));
-            CK(cudaMemcpyAsync(d_keep.p, hk.data(), sizeof(int32_t) * NG,
-                               cudaMemcpyHostToDevice, s));
-            if (nkeep > 0 && !all_active_kept) {
-                if (!new_id2.p) new_id2.reset(&A, (size_t)n0 + 1);
-                kernels += launch_renumber(n, size.p, d_vg.p, d_keep.p, new_id2.p, scratch32.p, s);
-                nid2 = new_id2.p;
-            }
-            kernels += launch_compose(n0, d_vg0.p, d_rec.p, d_keep.p, level == 0 ? nullptr : map0.p,
-                                      map0.p, st.C, new_id.p, d_base1.p, nid2, d_labels, s, lc);
-            CK(cudaStreamSynchronize(s));  // host vectors above are copied before they go
-        } else {
-            kernels += launch_compose(n0, nullptr, nullptr, nullptr, prev_labels, nullptr, st.C,
-                                      new_id.p, nullptr, nullptr, d_labels, s, lc);
-            prev_labels = d_labels;
-        }
-        if (nkeep == 0) break;
-
-        // ---------------- induce the next graph (Sec. 5.1.2)
-        if (!c_csize.p) {
-            c_csize.reset(&A, n0);
-            c_moff.reset(&A, (size_t)n0 + 1);
-            c_cursor.reset(&A, n0);
-            c_members.reset(&A, n0);
-            c_mpre.reset(&A, (size_t)n0 + 1);
-            c_ccnt.reset(&A, n0);
-            c_tmp_col.reset(&A, (size_t)nnz);
-            c_tmp_w.reset(&A, (size_t)nnz);
-        }
-        CoarsenBufs cb;
-        cb.csize = c_csize.p;
-        cb.moff = c_moff.p;
-        cb.cursor = c_cursor.p;
-        cb.members = c_members.p;
-        cb.mpre = c_mpre.p;
-        cb.ccnt = c_ccnt.p;
-        cb.tmp_col = c_tmp_col.p;
-        cb.tmp_w = c_tmp_w.p;
-        cb.counts = &d_sc->ccounts[0];
-        cb.scratch32 = scratch32.p;
-        cb.scratch64 = scratch64.p;
-        if (tm.on) CK(cudaEventRecord(coarsen_ev[0], s));
-        Bins cbins = proto;
-        const int64_t k = k_next;
-        kernels += launch_coarsen_stage1(G, st, nid2, k, batch ? n_keep : n,
-                                         batch ? d_vg.p : nullptr, batch ? d_keep.p : nullptr,
-                                         batch ? d_vg_next.p : nullptr, delta_next.p, cb, cbins,
-                                         s, lc);
-        sync_scalars();
-        cbins.list = lists.p;  // the sweep's lists are free again
-        cbins.off[0] = cbins.off[1] = cbins.off[2] = 0;
-        for (int b = 0; b < kNumBins; b++) {
-            cbins.nlist[b] = b < 2 ? 0 : h->pinned->ccounts[b];
-            if (b >= 2) cbins.off[b + 1] = cbins.off[b] + cbins.nlist[b];
-        }
-        kernels += launch_coarsen_binfill(k, cb, cbins, s, lc);
-        prep_huge(cbins, true, k, &cb);
-        kernels += launch_coarsen_stage2(G, st, nid2, k, cb, cbins, narrow, &d_sc->err, s, lc);
-        g_rp_next.reset(&A, (size_t)k + 1);
-        kernels += launch_coarsen_rowptr(k, cb, g_rp_next.p, s);
-        sync_scalars();
-        const int64_t nnz_next = read_one(g_rp_next.p + k);
-        const int wb_next = tw_max <= (u64)INT32_MAX ? 4 : 8;
-        g_col_next.reset(&A, (size_t)nnz_next);
-        g_w_next.reset(&A, (size_t)nnz_next * wb_next);
-        kernels += launch_coarsen_compact(k, nnz_next, cb, g_rp_next.p, g_col_next.p,
-                                          g_w_next.p, wb_next, s, lc);
-        if (tm.on) {
-            CK(cudaEventRecord(coarsen_ev[1], s));
-            CK(cudaEventSynchronize(coarsen_ev[1]));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, coarsen_ev[0], coarsen_ev[1]));
-            t_coarsen += ms;
-        }
-        g_rp.swap(g_rp_next);
-        g_col.swap(g_col_next);
-        g_w.swap(g_w_next);
-        g_rp_next.release();
-        g_col_next.release();
-        g_w_next.release();
-        G.n = k;
-        G.nnz = nnz_next;
-        G.rp = g_rp.p;
-        G.col = g_col.p;
-        G.w = g_w.p;
-        G.wbytes = wb_next;
-        if (batch) {
-            // vertex and entry offsets of every graph in the next level's graph
-            d_vg.swap(d_vg_next);
-            kernels += launch_gather_ids(nid2, d_gptr.p, NG + 1, d_gptr_next.p, s);
-            d_gptr.swap(d_gptr_next);
-            kernels += launch_gather64(G.rp, d_gptr.p, NG + 1, d_gnnz.p, s);
-            CK(cudaMemcpyAsync(h_gptr.data(), d_gptr.p, sizeof(int64_t) * (NG + 1),
-                               cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(h_gnnz.data(), d_gnnz.p, sizeof(int64_t) * (NG + 1),
-                               cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-        } else {
-            h_gptr[1] = k;
-            h_gnnz[1] = nnz_next;
-        }
-        if (level == 0) {  // the input copies are no longer needed
-            rp_own.release();
-            col_own.release();
-            w_own.release();
-        }
+        std::vector<Member *> left;
+        E.add(std::move(src), left);
+        while (!E.idle()) E.step(left);
     }
-    sync_scalars();
-    const double wall = now_ms() - wall0;
-    for (int g = 0; g < NG; g++) {
-        louvain_result *res = out[g];
-        res->counters[0] = batch ? visits[g] : edge_visits;
-        res->counters[1] = sweeps_launched;
-        res->counters[2] = (int64_t)alg_bytes;
-        res->counters[3] = (int64_t)cand_all;
-        res->counters[4] = kernels;
-        if (tm.on) {
-            int dom = 0;
-            for (int b = 1; b < kNumBins; b++)
-                if (t_kernel[b] > t_kernel[dom]) dom = b;
-            double tot = 0;
-            for (int b = 0; b < kNumBins; b++) tot += t_kernel[b];
-            res->times[0] = tot;
-            res->times[4] = t_kernel[dom];
-            res->times[5] = t_kernel[0];
-            res->times[6] = t_kernel[1] + t_kernel[2];
-            res->times[7] = t_kernel[3] + t_kernel[4] + t_kernel[5] + t_kernel[6];
-            res->counters[5] = launches_kernel[dom];
-            res->counters[6] = (int64_t)bytes_kernel[dom];
-            res->counters[7] = dom;
-            res->times[1] = t_coarsen;
-        }
-        for (int b = 0; b < kNumBins; b++) {
-            res->bin_time[b] = t_kernel[b];
-            res->bin_launches[b] = launches_kernel[b];
-            res->bin_bytes[b] = bytes_kernel[b];
-        }
-        res->times[3] = wall;
-    }
+    CK(cudaStreamSynchronize(s));
+    for (auto &m : members) finish_result(m.get());
 }
+
+struct RunCtx {
+    cudaStream_t s = nullptr;
+    DevAlloc A;
+};
 
 }  // namespace
 
@@ -1125,8 +1366,7 @@ int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int3
     res->device = h->device;
     res->ff = h->cfg.free;
     res->ctx = h->cfg.alloc_ctx;
-    Runner R;
-    R.h = h;
+    RunCtx R;
     R.s = (cudaStream_t)stream;
     R.A.fa = h->cfg.alloc;
     R.A.ff = h->cfg.free;
@@ -1137,7 +1377,8 @@ int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int3
     try {
         CK(cudaSetDevice(h->device));
         std::vector<louvain_result *> outs{res};
-        R.run(n, row_ptr, col_idx, weights, ptr_kind, 1, nullptr, nullptr, outs);
+        run_engine(h, R.s, R.A, n, row_ptr, col_idx, weights, ptr_kind, 1, nullptr, nullptr,
+                   outs);
     } catch (const LvErr &e) {
         rc = e.code;
         h->err = e.msg;
@@ -1196,8 +1437,7 @@ int louvain_run_batch(louvain_handle *h, int32_t num_graphs, const int64_t *grap
         outs[g]->ff = h->cfg.free;
         outs[g]->ctx = h->cfg.alloc_ctx;
     }
-    Runner R;
-    R.h = h;
+    RunCtx R;
     R.s = (cudaStream_t)stream;
     R.A.fa = h->cfg.alloc;
     R.A.ff = h->cfg.free;
@@ -1207,7 +1447,8 @@ int louvain_run_batch(louvain_handle *h, int32_t num_graphs, const int64_t *grap
     launch_site() = nullptr;
     try {
         CK(cudaSetDevice(h->device));
-        R.run(n, row_ptr, col_idx, weights, ptr_kind, num_graphs, graph_vptr, graph_eptr, outs);
+        run_engine(h, R.s, R.A, n, row_ptr, col_idx, weights, ptr_kind, num_graphs, graph_vptr,
+                   graph_eptr, outs);
     } catch (const LvErr &e) {
         rc = e.code;
         h->err = e.msg;
@@ -1330,18 +1571,7 @@ int louvain_result_bin_stats(const louvain_result *r, int bin, double *time_ms,
 void louvain_result_free(louvain_result *r)
 {
     if (!r) return;
-    if (r->store) {  // a batch's label arrays go with the last of its results
-        r->store.reset();
-        delete r;
-        return;
-    }
-    cudaSetDevice(r->device);
-    for (LevelRec &L : r->levels) {
-        if (!L.d_labels) continue;
-        if (r->ff) r->ff(L.d_labels, r->ctx, nullptr);
-        else cudaFreeAsync(L.d_labels, nullptr);
-        L.d_labels = nullptr;
-    }
+    r->stores.clear();  // label arrays go with the last result that refers to them
     delete r;
 }
 

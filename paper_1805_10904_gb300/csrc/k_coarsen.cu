@@ -40,7 +40,7 @@ __global__ void k_coarsen_prep(int64_t n, const int32_t *size, const i64 *deg,
             const int32_t a = new_id[c];
             csize[a] = size[c];
             delta_next[a] = deg[c];
-            if (vg) vg_next[a] = vg[c];
+            if (vg_next) vg_next[a] = vg[c];
         }
     }
 }

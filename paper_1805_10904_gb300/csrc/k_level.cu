@@ -302,10 +302,12 @@ __device__ __forceinline__ int sole_neighbour(const int64_t *rp, const int32_t *
 // community; an isolated pair joins the smaller id.  Targets never follow anyone, so
 // the deg/size updates below commute.  Runs right after k_init_state.
 __global__ void k_vertex_following(int64_t n, const int64_t *rp, const int32_t *col,
-                                   const i64 *delta, int32_t *C, i64 *deg, int32_t *size)
+                                   const i64 *delta, int32_t *C, i64 *deg, int32_t *size,
+                                   const int32_t *vg, const int32_t *vf_on)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+        if (vg && !vf_on[vg[i]]) continue;  // that graph's level does not follow
         int32_t j;
         if (!sole_neighbour(rp, col, (int32_t)i, &j)) continue;
         int32_t j2;
@@ -321,11 +323,11 @@ __global__ void k_vertex_following(int64_t n, const int64_t *rp, const int32_t *
 }
 
 int launch_vertex_following(const DevGraph &g, const PhaseState &st, cudaStream_t s,
-                            const LaunchCfg &lc)
+                            const LaunchCfg &lc, const int32_t *vg, const int32_t *vf_on)
 {
     if (g.n == 0) return 0;
     k_vertex_following<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        g.n, g.rp, g.col, st.delta, st.C, st.deg, st.size);
+        g.n, g.rp, g.col, st.delta, st.C, st.deg, st.size, vg, vf_on);
     return 1;
 }
 
@@ -674,32 +676,105 @@ int launch_graph_ids(int64_t n, const int64_t *gptr, int G, int32_t *vg, cudaStr
     return 1;
 }
 
-// Labels of the original vertices (Sec. 5.1.2: a vertex's community at level l is the
-// community of the level-l vertex it was merged into).  m = map_in[v] (v itself when
-// map_in is null) is v's vertex at this level; out[v] = new_id1[C[m]] - base1[g].
-__global__ void k_compose(int64_t n0, const int32_t *vg0, const int32_t *rec, const int32_t *keep,
-                          const int32_t *map_in, int32_t *map_out, const int32_t *C,
-                          const int32_t *new_id1, const int64_t *base1, const int32_t *new_id2,
-                          int32_t *out)
+// ------------------------------------------------------------------ stacking graphs
+// Rows of a source CSR (int32 weights, or all 1) appended at vertex v_base / entry e_base of
+// a stacked CSR, with its columns shifted to the stacked numbering and its weights widened.
+template <typename WD>
+__global__ void k_append_rows(int64_t n_src, int64_t nnz_src, const int64_t *src_rp,
+                              const int32_t *src_col, const int32_t *src_w, int64_t v_base,
+                              int64_t e_base, int64_t *dst_rp, int32_t *dst_col, WD *dst_w)
 {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n0;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int g = vg0 ? vg0[v] : 0;
-        if (rec && !rec[g]) continue;
-        const int32_t c = C[map_in ? map_in[v] : (int32_t)v];
-        out[v] = new_id1[c] - (base1 ? (int32_t)base1[g] : 0);
-        if (map_out && (!keep || keep[g])) map_out[v] = new_id2[c];
+    const int64_t tot = n_src > nnz_src ? n_src : nnz_src;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < n_src) dst_rp[v_base + t] = src_rp[t] + e_base;
+        if (t < nnz_src) {
+            dst_col[e_base + t] = src_col[t] + (int32_t)v_base;
+            dst_w[e_base + t] = src_w ? (WD)src_w[t] : (WD)1;
+        }
     }
 }
 
-int launch_compose(int64_t n0, const int32_t *vg0, const int32_t *rec, const int32_t *keep,
-                   const int32_t *map_in, int32_t *map_out, const int32_t *C,
+int launch_append_rows(int64_t n_src, int64_t nnz_src, const int64_t *src_rp,
+                       const int32_t *src_col, const int32_t *src_w, int64_t v_base,
+                       int64_t e_base, int64_t *dst_rp, int32_t *dst_col, void *dst_w, int wbytes,
+                       cudaStream_t s, const LaunchCfg &lc)
+{
+    const int64_t tot = n_src > nnz_src ? n_src : nnz_src;
+    if (tot == 0) return 0;
+    if (wbytes == 4)
+        k_append_rows<int32_t><<<grid_for(tot, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+            n_src, nnz_src, src_rp, src_col, src_w, v_base, e_base, dst_rp, dst_col,
+            (int32_t *)dst_w);
+    else
+        k_append_rows<i64><<<grid_for(tot, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+            n_src, nnz_src, src_rp, src_col, src_w, v_base, e_base, dst_rp, dst_col,
+            (i64 *)dst_w);
+    return 1;
+}
+
+// slot m with off[m] <= o < off[m+1] (empty slots own nothing)
+__device__ __forceinline__ int slot_of(const int64_t *off, int M, int64_t o)
+{
+    int lo = 0, hi = M;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= o) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// maps[m][k] = vbase[m] + k for the k < off[m+1] - off[m] original vertices of graph m:
+// a graph entering at level 0 is its own level-0 graph.
+__global__ void k_map_init(int64_t tot, int M, const int64_t *off, int32_t *const *maps,
+                           const int64_t *vbase)
+{
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < tot;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int m = slot_of(off, M, o);
+        const int64_t k = o - off[m];
+        maps[m][k] = (int32_t)(vbase[m] + k);
+    }
+}
+
+int launch_map_init(int64_t tot, int M, const int64_t *off, int32_t *const *maps,
+                    const int64_t *vbase, cudaStream_t s, const LaunchCfg &lc)
+{
+    if (tot == 0) return 0;
+    k_map_init<<<grid_for(tot, kBlock, lc.max_blocks), kBlock, 0, s>>>(tot, M, off, maps, vbase);
+    return 1;
+}
+
+// Labels of the original vertices (Sec. 5.1.2: a vertex's community at level l is the
+// community of the level-l vertex it was merged into).  Original vertex o belongs to
+// graph m (off[m] <= o < off[m+1]); v = maps[m][o - off[m]] is its vertex at this level.
+// For recorded graphs out[o] = new_id1[C[v]] - base1[m]; for kept graphs maps[m] moves on
+// to the next level's vertex new_id2[C[v]].
+__global__ void k_compose(int64_t n0, int M, const int64_t *off, int32_t *const *maps,
+                          const int32_t *rec, const int32_t *keep, const int32_t *C,
+                          const int32_t *new_id1, const int64_t *base1, const int32_t *new_id2,
+                          int32_t *out)
+{
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n0;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int m = slot_of(off, M, o);
+        if (!rec[m]) continue;
+        int32_t *map = maps[m] + (o - off[m]);
+        const int32_t c = C[*map];
+        out[o] = new_id1[c] - (int32_t)base1[m];
+        if (keep[m]) *map = new_id2[c];
+    }
+}
+
+int launch_compose(int64_t n0, int M, const int64_t *off, int32_t *const *maps,
+                   const int32_t *rec, const int32_t *keep, const int32_t *C,
                    const int32_t *new_id1, const int64_t *base1, const int32_t *new_id2,
                    int32_t *out, cudaStream_t s, const LaunchCfg &lc)
 {
     if (n0 == 0) return 0;
     k_compose<<<grid_for(n0, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        n0, vg0, rec, keep, map_in, map_out, C, new_id1, base1, new_id2, out);
+        n0, M, off, maps, rec, keep, C, new_id1, base1, new_id2, out);
     return 1;
 }
 

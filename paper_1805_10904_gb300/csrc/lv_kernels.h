@@ -127,8 +127,11 @@ int launch_row_sums(const DevGraph &g, const Bins &b, const int32_t *vg, const i
                     i64 *delta, u64 *tw, unsigned *err, cudaStream_t s, const LaunchCfg &lc);
 int launch_check_symmetry(const DevGraph &g, unsigned *err, cudaStream_t s, const LaunchCfg &lc);
 int launch_init_state(int64_t n, const PhaseState &st, cudaStream_t s, const LaunchCfg &lc);
+// Vertex following (degree-one vertices join their neighbour; an isolated pair takes the
+// smaller label).  In a batch, only vertices whose graph has vf_on[vg[i]] follow.
 int launch_vertex_following(const DevGraph &g, const PhaseState &st, cudaStream_t s,
-                            const LaunchCfg &lc);
+                            const LaunchCfg &lc, const int32_t *vg = nullptr,
+                            const int32_t *vf_on = nullptr);
 // Two passes: count rows and entries per bin (then the host reads counts and sets off[]),
 // fill the list grouped by bin.  In a batch (vg, gctl given) rows of graphs whose phase has
 // stopped are left out of every bin.
@@ -154,13 +157,21 @@ int launch_gather_ids(const int32_t *a, const int64_t *idx, int cnt, int64_t *ou
 // vg[v] = graph of vertex v from the vertex offsets gptr[0..G] of a batch.
 int launch_graph_ids(int64_t n, const int64_t *gptr, int G, int32_t *vg, cudaStream_t s,
                      const LaunchCfg &lc);
-// Labels of the original vertices.  For every v (graph g = vg0[v], 0 when vg0 is null) with
-// rec[g] (all when rec is null): m = map_in[v] (v when map_in is null) is v's vertex at this
-// level, out[v] = new_id1[C[m]] - base1[g] (base1 null: 0), and, when map_out is given and
-// keep[g] (all when keep is null), map_out[v] = new_id2[C[m]] (v's vertex at the next level).
-// map_in and map_out may be the same array.
-int launch_compose(int64_t n0, const int32_t *vg0, const int32_t *rec, const int32_t *keep,
-                   const int32_t *map_in, int32_t *map_out, const int32_t *C,
+// Appends a source CSR (int32 weights, NULL = all 1) at (v_base, e_base) of a stacked CSR
+// whose weights are wbytes wide; columns are shifted by v_base.  dst_rp[n] is the caller's.
+int launch_append_rows(int64_t n_src, int64_t nnz_src, const int64_t *src_rp,
+                       const int32_t *src_col, const int32_t *src_w, int64_t v_base,
+                       int64_t e_base, int64_t *dst_rp, int32_t *dst_col, void *dst_w, int wbytes,
+                       cudaStream_t s, const LaunchCfg &lc);
+// Original-vertex maps of M graphs entering at level 0: maps[m][k] = vbase[m] + k for the
+// off[m+1] - off[m] vertices of graph m (off, maps, vbase are device arrays).
+int launch_map_init(int64_t tot, int M, const int64_t *off, int32_t *const *maps,
+                    const int64_t *vbase, cudaStream_t s, const LaunchCfg &lc);
+// Labels of the original vertices of M graphs (original vertex o of graph m at
+// off[m] <= o < off[m+1], its current vertex maps[m][o - off[m]]): for rec[m],
+// out[o] = new_id1[C[v]] - base1[m]; for keep[m], the map moves to new_id2[C[v]].
+int launch_compose(int64_t n0, int M, const int64_t *off, int32_t *const *maps,
+                   const int32_t *rec, const int32_t *keep, const int32_t *C,
                    const int32_t *new_id1, const int64_t *base1, const int32_t *new_id2,
                    int32_t *out, cudaStream_t s, const LaunchCfg &lc);
 
