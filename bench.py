@@ -55,6 +55,13 @@ def parse_args(argv=None):
                         "one graph at a time (0: skip)")
     p.add_argument("--batch-only", action="store_true",
                    help="time only the batch workload (its own JSON line)")
+    p.add_argument("--serve-requests", type=int, default=0,
+                   help="also run the serving workload with this many requests (0: skip)")
+    p.add_argument("--serve-only", action="store_true",
+                   help="run only the serving workload (its own JSON line)")
+    p.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
+    p.add_argument("--serve-budget-gb", type=float, default=120.0)
+    p.add_argument("--serve-slots", type=int, default=256)
     return p.parse_args(argv)
 
 
@@ -345,6 +352,113 @@ def run_batch_workload(args, lv, dev, stream, steps, warmup):
     }
 
 
+SERVE_WORKLOAD = ("serving: Poisson arrivals; half R-MAT graphs of scale uniform in 10-21 (edge "
+                  "factor 16, a=0.57 b=0.19 c=0.19), half planted partitions as in the mixed "
+                  "batch; int32 weights uniform in [1, 16]; requests drawn with replacement "
+                  "from a pool of 48 distinct graphs (2 R-MAT per scale, 24 planted "
+                  "partitions); HBM admission budget and slot count as stated")
+
+
+def serve_pool(seed=4):
+    import numpy as np
+    import graphgen as gg
+    rmat = {s: [gg.rmat(s, 16, 0.57, 0.19, 0.19, 1, 16, seed=gg.graph_seed(seed, 100 * s + k))
+                for k in range(2)] for s in range(10, 22)}
+    sbm = []
+    for p in gg.batch_mix_params(48, seed=seed)[0::2]:
+        _, n, b, p_in, p_out, gs = p
+        sbm.append(gg.sbm(n, b, p_in, p_out, 1, 16, gs))
+    return rmat, sbm
+
+
+def run_serve_workload(args, lv, dev):
+    """Requests arrive as a Poisson stream and are served by the request loop; reports
+    p50/p99 submit-to-finish latency and graphs/s, against the same requests run one at a
+    time with louvain_run, and checks a sample of results against their plain runs."""
+    import threading
+    import numpy as np
+    import torch
+    import graphgen as gg
+    rmat, sbm = serve_pool()
+    rng = np.random.Generator(np.random.PCG64(gg.graph_seed(4, 0)))
+    nreq = args.serve_requests
+    picks = []
+    for k in range(nreq):
+        if rng.random() < 0.5:
+            s = int(rng.integers(10, 22))
+            picks.append(rmat[s][int(rng.integers(0, 2))])
+        else:
+            picks.append(sbm[int(rng.integers(0, len(sbm)))])
+    gaps = rng.exponential(1.0 / args.serve_rate, size=nreq)
+    h = lv.Louvain(dev.index, torch_alloc=False)
+    # warm-up: a few requests through the loop
+    h.serve_open(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
+    for t in [h.submit(g.rp, g.col, g.w) for g in (rmat[14][0], sbm[0], rmat[18][1])]:
+        h.poll(t, -1).close()
+    tickets = [None] * nreq
+    t_sub = [0.0] * nreq
+
+    def producer():
+        t0 = time.perf_counter()
+        due = 0.0
+        for k, g in enumerate(picks):
+            due += gaps[k]
+            wait = t0 + due - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            t_sub[k] = time.perf_counter()
+            tickets[k] = h.submit(g.rp, g.col, g.w)
+
+    th = threading.Thread(target=producer)
+    start = time.perf_counter()
+    th.start()
+    lat, waits, t_fin = [], [], []
+    sample = {}
+    for k in range(nreq):
+        while tickets[k] is None:
+            time.sleep(0.0005)
+        r = h.poll(tickets[k], -1)
+        t_fin.append(time.perf_counter())
+        _, tm = r.counters()
+        lat.append(float(tm[3]))
+        waits.append(float(tm[2]))
+        if k % max(1, nreq // 16) == 0:
+            sample[k] = [(r.level(l).qn, r.labels(l)) for l in range(r.num_levels)]
+        r.close()
+    th.join()
+    span = max(t_fin) - start
+    h.serve_close()
+    # the same requests one at a time, inputs resident on the device
+    uniq = {id(g): tuple(torch.from_numpy(a).to(dev) for a in (g.rp, g.col, g.w)) for g in picks}
+    hp = lv.Louvain(dev.index)
+    for g in (rmat[14][0], sbm[0]):
+        hp.run(*uniq.get(id(g), tuple(torch.from_numpy(a).to(dev) for a in (g.rp, g.col, g.w))))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    identical = True
+    for k, g in enumerate(picks):
+        r = hp.run(*uniq[id(g)])
+        if k in sample:
+            got = [(r.level(l).qn, r.labels(l)) for l in range(r.num_levels)]
+            identical = identical and len(got) == len(sample[k]) and all(
+                a[0] == b[0] and np.array_equal(a[1], b[1]) for a, b in zip(got, sample[k]))
+        r.close()
+    torch.cuda.synchronize(dev)
+    plain_s = time.perf_counter() - t0
+    lat = np.asarray(lat)
+    return {
+        "workload": SERVE_WORKLOAD, "requests": nreq, "rate_per_s": args.serve_rate,
+        "budget_gb": args.serve_budget_gb, "slots": args.serve_slots,
+        "total_entries": int(sum(g.nnz for g in picks)),
+        "latency_ms_p50": float(np.percentile(lat, 50)),
+        "latency_ms_p99": float(np.percentile(lat, 99)),
+        "admission_wait_ms_p99": float(np.percentile(np.asarray(waits), 99)),
+        "graphs_per_s_served": nreq / span, "served_span_s": span,
+        "graphs_per_s_plain": nreq / plain_s, "plain_span_s": plain_s,
+        "identical_to_plain_sample": identical, "sample_size": len(sample),
+    }
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -360,6 +474,11 @@ def run_native(args):
         b = run_batch_workload(args, lv, dev, stream, args.steps, args.warmup)
         if rank == 0:
             print(json.dumps({"batch": b}), flush=True)
+        return 0
+    if args.serve_only:
+        sv = run_serve_workload(args, lv, dev)
+        if rank == 0:
+            print(json.dumps({"serve": sv}), flush=True)
         return 0
     g = make_graph(args.scale)
     rp = torch.from_numpy(g.rp).to(dev)
@@ -419,6 +538,7 @@ def run_native(args):
     e2e = run_e2e(args, g, lv, local, stream, world, dev) if not args.no_e2e else None
     batch = (run_batch_workload(args, lv, dev, stream, 2, 1) if args.batch_graphs > 0
              else None)
+    serve = run_serve_workload(args, lv, dev) if args.serve_requests > 0 else None
 
     if rank != 0:
         if world > 1:
@@ -463,7 +583,7 @@ def run_native(args):
             for b, a in sorted(bins_acc.items()) if a["launches"]},
         "coarsen_ms_per_step": round(coarsen_ms / args.steps, 4),
         "e2e": e2e,
-        "batch": batch,
+        "batch": batch, "serve": serve,
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -158,6 +158,47 @@ int louvain_run_batch(louvain_handle *h, int32_t num_graphs, const int64_t *grap
                       const int64_t *graph_eptr, const int64_t *row_ptr, const int32_t *col_idx,
                       const int32_t *weights, int ptr_kind, void *stream, louvain_result **out);
 
+/* ---------------------------------------------------------------- serving */
+/* A request loop on the handle for graphs that arrive over time (this library's addition;
+ * the method itself is defined for one graph).  Submitted graphs wait in a FIFO queue and
+ * are admitted while fewer than max_slots graphs are in flight and the sum of their
+ * estimated device footprints (below) stays within hbm_budget_bytes.  An admitted graph is
+ * copied to the device and checked on a stream of its own, then joins the graphs already
+ * running at their next level boundary: every level step runs one set of launches for all
+ * resident graphs (as louvain_run_batch does), and each graph keeps its own 2W, controllers
+ * and outer test, so its result is identical to louvain_run on it alone.  When its run ends
+ * its result is ready for louvain_poll and its slot and budget go back to the queue.
+ * Footprint estimate: 8 (n + 1) + 8 nnz + 160 n + 40 nnz bytes.  Two native threads (upload
+ * and engine) serve the handle; device memory comes from the handle's allocator on the
+ * serving streams.  While serving is open, louvain_run and louvain_run_batch on this handle
+ * return INVALID_ARG.  Errors: INVALID_ARG (already open, max_slots < 1, budget 0), CUDA,
+ * OOM. */
+int louvain_serve_open(louvain_handle *h, uint64_t hbm_budget_bytes, int max_slots);
+
+/* Queue one graph (arrays as in louvain_run, HOST pointers only; they are copied before
+ * the call returns).  *ticket identifies it for louvain_poll.  Errors: INVALID_ARG (not
+ * serving, device pointers, closing), INDEX_RANGE (row_ptr[0] != 0 or row_ptr[n] < 0),
+ * TOO_LARGE, OOM.  Graphs failing the checks of louvain_run (INDEX_RANGE, BAD_WEIGHT,
+ * NOT_SYMMETRIC / DUPLICATE_EDGE with checks = 2, TOO_LARGE) and graphs whose footprint
+ * exceeds the whole budget (REJECTED) report their error through louvain_poll. */
+int louvain_submit(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                   const int32_t *weights, int ptr_kind, uint64_t *ticket);
+
+/* Wait up to wait_ms (0: do not wait, < 0: wait until done) for the graph of `ticket`.
+ * Returns OK with *out = its result (freed with louvain_result_free; times_ms[3] of
+ * louvain_result_counters is its submit-to-finish latency and times_ms[2] its wait for
+ * admission), PENDING if it is not done yet (poll again), or the graph's error; a ticket is
+ * consumed by the call that returns its outcome.  INVALID_ARG for an unknown ticket. */
+int louvain_poll(louvain_handle *h, uint64_t ticket, int wait_ms, louvain_result **out);
+
+/* status[0] = bytes admitted (footprints in flight), [1] slots in use, [2] graphs queued for
+ * admission, [3] finished graphs not yet polled. */
+int louvain_serve_status(const louvain_handle *h, int64_t status[4]);
+
+/* Stop accepting graphs, finish every graph already submitted, free the results that were
+ * never polled and end the request loop.  louvain_destroy closes an open loop itself. */
+int louvain_serve_close(louvain_handle *h);
+
 /* ---------------------------------------------------------------- results */
 /* Number of recorded levels (0 when nothing merged, e.g. no edges). */
 int louvain_result_num_levels(const louvain_result *r);

@@ -11,11 +11,16 @@
 #include <algorithm>
 #include <chrono>
 #include <climits>
-#include <memory>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/louvain.h"
@@ -174,6 +179,7 @@ struct louvain_handle {
     std::string err;
     LaunchCfg lc;
     Scalars *pinned = nullptr;
+    void *server = nullptr;  // the open request loop (louvain_serve_open), if any
 };
 
 // Label arrays of one engine step (every graph that recorded a level in it has its labels
@@ -1208,6 +1214,285 @@ void run_engine(louvain_handle *h, cudaStream_t s, DevAlloc &A, int64_t n0, cons
     for (auto &m : members) finish_result(m.get());
 }
 
+// ---------------------------------------------------------------------- serving
+//
+// A request loop for graphs that arrive over time.  Submitted graphs wait in a FIFO queue
+// and are admitted while a slot is free and their estimated device footprint fits the
+// budget; an upload thread copies and vets each admitted graph on a stream of its own, and
+// the engine thread lets every vetted graph join at its next step boundary, so a graph that
+// arrives while others run shares the following steps' launches with them.  A graph leaves
+// when its own run ends; its result is then ready for louvain_poll and its slot and budget
+// go back to the queue.
+
+enum { kQueued, kUploading, kReady, kResident, kDone };
+
+struct Request {
+    uint64_t ticket = 0;
+    int64_t n = 0, nnz = 0;
+    std::vector<int64_t> rp;
+    std::vector<int32_t> col, w;  // w empty: every weight is 1
+    uint64_t footprint = 0;
+    int state = kQueued;
+    int rc = LOUVAIN_OK;
+    std::string err;
+    louvain_result *res = nullptr;
+    double t_submit = 0.0, t_admit = 0.0;
+    int64_t *d_rp = nullptr;
+    int32_t *d_col = nullptr, *d_w = nullptr;
+    Member member;
+};
+
+// Device bytes a graph may hold while it is served: its device copy (row offsets, columns,
+// weights) and its share of the engine's buffers, about 160 bytes a vertex (state, bins,
+// induction and label arrays) and 40 bytes an entry (stacked copy, induction scratch and
+// the next level's graph).
+uint64_t footprint_estimate(int64_t n, int64_t nnz)
+{
+    return (uint64_t)(8 * (n + 1) + 8 * nnz) + 160ull * (uint64_t)n + 40ull * (uint64_t)nnz;
+}
+
+struct Server {
+    louvain_handle *h = nullptr;
+    uint64_t budget = 0, in_use = 0;
+    int max_slots = 0, slots_used = 0, n_uploading = 0;
+    std::mutex mu;
+    std::condition_variable cv;  // any change of the queues or of a request's state
+    std::deque<Request *> queue;      // submitted, waiting for admission
+    std::deque<Request *> to_upload;  // admitted, upload not started
+    std::vector<Request *> ready;     // uploaded and vetted, waiting to join
+    std::unordered_map<uint64_t, Request *> tickets;
+    uint64_t next_ticket = 1;
+    bool stopping = false;
+    std::thread uploader, worker;
+    cudaStream_t compute = nullptr, copy = nullptr;
+    DevAlloc A_compute, A_copy;
+    unsigned *d_chk = nullptr;  // upload checks: error bits, then 2W (u64) at d_chk + 2
+
+    // FIFO admission under the lock; a graph larger than the whole budget is rejected
+    void admit_locked()
+    {
+        while (!queue.empty()) {
+            Request *r = queue.front();
+            if (r->footprint > budget) {
+                queue.pop_front();
+                r->rc = LOUVAIN_ERR_REJECTED;
+                r->err = "graph footprint " + std::to_string(r->footprint) +
+                         " bytes exceeds the serving budget";
+                r->state = kDone;
+                continue;
+            }
+            if (slots_used >= max_slots || in_use + r->footprint > budget) break;
+            queue.pop_front();
+            slots_used++;
+            in_use += r->footprint;
+            n_uploading++;
+            r->state = kUploading;
+            r->t_admit = now_ms();
+            to_upload.push_back(r);
+        }
+        cv.notify_all();
+    }
+
+    void release_device(Request *r, DevAlloc &A)
+    {
+        A.put(r->d_rp);
+        A.put(r->d_col);
+        A.put(r->d_w);
+        r->d_rp = nullptr;
+        r->d_col = nullptr;
+        r->d_w = nullptr;
+    }
+
+    // the request leaves (done or failed): its slot and budget go back to the queue
+    void finish_locked(Request *r, int rc, const std::string &msg)
+    {
+        r->rc = rc;
+        r->err = msg;
+        r->state = kDone;
+        slots_used--;
+        in_use -= r->footprint;
+        admit_locked();
+    }
+
+    void upload_one(Request *r)
+    {
+        const LaunchCfg &lc = h->lc;
+        cudaStream_t s = copy;
+        r->d_rp = (int64_t *)A_copy.get(sizeof(int64_t) * (size_t)(r->n + 1));
+        r->d_col = (int32_t *)A_copy.get(sizeof(int32_t) * (size_t)r->nnz);
+        r->d_w = (int32_t *)A_copy.get(sizeof(int32_t) * (size_t)r->nnz);
+        CK(cudaMemcpyAsync(r->d_rp, r->rp.data(), sizeof(int64_t) * (size_t)(r->n + 1),
+                           cudaMemcpyHostToDevice, s));
+        if (r->nnz) {
+            CK(cudaMemcpyAsync(r->d_col, r->col.data(), sizeof(int32_t) * (size_t)r->nnz,
+                               cudaMemcpyHostToDevice, s));
+            if (!r->w.empty())
+                CK(cudaMemcpyAsync(r->d_w, r->w.data(), sizeof(int32_t) * (size_t)r->nnz,
+                                   cudaMemcpyHostToDevice, s));
+            else
+                launch_fill_ones(r->d_w, r->nnz, s, lc);
+        }
+        // vet the graph alone, so that a bad graph never reaches the others' steps
+        CK(cudaMemsetAsync(d_chk, 0, 16, s));
+        launch_validate_rowptr(r->d_rp, r->n, d_chk, s, lc);
+        unsigned hv[4] = {0, 0, 0, 0};
+        CK(cudaMemcpyAsync(hv, d_chk, sizeof(hv), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!hv[0]) {
+            launch_check_rows(r->n, r->d_rp, r->d_col, r->d_w, d_chk, (u64 *)(d_chk + 2), s, lc);
+            if (h->cfg.checks >= 2) {
+                DevGraph g;
+                g.n = r->n;
+                g.nnz = r->nnz;
+                g.rp = r->d_rp;
+                g.col = r->d_col;
+                g.w = r->d_w;
+                g.wbytes = 4;
+                launch_check_symmetry(g, d_chk, s, lc);
+            }
+            CK(cudaMemcpyAsync(hv, d_chk, sizeof(hv), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        CK(cudaGetLastError());
+        if (hv[0]) {
+            std::string msg;
+            const int code = map_err_bits(hv[0], msg);
+            throw LvErr{code, msg};
+        }
+        u64 tw = 0;
+        memcpy(&tw, &hv[2], sizeof(tw));
+        if (tw > ((u64)1 << 62)) throw LvErr{LOUVAIN_ERR_TOO_LARGE, "sum of weights above 2^62"};
+    }
+
+    void upload_loop()
+    {
+        cudaSetDevice(h->device);
+        for (;;) {
+            Request *r = nullptr;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return !to_upload.empty() || (stopping && queue.empty()); });
+                if (to_upload.empty()) return;
+                r = to_upload.front();
+                to_upload.pop_front();
+            }
+            int rc = LOUVAIN_OK;
+            std::string msg;
+            try {
+                upload_one(r);
+            } catch (const LvErr &e) {
+                rc = e.code;
+                msg = e.msg;
+                cudaStreamSynchronize(copy);
+                cudaGetLastError();
+            } catch (const std::bad_alloc &) {
+                rc = LOUVAIN_ERR_OOM;
+                msg = "host allocation failed";
+            }
+            std::vector<int64_t>().swap(r->rp);  // the host copy is no longer needed
+            std::vector<int32_t>().swap(r->col);
+            std::vector<int32_t>().swap(r->w);
+            if (rc != LOUVAIN_OK) release_device(r, A_copy);
+            std::lock_guard<std::mutex> lk(mu);
+            n_uploading--;
+            if (rc == LOUVAIN_OK) {
+                r->state = kReady;
+                ready.push_back(r);
+                cv.notify_all();
+            } else {
+                finish_locked(r, rc, msg);
+            }
+        }
+    }
+
+    void work_loop()
+    {
+        cudaSetDevice(h->device);
+        std::unique_ptr<Engine> E;
+        auto fresh_engine = [&] {
+            E.reset();
+            E.reset(new Engine(h, compute, A_compute, true));
+        };
+        try {
+            fresh_engine();
+        } catch (const LvErr &) {
+            cudaGetLastError();
+        }
+        std::vector<Request *> in_engine;
+        for (;;) {
+            std::vector<Request *> take;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] {
+                    return !ready.empty() || (E && !E->idle()) ||
+                           (stopping && queue.empty() && to_upload.empty() && n_uploading == 0);
+                });
+                take.swap(ready);
+                if (take.empty() && (!E || E->idle())) return;  // stopping and drained
+            }
+            std::vector<Member *> done;
+            int rc = LOUVAIN_OK;
+            std::string msg;
+            try {
+                if (!E) throw LvErr{LOUVAIN_ERR_CUDA, "serving engine could not start"};
+                for (Request *r : take) {
+                    r->state = kResident;
+                    r->member = Member();
+                    r->member.res = r->res;
+                    r->member.t0 = r->t_submit;
+                    r->member.tag = r;
+                    Source src;
+                    src.n = r->n;
+                    src.nnz = r->nnz;
+                    src.rp = r->d_rp;
+                    src.col = r->d_col;
+                    src.w = r->d_w;
+                    src.vptr = {0, r->n};
+                    src.eptr = {0, r->nnz};
+                    src.members = {&r->member};
+                    in_engine.push_back(r);
+                    E->add(std::move(src), done);
+                }
+                if (!E->idle()) E->step(done);
+                CK(cudaStreamSynchronize(compute));
+            } catch (const LvErr &e) {
+                rc = e.code;
+                msg = e.msg;
+            } catch (const std::bad_alloc &) {
+                rc = LOUVAIN_ERR_OOM;
+                msg = "host allocation failed";
+            }
+            if (rc != LOUVAIN_OK) {
+                // the engine state is lost: every graph in it fails with the error
+                cudaStreamSynchronize(compute);
+                cudaGetLastError();
+                done.clear();
+                for (Request *r : in_engine) done.push_back(&r->member);
+                try {
+                    fresh_engine();
+                } catch (const LvErr &) {
+                    E.reset();
+                    cudaGetLastError();
+                }
+            }
+            for (Member *m : done) {
+                Request *r = (Request *)m->tag;
+                if (rc == LOUVAIN_OK) {
+                    finish_result(m);
+                    r->res->times[2] = r->t_admit - r->t_submit;
+                } else if (m->map) {
+                    A_compute.put(m->map);
+                    m->map = nullptr;
+                }
+                release_device(r, A_compute);
+                in_engine.erase(std::find(in_engine.begin(), in_engine.end(), r));
+                std::lock_guard<std::mutex> lk(mu);
+                finish_locked(r, rc, msg);
+            }
+        }
+    }
+};
+
 struct RunCtx {
     cudaStream_t s = nullptr;
     DevAlloc A;
@@ -1337,6 +1622,7 @@ int louvain_create(const louvain_config *cfg, int device, louvain_handle **out)
 void louvain_destroy(louvain_handle *h)
 {
     if (!h) return;
+    if (h->server) louvain_serve_close(h);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
 }
@@ -1353,6 +1639,10 @@ int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int3
         return LOUVAIN_ERR_INVALID_ARG;
     }
     *out = nullptr;
+    if (h->server) {
+        h->err = "the handle is serving: use louvain_submit / louvain_poll";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
     if (n < 0 || !row_ptr || (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE)) {
         h->err = "bad n, row_ptr or ptr_kind";
         return LOUVAIN_ERR_INVALID_ARG;
@@ -1408,6 +1698,10 @@ int louvain_run_batch(louvain_handle *h, int32_t num_graphs, const int64_t *grap
         return LOUVAIN_ERR_INVALID_ARG;
     }
     for (int g = 0; g < num_graphs; g++) out[g] = nullptr;
+    if (h->server) {
+        h->err = "the handle is serving: use louvain_submit / louvain_poll";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
     if (num_graphs > LOUVAIN_MAX_BATCH_GRAPHS) {
         h->err = "more graphs than LOUVAIN_MAX_BATCH_GRAPHS";
         return LOUVAIN_ERR_TOO_LARGE;
@@ -1463,6 +1757,210 @@ int louvain_run_batch(louvain_handle *h, int32_t num_graphs, const int64_t *grap
         return rc;
     }
     for (int g = 0; g < num_graphs; g++) out[g] = outs[g];
+    return LOUVAIN_OK;
+}
+
+
+// ---------------------------------------------------------------- serving
+
+int louvain_serve_open(louvain_handle *h, uint64_t hbm_budget_bytes, int max_slots)
+{
+    if (!h) return LOUVAIN_ERR_INVALID_ARG;
+    h->err.clear();
+    if (h->server) {
+        h->err = "serving is already open on this handle";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (max_slots < 1 || hbm_budget_bytes == 0) {
+        h->err = "max_slots must be >= 1 and the budget above 0";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    Server *S = new (std::nothrow) Server();
+    if (!S) return LOUVAIN_ERR_OOM;
+    S->h = h;
+    S->budget = hbm_budget_bytes;
+    S->max_slots = max_slots;
+    if (cudaSetDevice(h->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        if (S->compute) cudaStreamDestroy(S->compute);
+        delete S;
+        h->err = "could not create the serving streams";
+        return LOUVAIN_ERR_CUDA;
+    }
+    for (DevAlloc *A : {&S->A_compute, &S->A_copy}) {
+        A->fa = h->cfg.alloc;
+        A->ff = h->cfg.free;
+        A->ctx = h->cfg.alloc_ctx;
+    }
+    S->A_compute.s = S->compute;
+    S->A_copy.s = S->copy;
+    try {
+        S->d_chk = (unsigned *)S->A_copy.get(16);
+        S->uploader = std::thread(&Server::upload_loop, S);
+        S->worker = std::thread(&Server::work_loop, S);
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->stopping = true;
+            S->cv.notify_all();
+        }
+        if (S->uploader.joinable()) S->uploader.join();
+        if (S->worker.joinable()) S->worker.join();
+        if (S->d_chk) S->A_copy.put(S->d_chk);
+        cudaStreamSynchronize(S->copy);
+        cudaStreamDestroy(S->compute);
+        cudaStreamDestroy(S->copy);
+        delete S;
+        cudaGetLastError();
+        h->err = "could not start serving";
+        return LOUVAIN_ERR_OOM;
+    }
+    h->server = S;
+    return LOUVAIN_OK;
+}
+
+int louvain_submit(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                   const int32_t *weights, int ptr_kind, uint64_t *ticket)
+{
+    if (!h) return LOUVAIN_ERR_INVALID_ARG;
+    Server *S = (Server *)h->server;
+    h->err.clear();
+    if (!S || !ticket) {
+        h->err = !S ? "serving is not open" : "ticket is NULL";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (ptr_kind != LOUVAIN_PTR_HOST || n < 0 || !row_ptr) {
+        h->err = "louvain_submit takes host arrays (ptr_kind LOUVAIN_PTR_HOST) and n >= 0";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (n > INT32_MAX) {
+        h->err = "n above 2^31 - 1";
+        return LOUVAIN_ERR_TOO_LARGE;
+    }
+    if (row_ptr[0] != 0 || row_ptr[n] < 0) {
+        h->err = "row_ptr[0] must be 0 and row_ptr[n] >= 0";
+        return LOUVAIN_ERR_INDEX_RANGE;
+    }
+    const int64_t nnz = row_ptr[n];
+    if (nnz > 0 && !col_idx) {
+        h->err = "col_idx is NULL";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    Request *r = new (std::nothrow) Request();
+    louvain_result *res = new (std::nothrow) louvain_result();
+    if (!r || !res) {
+        delete r;
+        delete res;
+        return LOUVAIN_ERR_OOM;
+    }
+    try {
+        r->n = n;
+        r->nnz = nnz;
+        r->rp.assign(row_ptr, row_ptr + n + 1);
+        r->col.assign(col_idx, col_idx + nnz);
+        if (weights) r->w.assign(weights, weights + nnz);
+    } catch (const std::bad_alloc &) {
+        delete r;
+        delete res;
+        return LOUVAIN_ERR_OOM;
+    }
+    res->device = h->device;
+    res->ff = h->cfg.free;
+    res->ctx = h->cfg.alloc_ctx;
+    res->n0 = n;
+    r->res = res;
+    r->footprint = footprint_estimate(n, nnz);
+    r->t_submit = now_ms();
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stopping) {
+        delete r;
+        delete res;
+        h->err = "serving is closing";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    r->ticket = S->next_ticket++;
+    S->tickets[r->ticket] = r;
+    S->queue.push_back(r);
+    S->admit_locked();
+    *ticket = r->ticket;
+    return LOUVAIN_OK;
+}
+
+int louvain_poll(louvain_handle *h, uint64_t ticket, int wait_ms, louvain_result **out)
+{
+    if (!h) return LOUVAIN_ERR_INVALID_ARG;
+    Server *S = (Server *)h->server;
+    if (!S || !out) {
+        h->err = !S ? "serving is not open" : "out is NULL";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    Request *r = nullptr;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        auto it = S->tickets.find(ticket);
+        if (it == S->tickets.end()) {
+            h->err = "unknown ticket";
+            return LOUVAIN_ERR_INVALID_ARG;
+        }
+        r = it->second;
+        auto is_done = [&] { return r->state == kDone; };
+        if (wait_ms < 0) S->cv.wait(lk, is_done);
+        else if (wait_ms > 0) S->cv.wait_for(lk, std::chrono::milliseconds(wait_ms), is_done);
+        if (!is_done()) return LOUVAIN_PENDING;
+        S->tickets.erase(it);
+    }
+    const int rc = r->rc;
+    if (rc == LOUVAIN_OK) {
+        *out = r->res;
+    } else {
+        h->err = r->err;
+        louvain_result_free(r->res);
+    }
+    delete r;
+    return rc;
+}
+
+int louvain_serve_status(const louvain_handle *h, int64_t status[4])
+{
+    if (!h || !status) return LOUVAIN_ERR_INVALID_ARG;
+    Server *S = (Server *)h->server;
+    if (!S) return LOUVAIN_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    status[0] = (int64_t)S->in_use;
+    status[1] = S->slots_used;
+    status[2] = (int64_t)S->queue.size();
+    int64_t done = 0;
+    for (const auto &kv : S->tickets) done += kv.second->state == kDone;
+    status[3] = done;
+    return LOUVAIN_OK;
+}
+
+int louvain_serve_close(louvain_handle *h)
+{
+    if (!h) return LOUVAIN_ERR_INVALID_ARG;
+    Server *S = (Server *)h->server;
+    if (!S) return LOUVAIN_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stopping = true;
+        S->cv.notify_all();
+    }
+    S->uploader.join();
+    S->worker.join();
+    for (auto &kv : S->tickets) {  // finished but never polled
+        louvain_result_free(kv.second->res);
+        delete kv.second;
+    }
+    S->A_copy.put(S->d_chk);
+    cudaStreamSynchronize(S->copy);
+    cudaStreamSynchronize(S->compute);
+    cudaStreamDestroy(S->compute);
+    cudaStreamDestroy(S->copy);
+    delete S;
+    h->server = nullptr;
     return LOUVAIN_OK;
 }
 

@@ -35,6 +35,40 @@ int launch_validate_rowptr(const int64_t *rp, int64_t n, unsigned *err, cudaStre
     return 1;
 }
 
+// Entry checks of one graph on its own (columns in [0, n), weights >= 1) and its 2W, one
+// warp per row; used to vet a graph before it joins others.
+__global__ void __launch_bounds__(kBlock) k_check_rows(int64_t n, const int64_t *rp,
+                                                       const int32_t *col, const int32_t *w,
+                                                       unsigned *err, u64 *tw)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned bad = 0;
+    u64 sum = 0;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+            const int32_t j = col[k];
+            const i64 x = w ? (i64)w[k] : 1;
+            if (j < 0 || (int64_t)j >= n) bad |= ERRF_INDEX;
+            if (x < 1) bad |= ERRF_WEIGHT;
+            sum += (u64)x;
+        }
+    }
+    sum = sum_reduce(sum, 32);
+    if (lane == 0 && sum) atomicAdd(tw, sum);
+    if (bad) atomicOr(err, bad);
+}
+
+int launch_check_rows(int64_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
+                      unsigned *err, u64 *tw, cudaStream_t s, const LaunchCfg &lc)
+{
+    if (n == 0) return 0;
+    k_check_rows<<<grid_for(n, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(n, rp, col, w, err,
+                                                                           tw);
+    return 1;
+}
+
 __global__ void k_fill_ones(int32_t *w, int64_t nnz)
 {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;

@@ -119,6 +119,9 @@ size_t shared_table_bytes(int log2cap, bool narrow);
 int launch_validate_rowptr(const int64_t *rp, int64_t n, unsigned *err, cudaStream_t s,
                            const LaunchCfg &lc);
 int launch_fill_ones(int32_t *w, int64_t nnz, cudaStream_t s, const LaunchCfg &lc);
+// Columns in [0, n) and weights >= 1 of one graph (w NULL: all 1), *tw += its 2W.
+int launch_check_rows(int64_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
+                      unsigned *err, u64 *tw, cudaStream_t s, const LaunchCfg &lc);
 // Weighted degrees and 2W with column / weight checks, one thread, warp or CTA per row
 // according to the row's degree bin (bins must have been filled for g).  With vg set (a
 // batch), 2W is summed per graph into tw[vg[i]] and a column must lie in its row's graph

@@ -92,6 +92,11 @@ def load():
     lib.louvain_last_error.restype = ctypes.c_char_p
     lib.louvain_run.argtypes = [P, i64, P, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
     lib.louvain_run_batch.argtypes = [P, i32, P, P, P, P, P, ctypes.c_int, P, P]
+    lib.louvain_serve_open.argtypes = [P, ctypes.c_uint64, ctypes.c_int]
+    lib.louvain_submit.argtypes = [P, i64, P, P, P, ctypes.c_int, P]
+    lib.louvain_poll.argtypes = [P, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(P)]
+    lib.louvain_serve_status.argtypes = [P, P]
+    lib.louvain_serve_close.argtypes = [P]
     lib.louvain_result_num_levels.argtypes = [P]
     lib.louvain_result_num_vertices.argtypes = [P]
     lib.louvain_result_num_vertices.restype = i64
@@ -374,6 +379,50 @@ class Louvain:
         if rc != OK:
             raise LouvainError(rc, self.last_error())
         return [Result(self._lib, ctypes.c_void_p(outs[g]), self) for g in range(G)]
+
+
+    # ------------------------------------------------------------ serving
+    def serve_open(self, hbm_budget_bytes: int, max_slots: int) -> None:
+        """Start the request loop (louvain_serve_open)."""
+        rc = self._lib.louvain_serve_open(self._h, int(hbm_budget_bytes), int(max_slots))
+        if rc != OK:
+            raise LouvainError(rc, self.last_error())
+
+    def submit(self, row_ptr, col_idx, weights=None) -> int:
+        """Queue one graph (host arrays, copied before the call returns); returns its ticket."""
+        rp = np.ascontiguousarray(np.asarray(row_ptr, dtype=np.int64))
+        col = np.ascontiguousarray(np.asarray(col_idx, dtype=np.int32))
+        w = None if weights is None else np.ascontiguousarray(np.asarray(weights, dtype=np.int32))
+        t = ctypes.c_uint64()
+        rc = self._lib.louvain_submit(self._h, int(rp.shape[0]) - 1, rp.ctypes.data,
+                                      col.ctypes.data, None if w is None else w.ctypes.data,
+                                      PTR_HOST, ctypes.addressof(t))
+        if rc != OK:
+            raise LouvainError(rc, self.last_error())
+        return t.value
+
+    def poll(self, ticket: int, wait_ms: int = 0) -> Optional[Result]:
+        """The ticket's result, or None while it is pending; raises the graph's error."""
+        out = ctypes.c_void_p()
+        rc = self._lib.louvain_poll(self._h, int(ticket), int(wait_ms), ctypes.byref(out))
+        if rc == PENDING:
+            return None
+        if rc != OK:
+            raise LouvainError(rc, self.last_error())
+        return Result(self._lib, out, self)
+
+    def serve_status(self):
+        """(bytes admitted, slots in use, queued, finished and not polled)."""
+        st = np.zeros(4, np.int64)
+        rc = self._lib.louvain_serve_status(self._h, st.ctypes.data)
+        if rc != OK:
+            raise LouvainError(rc, "serving is not open")
+        return tuple(int(x) for x in st)
+
+    def serve_close(self) -> None:
+        rc = self._lib.louvain_serve_close(self._h)
+        if rc != OK:
+            raise LouvainError(rc, "serving is not open")
 
 
 def stack_graphs(graphs):

@@ -77,6 +77,11 @@ def test_null_handle_calls_are_safe(lib):
     assert lib.louvain_result_num_levels(None) == 0
     assert lib.louvain_run(None, 0, None, None, None, 0, None, None) == 1
     assert lib.louvain_run_batch(None, 1, None, None, None, None, None, 0, None, None) == 1
+    assert lib.louvain_serve_open(None, ctypes.c_uint64(1), 1) == 1
+    assert lib.louvain_submit(None, 0, None, None, None, 0, None) == 1
+    assert lib.louvain_poll(None, ctypes.c_uint64(1), 0, None) == 1
+    assert lib.louvain_serve_status(None, None) == 1
+    assert lib.louvain_serve_close(None) == 1
 
 
 def test_stack_graphs_builds_block_diagonal_csr():
