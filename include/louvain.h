@@ -87,7 +87,14 @@ typedef struct {
     int32_t bin_cta3;
     int32_t chunk_entries;     /* power of two in [32, 4096]; 0 = default 4096           */
     int32_t profile;           /* 1: time kernel groups with CUDA events (louvain_result_counters) */
-    int32_t reserved[4];       /* must be zero                                           */
+    int32_t cuda_graphs;       /* 1 (default): each phase's sweeps run as a CUDA graph whose  */
+                               /* while node repeats sweep, controller and apply on the      */
+                               /* device until the controllers stop (no host round trip per  */
+                               /* sweep); 0, or profile = 1: one host round trip per sweep   */
+    int32_t autotune;          /* 1: louvain_run picks the bin thresholds and chunk length  */
+                               /* by measurement (louvain_autotune) on the first graph of   */
+                               /* each (n, nnz) and reuses them; the results do not change */
+    int32_t reserved[2];       /* must be zero                                           */
     /* device memory: both NULL means stream-ordered cudaMallocAsync/cudaFreeAsync */
     louvain_alloc_fn alloc;
     louvain_free_fn free;
@@ -127,6 +134,19 @@ const char *louvain_last_error(const louvain_handle *h);
  * INTERNAL. */
 int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                 const int32_t *weights, int ptr_kind, void *stream, louvain_result **out);
+
+/* Choose the degree-bin thresholds and chunk length for a graph by measurement (this
+ * library's addition; the thresholds only decide which kernel handles a row, never a
+ * result).  Each trial times the first two sweeps of level 0 with a candidate set (sum of
+ * the move kernels' CUDA-event times, best of two); a coordinate search over
+ * {bin_small, bin_mid1, bin_mid2, bin_cta1, bin_cta2, bin_cta3, chunk_entries} keeps a
+ * change when it is at least 2% faster.  The choice is cached on the handle per (n, nnz)
+ * and used by louvain_run when autotune = 1.  Arguments as in louvain_run; bins_out gets
+ * the seven values in that order, *best_ms the trial time of the choice (-1 on a cache
+ * hit), *trials the trial runs made (0 on a cache hit); either may be NULL. */
+int louvain_autotune(louvain_handle *h, int64_t n, const int64_t *row_ptr,
+                     const int32_t *col_idx, const int32_t *weights, int ptr_kind, void *stream,
+                     int32_t bins_out[7], double *best_ms, int32_t *trials);
 
 /* ---------------------------------------------------------------- batch of graphs */
 /* Largest number of graphs in one louvain_run_batch call. */
@@ -270,6 +290,13 @@ int louvain_result_bin_stats(const louvain_result *r, int bin, double *time_ms,
                              int64_t *entries);
 
 /* Free a result and its host and device memory; NULL is ignored. */
+/* How the result's level steps ran: info[0] sweeps run inside CUDA graphs (device-side
+ * loop, cuda_graphs = 1), [1] sweeps run with one host round trip each, [2] engine level
+ * steps, [3] sweep graphs captured, [4] autotuning trial runs made by this call, [5] 1 when
+ * the bins came from the handle's autotuning cache.  For a batch or served graph the
+ * numbers cover the steps it took part in. */
+int louvain_result_exec_info(const louvain_result *r, int64_t info[6]);
+
 void louvain_result_free(louvain_result *r);
 
 /* ---------------------------------------------------------------- without allocation */

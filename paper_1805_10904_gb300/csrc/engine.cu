@@ -9,10 +9,12 @@
 // per level; every step of the method runs in the kernels of k_level.cu, k_move.cu and
 // k_coarsen.cu.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <climits>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -124,6 +126,7 @@ struct Scalars {
     int32_t bin_counts[40];
     int32_t ccounts[16];
     u64 cand_total[16];
+    LoopCtl loop;
     int32_t tail[8];
 };
 
@@ -180,6 +183,8 @@ struct louvain_handle {
     LaunchCfg lc;
     Scalars *pinned = nullptr;
     void *server = nullptr;  // the open request loop (louvain_serve_open), if any
+    // bin thresholds chosen by the autotuner, per (vertex count, entry count) of a graph
+    std::vector<std::pair<std::pair<int64_t, int64_t>, std::array<int32_t, 7>>> tuned;
 };
 
 // Label arrays of one engine step (every graph that recorded a level in it has its labels
@@ -204,6 +209,8 @@ struct louvain_result {
     int batch_index = -1;  // graph index in its batch, -1 for a plain run
     std::vector<std::shared_ptr<LabelStore>> stores;  // label arrays of its levels
     int64_t acc_sweeps = 0, acc_cand = 0, acc_kernels = 0;
+    // graph sweeps, host-loop sweeps, steps, captures, autotuning trials, tuned-bins cache hit
+    int64_t exec_info[6] = {0, 0, 0, 0, 0, 0};
     double acc_alg_bytes = 0.0, acc_coarsen_ms = 0.0, acc_step_ms = 0.0;
     int64_t tw = 0;
     int device = 0;
@@ -334,9 +341,11 @@ struct Engine {
 
     SweepTimers tm;
     cudaEvent_t coarsen_ev[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;  // stream the sweep graphs are captured on (never runs work)
 
-    Engine(louvain_handle *h_, cudaStream_t s_, DevAlloc &A_, bool batch_)
-        : h(h_), s(s_), A(A_), cfg(h_->cfg), lc(h_->lc), batch(batch_)
+    Engine(louvain_handle *h_, cudaStream_t s_, DevAlloc &A_, bool batch_,
+           const louvain_config &cfg_)
+        : h(h_), s(s_), A(A_), cfg(cfg_), lc(h_->lc), batch(batch_)
     {
         sc_buf.reset(&A, 1);
         d_sc = sc_buf.p;
@@ -358,6 +367,7 @@ struct Engine {
             cudaEventDestroy(coarsen_ev[1]);
         }
         for (Member *m : mem) release_map(m);
+        if (cap) cudaStreamDestroy(cap);
     }
     Engine(const Engine &) = delete;
     Engine &operator=(const Engine &) = delete;
@@ -439,6 +449,101 @@ struct Engine {
     void prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *cbp);
     void join();
     void step(std::vector<Member *> &retired);
+};
+
+// One phase's sweep loop as a CUDA graph: a while node whose body is the sweep over all
+// bins, the controllers, the apply and the loop condition (k_loop_ctl).  Built per bin
+// layout (the launch shapes depend on it); any failure to capture or instantiate leaves
+// the host loop in charge.
+struct SweepGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int per_sweep = 0;
+
+    void reset()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
+    ~SweepGraph() { reset(); }
+
+    // LOUVAIN_GRAPH_DIAG=1 in the environment reports why a capture fell back
+    static bool fail(const char *what, cudaError_t e)
+    {
+        static const bool diag = getenv("LOUVAIN_GRAPH_DIAG") != nullptr;
+        if (diag) fprintf(stderr, "sweep graph: %s failed: %s\n", what, cudaGetErrorString(e));
+        cudaGetLastError();
+        return false;
+    }
+
+    bool build(Engine &E, const DevGraph &G, const PhaseState &st, const Bins &bins, i64 TW,
+               bool wide, bool narrow, SweepStats *st_dev, LevelCtl *ctl_dev, int M,
+               const BatchCtx &bc, int &out_per_sweep)
+    {
+        reset();
+        // capture on a stream of the engine's own: the caller's stream may be the legacy
+        // default stream, which cannot be captured; the graph is launched on the caller's
+        cudaError_t e;
+        if (!E.cap && (e = cudaStreamCreateWithFlags(&E.cap, cudaStreamNonBlocking)) != cudaSuccess) {
+            E.cap = nullptr;
+            return fail("stream create", e);
+        }
+        cudaStream_t s = E.cap;
+        cudaGraphConditionalHandle handle;
+        cudaGraphNode_t node;
+        cudaGraphNodeParams cp = {};
+        if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) {
+            reset();
+            return fail("graph create", e);
+        }
+        if ((e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault)) !=
+            cudaSuccess) {
+            reset();
+            return fail("conditional handle", e);
+        }
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if ((e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp)) != cudaSuccess) {
+            reset();
+            return fail("conditional node", e);
+        }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
+            reset();
+            return fail("begin capture", e);
+        }
+        int k = launch_sweep(G, st, bins, TW, wide, narrow, st_dev, &E.d_sc->err, s, E.lc,
+                             nullptr, bc);
+        k += launch_decide(st_dev, ctl_dev, M, E.tr_moved.p, E.tr_qn.p, &E.d_sc->cand_total[0],
+                           &E.d_sc->ndone, s);
+        k += launch_apply(G.n, st, ctl_dev, bc.vg, s, E.lc);
+        k += launch_loop_ctl(handle, &E.d_sc->loop, &E.d_sc->ndone, M, s);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(s, &captured);
+        const char *site = launch_site();
+        launch_site() = nullptr;
+        if (e != cudaSuccess) {
+            reset();
+            return fail("end capture", e);
+        }
+        if (site) {
+            reset();
+            return fail(site, cudaErrorInvalidValue);
+        }
+        if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
+            exec = nullptr;
+            reset();
+            return fail("instantiate", e);
+        }
+        per_sweep = k - 1;  // the loop-condition kernel is not a method step
+        out_per_sweep = per_sweep;
+        return true;
+    }
 };
 
 Bins Engine::make_proto(bool narrow_sums) const
@@ -801,16 +906,45 @@ void Engine::step(std::vector<Member *> &retired)
             entries_kernel[b] += bb.entries[b];
         }
     };
-    int sweeps = 0;
-    int ndone_binned = 0;
+    int sweeps = 0, graph_sweeps = 0, captures = 0;
+    int ndone_binned = 0, ndone = 0;
+    // the sweeps run either as a CUDA graph whose while node repeats sweep, controllers,
+    // apply and loop condition on the device, or (profiling, or no graph support) with one
+    // host round trip per sweep
+    bool use_graph = cfg.cuda_graphs && !tm.on;
+    SweepGraph sg;
     for (;;) {
-        kernels += launch_sweep(G, st, bins, TW, wide, narrow, st_dev, &d_sc->err, s, lc, &tm, bc);
-        kernels += launch_decide(st_dev, ctl_dev, M, tr_moved.p, tr_qn.p, &d_sc->cand_total[0],
-                                 &d_sc->ndone, s);
-        kernels += launch_apply(n, st, ctl_dev, bc.vg, s, lc);
-        sweeps++;
-        account_sweep(bins);
-        sync_scalars();
+        int ran = 0, per_sweep = 0;
+        if (use_graph && !sg.exec) {
+            if (sg.build(*this, G, st, bins, TW, wide, narrow, st_dev, ctl_dev, M, bc, per_sweep))
+                captures++;
+            else
+                use_graph = false;
+        }
+        if (use_graph) {
+            LoopCtl &lp = h->pinned->loop;
+            lp.iters = 0;
+            lp.nd0 = ndone;
+            lp.quota = batch ? std::max(1, (M - ndone) / 4) : 1;
+            lp.cap = cfg.max_iters + 3 - sweeps;
+            CK(cudaMemcpyAsync(&d_sc->loop, &lp, sizeof(LoopCtl), cudaMemcpyHostToDevice, s));
+            CK(cudaGraphLaunch(sg.exec, s));
+            sync_scalars();
+            ran = h->pinned->loop.iters;
+            per_sweep = sg.per_sweep;
+            graph_sweeps += ran;
+        } else {
+            per_sweep = launch_sweep(G, st, bins, TW, wide, narrow, st_dev, &d_sc->err, s, lc,
+                                     &tm, bc);
+            per_sweep += launch_decide(st_dev, ctl_dev, M, tr_moved.p, tr_qn.p,
+                                       &d_sc->cand_total[0], &d_sc->ndone, s);
+            per_sweep += launch_apply(n, st, ctl_dev, bc.vg, s, lc);
+            sync_scalars();
+            ran = 1;
+        }
+        kernels += (int64_t)per_sweep * ran;
+        sweeps += ran;
+        for (int r = 0; r < ran; r++) account_sweep(bins);
         for (int b = 0; b < kNumBins; b++) {
             if (tm.on) {
                 float ms = 0.f;
@@ -818,19 +952,21 @@ void Engine::step(std::vector<Member *> &retired)
                 t_kernel[b] += ms;
             }
             launches_kernel[b] +=
-                b == 0 ? 1 : (b == kChunkedBin ? bins.nchunks > 0 : bins.nlist[b] > 0);
+                ran * (b == 0 ? 1 : (b == kChunkedBin ? bins.nchunks > 0 : bins.nlist[b] > 0));
         }
-        const int ndone = h->pinned->ndone;
+        ndone = h->pinned->ndone;
         if (ndone >= M) break;
-        if (sweeps > cfg.max_iters + 2)
+        if (sweeps > cfg.max_iters + 2 || ran < 1)
             throw LvErr{LOUVAIN_ERR_INTERNAL, "phase controller did not stop"};
         if (batch && ndone > ndone_binned) {
             // some graphs stopped: bin again without their rows
             bins = make_bins(G, proto, vg.p, d_ctls.p);
             prep_huge(bins, false, 0, nullptr);
             ndone_binned = ndone;
+            sg.reset();
         }
     }
+    sg.reset();
     if (batch) {
         CK(cudaMemcpyAsync(h_ctl.data(), d_ctls.p, sizeof(LevelCtl) * M, cudaMemcpyDeviceToHost,
                            s));
@@ -1067,6 +1203,10 @@ void Engine::step(std::vector<Member *> &retired)
         r->acc_kernels += step_kernels;
         r->acc_coarsen_ms += t_coarsen;
         r->acc_step_ms += wall;
+        r->exec_info[0] += graph_sweeps;
+        r->exec_info[1] += sweeps - graph_sweeps;
+        r->exec_info[2] += 1;
+        r->exec_info[3] += captures;
         for (int b = 0; b < kNumBins; b++) {
             r->bin_time[b] += t_kernel[b];
             r->bin_launches[b] += launches_kernel[b];
@@ -1117,14 +1257,15 @@ void finish_result(Member *m)
 
 // Runs louvain_run (gvptr null: one graph, one-graph kernels) or louvain_run_batch on the
 // engine: the input enters as one source and the engine steps until every graph has left.
-void run_engine(louvain_handle *h, cudaStream_t s, DevAlloc &A, int64_t n0, const int64_t *rp_in,
+void run_engine(louvain_handle *h, const louvain_config &cfg, cudaStream_t s, DevAlloc &A,
+                int64_t n0, const int64_t *rp_in,
                 const int32_t *col_in, const int32_t *w_in, int kind, int NG,
                 const int64_t *gvptr, const int64_t *geptr, std::vector<louvain_result *> &out)
 {
     const double t0 = now_ms();
     const bool batch = gvptr != nullptr;
     std::vector<std::unique_ptr<Member>> members(NG);  // outlives the engine
-    Engine E(h, s, A, batch);
+    Engine E(h, s, A, batch, cfg);
     const LaunchCfg &lc = h->lc;
 
     // ---------------- input graph on the device
@@ -1411,7 +1552,7 @@ struct Server {
         std::unique_ptr<Engine> E;
         auto fresh_engine = [&] {
             E.reset();
-            E.reset(new Engine(h, compute, A_compute, true));
+            E.reset(new Engine(h, compute, A_compute, true, h->cfg));
         };
         try {
             fresh_engine();
@@ -1493,6 +1634,138 @@ struct Server {
     }
 };
 
+// ---------------------------------------------------------------------- autotuner
+//
+// Degree-bin thresholds and the chunk length only decide which kernel handles a row, never
+// a result, so they can be chosen by measurement: each trial runs the first two sweeps of
+// level 0 with a candidate set (best of two runs, sum of the move kernels' event times),
+// and a coordinate search over the thresholds keeps a change only when it is at least 2%
+// faster.  The choice is cached on the handle per (vertex count, entry count).
+
+void get_bins(const louvain_config &c, int32_t b[7])
+{
+    b[0] = c.bin_small;
+    b[1] = c.bin_mid1;
+    b[2] = c.bin_mid2;
+    b[3] = c.bin_cta1;
+    b[4] = c.bin_cta2;
+    b[5] = c.bin_cta3;
+    b[6] = c.chunk_entries;
+}
+
+void set_bins(louvain_config &c, const int32_t b[7])
+{
+    c.bin_small = b[0];
+    c.bin_mid1 = b[1];
+    c.bin_mid2 = b[2];
+    c.bin_cta1 = b[3];
+    c.bin_cta2 = b[4];
+    c.bin_cta3 = b[5];
+    c.chunk_entries = b[6];
+}
+
+bool bins_valid(const int32_t b[7])
+{
+    return b[0] >= 0 && b[0] <= 8 && b[0] <= b[1] && b[1] <= 32 && b[1] <= b[2] &&
+           b[2] <= 128 && b[2] <= b[3] && b[3] <= b[4] && b[4] <= b[5] && b[5] <= 12288 &&
+           b[6] >= 32 && b[6] <= 4096 && (b[6] & (b[6] - 1)) == 0;
+}
+
+void tuned_bins(louvain_handle *h, cudaStream_t s, DevAlloc &A, int64_t n, const int64_t *rp,
+                const int32_t *col, const int32_t *w, int kind, std::array<int32_t, 7> &out,
+                int64_t *trials_out, int64_t *hit_out, double *best_ms_out)
+{
+    int64_t nnz = 0;
+    if (kind == LOUVAIN_PTR_HOST) {
+        nnz = rp[n];
+    } else {
+        CK(cudaMemcpyAsync(&h->pinned->tail[0], rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                           s));
+        CK(cudaStreamSynchronize(s));
+        memcpy(&nnz, &h->pinned->tail[0], sizeof(nnz));
+    }
+    const std::pair<int64_t, int64_t> key(n, nnz);
+    for (const auto &e : h->tuned)
+        if (e.first == key) {
+            out = e.second;
+            *trials_out = 0;
+            *hit_out = 1;
+            if (best_ms_out) *best_ms_out = -1.0;
+            return;
+        }
+    // trials read the graph from device memory (one copy of a host graph for all of them)
+    DBuf<int64_t> rp_d;
+    DBuf<int32_t> col_d, w_d;
+    if (kind == LOUVAIN_PTR_HOST) {
+        rp_d.reset(&A, (size_t)n + 1);
+        col_d.reset(&A, (size_t)nnz);
+        CK(cudaMemcpyAsync(rp_d.p, rp, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice,
+                           s));
+        if (nnz) {
+            if (!col) throw LvErr{LOUVAIN_ERR_INVALID_ARG, "col_idx is NULL"};
+            CK(cudaMemcpyAsync(col_d.p, col, sizeof(int32_t) * (size_t)nnz,
+                               cudaMemcpyHostToDevice, s));
+        }
+        if (w) {
+            w_d.reset(&A, (size_t)nnz);
+            if (nnz)
+                CK(cudaMemcpyAsync(w_d.p, w, sizeof(int32_t) * (size_t)nnz,
+                                   cudaMemcpyHostToDevice, s));
+        }
+        rp = rp_d.p;
+        col = col_d.p;
+        w = w ? w_d.p : nullptr;
+        kind = LOUVAIN_PTR_DEVICE;
+    }
+    louvain_config base = h->cfg;
+    base.max_levels = 1;
+    base.max_iters = 2;
+    base.profile = 1;
+    base.autotune = 0;
+    base.cuda_graphs = 0;
+    int64_t trials = 0;
+    auto trial = [&](const int32_t b[7]) {
+        louvain_config t = base;
+        set_bins(t, b);
+        double best = 1e300;
+        for (int rep = 0; rep < 2; rep++) {
+            std::unique_ptr<louvain_result> r(new louvain_result());
+            r->device = h->device;
+            r->ff = h->cfg.free;
+            r->ctx = h->cfg.alloc_ctx;
+            std::vector<louvain_result *> outs{r.get()};
+            run_engine(h, t, s, A, n, rp, col, w, kind, 1, nullptr, nullptr, outs);
+            best = std::min(best, r->times[0]);
+            trials++;
+        }
+        return best;
+    };
+    static const int32_t cand[7][3] = {{0, 4, 8},       {16, 32, 32},       {64, 128, 128},
+                                       {256, 512, 1024}, {1024, 2048, 4096}, {4096, 8192, 12288},
+                                       {1024, 2048, 4096}};
+    int32_t cur[7];
+    get_bins(h->cfg, cur);
+    double cur_t = trial(cur);
+    for (int p = 0; p < 7; p++)
+        for (int v = 0; v < 3; v++) {
+            int32_t c[7];
+            memcpy(c, cur, sizeof(c));
+            if (cand[p][v] == cur[p]) continue;
+            c[p] = cand[p][v];
+            if (!bins_valid(c)) continue;
+            const double t = trial(c);
+            if (t < 0.98 * cur_t) {
+                memcpy(cur, c, sizeof(c));
+                cur_t = t;
+            }
+        }
+    for (int k = 0; k < 7; k++) out[k] = cur[k];
+    h->tuned.push_back({key, out});
+    *trials_out = trials;
+    *hit_out = 0;
+    if (best_ms_out) *best_ms_out = cur_t;
+}
+
 struct RunCtx {
     cudaStream_t s = nullptr;
     DevAlloc A;
@@ -1528,6 +1801,8 @@ int louvain_config_init(louvain_config *cfg)
     cfg->bin_cta3 = 12288;
     cfg->chunk_entries = 4096;
     cfg->profile = 0;
+    cfg->cuda_graphs = 1;
+    cfg->autotune = 0;
     return LOUVAIN_OK;
 }
 
@@ -1666,9 +1941,19 @@ int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int3
     launch_site() = nullptr;
     try {
         CK(cudaSetDevice(h->device));
+        louvain_config cfg = h->cfg;
+        int64_t trials = 0, hit = 0;
+        if (cfg.autotune && n > 0) {
+            std::array<int32_t, 7> b;
+            tuned_bins(h, R.s, R.A, n, row_ptr, col_idx, weights, ptr_kind, b, &trials, &hit,
+                       nullptr);
+            set_bins(cfg, b.data());
+        }
         std::vector<louvain_result *> outs{res};
-        run_engine(h, R.s, R.A, n, row_ptr, col_idx, weights, ptr_kind, 1, nullptr, nullptr,
+        run_engine(h, cfg, R.s, R.A, n, row_ptr, col_idx, weights, ptr_kind, 1, nullptr, nullptr,
                    outs);
+        res->exec_info[4] = trials;
+        res->exec_info[5] = hit;
     } catch (const LvErr &e) {
         rc = e.code;
         h->err = e.msg;
@@ -1683,6 +1968,49 @@ int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int3
         return rc;
     }
     *out = res;
+    return LOUVAIN_OK;
+}
+
+int louvain_autotune(louvain_handle *h, int64_t n, const int64_t *row_ptr,
+                     const int32_t *col_idx, const int32_t *weights, int ptr_kind, void *stream,
+                     int32_t bins_out[7], double *best_ms, int32_t *trials)
+{
+    if (!h) return LOUVAIN_ERR_INVALID_ARG;
+    h->err.clear();
+    if (h->server) {
+        h->err = "the handle is serving";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (n < 1 || n > INT32_MAX || !row_ptr || !bins_out ||
+        (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE)) {
+        h->err = "bad n, row_ptr, bins_out or ptr_kind";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    RunCtx R;
+    R.s = (cudaStream_t)stream;
+    R.A.fa = h->cfg.alloc;
+    R.A.ff = h->cfg.free;
+    R.A.ctx = h->cfg.alloc_ctx;
+    R.A.s = R.s;
+    launch_site() = nullptr;
+    try {
+        CK(cudaSetDevice(h->device));
+        std::array<int32_t, 7> b;
+        int64_t tr = 0, hit = 0;
+        double ms = 0.0;
+        tuned_bins(h, R.s, R.A, n, row_ptr, col_idx, weights, ptr_kind, b, &tr, &hit, &ms);
+        for (int k = 0; k < 7; k++) bins_out[k] = b[k];
+        if (best_ms) *best_ms = ms;
+        if (trials) *trials = (int32_t)tr;
+    } catch (const LvErr &e) {
+        h->err = e.msg;
+        cudaStreamSynchronize(R.s);
+        cudaGetLastError();
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        h->err = "host allocation failed";
+        return LOUVAIN_ERR_OOM;
+    }
     return LOUVAIN_OK;
 }
 
@@ -1741,7 +2069,8 @@ int louvain_run_batch(louvain_handle *h, int32_t num_graphs, const int64_t *grap
     launch_site() = nullptr;
     try {
         CK(cudaSetDevice(h->device));
-        run_engine(h, R.s, R.A, n, row_ptr, col_idx, weights, ptr_kind, num_graphs, graph_vptr,
+        run_engine(h, h->cfg, R.s, R.A, n, row_ptr, col_idx, weights, ptr_kind, num_graphs,
+                   graph_vptr,
                    graph_eptr, outs);
     } catch (const LvErr &e) {
         rc = e.code;
@@ -2048,6 +2377,13 @@ int louvain_result_counters(const louvain_result *r, int64_t counters[8], double
         if (counters) counters[k] = r->counters[k];
         if (times_ms) times_ms[k] = r->times[k];
     }
+    return LOUVAIN_OK;
+}
+
+int louvain_result_exec_info(const louvain_result *r, int64_t info[6])
+{
+    if (!r || !info) return LOUVAIN_ERR_INVALID_ARG;
+    for (int k = 0; k < 6; k++) info[k] = r->exec_info[k];
     return LOUVAIN_OK;
 }
 

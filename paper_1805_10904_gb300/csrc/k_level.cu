@@ -610,6 +610,26 @@ int launch_decide(SweepStats *st, LevelCtl *ctl, int G, i64 *tr_moved, i64 *tr_q
     return 1;
 }
 
+// Condition of the device-side sweep loop (a CUDA graph while node): go on while some
+// controller is still running, fewer than `quota` graphs stopped since the loop was
+// launched (a batch then returns to the host to drop their rows from the bins), and the
+// loop has run fewer than `cap` sweeps (a bound the controllers never reach).
+__global__ void k_loop_ctl(cudaGraphConditionalHandle handle, LoopCtl *lc, const int *ndone,
+                           int G)
+{
+    const int it = ++lc->iters;
+    const int nd = *(volatile const int *)ndone;
+    const bool go = nd < G && nd - lc->nd0 < lc->quota && it < lc->cap;
+    cudaGraphSetConditional(handle, go ? 1u : 0u);
+}
+
+int launch_loop_ctl(cudaGraphConditionalHandle handle, LoopCtl *lc, const int *ndone, int G,
+                    cudaStream_t s)
+{
+    k_loop_ctl<<<1, 1, 0, s>>>(handle, lc, ndone, G);
+    return 1;
+}
+
 // Apply the sweep's proposal (unless the controller of the vertex's graph stopped the
 // phase): deg_C and size_C follow the moved vertices (the paper's remove / insert with
 // atomics), then C <- C_next.

@@ -151,6 +151,17 @@ int launch_decide(SweepStats *st, LevelCtl *ctl, int G, i64 *tr_moved, i64 *tr_q
                   u64 *cand_total, int *ndone, cudaStream_t s);
 int launch_apply(int64_t n, const PhaseState &st, const LevelCtl *ctl, const int32_t *vg,
                  cudaStream_t s, const LaunchCfg &lc);
+// State of the device-side sweep loop: sweeps run so far, controllers stopped when it was
+// launched, how many more may stop before it returns, and its sweep bound.
+struct LoopCtl {
+    int iters;
+    int nd0;
+    int quota;
+    int cap;
+};
+// Sets the while-node condition of the sweep loop after a sweep (one thread).
+int launch_loop_ctl(cudaGraphConditionalHandle handle, LoopCtl *lc, const int *ndone, int G,
+                    cudaStream_t s);
 // new_id[c] = rank of c among used labels (size[c] > 0, and keep[vg[c]] when given).
 int launch_renumber(int64_t n, const int32_t *size, const int32_t *vg, const int32_t *keep,
                     int32_t *new_id, int32_t *scratch, cudaStream_t s);

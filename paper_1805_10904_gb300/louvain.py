@@ -57,7 +57,9 @@ class Config(ctypes.Structure):
         ("bin_cta3", ctypes.c_int32),
         ("chunk_entries", ctypes.c_int32),
         ("profile", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("cuda_graphs", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
@@ -107,6 +109,8 @@ def load():
     lib.louvain_result_trace.argtypes = [P, P, P, P, P, P]
     lib.louvain_result_counters.argtypes = [P, P, P]
     lib.louvain_num_bins.restype = ctypes.c_int
+    lib.louvain_result_exec_info.argtypes = [P, P]
+    lib.louvain_autotune.argtypes = [P, i64, P, P, P, ctypes.c_int, P, P, P, P]
     lib.louvain_result_bin_stats.argtypes = [P, ctypes.c_int, P, P, P, P, P]
     lib.louvain_result_free.argtypes = [P]
     lib.louvain_result_free.restype = None
@@ -248,6 +252,13 @@ class Result:
                         "rows": v[2].value, "entries": v[3].value})
         return out
 
+    def exec_info(self):
+        """(sweeps in CUDA graphs, host-loop sweeps, level steps, graph captures, autotuning
+        trials of this call, 1 if the tuned bins came from the cache)."""
+        v = np.zeros(6, np.int64)
+        self._lib.louvain_result_exec_info(self._p, v.ctypes.data)
+        return tuple(int(x) for x in v)
+
     def counters(self):
         c = np.zeros(8, np.int64)
         t = np.zeros(8, np.float64)
@@ -267,7 +278,8 @@ class Louvain:
                  max_levels: int = 64, vertex_following: bool = True,
                  vf_all_levels: bool = False, checks: int = 1, force_int128: bool = False,
                  wide_sums: bool = False, bins=None, chunk_entries: int = 0,
-                 profile: bool = False, torch_alloc: bool = True):
+                 profile: bool = False, torch_alloc: bool = True, cuda_graphs: bool = True,
+                 autotune: bool = False):
         lib = load()
         self._lib = lib
         cfg = Config()
@@ -286,6 +298,8 @@ class Louvain:
         if chunk_entries:
             cfg.chunk_entries = chunk_entries
         cfg.profile = int(profile)
+        cfg.cuda_graphs = int(cuda_graphs)
+        cfg.autotune = int(autotune)
         self.device = device
         if torch_alloc:
             import torch
@@ -348,6 +362,30 @@ class Louvain:
         if rc != OK:
             raise LouvainError(rc, self.last_error())
         return Result(self._lib, out, self)
+
+    def autotune(self, row_ptr, col_idx, weights=None, stream: Optional[int] = None):
+        """louvain_autotune: (bins 6-tuple, chunk_entries, best trial ms, trials)."""
+        rp, k1, keep1 = _ptr_of(row_ptr)
+        col, k2, keep2 = _ptr_of(col_idx)
+        w, k3, keep3 = _ptr_of(weights)
+        kinds = {k for k in (k1, k2, k3) if k is not None}
+        if len(kinds) != 1:
+            raise ValueError("row_ptr, col_idx and weights must all be on the host or all on the device")
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(self.device).cuda_stream
+            except Exception:
+                stream = 0
+        b = np.zeros(7, np.int32)
+        ms = ctypes.c_double()
+        tr = ctypes.c_int32()
+        rc = self._lib.louvain_autotune(self._h, int(keep1.shape[0]) - 1, rp, col, w,
+                                        kinds.pop(), ctypes.c_void_p(stream), b.ctypes.data,
+                                        ctypes.addressof(ms), ctypes.addressof(tr))
+        if rc != OK:
+            raise LouvainError(rc, self.last_error())
+        return tuple(int(x) for x in b[:6]), int(b[6]), ms.value, tr.value
 
     def run_batch(self, graph_vptr, row_ptr, col_idx, weights=None, graph_eptr=None,
                   stream: Optional[int] = None) -> List[Result]:

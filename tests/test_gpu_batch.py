@@ -81,6 +81,7 @@ BATCH_CONFIGS = [
     {"theta": (1, 100), "max_levels": 2},
     {"max_iters": 2, "vertex_following": False},
     {"vf_all_levels": True, "theta": (0, 1)},
+    {"cuda_graphs": False},
 ]
 
 

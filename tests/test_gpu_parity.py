@@ -71,6 +71,8 @@ BIN_CONFIGS = [
     {"bins": (8, 32, 128, 512, 2048, 12288), "chunk_entries": 128},
     {"bins": (0, 0, 0, 0, 0, 2)},                                # clusters of 2..16 CTAs
     {"bins": (1, 2, 3, 4, 5, 6), "wide_sums": True, "force_int128": True, "chunk_entries": 64},
+    {"cuda_graphs": False},                                      # one host round trip per sweep
+    {"cuda_graphs": False, "bins": (0, 0, 0, 0, 0, 2), "chunk_entries": 32},
 ]
 
 
@@ -221,3 +223,42 @@ def test_invalid_inputs_are_reported_and_handle_survives(torch, lv):
     res = h.run(rp, col, w)
     ref = oracle.louvain(g.rp, g.col, g.w)
     assert_parity(res, ref)
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_sweep_loop_modes_run_as_configured(torch, lv, graphs):
+    """cuda_graphs=True runs every sweep inside the device-side loop (a CUDA graph with a
+    while node), cuda_graphs=False one sweep per host round trip; both give the oracle's
+    result."""
+    g = gg.rmat(13, 16, seed=9)
+    res, ref = run_both(torch, lv, g, cuda_graphs=graphs)
+    assert_parity(res, ref)
+    in_graph, host_loop, steps, captures = res.exec_info()[:4]
+    assert steps >= res.num_levels
+    if graphs:
+        assert in_graph == res.counters()[0][1] and host_loop == 0 and captures >= 1
+    else:
+        assert in_graph == 0 and host_loop == res.counters()[0][1] and captures == 0
+
+
+def test_autotuned_bins_give_the_same_result(torch, lv):
+    """The autotuner only picks which kernel handles a row: a run with autotune = 1 matches
+    the oracle, the first call tunes, a second call on the same (n, nnz) reuses the choice,
+    and the bins louvain_autotune returns are a valid configuration giving the same result."""
+    g = gg.rmat(14, 16, seed=21)
+    ref = oracle.louvain(g.rp, g.col, g.w)
+    h = lv.Louvain(0, autotune=True)
+    d = to_dev(torch, g)
+    first = h.run(*d)
+    assert_parity(first, ref)
+    assert first.exec_info()[4] > 0 and first.exec_info()[5] == 0
+    second = h.run(*d)
+    assert_parity(second, ref)
+    assert second.exec_info()[4] == 0 and second.exec_info()[5] == 1
+    h2 = lv.Louvain(0)
+    bins, chunk, ms, trials = h2.autotune(g.rp, g.col, g.w)  # host arrays
+    assert trials > 0 and ms > 0
+    assert 0 <= bins[0] <= bins[1] <= bins[2] <= bins[3] <= bins[4] <= bins[5] <= 12288
+    assert chunk in (1024, 2048, 4096)
+    assert_parity(lv.Louvain(0, bins=bins, chunk_entries=chunk).run(*d), ref)
+    assert h2.autotune(*d)[3] == 0  # cached on the handle
