@@ -324,8 +324,11 @@ struct Engine {
     DBuf<u64> b_gloop;
     DBuf<int32_t> scratch32;
     DBuf<int64_t> scratch64;
-    DBuf<int32_t> chunk_b, gkeys, glist;
+    DBuf<int32_t> chunk_b, gkeys, glist, hp_best, hp_sdone, hp_slice_row;
+    DBuf<int64_t> hp_soff;
     DBuf<u64> gvals;
+    DBuf<i64> hp_ea;
+    DBuf<u128> hp_gain;
     DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_tmp_col;
     DBuf<int64_t> c_mpre;
     DBuf<u64> c_tmp_w;
@@ -620,6 +623,25 @@ void Engine::prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *
     b.gkeys = gkeys.p;
     b.gvals = gvals.p;
     b.glist = glist.p;
+    b.nslices = 0;
+    if (!coarsen_side && b.gslots > 0) {
+        ensure(hp_soff, (size_t)nb + 1);
+        b.soff = hp_soff.p;
+        kernels += launch_huge_slices(b, scratch64.p, s);
+        b.nslices = read_one(hp_soff.p + nb);
+        ensure(hp_slice_row, b.nslices);
+        b.slice_row = hp_slice_row.p;
+        kernels += launch_huge_slice_fill(b, s, lc);
+        ensure(hp_gain, b.nslices);
+        ensure(hp_best, b.nslices);
+        ensure(hp_ea, b.nslices);
+        ensure(hp_sdone, nb);
+        CK(cudaMemsetAsync(hp_sdone.p, 0, sizeof(int32_t) * nb, s));
+    }
+    b.pgain = hp_gain.p;
+    b.pbest = hp_best.p;
+    b.pea = hp_ea.p;
+    b.sdone = hp_sdone.p;
     CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
     CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
     CK(cudaMemsetAsync(b_gloop.p, 0, sizeof(u64) * nb, s));

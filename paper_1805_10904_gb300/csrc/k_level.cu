@@ -512,6 +512,45 @@ int launch_big_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc)
     return 1;
 }
 
+// Decision slices of the multi-chunk rows: row b gets max(1, gcap[b] / (2 kHugeSlice))
+// slices (its candidate list never exceeds gcap[b] / 2 entries); soff is their exclusive
+// scan and slice_row the row of every slice.
+struct HugeSlicesIn {
+    const int32_t *nch;
+    const int64_t *gcap;
+    __device__ __forceinline__ int64_t operator()(int64_t b) const
+    {
+        if (nch[b] <= 1) return 0;
+        const int64_t s = gcap[b] / (2 * kHugeSlice);
+        return s > 0 ? s : 1;
+    }
+};
+
+int launch_huge_slices(Bins &b, int64_t *scratch64, cudaStream_t s)
+{
+    const int nb = b.nlist[kChunkedBin];
+    if (nb == 0) return 0;
+    return exclusive_scan<int64_t>(HugeSlicesIn{b.nch, b.gcap}, nb, b.soff, scratch64, s);
+}
+
+__global__ void k_huge_slice_fill(int nb, const int64_t *soff, int32_t *slice_row)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int b = warp; b < nb; b += nwarps)
+        for (int64_t q = soff[b] + lane; q < soff[b + 1]; q += 32) slice_row[q] = b;
+}
+
+int launch_huge_slice_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc)
+{
+    const int nb = b.nlist[kChunkedBin];
+    if (nb == 0) return 0;
+    k_huge_slice_fill<<<grid_for(nb, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(nb, b.soff,
+                                                                                 b.slice_row);
+    return 1;
+}
+
 // ------------------------------------------------------------------ phase controller
 
 // (qn_new - qn_old) * den < num * tw^2, exact: both sides formed in 192 bits.

@@ -634,6 +634,13 @@ struct BigArgs {
     int32_t *glist;
     int chunk;
     int nchunks;
+    void *pgain;
+    int32_t *pbest;
+    i64 *pea;
+    int32_t *sdone;
+    const int64_t *soff;
+    const int32_t *slice_row;
+    int64_t nslices;
 };
 
 template <typename WT, typename GT, typename VT, bool BT>
@@ -646,7 +653,6 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
     int *keys = (int *)(vals + cap);
     int *list = keys + cap;
     __shared__ int s_cnt;
-    __shared__ int s_last;
     for (int s = threadIdx.x; s < cap; s += kHugeBlock) {
         keys[s] = -1;
         vals[s] = 0;
@@ -737,48 +743,94 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
             }
             loop = sum_reduce(loop, 32);
             if ((threadIdx.x & 31) == 0 && loop) atomicAdd(&B.gloop[b], (u64)loop);
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const int t = atomicAdd(&B.gdone[b], 1);
-                s_last = (t == nch - 1);
-            }
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-                const int gm = __ldcg(&B.gcnt[b]);
-                GT gbest = gain_min<GT>();
-                int32_t best = INT_MAX;
-                i64 e_a = 0, lz = 0;
-                for (int p = threadIdx.x; p < gm; p += kHugeBlock) {
-                    const int s = __ldcg(gl + p);
-                    const int32_t k2 = __ldcg(gk + s);
-                    const i64 e = (i64)__ldcg(gv + s);
-                    gk[s] = -1;
-                    gv[s] = 0;
-                    consider<GT>(k2, e, a, dl, tw, A.deg, gbest, best, e_a);
-                }
-                block_argmax(gbest, best, e_a, lz);
-                if (threadIdx.x == 0) {
-                    const i64 lp = (i64)__ldcg(&B.gloop[b]);
-                    const int32_t target =
-                        choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
-                    A.Cnext[i] = target;
-                    if constexpr (!BT) {
-                        moved += target != a;
-                        internal += (u64)(e_a + lp);
-                    } else {
-                        row_stats(A.st, gr, e_a + lp, target != a);
-                    }
-                    cand += (u64)gm;
-                    B.gcnt[b] = 0;
-                    B.gdone[b] = 0;
-                    B.gloop[b] = 0;
-                }
-            }
+            // the row is decided by k_move_huge_decide once every chunk has merged
         }
         __syncthreads();
         if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+    }
+    block_flush_stats(A.st, kChunkedBin, internal, moved, cand, 0);
+}
+
+// Decision of the rows spread over several chunks, after k_move_huge merged all their
+// chunks into the rows' global tables: a row's candidate list is cut into slices of
+// kHugeSlice entries (a fixed number per row, sized for the longest possible list), each
+// slice is one work item of a grid-stride loop (partial argmax, table cleared behind),
+// and the CTA that finishes a row's last slice combines the partials and decides the row.
+template <typename WT, typename GT, typename VT, bool BT>
+__global__ void __launch_bounds__(kHugeBlock) k_move_huge_decide(MoveArgs<WT> A, BigArgs B)
+{
+    __shared__ int s_last;
+    GT *pg = (GT *)B.pgain;
+    u64 internal = 0, moved = 0, cand = 0;
+    for (int64_t q = blockIdx.x; q < B.nslices; q += gridDim.x) {
+        const int b = B.slice_row[q];
+        const int32_t i = B.bverts[b];
+        const int gr = graph_of<BT>(A, i);
+        if (frozen<BT>(A, gr)) continue;  // its first chunk kept it in place
+        const int64_t s0 = B.soff[b];
+        const int ns = (int)(B.soff[b + 1] - s0);
+        const int sl = (int)(q - s0);
+        const int gm = __ldcg(&B.gcnt[b]);
+        const int64_t off = B.goff[b];
+        const int32_t *gl = B.glist + off;
+        int32_t *gk = B.gkeys + off;
+        VT *gv = (VT *)B.gvals + off;
+        const int32_t a = A.C[i];
+        const i64 dl = A.delta[i];
+        const i64 tw = tw_of<BT>(A, gr);
+        GT gbest = gain_min<GT>();
+        int32_t best = INT_MAX;
+        i64 e_a = 0, lz = 0;
+        const int pe = min(gm, (sl + 1) * kHugeSlice);
+        for (int p = sl * kHugeSlice + threadIdx.x; p < pe; p += kHugeBlock) {
+            const int s = __ldcg(gl + p);
+            const int32_t k2 = __ldcg(gk + s);
+            const i64 e = (i64)__ldcg(gv + s);
+            gk[s] = -1;
+            gv[s] = 0;
+            consider<GT>(k2, e, a, dl, tw, A.deg, gbest, best, e_a);
+        }
+        block_argmax(gbest, best, e_a, lz);
+        if (threadIdx.x == 0) {
+            pg[q] = gbest;
+            B.pbest[q] = best;
+            B.pea[q] = e_a;
+            __threadfence();
+            s_last = atomicAdd(&B.sdone[b], 1) == ns - 1;
+        }
+        __syncthreads();
+        if (s_last) {  // every slice of row b is in: combine and decide
+            __threadfence();
+            GT g = gain_min<GT>();
+            int32_t c = INT_MAX;
+            i64 ea = 0, l0 = 0;
+            for (int t = threadIdx.x; t < ns; t += kHugeBlock) {
+                const GT gt = *(volatile const GT *)&pg[s0 + t];  // bypasses L1
+                const int32_t ct = __ldcg(&B.pbest[s0 + t]);
+                if (better(gt, ct, g, c)) {
+                    g = gt;
+                    c = ct;
+                }
+                ea += __ldcg(&B.pea[s0 + t]);
+            }
+            block_argmax(g, c, ea, l0);
+            if (threadIdx.x == 0) {
+                const i64 lp = (i64)__ldcg(&B.gloop[b]);
+                const int32_t target = choose_target<GT>(a, c, g, ea, dl, tw, A.deg, A.size);
+                A.Cnext[i] = target;
+                if constexpr (!BT) {
+                    moved += target != a;
+                    internal += (u64)(ea + lp);
+                } else {
+                    row_stats(A.st, gr, ea + lp, target != a);
+                }
+                cand += (u64)gm;
+                B.gcnt[b] = 0;
+                B.gloop[b] = 0;
+                B.sdone[b] = 0;
+            }
+        }
         __syncthreads();
     }
     block_flush_stats(A.st, kChunkedBin, internal, moved, cand, 0);
@@ -911,8 +963,10 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
                 break;
             }
         } else if (sp.kind == BIN_CHUNKED && b.nchunks > 0) {
-            BigArgs B{rows,    b.chunk_b, b.chunk_first, b.nch,   b.goff,  b.glog2, b.gcnt,
-                      b.gdone, b.gloop,   b.gkeys,       b.gvals, b.glist, b.chunk, b.nchunks};
+            BigArgs B{rows,    b.chunk_b, b.chunk_first, b.nch,   b.goff,    b.glog2,
+                      b.gcnt,  b.gdone,   b.gloop,       b.gkeys, b.gvals,   b.glist,
+                      b.chunk, b.nchunks, b.pgain,       b.pbest, b.pea,     b.sdone,
+                      b.soff,  b.slice_row, b.nslices};
             const int l2 = 31 - __builtin_clz(2 * b.chunk);
             const size_t smem = table_bytes<VT>(l2, true);
             const int grid = launch_cta_kernel(k_move_huge<WT, GT, VT, BT>, kHugeBlock, smem,
@@ -920,6 +974,13 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
             k_move_huge<WT, GT, VT, BT><<<grid, kHugeBlock, smem, s>>>(A, B);
             note_launch("k_move_huge");
             launched++;
+            if (b.nslices > 0) {  // some rows span several chunks
+                const int64_t cap = (int64_t)lc.num_sms * 4;
+                const int dgrid = (int)(b.nslices < cap ? b.nslices : cap);
+                k_move_huge_decide<WT, GT, VT, BT><<<dgrid, kHugeBlock, 0, s>>>(A, B);
+                note_launch("k_move_huge_decide");
+                launched++;
+            }
         }
         if (timed) cudaEventRecord(tm->ev[2 * bin + 1], s);
     }

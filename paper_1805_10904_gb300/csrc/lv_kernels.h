@@ -54,6 +54,7 @@ constexpr BinSpec kBinSpec[kNumBins] = {
     {BIN_CHUNKED, 512, 1},   // 10: CTA chunks merged in a global-memory table
 };
 constexpr int kChunkedBin = kNumBins - 1;
+constexpr int kHugeSlice = 4096;  // candidate-list entries per CTA when deciding a long row
 static_assert(kNumBins <= 16, "per-bin counters of SweepStats hold 16 bins");
 
 struct Bins {
@@ -80,6 +81,15 @@ struct Bins {
     void *gvals = nullptr;     // u32 or u64 per slot
     int32_t *glist = nullptr;
     int64_t gslots = 0;
+    // decision of multi-chunk rows: per slice of a row's candidate list one partial argmax
+    // (gain, label, e_{i->C(i)})
+    void *pgain = nullptr;     // 16 bytes per slice (int64 or int128 gain)
+    int32_t *pbest = nullptr;
+    i64 *pea = nullptr;
+    int32_t *sdone = nullptr;  // slices finished per row
+    int64_t *soff = nullptr;   // row b's slices are soff[b] .. soff[b+1] (nb + 1)
+    int32_t *slice_row = nullptr;
+    int64_t nslices = 0;
     const int32_t *rows(int b) const { return list + off[b]; }
 };
 
@@ -145,6 +155,10 @@ int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg 
 int launch_big_prep(const DevGraph &g, Bins &b, int64_t *scratch64, int32_t *scratch32,
                     cudaStream_t s, const LaunchCfg &lc);
 int launch_big_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc);
+// Decision slices of the multi-chunk rows (soff, then slice_row once the host has read the
+// total soff[nb] into nslices and sized slice_row).
+int launch_huge_slices(Bins &b, int64_t *scratch64, cudaStream_t s);
+int launch_huge_slice_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc);
 // Phase controllers of G graphs (one thread each): trace entry t of graph g at t * G + g;
 // *ndone counts the graphs whose phase has stopped.
 int launch_decide(SweepStats *st, LevelCtl *ctl, int G, i64 *tr_moved, i64 *tr_qn,

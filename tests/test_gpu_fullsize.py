@@ -54,7 +54,7 @@ def _qn_numpy(g, labels):
 
 def test_full_run_properties(graph, dev_graph):
     import paper_1805_10904_gb300 as lv
-    res = lv.Louvain(0, profile=True).run(*dev_graph)
+    res = lv.Louvain(0, profile=True, autotune=True).run(*dev_graph)
     assert res.num_levels >= 2
     prev = None
     for l in range(res.num_levels):
