@@ -30,9 +30,11 @@ if ROOT not in sys.path:
 
 METRIC = "local-move edge-visits/s, HBM % of peak; batched graphs/s vs plain (bit-exact)"
 UNIT = "edge-visits/s"
-WORKLOAD = ("R-MAT scale 22 (4,194,304 vertices, edge factor 16, a=0.57 b=0.19 c=0.19), "
-            "symmetrised, duplicates and self-loops dropped, int32 weights uniform in [1,16], "
-            "int32 ids, seed 22; full multi-level run to threshold 1e-6")
+def workload(scale: int) -> str:
+    return (f"R-MAT scale {scale} ({1 << scale:,} vertices, edge factor 16, a=0.57 b=0.19 "
+            "c=0.19), symmetrised, duplicates and self-loops dropped, int32 weights uniform in "
+            f"[1,16], int32 ids, seed {scale}; full multi-level run to threshold 1e-6; "
+            "autotuned degree bins")
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129 * 1024 * 1024
 KERNEL_NAMES = ["k_move_small", "k_move_group<8>", "k_move_group<32>", "k_move_cta<128>",
@@ -50,12 +52,12 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-sweeps", type=int, default=2)
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer arm (profiling)")
-    p.add_argument("--batch-graphs", type=int, default=0,
+    p.add_argument("--batch-graphs", type=int, default=512,
                    help="also time the mixed batch workload of this many graphs, batched vs "
                         "one graph at a time (0: skip)")
     p.add_argument("--batch-only", action="store_true",
                    help="time only the batch workload (its own JSON line)")
-    p.add_argument("--serve-requests", type=int, default=0,
+    p.add_argument("--serve-requests", type=int, default=400,
                    help="also run the serving workload with this many requests (0: skip)")
     p.add_argument("--serve-only", action="store_true",
                    help="run only the serving workload (its own JSON line)")
@@ -181,9 +183,9 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_traffic(kernel_name: str):
+def kernel_traffic(kernel_name: str, bins=None, chunk=None):
     """DRAM bytes per launch of the kernel from the committed ncu summary, or None when
-    the summary is missing or was taken on a different kernel source."""
+    the summary is missing or was taken on a different kernel source or bin layout."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -197,12 +199,15 @@ def kernel_traffic(kernel_name: str):
     entry = rec.get("kernels", {}).get(kernel_name)
     if not entry or entry.get("source_sha256") != sha:
         return None
+    if bins is not None and (list(entry.get("bins", [])) != list(bins) or
+                             entry.get("chunk_entries") != chunk):
+        return None
     return entry.get("dram_bytes_per_launch_full")
 
 
 def make_graph(scale: int):
     import graphgen as gg
-    return gg.rmat(scale, 16, 0.57, 0.19, 0.19, 1, 16, seed=22)
+    return gg.rmat(scale, 16, 0.57, 0.19, 0.19, 1, 16, seed=scale)
 
 
 # ---------------------------------------------------------------- CPU oracle timing
@@ -237,7 +242,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "graph_n": g.n, "graph_nnz": g.nnz,
+        "config": {"workload": workload(args.scale), "graph_n": g.n, "graph_nnz": g.nnz,
                    "parallelism": "single host thread"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -502,6 +507,7 @@ def run_native(args):
     for _ in range(args.warmup):
         step().close()
     torch.cuda.synchronize(dev)
+    tuned_bins, tuned_chunk, _, _ = h.autotune(rp, col, w)  # the cached choice of the warm-up
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -558,7 +564,7 @@ def run_native(args):
     if dom["time_ms"] > 0 and dom["launches"] > 0:
         achieved = dom["bytes"] / (dom["time_ms"] / 1000.0) / 1e9
         name = KERNEL_NAMES[dom["id"]]
-        traffic = kernel_traffic(name)
+        traffic = kernel_traffic(name, tuned_bins, tuned_chunk)
         roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": traffic,
@@ -579,8 +585,9 @@ def run_native(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "graph_n": g.n, "graph_nnz": g.nnz,
+        "config": {"workload": workload(args.scale), "graph_n": g.n, "graph_nnz": g.nnz,
                    "levels": levels, "parallelism": "replicas" if world > 1 else "single",
+                   "bins": list(tuned_bins), "chunk_entries": tuned_chunk,
                    "l2": "L2 flushed between timed steps (258 MB write); CSR of 1 GB > L2"},
         "roofline": roofline, "cpu_baseline": cpu,
         "kernels_ms_per_step": {

@@ -137,8 +137,8 @@ int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int3
 
 /* Choose the degree-bin thresholds and chunk length for a graph by measurement (this
  * library's addition; the thresholds only decide which kernel handles a row, never a
- * result).  Each trial times the first two sweeps of level 0 with a candidate set (sum of
- * the move kernels' CUDA-event times, best of two); a coordinate search over
+ * result).  Each trial is a whole run with a candidate set, timed as the sum of the local-
+ * move and induction kernels' CUDA-event times (best of two); a coordinate search over
  * {bin_small, bin_mid1, bin_mid2, bin_cta1, bin_cta2, bin_cta3, chunk_entries} keeps a
  * change when it is at least 2% faster.  The choice is cached on the handle per (n, nnz)
  * and used by louvain_run when autotune = 1.  Arguments as in louvain_run; bins_out gets

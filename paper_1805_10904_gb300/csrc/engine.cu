@@ -1659,9 +1659,9 @@ struct Server {
 // ---------------------------------------------------------------------- autotuner
 //
 // Degree-bin thresholds and the chunk length only decide which kernel handles a row, never
-// a result, so they can be chosen by measurement: each trial runs the first two sweeps of
-// level 0 with a candidate set (best of two runs, sum of the move kernels' event times),
-// and a coordinate search over the thresholds keeps a change only when it is at least 2%
+// a result, so they can be chosen by measurement: each trial is a whole run with a
+// candidate set (best of two, sum of the move and induction kernels' event times), and a
+// coordinate search over the thresholds keeps a change only when it is at least 2%
 // faster.  The choice is cached on the handle per (vertex count, entry count).
 
 void get_bins(const louvain_config &c, int32_t b[7])
@@ -1740,8 +1740,6 @@ void tuned_bins(louvain_handle *h, cudaStream_t s, DevAlloc &A, int64_t n, const
         kind = LOUVAIN_PTR_DEVICE;
     }
     louvain_config base = h->cfg;
-    base.max_levels = 1;
-    base.max_iters = 2;
     base.profile = 1;
     base.autotune = 0;
     base.cuda_graphs = 0;
@@ -1757,7 +1755,7 @@ void tuned_bins(louvain_handle *h, cudaStream_t s, DevAlloc &A, int64_t n, const
             r->ctx = h->cfg.alloc_ctx;
             std::vector<louvain_result *> outs{r.get()};
             run_engine(h, t, s, A, n, rp, col, w, kind, 1, nullptr, nullptr, outs);
-            best = std::min(best, r->times[0]);
+            best = std::min(best, r->times[0] + r->times[1]);
             trials++;
         }
         return best;
