@@ -52,6 +52,8 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-sweeps", type=int, default=2)
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer arm (profiling)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="use the default degree bins instead of tuning them (profiling)")
     p.add_argument("--batch-graphs", type=int, default=512,
                    help="also time the mixed batch workload of this many graphs, batched vs "
                         "one graph at a time (0: skip)")
@@ -261,7 +263,7 @@ def run_e2e(args, g, lv, local, stream, world, dev):
     rp_h = torch.from_numpy(g.rp).pin_memory()
     col_h = torch.from_numpy(g.col).pin_memory()
     w_h = torch.from_numpy(g.w).pin_memory()
-    h2 = lv.Louvain(local, profile=False, autotune=True)
+    h2 = lv.Louvain(local, profile=False, autotune=not args.no_autotune)
     for _ in range(max(1, args.warmup)):
         r = h2.run(rp_h, col_h, w_h, stream=stream.cuda_stream)
         for l in range(r.num_levels):
@@ -498,7 +500,7 @@ def run_native(args):
     col = torch.from_numpy(g.col).to(dev)
     w = torch.from_numpy(g.w).to(dev)
     stream = torch.cuda.current_stream(dev)
-    h = lv.Louvain(local, profile=True, autotune=True)
+    h = lv.Louvain(local, profile=True, autotune=not args.no_autotune)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
 
     def step():
@@ -507,7 +509,10 @@ def run_native(args):
     for _ in range(args.warmup):
         step().close()
     torch.cuda.synchronize(dev)
-    tuned_bins, tuned_chunk, _, _ = h.autotune(rp, col, w)  # the cached choice of the warm-up
+    if args.no_autotune:
+        tuned_bins, tuned_chunk = (8, 32, 128, 512, 2048, 12288), 4096
+    else:
+        tuned_bins, tuned_chunk, _, _ = h.autotune(rp, col, w)  # the warm-up's cached choice
 
     clocks = ClockSampler(local)
     clocks.start()
