@@ -39,6 +39,9 @@
  *       i moves only if the best gain is strictly larger than the gain of staying.
  *   R6  singlet rule as a veto: if C(i) and the chosen target are both singletons in the
  *       previous iteration's state and target > C(i), i stays.
+ *   R14 threshold_mode 1 (a variant): the phase test is the relative one printed in
+ *       Algorithm 1, |Q_curr - Q_prev| / |Q_prev| < theta, exact; Q_prev = 0 only stops on
+ *       an unchanged Q; the outer test stays absolute (R9)
  *   R7  phase stop: no vertex moved, or (Qn_new - Qn_prev) * theta_den < theta_num * TW^2
  *       (absolute gain test on exact integers, theta = 1/10^6 by default, Qn_prev starts at
  *       the state before the first sweep), or the sweep cap is reached.  The state after
@@ -453,9 +456,22 @@ static int below_threshold(i128 qn_new, i128 qn_old, int64_t tw, int64_t num, in
                      mul_u128_u64(tw2, (uint64_t)num));
 }
 
+/* Relative form of the phase test, as printed in Algorithm 1 (reading R14):
+ *   |Q_curr - Q_prev| / |Q_prev| < theta   <=>   |qn_new - qn_old| * den < num * |qn_old|,
+ * exact in 192 bits (both Qn carry the same factor TW^2).  Q_prev = 0 leaves the ratio
+ * undefined; the test then holds only when Q did not change. */
+static int below_threshold_rel(i128 qn_new, i128 qn_old, int64_t num, int64_t den)
+{
+    i128 diff = qn_new - qn_old;
+    unsigned __int128 ad = (unsigned __int128)(diff < 0 ? -diff : diff);
+    unsigned __int128 ao = (unsigned __int128)(qn_old < 0 ? -qn_old : qn_old);
+    if (ao == 0) return ad == 0;
+    return u192_less(mul_u128_u64(ad, (uint64_t)den), mul_u128_u64(ao, (uint64_t)num));
+}
+
 static int louvain_run_impl(const og_graph *g0, int64_t theta_num, int64_t theta_den,
                             int32_t max_iters, int32_t max_levels, int32_t vf, int32_t vf_all,
-                            og_result *r)
+                            int32_t rel, og_result *r)
 {
     int64_t n0 = g0->n;
     og_graph g = {0, 0, NULL, NULL, NULL};
@@ -526,7 +542,9 @@ static int louvain_run_impl(const og_graph *g0, int64_t theta_num, int64_t theta
             qn_new = modularity_qn(&g, C, delta, TW, deg_tmp, size_tmp);
             if ((rc = trace_push(r, level, iters, moved, qn_new)) != ORACLE_OK) goto done;
             if (moved == 0) break;
-            if (below_threshold(qn_new, qn_prev, TW, theta_num, theta_den)) break;
+            if (rel ? below_threshold_rel(qn_new, qn_prev, theta_num, theta_den)
+                    : below_threshold(qn_new, qn_prev, TW, theta_num, theta_den))
+                break;
             if (iters >= max_iters) {
                 r->hit_iter_cap = 1;
                 break;
@@ -594,11 +612,18 @@ static void put_i128(i128 v, int64_t out[2])
 
 int32_t oracle_abi_version(void) { return 1; }
 
-/* Full run.  Returns an opaque result or NULL; *status gets ORACLE_OK / _INVALID / _OOM. */
-void *oracle_run(int64_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
-                 int64_t theta_num, int64_t theta_den, int32_t max_iters, int32_t max_levels,
-                 int32_t vertex_following_on, int32_t vf_all_levels, int32_t *status)
+/* Full run.  Returns an opaque result or NULL; *status gets ORACLE_OK / _INVALID / _OOM.
+ * threshold_mode 0: absolute phase test (R7); 1: relative phase test of Algorithm 1 (R14).
+ * The outer test of Algorithm 2 is absolute in both modes. */
+void *oracle_run_ex(int64_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
+                    int64_t theta_num, int64_t theta_den, int32_t max_iters, int32_t max_levels,
+                    int32_t vertex_following_on, int32_t vf_all_levels, int32_t threshold_mode,
+                    int32_t *status)
 {
+    if (threshold_mode != 0 && threshold_mode != 1) {
+        if (status) *status = ORACLE_ERR_INVALID;
+        return NULL;
+    }
     og_graph g = {0, 0, NULL, NULL, NULL};
     int rc = graph_from_input(&g, n, rp, col, w, NULL);
     if (rc != ORACLE_OK || theta_den <= 0 || theta_num < 0 || theta_den > INT32_MAX ||
@@ -632,7 +657,7 @@ void *oracle_run(int64_t n, const int64_t *rp, const int32_t *col, const int32_t
         return NULL;
     }
     rc = louvain_run_impl(&g, theta_num, theta_den, max_iters, max_levels, vertex_following_on,
-                          vf_all_levels, r);
+                          vf_all_levels, threshold_mode, r);
     graph_free(&g);
     if (rc != ORACLE_OK) {
         result_free(r);
@@ -640,6 +665,14 @@ void *oracle_run(int64_t n, const int64_t *rp, const int32_t *col, const int32_t
     }
     if (status) *status = rc;
     return r;
+}
+
+void *oracle_run(int64_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
+                 int64_t theta_num, int64_t theta_den, int32_t max_iters, int32_t max_levels,
+                 int32_t vertex_following_on, int32_t vf_all_levels, int32_t *status)
+{
+    return oracle_run_ex(n, rp, col, w, theta_num, theta_den, max_iters, max_levels,
+                         vertex_following_on, vf_all_levels, 0, status);
 }
 
 int32_t oracle_res_num_levels(const void *h) { return ((const og_result *)h)->num_levels; }

@@ -377,3 +377,47 @@ def test_run_trace_equals_repeated_sweeps(seed, kind):
     if r.levels:
         new_id, _ = oracle.renumber(C)
         assert np.array_equal(r.levels[0].labels, new_id[C])
+
+
+@pytest.mark.parametrize("seed,theta", [(s, t) for s in range(4) for t in ((1, 100), (1, 10_000))])
+def test_relative_threshold_trace(seed, theta):
+    """Relative phase test of Algorithm 1 (threshold_mode 1): the phase stops at the first
+    sweep with |Q_curr - Q_prev| / |Q_prev| < theta, evaluated here with exact fractions on
+    repeated single sweeps, or when nothing moved; Q_prev starts at the initial state's Q."""
+    from fractions import Fraction
+    g = gg.rmat(9 + seed % 2, 8, seed=40 + seed) if seed % 2 else \
+        gg.sbm(400, 40, 0.2, 0.01, 1, 4, seed=seed)
+    r = oracle.louvain(g.rp, g.col, g.w, max_levels=1, theta=theta, threshold_mode=1)
+    w = g.w.astype(np.int64)
+    C = oracle.vertex_following(g.rp, g.col)
+    qn_prev, tw = oracle.modularity(g.rp, g.col, w, C)
+    th = Fraction(theta[0], theta[1])
+    trace = []
+    for it in range(1, 1001):
+        C, moved = oracle.sweep(g.rp, g.col, w, C)
+        qn, _ = oracle.modularity(g.rp, g.col, w, C)
+        trace.append((0, it, moved, qn))
+        if moved == 0:
+            break
+        if qn_prev == 0:
+            if qn == 0:
+                break
+        elif abs(Fraction(qn - qn_prev, qn_prev)) < th:
+            break
+        qn_prev = qn
+    assert r.trace == trace
+    # the absolute and the relative test are different rules: at least one case differs
+    a = oracle.louvain(g.rp, g.col, g.w, max_levels=1, theta=theta)
+    assert a.trace[0] == r.trace[0]
+
+
+def test_relative_threshold_differs_from_absolute():
+    g = gg.sbm(600, 30, 0.3, 0.01, 1, 4, seed=5)
+    diffs = 0
+    for theta in ((1, 10), (1, 100), (1, 1000)):
+        a = oracle.louvain(g.rp, g.col, g.w, theta=theta)
+        r = oracle.louvain(g.rp, g.col, g.w, theta=theta, threshold_mode=1)
+        diffs += a.trace != r.trace
+    assert diffs > 0
+    with pytest.raises(oracle.OracleError):
+        oracle.louvain(g.rp, g.col, g.w, threshold_mode=2)
