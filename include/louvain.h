@@ -94,7 +94,12 @@ typedef struct {
     int32_t autotune;          /* 1: louvain_run picks the bin thresholds and chunk length  */
                                /* by measurement (louvain_autotune) on the first graph of   */
                                /* each (n, nnz) and reuses them; the results do not change */
-    int32_t reserved[2];       /* must be zero                                           */
+    int32_t threshold_mode;    /* 0 (default): absolute phase test (Qn_new - Qn_prev) < theta */
+                               /* * (2W)^2; 1: the relative test printed in Algorithm 1,    */
+                               /* |Q_new - Q_prev| / |Q_prev| < theta (Q_prev = 0 stops only */
+                               /* when Q is unchanged); the outer test of Algorithm 2 is    */
+                               /* absolute in both modes                                    */
+    int32_t reserved[1];       /* must be zero                                           */
     /* device memory: both NULL means stream-ordered cudaMallocAsync/cudaFreeAsync */
     louvain_alloc_fn alloc;
     louvain_free_fn free;

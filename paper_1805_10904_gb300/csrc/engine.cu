@@ -883,6 +883,7 @@ void Engine::step(std::vector<Member *> &retired)
         c.theta_num = cfg.theta_num;
         c.theta_den = cfg.theta_den;
         c.max_iters = cfg.max_iters;
+        c.rel = cfg.threshold_mode == 1;
     }
     LevelCtl *ctl_dev = batch ? d_ctls.p : &d_sc->ctl;
     SweepStats *st_dev = batch ? d_stats.p : &d_sc->st;
@@ -1855,6 +1856,10 @@ static int check_config(louvain_config &c, std::string &msg)
         c.bin_cta2 < c.bin_cta1 || c.bin_cta3 < c.bin_cta2 || c.bin_cta3 > 12288) {
         msg = "bins need 0 <= small <= 8 <= ..., small <= mid1 <= 32, mid1 <= mid2 <= 128, "
               "mid2 <= cta1 <= cta2 <= cta3 <= 12288";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (c.threshold_mode != 0 && c.threshold_mode != 1) {
+        msg = "threshold_mode must be 0 (absolute) or 1 (relative)";
         return LOUVAIN_ERR_INVALID_ARG;
     }
     if (c.chunk_entries == 0) c.chunk_entries = 4096;

@@ -571,6 +571,32 @@ __device__ bool dev_below_threshold(i128 qn_new, i128 qn_old, i64 tw, i64 num, i
     return x0 < y0;
 }
 
+// 192-bit a * m for a 128-bit magnitude a and a 64-bit m: (top 64, middle 64, low 64)
+__device__ __forceinline__ void mul192(u128 a, u64 m, u64 &t2, u64 &t1, u64 &t0)
+{
+    const u128 lo = (u128)(u64)a * m, hi = (u128)(u64)(a >> 64) * m;
+    const u128 mid = (lo >> 64) + (u64)hi;
+    t2 = (u64)(hi >> 64) + (u64)(mid >> 64);
+    t1 = (u64)mid;
+    t0 = (u64)lo;
+}
+
+// Relative phase test printed in Algorithm 1: |qn_new - qn_old| * den < num * |qn_old|
+// (both Qn carry the factor (2W)^2); Q_prev = 0 stops only on an unchanged Q.
+__device__ bool dev_below_threshold_rel(i128 qn_new, i128 qn_old, i64 num, i64 den)
+{
+    const i128 diff = qn_new - qn_old;
+    const u128 ad = (u128)(diff < 0 ? -diff : diff);
+    const u128 ao = (u128)(qn_old < 0 ? -qn_old : qn_old);
+    if (ao == 0) return ad == 0;
+    u64 x2, x1, x0, y2, y1, y0;
+    mul192(ad, (u64)den, x2, x1, x0);
+    mul192(ao, (u64)num, y2, y1, y0);
+    if (x2 != y2) return x2 < y2;
+    if (x1 != y1) return x1 < y1;
+    return x0 < y0;
+}
+
 // Runs after sweep k (1-based) on state C_{k-1}; the sweep measured Qn(C_{k-1}) and
 // proposed C_k.  Stopping rule (Algorithm 1 with the absolute threshold on exact Qn):
 //   k >= 2: stop with C_{k-1} if Qn(C_{k-1}) - Qn(C_{k-2}) is below theta, or if k-1
@@ -600,8 +626,9 @@ __global__ void k_decide(SweepStats *sts, LevelCtl *ctls, int G, i64 *tr_moved, 
                 tr_moved[(size_t)t * G + g] = ctl->moved_last;
                 i128_to(qn, &tr_qn[2 * ((size_t)t * G + g)]);
             }
-            if (dev_below_threshold(qn, i128_from(ctl->qn_prev), ctl->tw, ctl->theta_num,
-                                    ctl->theta_den)) {
+            const i128 qp = i128_from(ctl->qn_prev);
+            if (ctl->rel ? dev_below_threshold_rel(qn, qp, ctl->theta_num, ctl->theta_den)
+                         : dev_below_threshold(qn, qp, ctl->tw, ctl->theta_num, ctl->theta_den)) {
                 stop = true;
                 iters = k - 1;
             } else if (k - 1 >= ctl->max_iters) {

@@ -49,7 +49,7 @@ struct LevelCtl {
     int done;      // 1 once the phase has stopped
     int hit_cap;
     int iters;     // sweeps applied when the phase stopped
-    int pad0;
+    int rel;       // 1: relative phase test |dQ / Q_prev| < theta (Algorithm 1 as printed)
     i64 moved_last;
     i64 qn_init[2];   // {hi, lo}
     i64 qn_prev[2];

@@ -59,7 +59,8 @@ class Config(ctypes.Structure):
         ("profile", ctypes.c_int32),
         ("cuda_graphs", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("threshold_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
@@ -279,7 +280,7 @@ class Louvain:
                  vf_all_levels: bool = False, checks: int = 1, force_int128: bool = False,
                  wide_sums: bool = False, bins=None, chunk_entries: int = 0,
                  profile: bool = False, torch_alloc: bool = True, cuda_graphs: bool = True,
-                 autotune: bool = False):
+                 autotune: bool = False, threshold_mode: int = 0):
         lib = load()
         self._lib = lib
         cfg = Config()
@@ -300,6 +301,7 @@ class Louvain:
         cfg.profile = int(profile)
         cfg.cuda_graphs = int(cuda_graphs)
         cfg.autotune = int(autotune)
+        cfg.threshold_mode = int(threshold_mode)
         self.device = device
         if torch_alloc:
             import torch

@@ -82,6 +82,7 @@ BATCH_CONFIGS = [
     {"max_iters": 2, "vertex_following": False},
     {"vf_all_levels": True, "theta": (0, 1)},
     {"cuda_graphs": False},
+    {"threshold_mode": 1, "theta": (1, 1000)},
 ]
 
 
@@ -94,7 +95,7 @@ def test_batch_equals_plain_and_oracle(torch, lv, ci):
     batch = h.run_batch(vptr, *dev(torch, rp, col, w), graph_eptr=eptr)
     assert len(batch) == len(graphs)
     okw = {k: kw[k] for k in ("theta", "max_iters", "max_levels", "vertex_following",
-                              "vf_all_levels") if k in kw}
+                              "vf_all_levels", "threshold_mode") if k in kw}
     for g, res in zip(graphs, batch):
         plain = h.run(*dev(torch, g.rp, g.col, g.w))
         same_result(res, plain)
@@ -164,3 +165,20 @@ def test_batch_rejects_bad_input(torch, lv):
     # the handle stays usable
     res = h.run_batch(vptr, *dev(torch, rp, col, w))
     matches_oracle(res[1], oracle.louvain(b.rp, b.col, b.w))
+
+
+def test_batch_mixing_wide_and_narrow_graphs(torch, lv):
+    """One graph with 2W above 2^32 switches the whole step to int128 gains, 64-bit table
+    sums and int64 coarse weights; the other graphs' results must not change."""
+    big_w = gg.sbm(500, 25, 0.3, 0.01, 1, 4, seed=9)
+    w = big_w.w.astype(np.int64) * (1 << 22)  # weights up to 2^24, 2W above 2^32
+    assert int(w.sum()) > 2 ** 32 and int(w.max()) < 2 ** 31
+    heavy = gg.Graph(big_w.rp, big_w.col, w.astype(np.int32), "heavy")
+    graphs = [gg.sbm(700, 35, 0.25, 0.01, 1, 4, seed=1), heavy, gg.rmat(10, 8, seed=4),
+              gg.cliques_ring(8, 6)]
+    h = lv.Louvain(0)
+    vptr, eptr, rp, col, ww = lv.stack_graphs([(g.rp, g.col, g.w) for g in graphs])
+    batch = h.run_batch(vptr, *dev(torch, rp, col, ww), graph_eptr=eptr)
+    for g, res in zip(graphs, batch):
+        same_result(res, h.run(*dev(torch, g.rp, g.col, g.w)))
+        matches_oracle(res, oracle.louvain(g.rp, g.col, g.w))

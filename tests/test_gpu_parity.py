@@ -53,7 +53,7 @@ def assert_parity(res, ref, check_trace=True):
 
 def run_both(torch, lv, g, **kw):
     okw = {k: kw[k] for k in ("theta", "max_iters", "max_levels", "vertex_following",
-                              "vf_all_levels") if k in kw}
+                              "vf_all_levels", "threshold_mode") if k in kw}
     ref = oracle.louvain(g.rp, g.col, g.w, **okw)
     h = lv.Louvain(0, **kw)
     res = h.run(*to_dev(torch, g))
@@ -262,3 +262,17 @@ def test_autotuned_bins_give_the_same_result(torch, lv):
     assert chunk in (1024, 2048, 4096)
     assert_parity(lv.Louvain(0, bins=bins, chunk_entries=chunk).run(*d), ref)
     assert h2.autotune(*d)[3] == 0  # cached on the handle
+
+
+@pytest.mark.parametrize("theta", [(1, 1_000_000), (1, 1000), (1, 20)])
+@pytest.mark.parametrize("kind", ["sbm", "rmat", "small"])
+def test_relative_threshold_mode(torch, lv, theta, kind):
+    """threshold_mode 1: the relative phase test of Algorithm 1 on the device controller."""
+    if kind == "sbm":
+        g = gg.sbm(2048, 64, 0.15, 0.003, 1, 4, seed=3)
+    elif kind == "rmat":
+        g = gg.rmat(13, 16, seed=31)
+    else:
+        g = gg.random_small(4242, n_max=60)
+    res, ref = run_both(torch, lv, g, theta=theta, threshold_mode=1)
+    assert_parity(res, ref)
