@@ -58,7 +58,7 @@ def _load():
     lib.oracle_run.restype = P
     lib.oracle_run.argtypes = [i64, P, P, P, i64, i64, i32, i32, i32, i32, P]
     lib.oracle_run_ex.restype = P
-    lib.oracle_run_ex.argtypes = [i64, P, P, P, i64, i64, i32, i32, i32, i32, i32, P]
+    lib.oracle_run_ex.argtypes = [i64, P, P, P, i64, i64, i32, i32, i32, i32, i32, i32, P]
     lib.oracle_res_num_levels.restype = i32
     lib.oracle_res_num_levels.argtypes = [P]
     lib.oracle_res_tw.restype = i64
@@ -151,16 +151,19 @@ class OracleResult:
 
 
 def louvain(rp, col, w=None, theta=(1, 1_000_000), max_iters=1000, max_levels=64,
-            vertex_following=True, vf_all_levels=False, threshold_mode=0) -> OracleResult:
+            vertex_following=True, vf_all_levels=False, threshold_mode=0,
+            post_merge=False) -> OracleResult:
     """Full multi-level synchronous Louvain (Algorithm 2 around Algorithm 1).
-    threshold_mode 0: absolute phase test; 1: the relative test printed in Algorithm 1."""
+    threshold_mode 0: absolute phase test; 1: the relative test printed in Algorithm 1.
+    post_merge: the post-phase merge of single-neighbour-community vertices (Sec. 5.1.2)."""
     lib = _load()
     rp, col, w = _csr(rp, col, w, np.int32)
     n = len(rp) - 1
     st = ctypes.c_int32(0)
     h = lib.oracle_run_ex(n, _ptr(rp), _ptr(col), _ptr(w), int(theta[0]), int(theta[1]),
                           int(max_iters), int(max_levels), int(bool(vertex_following)),
-                          int(bool(vf_all_levels)), int(threshold_mode), ctypes.addressof(st))
+                          int(bool(vf_all_levels)), int(threshold_mode), int(bool(post_merge)),
+                          ctypes.addressof(st))
     if not h:
         raise OracleError(f"oracle_run failed with status {st.value}")
     try:

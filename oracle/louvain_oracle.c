@@ -39,6 +39,9 @@
  *       i moves only if the best gain is strictly larger than the gain of staying.
  *   R6  singlet rule as a veto: if C(i) and the chosen target are both singletons in the
  *       previous iteration's state and target > C(i), i stays.
+ *   R15 post_merge (a variant): after each phase, a vertex whose non-loop neighbours all
+ *       lie in one other community joins it if that move's Eq. 4 gain is positive; all
+ *       decisions on the post-phase state; the level records the merged state and its Qn
  *   R14 threshold_mode 1 (a variant): the phase test is the relative one printed in
  *       Algorithm 1, |Q_curr - Q_prev| / |Q_prev| < theta, exact; Q_prev = 0 only stops on
  *       an unchanged Q; the outer test stays absolute (R9)
@@ -419,6 +422,40 @@ static int trace_push(og_result *r, int32_t level, int32_t iter, int64_t moved, 
     return ORACLE_OK;
 }
 
+/* Post-phase merge of Sec. 5.1.2 (a variant, reading R15).  On the post-phase state C
+ * (deg, size its community degrees), every vertex i whose non-loop neighbours all lie in
+ * one community c != C(i) joins c when that move has a positive Eq. 4 gain:
+ *   TW * e_{i->c} - delta_i * deg_c  >  TW * e_{i->C(i)} - delta_i * (deg_{C(i)} - delta_i),
+ * with e_{i->C(i)} = 0 here (no neighbour shares i's community).  All decisions read the
+ * same state; the moves are written to Cnext and returned as a count. */
+static int64_t post_merge(const og_graph *g, const int32_t *C, const int64_t *deg,
+                          const int64_t *delta, int64_t TW, int32_t *Cnext)
+{
+    int64_t moved = 0;
+    for (int64_t i = 0; i < g->n; i++) {
+        int32_t a = C[i];
+        Cnext[i] = a;
+        int32_t c = -1;
+        int single = 1;
+        int64_t e = 0;
+        for (int64_t k = g->rp[i]; k < g->rp[i + 1]; k++) {
+            int32_t j = g->col[k];
+            if (j == (int32_t)i) continue; /* the loop is not a neighbour */
+            if (c < 0) c = C[j];
+            else if (C[j] != c) single = 0;
+            e += g->w[k];
+        }
+        if (c < 0 || !single || c == a) continue;
+        i128 g_move = (i128)TW * e - (i128)delta[i] * deg[c];
+        i128 g_stay = -(i128)delta[i] * (deg[a] - delta[i]);
+        if (g_move > g_stay) {
+            Cnext[i] = c;
+            moved++;
+        }
+    }
+    return moved;
+}
+
 /* 192-bit unsigned product of a 128-bit and a 64-bit magnitude, limbs little-endian. */
 typedef struct {
     uint64_t limb[3];
@@ -471,7 +508,7 @@ static int below_threshold_rel(i128 qn_new, i128 qn_old, int64_t num, int64_t de
 
 static int louvain_run_impl(const og_graph *g0, int64_t theta_num, int64_t theta_den,
                             int32_t max_iters, int32_t max_levels, int32_t vf, int32_t vf_all,
-                            int32_t rel, og_result *r)
+                            int32_t rel, int32_t merge, og_result *r)
 {
     int64_t n0 = g0->n;
     og_graph g = {0, 0, NULL, NULL, NULL};
@@ -551,6 +588,14 @@ static int louvain_run_impl(const og_graph *g0, int64_t theta_num, int64_t theta
             }
             qn_prev = qn_new;
         }
+        if (merge) { /* R15: after the phase, before renumbering; Qn of the merged state */
+            post_merge(&g, C, deg, delta, TW, Cnext);
+            int32_t *t = C;
+            C = Cnext;
+            Cnext = t;
+            community_degrees(n, C, delta, deg, size);
+            qn_new = modularity_qn(&g, C, delta, TW, deg_tmp, size_tmp);
+        }
 
         int64_t k = renumber(n, C, new_id);
         if (k == n) break; /* nothing merged: no new level (R9) */
@@ -614,11 +659,12 @@ int32_t oracle_abi_version(void) { return 1; }
 
 /* Full run.  Returns an opaque result or NULL; *status gets ORACLE_OK / _INVALID / _OOM.
  * threshold_mode 0: absolute phase test (R7); 1: relative phase test of Algorithm 1 (R14).
- * The outer test of Algorithm 2 is absolute in both modes. */
+ * The outer test of Algorithm 2 is absolute in both modes.  post_merge_on: the post-phase
+ * merge of Sec. 5.1.2 (R15) after every phase. */
 void *oracle_run_ex(int64_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
                     int64_t theta_num, int64_t theta_den, int32_t max_iters, int32_t max_levels,
                     int32_t vertex_following_on, int32_t vf_all_levels, int32_t threshold_mode,
-                    int32_t *status)
+                    int32_t post_merge_on, int32_t *status)
 {
     if (threshold_mode != 0 && threshold_mode != 1) {
         if (status) *status = ORACLE_ERR_INVALID;
@@ -657,7 +703,7 @@ void *oracle_run_ex(int64_t n, const int64_t *rp, const int32_t *col, const int3
         return NULL;
     }
     rc = louvain_run_impl(&g, theta_num, theta_den, max_iters, max_levels, vertex_following_on,
-                          vf_all_levels, threshold_mode, r);
+                          vf_all_levels, threshold_mode, post_merge_on, r);
     graph_free(&g);
     if (rc != ORACLE_OK) {
         result_free(r);
@@ -672,7 +718,7 @@ void *oracle_run(int64_t n, const int64_t *rp, const int32_t *col, const int32_t
                  int32_t vertex_following_on, int32_t vf_all_levels, int32_t *status)
 {
     return oracle_run_ex(n, rp, col, w, theta_num, theta_den, max_iters, max_levels,
-                         vertex_following_on, vf_all_levels, 0, status);
+                         vertex_following_on, vf_all_levels, 0, 0, status);
 }
 
 int32_t oracle_res_num_levels(const void *h) { return ((const og_result *)h)->num_levels; }

@@ -421,3 +421,46 @@ def test_relative_threshold_differs_from_absolute():
     assert diffs > 0
     with pytest.raises(oracle.OracleError):
         oracle.louvain(g.rp, g.col, g.w, threshold_mode=2)
+
+
+def test_post_merge_hand_cases():
+    """Post-phase merge (Sec. 5.1.2, reading R15), worked by hand with vertex following off
+    and one sweep per phase.
+
+    Path 0-1-2, unit weights (2W = 4, delta = 1, 2, 1): from singletons vertex 0 is vetoed
+    (target 1 > 0, both singletons), 1 joins 0 (gains to 0 and 2 tie at 2, smaller label),
+    2 joins 1, so the phase ends with (0, 0, 1), Qn = 4*2 - (3^2 + 1^2) = -2.  Vertex 2's
+    only neighbour community is {0, 1} with gain 4*1 - 1*3 = 1 > 0 (staying: 0), so the
+    merge moves it: one community, Qn = 4*4 - 4^2 = 0.
+
+    An isolated pair with loops of weight 10 (2W = 22, delta = 11 each) never merges: the
+    move's gain 22*1 - 11*11 is negative, in the phase and in the merge."""
+    g = gg.from_edges(3, [(0, 1, 1), (1, 2, 1)])
+    plain = oracle.louvain(g.rp, g.col, g.w, vertex_following=False, max_iters=1, max_levels=1)
+    merged = oracle.louvain(g.rp, g.col, g.w, vertex_following=False, max_iters=1, max_levels=1,
+                            post_merge=True)
+    assert list(plain.levels[0].labels) == [0, 0, 1] and plain.levels[0].qn == -2
+    assert list(merged.levels[0].labels) == [0, 0, 0] and merged.levels[0].qn == 0
+    assert merged.levels[0].ncomm == 1 and merged.trace == plain.trace
+    pair = gg.from_edges(2, [(0, 1, 1), (0, 0, 10), (1, 1, 10)])
+    for pm in (False, True):
+        r = oracle.louvain(pair.rp, pair.col, pair.w, vertex_following=False, post_merge=pm)
+        assert r.levels == [] and r.trace == [(0, 1, 0, 22 * 20 - 2 * 121)]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_post_merge_levels_are_consistent(seed):
+    """With the merge, every recorded level's Qn is Eq. 3 of its labels, levels nest, and 2W
+    and Theorem 1 hold."""
+    g = gg.random_small(5000 + seed, n_max=70) if seed % 2 else gg.rmat(9, 8, seed=seed)
+    r = oracle.louvain(g.rp, g.col, g.w, post_merge=True, max_iters=2)
+    w = g.w.astype(np.int64)
+    prev = None
+    for lev in r.levels:
+        qn, tw = oracle.modularity(g.rp, g.col, w, lev.labels)
+        assert qn == lev.qn and tw == r.tw
+        if prev is not None:
+            first = np.full(int(prev.max()) + 1, -1, np.int64)
+            first[prev] = lev.labels
+            assert np.array_equal(first[prev], lev.labels)
+        prev = lev.labels
