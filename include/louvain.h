@@ -99,6 +99,10 @@ typedef struct {
                                /* |Q_new - Q_prev| / |Q_prev| < theta (Q_prev = 0 stops only */
                                /* when Q is unchanged); the outer test of Algorithm 2 is    */
                                /* absolute in both modes                                    */
+    int32_t post_merge;        /* 1: after every phase, a vertex whose non-loop neighbours  */
+                               /* all lie in one other community joins it if that move's    */
+                               /* Eq. 4 gain is positive (Sec. 5.1.2); the level then       */
+                               /* records the merged state and its modularity; 0 (default) */
     int32_t reserved[1];       /* must be zero                                           */
     /* device memory: both NULL means stream-ordered cudaMallocAsync/cudaFreeAsync */
     louvain_alloc_fn alloc;

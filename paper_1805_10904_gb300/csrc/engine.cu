@@ -990,6 +990,11 @@ void Engine::step(std::vector<Member *> &retired)
         }
     }
     sg.reset();
+    if (cfg.post_merge) {  // Sec. 5.1.2: after the phase, before renumbering
+        kernels += launch_post_merge(G, st, vgp, batch ? (const i64 *)d_tw.p : nullptr, TW, wide,
+                                     st_dev, ctl_dev, M, s, lc);
+        sync_scalars();
+    }
     if (batch) {
         CK(cudaMemcpyAsync(h_ctl.data(), d_ctls.p, sizeof(LevelCtl) * M, cudaMemcpyDeviceToHost,
                            s));
@@ -1856,6 +1861,10 @@ static int check_config(louvain_config &c, std::string &msg)
         c.bin_cta2 < c.bin_cta1 || c.bin_cta3 < c.bin_cta2 || c.bin_cta3 > 12288) {
         msg = "bins need 0 <= small <= 8 <= ..., small <= mid1 <= 32, mid1 <= mid2 <= 128, "
               "mid2 <= cta1 <= cta2 <= cta3 <= 12288";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (c.post_merge != 0 && c.post_merge != 1) {
+        msg = "post_merge must be 0 or 1";
         return LOUVAIN_ERR_INVALID_ARG;
     }
     if (c.threshold_mode != 0 && c.threshold_mode != 1) {

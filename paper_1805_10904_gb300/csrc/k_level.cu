@@ -703,12 +703,12 @@ __global__ void __launch_bounds__(kBlock) k_apply(int64_t n, int32_t *C, const i
                                                   i64 *deg, int32_t *size, const i64 *delta,
                                                   const LevelCtl *ctl, const int32_t *vg)
 {
-    if (!vg && *(volatile const int *)&ctl->done) return;
+    if (!vg && ctl && *(volatile const int *)&ctl->done) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = C[i], b = Cnext[i];
         if (a == b) continue;
-        if (vg && ctl[vg[i]].done) continue;
+        if (vg && ctl && ctl[vg[i]].done) continue;
         const i64 d = delta[i];
         atomicAdd((u64 *)&deg[b], (u64)d);
         atomicAdd((u64 *)&deg[a], (u64)(-d));
@@ -725,6 +725,141 @@ int launch_apply(int64_t n, const PhaseState &st, const LevelCtl *ctl, const int
     k_apply<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(n, st.C, st.Cnext, st.deg,
                                                                  st.size, st.delta, ctl, vg);
     return 1;
+}
+
+// ------------------------------------------------------------------ post-phase merge
+// Sec. 5.1.2 pushes the vertices that have a single neighbouring community into it once the
+// iterations are done (reading: only when the move's Eq. 4 gain is positive).  One warp per
+// vertex: the smallest and largest community among the non-loop neighbours decide whether
+// there is exactly one, the weight into it is their sum; the decision reads the post-phase
+// state only and is written to Cnext.
+template <typename WT, typename GT>
+__global__ void __launch_bounds__(kBlock) k_post_merge(int64_t n, const int64_t *rp,
+                                                       const int32_t *col, const WT *w,
+                                                       const int32_t *C, const i64 *deg,
+                                                       const i64 *delta, const int32_t *vg,
+                                                       const i64 *gtw, i64 tw1, int32_t *Cnext)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int32_t a = C[i];
+        int cmin = INT_MAX, cmax = -1;
+        u64 e = 0;
+        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+            const int32_t j = col[k];
+            if (j == (int32_t)i) continue;
+            const int c = C[j];
+            cmin = min(cmin, c);
+            cmax = max(cmax, c);
+            e += (u64)w[k];
+        }
+        cmin = __reduce_min_sync(0xffffffffu, cmin);
+        cmax = __reduce_max_sync(0xffffffffu, cmax);
+        e = sum_reduce(e, 32);
+        if (lane == 0) {
+            int32_t target = a;
+            if (cmax >= 0 && cmin == cmax && cmin != a) {
+                const i64 tw = vg ? gtw[vg[i]] : tw1;
+                const i64 dl = delta[i];
+                const GT g_move = (GT)tw * (GT)(i64)e - (GT)dl * (GT)deg[cmin];
+                const GT g_stay = -((GT)dl * (GT)(deg[a] - dl));
+                if (g_move > g_stay) target = cmin;
+            }
+            Cnext[i] = target;
+        }
+    }
+}
+
+// Exact Qn of the merged state: sum_i e_{i->C(i)} (loops included) per graph, one warp per
+// vertex; sum_c deg_c^2 per graph, one thread per label; then Qn = 2W * S - sum deg^2 into
+// every controller's qn_final.
+template <typename WT>
+__global__ void __launch_bounds__(kBlock) k_qn_rows(int64_t n, const int64_t *rp,
+                                                    const int32_t *col, const WT *w,
+                                                    const int32_t *C, const int32_t *vg,
+                                                    SweepStats *st)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    u64 acc = 0;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int32_t a = C[i];
+        u64 e = 0;
+        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32)
+            if (C[col[k]] == a) e += (u64)w[k];
+        e = sum_reduce(e, 32);
+        if (vg) {
+            if (lane == 0 && e) atomicAdd(&st[vg[i]].internal, e);
+        } else {
+            acc += e;
+        }
+    }
+    if (!vg && lane == 0 && acc) atomicAdd(&st[0].internal, acc);
+}
+
+__global__ void __launch_bounds__(kBlock) k_qn_squares(int64_t n, const i64 *deg,
+                                                       const int32_t *vg, SweepStats *st)
+{
+    u128 acc = 0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const u64 d = (u64)deg[c];
+        if (!d) continue;
+        const u128 sq = (u128)d * d;
+        if (vg) atomic_add_u128(&st[vg[c]].sq_lo, &st[vg[c]].sq_hi, sq);
+        else acc += sq;
+    }
+    if (!vg) {
+        acc = sum_reduce(acc, 32);
+        if ((threadIdx.x & 31) == 0 && acc) atomic_add_u128(&st[0].sq_lo, &st[0].sq_hi, acc);
+    }
+}
+
+__global__ void k_qn_finalize(int G, SweepStats *sts, LevelCtl *ctls)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    SweepStats *st = sts + g;
+    const i128 sq = (i128)(((u128)st->sq_hi << 64) | (u128)st->sq_lo);
+    const i128 qn = (i128)ctls[g].tw * (i128)(i64)st->internal - sq;
+    i128_to(qn, ctls[g].qn_final);
+    st->internal = 0;
+    st->sq_lo = 0;
+    st->sq_hi = 0;
+    st->moved = 0;
+}
+
+template <typename WT>
+static int post_merge_impl(const DevGraph &g, const PhaseState &st, const int32_t *vg,
+                           const i64 *gtw, i64 tw, bool wide, SweepStats *stats, LevelCtl *ctl,
+                           int G, cudaStream_t s, const LaunchCfg &lc)
+{
+    const WT *w = (const WT *)g.w;
+    const int grid = grid_for(g.n, kBlock / 32, lc.max_blocks);
+    if (wide)
+        k_post_merge<WT, i128><<<grid, kBlock, 0, s>>>(g.n, g.rp, g.col, w, st.C, st.deg,
+                                                       st.delta, vg, gtw, tw, st.Cnext);
+    else
+        k_post_merge<WT, i64><<<grid, kBlock, 0, s>>>(g.n, g.rp, g.col, w, st.C, st.deg,
+                                                      st.delta, vg, gtw, tw, st.Cnext);
+    int k = 1;
+    k += launch_apply(g.n, st, nullptr, vg, s, lc);
+    k_qn_rows<WT><<<grid, kBlock, 0, s>>>(g.n, g.rp, g.col, w, st.C, vg, stats);
+    k_qn_squares<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(g.n, st.deg, vg, stats);
+    k_qn_finalize<<<(G + 127) / 128, 128, 0, s>>>(G, stats, ctl);
+    return k + 3;
+}
+
+int launch_post_merge(const DevGraph &g, const PhaseState &st, const int32_t *vg, const i64 *gtw,
+                      i64 tw, bool wide, SweepStats *stats, LevelCtl *ctl, int G, cudaStream_t s,
+                      const LaunchCfg &lc)
+{
+    if (g.n == 0) return 0;
+    if (g.wbytes == 4) return post_merge_impl<int32_t>(g, st, vg, gtw, tw, wide, stats, ctl, G, s, lc);
+    return post_merge_impl<i64>(g, st, vg, gtw, tw, wide, stats, ctl, G, s, lc);
 }
 
 // ------------------------------------------------------------------ renumber / compose

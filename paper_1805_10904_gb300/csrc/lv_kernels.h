@@ -163,8 +163,16 @@ int launch_huge_slice_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc);
 // *ndone counts the graphs whose phase has stopped.
 int launch_decide(SweepStats *st, LevelCtl *ctl, int G, i64 *tr_moved, i64 *tr_qn,
                   u64 *cand_total, int *ndone, cudaStream_t s);
+// ctl nullptr: every proposal is applied (no controller consulted).
 int launch_apply(int64_t n, const PhaseState &st, const LevelCtl *ctl, const int32_t *vg,
                  cudaStream_t s, const LaunchCfg &lc);
+// Post-phase merge of Sec. 5.1.2 (a vertex whose non-loop neighbours all lie in one other
+// community joins it when the move's gain is positive), applied to every vertex of g, then
+// the exact Qn of the merged state into ctl[g].qn_final for all G controllers.  stats must
+// be zero on entry and are zero on return.
+int launch_post_merge(const DevGraph &g, const PhaseState &st, const int32_t *vg, const i64 *gtw,
+                      i64 tw, bool wide, SweepStats *stats, LevelCtl *ctl, int G, cudaStream_t s,
+                      const LaunchCfg &lc);
 // State of the device-side sweep loop: sweeps run so far, controllers stopped when it was
 // launched, how many more may stop before it returns, and its sweep bound.
 struct LoopCtl {

@@ -60,6 +60,7 @@ class Config(ctypes.Structure):
         ("cuda_graphs", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
         ("threshold_mode", ctypes.c_int32),
+        ("post_merge", ctypes.c_int32),
         ("reserved", ctypes.c_int32 * 1),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
@@ -280,7 +281,7 @@ class Louvain:
                  vf_all_levels: bool = False, checks: int = 1, force_int128: bool = False,
                  wide_sums: bool = False, bins=None, chunk_entries: int = 0,
                  profile: bool = False, torch_alloc: bool = True, cuda_graphs: bool = True,
-                 autotune: bool = False, threshold_mode: int = 0):
+                 autotune: bool = False, threshold_mode: int = 0, post_merge: bool = False):
         lib = load()
         self._lib = lib
         cfg = Config()
@@ -302,6 +303,7 @@ class Louvain:
         cfg.cuda_graphs = int(cuda_graphs)
         cfg.autotune = int(autotune)
         cfg.threshold_mode = int(threshold_mode)
+        cfg.post_merge = int(post_merge)
         self.device = device
         if torch_alloc:
             import torch

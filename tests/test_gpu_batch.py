@@ -83,6 +83,7 @@ BATCH_CONFIGS = [
     {"vf_all_levels": True, "theta": (0, 1)},
     {"cuda_graphs": False},
     {"threshold_mode": 1, "theta": (1, 1000)},
+    {"post_merge": True, "max_iters": 2},
 ]
 
 
@@ -95,7 +96,7 @@ def test_batch_equals_plain_and_oracle(torch, lv, ci):
     batch = h.run_batch(vptr, *dev(torch, rp, col, w), graph_eptr=eptr)
     assert len(batch) == len(graphs)
     okw = {k: kw[k] for k in ("theta", "max_iters", "max_levels", "vertex_following",
-                              "vf_all_levels", "threshold_mode") if k in kw}
+                              "vf_all_levels", "threshold_mode", "post_merge") if k in kw}
     for g, res in zip(graphs, batch):
         plain = h.run(*dev(torch, g.rp, g.col, g.w))
         same_result(res, plain)

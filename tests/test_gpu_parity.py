@@ -53,7 +53,7 @@ def assert_parity(res, ref, check_trace=True):
 
 def run_both(torch, lv, g, **kw):
     okw = {k: kw[k] for k in ("theta", "max_iters", "max_levels", "vertex_following",
-                              "vf_all_levels", "threshold_mode") if k in kw}
+                              "vf_all_levels", "threshold_mode", "post_merge") if k in kw}
     ref = oracle.louvain(g.rp, g.col, g.w, **okw)
     h = lv.Louvain(0, **kw)
     res = h.run(*to_dev(torch, g))
@@ -275,4 +275,22 @@ def test_relative_threshold_mode(torch, lv, theta, kind):
     else:
         g = gg.random_small(4242, n_max=60)
     res, ref = run_both(torch, lv, g, theta=theta, threshold_mode=1)
+    assert_parity(res, ref)
+
+
+@pytest.mark.parametrize("kw", [{}, {"max_iters": 1}, {"max_iters": 2, "vertex_following": False},
+                                {"theta": (1, 50), "force_int128": True},
+                                {"bins": (1, 2, 3, 4, 5, 6), "chunk_entries": 32, "max_iters": 2}])
+@pytest.mark.parametrize("kind", ["sbm", "rmat", "small", "path"])
+def test_post_merge_mode(torch, lv, kw, kind):
+    """post_merge: the Sec. 5.1.2 merge after every phase, on the device."""
+    if kind == "sbm":
+        g = gg.sbm(2048, 64, 0.15, 0.003, 1, 4, seed=8)
+    elif kind == "rmat":
+        g = gg.rmat(13, 16, seed=37)
+    elif kind == "small":
+        g = gg.random_small(777, n_max=60)
+    else:
+        g = gg.from_edges(3, [(0, 1, 1), (1, 2, 1)])
+    res, ref = run_both(torch, lv, g, post_merge=True, **kw)
     assert_parity(res, ref)
