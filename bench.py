@@ -64,6 +64,8 @@ def parse_args(argv=None):
     p.add_argument("--serve-only", action="store_true",
                    help="run only the serving workload (its own JSON line)")
     p.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
+    p.add_argument("--no-edges", action="store_true",
+                   help="skip timing the edge-list to CSR conversion")
     p.add_argument("--serve-budget-gb", type=float, default=120.0)
     p.add_argument("--serve-slots", type=int, default=256)
     return p.parse_args(argv)
@@ -474,6 +476,43 @@ def run_serve_workload(args, lv, dev):
     }
 
 
+def run_edges_workload(lv, g, dev, stream, reps=5):
+    """Edge-list input (Sec. 5.1.2 neighbour computation): the workload graph's undirected
+    edges (one per pair, loops once) in a seeded random order and orientation, resident in
+    HBM, converted to the symmetric CSR by louvain_csr_from_edges; checks the result equals
+    the generated CSR and reports input edges/s."""
+    import numpy as np
+    import torch
+    rows = np.repeat(np.arange(g.n, dtype=np.int32), np.diff(g.rp))
+    keep = rows <= g.col
+    rng = np.random.Generator(np.random.PCG64(2205))
+    perm = rng.permutation(int(keep.sum()))
+    u, v, w = rows[keep][perm], g.col[keep][perm], g.w[keep][perm]
+    flip = rng.random(len(u)) < 0.5
+    u, v = np.where(flip, v, u), np.where(flip, u, v)
+    du, dv, dw = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (u, v, w))
+    h = lv.Louvain(dev.index)
+    rp, col, ww = h.csr_from_edges(g.n, du, dv, dw, stream=stream.cuda_stream)
+    same = (np.array_equal(rp.cpu().numpy(), g.rp) and np.array_equal(col.cpu().numpy(), g.col)
+            and np.array_equal(ww.cpu().numpy(), g.w))
+    del rp, col, ww
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = h.csr_from_edges(g.n, du, dv, dw, stream=stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        del out
+    ms = statistics.median(times)
+    return {"edges": int(len(u)), "csr_entries": int(g.nnz), "ms": ms,
+            "edges_per_s": len(u) / (ms / 1000.0), "identical_to_generated_csr": bool(same),
+            "note": "median of %d calls, inputs on the device; each call allocates its "
+                    "scratch and synchronises once" % reps}
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -558,6 +597,7 @@ def run_native(args):
     batch = (run_batch_workload(args, lv, dev, stream, 2, 1) if args.batch_graphs > 0
              else None)
     serve = run_serve_workload(args, lv, dev) if args.serve_requests > 0 else None
+    edges = None if args.no_edges else run_edges_workload(lv, g, dev, stream)
 
     if rank != 0:
         if world > 1:
@@ -603,7 +643,7 @@ def run_native(args):
             for b, a in sorted(bins_acc.items()) if a["launches"]},
         "coarsen_ms_per_step": round(coarsen_ms / args.steps, 4),
         "e2e": e2e,
-        "batch": batch, "serve": serve,
+        "batch": batch, "serve": serve, "edges": edges,
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -228,6 +228,29 @@ int louvain_serve_status(const louvain_handle *h, int64_t status[4]);
  * never polled and end the request loop.  louvain_destroy closes an open loop itself. */
 int louvain_serve_close(louvain_handle *h);
 
+/* ---------------------------------------------------------------- edge-list input */
+/* Symmetric CSR for louvain_run from an undirected edge list in any order (the neighbour
+ * computation of Sec. 5.1.2: source-target pairs plus their reverses, sorted by source and
+ * target, counted per source and prefix-summed into row offsets).  Reading of this
+ * library: a pair (u, v, w) with u != v gives the entries (u, v) and (v, u); a loop (u, u)
+ * gives one entry (u, u); entries with the same (row, column) are merged by adding their
+ * weights; rows come out sorted by column.
+ *   n          vertices (0 <= n <= 2^31 - 1; n = 0 needs m = 0)
+ *   m          edges (0 <= m <= 2^40)
+ *   src, dst   int32[m] endpoints in [0, n); weights int32[m] >= 1 or NULL (all 1);
+ *              ptr_kind LOUVAIN_PTR_HOST (copied inside the call) or LOUVAIN_PTR_DEVICE
+ *   row_ptr    DEVICE int64[n + 1], written
+ *   col_idx, w_out  DEVICE int32, room for 2m entries; the first *nnz are the CSR, the rest
+ *              is scratch of the call
+ *   nnz        HOST int64 out
+ * Work is ordered on `stream` and finished when the call returns.  Scratch is about 48
+ * bytes per edge from the handle's allocator.  Errors: INVALID_ARG, INDEX_RANGE (an
+ * endpoint outside [0, n)), BAD_WEIGHT, TOO_LARGE (a merged weight above 2^31 - 1, or the
+ * size limits), OOM, CUDA. */
+int louvain_csr_from_edges(louvain_handle *h, int64_t n, int64_t m, const int32_t *src,
+                           const int32_t *dst, const int32_t *weights, int ptr_kind, void *stream,
+                           int64_t *row_ptr, int32_t *col_idx, int32_t *w_out, int64_t *nnz);
+
 /* ---------------------------------------------------------------- results */
 /* Number of recorded levels (0 when nothing merged, e.g. no edges). */
 int louvain_result_num_levels(const louvain_result *r);

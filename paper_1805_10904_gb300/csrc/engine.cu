@@ -252,6 +252,10 @@ int map_err_bits(unsigned bits, std::string &msg)
         msg = "the adjacency is not symmetric (A_ij != A_ji)";
         return LOUVAIN_ERR_NOT_SYMMETRIC;
     }
+    if (bits & ERRF_OVERFLOW) {
+        msg = "a merged edge weight exceeds 2^31 - 1";
+        return LOUVAIN_ERR_TOO_LARGE;
+    }
     if (bits & ERRF_HASH_FULL) {
         msg = "internal: a hash table overflowed";
         return LOUVAIN_ERR_INTERNAL;
@@ -2040,6 +2044,107 @@ int louvain_autotune(louvain_handle *h, int64_t n, const int64_t *row_ptr,
         h->err = e.msg;
         cudaStreamSynchronize(R.s);
         cudaGetLastError();
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        h->err = "host allocation failed";
+        return LOUVAIN_ERR_OOM;
+    }
+    return LOUVAIN_OK;
+}
+
+int louvain_csr_from_edges(louvain_handle *h, int64_t n, int64_t m, const int32_t *src,
+                           const int32_t *dst, const int32_t *weights, int ptr_kind, void *stream,
+                           int64_t *row_ptr, int32_t *col_idx, int32_t *w_out, int64_t *nnz)
+{
+    if (!h) return LOUVAIN_ERR_INVALID_ARG;
+    h->err.clear();
+    if (h->server) {
+        h->err = "the handle is serving";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (n < 0 || m < 0 || !row_ptr || !nnz || (m > 0 && (!src || !dst || !col_idx || !w_out)) ||
+        (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE) || (n == 0 && m > 0)) {
+        h->err = "bad n, m, pointers or ptr_kind";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (n > INT32_MAX || m > ((int64_t)1 << 40)) {
+        h->err = "n above 2^31 - 1 or m above 2^40";
+        return LOUVAIN_ERR_TOO_LARGE;
+    }
+    RunCtx R;
+    R.s = (cudaStream_t)stream;
+    R.A.fa = h->cfg.alloc;
+    R.A.ff = h->cfg.free;
+    R.A.ctx = h->cfg.alloc_ctx;
+    R.A.s = R.s;
+    cudaStream_t s = R.s;
+    launch_site() = nullptr;
+    try {
+        CK(cudaSetDevice(h->device));
+        DBuf<int32_t> s_own, d_own, w_own;
+        if (ptr_kind == LOUVAIN_PTR_HOST && m > 0) {
+            s_own.reset(&R.A, m);
+            d_own.reset(&R.A, m);
+            CK(cudaMemcpyAsync(s_own.p, src, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice,
+                               s));
+            CK(cudaMemcpyAsync(d_own.p, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice,
+                               s));
+            src = s_own.p;
+            dst = d_own.p;
+            if (weights) {
+                w_own.reset(&R.A, m);
+                CK(cudaMemcpyAsync(w_own.p, weights, sizeof(int32_t) * (size_t)m,
+                                   cudaMemcpyHostToDevice, s));
+                weights = w_own.p;
+            }
+        }
+        const int64_t len = 2 * m;
+        const int64_t tiles = edges_scratch_tiles(m);
+        EdgeScratch sc;
+        DBuf<u64> k0, k1, wacc;
+        DBuf<int32_t> v0, v1, rowcnt;
+        DBuf<int64_t> pos, hist, offs, scan64, word;
+        k0.reset(&R.A, len);
+        k1.reset(&R.A, len);
+        v0.reset(&R.A, len);
+        v1.reset(&R.A, len);
+        pos.reset(&R.A, len + 1);
+        wacc.reset(&R.A, len);
+        rowcnt.reset(&R.A, n);
+        hist.reset(&R.A, 256 * tiles);
+        offs.reset(&R.A, 256 * tiles + 1);
+        scan64.reset(&R.A, scan_scratch_elems(std::max(std::max(len, 256 * tiles), n) + 1) + 64);
+        word.reset(&R.A, 2);  // [0]: error bits, [1]: nnz
+        sc.keys[0] = k0.p;
+        sc.keys[1] = k1.p;
+        sc.vals[0] = v0.p;
+        sc.vals[1] = v1.p;
+        sc.pos = pos.p;
+        sc.wacc = wacc.p;
+        sc.rowcnt = rowcnt.p;
+        sc.hist = hist.p;
+        sc.offs = offs.p;
+        sc.scan64 = scan64.p;
+        CK(cudaMemsetAsync(word.p, 0, 16, s));
+        launch_edges_to_csr(n, m, src, dst, weights, sc, row_ptr, col_idx, w_out, word.p + 1,
+                            (unsigned *)word.p, s, h->lc);
+        CK(cudaGetLastError());
+        if (launch_site()) throw LvErr{LOUVAIN_ERR_CUDA, launch_site()};
+        int64_t hw[2] = {0, 0};
+        CK(cudaMemcpyAsync(hw, word.p, sizeof(hw), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const unsigned bits = (unsigned)hw[0];
+        if (bits) {
+            std::string msg;
+            const int code = map_err_bits(bits, msg);
+            throw LvErr{code, msg};
+        }
+        *nnz = hw[1];
+    } catch (const LvErr &e) {
+        h->err = e.msg;
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        launch_site() = nullptr;
         return e.code;
     } catch (const std::bad_alloc &) {
         h->err = "host allocation failed";

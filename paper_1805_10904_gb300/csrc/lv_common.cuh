@@ -27,6 +27,7 @@ enum : unsigned {
     ERRF_ASYM = 16u,      // A_ij != A_ji (full checks)
     ERRF_DUP = 32u,       // unsorted or duplicate column in a row (full checks)
     ERRF_INTERNAL = 64u,  // consistency check failed
+    ERRF_OVERFLOW = 128u, // a merged weight does not fit int32
 };
 
 // Per-sweep accumulators, zeroed by the decide kernel after it reads them.

@@ -211,6 +211,27 @@ int launch_compose(int64_t n0, int M, const int64_t *off, int32_t *const *maps,
                    const int32_t *new_id1, const int64_t *base1, const int32_t *new_id2,
                    int32_t *out, cudaStream_t s, const LaunchCfg &lc);
 
+// ---- k_edges.cu: symmetric CSR from an undirected edge list (Sec. 5.1.2 neighbour computation)
+struct EdgeScratch {
+    u64 *keys[2] = {nullptr, nullptr};     // 2m each
+    int32_t *vals[2] = {nullptr, nullptr}; // 2m each
+    int64_t *pos = nullptr;                // 2m + 1
+    u64 *wacc = nullptr;                   // 2m
+    int32_t *rowcnt = nullptr;             // n
+    int64_t *hist = nullptr;               // 256 * edges_scratch_tiles(m)
+    int64_t *offs = nullptr;               // 256 * edges_scratch_tiles(m) + 1
+    int64_t *scan64 = nullptr;             // scan_scratch_elems(max(2m, 256 * tiles, n) + 1)
+};
+int edges_scratch_tiles(int64_t m);
+// Entries of non-loop edges in both directions, loops once, equal (row, column) merged by
+// adding weights, rows sorted by column.  col_out / w_out need room for 2m entries; the row
+// offsets (n + 1) and *nnz_out (device) are written on `s`; bad endpoints, weights or a
+// merged weight above 2^31 - 1 set bits of *err.
+int launch_edges_to_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                        const int32_t *w, const EdgeScratch &sc, int64_t *rp_out,
+                        int32_t *col_out, int32_t *w_out, int64_t *nnz_out, unsigned *err,
+                        cudaStream_t s, const LaunchCfg &lc);
+
 // ---- k_move.cu: one synchronous sweep (Algorithm 1 body) over all bins
 struct SweepTimers {
     cudaEvent_t ev[2 * kNumBins];  // start/stop pair around each bin's kernel

@@ -113,6 +113,7 @@ def load():
     lib.louvain_num_bins.restype = ctypes.c_int
     lib.louvain_result_exec_info.argtypes = [P, P]
     lib.louvain_autotune.argtypes = [P, i64, P, P, P, ctypes.c_int, P, P, P, P]
+    lib.louvain_csr_from_edges.argtypes = [P, i64, i64, P, P, P, ctypes.c_int, P, P, P, P, P]
     lib.louvain_result_bin_stats.argtypes = [P, ctypes.c_int, P, P, P, P, P]
     lib.louvain_result_free.argtypes = [P]
     lib.louvain_result_free.restype = None
@@ -390,6 +391,32 @@ class Louvain:
         if rc != OK:
             raise LouvainError(rc, self.last_error())
         return tuple(int(x) for x in b[:6]), int(b[6]), ms.value, tr.value
+
+    def csr_from_edges(self, n: int, src, dst, weights=None, stream: Optional[int] = None):
+        """louvain_csr_from_edges: (row_ptr, col_idx, weights) as torch CUDA tensors of the
+        symmetric CSR of an undirected edge list (numpy / torch arrays, host or device)."""
+        import torch
+        s_, k1, keep1 = _ptr_of(src)
+        d_, k2, keep2 = _ptr_of(dst)
+        w_, k3, keep3 = _ptr_of(weights)
+        kinds = {k for k in (k1, k2, k3) if k is not None}
+        if len(kinds) != 1:
+            raise ValueError("src, dst and weights must all be on the host or all on the device")
+        m = int(keep1.shape[0])
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        dev = torch.device("cuda", self.device)
+        rp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(max(2 * m, 1), dtype=torch.int32, device=dev)
+        w = torch.empty(max(2 * m, 1), dtype=torch.int32, device=dev)
+        nnz = ctypes.c_int64()
+        rc = self._lib.louvain_csr_from_edges(self._h, n, m, s_, d_, w_, kinds.pop(),
+                                              ctypes.c_void_p(stream), rp.data_ptr(),
+                                              col.data_ptr(), w.data_ptr(),
+                                              ctypes.addressof(nnz))
+        if rc != OK:
+            raise LouvainError(rc, self.last_error())
+        return rp, col[:nnz.value], w[:nnz.value]
 
     def run_batch(self, graph_vptr, row_ptr, col_idx, weights=None, graph_eptr=None,
                   stream: Optional[int] = None) -> List[Result]:
