@@ -25,6 +25,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/louvain.h"
 #include "lv_common.cuh"
 #include "lv_kernels.h"
@@ -33,6 +35,23 @@
 using namespace lv;
 
 namespace {
+
+// NVTX range named after the paper's processes (Sec. 5.1.2: neighbour computation, init,
+// one level, renumbering, induction); phase() closes the current range and opens the next.
+struct ProcRange {
+    bool open = false;
+    explicit ProcRange(const char *name) { phase(name); }
+    void phase(const char *name)
+    {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    ~ProcRange()
+    {
+        if (open) nvtxRangePop();
+    }
+};
 
 struct LvErr {
     int code;
@@ -772,6 +791,7 @@ void Engine::join()
 
 void Engine::step(std::vector<Member *> &retired)
 {
+    ProcRange proc("init");
     const double wall0 = now_ms();
     const int64_t k_start = kernels;
     if (!pending.empty()) join();
@@ -914,6 +934,7 @@ void Engine::step(std::vector<Member *> &retired)
         bc.gctl = d_ctls.p;
     }
 
+    proc.phase("onelevel");
     // sweeps (Algorithm 1); one host read of the controllers' count per sweep
     double t_kernel[kNumBins] = {};
     int64_t launches_kernel[kNumBins] = {};
@@ -1035,6 +1056,7 @@ void Engine::step(std::vector<Member *> &retired)
         mb->visits += (int64_t)it * mb->nnz;
     }
 
+    proc.phase("renumber");
     // renumber (Sec. 5.1.2) -- used labels in increasing order; labels of one graph are
     // contiguous, so the scan also numbers each graph's communities
     kernels += launch_renumber(n, size.p, nullptr, nullptr, new_id.p, scratch32.p, s);
@@ -1121,6 +1143,7 @@ void Engine::step(std::vector<Member *> &retired)
         CK(cudaStreamSynchronize(s));  // host vectors above are uploaded before they go
     }
 
+    proc.phase("induce");
     // ---------------- induce the next graph of the kept graphs (Sec. 5.1.2)
     double t_coarsen = 0.0;
     std::vector<int64_t> gptr_next(M + 1, 0), gnnz_next(M + 1, 0);
@@ -2079,6 +2102,7 @@ int louvain_csr_from_edges(louvain_handle *h, int64_t n, int64_t m, const int32_
     R.A.s = R.s;
     cudaStream_t s = R.s;
     launch_site() = nullptr;
+    ProcRange proc("neighbour");
     try {
         CK(cudaSetDevice(h->device));
         DBuf<int32_t> s_own, d_own, w_own;

@@ -282,7 +282,8 @@ class Louvain:
                  vf_all_levels: bool = False, checks: int = 1, force_int128: bool = False,
                  wide_sums: bool = False, bins=None, chunk_entries: int = 0,
                  profile: bool = False, torch_alloc: bool = True, cuda_graphs: bool = True,
-                 autotune: bool = False, threshold_mode: int = 0, post_merge: bool = False):
+                 autotune: bool = False, threshold_mode: int = 0, post_merge: bool = False,
+                 alloc_hook=None):
         lib = load()
         self._lib = lib
         cfg = Config()
@@ -306,10 +307,15 @@ class Louvain:
         cfg.threshold_mode = int(threshold_mode)
         cfg.post_merge = int(post_merge)
         self.device = device
+        # alloc_hook(bytes) -> bool may refuse an allocation (failure-injection tests)
+        self.alloc_hook = alloc_hook
         if torch_alloc:
             import torch
 
             def _alloc(size, ctx, stream):
+                hook = self.alloc_hook
+                if hook is not None and not hook(int(size)):
+                    return None
                 try:
                     return torch.cuda.caching_allocator_alloc(int(size), device,
                                                               int(stream or 0))
