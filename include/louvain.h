@@ -103,6 +103,9 @@ typedef struct {
                                /* all lie in one other community joins it if that move's    */
                                /* Eq. 4 gain is positive (Sec. 5.1.2); the level then       */
                                /* records the merged state and its modularity; 0 (default) */
+    int32_t keep_coarse;       /* 1: a one-graph run keeps the graph induced after every    */
+                               /* recorded level (louvain_result_coarse_graph), so a run   */
+                               /* can be resumed from it (louvain_resume)                   */
     int32_t reserved[1];       /* must be zero                                           */
     /* device memory: both NULL means stream-ordered cudaMallocAsync/cudaFreeAsync */
     louvain_alloc_fn alloc;
@@ -227,6 +230,29 @@ int louvain_serve_status(const louvain_handle *h, int64_t status[4]);
 /* Stop accepting graphs, finish every graph already submitted, free the results that were
  * never polled and end the request loop.  louvain_destroy closes an open loop itself. */
 int louvain_serve_close(louvain_handle *h);
+
+/* ---------------------------------------------------------------- checkpoint / resume */
+/* With keep_coarse = 1 a one-graph run keeps, for every recorded level l that the run went
+ * on from, the graph induced after it (the input of level l + 1; Sec. 5.1.2).  Its sizes:
+ * louvain_result_coarse_graph (INVALID_ARG when level l has none); its arrays, copied into
+ * caller buffers on the host or the device: louvain_result_coarse_copy (int64 row offsets
+ * [n + 1], int32 columns [nnz], weights of weight_bytes 4 or 8 each [nnz]; NULL skips one). */
+int louvain_result_coarse_graph(const louvain_result *r, int level, int64_t *n, int64_t *nnz,
+                                int32_t *weight_bytes);
+int louvain_result_coarse_copy(const louvain_result *r, int level, int64_t *row_ptr,
+                               int32_t *col_idx, void *weights, int ptr_kind);
+
+/* Continue a run from a saved level: the graph induced after level start_level - 1 (as
+ * louvain_result_coarse_copy gives it; weights int32 or int64 by weight_bytes) and that
+ * level's Qn (qn_prev, {high, low}) for the outer test of Algorithm 2.  The run computes
+ * levels start_level, start_level + 1, ... exactly as the uninterrupted run did (vertex
+ * following only with vf_all_levels, max_levels counted from level 0); the result's level
+ * k is level start_level + k, its labels number the given graph's vertices, and its trace
+ * carries the true level numbers.  Errors as louvain_run, plus INVALID_ARG for start_level
+ * < 1 or >= max_levels. */
+int louvain_resume(louvain_handle *h, int32_t start_level, const int64_t qn_prev[2], int64_t n,
+                   const int64_t *row_ptr, const int32_t *col_idx, const void *weights,
+                   int32_t weight_bytes, int ptr_kind, void *stream, louvain_result **out);
 
 /* ---------------------------------------------------------------- edge-list input */
 /* Symmetric CSR for louvain_run from an undirected edge list in any order (the neighbour

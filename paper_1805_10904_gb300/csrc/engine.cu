@@ -209,14 +209,14 @@ struct louvain_handle {
 // Label arrays of one engine step (every graph that recorded a level in it has its labels
 // there); freed with the last result that refers to it.
 struct LabelStore {
-    std::vector<int32_t *> arrays;
+    std::vector<void *> arrays;
     louvain_free_fn ff = nullptr;
     void *ctx = nullptr;
     int device = 0;
     ~LabelStore()
     {
         cudaSetDevice(device);
-        for (int32_t *p : arrays) {
+        for (void *p : arrays) {
             if (ff) ff(p, ctx, nullptr);
             else cudaFreeAsync(p, nullptr);
         }
@@ -227,6 +227,15 @@ struct louvain_result {
     int64_t n0 = 0;
     int batch_index = -1;  // graph index in its batch, -1 for a plain run
     std::vector<std::shared_ptr<LabelStore>> stores;  // label arrays of its levels
+    // graph induced after recorded level l (keep_coarse): input of level l + 1
+    struct Coarse {
+        int64_t n = 0, nnz = 0;
+        int32_t wbytes = 4;
+        const int64_t *rp = nullptr;
+        const int32_t *col = nullptr;
+        const void *w = nullptr;
+    };
+    std::vector<Coarse> coarse;  // indexed by recorded level; n = -1 when none was induced
     int64_t acc_sweeps = 0, acc_cand = 0, acc_kernels = 0;
     // graph sweeps, host-loop sweeps, steps, captures, autotuning trials, tuned-bins cache hit
     int64_t exec_info[6] = {0, 0, 0, 0, 0, 0};
@@ -313,7 +322,8 @@ struct Source {
     int64_t n = 0, nnz = 0;
     const int64_t *rp = nullptr;
     const int32_t *col = nullptr;
-    const int32_t *w = nullptr;
+    const int32_t *w = nullptr;  // int32, or int64 when wbytes = 8 (a resumed coarse graph)
+    int wbytes = 4;
     std::vector<int64_t> vptr, eptr;  // K + 1 each
     std::vector<Member *> members;    // K
 };
@@ -685,6 +695,9 @@ void Engine::join()
     if (n > INT32_MAX) throw LvErr{LOUVAIN_ERR_TOO_LARGE, "stacked vertex count above 2^31 - 1"};
     std::vector<Member *> fresh;
     std::vector<int64_t> vbase;
+    for (const Source &src : pending)
+        if (src.wbytes != 4 && !(n_cont == 0 && pending.size() == 1))
+            throw LvErr{LOUVAIN_ERR_INVALID_ARG, "64-bit weights enter only alone"};
     if (n_cont == 0 && pending.size() == 1) {
         const Source &src = pending[0];
         g_rp.release();
@@ -695,7 +708,7 @@ void Engine::join()
         G.rp = src.rp;
         G.col = src.col;
         G.w = src.w;
-        G.wbytes = 4;
+        G.wbytes = src.wbytes;
     } else {
         const int wb = n_cont > 0 ? G.wbytes : 4;
         DBuf<int64_t> j_rp;
@@ -740,8 +753,7 @@ void Engine::join()
             Member *m = src.members[k];
             if (m->n0 == 0) continue;
             m->map = (int32_t *)A.get(sizeof(int32_t) * (size_t)m->n0);
-            m->level = 0;
-            fresh.push_back(m);
+            fresh.push_back(m);  // at its own level (0, or the level a resumed run starts at)
             vbase.push_back(v_base + src.vptr[k]);
             mem.push_back(m);
         }
@@ -1096,6 +1108,7 @@ void Engine::step(std::vector<Member *> &retired)
         r.nnz = mb->nnz;
         r.hit_cap = hc.hit_cap;
         mb->res->levels.push_back(r);
+        mb->res->coarse.push_back(louvain_result::Coarse{-1, 0, 4, nullptr, nullptr, nullptr});
         const bool stop = (mb->level >= 1 && host_below_threshold(r.qn, mb->qn_prev, mb->tw,
                                                                   cfg.theta_num, cfg.theta_den)) ||
                           mb->level + 1 >= cfg.max_levels;
@@ -1225,6 +1238,30 @@ void Engine::step(std::vector<Member *> &retired)
             gptr_next[1] = k;
             gnnz_next[1] = nnz_next;
         }
+        if (cfg.keep_coarse && !batch) {  // checkpoint: the next level's input graph
+            louvain_result *res0 = mem[0]->res;
+            auto store = std::make_shared<LabelStore>();
+            store->ff = cfg.free;
+            store->ctx = cfg.alloc_ctx;
+            store->device = h->device;
+            void *crp = A.get(sizeof(int64_t) * (size_t)(k + 1));
+            store->arrays.push_back(crp);
+            void *ccol = A.get(sizeof(int32_t) * (size_t)nnz_next);
+            store->arrays.push_back(ccol);
+            void *cw = A.get((size_t)wb_next * (size_t)nnz_next);
+            store->arrays.push_back(cw);
+            CK(cudaMemcpyAsync(crp, rp_next.p, sizeof(int64_t) * (size_t)(k + 1),
+                               cudaMemcpyDeviceToDevice, s));
+            if (nnz_next) {
+                CK(cudaMemcpyAsync(ccol, col_next.p, sizeof(int32_t) * (size_t)nnz_next,
+                                   cudaMemcpyDeviceToDevice, s));
+                CK(cudaMemcpyAsync(cw, w_next.p, (size_t)wb_next * (size_t)nnz_next,
+                                   cudaMemcpyDeviceToDevice, s));
+            }
+            res0->coarse.back() = louvain_result::Coarse{k, nnz_next, wb_next, (const int64_t *)crp,
+                                                        (const int32_t *)ccol, cw};
+            res0->stores.push_back(store);
+        }
         g_rp.swap(rp_next);
         g_col.swap(col_next);
         g_w.swap(w_next);
@@ -1312,10 +1349,13 @@ void finish_result(Member *m)
 
 // Runs louvain_run (gvptr null: one graph, one-graph kernels) or louvain_run_batch on the
 // engine: the input enters as one source and the engine steps until every graph has left.
+// A resumed run (start_level > 0) enters at that level with the previous level's Qn for
+// the outer test and may carry int64 weights (wbytes = 8); w_in then points to int64.
 void run_engine(louvain_handle *h, const louvain_config &cfg, cudaStream_t s, DevAlloc &A,
                 int64_t n0, const int64_t *rp_in,
                 const int32_t *col_in, const int32_t *w_in, int kind, int NG,
-                const int64_t *gvptr, const int64_t *geptr, std::vector<louvain_result *> &out)
+                const int64_t *gvptr, const int64_t *geptr, std::vector<louvain_result *> &out,
+                int start_level = 0, i128 qn_prev_level = 0, int wbytes = 4)
 {
     const double t0 = now_ms();
     const bool batch = gvptr != nullptr;
@@ -1345,9 +1385,9 @@ void run_engine(louvain_handle *h, const louvain_config &cfg, cudaStream_t s, De
                                cudaMemcpyHostToDevice, s));
         d_col = col_own.p;
         if (w_in) {
-            w_own.reset(&A, (size_t)nnz);
+            w_own.reset(&A, (size_t)nnz * (wbytes / 4));
             if (nnz)
-                CK(cudaMemcpyAsync(w_own.p, w_in, sizeof(int32_t) * (size_t)nnz,
+                CK(cudaMemcpyAsync(w_own.p, w_in, (size_t)wbytes * (size_t)nnz,
                                    cudaMemcpyHostToDevice, s));
             d_w = w_own.p;
         }
@@ -1359,11 +1399,13 @@ void run_engine(louvain_handle *h, const louvain_config &cfg, cudaStream_t s, De
         if (nnz > 0 && !col_in) throw LvErr{LOUVAIN_ERR_INVALID_ARG, "col_idx is NULL"};
     }
     if (!d_w) {
+        wbytes = 4;
         w_own.reset(&A, (size_t)nnz);
         E.kernels += launch_fill_ones(w_own.p, nnz, s, lc);
         d_w = w_own.p;
     }
     Source src;
+    src.wbytes = wbytes;
     src.n = n0;
     src.nnz = nnz;
     src.rp = d_rp;
@@ -1376,6 +1418,8 @@ void run_engine(louvain_handle *h, const louvain_config &cfg, cudaStream_t s, De
         members[g].reset(new Member());
         members[g]->res = out[g];
         members[g]->t0 = t0;
+        members[g]->level = start_level;
+        members[g]->qn_prev = qn_prev_level;
         src.members.push_back(members[g].get());
         out[g]->n0 = src.vptr[g + 1] - src.vptr[g];
         out[g]->batch_index = batch ? g : -1;
@@ -1890,6 +1934,10 @@ static int check_config(louvain_config &c, std::string &msg)
               "mid2 <= cta1 <= cta2 <= cta3 <= 12288";
         return LOUVAIN_ERR_INVALID_ARG;
     }
+    if (c.keep_coarse != 0 && c.keep_coarse != 1) {
+        msg = "keep_coarse must be 0 or 1";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
     if (c.post_merge != 0 && c.post_merge != 1) {
         msg = "post_merge must be 0 or 1";
         return LOUVAIN_ERR_INVALID_ARG;
@@ -2071,6 +2119,98 @@ int louvain_autotune(louvain_handle *h, int64_t n, const int64_t *row_ptr,
     } catch (const std::bad_alloc &) {
         h->err = "host allocation failed";
         return LOUVAIN_ERR_OOM;
+    }
+    return LOUVAIN_OK;
+}
+
+int louvain_resume(louvain_handle *h, int32_t start_level, const int64_t qn_prev[2], int64_t n,
+                   const int64_t *row_ptr, const int32_t *col_idx, const void *weights,
+                   int32_t weight_bytes, int ptr_kind, void *stream, louvain_result **out)
+{
+    if (!h) return LOUVAIN_ERR_INVALID_ARG;
+    h->err.clear();
+    if (!out) return LOUVAIN_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (h->server) {
+        h->err = "the handle is serving";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (start_level < 1 || start_level >= h->cfg.max_levels || !qn_prev || n < 0 || !row_ptr ||
+        (weight_bytes != 4 && weight_bytes != 8) ||
+        (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE)) {
+        h->err = "bad start_level, qn_prev, n, row_ptr, weight_bytes or ptr_kind";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (n > INT32_MAX) {
+        h->err = "n above 2^31 - 1";
+        return LOUVAIN_ERR_TOO_LARGE;
+    }
+    louvain_result *res = new (std::nothrow) louvain_result();
+    if (!res) return LOUVAIN_ERR_OOM;
+    res->device = h->device;
+    res->ff = h->cfg.free;
+    res->ctx = h->cfg.alloc_ctx;
+    RunCtx R;
+    R.s = (cudaStream_t)stream;
+    R.A.fa = h->cfg.alloc;
+    R.A.ff = h->cfg.free;
+    R.A.ctx = h->cfg.alloc_ctx;
+    R.A.s = R.s;
+    int rc = LOUVAIN_OK;
+    launch_site() = nullptr;
+    try {
+        CK(cudaSetDevice(h->device));
+        std::vector<louvain_result *> outs{res};
+        run_engine(h, h->cfg, R.s, R.A, n, row_ptr, col_idx, (const int32_t *)weights, ptr_kind,
+                   1, nullptr, nullptr, outs, start_level,
+                   limbs_to_i128((const i64 *)qn_prev), weight_bytes);
+    } catch (const LvErr &e) {
+        rc = e.code;
+        h->err = e.msg;
+    } catch (const std::bad_alloc &) {
+        rc = LOUVAIN_ERR_OOM;
+        h->err = "host allocation failed";
+    }
+    if (rc != LOUVAIN_OK) {
+        cudaStreamSynchronize(R.s);
+        cudaGetLastError();
+        louvain_result_free(res);
+        return rc;
+    }
+    *out = res;
+    return LOUVAIN_OK;
+}
+
+int louvain_result_coarse_graph(const louvain_result *r, int level, int64_t *n, int64_t *nnz,
+                                int32_t *weight_bytes)
+{
+    if (!r || level < 0 || level >= (int)r->coarse.size() || r->coarse[level].n < 0)
+        return LOUVAIN_ERR_INVALID_ARG;
+    const louvain_result::Coarse &c = r->coarse[level];
+    if (n) *n = c.n;
+    if (nnz) *nnz = c.nnz;
+    if (weight_bytes) *weight_bytes = c.wbytes;
+    return LOUVAIN_OK;
+}
+
+int louvain_result_coarse_copy(const louvain_result *r, int level, int64_t *row_ptr,
+                               int32_t *col_idx, void *weights, int ptr_kind)
+{
+    if (!r || level < 0 || level >= (int)r->coarse.size() || r->coarse[level].n < 0 ||
+        (ptr_kind != LOUVAIN_PTR_HOST && ptr_kind != LOUVAIN_PTR_DEVICE))
+        return LOUVAIN_ERR_INVALID_ARG;
+    const louvain_result::Coarse &c = r->coarse[level];
+    const cudaMemcpyKind kind =
+        ptr_kind == LOUVAIN_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (cudaSetDevice(r->device) != cudaSuccess ||
+        (row_ptr && cudaMemcpy(row_ptr, c.rp, sizeof(int64_t) * (size_t)(c.n + 1), kind) !=
+                        cudaSuccess) ||
+        (col_idx && c.nnz &&
+         cudaMemcpy(col_idx, c.col, sizeof(int32_t) * (size_t)c.nnz, kind) != cudaSuccess) ||
+        (weights && c.nnz &&
+         cudaMemcpy(weights, c.w, (size_t)c.wbytes * (size_t)c.nnz, kind) != cudaSuccess)) {
+        cudaGetLastError();
+        return LOUVAIN_ERR_CUDA;
     }
     return LOUVAIN_OK;
 }

@@ -61,6 +61,7 @@ class Config(ctypes.Structure):
         ("autotune", ctypes.c_int32),
         ("threshold_mode", ctypes.c_int32),
         ("post_merge", ctypes.c_int32),
+        ("keep_coarse", ctypes.c_int32),
         ("reserved", ctypes.c_int32 * 1),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
@@ -114,6 +115,10 @@ def load():
     lib.louvain_result_exec_info.argtypes = [P, P]
     lib.louvain_autotune.argtypes = [P, i64, P, P, P, ctypes.c_int, P, P, P, P]
     lib.louvain_csr_from_edges.argtypes = [P, i64, i64, P, P, P, ctypes.c_int, P, P, P, P, P]
+    lib.louvain_result_coarse_graph.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.louvain_result_coarse_copy.argtypes = [P, ctypes.c_int, P, P, P, ctypes.c_int]
+    lib.louvain_resume.argtypes = [P, i32, P, i64, P, P, P, i32, ctypes.c_int, P,
+                                   ctypes.POINTER(P)]
     lib.louvain_result_bin_stats.argtypes = [P, ctypes.c_int, P, P, P, P, P]
     lib.louvain_result_free.argtypes = [P]
     lib.louvain_result_free.restype = None
@@ -255,6 +260,23 @@ class Result:
                         "rows": v[2].value, "entries": v[3].value})
         return out
 
+    def coarse_graph(self, level: int):
+        """(row_ptr, col_idx, weights) numpy arrays of the graph induced after recorded level
+        `level` (keep_coarse runs), or None when the run stopped there."""
+        n, nnz, wb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        rc = self._lib.louvain_result_coarse_graph(self._p, level, ctypes.addressof(n),
+                                                   ctypes.addressof(nnz), ctypes.addressof(wb))
+        if rc != OK:
+            return None
+        rp = np.empty(n.value + 1, np.int64)
+        col = np.empty(max(nnz.value, 1), np.int32)
+        w = np.empty(max(nnz.value, 1), np.int32 if wb.value == 4 else np.int64)
+        rc = self._lib.louvain_result_coarse_copy(self._p, level, rp.ctypes.data, col.ctypes.data,
+                                                  w.ctypes.data, PTR_HOST)
+        if rc != OK:
+            raise LouvainError(rc, "louvain_result_coarse_copy")
+        return rp, col[:nnz.value], w[:nnz.value]
+
     def exec_info(self):
         """(sweeps in CUDA graphs, host-loop sweeps, level steps, graph captures, autotuning
         trials of this call, 1 if the tuned bins came from the cache)."""
@@ -283,7 +305,7 @@ class Louvain:
                  wide_sums: bool = False, bins=None, chunk_entries: int = 0,
                  profile: bool = False, torch_alloc: bool = True, cuda_graphs: bool = True,
                  autotune: bool = False, threshold_mode: int = 0, post_merge: bool = False,
-                 alloc_hook=None):
+                 alloc_hook=None, keep_coarse: bool = False):
         lib = load()
         self._lib = lib
         cfg = Config()
@@ -306,6 +328,7 @@ class Louvain:
         cfg.autotune = int(autotune)
         cfg.threshold_mode = int(threshold_mode)
         cfg.post_merge = int(post_merge)
+        cfg.keep_coarse = int(keep_coarse)
         self.device = device
         # alloc_hook(bytes) -> bool may refuse an allocation (failure-injection tests)
         self.alloc_hook = alloc_hook
@@ -397,6 +420,29 @@ class Louvain:
         if rc != OK:
             raise LouvainError(rc, self.last_error())
         return tuple(int(x) for x in b[:6]), int(b[6]), ms.value, tr.value
+
+    def resume(self, start_level: int, qn_prev: int, row_ptr, col_idx, weights,
+               stream: Optional[int] = None) -> Result:
+        """louvain_resume from a saved level (weights int32 or int64 host arrays)."""
+        rp = np.ascontiguousarray(np.asarray(row_ptr, np.int64))
+        col = np.ascontiguousarray(np.asarray(col_idx, np.int32))
+        w = np.ascontiguousarray(weights)
+        wb = 8 if w.dtype == np.int64 else 4
+        w = w.astype(np.int64 if wb == 8 else np.int32, copy=False)
+        q = np.array([qn_prev >> 64, qn_prev & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64).view(np.int64)
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(self.device).cuda_stream
+            except Exception:
+                stream = 0
+        out = ctypes.c_void_p()
+        rc = self._lib.louvain_resume(self._h, int(start_level), q.ctypes.data, len(rp) - 1,
+                                      rp.ctypes.data, col.ctypes.data, w.ctypes.data, wb,
+                                      PTR_HOST, ctypes.c_void_p(stream), ctypes.byref(out))
+        if rc != OK:
+            raise LouvainError(rc, self.last_error())
+        return Result(self._lib, out, self)
 
     def csr_from_edges(self, n: int, src, dst, weights=None, stream: Optional[int] = None):
         """louvain_csr_from_edges: (row_ptr, col_idx, weights) as torch CUDA tensors of the
