@@ -542,7 +542,14 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_compact(int64_t k, int64_t n
         const int64_t o1 = min(nnz_next, o0 + kCompactSlice);
         int64_t a = row_of(rp_next, 0, k, o0);
         for (int64_t o = o0 + lane; o < o1; o += 32) {
-            if (rp_next[a + 1] <= o) a = row_of(rp_next, a + 1, k, o);
+            if (rp_next[a + 1] <= o) {  // gallop from the next row, then bisect
+                int64_t lo = a + 1, step = 1;
+                while (lo + step < k && rp_next[lo + step] <= o) {
+                    lo += step;
+                    step <<= 1;
+                }
+                a = row_of(rp_next, lo, lo + step < k ? lo + step : k, o);
+            }
             const int64_t src = mpre[moff[a]] + (o - rp_next[a]);
             col_next[o] = tmp_col[src];
             w_next[o] = (WO)tmp_w[src];
