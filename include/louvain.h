@@ -106,6 +106,8 @@ typedef struct {
     int32_t keep_coarse;       /* 1: a one-graph run keeps the graph induced after every    */
                                /* recorded level (louvain_result_coarse_graph), so a run   */
                                /* can be resumed from it (louvain_resume)                   */
+    int32_t sweep_streams;     /* streams the degree bins of one sweep run on side by side */
+                               /* (0..4; default 4; 0 or 1: one after another)             */
     int32_t reserved[1];       /* must be zero                                           */
     /* device memory: both NULL means stream-ordered cudaMallocAsync/cudaFreeAsync */
     louvain_alloc_fn alloc;
@@ -149,8 +151,8 @@ int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int3
 
 /* Choose the degree-bin thresholds and chunk length for a graph by measurement (this
  * library's addition; the thresholds only decide which kernel handles a row, never a
- * result).  Each trial is a whole run with a candidate set, timed as the sum of the local-
- * move and induction kernels' CUDA-event times (best of two); a coordinate search over
+ * result).  Each trial is a whole run with a candidate set in the handle's configuration,
+ * timed with CUDA events around the run (best of two); a coordinate search over
  * {bin_small, bin_mid1, bin_mid2, bin_cta1, bin_cta2, bin_cta3, chunk_entries} keeps a
  * change when it is at least 2% faster.  The choice is cached on the handle per (n, nnz)
  * and used by louvain_run when autotune = 1.  Arguments as in louvain_run; bins_out gets

@@ -378,6 +378,7 @@ struct Engine {
     SweepTimers tm;
     cudaEvent_t coarsen_ev[2] = {nullptr, nullptr};
     cudaStream_t cap = nullptr;  // stream the sweep graphs are captured on (never runs work)
+    SweepStreams ss;             // streams the bins of a sweep run on side by side
 
     Engine(louvain_handle *h_, cudaStream_t s_, DevAlloc &A_, bool batch_,
            const louvain_config &cfg_)
@@ -388,6 +389,12 @@ struct Engine {
         CK(cudaMemsetAsync(d_sc, 0, sizeof(Scalars), s));
         G.n = 0;
         G.nnz = 0;
+        for (int q = 0; q < cfg.sweep_streams && q < 4; q++) {
+            CK(cudaStreamCreateWithFlags(&ss.aux[q], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&ss.join[q], cudaEventDisableTiming));
+            ss.k = q + 1;
+        }
+        if (ss.k) CK(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
         if (cfg.profile) {
             for (auto &e : tm.ev) CK(cudaEventCreate(&e));
             CK(cudaEventCreate(&coarsen_ev[0]));
@@ -404,6 +411,11 @@ struct Engine {
         }
         for (Member *m : mem) release_map(m);
         if (cap) cudaStreamDestroy(cap);
+        for (int q = 0; q < ss.k; q++) {
+            cudaStreamDestroy(ss.aux[q]);
+            cudaEventDestroy(ss.join[q]);
+        }
+        if (ss.fork) cudaEventDestroy(ss.fork);
     }
     Engine(const Engine &) = delete;
     Engine &operator=(const Engine &) = delete;
@@ -940,6 +952,7 @@ void Engine::step(std::vector<Member *> &retired)
     ensure(tr_moved, (size_t)tcap * M);
     ensure(tr_qn, 2 * (size_t)tcap * M);
     BatchCtx bc;
+    bc.ss = ss.k ? &ss : nullptr;
     if (batch) {
         bc.vg = vg.p;
         bc.gtw = (const i64 *)d_tw.p;
@@ -1737,7 +1750,7 @@ struct Server {
 //
 // Degree-bin thresholds and the chunk length only decide which kernel handles a row, never
 // a result, so they can be chosen by measurement: each trial is a whole run with a
-// candidate set (best of two, sum of the move and induction kernels' event times), and a
+// candidate set in the handle's own mode (best of two, CUDA-event time of the run), and a
 // coordinate search over the thresholds keeps a change only when it is at least 2%
 // faster.  The choice is cached on the handle per (vertex count, entry count).
 
@@ -1817,10 +1830,20 @@ void tuned_bins(louvain_handle *h, cudaStream_t s, DevAlloc &A, int64_t n, const
         kind = LOUVAIN_PTR_DEVICE;
     }
     louvain_config base = h->cfg;
-    base.profile = 1;
+    base.profile = 0;  // trials run as the tuned runs will (graphs, concurrent bins)
     base.autotune = 0;
-    base.cuda_graphs = 0;
     int64_t trials = 0;
+    cudaEvent_t ev[2];
+    CK(cudaEventCreate(&ev[0]));
+    CK(cudaEventCreate(&ev[1]));
+    struct EvFree {
+        cudaEvent_t *e;
+        ~EvFree()
+        {
+            cudaEventDestroy(e[0]);
+            cudaEventDestroy(e[1]);
+        }
+    } evf{ev};
     auto trial = [&](const int32_t b[7]) {
         louvain_config t = base;
         set_bins(t, b);
@@ -1831,8 +1854,13 @@ void tuned_bins(louvain_handle *h, cudaStream_t s, DevAlloc &A, int64_t n, const
             r->ff = h->cfg.free;
             r->ctx = h->cfg.alloc_ctx;
             std::vector<louvain_result *> outs{r.get()};
+            CK(cudaEventRecord(ev[0], s));
             run_engine(h, t, s, A, n, rp, col, w, kind, 1, nullptr, nullptr, outs);
-            best = std::min(best, r->times[0] + r->times[1]);
+            CK(cudaEventRecord(ev[1], s));
+            CK(cudaEventSynchronize(ev[1]));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+            best = std::min(best, (double)ms);
             trials++;
         }
         return best;
@@ -1900,6 +1928,7 @@ int louvain_config_init(louvain_config *cfg)
     cfg->profile = 0;
     cfg->cuda_graphs = 1;
     cfg->autotune = 0;
+    cfg->sweep_streams = 4;
     return LOUVAIN_OK;
 }
 
@@ -1932,6 +1961,10 @@ static int check_config(louvain_config &c, std::string &msg)
         c.bin_cta2 < c.bin_cta1 || c.bin_cta3 < c.bin_cta2 || c.bin_cta3 > 12288) {
         msg = "bins need 0 <= small <= 8 <= ..., small <= mid1 <= 32, mid1 <= mid2 <= 128, "
               "mid2 <= cta1 <= cta2 <= cta3 <= 12288";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (c.sweep_streams < 0 || c.sweep_streams > 4) {
+        msg = "sweep_streams must be in [0, 4]";
         return LOUVAIN_ERR_INVALID_ARG;
     }
     if (c.keep_coarse != 0 && c.keep_coarse != 1) {

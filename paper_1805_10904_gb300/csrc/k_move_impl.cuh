@@ -901,43 +901,51 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
                    bc.gctl};
     const bool timed = tm && tm->on;
     int launched = 0;
+    // the bins read the same snapshot and write disjoint rows: with a stream set they run
+    // concurrently (fork from s, join back into s), so one bin's last wave overlaps the next
+    const SweepStreams *ss = bc.ss;
+    if (ss) {
+        cudaEventRecord(ss->fork, s);
+        for (int q = 0; q < ss->k; q++) cudaStreamWaitEvent(ss->aux[q], ss->fork, 0);
+    }
     for (int bin = 0; bin < kNumBins; bin++) {
-        if (timed) cudaEventRecord(tm->ev[2 * bin], s);
+        const cudaStream_t bs = ss ? ss->aux[bin % ss->k] : s;
+        if (timed) cudaEventRecord(tm->ev[2 * bin], bs);
         const BinSpec sp = kBinSpec[bin];
         const int nr = b.nlist[bin];
         const int32_t *rows = b.rows(bin);
         if (sp.kind == BIN_THREAD) {
             if (g.n > 0) {  // dense over every vertex: also sums deg_c^2 over all labels
-                k_move_small<WT, GT, BT><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+                k_move_small<WT, GT, BT><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, bs>>>(
                     A, (int)b.upper[0]);
                 note_launch("k_move_small");
                 launched++;
             }
         } else if (nr > 0 && sp.kind == BIN_GROUP8) {
             k_move_group<8, 6, WT, GT, VT, BT><<<grid_for(nr, kBlock / 8, lc.max_blocks), kBlock, 0,
-                                             s>>>(A, rows, nr, bin);
+                                             bs>>>(A, rows, nr, bin);
             note_launch("k_move_group<8>");
             launched++;
         } else if (nr > 0 && sp.kind == BIN_WARP) {
             k_move_group<32, 8, WT, GT, VT, BT><<<grid_for(nr, kBlock / 32, lc.max_blocks), kBlock,
-                                              0, s>>>(A, rows, nr, bin);
+                                              0, bs>>>(A, rows, nr, bin);
             note_launch("k_move_group<32>");
             launched++;
         } else if (nr > 0 && sp.kind == BIN_CTA) {
             const int l2 = cta_log2cap(b, bin);
             const size_t smem = table_bytes<VT>(l2, true);
             if (sp.block == 128) {
-                const int grid = launch_cta_kernel(k_move_cta<128, WT, GT, VT, BT>, 128, smem, nr, s,
+                const int grid = launch_cta_kernel(k_move_cta<128, WT, GT, VT, BT>, 128, smem, nr, bs,
                                                    lc, "k_move_cta<128>");
-                k_move_cta<128, WT, GT, VT, BT><<<grid, 128, smem, s>>>(A, rows, nr, l2, bin);
+                k_move_cta<128, WT, GT, VT, BT><<<grid, 128, smem, bs>>>(A, rows, nr, l2, bin);
             } else if (sp.block == 256) {
-                const int grid = launch_cta_kernel(k_move_cta<256, WT, GT, VT, BT>, 256, smem, nr, s,
+                const int grid = launch_cta_kernel(k_move_cta<256, WT, GT, VT, BT>, 256, smem, nr, bs,
                                                    lc, "k_move_cta<256>");
-                k_move_cta<256, WT, GT, VT, BT><<<grid, 256, smem, s>>>(A, rows, nr, l2, bin);
+                k_move_cta<256, WT, GT, VT, BT><<<grid, 256, smem, bs>>>(A, rows, nr, l2, bin);
             } else {
                 const int grid = launch_cta_kernel(k_move_cta<1024, WT, GT, VT, BT>, 1024, smem, nr,
-                                                   s, lc, "k_move_cta<1024>");
-                k_move_cta<1024, WT, GT, VT, BT><<<grid, 1024, smem, s>>>(A, rows, nr, l2, bin);
+                                                   bs, lc, "k_move_cta<1024>");
+                k_move_cta<1024, WT, GT, VT, BT><<<grid, 1024, smem, bs>>>(A, rows, nr, l2, bin);
             }
             note_launch("k_move_cta");
             launched++;
@@ -946,19 +954,19 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
             const size_t smem = table_bytes<VT>(l2);
             switch (sp.cluster) {
             case 2:
-                launched += launch_cluster_kernel<2>(k_move_cluster<2, WT, GT, VT, BT>, smem, nr, s,
+                launched += launch_cluster_kernel<2>(k_move_cluster<2, WT, GT, VT, BT>, smem, nr, bs,
                                                      "k_move_cluster<2>", A, rows, nr, l2, bin);
                 break;
             case 4:
-                launched += launch_cluster_kernel<4>(k_move_cluster<4, WT, GT, VT, BT>, smem, nr, s,
+                launched += launch_cluster_kernel<4>(k_move_cluster<4, WT, GT, VT, BT>, smem, nr, bs,
                                                      "k_move_cluster<4>", A, rows, nr, l2, bin);
                 break;
             case 8:
-                launched += launch_cluster_kernel<8>(k_move_cluster<8, WT, GT, VT, BT>, smem, nr, s,
+                launched += launch_cluster_kernel<8>(k_move_cluster<8, WT, GT, VT, BT>, smem, nr, bs,
                                                      "k_move_cluster<8>", A, rows, nr, l2, bin);
                 break;
             default:
-                launched += launch_cluster_kernel<16>(k_move_cluster<16, WT, GT, VT, BT>, smem, nr, s,
+                launched += launch_cluster_kernel<16>(k_move_cluster<16, WT, GT, VT, BT>, smem, nr, bs,
                                                       "k_move_cluster<16>", A, rows, nr, l2, bin);
                 break;
             }
@@ -970,19 +978,25 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
             const int l2 = 31 - __builtin_clz(2 * b.chunk);
             const size_t smem = table_bytes<VT>(l2, true);
             const int grid = launch_cta_kernel(k_move_huge<WT, GT, VT, BT>, kHugeBlock, smem,
-                                               b.nchunks, s, lc, "k_move_huge");
-            k_move_huge<WT, GT, VT, BT><<<grid, kHugeBlock, smem, s>>>(A, B);
+                                               b.nchunks, bs, lc, "k_move_huge");
+            k_move_huge<WT, GT, VT, BT><<<grid, kHugeBlock, smem, bs>>>(A, B);
             note_launch("k_move_huge");
             launched++;
             if (b.nslices > 0) {  // some rows span several chunks
                 const int64_t cap = (int64_t)lc.num_sms * 4;
                 const int dgrid = (int)(b.nslices < cap ? b.nslices : cap);
-                k_move_huge_decide<WT, GT, VT, BT><<<dgrid, kHugeBlock, 0, s>>>(A, B);
+                k_move_huge_decide<WT, GT, VT, BT><<<dgrid, kHugeBlock, 0, bs>>>(A, B);
                 note_launch("k_move_huge_decide");
                 launched++;
             }
         }
-        if (timed) cudaEventRecord(tm->ev[2 * bin + 1], s);
+        if (timed) cudaEventRecord(tm->ev[2 * bin + 1], bs);
+    }
+    if (ss) {
+        for (int q = 0; q < ss->k; q++) {
+            cudaEventRecord(ss->join[q], ss->aux[q]);
+            cudaStreamWaitEvent(s, ss->join[q], 0);
+        }
     }
     return launched;
 }

@@ -107,10 +107,20 @@ inline int cta_log2cap(const Bins &b, int bin)
 
 // Graph context of a batch of graphs stored as one disjoint union (nullptr pointers for a
 // single graph): the graph of every vertex, every graph's 2W and phase controller.
+// Streams on which the bins of one sweep run side by side (forked from and joined back
+// into the sweep's stream with the events).
+struct SweepStreams {
+    int k = 0;
+    cudaStream_t aux[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
 struct BatchCtx {
     const int32_t *vg = nullptr;
     const i64 *gtw = nullptr;
     const LevelCtl *gctl = nullptr;
+    const SweepStreams *ss = nullptr;  // concurrent bins (nullptr: all on the sweep's stream)
 };
 
 struct LaunchCfg {

@@ -62,6 +62,7 @@ class Config(ctypes.Structure):
         ("threshold_mode", ctypes.c_int32),
         ("post_merge", ctypes.c_int32),
         ("keep_coarse", ctypes.c_int32),
+        ("sweep_streams", ctypes.c_int32),
         ("reserved", ctypes.c_int32 * 1),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
@@ -305,7 +306,7 @@ class Louvain:
                  wide_sums: bool = False, bins=None, chunk_entries: int = 0,
                  profile: bool = False, torch_alloc: bool = True, cuda_graphs: bool = True,
                  autotune: bool = False, threshold_mode: int = 0, post_merge: bool = False,
-                 alloc_hook=None, keep_coarse: bool = False):
+                 alloc_hook=None, keep_coarse: bool = False, sweep_streams: int = 4):
         lib = load()
         self._lib = lib
         cfg = Config()
@@ -329,6 +330,7 @@ class Louvain:
         cfg.threshold_mode = int(threshold_mode)
         cfg.post_merge = int(post_merge)
         cfg.keep_coarse = int(keep_coarse)
+        cfg.sweep_streams = int(sweep_streams)
         self.device = device
         # alloc_hook(bytes) -> bool may refuse an allocation (failure-injection tests)
         self.alloc_hook = alloc_hook

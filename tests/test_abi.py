@@ -49,6 +49,8 @@ def test_config_defaults(lib):
     assert cfg.struct_size == ctypes.sizeof(Config)
     assert (cfg.theta_num, cfg.theta_den) == (1, 1_000_000)
     assert cfg.max_iters == 1000 and cfg.vertex_following == 1 and cfg.checks == 1
+    assert cfg.cuda_graphs == 1 and cfg.sweep_streams == 4 and cfg.autotune == 0
+    assert cfg.threshold_mode == 0 and cfg.post_merge == 0 and cfg.keep_coarse == 0
     assert lib.louvain_config_init(None) == 1
 
 
@@ -66,6 +68,11 @@ def test_invalid_config_rejected_before_any_device_call(lib):
     bad = Config.from_buffer_copy(cfg)
     bad.bin_small = 9
     assert lib.louvain_create(ctypes.byref(bad), 0, ctypes.byref(h)) == 1
+    for field, value in (("sweep_streams", 5), ("threshold_mode", 2), ("post_merge", 3),
+                         ("keep_coarse", -1)):
+        bad = Config.from_buffer_copy(cfg)
+        setattr(bad, field, value)
+        assert lib.louvain_create(ctypes.byref(bad), 0, ctypes.byref(h)) == 1
     assert not h.value
 
 

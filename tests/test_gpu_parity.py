@@ -72,6 +72,8 @@ BIN_CONFIGS = [
     {"bins": (0, 0, 0, 0, 0, 2)},                                # clusters of 2..16 CTAs
     {"bins": (1, 2, 3, 4, 5, 6), "wide_sums": True, "force_int128": True, "chunk_entries": 64},
     {"cuda_graphs": False},                                      # one host round trip per sweep
+    {"sweep_streams": 0},                                        # bins one after another
+    {"sweep_streams": 2, "cuda_graphs": False, "bins": (1, 2, 3, 4, 5, 6), "chunk_entries": 32},
     {"cuda_graphs": False, "bins": (0, 0, 0, 0, 0, 2), "chunk_entries": 32},
 ]
 
