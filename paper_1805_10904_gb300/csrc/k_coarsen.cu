@@ -137,7 +137,7 @@ struct CoarsenArgs {
     const int64_t *rp;
     const int32_t *col;
     const WT *w;
-    const int32_t *C;
+    const int32_t *C;       // renumbered label of every vertex, new_id[C(v)]
     const int32_t *new_id;
     const int32_t *moff;
     const int32_t *members;
@@ -168,7 +168,7 @@ __device__ __forceinline__ void flat_entry(const CoarsenArgs<WT> &A, int32_t &p,
     if (A.mpre[p + 1] <= t) p = find_member(A.mpre, p + 1, pe, t);
     const int32_t u = A.members[p];
     const int64_t kk = A.rp[u] + (t - A.mpre[p]);
-    key = A.new_id[A.C[A.col[kk]]];
+    key = A.C[A.col[kk]];  // A.C holds the renumbered labels new_id[C[v]]
     wv = (i64)A.w[kk];
 }
 
@@ -657,14 +657,27 @@ static int cluster_launch(K kernel, size_t smem, int nrows, cudaStream_t s, cons
     return 1;
 }
 
+// cn[v] = new_id[C[v]]: the next-level vertex of every vertex, so that the aggregation
+// gathers one label per entry instead of two in a row
+__global__ void k_renumbered_labels(int64_t n, const int32_t *C, const int32_t *new_id,
+                                    int32_t *cn)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        cn[v] = new_id[C[v]];
+}
+
 template <typename WT, typename VT>
 static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *new_id, int64_t k,
                        CoarsenBufs &cb, Bins &bins, unsigned *err, cudaStream_t s,
                        const LaunchCfg &lc)
 {
-    CoarsenArgs<WT> A{g.rp,       g.col,       (const WT *)g.w, st.C,       new_id, cb.moff,
+    // the phase is over: C_next is free to hold the renumbered labels
+    k_renumbered_labels<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(g.n, st.C, new_id,
+                                                                              st.Cnext);
+    CoarsenArgs<WT> A{g.rp,       g.col,       (const WT *)g.w, st.Cnext,   new_id, cb.moff,
                       cb.members, cb.mpre,     cb.ccnt,         cb.tmp_col, cb.tmp_w, err};
-    int launched = 0;
+    int launched = 1;
     for (int bin = 2; bin < kNumBins; bin++) {
         const BinSpec sp = kBinSpec[bin];
         const int nr = bins.nlist[bin];
