@@ -363,7 +363,7 @@ struct Engine {
     DBuf<i64> hp_ea;
     DBuf<u128> hp_gain;
     DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_tmp_col;
-    DBuf<int64_t> c_mpre;
+    DBuf<int64_t> c_mpre, c_mrow;
     DBuf<u64> c_tmp_w;
     // per-slot arrays
     DBuf<int64_t> d_gptr, d_base1, d_gnnz, d_off, d_vbase;
@@ -1179,6 +1179,7 @@ void Engine::step(std::vector<Member *> &retired)
         ensure(c_cursor, n);
         ensure(c_members, n);
         ensure(c_mpre, (size_t)n + 1);
+        ensure(c_mrow, n);
         ensure(c_ccnt, n);
         ensure(c_tmp_col, (size_t)G.nnz);
         ensure(c_tmp_w, (size_t)G.nnz);
@@ -1188,6 +1189,7 @@ void Engine::step(std::vector<Member *> &retired)
         cb.cursor = c_cursor.p;
         cb.members = c_members.p;
         cb.mpre = c_mpre.p;
+        cb.mrow = c_mrow.p;
         cb.ccnt = c_ccnt.p;
         cb.tmp_col = c_tmp_col.p;
         cb.tmp_w = c_tmp_w.p;

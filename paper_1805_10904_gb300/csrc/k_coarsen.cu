@@ -45,9 +45,11 @@ __global__ void k_coarsen_prep(int64_t n, const int32_t *size, const i64 *deg,
     }
 }
 
+// members[p] = u and, for the aggregation, the first entry of u's row mrow[p] = rp[u]
 __global__ void k_coarsen_scatter(int64_t n, const int32_t *C, const int32_t *new_id,
                                   const int32_t *vg, const int32_t *keep, const int32_t *moff,
-                                  int32_t *cursor, int32_t *members)
+                                  const int64_t *rp, int32_t *cursor, int32_t *members,
+                                  int64_t *mrow)
 {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
          u += (int64_t)gridDim.x * blockDim.x) {
@@ -55,6 +57,7 @@ __global__ void k_coarsen_scatter(int64_t n, const int32_t *C, const int32_t *ne
         const int32_t a = new_id[C[u]];
         const int32_t p = moff[a] + atomicAdd(&cursor[a], 1);
         members[p] = (int32_t)u;
+        mrow[p] = rp[u];
     }
 }
 
@@ -140,7 +143,7 @@ struct CoarsenArgs {
     const int32_t *C;       // renumbered label of every vertex, new_id[C(v)]
     const int32_t *new_id;
     const int32_t *moff;
-    const int32_t *members;
+    const int64_t *mrow;  // first entry of every member's row
     const int64_t *mpre;
     int32_t *ccnt;
     int32_t *tmp_col;
@@ -166,8 +169,7 @@ __device__ __forceinline__ void flat_entry(const CoarsenArgs<WT> &A, int32_t &p,
                                            int64_t t, int32_t &key, i64 &wv)
 {
     if (A.mpre[p + 1] <= t) p = find_member(A.mpre, p + 1, pe, t);
-    const int32_t u = A.members[p];
-    const int64_t kk = A.rp[u] + (t - A.mpre[p]);
+    const int64_t kk = A.mrow[p] + (t - A.mpre[p]);
     key = A.C[A.col[kk]];  // A.C holds the renumbered labels new_id[C[v]]
     wv = (i64)A.w[kk];
 }
@@ -586,7 +588,7 @@ int launch_coarsen_stage1(const DevGraph &g, const PhaseState &st, const int32_t
     launched += exclusive_scan<int32_t>(ArrayIn<int32_t>{cb.csize}, k, cb.moff, cb.scratch32, s);
     cudaMemsetAsync(cb.cursor, 0, sizeof(int32_t) * (size_t)k, s);
     k_coarsen_scatter<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        n, st.C, new_id, vg, keep, cb.moff, cb.cursor, cb.members);
+        n, st.C, new_id, vg, keep, cb.moff, g.rp, cb.cursor, cb.members, cb.mrow);
     launched++;
     launched += exclusive_scan<int64_t>(MemberDegIn{cb.members, g.rp}, n_keep, cb.mpre,
                                         cb.scratch64, s);
@@ -675,8 +677,8 @@ static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *n
     // the phase is over: C_next is free to hold the renumbered labels
     k_renumbered_labels<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(g.n, st.C, new_id,
                                                                               st.Cnext);
-    CoarsenArgs<WT> A{g.rp,       g.col,       (const WT *)g.w, st.Cnext,   new_id, cb.moff,
-                      cb.members, cb.mpre,     cb.ccnt,         cb.tmp_col, cb.tmp_w, err};
+    CoarsenArgs<WT> A{g.rp,    g.col,   (const WT *)g.w, st.Cnext,   new_id,   cb.moff,
+                      cb.mrow, cb.mpre, cb.ccnt,         cb.tmp_col, cb.tmp_w, err};
     int launched = 1;
     for (int bin = 2; bin < kNumBins; bin++) {
         const BinSpec sp = kBinSpec[bin];

@@ -258,6 +258,7 @@ struct CoarsenBufs {
     int32_t *moff = nullptr;      // k + 1
     int32_t *cursor = nullptr;    // k
     int32_t *members = nullptr;   // n
+    int64_t *mrow = nullptr;      // n: row start of every member
     int64_t *mpre = nullptr;      // n + 1
     int32_t *ccnt = nullptr;      // k (distinct neighbours of each community)
     int32_t *tmp_col = nullptr;   // nnz
