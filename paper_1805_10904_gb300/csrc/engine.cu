@@ -1232,7 +1232,7 @@ void Engine::step(std::vector<Member *> &retired)
         col_next.reset(&A, (size_t)nnz_next);
         w_next.reset(&A, (size_t)nnz_next * wb_next);
         kernels += launch_coarsen_compact(k, nnz_next, cb, rp_next.p, col_next.p, w_next.p,
-                                          wb_next, s, lc);
+                                          wb_next, narrow, s, lc);
         if (tm.on) {
             CK(cudaEventRecord(coarsen_ev[1], s));
             CK(cudaEventSynchronize(coarsen_ev[1]));

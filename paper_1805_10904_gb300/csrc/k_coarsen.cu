@@ -147,7 +147,7 @@ struct CoarsenArgs {
     const int64_t *mpre;
     int32_t *ccnt;
     int32_t *tmp_col;
-    u64 *tmp_w;
+    void *tmp_w;  // VT per entry (the aggregation's sum width)
     unsigned *err;
 };
 
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
         for (int q = lane; q < m; q += 32) {
             const int s = list[q];
             A.tmp_col[tb + q] = keys[s];
-            A.tmp_w[tb + q] = (u64)vals[s];
+            ((VT *)A.tmp_w)[tb + q] = vals[s];
             keys[s] = -1;
             vals[s] = 0;
         }
@@ -266,7 +266,7 @@ __device__ __forceinline__ int cta_excl_scan(int v, int *total)
 // CTA-strided walk, clearing them; returns this CTA's count (valid in every thread).
 template <int BLOCK, typename VT>
 __device__ __forceinline__ int drain_table(int *keys, VT *vals, int cap, int32_t *out_col,
-                                           u64 *out_w, int64_t base, int rank_off)
+                                           VT *out_w, int64_t base, int rank_off)
 {
     int mine = 0;
     for (int s = threadIdx.x; s < cap; s += BLOCK) mine += keys[s] >= 0;
@@ -276,7 +276,7 @@ __device__ __forceinline__ int drain_table(int *keys, VT *vals, int cap, int32_t
         const int key = keys[s];
         if (key < 0) continue;
         out_col[base + off] = key;
-        out_w[base + off] = (u64)vals[s];
+        out_w[base + off] = vals[s];
         off++;
         keys[s] = -1;
         vals[s] = 0;
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const 
         for (int q = threadIdx.x; q < m; q += BLOCK) {
             const int s = list[q];
             A.tmp_col[tb + q] = keys[s];
-            A.tmp_w[tb + q] = (u64)vals[s];
+            ((VT *)A.tmp_w)[tb + q] = vals[s];
             keys[s] = -1;
             vals[s] = 0;
         }
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(1024) k_coarsen_cluster(CoarsenArgs<WT> A, con
             s_tot = tot;
         }
         __syncthreads();
-        drain_table<BLOCK, VT>(keys, vals, cap, A.tmp_col, A.tmp_w, tb, s_off);
+        drain_table<BLOCK, VT>(keys, vals, cap, A.tmp_col, (VT *)A.tmp_w, tb, s_off);
         if (threadIdx.x == 0 && rank == 0) A.ccnt[a] = s_tot;
         cluster.sync();  // counts read and tables cleared before the next community
     }
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A,
             for (int r = threadIdx.x; r < m; r += kCHugeBlock) {
                 const int s = list[r];
                 A.tmp_col[tb + r] = keys[s];
-                A.tmp_w[tb + r] = (u64)vals[s];
+                ((VT *)A.tmp_w)[tb + r] = vals[s];
                 keys[s] = -1;
                 vals[s] = 0;
             }
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A,
 template <typename VT>
 __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge_extract(
     CBigArgs B, const int32_t *moff, const int64_t *mpre, int32_t *ccnt, int32_t *tmp_col,
-    u64 *tmp_w)
+    void *tmp_w)
 {
     for (int c = blockIdx.x; c < B.nchunks; c += gridDim.x) {
         const int b = B.chunk_b[c];
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge_extract(
         for (int64_t p = pb + threadIdx.x; p < pe; p += kCHugeBlock) {
             const int s = B.glist[off + p];
             tmp_col[tb + p] = B.gkeys[off + s];
-            tmp_w[tb + p] = (u64)((const VT *)B.gvals)[off + s];
+            ((VT *)tmp_w)[tb + p] = ((const VT *)B.gvals)[off + s];
         }
         if (q == 0 && threadIdx.x == 0) ccnt[a] = gm;
     }
@@ -528,13 +528,13 @@ __device__ __forceinline__ int64_t row_of(const int64_t *rp, int64_t lo, int64_t
     return lo;
 }
 
-template <typename WO>
+template <typename WO, typename VT>
 __global__ void __launch_bounds__(kBlock) k_coarsen_compact(int64_t k, int64_t nnz_next,
                                                             const int32_t *moff,
                                                             const int64_t *mpre,
                                                             const int64_t *rp_next,
                                                             const int32_t *tmp_col,
-                                                            const u64 *tmp_w, int32_t *col_next,
+                                                            const VT *tmp_w, int32_t *col_next,
                                                             WO *w_next)
 {
     const int lane = threadIdx.x & 31;
@@ -777,21 +777,31 @@ int launch_coarsen_rowptr(int64_t k, CoarsenBufs &cb, int64_t *rp_next, cudaStre
     return exclusive_scan<int64_t>(I32AsI64In{cb.ccnt}, k, rp_next, cb.scratch64, s);
 }
 
+template <typename VT>
+static void compact_impl(int grid, int64_t k, int64_t nnz_next, const CoarsenBufs &cb,
+                         const int64_t *rp_next, int32_t *col_next, void *w_next,
+                         int wbytes_next, cudaStream_t s)
+{
+    const VT *tw = (const VT *)cb.tmp_w;
+    if (wbytes_next == 4)
+        k_coarsen_compact<int32_t, VT><<<grid, kBlock, 0, s>>>(
+            k, nnz_next, cb.moff, cb.mpre, rp_next, cb.tmp_col, tw, col_next, (int32_t *)w_next);
+    else
+        k_coarsen_compact<i64, VT><<<grid, kBlock, 0, s>>>(
+            k, nnz_next, cb.moff, cb.mpre, rp_next, cb.tmp_col, tw, col_next, (i64 *)w_next);
+}
+
 int launch_coarsen_compact(int64_t k, int64_t nnz_next, const CoarsenBufs &cb,
                            const int64_t *rp_next, int32_t *col_next, void *w_next,
-                           int wbytes_next, cudaStream_t s, const LaunchCfg &lc)
+                           int wbytes_next, bool narrow, cudaStream_t s, const LaunchCfg &lc)
 {
     if (k == 0 || nnz_next == 0) return 0;
     const int grid = grid_for((nnz_next + kCompactSlice - 1) / kCompactSlice, kBlock / 32,
                               lc.max_blocks);
-    if (wbytes_next == 4)
-        k_coarsen_compact<int32_t><<<grid, kBlock, 0, s>>>(k, nnz_next, cb.moff, cb.mpre,
-                                                           rp_next, cb.tmp_col, cb.tmp_w,
-                                                           col_next, (int32_t *)w_next);
+    if (narrow)
+        compact_impl<unsigned int>(grid, k, nnz_next, cb, rp_next, col_next, w_next, wbytes_next, s);
     else
-        k_coarsen_compact<i64><<<grid, kBlock, 0, s>>>(k, nnz_next, cb.moff, cb.mpre, rp_next,
-                                                       cb.tmp_col, cb.tmp_w, col_next,
-                                                       (i64 *)w_next);
+        compact_impl<u64>(grid, k, nnz_next, cb, rp_next, col_next, w_next, wbytes_next, s);
     return 1;
 }
 

@@ -262,7 +262,7 @@ struct CoarsenBufs {
     int64_t *mpre = nullptr;      // n + 1
     int32_t *ccnt = nullptr;      // k (distinct neighbours of each community)
     int32_t *tmp_col = nullptr;   // nnz
-    u64 *tmp_w = nullptr;         // nnz
+    void *tmp_w = nullptr;        // nnz sums of the aggregation's width (32 bits when narrow)
     int32_t *counts = nullptr;    // device counters of the community bins
     int64_t *scratch64 = nullptr;
     int32_t *scratch32 = nullptr;
@@ -290,6 +290,6 @@ int launch_coarsen_stage2(const DevGraph &g, const PhaseState &st, const int32_t
 int launch_coarsen_rowptr(int64_t k, CoarsenBufs &cb, int64_t *rp_next, cudaStream_t s);
 int launch_coarsen_compact(int64_t k, int64_t nnz_next, const CoarsenBufs &cb,
                            const int64_t *rp_next, int32_t *col_next, void *w_next,
-                           int wbytes_next, cudaStream_t s, const LaunchCfg &lc);
+                           int wbytes_next, bool narrow, cudaStream_t s, const LaunchCfg &lc);
 
 }  // namespace lv
