@@ -37,9 +37,16 @@ def workload(scale: int) -> str:
             "autotuned degree bins")
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129 * 1024 * 1024
+# kernel of every bin slot (louvain_result_bin_stats): the table kernels, then the
+# first-sweep kernels of the same bins (bins 5-9 share the 1024-thread CTA kernel there)
 KERNEL_NAMES = ["k_move_small", "k_move_group<8>", "k_move_group<32>", "k_move_cta<128>",
                 "k_move_cta<256>", "k_move_cta<1024>", "k_move_cluster<2>", "k_move_cluster<4>",
-                "k_move_cluster<8>", "k_move_cluster<16>", "k_move_huge"]
+                "k_move_cluster<8>", "k_move_cluster<16>", "k_move_huge",
+                "k_move_small<first>", "k_move_group_first<8>", "k_move_group_first<32>",
+                "k_move_cta_first<128>", "k_move_cta_first<256>", "k_move_cta_first<1024>",
+                "k_move_cta_first<1024> (bin 6)", "k_move_cta_first<1024> (bin 7)",
+                "k_move_cta_first<1024> (bin 8)", "k_move_cta_first<1024> (bin 9)",
+                "k_move_huge (first sweep)"]
 
 
 def parse_args(argv=None):

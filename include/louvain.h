@@ -143,9 +143,11 @@ const char *louvain_last_error(const louvain_handle *h);
  *   ptr_kind LOUVAIN_PTR_HOST or LOUVAIN_PTR_DEVICE for all three arrays
  *   stream   stream the work is ordered on
  * On success *out receives the result: one entry per recorded level, a level being
- * recorded when it merged at least two communities.  Errors: INVALID_ARG, INDEX_RANGE,
- * BAD_WEIGHT, NOT_SYMMETRIC / DUPLICATE_EDGE (checks = 2), TOO_LARGE, OOM, CUDA,
- * INTERNAL. */
+ * recorded when it merged at least two communities.  A graph that is not symmetric is
+ * detected only with checks = 2; with checks = 1 its result is unspecified (every access
+ * still stays in bounds).  A column repeated in a row is merged as one neighbour.
+ * Errors: INVALID_ARG, INDEX_RANGE, BAD_WEIGHT, NOT_SYMMETRIC / DUPLICATE_EDGE
+ * (checks = 2), TOO_LARGE, OOM, CUDA, INTERNAL. */
 int louvain_run(louvain_handle *h, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                 const int32_t *weights, int ptr_kind, void *stream, louvain_result **out);
 
@@ -331,9 +333,9 @@ int louvain_result_trace(const louvain_result *r, int64_t *len, int32_t *level, 
  *   counters[4] kernels launched by the run
  * times_ms[0] local-move kernels (device time), [1] graph induction from its first to its
  * last kernel, [2] reserved, [3] wall time of louvain_run; [4] the dominant local-move kernel alone,
- * [5] the thread-per-vertex kernel, [6] the lane-group kernels, [7] the CTA and chunk
- * kernels; counters[5] launches of the dominant kernel, counters[6] its algorithmic bytes,
- * counters[7] which degree bin it serves (0 thread, 1 8-lane, 2 warp, 3-5 CTA, 6 chunks).
+ * [5] the thread-per-vertex kernel, [6] the lane-group kernels, [7] the CTA, cluster and
+ * chunk kernels; counters[5] launches of the dominant kernel, counters[6] its algorithmic
+ * bytes, counters[7] the bin slot it serves (louvain_result_bin_stats numbering).
  * Arrays of 8; unused slots are zero.  Device times are filled only when the config had
  * profile = 1. */
 int louvain_result_counters(const louvain_result *r, int64_t counters[8], double times_ms[8]);
@@ -341,22 +343,28 @@ int louvain_result_counters(const louvain_result *r, int64_t counters[8], double
 /* Number of degree bins of the local-move sweep (see louvain_config's bin thresholds). */
 int louvain_num_bins(void);
 
-/* Statistics of degree bin `bin` summed over every sweep of the run: device time of its
+/* Statistics of degree bin `bin` summed over the sweeps of the run: device time of its
  * kernel (profile = 1 only, else 0), kernel launches, algorithmic bytes (formula of
- * louvain_result_counters), rows handled and stored entries of those rows.  Any out pointer
- * may be NULL. */
+ * louvain_result_counters), rows handled and stored entries of those rows.  Slots
+ * 0 .. louvain_num_bins() - 1 cover every sweep but the first of each phase; slot
+ * louvain_num_bins() + b covers bin b in the first sweep of each phase, which (when every
+ * row of the phase's graph lists each column at most once: always after the first level,
+ * and at the first level when every input row has strictly increasing columns) scores row
+ * entries directly instead of aggregating them in tables, its candidates other than the
+ * vertex's own community being distinct then.  Any out pointer may be NULL. */
 int louvain_result_bin_stats(const louvain_result *r, int bin, double *time_ms,
                              int64_t *launches, int64_t *alg_bytes, int64_t *rows,
                              int64_t *entries);
 
-/* Free a result and its host and device memory; NULL is ignored. */
 /* How the result's level steps ran: info[0] sweeps run inside CUDA graphs (device-side
- * loop, cuda_graphs = 1), [1] sweeps run with one host round trip each, [2] engine level
+ * loop, cuda_graphs = 1), [1] sweeps run with one host round trip each (with cuda_graphs = 1
+ * only the table-free first sweeps, see louvain_result_bin_stats), [2] engine level
  * steps, [3] sweep graphs captured, [4] autotuning trial runs made by this call, [5] 1 when
  * the bins came from the handle's autotuning cache.  For a batch or served graph the
  * numbers cover the steps it took part in. */
 int louvain_result_exec_info(const louvain_result *r, int64_t info[6]);
 
+/* Free a result and its host and device memory; NULL is ignored. */
 void louvain_result_free(louvain_result *r);
 
 /* ---------------------------------------------------------------- without allocation */

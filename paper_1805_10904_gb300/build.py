@@ -12,8 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libgb300louvain.so")
-SOURCES = ["k_move.cu", "k_move_batch.cu", "k_coarsen.cu", "k_level.cu", "engine.cu",
-           "noalloc.cu", "k_edges.cu"]
+SOURCES = ["k_move.cu", "k_move_batch.cu", "k_move_first.cu", "k_coarsen.cu", "k_level.cu",
+           "engine.cu", "noalloc.cu", "k_edges.cu"]
 HEADERS = ["lv_common.cuh", "lv_scan.cuh", "lv_kernels.h", "k_move_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",

@@ -146,6 +146,8 @@ struct Scalars {
     int32_t ccounts[16];
     u64 cand_total[16];
     LoopCtl loop;
+    unsigned unsorted;  // one graph: a row without strictly increasing columns was seen
+    int32_t pad_;
     int32_t tail[8];
 };
 
@@ -247,11 +249,12 @@ struct louvain_result {
     std::vector<TraceRec> trace;
     int64_t counters[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double times[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    double bin_time[kNumBins] = {};
-    int64_t bin_launches[kNumBins] = {};
-    double bin_bytes[kNumBins] = {};
-    int64_t bin_rows[kNumBins] = {};
-    int64_t bin_entries[kNumBins] = {};
+    // per degree bin; slots kNumBins + b: bin b in the first sweep of each phase
+    double bin_time[2 * kNumBins] = {};
+    int64_t bin_launches[2 * kNumBins] = {};
+    double bin_bytes[2 * kNumBins] = {};
+    int64_t bin_rows[2 * kNumBins] = {};
+    int64_t bin_entries[2 * kNumBins] = {};
     louvain_free_fn ff = nullptr;
     void *ctx = nullptr;
 };
@@ -314,6 +317,9 @@ struct Member {
     int64_t visits = 0;
     double t0 = 0.0;         // when it was handed to the engine (host ms)
     void *tag = nullptr;     // owner of the member (a served request)
+    // its rows list every column at most once: known for an induced graph, checked (strictly
+    // increasing columns) for an input graph when it joins
+    bool rows_checked = false, distinct_rows = false;
 };
 
 // Graphs waiting to enter: one CSR holding K graphs (block-diagonal, global column ids,
@@ -369,6 +375,7 @@ struct Engine {
     DBuf<int64_t> d_gptr, d_base1, d_gnnz, d_off, d_vbase;
     DBuf<int32_t> d_rec, d_keep, d_vf;
     DBuf<u64> d_tw;
+    DBuf<unsigned> d_unsorted;
     DBuf<SweepStats> d_stats;
     DBuf<LevelCtl> d_ctls;
     DBuf<int32_t *> d_maps;
@@ -565,7 +572,7 @@ struct SweepGraph {
             reset();
             return fail("begin capture", e);
         }
-        int k = launch_sweep(G, st, bins, TW, wide, narrow, st_dev, &E.d_sc->err, s, E.lc,
+        int k = launch_sweep(G, st, bins, TW, wide, narrow, false, st_dev, &E.d_sc->err, s, E.lc,
                              nullptr, bc);
         k += launch_decide(st_dev, ctl_dev, M, E.tr_moved.p, E.tr_qn.p, &E.d_sc->cand_total[0],
                            &E.d_sc->ndone, s);
@@ -851,18 +858,34 @@ void Engine::step(std::vector<Member *> &retired)
     if (need_row_sums) {
         bins0 = make_bins(G, make_proto(true));
         have_bins0 = true;
-        if (batch) CK(cudaMemsetAsync(d_tw.p, 0, sizeof(u64) * M, s));
-        else CK(cudaMemsetAsync(&d_sc->tw, 0, sizeof(u64), s));
+        if (batch) {
+            ensure(d_unsorted, M);
+            CK(cudaMemsetAsync(d_tw.p, 0, sizeof(u64) * M, s));
+            CK(cudaMemsetAsync(d_unsorted.p, 0, sizeof(unsigned) * M, s));
+        } else {
+            CK(cudaMemsetAsync(&d_sc->tw, 0, sizeof(u64), s));
+            CK(cudaMemsetAsync(&d_sc->unsorted, 0, sizeof(unsigned), s));
+        }
         kernels += launch_row_sums(G, bins0, vgp, batch ? d_gptr.p : nullptr, delta.p,
-                                   batch ? d_tw.p : &d_sc->tw, &d_sc->err, s, lc);
+                                   batch ? d_tw.p : &d_sc->tw,
+                                   batch ? d_unsorted.p : &d_sc->unsorted, &d_sc->err, s, lc);
         if (cfg.checks >= 2) kernels += launch_check_symmetry(G, &d_sc->err, s, lc);
         sync_scalars();
         std::vector<u64> tws(M);
+        std::vector<unsigned> uns(M);
         if (batch) {
             CK(cudaMemcpyAsync(tws.data(), d_tw.p, sizeof(u64) * M, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(uns.data(), d_unsorted.p, sizeof(unsigned) * M,
+                               cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
         } else {
             tws[0] = h->pinned->tw;
+            uns[0] = h->pinned->unsorted;
+        }
+        for (int m = 0; m < M; m++) {  // graphs that joined: their rows as given
+            if (mem[m]->rows_checked) continue;
+            mem[m]->rows_checked = true;
+            mem[m]->distinct_rows = uns[m] == 0;
         }
         for (int m = 0; m < M; m++) {
             if (tws[m] > ((u64)1 << 62))
@@ -961,24 +984,32 @@ void Engine::step(std::vector<Member *> &retired)
 
     proc.phase("onelevel");
     // sweeps (Algorithm 1); one host read of the controllers' count per sweep
-    double t_kernel[kNumBins] = {};
-    int64_t launches_kernel[kNumBins] = {};
-    double bytes_kernel[kNumBins] = {};
-    int64_t rows_kernel[kNumBins] = {}, entries_kernel[kNumBins] = {};
+    // per bin; slots kNumBins + b: bin b in the first sweep of the phase
+    double t_kernel[2 * kNumBins] = {};
+    int64_t launches_kernel[2 * kNumBins] = {};
+    double bytes_kernel[2 * kNumBins] = {};
+    int64_t rows_kernel[2 * kNumBins] = {}, entries_kernel[2 * kNumBins] = {};
     double alg_bytes = 0.0;
     u64 cand_all = 0;
-    auto account_sweep = [&](const Bins &bb) {  // algorithmic bytes (formula in louvain.h)
+    auto account_sweep = [&](const Bins &bb, int slot0) {  // algorithmic bytes (louvain.h)
         const double per_entry = 8.0 + (double)G.wbytes;
         for (int b = 0; b < kNumBins; b++) {
             double kb = (double)bb.entries[b] * per_entry;
             kb += b == 0 ? (double)n * 16.0 + (double)bb.nlist[0] * 24.0
                          : (double)bb.nlist[b] * 36.0;
-            bytes_kernel[b] += kb;
+            bytes_kernel[slot0 + b] += kb;
             alg_bytes += kb;
-            rows_kernel[b] += b == 0 ? n : bb.nlist[b];
-            entries_kernel[b] += bb.entries[b];
+            rows_kernel[slot0 + b] += b == 0 ? n : bb.nlist[b];
+            entries_kernel[slot0 + b] += bb.entries[b];
         }
     };
+    // The first sweep of the phase scores row entries without tables when every graph's
+    // rows list each column at most once: the phase starts from singletons (and vertex
+    // following), so a row's candidates other than its own community are then distinct.
+    bool first = true;
+    for (int m = 0; m < M; m++) first = first && mem[m]->distinct_rows;
+    bool had_first = false;
+    u64 cand_first[kNumBins] = {};
     int sweeps = 0, graph_sweeps = 0, captures = 0;
     int ndone_binned = 0, ndone = 0;
     // the sweeps run either as a CUDA graph whose while node repeats sweep, controllers,
@@ -988,13 +1019,15 @@ void Engine::step(std::vector<Member *> &retired)
     SweepGraph sg;
     for (;;) {
         int ran = 0, per_sweep = 0;
-        if (use_graph && !sg.exec) {
+        const bool fs = first;  // this round is the table-free first sweep
+        first = false;
+        if (use_graph && !fs && !sg.exec) {
             if (sg.build(*this, G, st, bins, TW, wide, narrow, st_dev, ctl_dev, M, bc, per_sweep))
                 captures++;
             else
                 use_graph = false;
         }
-        if (use_graph) {
+        if (use_graph && !fs) {
             LoopCtl &lp = h->pinned->loop;
             lp.iters = 0;
             lp.nd0 = ndone;
@@ -1007,8 +1040,8 @@ void Engine::step(std::vector<Member *> &retired)
             per_sweep = sg.per_sweep;
             graph_sweeps += ran;
         } else {
-            per_sweep = launch_sweep(G, st, bins, TW, wide, narrow, st_dev, &d_sc->err, s, lc,
-                                     &tm, bc);
+            per_sweep = launch_sweep(G, st, bins, TW, wide, narrow, fs, st_dev, &d_sc->err, s,
+                                     lc, &tm, bc);
             per_sweep += launch_decide(st_dev, ctl_dev, M, tr_moved.p, tr_qn.p,
                                        &d_sc->cand_total[0], &d_sc->ndone, s);
             per_sweep += launch_apply(n, st, ctl_dev, bc.vg, s, lc);
@@ -1017,15 +1050,20 @@ void Engine::step(std::vector<Member *> &retired)
         }
         kernels += (int64_t)per_sweep * ran;
         sweeps += ran;
-        for (int r = 0; r < ran; r++) account_sweep(bins);
+        const int slot0 = fs ? kNumBins : 0;
+        for (int r = 0; r < ran; r++) account_sweep(bins, slot0);
         for (int b = 0; b < kNumBins; b++) {
             if (tm.on) {
                 float ms = 0.f;
                 CK(cudaEventElapsedTime(&ms, tm.ev[2 * b], tm.ev[2 * b + 1]));
-                t_kernel[b] += ms;
+                t_kernel[slot0 + b] += ms;
             }
-            launches_kernel[b] +=
+            launches_kernel[slot0 + b] +=
                 ran * (b == 0 ? 1 : (b == kChunkedBin ? bins.nchunks > 0 : bins.nlist[b] > 0));
+        }
+        if (fs) {  // candidates of the first sweep (the totals were zeroed at phase start)
+            had_first = true;
+            for (int b = 0; b < kNumBins; b++) cand_first[b] = h->pinned->cand_total[b];
         }
         ndone = h->pinned->ndone;
         if (ndone >= M) break;
@@ -1054,7 +1092,9 @@ void Engine::step(std::vector<Member *> &retired)
     }
     for (int b = 0; b < kNumBins; b++) {  // candidate reads, 8 bytes each
         const u64 cb = h->pinned->cand_total[b];
-        bytes_kernel[b] += 8.0 * (double)cb;
+        const u64 cf = had_first ? cand_first[b] : 0;
+        bytes_kernel[b] += 8.0 * (double)(cb - cf);
+        bytes_kernel[kNumBins + b] += 8.0 * (double)cf;
         alg_bytes += 8.0 * (double)cb;
         cand_all += cb;
     }
@@ -1314,7 +1354,7 @@ void Engine::step(std::vector<Member *> &retired)
         r->exec_info[1] += sweeps - graph_sweeps;
         r->exec_info[2] += 1;
         r->exec_info[3] += captures;
-        for (int b = 0; b < kNumBins; b++) {
+        for (int b = 0; b < 2 * kNumBins; b++) {
             r->bin_time[b] += t_kernel[b];
             r->bin_launches[b] += launches_kernel[b];
             r->bin_bytes[b] += bytes_kernel[b];
@@ -1323,6 +1363,7 @@ void Engine::step(std::vector<Member *> &retired)
         }
         if (keep[m]) {
             mb->level++;
+            mb->distinct_rows = true;  // induced rows merge every column once
             mb->nv = gptr_next[m + 1] - gptr_next[m];
             mb->nnz = gnnz_next[m + 1] - gnnz_next[m];
             next.push_back(mb);
@@ -1344,16 +1385,20 @@ void finish_result(Member *m)
     r->counters[3] = r->acc_cand;
     r->counters[4] = r->acc_kernels;
     int dom = 0;
-    for (int b = 1; b < kNumBins; b++)
+    for (int b = 1; b < 2 * kNumBins; b++)
         if (r->bin_time[b] > r->bin_time[dom]) dom = b;
-    double tot = 0;
-    for (int b = 0; b < kNumBins; b++) tot += r->bin_time[b];
+    double tot = 0, t_cta = 0;
+    for (int b = 0; b < 2 * kNumBins; b++) {
+        tot += r->bin_time[b];
+        if (b % kNumBins >= 3) t_cta += r->bin_time[b];
+    }
     if (tot > 0) {
         r->times[0] = tot;
         r->times[4] = r->bin_time[dom];
-        r->times[5] = r->bin_time[0];
-        r->times[6] = r->bin_time[1] + r->bin_time[2];
-        r->times[7] = r->bin_time[3] + r->bin_time[4] + r->bin_time[5] + r->bin_time[6];
+        r->times[5] = r->bin_time[0] + r->bin_time[kNumBins];
+        r->times[6] = r->bin_time[1] + r->bin_time[2] + r->bin_time[kNumBins + 1] +
+                      r->bin_time[kNumBins + 2];
+        r->times[7] = t_cta;
         r->counters[5] = r->bin_launches[dom];
         r->counters[6] = (int64_t)r->bin_bytes[dom];
         r->counters[7] = dom;
@@ -2731,7 +2776,7 @@ int louvain_result_bin_stats(const louvain_result *r, int bin, double *time_ms,
                              int64_t *launches, int64_t *alg_bytes, int64_t *rows,
                              int64_t *entries)
 {
-    if (!r || bin < 0 || bin >= kNumBins) return LOUVAIN_ERR_INVALID_ARG;
+    if (!r || bin < 0 || bin >= 2 * kNumBins) return LOUVAIN_ERR_INVALID_ARG;
     if (time_ms) *time_ms = r->bin_time[bin];
     if (launches) *launches = r->bin_launches[bin];
     if (alg_bytes) *alg_bytes = (int64_t)r->bin_bytes[bin];

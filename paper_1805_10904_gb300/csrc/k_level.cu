@@ -87,11 +87,18 @@ int launch_fill_ones(int32_t *w, int64_t nnz, cudaStream_t s, const LaunchCfg &l
 // checked on the way.  Rows of bin 0 take one thread each (dense kernel), rows of bins 1-2
 // one warp each, longer rows one CTA each, so a hub row never serialises on one warp.
 // In a batch (vg set) 2W is per graph and a column must stay inside its row's graph.
+// unsorted[g] is set when a row of graph g does not list strictly increasing columns (then
+// a column may repeat, and the first sweep of its phase cannot score entries one by one).
 struct RowCtx {
     int64_t n;
     const int32_t *vg;
     const int64_t *gptr;
     u64 *tw;
+    unsigned *unsorted;
+    __device__ __forceinline__ void flag_unsorted(int g) const
+    {
+        if (!*(volatile unsigned *)&unsorted[g]) atomicOr(&unsorted[g], 1u);
+    }
     __device__ __forceinline__ int graph(int64_t i) const { return vg ? vg[i] : 0; }
     __device__ __forceinline__ void range(int g, int64_t &lo, int64_t &hi) const
     {
@@ -124,12 +131,18 @@ __global__ void __launch_bounds__(kBlock) k_row_sums_thread(RowCtx R, const int6
                 g = R.graph(i);
                 int64_t lo, hi;
                 R.range(g, lo, hi);
+                int32_t prev = -1;
+                bool uns = false;
                 for (int64_t k = b; k < e; k++) {
                     const i64 x = (i64)w[k];
-                    check_entry(col[k], x, lo, hi, bad);
+                    const int32_t j = col[k];
+                    check_entry(j, x, lo, hi, bad);
+                    uns = uns || j <= prev;
+                    prev = j;
                     sum += (u64)x;
                 }
                 delta[i] = (i64)sum;
+                if (uns) R.flag_unsorted(g);
             }
         }
         // one atomic per warp when its rows share a graph
@@ -161,11 +174,15 @@ __global__ void __launch_bounds__(kBlock) k_row_sums_warp(RowCtx R, const int64_
         R.range(g, lo, hi);
         const int64_t b = rp[i], e = rp[i + 1];
         u64 sum = 0;
+        bool uns = false;
         for (int64_t k = b + lane; k < e; k += 32) {
             const i64 x = (i64)w[k];
-            check_entry(col[k], x, lo, hi, bad);
+            const int32_t j = col[k];
+            check_entry(j, x, lo, hi, bad);
+            uns = uns || (k > b && j <= col[k - 1]);
             sum += (u64)x;
         }
+        if (uns) R.flag_unsorted(g);
         sum = sum_reduce(sum, 32);
         if (lane == 0) {
             delta[i] = (i64)sum;
@@ -190,11 +207,15 @@ __global__ void __launch_bounds__(kBlock) k_row_sums_cta(RowCtx R, const int64_t
         R.range(g, lo, hi);
         const int64_t b = rp[i], e = rp[i + 1];
         u64 sum = 0;
+        bool uns = false;
         for (int64_t k = b + threadIdx.x; k < e; k += kBlock) {
             const i64 x = (i64)w[k];
-            check_entry(col[k], x, lo, hi, bad);
+            const int32_t j = col[k];
+            check_entry(j, x, lo, hi, bad);
+            uns = uns || (k > b && j <= col[k - 1]);
             sum += (u64)x;
         }
+        if (uns) R.flag_unsorted(g);
         sum = sum_reduce(sum, 32);
         if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
         __syncthreads();
@@ -233,10 +254,11 @@ static int row_sums_impl(const DevGraph &g, const Bins &b, const RowCtx &R, i64 
 }
 
 int launch_row_sums(const DevGraph &g, const Bins &b, const int32_t *vg, const int64_t *gptr,
-                    i64 *delta, u64 *tw, unsigned *err, cudaStream_t s, const LaunchCfg &lc)
+                    i64 *delta, u64 *tw, unsigned *unsorted, unsigned *err, cudaStream_t s,
+                    const LaunchCfg &lc)
 {
     if (g.n == 0) return 0;
-    RowCtx R{g.n, vg, gptr, tw};
+    RowCtx R{g.n, vg, gptr, tw, unsorted};
     if (g.wbytes == 4) return row_sums_impl<int32_t>(g, b, R, delta, err, s, lc);
     return row_sums_impl<i64>(g, b, R, delta, err, s, lc);
 }

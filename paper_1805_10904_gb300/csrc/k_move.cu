@@ -44,17 +44,23 @@ size_t shared_table_bytes(int log2cap, bool narrow)
     return narrow ? table_bytes<unsigned int>(log2cap) : table_bytes<u64>(log2cap);
 }
 
-// Batch instantiation, compiled in k_move_batch.cu.
+// The other instantiations, each a translation unit of its own so that they compile in
+// parallel: k_move_batch.cu (a batch of graphs), k_move_first.cu (first sweep of a phase,
+// one graph and a batch).
 int launch_sweep_batch(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, bool wide,
+                       bool narrow, SweepStats *stats, unsigned *err, cudaStream_t s,
+                       const LaunchCfg &lc, SweepTimers *tm, const BatchCtx &bc);
+int launch_sweep_first(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, bool wide,
                        bool narrow, SweepStats *stats, unsigned *err, cudaStream_t s,
                        const LaunchCfg &lc, SweepTimers *tm, const BatchCtx &bc);
 
 int launch_sweep(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, bool wide,
-                 bool narrow, SweepStats *stats, unsigned *err, cudaStream_t s,
+                 bool narrow, bool first, SweepStats *stats, unsigned *err, cudaStream_t s,
                  const LaunchCfg &lc, SweepTimers *tm, const BatchCtx &bc)
 {
+    if (first) return launch_sweep_first(g, st, b, tw, wide, narrow, stats, err, s, lc, tm, bc);
     if (bc.vg) return launch_sweep_batch(g, st, b, tw, wide, narrow, stats, err, s, lc, tm, bc);
-    return sweep_typed<false>(g, st, b, tw, wide, narrow, stats, err, s, lc, tm, bc);
+    return sweep_typed<false, false>(g, st, b, tw, wide, narrow, stats, err, s, lc, tm, bc);
 }
 
 }  // namespace lv

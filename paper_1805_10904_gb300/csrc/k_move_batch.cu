@@ -9,7 +9,7 @@ int launch_sweep_batch(const DevGraph &g, const PhaseState &st, const Bins &b, i
                        bool narrow, SweepStats *stats, unsigned *err, cudaStream_t s,
                        const LaunchCfg &lc, SweepTimers *tm, const BatchCtx &bc)
 {
-    return sweep_typed<true>(g, st, b, tw, wide, narrow, stats, err, s, lc, tm, bc);
+    return sweep_typed<true, false>(g, st, b, tw, wide, narrow, stats, err, s, lc, tm, bc);
 }
 
 }  // namespace lv

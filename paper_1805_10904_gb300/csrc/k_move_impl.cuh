@@ -114,6 +114,30 @@ __device__ __forceinline__ void consider(int32_t c, i64 e, int32_t a, i64 dl, i6
     }
 }
 
+// Helpers of the first sweep of a phase (kernels and the reason they hold below).
+__device__ __forceinline__ u64 first_cand(u64 cnt)
+{
+    return (cnt & 0xffffffffull) + ((cnt >> 32) != 0 ? 1 : 0);
+}
+
+// Score of one non-loop entry with community c and weight x (first sweep).
+template <typename GT>
+__device__ __forceinline__ void first_entry(int32_t c, i64 x, i64 dc, int32_t a, i64 dl, i64 tw,
+                                            GT &gbest, int32_t &best, i64 &e_a, u64 &cnt)
+{
+    if (c == a) {
+        e_a += x;
+        cnt += (u64)1 << 32;
+        return;
+    }
+    cnt += 1;
+    const GT g = (GT)tw * (GT)x - (GT)dl * (GT)dc;
+    if (better(g, c, gbest, best)) {
+        gbest = g;
+        best = c;
+    }
+}
+
 // CTA-wide argmax and sums; results valid in thread 0.  Warp 0 combines the per-warp
 // partials with shuffles.  Ends with a barrier.
 template <typename GT>
@@ -150,7 +174,9 @@ __device__ __forceinline__ void block_argmax(GT &g, int32_t &c, i64 &e_a, i64 &l
 // Dense over every vertex: also adds deg[i]^2 of label i to sum_c deg_c^2.  The loop is
 // uniform across each warp so a batch of graphs can combine a warp's statistics when all
 // its vertices belong to one graph.
-template <typename WT, typename GT, bool BT>
+// FIRST: the first sweep of a phase, whose non-own candidates are pairwise distinct (see
+// the first-sweep kernels below), so entries are scored without the pairwise merge.
+template <typename WT, typename GT, bool BT, bool FIRST>
 __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small_max)
 {
     u64 internal = 0, moved = 0, cand = 0;
@@ -199,18 +225,30 @@ __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small
                 GT gbest = gain_min<GT>();
                 int32_t best = INT_MAX;
                 int m = 0;
+                if constexpr (FIRST) {
+                    u64 cnt = 0;
 #pragma unroll
-                for (int t = 0; t < kSmallMax; t++) {
-                    const int32_t c = lab[t];
-                    bool first = c >= 0;
+                    for (int t = 0; t < kSmallMax; t++) {
+                        const int32_t c = lab[t];
+                        if (c >= 0)
+                            first_entry<GT>(c, wt[t], c == a ? 0 : A.deg[c], a, dl, tw, gbest,
+                                            best, e_a, cnt);
+                    }
+                    m = (int)first_cand(cnt);
+                } else {
 #pragma unroll
-                    for (int u = 0; u < t; u++) first = first && (lab[u] != c);
-                    if (first) {
-                        i64 e = 0;
+                    for (int t = 0; t < kSmallMax; t++) {
+                        const int32_t c = lab[t];
+                        bool first = c >= 0;
 #pragma unroll
-                        for (int u = t; u < kSmallMax; u++) e += (lab[u] == c) ? wt[u] : 0;
-                        m++;
-                        consider<GT>(c, e, a, dl, tw, A.deg, gbest, best, e_a);
+                        for (int u = 0; u < t; u++) first = first && (lab[u] != c);
+                        if (first) {
+                            i64 e = 0;
+#pragma unroll
+                            for (int u = t; u < kSmallMax; u++) e += (lab[u] == c) ? wt[u] : 0;
+                            m++;
+                            consider<GT>(c, e, a, dl, tw, A.deg, gbest, best, e_a);
+                        }
                     }
                 }
                 const int32_t target = choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
@@ -836,6 +874,162 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge_decide(MoveArgs<WT> A,
     block_flush_stats(A.st, kChunkedBin, internal, moved, cand, 0);
 }
 
+// ------------------------------------------------------------------ first sweep of a phase
+// Every phase starts from singleton communities, plus, at vertex-following levels,
+// degree-one vertices placed in their only neighbour's community.  On a graph whose rows
+// list every column at most once, the communities of row i's entries other than C(i) are
+// then pairwise distinct: a non-loop neighbour j either keeps its own label j, or it
+// follows, and then its only neighbour is i and C(j) = C(i) (an isolated pair shares
+// min(i, j)).  So each candidate c != C(i) comes from a single entry, e_{i->c} = A_ij, and
+// the first sweep scores the entries directly, without any table; e_{i->C(i)} sums the
+// entries labelled C(i).  The distinct neighbouring communities of a row (the candidate
+// statistic) are its entries labelled c != C(i), plus one when some entry is labelled C(i):
+// the counters carry (entries labelled C(i)) << 32 | (other entries).
+// G lanes per row (bins 1-2): each lane scores its entries, then the group reduces.
+template <int G, typename WT, typename GT, bool BT>
+__global__ void __launch_bounds__(kBlock) k_move_group_first(MoveArgs<WT> A, const int32_t *verts,
+                                                             int nverts, int slot)
+{
+    constexpr int NG = kBlock / G;
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    u64 internal = 0, moved = 0, cand = 0;
+    for (int base = blockIdx.x * NG; base < nverts; base += gridDim.x * NG) {
+        const int vi = base + g;
+        const bool valid = vi < nverts;
+        int32_t i = 0, a = 0;
+        int64_t rb = 0, re = 0;
+        i64 dl = 0, tw = 0;
+        int gr = 0;
+        bool fz = false;
+        if (valid) {
+            i = verts[vi];
+            gr = graph_of<BT>(A, i);
+            tw = tw_of<BT>(A, gr);
+            fz = frozen<BT>(A, gr);
+            rb = A.rp[i];
+            re = fz ? rb : A.rp[i + 1];
+            a = A.C[i];
+            dl = A.delta[i];
+        }
+        i64 loop = 0, e_a = 0;
+        u64 cnt = 0;
+        GT gbest = gain_min<GT>();
+        int32_t best = INT_MAX;
+#pragma unroll 2
+        for (int64_t k = rb + lane; k < re; k += G) {
+            const int32_t j = A.col[k];
+            const i64 x = (i64)A.w[k];
+            if (j == i) {
+                loop += x;
+                continue;
+            }
+            const int32_t c = A.C[j];
+            first_entry<GT>(c, x, c == a ? 0 : A.deg[c], a, dl, tw, gbest, best, e_a, cnt);
+        }
+        argmax_reduce(gbest, best, G);
+        e_a = sum_reduce(e_a, G);
+        loop = sum_reduce(loop, G);
+        cnt = sum_reduce(cnt, G);
+        if (lane == 0 && valid) {
+            const int32_t target = choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
+            A.Cnext[i] = target;
+            if constexpr (!BT) {
+                moved += target != a;
+                internal += (u64)(e_a + loop);
+            } else if (!fz) {
+                row_stats(A.st, gr, e_a + loop, target != a);
+            }
+            cand += first_cand(cnt);
+        }
+    }
+    block_flush_stats(A.st, slot, internal, moved, cand, 0);
+}
+
+// CTA-wide argmax and sums including the entry counter; results valid in thread 0.
+template <typename GT>
+__device__ __forceinline__ void block_argmax_cnt(GT &g, int32_t &c, i64 &e_a, i64 &loop, u64 &cnt)
+{
+    __shared__ GT s_g[32];
+    __shared__ int32_t s_c[32];
+    __shared__ i64 s_e[32], s_l[32];
+    __shared__ u64 s_n[32];
+    argmax_reduce(g, c, 32);
+    e_a = sum_reduce(e_a, 32);
+    loop = sum_reduce(loop, 32);
+    cnt = sum_reduce(cnt, 32);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_g[warp] = g;
+        s_c[warp] = c;
+        s_e[warp] = e_a;
+        s_l[warp] = loop;
+        s_n[warp] = cnt;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        g = lane < nw ? s_g[lane] : gain_min<GT>();
+        c = lane < nw ? s_c[lane] : INT_MAX;
+        e_a = lane < nw ? s_e[lane] : 0;
+        loop = lane < nw ? s_l[lane] : 0;
+        cnt = lane < nw ? s_n[lane] : 0;
+        argmax_reduce(g, c, 32);
+        e_a = sum_reduce(e_a, 32);
+        loop = sum_reduce(loop, 32);
+        cnt = sum_reduce(cnt, 32);
+    }
+    __syncthreads();
+}
+
+// One CTA per row (bins 3-9): kUnroll entries in flight per thread, each scored after its
+// label and community-degree gathers; no shared table, so many CTAs fit on an SM.
+template <int BLOCK, typename WT, typename GT, bool BT>
+__global__ void __launch_bounds__(BLOCK) k_move_cta_first(MoveArgs<WT> A, const int32_t *verts,
+                                                          int nverts, int slot)
+{
+    u64 internal = 0, moved = 0, cand = 0;
+    for (int v = blockIdx.x; v < nverts; v += gridDim.x) {
+        const int32_t i = verts[v];
+        const int gr = graph_of<BT>(A, i);
+        const i64 tw = tw_of<BT>(A, gr);
+        const bool fz = frozen<BT>(A, gr);
+        const int64_t rb = A.rp[i];
+        const int64_t re = fz ? rb : A.rp[i + 1];
+        const int32_t a = A.C[i];
+        const i64 dl = A.delta[i];
+        i64 loop = 0, e_a = 0;
+        u64 cnt = 0;
+        GT gbest = gain_min<GT>();
+        int32_t best = INT_MAX;
+        for (int64_t k0 = rb + threadIdx.x; k0 < re; k0 += (int64_t)kUnroll * BLOCK) {
+            int32_t j[kUnroll], c[kUnroll];
+            i64 x[kUnroll], dc[kUnroll];
+            load_chunk<BLOCK>(A, k0, re, j, x);
+            gather_chunk(A, i, j, c);
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) dc[u] = (c[u] >= 0 && c[u] != a) ? A.deg[c[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (j[u] == i) loop += x[u];
+                else if (c[u] >= 0) first_entry<GT>(c[u], x[u], dc[u], a, dl, tw, gbest, best, e_a, cnt);
+            }
+        }
+        block_argmax_cnt(gbest, best, e_a, loop, cnt);
+        if (threadIdx.x == 0) {
+            const int32_t target = choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
+            A.Cnext[i] = target;
+            if constexpr (!BT) {
+                moved += target != a;
+                internal += (u64)(e_a + loop);
+            } else if (!fz) {
+                row_stats(A.st, gr, e_a + loop, target != a);
+            }
+            cand += first_cand(cnt);
+        }
+    }
+    block_flush_stats(A.st, slot, internal, moved, cand, 0);
+}
+
 // ------------------------------------------------------------------ launch
 
 // shared table bytes: keys + values, plus a claim list when `with_list`
@@ -845,15 +1039,22 @@ inline size_t table_bytes(int log2cap, bool with_list = false)
     return ((size_t)1 << log2cap) * (sizeof(VT) + (with_list ? 8 : 4));
 }
 
+// Grid of a persistent CTA-per-row kernel: the CTAs that can be resident at once (threads,
+// registers and shared memory all counted), at most one per row.  A larger grid would leave
+// CTAs waiting for a slot that only frees when a resident CTA has finished all its rows.
 template <typename K>
 static int launch_cta_kernel(K kernel, int block, size_t smem, int nrows, cudaStream_t s,
                              const LaunchCfg &lc, const char *name)
 {
+    (void)s;
     set_dyn_smem(kernel, smem, name);
-    const int per_sm_smem = (int)((227 * 1024) / (smem + 1024));
-    const int per_sm_thr = 2048 / block;
-    int per_sm = per_sm_smem < per_sm_thr ? per_sm_smem : per_sm_thr;
-    if (per_sm < 1) per_sm = 1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
     const int maxg = lc.num_sms * per_sm;
     return nrows < maxg ? nrows : maxg;
 }
@@ -891,7 +1092,122 @@ static int launch_cluster_kernel(K kernel, size_t smem, int nrows, cudaStream_t 
     return 1;
 }
 
+// Bins 1-9 with shared / distributed shared tables.  Returns the kernels launched.
 template <typename WT, typename GT, typename VT, bool BT>
+static int launch_bin_table(const MoveArgs<WT> &A, const Bins &b, const BinSpec &sp,
+                            const int32_t *rows, int nr, int bin, cudaStream_t bs,
+                            const LaunchCfg &lc)
+{
+    if (sp.kind == BIN_GROUP8) {
+        k_move_group<8, 6, WT, GT, VT, BT>
+            <<<grid_for(nr, kBlock / 8, lc.max_blocks), kBlock, 0, bs>>>(A, rows, nr, bin);
+        note_launch("k_move_group<8>");
+        return 1;
+    }
+    if (sp.kind == BIN_WARP) {
+        k_move_group<32, 8, WT, GT, VT, BT>
+            <<<grid_for(nr, kBlock / 32, lc.max_blocks), kBlock, 0, bs>>>(A, rows, nr, bin);
+        note_launch("k_move_group<32>");
+        return 1;
+    }
+    const int l2 = cta_log2cap(b, bin);
+    if (sp.kind == BIN_CTA) {
+        const size_t smem = table_bytes<VT>(l2, true);
+        if (sp.block == 128) {
+            const int grid = launch_cta_kernel(k_move_cta<128, WT, GT, VT, BT>, 128, smem, nr, bs,
+                                               lc, "k_move_cta<128>");
+            k_move_cta<128, WT, GT, VT, BT><<<grid, 128, smem, bs>>>(A, rows, nr, l2, bin);
+        } else if (sp.block == 256) {
+            const int grid = launch_cta_kernel(k_move_cta<256, WT, GT, VT, BT>, 256, smem, nr, bs,
+                                               lc, "k_move_cta<256>");
+            k_move_cta<256, WT, GT, VT, BT><<<grid, 256, smem, bs>>>(A, rows, nr, l2, bin);
+        } else {
+            const int grid = launch_cta_kernel(k_move_cta<1024, WT, GT, VT, BT>, 1024, smem, nr,
+                                               bs, lc, "k_move_cta<1024>");
+            k_move_cta<1024, WT, GT, VT, BT><<<grid, 1024, smem, bs>>>(A, rows, nr, l2, bin);
+        }
+        note_launch("k_move_cta");
+        return 1;
+    }
+    const size_t smem = table_bytes<VT>(l2);
+    switch (sp.cluster) {
+    case 2:
+        return launch_cluster_kernel<2>(k_move_cluster<2, WT, GT, VT, BT>, smem, nr, bs,
+                                        "k_move_cluster<2>", A, rows, nr, l2, bin);
+    case 4:
+        return launch_cluster_kernel<4>(k_move_cluster<4, WT, GT, VT, BT>, smem, nr, bs,
+                                        "k_move_cluster<4>", A, rows, nr, l2, bin);
+    case 8:
+        return launch_cluster_kernel<8>(k_move_cluster<8, WT, GT, VT, BT>, smem, nr, bs,
+                                        "k_move_cluster<8>", A, rows, nr, l2, bin);
+    default:
+        return launch_cluster_kernel<16>(k_move_cluster<16, WT, GT, VT, BT>, smem, nr, bs,
+                                         "k_move_cluster<16>", A, rows, nr, l2, bin);
+    }
+}
+
+// Bins 1-9 of the first sweep of a phase: entries scored without tables.
+template <typename WT, typename GT, bool BT>
+static int launch_bin_first(const MoveArgs<WT> &A, const BinSpec &sp, const int32_t *rows, int nr,
+                            int bin, cudaStream_t bs, const LaunchCfg &lc)
+{
+    if (sp.kind == BIN_GROUP8) {
+        k_move_group_first<8, WT, GT, BT>
+            <<<grid_for(nr, kBlock / 8, lc.max_blocks), kBlock, 0, bs>>>(A, rows, nr, bin);
+        note_launch("k_move_group_first<8>");
+    } else if (sp.kind == BIN_WARP) {
+        k_move_group_first<32, WT, GT, BT>
+            <<<grid_for(nr, kBlock / 32, lc.max_blocks), kBlock, 0, bs>>>(A, rows, nr, bin);
+        note_launch("k_move_group_first<32>");
+    } else if (sp.kind == BIN_CTA && sp.block == 128) {
+        const int grid = launch_cta_kernel(k_move_cta_first<128, WT, GT, BT>, 128, 0, nr, bs, lc,
+                                           "k_move_cta_first<128>");
+        k_move_cta_first<128, WT, GT, BT><<<grid, 128, 0, bs>>>(A, rows, nr, bin);
+        note_launch("k_move_cta_first");
+    } else if (sp.kind == BIN_CTA && sp.block == 256) {
+        const int grid = launch_cta_kernel(k_move_cta_first<256, WT, GT, BT>, 256, 0, nr, bs, lc,
+                                           "k_move_cta_first<256>");
+        k_move_cta_first<256, WT, GT, BT><<<grid, 256, 0, bs>>>(A, rows, nr, bin);
+        note_launch("k_move_cta_first");
+    } else {  // bin 5 and the cluster bins: one 1024-thread CTA per row
+        const int grid = launch_cta_kernel(k_move_cta_first<1024, WT, GT, BT>, 1024, 0, nr, bs, lc,
+                                           "k_move_cta_first<1024>");
+        k_move_cta_first<1024, WT, GT, BT><<<grid, 1024, 0, bs>>>(A, rows, nr, bin);
+        note_launch("k_move_cta_first");
+    }
+    return 1;
+}
+
+// Bin 10: chunk tables, then the slice-parallel decision for rows spanning several chunks.
+template <typename WT, typename GT, typename VT, bool BT>
+static int launch_huge(const MoveArgs<WT> &A, const Bins &b, cudaStream_t bs, const LaunchCfg &lc)
+{
+    const int32_t *rows = b.rows(kChunkedBin);
+    BigArgs B{rows,    b.chunk_b, b.chunk_first, b.nch,   b.goff,    b.glog2,
+              b.gcnt,  b.gdone,   b.gloop,       b.gkeys, b.gvals,   b.glist,
+              b.chunk, b.nchunks, b.pgain,       b.pbest, b.pea,     b.sdone,
+              b.soff,  b.slice_row, b.nslices};
+    const int l2 = 31 - __builtin_clz(2 * b.chunk);
+    const size_t smem = table_bytes<VT>(l2, true);
+    const int grid = launch_cta_kernel(k_move_huge<WT, GT, VT, BT>, kHugeBlock, smem, b.nchunks, bs,
+                                       lc, "k_move_huge");
+    k_move_huge<WT, GT, VT, BT><<<grid, kHugeBlock, smem, bs>>>(A, B);
+    note_launch("k_move_huge");
+    int launched = 1;
+    if (b.nslices > 0) {  // some rows span several chunks
+        const int64_t cap = (int64_t)lc.num_sms * 4;
+        const int dgrid = (int)(b.nslices < cap ? b.nslices : cap);
+        k_move_huge_decide<WT, GT, VT, BT><<<dgrid, kHugeBlock, 0, bs>>>(A, B);
+        note_launch("k_move_huge_decide");
+        launched++;
+    }
+    return launched;
+}
+
+// FIRST: the first sweep of a phase on a graph without repeated columns in a row; bins 1-9
+// then score entries directly (k_move_group_first / k_move_cta_first), bin 10 keeps its
+// chunk tables.
+template <typename WT, typename GT, typename VT, bool BT, bool FIRST>
 static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw,
                       SweepStats *stats, unsigned *err, cudaStream_t s, const LaunchCfg &lc,
                       SweepTimers *tm, const BatchCtx &bc)
@@ -916,79 +1232,16 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
         const int32_t *rows = b.rows(bin);
         if (sp.kind == BIN_THREAD) {
             if (g.n > 0) {  // dense over every vertex: also sums deg_c^2 over all labels
-                k_move_small<WT, GT, BT><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, bs>>>(
-                    A, (int)b.upper[0]);
+                k_move_small<WT, GT, BT, FIRST>
+                    <<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, bs>>>(A, (int)b.upper[0]);
                 note_launch("k_move_small");
                 launched++;
             }
-        } else if (nr > 0 && sp.kind == BIN_GROUP8) {
-            k_move_group<8, 6, WT, GT, VT, BT><<<grid_for(nr, kBlock / 8, lc.max_blocks), kBlock, 0,
-                                             bs>>>(A, rows, nr, bin);
-            note_launch("k_move_group<8>");
-            launched++;
-        } else if (nr > 0 && sp.kind == BIN_WARP) {
-            k_move_group<32, 8, WT, GT, VT, BT><<<grid_for(nr, kBlock / 32, lc.max_blocks), kBlock,
-                                              0, bs>>>(A, rows, nr, bin);
-            note_launch("k_move_group<32>");
-            launched++;
-        } else if (nr > 0 && sp.kind == BIN_CTA) {
-            const int l2 = cta_log2cap(b, bin);
-            const size_t smem = table_bytes<VT>(l2, true);
-            if (sp.block == 128) {
-                const int grid = launch_cta_kernel(k_move_cta<128, WT, GT, VT, BT>, 128, smem, nr, bs,
-                                                   lc, "k_move_cta<128>");
-                k_move_cta<128, WT, GT, VT, BT><<<grid, 128, smem, bs>>>(A, rows, nr, l2, bin);
-            } else if (sp.block == 256) {
-                const int grid = launch_cta_kernel(k_move_cta<256, WT, GT, VT, BT>, 256, smem, nr, bs,
-                                                   lc, "k_move_cta<256>");
-                k_move_cta<256, WT, GT, VT, BT><<<grid, 256, smem, bs>>>(A, rows, nr, l2, bin);
-            } else {
-                const int grid = launch_cta_kernel(k_move_cta<1024, WT, GT, VT, BT>, 1024, smem, nr,
-                                                   bs, lc, "k_move_cta<1024>");
-                k_move_cta<1024, WT, GT, VT, BT><<<grid, 1024, smem, bs>>>(A, rows, nr, l2, bin);
-            }
-            note_launch("k_move_cta");
-            launched++;
-        } else if (nr > 0 && sp.kind == BIN_CLUSTER) {
-            const int l2 = cta_log2cap(b, bin);
-            const size_t smem = table_bytes<VT>(l2);
-            switch (sp.cluster) {
-            case 2:
-                launched += launch_cluster_kernel<2>(k_move_cluster<2, WT, GT, VT, BT>, smem, nr, bs,
-                                                     "k_move_cluster<2>", A, rows, nr, l2, bin);
-                break;
-            case 4:
-                launched += launch_cluster_kernel<4>(k_move_cluster<4, WT, GT, VT, BT>, smem, nr, bs,
-                                                     "k_move_cluster<4>", A, rows, nr, l2, bin);
-                break;
-            case 8:
-                launched += launch_cluster_kernel<8>(k_move_cluster<8, WT, GT, VT, BT>, smem, nr, bs,
-                                                     "k_move_cluster<8>", A, rows, nr, l2, bin);
-                break;
-            default:
-                launched += launch_cluster_kernel<16>(k_move_cluster<16, WT, GT, VT, BT>, smem, nr, bs,
-                                                      "k_move_cluster<16>", A, rows, nr, l2, bin);
-                break;
-            }
-        } else if (sp.kind == BIN_CHUNKED && b.nchunks > 0) {
-            BigArgs B{rows,    b.chunk_b, b.chunk_first, b.nch,   b.goff,    b.glog2,
-                      b.gcnt,  b.gdone,   b.gloop,       b.gkeys, b.gvals,   b.glist,
-                      b.chunk, b.nchunks, b.pgain,       b.pbest, b.pea,     b.sdone,
-                      b.soff,  b.slice_row, b.nslices};
-            const int l2 = 31 - __builtin_clz(2 * b.chunk);
-            const size_t smem = table_bytes<VT>(l2, true);
-            const int grid = launch_cta_kernel(k_move_huge<WT, GT, VT, BT>, kHugeBlock, smem,
-                                               b.nchunks, bs, lc, "k_move_huge");
-            k_move_huge<WT, GT, VT, BT><<<grid, kHugeBlock, smem, bs>>>(A, B);
-            note_launch("k_move_huge");
-            launched++;
-            if (b.nslices > 0) {  // some rows span several chunks
-                const int64_t cap = (int64_t)lc.num_sms * 4;
-                const int dgrid = (int)(b.nslices < cap ? b.nslices : cap);
-                k_move_huge_decide<WT, GT, VT, BT><<<dgrid, kHugeBlock, 0, bs>>>(A, B);
-                note_launch("k_move_huge_decide");
-                launched++;
-            }
+        } else if (sp.kind == BIN_CHUNKED) {
+            if (b.nchunks > 0) launched += launch_huge<WT, GT, VT, BT>(A, b, bs, lc);
+        } else if (nr > 0) {
+            if constexpr (FIRST) launched += launch_bin_first<WT, GT, BT>(A, sp, rows, nr, bin, bs, lc);
+            else launched += launch_bin_table<WT, GT, VT, BT>(A, b, sp, rows, nr, bin, bs, lc);
         }
         if (timed) cudaEventRecord(tm->ev[2 * bin + 1], bs);
     }
@@ -1001,7 +1254,7 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
     return launched;
 }
 
-template <bool BT>
+template <bool BT, bool FIRST>
 int sweep_typed(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, bool wide,
                  bool narrow, SweepStats *stats, unsigned *err, cudaStream_t s,
                  const LaunchCfg &lc, SweepTimers *tm, const BatchCtx &bc)
@@ -1009,16 +1262,16 @@ int sweep_typed(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, 
     typedef unsigned int u32;
     if (g.wbytes == 4) {
         if (wide)
-            return narrow ? sweep_impl<int32_t, i128, u32, BT>(g, st, b, tw, stats, err, s, lc, tm, bc)
-                          : sweep_impl<int32_t, i128, u64, BT>(g, st, b, tw, stats, err, s, lc, tm, bc);
-        return narrow ? sweep_impl<int32_t, i64, u32, BT>(g, st, b, tw, stats, err, s, lc, tm, bc)
-                      : sweep_impl<int32_t, i64, u64, BT>(g, st, b, tw, stats, err, s, lc, tm, bc);
+            return narrow ? sweep_impl<int32_t, i128, u32, BT, FIRST>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                          : sweep_impl<int32_t, i128, u64, BT, FIRST>(g, st, b, tw, stats, err, s, lc, tm, bc);
+        return narrow ? sweep_impl<int32_t, i64, u32, BT, FIRST>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                      : sweep_impl<int32_t, i64, u64, BT, FIRST>(g, st, b, tw, stats, err, s, lc, tm, bc);
     }
     if (wide)
-        return narrow ? sweep_impl<i64, i128, u32, BT>(g, st, b, tw, stats, err, s, lc, tm, bc)
-                      : sweep_impl<i64, i128, u64, BT>(g, st, b, tw, stats, err, s, lc, tm, bc);
-    return narrow ? sweep_impl<i64, i64, u32, BT>(g, st, b, tw, stats, err, s, lc, tm, bc)
-                  : sweep_impl<i64, i64, u64, BT>(g, st, b, tw, stats, err, s, lc, tm, bc);
+        return narrow ? sweep_impl<i64, i128, u32, BT, FIRST>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                      : sweep_impl<i64, i128, u64, BT, FIRST>(g, st, b, tw, stats, err, s, lc, tm, bc);
+    return narrow ? sweep_impl<i64, i64, u32, BT, FIRST>(g, st, b, tw, stats, err, s, lc, tm, bc)
+                  : sweep_impl<i64, i64, u64, BT, FIRST>(g, st, b, tw, stats, err, s, lc, tm, bc);
 }
 
 }  // namespace lv

@@ -146,8 +146,11 @@ int launch_check_rows(int64_t n, const int64_t *rp, const int32_t *col, const in
 // according to the row's degree bin (bins must have been filled for g).  With vg set (a
 // batch), 2W is summed per graph into tw[vg[i]] and a column must lie in its row's graph
 // [gptr[g], gptr[g+1]); otherwise tw[0] gets the total and columns lie in [0, n).
+// delta and 2W (per graph in a batch) with the input checks; unsorted[g] (zeroed by the
+// caller) is set when a row of graph g does not list strictly increasing columns
 int launch_row_sums(const DevGraph &g, const Bins &b, const int32_t *vg, const int64_t *gptr,
-                    i64 *delta, u64 *tw, unsigned *err, cudaStream_t s, const LaunchCfg &lc);
+                    i64 *delta, u64 *tw, unsigned *unsorted, unsigned *err, cudaStream_t s,
+                    const LaunchCfg &lc);
 int launch_check_symmetry(const DevGraph &g, unsigned *err, cudaStream_t s, const LaunchCfg &lc);
 int launch_init_state(int64_t n, const PhaseState &st, cudaStream_t s, const LaunchCfg &lc);
 // Vertex following (degree-one vertices join their neighbour; an isolated pair takes the
@@ -247,9 +250,10 @@ struct SweepTimers {
     cudaEvent_t ev[2 * kNumBins];  // start/stop pair around each bin's kernel
     bool on = false;
 };
-// narrow: tables hold 32-bit sums (valid when 2W < 2^32); wide: int128 gains.
+// narrow: tables hold 32-bit sums (valid when 2W < 2^32); wide: int128 gains; first: the
+// first sweep of a phase on rows without repeated columns (scored without tables).
 int launch_sweep(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw, bool wide,
-                 bool narrow, SweepStats *stats, unsigned *err, cudaStream_t s,
+                 bool narrow, bool first, SweepStats *stats, unsigned *err, cudaStream_t s,
                  const LaunchCfg &lc, SweepTimers *tm, const BatchCtx &bc);
 
 // ---- k_coarsen.cu: graph induction (Sec. 5.1.2), renumbered labels new_id[C[u]]

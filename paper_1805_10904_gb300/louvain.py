@@ -250,9 +250,11 @@ class Result:
                 for t in range(T)]
 
     def bin_stats(self):
-        """Per degree bin: dict(time_ms, launches, alg_bytes, rows, entries) over all sweeps."""
+        """Per bin slot: dict(time_ms, launches, alg_bytes, rows, entries).  Slots
+        0 .. num_bins - 1 cover every sweep but the first of each phase, slot num_bins + b
+        bin b in the first sweep of each phase (entries scored without tables)."""
         out = []
-        for b in range(self._lib.louvain_num_bins()):
+        for b in range(2 * self._lib.louvain_num_bins()):
             t = ctypes.c_double()
             v = [ctypes.c_int64() for _ in range(4)]
             self._lib.louvain_result_bin_stats(self._p, b, ctypes.addressof(t),
