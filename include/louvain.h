@@ -76,6 +76,9 @@ typedef struct {
      *   d <= bin_cta1 / bin_cta2 / bin_cta3 -> one CTA of 128 / 256 / 1024 threads per
      *                     vertex with a shared-memory table of at least 4/3 d slots
      *                     (bin_cta3 <= 12288; lowered to 6144 when sums are 64-bit)
+     *   d <= 2/4/8/16 * bin_cta3 -> a thread-block cluster of 2/4/8/16 such CTAs per
+     *                     vertex, the table spread over the cluster's shared memory
+     *                     (sizes the device cannot host are skipped)
      *   larger         -> CTA chunks of chunk_entries entries merged in a global table.
      * Thresholds must not decrease.  All zero selects the defaults 8, 32, 128, 512, 2048,
      * 12288.  The same thresholds bin the communities (by entries) when coarsening. */

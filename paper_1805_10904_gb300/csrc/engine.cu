@@ -367,6 +367,7 @@ struct Engine {
     DBuf<int64_t> hp_soff;
     DBuf<u64> gvals;
     DBuf<i64> hp_ea;
+    DBuf<u64> hp_cnt;
     DBuf<u128> hp_gain;
     DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_tmp_col;
     DBuf<int64_t> c_mpre, c_mrow;
@@ -684,15 +685,19 @@ void Engine::prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *
         ensure(hp_slice_row, b.nslices);
         b.slice_row = hp_slice_row.p;
         kernels += launch_huge_slice_fill(b, s, lc);
-        ensure(hp_gain, b.nslices);
-        ensure(hp_best, b.nslices);
-        ensure(hp_ea, b.nslices);
+        // partials: one per slice (table sweeps), one per chunk (first sweeps)
+        const int64_t np = std::max<int64_t>(b.nslices, b.nchunks);
+        ensure(hp_gain, np);
+        ensure(hp_best, np);
+        ensure(hp_ea, np);
+        ensure(hp_cnt, b.nchunks);
         ensure(hp_sdone, nb);
         CK(cudaMemsetAsync(hp_sdone.p, 0, sizeof(int32_t) * nb, s));
     }
     b.pgain = hp_gain.p;
     b.pbest = hp_best.p;
     b.pea = hp_ea.p;
+    b.pcnt = hp_cnt.p;
     b.sdone = hp_sdone.p;
     CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
     CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));

@@ -471,13 +471,21 @@ __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A,
             int32_t *gk = B.gkeys + off;
             VT *gv = (VT *)B.gvals + off;
             int32_t *gl = B.glist + off;
-            for (int r = threadIdx.x; r < m; r += kCHugeBlock) {
-                const int s = list[r];
-                const int32_t key = keys[s];
-                const VT v = vals[s];
-                keys[s] = -1;
-                vals[s] = 0;
-                tbl_insert<true, VT>(gk, gv, gl, &B.gcnt[b], l2, key, v, A.err);
+            // claims appended a warp at a time (warp-uniform loop): one list counter per
+            // community takes every distinct key
+            for (int r0 = threadIdx.x & ~31; r0 < m; r0 += kCHugeBlock) {
+                const int r = r0 + (threadIdx.x & 31);
+                bool claimed = false;
+                int gs = 0;
+                if (r < m) {
+                    const int s = list[r];
+                    const int32_t key = keys[s];
+                    const VT v = vals[s];
+                    keys[s] = -1;
+                    vals[s] = 0;
+                    claimed = tbl_insert_claim<VT>(gk, gv, l2, key, v, A.err, gs);
+                }
+                warp_append(claimed, gs, gl, &B.gcnt[b]);
             }
         }
         __syncthreads();

@@ -679,6 +679,7 @@ struct BigArgs {
     const int64_t *soff;
     const int32_t *slice_row;
     int64_t nslices;
+    u64 *pcnt;
 };
 
 template <typename WT, typename GT, typename VT, bool BT>
@@ -771,13 +772,21 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
             int32_t *gk = B.gkeys + off;
             VT *gv = (VT *)B.gvals + off;
             int32_t *gl = B.glist + off;
-            for (int p = threadIdx.x; p < m; p += kHugeBlock) {
-                const int s = list[p];
-                const int32_t k2 = keys[s];
-                const VT e = vals[s];
-                keys[s] = -1;
-                vals[s] = 0;
-                tbl_insert<true, VT>(gk, gv, gl, &B.gcnt[b], l2, k2, e, A.err);
+            // every distinct key of a row lands on one list counter: claims are appended a
+            // warp at a time (the loop is warp-uniform so every lane reaches the append)
+            for (int p0 = threadIdx.x & ~31; p0 < m; p0 += kHugeBlock) {
+                const int p = p0 + (threadIdx.x & 31);
+                bool claimed = false;
+                int gs = 0;
+                if (p < m) {
+                    const int s = list[p];
+                    const int32_t k2 = keys[s];
+                    const VT e = vals[s];
+                    keys[s] = -1;
+                    vals[s] = 0;
+                    claimed = tbl_insert_claim<VT>(gk, gv, l2, k2, e, A.err, gs);
+                }
+                warp_append(claimed, gs, gl, &B.gcnt[b]);
             }
             loop = sum_reduce(loop, 32);
             if ((threadIdx.x & 31) == 0 && loop) atomicAdd(&B.gloop[b], (u64)loop);
@@ -1030,6 +1039,115 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta_first(MoveArgs<WT> A, const 
     block_flush_stats(A.st, slot, internal, moved, cand, 0);
 }
 
+// Bin 10 in the first sweep: each CTA chunk of a row scores its entries; a single-chunk
+// row is decided at once, otherwise the chunk's partial argmax, e_{i->C(i)} and counters go
+// to its slot (index = chunk) and the CTA that finishes the row's last chunk combines them.
+template <typename WT, typename GT, bool BT>
+__global__ void __launch_bounds__(kHugeBlock) k_move_huge_first(MoveArgs<WT> A, BigArgs B)
+{
+    __shared__ int s_last;
+    GT *pg = (GT *)B.pgain;
+    u64 internal = 0, moved = 0, cand = 0;
+    for (int c = blockIdx.x; c < B.nchunks; c += gridDim.x) {
+        const int b = B.chunk_b[c];
+        const int32_t i = B.bverts[b];
+        const int c0 = B.chunk_first[b];
+        const int q = c - c0;
+        const int nch = B.nch[b];
+        const int64_t rb = A.rp[i], re = A.rp[i + 1];
+        const int64_t cb = rb + (int64_t)q * B.chunk;
+        const int64_t ce = min(re, cb + (int64_t)B.chunk);
+        const int32_t a = A.C[i];
+        const i64 dl = A.delta[i];
+        const int gr = graph_of<BT>(A, i);
+        const i64 tw = tw_of<BT>(A, gr);
+        if (frozen<BT>(A, gr)) {  // a frozen row stays; its first chunk records that
+            if (q == 0 && threadIdx.x == 0) A.Cnext[i] = a;
+            continue;
+        }
+        i64 loop = 0, e_a = 0;
+        u64 cnt = 0;
+        GT gbest = gain_min<GT>();
+        int32_t best = INT_MAX;
+        for (int64_t k0 = cb + threadIdx.x; k0 < ce; k0 += (int64_t)kUnroll * kHugeBlock) {
+            int32_t j[kUnroll], cc[kUnroll];
+            i64 x[kUnroll], dc[kUnroll];
+            load_chunk<kHugeBlock>(A, k0, ce, j, x);
+            gather_chunk(A, i, j, cc);
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++)
+                dc[u] = (cc[u] >= 0 && cc[u] != a) ? A.deg[cc[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (j[u] == i) loop += x[u];
+                else if (cc[u] >= 0)
+                    first_entry<GT>(cc[u], x[u], dc[u], a, dl, tw, gbest, best, e_a, cnt);
+            }
+        }
+        block_argmax_cnt(gbest, best, e_a, loop, cnt);
+        if (nch == 1) {
+            if (threadIdx.x == 0) {
+                const int32_t target =
+                    choose_target<GT>(a, best, gbest, e_a, dl, tw, A.deg, A.size);
+                A.Cnext[i] = target;
+                if constexpr (!BT) {
+                    moved += target != a;
+                    internal += (u64)(e_a + loop);
+                } else {
+                    row_stats(A.st, gr, e_a + loop, target != a);
+                }
+                cand += first_cand(cnt);
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                pg[c] = gbest;
+                B.pbest[c] = best;
+                B.pea[c] = e_a;
+                B.pcnt[c] = cnt;
+                if (loop) atomicAdd(&B.gloop[b], (u64)loop);
+                __threadfence();
+                s_last = atomicAdd(&B.sdone[b], 1) == nch - 1;
+            }
+            __syncthreads();
+            if (s_last) {  // every chunk of row b is in: combine and decide
+                __threadfence();
+                GT g = gain_min<GT>();
+                int32_t cbest = INT_MAX;
+                i64 ea = 0, l0 = 0;
+                u64 n = 0;
+                for (int t = threadIdx.x; t < nch; t += kHugeBlock) {
+                    const GT gt = *(volatile const GT *)&pg[c0 + t];  // bypasses L1
+                    const int32_t ct = __ldcg(&B.pbest[c0 + t]);
+                    if (better(gt, ct, g, cbest)) {
+                        g = gt;
+                        cbest = ct;
+                    }
+                    ea += __ldcg(&B.pea[c0 + t]);
+                    n += __ldcg(&B.pcnt[c0 + t]);
+                }
+                block_argmax_cnt(g, cbest, ea, l0, n);
+                if (threadIdx.x == 0) {
+                    const i64 lp = (i64)__ldcg(&B.gloop[b]);
+                    const int32_t target =
+                        choose_target<GT>(a, cbest, g, ea, dl, tw, A.deg, A.size);
+                    A.Cnext[i] = target;
+                    if constexpr (!BT) {
+                        moved += target != a;
+                        internal += (u64)(ea + lp);
+                    } else {
+                        row_stats(A.st, gr, ea + lp, target != a);
+                    }
+                    cand += first_cand(n);
+                    B.gloop[b] = 0;
+                    B.sdone[b] = 0;
+                }
+            }
+        }
+        __syncthreads();  // s_last read before the next chunk sets it
+    }
+    block_flush_stats(A.st, kChunkedBin, internal, moved, cand, 0);
+}
+
 // ------------------------------------------------------------------ launch
 
 // shared table bytes: keys + values, plus a claim list when `with_list`
@@ -1178,6 +1296,22 @@ static int launch_bin_first(const MoveArgs<WT> &A, const BinSpec &sp, const int3
     return 1;
 }
 
+// Bin 10 in the first sweep: chunks scored without tables, combined per row.
+template <typename WT, typename GT, bool BT>
+static int launch_huge_first(const MoveArgs<WT> &A, const Bins &b, cudaStream_t bs,
+                             const LaunchCfg &lc)
+{
+    BigArgs B{b.rows(kChunkedBin), b.chunk_b, b.chunk_first, b.nch, b.goff, b.glog2,
+              b.gcnt,  b.gdone,   b.gloop,       b.gkeys, b.gvals,   b.glist,
+              b.chunk, b.nchunks, b.pgain,       b.pbest, b.pea,     b.sdone,
+              b.soff,  b.slice_row, b.nslices, b.pcnt};
+    const int grid = launch_cta_kernel(k_move_huge_first<WT, GT, BT>, kHugeBlock, 0, b.nchunks,
+                                       bs, lc, "k_move_huge_first");
+    k_move_huge_first<WT, GT, BT><<<grid, kHugeBlock, 0, bs>>>(A, B);
+    note_launch("k_move_huge_first");
+    return 1;
+}
+
 // Bin 10: chunk tables, then the slice-parallel decision for rows spanning several chunks.
 template <typename WT, typename GT, typename VT, bool BT>
 static int launch_huge(const MoveArgs<WT> &A, const Bins &b, cudaStream_t bs, const LaunchCfg &lc)
@@ -1186,7 +1320,7 @@ static int launch_huge(const MoveArgs<WT> &A, const Bins &b, cudaStream_t bs, co
     BigArgs B{rows,    b.chunk_b, b.chunk_first, b.nch,   b.goff,    b.glog2,
               b.gcnt,  b.gdone,   b.gloop,       b.gkeys, b.gvals,   b.glist,
               b.chunk, b.nchunks, b.pgain,       b.pbest, b.pea,     b.sdone,
-              b.soff,  b.slice_row, b.nslices};
+              b.soff,  b.slice_row, b.nslices, b.pcnt};
     const int l2 = 31 - __builtin_clz(2 * b.chunk);
     const size_t smem = table_bytes<VT>(l2, true);
     const int grid = launch_cta_kernel(k_move_huge<WT, GT, VT, BT>, kHugeBlock, smem, b.nchunks, bs,
@@ -1204,9 +1338,8 @@ static int launch_huge(const MoveArgs<WT> &A, const Bins &b, cudaStream_t bs, co
     return launched;
 }
 
-// FIRST: the first sweep of a phase on a graph without repeated columns in a row; bins 1-9
-// then score entries directly (k_move_group_first / k_move_cta_first), bin 10 keeps its
-// chunk tables.
+// FIRST: the first sweep of a phase on a graph without repeated columns in a row; every bin
+// then scores entries directly (k_move_group_first / k_move_cta_first / k_move_huge_first).
 template <typename WT, typename GT, typename VT, bool BT, bool FIRST>
 static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i64 tw,
                       SweepStats *stats, unsigned *err, cudaStream_t s, const LaunchCfg &lc,
@@ -1238,7 +1371,10 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
                 launched++;
             }
         } else if (sp.kind == BIN_CHUNKED) {
-            if (b.nchunks > 0) launched += launch_huge<WT, GT, VT, BT>(A, b, bs, lc);
+            if (b.nchunks > 0) {
+                if constexpr (FIRST) launched += launch_huge_first<WT, GT, BT>(A, b, bs, lc);
+                else launched += launch_huge<WT, GT, VT, BT>(A, b, bs, lc);
+            }
         } else if (nr > 0) {
             if constexpr (FIRST) launched += launch_bin_first<WT, GT, BT>(A, sp, rows, nr, bin, bs, lc);
             else launched += launch_bin_table<WT, GT, VT, BT>(A, b, sp, rows, nr, bin, bs, lc);

@@ -90,6 +90,9 @@ struct Bins {
     int64_t *soff = nullptr;   // row b's slices are soff[b] .. soff[b+1] (nb + 1)
     int32_t *slice_row = nullptr;
     int64_t nslices = 0;
+    // first sweep of a phase: the partial arrays above hold one entry per chunk instead,
+    // with the chunk's (entries labelled C(i)) << 32 | (other entries) here
+    u64 *pcnt = nullptr;
     const int32_t *rows(int b) const { return list + off[b]; }
 };
 

@@ -77,7 +77,7 @@ BATCH_CONFIGS = [
     {},
     {"bins": (1, 2, 3, 4, 5, 6), "chunk_entries": 32},
     {"bins": (0, 0, 0, 0, 0, 2)},
-    {"force_int128": True, "wide_sums": True, "bins": (0, 0, 0, 0, 0, 0), "chunk_entries": 32},
+    {"force_int128": True, "wide_sums": True, "bins": (0, 0, 0, 0, 0, 1), "chunk_entries": 32},
     {"theta": (1, 100), "max_levels": 2},
     {"max_iters": 2, "vertex_following": False},
     {"vf_all_levels": True, "theta": (0, 1)},

@@ -148,6 +148,22 @@ def test_first_sweep_every_phase(torch, lv, case, ci):
     assert res.bin_stats()[0]["launches"] == res.counters()[0][1] - phases(res)
 
 
+@pytest.mark.parametrize("case", [0, 1, 2])
+@pytest.mark.parametrize("chunk", [32, 256])
+def test_every_row_chunked(torch, lv, case, chunk):
+    """Bin bounds (0, 0, 0, 0, 0, 1) send every row longer than 16 (the largest cluster
+    bin's bound) to the chunked bin (all-zero bounds mean the defaults); in the first sweep
+    a row spanning several chunks is combined from per-chunk partial argmaxes."""
+    g = CASES[case]()
+    h = lv.Louvain(0, profile=True, bins=(0, 0, 0, 0, 0, 1), chunk_entries=chunk)
+    res = h.run(*dev(torch, g.rp, g.col, g.w))
+    assert_parity(res, oracle.louvain(g.rp, g.col, g.w))
+    nb = len(res.bin_stats()) // 2
+    # every phase whose graph still has a row longer than 16 launched the chunk kernels
+    assert 1 <= res.bin_stats()[2 * nb - 1]["launches"] <= phases(res)
+    assert 1 <= res.bin_stats()[nb - 1]["launches"] <= res.counters()[0][1] - phases(res)
+
+
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_unsorted_rows_take_tables_at_the_first_level(torch, lv, case):
     g = shuffled_rows(CASES[case](), seed=case)

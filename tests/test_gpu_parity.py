@@ -64,10 +64,10 @@ BIN_CONFIGS = [
     {},                                                          # default bins
     {"bins": (0, 0, 0, 0, 0, 12288)},                            # every row in one CTA
     {"bins": (1, 2, 3, 4, 5, 6), "chunk_entries": 32},           # every bin, many chunked rows
-    {"bins": (0, 0, 0, 0, 0, 0), "chunk_entries": 32},           # every row chunked
+    {"bins": (0, 0, 0, 0, 0, 1), "chunk_entries": 32},           # rows above 16 chunked
     {"force_int128": True},
     {"wide_sums": True, "bins": (2, 4, 8, 16, 32, 64), "chunk_entries": 64},
-    {"force_int128": True, "wide_sums": True, "bins": (0, 0, 0, 0, 0, 0), "chunk_entries": 32},
+    {"force_int128": True, "wide_sums": True, "bins": (0, 0, 0, 0, 0, 1), "chunk_entries": 32},
     {"bins": (8, 32, 128, 512, 2048, 12288), "chunk_entries": 128},
     {"bins": (0, 0, 0, 0, 0, 2)},                                # clusters of 2..16 CTAs
     {"bins": (1, 2, 3, 4, 5, 6), "wide_sums": True, "force_int128": True, "chunk_entries": 64},
