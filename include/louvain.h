@@ -111,7 +111,9 @@ typedef struct {
                                /* can be resumed from it (louvain_resume)                   */
     int32_t sweep_streams;     /* streams the degree bins of one sweep run on side by side */
                                /* (0..4; default 4; 0 or 1: one after another)             */
-    int32_t reserved[1];       /* must be zero                                           */
+    int32_t part_keys;         /* rows spanning several chunks are merged by partition: the */
+                               /* expected distinct keys per partition (64 .. 2^30; 0 or */
+                               /* the default 2048); larger means fewer partitions      */
     /* device memory: both NULL means stream-ordered cudaMallocAsync/cudaFreeAsync */
     louvain_alloc_fn alloc;
     louvain_free_fn free;

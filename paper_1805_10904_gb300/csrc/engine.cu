@@ -358,8 +358,8 @@ struct Engine {
     // per-vertex state, sized for the largest stacked graph so far
     DBuf<i64> delta, delta_next, deg;
     DBuf<int32_t> C, Cnext, size, new_id, new_id2, lists, vg;
-    DBuf<int32_t> b_nch, b_chunk_first, b_glog2, b_gcnt, b_gdone;
-    DBuf<int64_t> b_gcap, b_goff;
+    DBuf<int32_t> b_nch, b_chunk_first, b_glog2, b_gcnt, b_gdone, b_plog2;
+    DBuf<int64_t> b_gcap, b_goff, b_hoff;
     DBuf<u64> b_gloop;
     DBuf<int32_t> scratch32;
     DBuf<int64_t> scratch64;
@@ -368,6 +368,8 @@ struct Engine {
     DBuf<u64> gvals;
     DBuf<i64> hp_ea;
     DBuf<u64> hp_cnt;
+    DBuf<int32_t> hp_hofs, hp_pkeys;  // partitioned aggregation of multi-chunk rows
+    DBuf<u64> hp_pvals;
     DBuf<u128> hp_gain;
     DBuf<int32_t> c_csize, c_moff, c_cursor, c_members, c_ccnt, c_tmp_col;
     DBuf<int64_t> c_mpre, c_mrow;
@@ -621,6 +623,7 @@ Bins Engine::make_proto(bool narrow_sums) const
         pr.upper[6 + t] = lc.cluster_ok[t] ? pr.upper[5] * cl : pr.upper[5 + t];
     }
     pr.chunk = cfg.chunk_entries;
+    pr.part_keys = cfg.part_keys;
     return pr;
 }
 
@@ -640,6 +643,8 @@ Bins Engine::make_bins(const DevGraph &gr, const Bins &pr, const int32_t *vgp,
     bins.gcnt = b_gcnt.p;
     bins.gdone = b_gdone.p;
     bins.gloop = b_gloop.p;
+    bins.plog2 = b_plog2.p;
+    bins.hoff = b_hoff.p;
     kernels += launch_bin_count(gr, bins, s, lc, vgp, gctl);
     sync_scalars();
     bins.off[0] = bins.off[1] = 0;
@@ -690,8 +695,12 @@ void Engine::prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *
         ensure(hp_gain, np);
         ensure(hp_best, np);
         ensure(hp_ea, np);
-        ensure(hp_cnt, b.nchunks);
+        ensure(hp_cnt, np);
         ensure(hp_sdone, nb);
+        // each chunk's distinct (key, sum) pairs grouped by partition, with the offsets
+        ensure(hp_hofs, std::max<int64_t>(1, read_one(b_hoff.p + nb)));
+        ensure(hp_pkeys, (int64_t)b.nchunks * b.chunk);
+        ensure(hp_pvals, (int64_t)b.nchunks * b.chunk);
         CK(cudaMemsetAsync(hp_sdone.p, 0, sizeof(int32_t) * nb, s));
     }
     b.pgain = hp_gain.p;
@@ -699,6 +708,9 @@ void Engine::prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *
     b.pea = hp_ea.p;
     b.pcnt = hp_cnt.p;
     b.sdone = hp_sdone.p;
+    b.hofs = hp_hofs.p;
+    b.pkeys = hp_pkeys.p;
+    b.pvals = hp_pvals.p;
     CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
     CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
     CK(cudaMemsetAsync(b_gloop.p, 0, sizeof(u64) * nb, s));
@@ -814,6 +826,8 @@ void Engine::join()
     ensure(b_gdone, n);
     ensure(b_gcap, n);
     ensure(b_goff, (size_t)n + 1);
+    ensure(b_plog2, n);
+    ensure(b_hoff, (size_t)n + 1);
     ensure(b_gloop, n);
     const int64_t scratch_n = scan_scratch_elems(n + 1) + 64;
     ensure(scratch32, scratch_n);
@@ -1981,6 +1995,7 @@ int louvain_config_init(louvain_config *cfg)
     cfg->cuda_graphs = 1;
     cfg->autotune = 0;
     cfg->sweep_streams = 4;
+    cfg->part_keys = kPartKeys;
     return LOUVAIN_OK;
 }
 
@@ -2037,11 +2052,11 @@ static int check_config(louvain_config &c, std::string &msg)
         msg = "chunk_entries must be a power of two in [32, 4096]";
         return LOUVAIN_ERR_INVALID_ARG;
     }
-    for (int r : c.reserved)
-        if (r != 0) {
-            msg = "reserved config fields must be zero";
-            return LOUVAIN_ERR_INVALID_ARG;
-        }
+    if (c.part_keys == 0) c.part_keys = kPartKeys;
+    if (c.part_keys < 64 || c.part_keys > (1 << 30)) {
+        msg = "part_keys must be in [64, 2^30]";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
     if ((c.alloc == nullptr) != (c.free == nullptr)) {
         msg = "alloc and free callbacks must be given together";
         return LOUVAIN_ERR_INVALID_ARG;

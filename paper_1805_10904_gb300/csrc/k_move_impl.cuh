@@ -25,6 +25,7 @@
 //            tables into a global-memory table and the last chunk to finish decides.
 // Table values are 32-bit when 2W < 2^32 (every e_{i->c} <= delta_i <= 2W fits), else 64-bit.
 #pragma once
+#include <algorithm>
 #include <climits>
 
 #include <cooperative_groups.h>
@@ -166,6 +167,42 @@ __device__ __forceinline__ void block_argmax(GT &g, int32_t &c, i64 &e_a, i64 &l
         argmax_reduce(g, c, 32);
         e_a = sum_reduce(e_a, 32);
         loop = sum_reduce(loop, 32);
+    }
+    __syncthreads();
+}
+
+// CTA-wide argmax and sums including the entry counter; results valid in thread 0.
+template <typename GT>
+__device__ __forceinline__ void block_argmax_cnt(GT &g, int32_t &c, i64 &e_a, i64 &loop, u64 &cnt)
+{
+    __shared__ GT s_g[32];
+    __shared__ int32_t s_c[32];
+    __shared__ i64 s_e[32], s_l[32];
+    __shared__ u64 s_n[32];
+    argmax_reduce(g, c, 32);
+    e_a = sum_reduce(e_a, 32);
+    loop = sum_reduce(loop, 32);
+    cnt = sum_reduce(cnt, 32);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_g[warp] = g;
+        s_c[warp] = c;
+        s_e[warp] = e_a;
+        s_l[warp] = loop;
+        s_n[warp] = cnt;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        g = lane < nw ? s_g[lane] : gain_min<GT>();
+        c = lane < nw ? s_c[lane] : INT_MAX;
+        e_a = lane < nw ? s_e[lane] : 0;
+        loop = lane < nw ? s_l[lane] : 0;
+        cnt = lane < nw ? s_n[lane] : 0;
+        argmax_reduce(g, c, 32);
+        e_a = sum_reduce(e_a, 32);
+        loop = sum_reduce(loop, 32);
+        cnt = sum_reduce(cnt, 32);
     }
     __syncthreads();
 }
@@ -680,7 +717,65 @@ struct BigArgs {
     const int32_t *slice_row;
     int64_t nslices;
     u64 *pcnt;
+    const int32_t *plog2;
+    const int64_t *hoff;
+    int32_t *hofs;
+    int32_t *pkeys;
+    void *pvals;
 };
+
+// Partition of a key among a row's 2^log2p partitions: the top bits of a mixing hash
+// (multiply, xor-shift, multiply; constants of MurmurHash3's finaliser) that is independent
+// of the multiplicative hash indexing the shared table inside a partition.
+__device__ __forceinline__ int part_of(int key, int log2p)
+{
+    unsigned x = (unsigned)key * 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return log2p == 0 ? 0 : (int)(x >> (32 - log2p));
+}
+
+// In-place exclusive prefix sum of a[0..len) in shared memory by a CTA of kHugeBlock
+// threads (len <= 8 * kHugeBlock); a[len] receives the total.  Ends with a barrier.
+__device__ __forceinline__ void cta_excl_scan_smem(int *a, int len)
+{
+    __shared__ int s_w[kHugeBlock / 32];
+    __shared__ int s_tot;
+    const int per = (len + kHugeBlock - 1) / kHugeBlock;
+    const int lo = threadIdx.x * per;
+    int sum = 0;
+    for (int t = 0; t < per; t++)
+        if (lo + t < len) sum += a[lo + t];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = sum;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += u;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int x = lane < kHugeBlock / 32 ? s_w[lane] : 0;
+        int xi = x;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, xi, off);
+            if (lane >= off) xi += u;
+        }
+        if (lane < kHugeBlock / 32) s_w[lane] = xi - x;
+        if (lane == kHugeBlock / 32 - 1) s_tot = xi;
+    }
+    __syncthreads();
+    int run = s_w[warp] + incl - sum;
+    for (int t = 0; t < per; t++)
+        if (lo + t < len) {
+            const int v = a[lo + t];
+            a[lo + t] = run;
+            run += v;
+        }
+    if (threadIdx.x == 0) a[len] = s_tot;
+    __syncthreads();
+}
 
 template <typename WT, typename GT, typename VT, bool BT>
 __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArgs B)
@@ -692,6 +787,7 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
     int *keys = (int *)(vals + cap);
     int *list = keys + cap;
     __shared__ int s_cnt;
+    __shared__ int s_hist[(1 << kMaxPartLog2) + 1];
     for (int s = threadIdx.x; s < cap; s += kHugeBlock) {
         keys[s] = -1;
         vals[s] = 0;
@@ -767,30 +863,34 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
                 cand += (u64)m;
             }
         } else {
-            const int64_t off = B.goff[b];
-            const int l2 = B.glog2[b];
-            int32_t *gk = B.gkeys + off;
-            VT *gv = (VT *)B.gvals + off;
-            int32_t *gl = B.glist + off;
-            // every distinct key of a row lands on one list counter: claims are appended a
-            // warp at a time (the loop is warp-uniform so every lane reaches the append)
-            for (int p0 = threadIdx.x & ~31; p0 < m; p0 += kHugeBlock) {
-                const int p = p0 + (threadIdx.x & 31);
-                bool claimed = false;
-                int gs = 0;
-                if (p < m) {
-                    const int s = list[p];
-                    const int32_t k2 = keys[s];
-                    const VT e = vals[s];
-                    keys[s] = -1;
-                    vals[s] = 0;
-                    claimed = tbl_insert_claim<VT>(gk, gv, l2, k2, e, A.err, gs);
-                }
-                warp_append(claimed, gs, gl, &B.gcnt[b]);
+            // partitioned aggregation: the chunk's distinct keys, grouped by partition, go to
+            // the chunk's own region of the pair buffer, with the partitions' offsets;
+            // k_move_huge_decide merges each partition of the row over all its chunks
+            const int lp = B.plog2[b];
+            const int P = 1 << lp;
+            for (int p = threadIdx.x; p <= P; p += kHugeBlock) s_hist[p] = 0;
+            __syncthreads();
+            for (int r = threadIdx.x; r < m; r += kHugeBlock)
+                atomicAdd(&s_hist[part_of(keys[list[r]], lp)], 1);
+            __syncthreads();
+            cta_excl_scan_smem(s_hist, P);
+            int32_t *ho = B.hofs + B.hoff[b] + (int64_t)q * (P + 1);
+            for (int p = threadIdx.x; p <= P; p += kHugeBlock) ho[p] = s_hist[p];
+            __syncthreads();  // offsets published before they turn into cursors
+            int32_t *pk = B.pkeys + (int64_t)c * B.chunk;
+            VT *pv = (VT *)B.pvals + (int64_t)c * B.chunk;
+            for (int r = threadIdx.x; r < m; r += kHugeBlock) {
+                const int s = list[r];
+                const int32_t k2 = keys[s];
+                const VT e = vals[s];
+                keys[s] = -1;
+                vals[s] = 0;
+                const int pos = atomicAdd(&s_hist[part_of(k2, lp)], 1);
+                pk[pos] = k2;
+                pv[pos] = e;
             }
             loop = sum_reduce(loop, 32);
             if ((threadIdx.x & 31) == 0 && loop) atomicAdd(&B.gloop[b], (u64)loop);
-            // the row is decided by k_move_huge_decide once every chunk has merged
         }
         __syncthreads();
         if (threadIdx.x == 0) s_cnt = 0;
@@ -799,16 +899,34 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
     block_flush_stats(A.st, kChunkedBin, internal, moved, cand, 0);
 }
 
-// Decision of the rows spread over several chunks, after k_move_huge merged all their
-// chunks into the rows' global tables: a row's candidate list is cut into slices of
-// kHugeSlice entries (a fixed number per row, sized for the longest possible list), each
-// slice is one work item of a grid-stride loop (partial argmax, table cleared behind),
-// and the CTA that finishes a row's last slice combines the partials and decides the row.
+// Decision of the rows spread over several chunks, after k_move_huge wrote their chunks'
+// pairs: one work item per partition of a row merges that partition's pairs of every chunk
+// in a shared table and scores its keys (partial argmax); the CTA finishing a row's last
+// partition combines the partials and decides the row.  A partition whose distinct keys
+// would crowd the shared table spills into the row's global table (sized for every key of
+// the row, so it never fills), whose keys the combining CTA scores.
 template <typename WT, typename GT, typename VT, bool BT>
 __global__ void __launch_bounds__(kHugeBlock) k_move_huge_decide(MoveArgs<WT> A, BigArgs B)
 {
-    __shared__ int s_last;
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int log2cap = kPartTableLog2;
+    constexpr int cap = 1 << log2cap;
+    constexpr int thresh = cap - 3 * kHugeBlock;  // claims after the flag: < kHugeBlock
+    VT *vals = (VT *)smem;
+    int *keys = (int *)(vals + cap);
+    int *list = keys + cap;
+    __shared__ int s_cnt, s_over, s_last;
+    for (int s = threadIdx.x; s < cap; s += kHugeBlock) {
+        keys[s] = -1;
+        vals[s] = 0;
+    }
+    if (threadIdx.x == 0) {
+        s_cnt = 0;
+        s_over = 0;
+    }
+    __syncthreads();
     GT *pg = (GT *)B.pgain;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     u64 internal = 0, moved = 0, cand = 0;
     for (int64_t q = blockIdx.x; q < B.nslices; q += gridDim.x) {
         const int b = B.slice_row[q];
@@ -817,54 +935,98 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge_decide(MoveArgs<WT> A,
         if (frozen<BT>(A, gr)) continue;  // its first chunk kept it in place
         const int64_t s0 = B.soff[b];
         const int ns = (int)(B.soff[b + 1] - s0);
-        const int sl = (int)(q - s0);
-        const int gm = __ldcg(&B.gcnt[b]);
+        const int p = (int)(q - s0);
+        const int P = 1 << B.plog2[b];
+        const int nch = B.nch[b];
+        const int64_t c0 = B.chunk_first[b];
+        const int32_t *ho = B.hofs + B.hoff[b];
         const int64_t off = B.goff[b];
-        const int32_t *gl = B.glist + off;
+        const int l2 = B.glog2[b];
         int32_t *gk = B.gkeys + off;
         VT *gv = (VT *)B.gvals + off;
+        int32_t *gl = B.glist + off;
         const int32_t a = A.C[i];
         const i64 dl = A.delta[i];
         const i64 tw = tw_of<BT>(A, gr);
+        // partition p of every chunk: warps take chunks in turn, lanes the chunk's pairs
+        for (int t = warp; t < nch; t += kHugeBlock / 32) {
+            const int lo = ho[(int64_t)t * (P + 1) + p];
+            const int hi = ho[(int64_t)t * (P + 1) + p + 1];
+            const int32_t *pk = B.pkeys + (c0 + t) * B.chunk;
+            const VT *pv = (const VT *)B.pvals + (c0 + t) * B.chunk;
+            for (int r = lo + lane; r < hi; r += 32) {
+                const int32_t k2 = pk[r];
+                const VT e = pv[r];
+                if (!*(volatile int *)&s_over) {
+                    tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, k2, e, A.err);
+                    if (*(volatile int *)&s_cnt >= thresh) s_over = 1;
+                } else {
+                    tbl_insert<true, VT>(gk, gv, gl, &B.gcnt[b], l2, k2, e, A.err);
+                }
+            }
+        }
+        __syncthreads();
+        const int m = s_cnt;
+        const bool over = s_over;
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
         i64 e_a = 0, lz = 0;
-        const int pe = min(gm, (sl + 1) * kHugeSlice);
-        for (int p = sl * kHugeSlice + threadIdx.x; p < pe; p += kHugeBlock) {
-            const int s = __ldcg(gl + p);
-            const int32_t k2 = __ldcg(gk + s);
-            const i64 e = (i64)__ldcg(gv + s);
-            gk[s] = -1;
-            gv[s] = 0;
-            consider<GT>(k2, e, a, dl, tw, A.deg, gbest, best, e_a);
+        u64 mm = 0;
+        for (int r = threadIdx.x; r < m; r += kHugeBlock) {
+            const int s = list[r];
+            const int32_t k2 = keys[s];
+            const VT e = vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+            if (over) tbl_insert<true, VT>(gk, gv, gl, &B.gcnt[b], l2, k2, e, A.err);
+            else consider<GT>(k2, (i64)e, a, dl, tw, A.deg, gbest, best, e_a);
         }
-        block_argmax(gbest, best, e_a, lz);
+        if (threadIdx.x == 0 && !over) mm = (u64)m;
+        block_argmax_cnt(gbest, best, e_a, lz, mm);
         if (threadIdx.x == 0) {
             pg[q] = gbest;
             B.pbest[q] = best;
             B.pea[q] = e_a;
+            B.pcnt[q] = mm;
+            s_cnt = 0;
+            s_over = 0;
             __threadfence();
             s_last = atomicAdd(&B.sdone[b], 1) == ns - 1;
         }
         __syncthreads();
-        if (s_last) {  // every slice of row b is in: combine and decide
+        if (s_last) {  // every partition of row b is in: combine and decide
             __threadfence();
             GT g = gain_min<GT>();
-            int32_t c = INT_MAX;
+            int32_t cb = INT_MAX;
             i64 ea = 0, l0 = 0;
+            u64 n = 0;
             for (int t = threadIdx.x; t < ns; t += kHugeBlock) {
                 const GT gt = *(volatile const GT *)&pg[s0 + t];  // bypasses L1
                 const int32_t ct = __ldcg(&B.pbest[s0 + t]);
-                if (better(gt, ct, g, c)) {
+                if (better(gt, ct, g, cb)) {
                     g = gt;
-                    c = ct;
+                    cb = ct;
                 }
                 ea += __ldcg(&B.pea[s0 + t]);
+                n += __ldcg(&B.pcnt[s0 + t]);
             }
-            block_argmax(g, c, ea, l0);
+            // keys of partitions that spilled into the global table
+            const int gm = __ldcg(&B.gcnt[b]);
+            i64 eg = 0;
+            for (int r = threadIdx.x; r < gm; r += kHugeBlock) {
+                const int s = __ldcg(gl + r);
+                const int32_t k2 = __ldcg(gk + s);
+                const i64 e = (i64)__ldcg(gv + s);
+                gk[s] = -1;
+                gv[s] = 0;
+                consider<GT>(k2, e, a, dl, tw, A.deg, g, cb, eg);
+            }
+            ea += eg;
+            if (threadIdx.x == 0) n += (u64)gm;
+            block_argmax_cnt(g, cb, ea, l0, n);
             if (threadIdx.x == 0) {
                 const i64 lp = (i64)__ldcg(&B.gloop[b]);
-                const int32_t target = choose_target<GT>(a, c, g, ea, dl, tw, A.deg, A.size);
+                const int32_t target = choose_target<GT>(a, cb, g, ea, dl, tw, A.deg, A.size);
                 A.Cnext[i] = target;
                 if constexpr (!BT) {
                     moved += target != a;
@@ -872,13 +1034,13 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge_decide(MoveArgs<WT> A,
                 } else {
                     row_stats(A.st, gr, ea + lp, target != a);
                 }
-                cand += (u64)gm;
+                cand += n;
                 B.gcnt[b] = 0;
                 B.gloop[b] = 0;
                 B.sdone[b] = 0;
             }
         }
-        __syncthreads();
+        __syncthreads();  // s_last read before the next item sets it
     }
     block_flush_stats(A.st, kChunkedBin, internal, moved, cand, 0);
 }
@@ -952,42 +1114,6 @@ __global__ void __launch_bounds__(kBlock) k_move_group_first(MoveArgs<WT> A, con
         }
     }
     block_flush_stats(A.st, slot, internal, moved, cand, 0);
-}
-
-// CTA-wide argmax and sums including the entry counter; results valid in thread 0.
-template <typename GT>
-__device__ __forceinline__ void block_argmax_cnt(GT &g, int32_t &c, i64 &e_a, i64 &loop, u64 &cnt)
-{
-    __shared__ GT s_g[32];
-    __shared__ int32_t s_c[32];
-    __shared__ i64 s_e[32], s_l[32];
-    __shared__ u64 s_n[32];
-    argmax_reduce(g, c, 32);
-    e_a = sum_reduce(e_a, 32);
-    loop = sum_reduce(loop, 32);
-    cnt = sum_reduce(cnt, 32);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        s_g[warp] = g;
-        s_c[warp] = c;
-        s_e[warp] = e_a;
-        s_l[warp] = loop;
-        s_n[warp] = cnt;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = (int)(blockDim.x >> 5);
-        g = lane < nw ? s_g[lane] : gain_min<GT>();
-        c = lane < nw ? s_c[lane] : INT_MAX;
-        e_a = lane < nw ? s_e[lane] : 0;
-        loop = lane < nw ? s_l[lane] : 0;
-        cnt = lane < nw ? s_n[lane] : 0;
-        argmax_reduce(g, c, 32);
-        e_a = sum_reduce(e_a, 32);
-        loop = sum_reduce(loop, 32);
-        cnt = sum_reduce(cnt, 32);
-    }
-    __syncthreads();
 }
 
 // One CTA per row (bins 3-9): kUnroll entries in flight per thread, each scored after its
@@ -1304,7 +1430,8 @@ static int launch_huge_first(const MoveArgs<WT> &A, const Bins &b, cudaStream_t 
     BigArgs B{b.rows(kChunkedBin), b.chunk_b, b.chunk_first, b.nch, b.goff, b.glog2,
               b.gcnt,  b.gdone,   b.gloop,       b.gkeys, b.gvals,   b.glist,
               b.chunk, b.nchunks, b.pgain,       b.pbest, b.pea,     b.sdone,
-              b.soff,  b.slice_row, b.nslices, b.pcnt};
+              b.soff,  b.slice_row, b.nslices, b.pcnt, b.plog2, b.hoff, b.hofs,
+              b.pkeys, b.pvals};
     const int grid = launch_cta_kernel(k_move_huge_first<WT, GT, BT>, kHugeBlock, 0, b.nchunks,
                                        bs, lc, "k_move_huge_first");
     k_move_huge_first<WT, GT, BT><<<grid, kHugeBlock, 0, bs>>>(A, B);
@@ -1320,7 +1447,8 @@ static int launch_huge(const MoveArgs<WT> &A, const Bins &b, cudaStream_t bs, co
     BigArgs B{rows,    b.chunk_b, b.chunk_first, b.nch,   b.goff,    b.glog2,
               b.gcnt,  b.gdone,   b.gloop,       b.gkeys, b.gvals,   b.glist,
               b.chunk, b.nchunks, b.pgain,       b.pbest, b.pea,     b.sdone,
-              b.soff,  b.slice_row, b.nslices, b.pcnt};
+              b.soff,  b.slice_row, b.nslices, b.pcnt, b.plog2, b.hoff, b.hofs,
+              b.pkeys, b.pvals};
     const int l2 = 31 - __builtin_clz(2 * b.chunk);
     const size_t smem = table_bytes<VT>(l2, true);
     const int grid = launch_cta_kernel(k_move_huge<WT, GT, VT, BT>, kHugeBlock, smem, b.nchunks, bs,
@@ -1329,9 +1457,11 @@ static int launch_huge(const MoveArgs<WT> &A, const Bins &b, cudaStream_t bs, co
     note_launch("k_move_huge");
     int launched = 1;
     if (b.nslices > 0) {  // some rows span several chunks
-        const int64_t cap = (int64_t)lc.num_sms * 4;
-        const int dgrid = (int)(b.nslices < cap ? b.nslices : cap);
-        k_move_huge_decide<WT, GT, VT, BT><<<dgrid, kHugeBlock, 0, bs>>>(A, B);
+        const size_t dsmem = table_bytes<VT>(kPartTableLog2, true);
+        const int dgrid = launch_cta_kernel(k_move_huge_decide<WT, GT, VT, BT>, kHugeBlock, dsmem,
+                                            (int)std::min<int64_t>(b.nslices, INT_MAX), bs, lc,
+                                            "k_move_huge_decide");
+        k_move_huge_decide<WT, GT, VT, BT><<<dgrid, kHugeBlock, dsmem, bs>>>(A, B);
         note_launch("k_move_huge_decide");
         launched++;
     }

@@ -55,11 +55,20 @@ constexpr BinSpec kBinSpec[kNumBins] = {
 };
 constexpr int kChunkedBin = kNumBins - 1;
 constexpr int kHugeSlice = 4096;  // candidate-list entries per CTA when deciding a long row
+// Partitioned aggregation of rows spanning several chunks (table sweeps): a row's distinct
+// keys are split by hash over P = 2^plog2 partitions, P the smallest power of two that keeps
+// the expected keys per partition at or below the configured part_keys (default kPartKeys,
+// P <= 2^kMaxPartLog2); each partition is merged in a shared table of 2^kPartTableLog2
+// slots.
+constexpr int kPartKeys = 2048;
+constexpr int kMaxPartLog2 = 11;
+constexpr int kPartTableLog2 = 13;
 static_assert(kNumBins <= 16, "per-bin counters of SweepStats hold 16 bins");
 
 struct Bins {
     int64_t upper[kNumBins - 1] = {8, 32, 128, 512, 2048, 12288, 24576, 49152, 98304, 196608};
     int chunk = 4096;               // entries per CTA chunk of a chunked row
+    int part_keys = kPartKeys;      // expected distinct keys per partition of a chunked row
     int32_t *list = nullptr;        // rows of bins 1.., grouped by bin
     int64_t off[kNumBins + 1] = {}; // bin b's rows are list[off[b] .. off[b+1])
     int nlist[kNumBins] = {};
@@ -91,8 +100,17 @@ struct Bins {
     int32_t *slice_row = nullptr;
     int64_t nslices = 0;
     // first sweep of a phase: the partial arrays above hold one entry per chunk instead,
-    // with the chunk's (entries labelled C(i)) << 32 | (other entries) here
+    // with the chunk's (entries labelled C(i)) << 32 | (other entries) here; table sweeps:
+    // one entry per partition, its distinct keys here
     u64 *pcnt = nullptr;
+    // partitioned aggregation: chunk q of row b writes its distinct (key, sum) pairs grouped
+    // by partition to its region of pkeys / pvals (chunk entries each) and the partitions'
+    // offsets to hofs[hoff[b] + q * (P + 1) + p]
+    int32_t *plog2 = nullptr;
+    int64_t *hoff = nullptr;  // exclusive scan of nch * (P + 1) over multi-chunk rows (nb + 1)
+    int32_t *hofs = nullptr;
+    int32_t *pkeys = nullptr;
+    void *pvals = nullptr;    // u32 or u64 per pair (8 bytes per pair allocated)
     const int32_t *rows(int b) const { return list + off[b]; }
 };
 

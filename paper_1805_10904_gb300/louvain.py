@@ -63,7 +63,7 @@ class Config(ctypes.Structure):
         ("post_merge", ctypes.c_int32),
         ("keep_coarse", ctypes.c_int32),
         ("sweep_streams", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 1),
+        ("part_keys", ctypes.c_int32),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
@@ -308,7 +308,8 @@ class Louvain:
                  wide_sums: bool = False, bins=None, chunk_entries: int = 0,
                  profile: bool = False, torch_alloc: bool = True, cuda_graphs: bool = True,
                  autotune: bool = False, threshold_mode: int = 0, post_merge: bool = False,
-                 alloc_hook=None, keep_coarse: bool = False, sweep_streams: int = 4):
+                 alloc_hook=None, keep_coarse: bool = False, sweep_streams: int = 4,
+                 part_keys: int = 0):
         lib = load()
         self._lib = lib
         cfg = Config()
@@ -333,6 +334,8 @@ class Louvain:
         cfg.post_merge = int(post_merge)
         cfg.keep_coarse = int(keep_coarse)
         cfg.sweep_streams = int(sweep_streams)
+        if part_keys:
+            cfg.part_keys = int(part_keys)
         self.device = device
         # alloc_hook(bytes) -> bool may refuse an allocation (failure-injection tests)
         self.alloc_hook = alloc_hook

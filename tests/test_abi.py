@@ -51,6 +51,7 @@ def test_config_defaults(lib):
     assert cfg.max_iters == 1000 and cfg.vertex_following == 1 and cfg.checks == 1
     assert cfg.cuda_graphs == 1 and cfg.sweep_streams == 4 and cfg.autotune == 0
     assert cfg.threshold_mode == 0 and cfg.post_merge == 0 and cfg.keep_coarse == 0
+    assert cfg.part_keys == 2048
     assert lib.louvain_config_init(None) == 1
 
 
@@ -69,7 +70,7 @@ def test_invalid_config_rejected_before_any_device_call(lib):
     bad.bin_small = 9
     assert lib.louvain_create(ctypes.byref(bad), 0, ctypes.byref(h)) == 1
     for field, value in (("sweep_streams", 5), ("threshold_mode", 2), ("post_merge", 3),
-                         ("keep_coarse", -1)):
+                         ("keep_coarse", -1), ("part_keys", 63), ("part_keys", -5)):
         bad = Config.from_buffer_copy(cfg)
         setattr(bad, field, value)
         assert lib.louvain_create(ctypes.byref(bad), 0, ctypes.byref(h)) == 1

@@ -193,3 +193,16 @@ def test_batch_with_one_unsorted_graph(torch, lv):
     batch = h.run_batch(vptr, *dev(torch, rp, col, w), graph_eptr=eptr)
     for g, res in zip(graphs, batch):
         assert_parity(res, oracle.louvain(g.rp, g.col, g.w))
+
+
+@pytest.mark.parametrize("part_keys", [64, 1 << 30])
+@pytest.mark.parametrize("scale", [16, 17])
+def test_chunked_rows_partitioned_merge(torch, lv, scale, part_keys):
+    """Table sweeps merge a chunked row's keys partition by partition.  part_keys = 64 gives
+    many small partitions; 2^30 gives one partition per row, so the hub rows' partitions
+    outgrow the shared table and spill into the row's global table."""
+    g = gg.rmat(scale, 16, seed=5)
+    h = lv.Louvain(0, profile=True, bins=(0, 0, 0, 0, 0, 1), chunk_entries=256,
+                   part_keys=part_keys)
+    res = h.run(*dev(torch, g.rp, g.col, g.w))
+    assert_parity(res, oracle.louvain(g.rp, g.col, g.w))
