@@ -358,14 +358,14 @@ struct Engine {
     // per-vertex state, sized for the largest stacked graph so far
     DBuf<i64> delta, delta_next, deg;
     DBuf<int32_t> C, Cnext, size, new_id, new_id2, lists, vg;
-    DBuf<int32_t> b_nch, b_chunk_first, b_glog2, b_gcnt, b_gdone, b_plog2;
-    DBuf<int64_t> b_gcap, b_goff, b_hoff;
+    DBuf<int32_t> b_nch, b_chunk_first, b_plog2, b_glog2, b_gcnt, b_gdone;
+    DBuf<int64_t> b_hoff, b_gcap, b_goff;
     DBuf<u64> b_gloop;
     DBuf<int32_t> scratch32;
     DBuf<int64_t> scratch64;
     DBuf<int32_t> chunk_b, gkeys, glist, hp_best, hp_sdone, hp_slice_row;
-    DBuf<int64_t> hp_soff;
     DBuf<u64> gvals;
+    DBuf<int64_t> hp_soff;
     DBuf<i64> hp_ea;
     DBuf<u64> hp_cnt;
     DBuf<int32_t> hp_hofs, hp_pkeys;  // partitioned aggregation of multi-chunk rows
@@ -637,11 +637,6 @@ Bins Engine::make_bins(const DevGraph &gr, const Bins &pr, const int32_t *vgp,
     bins.counts = &d_sc->bin_counts[0];
     bins.nch = b_nch.p;
     bins.chunk_first = b_chunk_first.p;
-    bins.gcap = b_gcap.p;
-    bins.goff = b_goff.p;
-    bins.glog2 = b_glog2.p;
-    bins.gcnt = b_gcnt.p;
-    bins.gdone = b_gdone.p;
     bins.gloop = b_gloop.p;
     bins.plog2 = b_plog2.p;
     bins.hoff = b_hoff.p;
@@ -661,28 +656,33 @@ Bins Engine::make_bins(const DevGraph &gr, const Bins &pr, const int32_t *vgp,
 void Engine::prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *cbp)
 {
     b.nchunks = 0;
+    b.nslices = 0;
     b.gslots = 0;
     const int nb = b.nlist[kChunkedBin];
     if (nb == 0) return;
     if (coarsen_side) kernels += launch_coarsen_bigprep(k_comm, *cbp, b, s, lc);
     else kernels += launch_big_prep(G, b, scratch64.p, scratch32.p, s, lc);
     b.nchunks = read_one(b_chunk_first.p + nb);
-    b.gslots = read_one(b_goff.p + nb);
     chunk_b.reset(&A, b.nchunks);
     b.chunk_b = chunk_b.p;
     kernels += launch_big_fill(b, s, lc);
-    if (b.gslots > 0) {
-        gkeys.reset(&A, b.gslots);
-        gvals.reset(&A, b.gslots);  // 8 bytes per slot covers both sum widths
-        glist.reset(&A, b.gslots);
-        CK(cudaMemsetAsync(gkeys.p, 0xFF, sizeof(int32_t) * b.gslots, s));
-        CK(cudaMemsetAsync(gvals.p, 0, sizeof(u64) * b.gslots, s));
+    if (coarsen_side) {  // one global table per multi-chunk community
+        b.gslots = read_one(b_goff.p + nb);
+        if (b.gslots > 0) {
+            gkeys.reset(&A, b.gslots);
+            gvals.reset(&A, b.gslots);  // 8 bytes per slot covers both sum widths
+            glist.reset(&A, b.gslots);
+            CK(cudaMemsetAsync(gkeys.p, 0xFF, sizeof(int32_t) * b.gslots, s));
+            CK(cudaMemsetAsync(gvals.p, 0, sizeof(u64) * b.gslots, s));
+        }
+        b.gkeys = gkeys.p;
+        b.gvals = gvals.p;
+        b.glist = glist.p;
+        CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
+        CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
+        return;
     }
-    b.gkeys = gkeys.p;
-    b.gvals = gvals.p;
-    b.glist = glist.p;
-    b.nslices = 0;
-    if (!coarsen_side && b.gslots > 0) {
+    if (b.nchunks > nb) {  // some rows span several chunks
         ensure(hp_soff, (size_t)nb + 1);
         b.soff = hp_soff.p;
         kernels += launch_huge_slices(b, scratch64.p, s);
@@ -690,7 +690,7 @@ void Engine::prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *
         ensure(hp_slice_row, b.nslices);
         b.slice_row = hp_slice_row.p;
         kernels += launch_huge_slice_fill(b, s, lc);
-        // partials: one per slice (table sweeps), one per chunk (first sweeps)
+        // partials: one per partition (table sweeps), one per chunk (first sweeps)
         const int64_t np = std::max<int64_t>(b.nslices, b.nchunks);
         ensure(hp_gain, np);
         ensure(hp_best, np);
@@ -711,8 +711,6 @@ void Engine::prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *
     b.hofs = hp_hofs.p;
     b.pkeys = hp_pkeys.p;
     b.pvals = hp_pvals.p;
-    CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
-    CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
     CK(cudaMemsetAsync(b_gloop.p, 0, sizeof(u64) * nb, s));
 }
 
@@ -821,12 +819,13 @@ void Engine::join()
     ensure(lists, n);
     ensure(b_nch, n);
     ensure(b_chunk_first, (size_t)n + 1);
+
+    ensure(b_plog2, n);
     ensure(b_glog2, n);
     ensure(b_gcnt, n);
     ensure(b_gdone, n);
     ensure(b_gcap, n);
     ensure(b_goff, (size_t)n + 1);
-    ensure(b_plog2, n);
     ensure(b_hoff, (size_t)n + 1);
     ensure(b_gloop, n);
     const int64_t scratch_n = scan_scratch_elems(n + 1) + 64;
@@ -1259,12 +1258,14 @@ void Engine::step(std::vector<Member *> &retired)
         Bins cbins = proto;
         cbins.nch = b_nch.p;
         cbins.chunk_first = b_chunk_first.p;
+        cbins.gloop = b_gloop.p;
         cbins.gcap = b_gcap.p;
         cbins.goff = b_goff.p;
         cbins.glog2 = b_glog2.p;
         cbins.gcnt = b_gcnt.p;
         cbins.gdone = b_gdone.p;
-        cbins.gloop = b_gloop.p;
+        cbins.plog2 = b_plog2.p;
+        cbins.hoff = b_hoff.p;
         const int64_t k = k_next;
         const bool masked = batch && !all_kept;
         kernels += launch_coarsen_stage1(G, st, nid2, k, masked ? n_keep : n,

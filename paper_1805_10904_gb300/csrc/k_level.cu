@@ -483,29 +483,19 @@ int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg 
 // Chunked rows: chunk counts and, for multi-chunk rows, a global table of 2^k >= 2*min(d, n)
 // slots (distinct neighbour labels <= min(d, n) < slots, so it never fills).
 __global__ void k_big_prep(int nb, const int32_t *bverts, const int64_t *rp, int64_t n, int chunk,
-                           int part_keys, int32_t *nch, int64_t *gcap, int32_t *glog2,
-                           int32_t *plog2)
+                           int part_keys, int32_t *nch, int32_t *plog2)
 {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
         const int32_t v = bverts[b];
         const int64_t d = rp[v + 1] - rp[v];
         const int64_t c = (d + chunk - 1) / chunk;
         nch[b] = (int32_t)c;
+        int pl = 0;
         if (c > 1) {
             const int64_t keys = d < n ? d : n;  // distinct keys of the row at most
-            const int64_t need = 2 * keys;
-            int l = 1;
-            while (((int64_t)1 << l) < need) l++;
-            gcap[b] = (int64_t)1 << l;
-            glog2[b] = l;
-            int pl = 0;
             while (pl < kMaxPartLog2 && ((int64_t)part_keys << pl) < keys) pl++;
-            plog2[b] = pl;
-        } else {
-            gcap[b] = 0;
-            glog2[b] = 0;
-            plog2[b] = 0;
         }
+        plog2[b] = pl;
     }
 }
 
@@ -525,11 +515,9 @@ int launch_big_prep(const DevGraph &g, Bins &b, int64_t *scratch64, int32_t *scr
     const int nb = b.nlist[kChunkedBin];
     if (nb == 0) return 0;
     k_big_prep<<<grid_for(nb, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        nb, b.rows(kChunkedBin), g.rp, g.n, b.chunk, b.part_keys, b.nch, b.gcap, b.glog2,
-        b.plog2);
+        nb, b.rows(kChunkedBin), g.rp, g.n, b.chunk, b.part_keys, b.nch, b.plog2);
     int k = 1;
     k += exclusive_scan<int32_t>(ArrayIn<int32_t>{b.nch}, nb, b.chunk_first, scratch32, s);
-    k += exclusive_scan<int64_t>(ArrayIn<int64_t>{b.gcap}, nb, b.goff, scratch64, s);
     k += exclusive_scan<int64_t>(HistIn{b.nch, b.plog2}, nb, b.hoff, scratch64, s);
     return k;
 }

@@ -699,24 +699,19 @@ struct BigArgs {
     const int32_t *chunk_b;
     const int32_t *chunk_first;
     const int32_t *nch;
-    const int64_t *goff;
-    const int32_t *glog2;
-    int32_t *gcnt;
-    int32_t *gdone;
-    u64 *gloop;
-    int32_t *gkeys;
-    void *gvals;
-    int32_t *glist;
+    u64 *gloop;        // loop weight of every multi-chunk row
     int chunk;
     int nchunks;
+    // partials of multi-chunk rows: one per partition (table sweeps) or chunk (first sweeps)
     void *pgain;
     int32_t *pbest;
     i64 *pea;
-    int32_t *sdone;
+    u64 *pcnt;
+    int32_t *sdone;    // partials finished per row
     const int64_t *soff;
     const int32_t *slice_row;
     int64_t nslices;
-    u64 *pcnt;
+    // partitioned aggregation (table sweeps)
     const int32_t *plog2;
     const int64_t *hoff;
     int32_t *hofs;
@@ -724,57 +719,30 @@ struct BigArgs {
     void *pvals;
 };
 
-// Partition of a key among a row's 2^log2p partitions: the top bits of a mixing hash
-// (multiply, xor-shift, multiply; constants of MurmurHash3's finaliser) that is independent
-// of the multiplicative hash indexing the shared table inside a partition.
-__device__ __forceinline__ int part_of(int key, int log2p)
+inline BigArgs big_args(const Bins &b)
 {
-    unsigned x = (unsigned)key * 0x85EBCA6Bu;
-    x ^= x >> 13;
-    x *= 0xC2B2AE35u;
-    x ^= x >> 16;
-    return log2p == 0 ? 0 : (int)(x >> (32 - log2p));
-}
-
-// In-place exclusive prefix sum of a[0..len) in shared memory by a CTA of kHugeBlock
-// threads (len <= 8 * kHugeBlock); a[len] receives the total.  Ends with a barrier.
-__device__ __forceinline__ void cta_excl_scan_smem(int *a, int len)
-{
-    __shared__ int s_w[kHugeBlock / 32];
-    __shared__ int s_tot;
-    const int per = (len + kHugeBlock - 1) / kHugeBlock;
-    const int lo = threadIdx.x * per;
-    int sum = 0;
-    for (int t = 0; t < per; t++)
-        if (lo + t < len) sum += a[lo + t];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = sum;
-    for (int off = 1; off < 32; off <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += u;
-    }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const int x = lane < kHugeBlock / 32 ? s_w[lane] : 0;
-        int xi = x;
-        for (int off = 1; off < 32; off <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, xi, off);
-            if (lane >= off) xi += u;
-        }
-        if (lane < kHugeBlock / 32) s_w[lane] = xi - x;
-        if (lane == kHugeBlock / 32 - 1) s_tot = xi;
-    }
-    __syncthreads();
-    int run = s_w[warp] + incl - sum;
-    for (int t = 0; t < per; t++)
-        if (lo + t < len) {
-            const int v = a[lo + t];
-            a[lo + t] = run;
-            run += v;
-        }
-    if (threadIdx.x == 0) a[len] = s_tot;
-    __syncthreads();
+    BigArgs B;
+    B.bverts = b.rows(kChunkedBin);
+    B.chunk_b = b.chunk_b;
+    B.chunk_first = b.chunk_first;
+    B.nch = b.nch;
+    B.gloop = b.gloop;
+    B.chunk = b.chunk;
+    B.nchunks = b.nchunks;
+    B.pgain = b.pgain;
+    B.pbest = b.pbest;
+    B.pea = b.pea;
+    B.pcnt = b.pcnt;
+    B.sdone = b.sdone;
+    B.soff = b.soff;
+    B.slice_row = b.slice_row;
+    B.nslices = b.nslices;
+    B.plog2 = b.plog2;
+    B.hoff = b.hoff;
+    B.hofs = b.hofs;
+    B.pkeys = b.pkeys;
+    B.pvals = b.pvals;
+    return B;
 }
 
 template <typename WT, typename GT, typename VT, bool BT>
@@ -873,7 +841,7 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
             for (int r = threadIdx.x; r < m; r += kHugeBlock)
                 atomicAdd(&s_hist[part_of(keys[list[r]], lp)], 1);
             __syncthreads();
-            cta_excl_scan_smem(s_hist, P);
+            cta_excl_scan_smem<kHugeBlock>(s_hist, P);
             int32_t *ho = B.hofs + B.hoff[b] + (int64_t)q * (P + 1);
             for (int p = threadIdx.x; p <= P; p += kHugeBlock) ho[p] = s_hist[p];
             __syncthreads();  // offsets published before they turn into cursors
@@ -901,28 +869,23 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
 
 // Decision of the rows spread over several chunks, after k_move_huge wrote their chunks'
 // pairs: one work item per partition of a row merges that partition's pairs of every chunk
-// in a shared table and scores its keys (partial argmax); the CTA finishing a row's last
-// partition combines the partials and decides the row.  A partition whose distinct keys
-// would crowd the shared table spills into the row's global table (sized for every key of
-// the row, so it never fills), whose keys the combining CTA scores.
+// in a shared table (merge_partition, split into residue classes if its keys would crowd
+// the table) and scores its keys (partial argmax); the CTA finishing a row's last partition
+// combines the partials and decides the row.
 template <typename WT, typename GT, typename VT, bool BT>
 __global__ void __launch_bounds__(kHugeBlock) k_move_huge_decide(MoveArgs<WT> A, BigArgs B)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int log2cap = kPartTableLog2;
     constexpr int cap = 1 << log2cap;
-    constexpr int thresh = cap - 3 * kHugeBlock;  // claims after the flag: < kHugeBlock
+    constexpr int thresh = cap - 2 * kHugeBlock;
     VT *vals = (VT *)smem;
     int *keys = (int *)(vals + cap);
     int *list = keys + cap;
-    __shared__ int s_cnt, s_over, s_last;
+    __shared__ int s_last;
     for (int s = threadIdx.x; s < cap; s += kHugeBlock) {
         keys[s] = -1;
         vals[s] = 0;
-    }
-    if (threadIdx.x == 0) {
-        s_cnt = 0;
-        s_over = 0;
     }
     __syncthreads();
     GT *pg = (GT *)B.pgain;
@@ -940,56 +903,41 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge_decide(MoveArgs<WT> A,
         const int nch = B.nch[b];
         const int64_t c0 = B.chunk_first[b];
         const int32_t *ho = B.hofs + B.hoff[b];
-        const int64_t off = B.goff[b];
-        const int l2 = B.glog2[b];
-        int32_t *gk = B.gkeys + off;
-        VT *gv = (VT *)B.gvals + off;
-        int32_t *gl = B.glist + off;
         const int32_t a = A.C[i];
         const i64 dl = A.delta[i];
         const i64 tw = tw_of<BT>(A, gr);
-        // partition p of every chunk: warps take chunks in turn, lanes the chunk's pairs
-        for (int t = warp; t < nch; t += kHugeBlock / 32) {
-            const int lo = ho[(int64_t)t * (P + 1) + p];
-            const int hi = ho[(int64_t)t * (P + 1) + p + 1];
-            const int32_t *pk = B.pkeys + (c0 + t) * B.chunk;
-            const VT *pv = (const VT *)B.pvals + (c0 + t) * B.chunk;
-            for (int r = lo + lane; r < hi; r += 32) {
-                const int32_t k2 = pk[r];
-                const VT e = pv[r];
-                if (!*(volatile int *)&s_over) {
-                    tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, k2, e, A.err);
-                    if (*(volatile int *)&s_cnt >= thresh) s_over = 1;
-                } else {
-                    tbl_insert<true, VT>(gk, gv, gl, &B.gcnt[b], l2, k2, e, A.err);
-                }
-            }
-        }
-        __syncthreads();
-        const int m = s_cnt;
-        const bool over = s_over;
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
         i64 e_a = 0, lz = 0;
         u64 mm = 0;
-        for (int r = threadIdx.x; r < m; r += kHugeBlock) {
-            const int s = list[r];
-            const int32_t k2 = keys[s];
-            const VT e = vals[s];
-            keys[s] = -1;
-            vals[s] = 0;
-            if (over) tbl_insert<true, VT>(gk, gv, gl, &B.gcnt[b], l2, k2, e, A.err);
-            else consider<GT>(k2, (i64)e, a, dl, tw, A.deg, gbest, best, e_a);
-        }
-        if (threadIdx.x == 0 && !over) mm = (u64)m;
+        // partition p of every chunk: warps take chunks in turn, lanes the chunk's pairs
+        auto for_pairs = [&](auto f) {
+            for (int t = warp; t < nch; t += kHugeBlock / 32) {
+                const int lo = ho[(int64_t)t * (P + 1) + p];
+                const int hi = ho[(int64_t)t * (P + 1) + p + 1];
+                const int32_t *pk = B.pkeys + (c0 + t) * B.chunk;
+                const VT *pv = (const VT *)B.pvals + (c0 + t) * B.chunk;
+                for (int r = lo + lane; r < hi; r += 32) f(pk[r], pv[r]);
+            }
+        };
+        auto emit = [&](int m) {
+            for (int r = threadIdx.x; r < m; r += kHugeBlock) {
+                const int s = list[r];
+                const int32_t k2 = keys[s];
+                const i64 e = (i64)vals[s];
+                keys[s] = -1;
+                vals[s] = 0;
+                consider<GT>(k2, e, a, dl, tw, A.deg, gbest, best, e_a);
+            }
+            if (threadIdx.x == 0) mm += (u64)m;
+        };
+        merge_partition<kHugeBlock, VT>(keys, vals, list, log2cap, thresh, A.err, for_pairs, emit);
         block_argmax_cnt(gbest, best, e_a, lz, mm);
         if (threadIdx.x == 0) {
             pg[q] = gbest;
             B.pbest[q] = best;
             B.pea[q] = e_a;
             B.pcnt[q] = mm;
-            s_cnt = 0;
-            s_over = 0;
             __threadfence();
             s_last = atomicAdd(&B.sdone[b], 1) == ns - 1;
         }
@@ -1010,19 +958,6 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge_decide(MoveArgs<WT> A,
                 ea += __ldcg(&B.pea[s0 + t]);
                 n += __ldcg(&B.pcnt[s0 + t]);
             }
-            // keys of partitions that spilled into the global table
-            const int gm = __ldcg(&B.gcnt[b]);
-            i64 eg = 0;
-            for (int r = threadIdx.x; r < gm; r += kHugeBlock) {
-                const int s = __ldcg(gl + r);
-                const int32_t k2 = __ldcg(gk + s);
-                const i64 e = (i64)__ldcg(gv + s);
-                gk[s] = -1;
-                gv[s] = 0;
-                consider<GT>(k2, e, a, dl, tw, A.deg, g, cb, eg);
-            }
-            ea += eg;
-            if (threadIdx.x == 0) n += (u64)gm;
             block_argmax_cnt(g, cb, ea, l0, n);
             if (threadIdx.x == 0) {
                 const i64 lp = (i64)__ldcg(&B.gloop[b]);
@@ -1035,7 +970,6 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge_decide(MoveArgs<WT> A,
                     row_stats(A.st, gr, ea + lp, target != a);
                 }
                 cand += n;
-                B.gcnt[b] = 0;
                 B.gloop[b] = 0;
                 B.sdone[b] = 0;
             }
@@ -1427,11 +1361,7 @@ template <typename WT, typename GT, bool BT>
 static int launch_huge_first(const MoveArgs<WT> &A, const Bins &b, cudaStream_t bs,
                              const LaunchCfg &lc)
 {
-    BigArgs B{b.rows(kChunkedBin), b.chunk_b, b.chunk_first, b.nch, b.goff, b.glog2,
-              b.gcnt,  b.gdone,   b.gloop,       b.gkeys, b.gvals,   b.glist,
-              b.chunk, b.nchunks, b.pgain,       b.pbest, b.pea,     b.sdone,
-              b.soff,  b.slice_row, b.nslices, b.pcnt, b.plog2, b.hoff, b.hofs,
-              b.pkeys, b.pvals};
+    const BigArgs B = big_args(b);
     const int grid = launch_cta_kernel(k_move_huge_first<WT, GT, BT>, kHugeBlock, 0, b.nchunks,
                                        bs, lc, "k_move_huge_first");
     k_move_huge_first<WT, GT, BT><<<grid, kHugeBlock, 0, bs>>>(A, B);
@@ -1443,12 +1373,7 @@ static int launch_huge_first(const MoveArgs<WT> &A, const Bins &b, cudaStream_t 
 template <typename WT, typename GT, typename VT, bool BT>
 static int launch_huge(const MoveArgs<WT> &A, const Bins &b, cudaStream_t bs, const LaunchCfg &lc)
 {
-    const int32_t *rows = b.rows(kChunkedBin);
-    BigArgs B{rows,    b.chunk_b, b.chunk_first, b.nch,   b.goff,    b.glog2,
-              b.gcnt,  b.gdone,   b.gloop,       b.gkeys, b.gvals,   b.glist,
-              b.chunk, b.nchunks, b.pgain,       b.pbest, b.pea,     b.sdone,
-              b.soff,  b.slice_row, b.nslices, b.pcnt, b.plog2, b.hoff, b.hofs,
-              b.pkeys, b.pvals};
+    const BigArgs B = big_args(b);
     const int l2 = 31 - __builtin_clz(2 * b.chunk);
     const size_t smem = table_bytes<VT>(l2, true);
     const int grid = launch_cta_kernel(k_move_huge<WT, GT, VT, BT>, kHugeBlock, smem, b.nchunks, bs,

@@ -243,33 +243,6 @@ __device__ __forceinline__ void tbl_insert(int *keys, VT *vals, int *list, int *
                               err);
 }
 
-// Insert-or-add without a claim list (the owner scans the whole table afterwards): one CAS
-// to claim a slot, no shared counter.
-template <typename VT>
-__device__ __forceinline__ void tbl_insert_scan(int *keys, VT *vals, int log2cap, int key, VT val,
-                                                unsigned *err)
-{
-    const unsigned mask = (1u << log2cap) - 1u;
-    unsigned h = hash_slot(key, log2cap);
-#pragma unroll 1
-    for (unsigned probe = 0; probe <= mask; probe++) {
-        const int k = ((volatile const int *)keys)[h];
-        if (k == key) {
-            atomicAdd(&vals[h], val);
-            return;
-        }
-        if (k == -1) {
-            const int old = atomicCAS(&keys[h], -1, key);
-            if (old == -1 || old == key) {
-                atomicAdd(&vals[h], val);
-                return;
-            }
-        }
-        h = (h + 1) & mask;
-    }
-    atomicOr(err, ERRF_HASH_FULL);
-}
-
 // Insert-or-add that reports a newly claimed slot instead of appending it to a list, so
 // the caller can append claims of a whole warp with one counter update.  Returns true
 // (and the slot) only for the call that claimed the slot.
@@ -311,6 +284,140 @@ __device__ __forceinline__ void warp_append(bool claimed, int slot, int *list, i
     if (lane == leader) base = atomicAdd(cnt, __popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (claimed) list[base + __popc(m & ((1u << lane) - 1u))] = slot;
+}
+
+// Mixing hash of a key (multiply, xor-shift, multiply, xor-shift; the constants of
+// MurmurHash3's 32-bit finaliser), a bijection of 32-bit values independent of the
+// multiplicative hash that indexes the shared tables.  Its top bits choose a key's
+// partition, its low bits split a crowded partition into residue classes.
+__device__ __forceinline__ unsigned mix_hash(int key)
+{
+    unsigned x = (unsigned)key * 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x;
+}
+
+// Partition of a key among a row's 2^log2p partitions.
+__device__ __forceinline__ int part_of(int key, int log2p)
+{
+    return log2p == 0 ? 0 : (int)(mix_hash(key) >> (32 - log2p));
+}
+
+// In-place exclusive prefix sum of a[0..len) in shared memory by a CTA of BLOCK threads;
+// a[len] receives the total.  Ends with a barrier.
+template <int BLOCK>
+__device__ __forceinline__ void cta_excl_scan_smem(int *a, int len)
+{
+    __shared__ int s_w[BLOCK / 32];
+    __shared__ int s_tot;
+    const int per = (len + BLOCK - 1) / BLOCK;
+    const int lo = threadIdx.x * per;
+    int sum = 0;
+    for (int t = 0; t < per; t++)
+        if (lo + t < len) sum += a[lo + t];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = sum;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += u;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int x = lane < BLOCK / 32 ? s_w[lane] : 0;
+        int xi = x;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, xi, off);
+            if (lane >= off) xi += u;
+        }
+        if (lane < BLOCK / 32) s_w[lane] = xi - x;
+        if (lane == BLOCK / 32 - 1) s_tot = xi;
+    }
+    __syncthreads();
+    int run = s_w[warp] + incl - sum;
+    for (int t = 0; t < per; t++)
+        if (lo + t < len) {
+            const int v = a[lo + t];
+            a[lo + t] = run;
+            run += v;
+        }
+    if (threadIdx.x == 0) a[len] = s_tot;
+    __syncthreads();
+}
+
+// Merge of the (key, value) pairs of one partition in a shared table of 2^log2cap slots
+// (keys -1, values 0 on entry and on return), class by class: class (res, mod) holds the keys
+// whose mix_hash is res modulo mod (mod a power of two).  A class whose distinct keys reach
+// `thresh` claims is abandoned, its slots cleared, and redone as its two halves (res, 2 mod)
+// and (res + mod, 2 mod); inserts stop once the flag is up, so at most thresh + BLOCK slots
+// are ever claimed (thresh + BLOCK <= 2^log2cap), and since mix_hash is a bijection a class
+// shrinks to one key before mod runs out of bits.  for_pairs(f) calls f(key, value) for
+// every pair of the partition, its work spread over the CTA; emit(m) runs on every thread
+// for each completed class with m distinct keys in list[0..m) and must clear their slots.
+// Every thread of the CTA calls this; it ends with a barrier.
+template <int BLOCK, typename VT, typename ForPairs, typename Emit>
+__device__ __forceinline__ void merge_partition(int *keys, VT *vals, int *list, int log2cap,
+                                                int thresh, unsigned *err, ForPairs for_pairs,
+                                                Emit emit)
+{
+    __shared__ unsigned s_res[34], s_mod[34];
+    __shared__ unsigned s_r, s_m;
+    __shared__ int s_top, s_cnt, s_over;
+    if (threadIdx.x == 0) {
+        s_top = 1;
+        s_res[0] = 0;
+        s_mod[0] = 1;
+        s_cnt = 0;
+        s_over = 0;
+    }
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            if (s_top > 0) {
+                --s_top;
+                s_r = s_res[s_top];
+                s_m = s_mod[s_top];
+            } else {
+                s_m = 0;
+            }
+        }
+        __syncthreads();
+        const unsigned res = s_r, mod = s_m;
+        if (mod == 0) break;
+        for_pairs([&](int key, VT v) {
+            if ((mix_hash(key) & (mod - 1u)) != res || *(volatile int *)&s_over) return;
+            tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, v, err);
+            if (*(volatile int *)&s_cnt >= thresh) s_over = 1;
+        });
+        __syncthreads();
+        const int m = s_cnt;
+        if (s_over && mod >= 0x80000000u && threadIdx.x == 0)
+            atomicOr(err, ERRF_HASH_FULL);  // unreachable: such a class holds two keys at most
+        if (s_over && mod < 0x80000000u) {  // crowded: clear, then its two halves
+            for (int r = threadIdx.x; r < m; r += BLOCK) {
+                const int s = list[r];
+                keys[s] = -1;
+                vals[s] = 0;
+            }
+            if (threadIdx.x == 0) {
+                s_res[s_top] = res + mod;
+                s_mod[s_top] = 2u * mod;
+                s_res[s_top + 1] = res;
+                s_mod[s_top + 1] = 2u * mod;
+                s_top += 2;
+            }
+        } else {
+            emit(m);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_cnt = 0;
+            s_over = 0;
+        }
+        __syncthreads();
+    }
 }
 
 // Table spread over the CTAs of a thread-block cluster: one linear-probing table of

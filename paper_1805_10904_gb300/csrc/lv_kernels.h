@@ -79,30 +79,29 @@ struct Bins {
     int32_t *chunk_first = nullptr;  // exclusive scan of nch (nb + 1)
     int32_t *chunk_b = nullptr;      // chunked-list index of every chunk
     int nchunks = 0;
-    // global hash tables of multi-chunk rows
-    int64_t *gcap = nullptr;   // slots (0 for single-chunk rows)
+    u64 *gloop = nullptr;      // loop weight of every multi-chunk row
+    // graph induction: one global hash table per multi-chunk community
+    int64_t *gcap = nullptr;   // slots (0 for single-chunk communities)
     int64_t *goff = nullptr;   // exclusive scan of gcap (nb + 1)
     int32_t *glog2 = nullptr;
     int32_t *gcnt = nullptr;
     int32_t *gdone = nullptr;
-    u64 *gloop = nullptr;
     int32_t *gkeys = nullptr;
     void *gvals = nullptr;     // u32 or u64 per slot
     int32_t *glist = nullptr;
     int64_t gslots = 0;
-    // decision of multi-chunk rows: per slice of a row's candidate list one partial argmax
-    // (gain, label, e_{i->C(i)})
-    void *pgain = nullptr;     // 16 bytes per slice (int64 or int128 gain)
+    // decision of multi-chunk rows, one work item ("slice") per partition of a row's keys:
+    // partial argmax (gain, label, e_{i->C(i)}) and distinct keys of every slice; in the
+    // first sweep of a phase one partial per chunk instead, pcnt then holding the chunk's
+    // (entries labelled C(i)) << 32 | (other entries)
+    void *pgain = nullptr;     // 16 bytes per partial (int64 or int128 gain)
     int32_t *pbest = nullptr;
     i64 *pea = nullptr;
-    int32_t *sdone = nullptr;  // slices finished per row
+    u64 *pcnt = nullptr;
+    int32_t *sdone = nullptr;  // partials finished per row
     int64_t *soff = nullptr;   // row b's slices are soff[b] .. soff[b+1] (nb + 1)
     int32_t *slice_row = nullptr;
     int64_t nslices = 0;
-    // first sweep of a phase: the partial arrays above hold one entry per chunk instead,
-    // with the chunk's (entries labelled C(i)) << 32 | (other entries) here; table sweeps:
-    // one entry per partition, its distinct keys here
-    u64 *pcnt = nullptr;
     // partitioned aggregation: chunk q of row b writes its distinct (key, sum) pairs grouped
     // by partition to its region of pkeys / pvals (chunk entries each) and the partitions'
     // offsets to hofs[hoff[b] + q * (P + 1) + p]
