@@ -7,6 +7,8 @@
 //   the phase controller (Algorithm 1 stopping rule on exact Qn = (2W)^2 Q, Eq. 3),
 //   applying a sweep's moves with deg_C / size_C updates (Sec. 5.1.2 "oneLevelKernel"),
 //   renumbering by prefix-sum compaction and label composition (Sec. 5.1.2).
+#include <climits>
+
 #include "lv_common.cuh"
 #include "lv_kernels.h"
 #include "lv_scan.cuh"
@@ -84,7 +86,7 @@ int launch_fill_ones(int32_t *w, int64_t nnz, cudaStream_t s, const LaunchCfg &l
 }
 
 // delta_i = sum of row i's weights (loop once), 2W = sum delta; columns and weights are
-// checked on the way.  Rows of bin 0 take one thread each (dense kernel), rows of bins 1-2
+// checked on the way.  Rows of bin 0 take one thread each (dense kernel), rows of bins 1-4
 // one warp each, longer rows one CTA each, so a hub row never serialises on one warp.
 // In a batch (vg set) 2W is per graph and a column must stay inside its row's graph.
 // unsorted[g] is set when a row of graph g does not list strictly increasing columns (then
@@ -113,60 +115,100 @@ __device__ __forceinline__ void check_entry(int32_t j, i64 x, int64_t lo, int64_
     if (x < 1) bad |= ERRF_WEIGHT;
 }
 
+// 2W of one graph accumulated by a thread over the rows it visits: flushed to tw[g] when the
+// graph changes (rows of a batch are grouped by graph) and at the end, so a one-graph run
+// issues one atomic per thread instead of one per row.
+struct TwAcc {
+    int g = -1;
+    u64 s = 0;
+    __device__ __forceinline__ void add(const RowCtx &R, int gr, u64 x)
+    {
+        if (gr != g) {
+            if (g >= 0 && s) atomicAdd(&R.tw[g], s);
+            g = gr;
+            s = 0;
+        }
+        s += x;
+    }
+    __device__ __forceinline__ void flush(const RowCtx &R)
+    {
+        if (g >= 0 && s) atomicAdd(&R.tw[g], s);
+        g = -1;
+        s = 0;
+    }
+    // every lane of the warp calls this: one atomic per warp when the lanes share a graph
+    __device__ __forceinline__ void flush_warp(const RowCtx &R)
+    {
+        const int g0 = __shfl_sync(0xffffffffu, g, 0);
+        if (__all_sync(0xffffffffu, g == g0 || s == 0)) {
+            const u64 t = sum_reduce(s, 32);
+            if ((threadIdx.x & 31) == 0 && g0 >= 0 && t) atomicAdd(&R.tw[g0], t);
+            g = -1;
+            s = 0;
+        } else {
+            flush(R);
+        }
+    }
+};
+
+// Rows of at most dmax (<= 8) entries, one thread each: the row's entries are loaded
+// together into registers, then checked and summed.
 template <typename WT>
 __global__ void __launch_bounds__(kBlock) k_row_sums_thread(RowCtx R, const int64_t *rp,
                                                             const int32_t *col, const WT *w,
                                                             int64_t dmax, i64 *delta,
                                                             unsigned *err)
 {
+    constexpr int kMax = 8;
     unsigned bad = 0;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < R.n;
-         i0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = i0 + threadIdx.x;
+    TwAcc acc;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = rp[i], e = rp[i + 1];
+        const int64_t d = e - b;
+        if (d > dmax) continue;
+        int32_t j[kMax];
+        i64 x[kMax];
+#pragma unroll
+        for (int t = 0; t < kMax; t++) {
+            j[t] = t < d ? col[b + t] : 0;
+            x[t] = t < d ? (i64)w[b + t] : 1;
+        }
+        const int g = R.graph(i);
+        int64_t lo, hi;
+        R.range(g, lo, hi);
         u64 sum = 0;
-        int g = -1;
-        if (i < R.n) {
-            const int64_t b = rp[i], e = rp[i + 1];
-            if (e - b <= dmax) {
-                g = R.graph(i);
-                int64_t lo, hi;
-                R.range(g, lo, hi);
-                int32_t prev = -1;
-                bool uns = false;
-                for (int64_t k = b; k < e; k++) {
-                    const i64 x = (i64)w[k];
-                    const int32_t j = col[k];
-                    check_entry(j, x, lo, hi, bad);
-                    uns = uns || j <= prev;
-                    prev = j;
-                    sum += (u64)x;
-                }
-                delta[i] = (i64)sum;
-                if (uns) R.flag_unsorted(g);
+        bool uns = false;
+#pragma unroll
+        for (int t = 0; t < kMax; t++) {
+            if (t < d) {
+                check_entry(j[t], x[t], lo, hi, bad);
+                if (t > 0) uns = uns || j[t] <= j[t - 1];
+                sum += (u64)x[t];
             }
         }
-        // one atomic per warp when its rows share a graph
-        const int g0 = __shfl_sync(0xffffffffu, g, 0);
-        if (__all_sync(0xffffffffu, g == g0 || g < 0)) {
-            const u64 ws = sum_reduce(sum, 32);
-            if ((threadIdx.x & 31) == 0 && g0 >= 0 && ws) atomicAdd(&R.tw[g0], ws);
-        } else if (g >= 0 && sum) {
-            atomicAdd(&R.tw[g], sum);
-        }
+        delta[i] = (i64)sum;
+        if (uns) R.flag_unsorted(g);
+        acc.add(R, g, sum);
     }
+    acc.flush_warp(R);
     if (bad) atomicOr(err, bad);
 }
 
+// One warp per row (bins 1-4), four entries in flight per lane; the previous entry of a
+// lane's entry (for the order check) is its left neighbour's, or the last of the round before.
 template <typename WT>
 __global__ void __launch_bounds__(kBlock) k_row_sums_warp(RowCtx R, const int64_t *rp,
                                                           const int32_t *col, const WT *w,
                                                           const int32_t *rows, int64_t nrows,
                                                           i64 *delta, unsigned *err)
 {
+    constexpr int U = 4;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned bad = 0;
+    TwAcc acc;
     for (int64_t r = warp; r < nrows; r += nwarps) {
         const int32_t i = rows[r];
         const int g = R.graph(i);
@@ -175,31 +217,55 @@ __global__ void __launch_bounds__(kBlock) k_row_sums_warp(RowCtx R, const int64_
         const int64_t b = rp[i], e = rp[i + 1];
         u64 sum = 0;
         bool uns = false;
-        for (int64_t k = b + lane; k < e; k += 32) {
-            const i64 x = (i64)w[k];
-            const int32_t j = col[k];
-            check_entry(j, x, lo, hi, bad);
-            uns = uns || (k > b && j <= col[k - 1]);
-            sum += (u64)x;
+        int32_t last = INT_MIN;  // column of the entry before this round
+        for (int64_t k0 = b + lane; k0 - lane < e; k0 += 32 * U) {
+            int32_t j[U];
+            i64 x[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t k = k0 + 32 * u;
+                j[u] = k < e ? col[k] : INT_MAX;
+                x[u] = k < e ? (i64)w[k] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t k = k0 + 32 * u;
+                int32_t prev = __shfl_up_sync(0xffffffffu, j[u], 1);
+                if (lane == 0) prev = last;
+                last = __shfl_sync(0xffffffffu, j[u], 31);
+                if (k < e) {
+                    check_entry(j[u], x[u], lo, hi, bad);
+                    uns = uns || (k > b && j[u] <= prev);
+                    sum += (u64)x[u];
+                }
+            }
         }
-        if (uns) R.flag_unsorted(g);
+        if (__any_sync(0xffffffffu, uns) && lane == 0) R.flag_unsorted(g);
         sum = sum_reduce(sum, 32);
         if (lane == 0) {
             delta[i] = (i64)sum;
-            atomicAdd(&R.tw[g], sum);
+            acc.add(R, g, sum);
         }
     }
+    if (lane == 0) acc.flush(R);
     if (bad) atomicOr(err, bad);
 }
 
+// One CTA per longer row, four entries in flight per thread.
 template <typename WT>
 __global__ void __launch_bounds__(kBlock) k_row_sums_cta(RowCtx R, const int64_t *rp,
                                                          const int32_t *col, const WT *w,
                                                          const int32_t *rows, int64_t nrows,
                                                          i64 *delta, unsigned *err)
 {
+    constexpr int U = 4;
     __shared__ u64 s_part[kBlock / 32];
+    __shared__ int s_uns;
+    const int lane = threadIdx.x & 31;
     unsigned bad = 0;
+    TwAcc acc;
+    if (threadIdx.x == 0) s_uns = 0;
+    __syncthreads();
     for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
         const int32_t i = rows[r];
         const int g = R.graph(i);
@@ -208,25 +274,42 @@ __global__ void __launch_bounds__(kBlock) k_row_sums_cta(RowCtx R, const int64_t
         const int64_t b = rp[i], e = rp[i + 1];
         u64 sum = 0;
         bool uns = false;
-        for (int64_t k = b + threadIdx.x; k < e; k += kBlock) {
-            const i64 x = (i64)w[k];
-            const int32_t j = col[k];
-            check_entry(j, x, lo, hi, bad);
-            uns = uns || (k > b && j <= col[k - 1]);
-            sum += (u64)x;
+        for (int64_t k0 = b + threadIdx.x; k0 - threadIdx.x < e; k0 += (int64_t)kBlock * U) {
+            int32_t j[U];
+            i64 x[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t k = k0 + (int64_t)kBlock * u;
+                j[u] = k < e ? col[k] : INT_MAX;
+                x[u] = k < e ? (i64)w[k] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t k = k0 + (int64_t)kBlock * u;
+                int32_t prev = __shfl_up_sync(0xffffffffu, j[u], 1);
+                if (lane == 0 && k > b && k < e) prev = col[k - 1];  // left entry in another warp
+                if (k < e) {
+                    check_entry(j[u], x[u], lo, hi, bad);
+                    uns = uns || (k > b && j[u] <= prev);
+                    sum += (u64)x[u];
+                }
+            }
         }
-        if (uns) R.flag_unsorted(g);
+        if (uns) s_uns = 1;
         sum = sum_reduce(sum, 32);
-        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
+        if (lane == 0) s_part[threadIdx.x >> 5] = sum;
         __syncthreads();
         if (threadIdx.x == 0) {
             u64 t = 0;
             for (int q = 0; q < kBlock / 32; q++) t += s_part[q];
             delta[i] = (i64)t;
-            atomicAdd(&R.tw[g], t);
+            acc.add(R, g, t);
+            if (s_uns) R.flag_unsorted(g);
+            s_uns = 0;
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0) acc.flush(R);
     if (bad) atomicOr(err, bad);
 }
 
@@ -238,16 +321,18 @@ static int row_sums_impl(const DevGraph &g, const Bins &b, const RowCtx &R, i64 
     int launched = 1;
     k_row_sums_thread<WT><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
         R, g.rp, g.col, w, b.upper[0], delta, err);
-    const int64_t nwarp = b.off[3] - b.off[1];
+    // a warp per row up to bin 4's rows, a CTA per longer row (the per-row barriers and
+    // reduction of a CTA cost more than the extra rounds of a warp on rows up to 2,048)
+    const int64_t nwarp = b.off[5] - b.off[1];
     if (nwarp > 0) {
         k_row_sums_warp<WT><<<grid_for(nwarp, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(
             R, g.rp, g.col, w, b.list + b.off[1], nwarp, delta, err);
         launched++;
     }
-    const int64_t ncta = b.off[kNumBins] - b.off[3];
+    const int64_t ncta = b.off[kNumBins] - b.off[5];
     if (ncta > 0) {
         k_row_sums_cta<WT><<<grid_for(ncta, 1, lc.max_blocks), kBlock, 0, s>>>(
-            R, g.rp, g.col, w, b.list + b.off[3], ncta, delta, err);
+            R, g.rp, g.col, w, b.list + b.off[5], ncta, delta, err);
         launched++;
     }
     return launched;
@@ -412,6 +497,9 @@ __global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, Bi
                                                 int32_t *counts)
 {
     const int lane = threadIdx.x & 31;
+    // count pass: per-thread counts and entries, reduced per warp and per CTA, so each CTA
+    // adds once per bin
+    int cnt[kNumBins] = {};
     u64 ent[kNumBins] = {};
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n;
          i0 += (int64_t)gridDim.x * blockDim.x) {
@@ -422,16 +510,18 @@ __global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, Bi
             d = rp[i + 1] - rp[i];
             bin = bin_of(d, ba.upper);
         }
+        if (!FILL) {
 #pragma unroll
-        for (int b = 0; b < kNumBins; b++) {
+            for (int b = 0; b < kNumBins; b++) {
+                cnt[b] += bin == b;
+                ent[b] += bin == b ? (u64)d : 0;
+            }
+            continue;
+        }
+#pragma unroll
+        for (int b = 1; b < kNumBins; b++) {
             const unsigned mask = __ballot_sync(0xffffffffu, bin == b);
             if (!mask) continue;
-            if (!FILL) {
-                if (bin == b) ent[b] += (u64)d;
-                if (lane == __ffs(mask) - 1) atomicAdd(&counts[b], __popc(mask));
-                continue;
-            }
-            if (b == 0) continue;
             const int leader = __ffs(mask) - 1;
             int base = 0;
             if (lane == leader) base = atomicAdd(&counts[b], __popc(mask));
@@ -441,10 +531,26 @@ __global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, Bi
         }
     }
     if (!FILL) {
+        __shared__ int s_cnt[kNumBins];
+        __shared__ unsigned long long s_ent[kNumBins];
+        if (threadIdx.x < kNumBins) {
+            s_cnt[threadIdx.x] = 0;
+            s_ent[threadIdx.x] = 0;
+        }
+        __syncthreads();
 #pragma unroll
         for (int b = 0; b < kNumBins; b++) {
-            u64 v = sum_reduce(ent[b], 32);
-            if (lane == 0 && v) atomicAdd((u64 *)(counts + 16 + 2 * b), v);
+            const int c = sum_reduce(cnt[b], 32);
+            const u64 e = sum_reduce(ent[b], 32);
+            if (lane == 0 && c) {
+                atomicAdd(&s_cnt[b], c);
+                atomicAdd(&s_ent[b], (unsigned long long)e);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumBins && s_cnt[threadIdx.x]) {
+            atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]);
+            atomicAdd((u64 *)(counts + 16 + 2 * threadIdx.x), (u64)s_ent[threadIdx.x]);
         }
     }
 }
