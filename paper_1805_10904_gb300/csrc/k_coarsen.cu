@@ -91,6 +91,8 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_bin(int64_t k, const int32_t
                                                         int32_t *counts)
 {
     const int lane = threadIdx.x & 31;
+    __shared__ int s_cnt[kNumBins], s_base[kNumBins];
+    int cnt[kNumBins] = {};
     for (int64_t a0 = (int64_t)blockIdx.x * blockDim.x; a0 < k; a0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = a0 + threadIdx.x;
         int bin = -1;
@@ -101,17 +103,43 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_bin(int64_t k, const int32_t
             for (int t = 0; t < kNumBins - 1; t++) b += e > ba.upper[t];
             bin = b < 2 ? 2 : b;
         }
+        if (!FILL) {  // count pass: per thread, added once per CTA and bin at the end
+#pragma unroll
+            for (int b = 2; b < kNumBins; b++) cnt[b] += bin == b;
+            continue;
+        }
+        // fill pass: positions claimed once per CTA and bin, warps ranked in shared memory
+        if (threadIdx.x < kNumBins) s_cnt[threadIdx.x] = 0;
+        __syncthreads();
+        int rank = 0;
 #pragma unroll
         for (int b = 2; b < kNumBins; b++) {
             const unsigned mask = __ballot_sync(0xffffffffu, bin == b);
             if (!mask) continue;
             const int leader = __ffs(mask) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(&counts[b], __popc(mask));
-            if (!FILL) continue;
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (bin == b) ba.list[ba.off[b] + base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)a;
+            int wbase = 0;
+            if (lane == leader) wbase = atomicAdd(&s_cnt[b], __popc(mask));
+            wbase = __shfl_sync(0xffffffffu, wbase, leader);
+            if (bin == b) rank = wbase + __popc(mask & ((1u << lane) - 1u));
         }
+        __syncthreads();
+        if (threadIdx.x < kNumBins)
+            s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]) : 0;
+        __syncthreads();
+        if (bin >= 2) ba.list[ba.off[bin] + s_base[bin] + rank] = (int32_t)a;
+        __syncthreads();  // s_cnt / s_base read before the next round resets them
+    }
+    if (!FILL) {
+        if (threadIdx.x < kNumBins) s_cnt[threadIdx.x] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int b = 2; b < kNumBins; b++) {
+            const int c = sum_reduce(cnt[b], 32);
+            if (lane == 0 && c) atomicAdd(&s_cnt[b], c);
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumBins && s_cnt[threadIdx.x])
+            atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]);
     }
 }
 

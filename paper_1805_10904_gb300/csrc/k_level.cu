@@ -497,6 +497,7 @@ __global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, Bi
                                                 int32_t *counts)
 {
     const int lane = threadIdx.x & 31;
+    __shared__ int s_fcnt[kNumBins], s_fbase[kNumBins];
     // count pass: per-thread counts and entries, reduced per warp and per CTA, so each CTA
     // adds once per bin
     int cnt[kNumBins] = {};
@@ -518,17 +519,27 @@ __global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, Bi
             }
             continue;
         }
+        // fill pass: positions claimed once per CTA and bin, warps ranked in shared memory
+        if (threadIdx.x < kNumBins) s_fcnt[threadIdx.x] = 0;
+        __syncthreads();
+        int rank = 0;
 #pragma unroll
         for (int b = 1; b < kNumBins; b++) {
             const unsigned mask = __ballot_sync(0xffffffffu, bin == b);
             if (!mask) continue;
             const int leader = __ffs(mask) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(&counts[b], __popc(mask));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (bin == b)
-                ba.list[ba.off[b] + base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
+            int wbase = 0;
+            if (lane == leader) wbase = atomicAdd(&s_fcnt[b], __popc(mask));
+            wbase = __shfl_sync(0xffffffffu, wbase, leader);
+            if (bin == b) rank = wbase + __popc(mask & ((1u << lane) - 1u));
         }
+        __syncthreads();
+        if (threadIdx.x < kNumBins)
+            s_fbase[threadIdx.x] =
+                s_fcnt[threadIdx.x] ? atomicAdd(&counts[threadIdx.x], s_fcnt[threadIdx.x]) : 0;
+        __syncthreads();
+        if (bin >= 1) ba.list[ba.off[bin] + s_fbase[bin] + rank] = (int32_t)i;
+        __syncthreads();  // counts read before the next round resets them
     }
     if (!FILL) {
         __shared__ int s_cnt[kNumBins];
