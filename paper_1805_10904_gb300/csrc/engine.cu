@@ -1273,10 +1273,10 @@ void Engine::step(std::vector<Member *> &retired)
                                          nullptr, delta_next.p, cb, cbins, s, lc);
         sync_scalars();
         cbins.list = lists.p;  // the sweep's lists are free again
-        cbins.off[0] = cbins.off[1] = cbins.off[2] = 0;
+        cbins.off[0] = cbins.off[1] = 0;  // bin-0 communities are counted in bin 1
         for (int b = 0; b < kNumBins; b++) {
-            cbins.nlist[b] = b < 2 ? 0 : h->pinned->ccounts[b];
-            if (b >= 2) cbins.off[b + 1] = cbins.off[b] + cbins.nlist[b];
+            cbins.nlist[b] = b < 1 ? 0 : h->pinned->ccounts[b];
+            if (b >= 1) cbins.off[b + 1] = cbins.off[b] + cbins.nlist[b];
         }
         kernels += launch_coarsen_binfill(k, cb, cbins, s, lc);
         prep_huge(cbins, true, k, &cb);

@@ -77,8 +77,8 @@ __device__ __forceinline__ int64_t comm_entries(const int32_t *moff, const int64
     return mpre[moff[a + 1]] - mpre[moff[a]];
 }
 
-// Communities binned by entry count with the sweep's thresholds (rows of bins 0..2 all go
-// to the warp kernel of bin 2).  Count pass: counts[b] and entries; fill pass: list regions.
+// Communities binned by entry count with the sweep's thresholds (communities of bin 0 join
+// the 8-lane groups of bin 1).  Count pass: counts[b]; fill pass: list regions.
 struct CBinArgs {
     int64_t upper[kNumBins - 1];
     int64_t off[kNumBins + 1];
@@ -101,11 +101,11 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_bin(int64_t k, const int32_t
             int b = 0;
 #pragma unroll
             for (int t = 0; t < kNumBins - 1; t++) b += e > ba.upper[t];
-            bin = b < 2 ? 2 : b;
+            bin = b < 1 ? 1 : b;  // bin-0 communities join the 8-lane groups of bin 1
         }
         if (!FILL) {  // count pass: per thread, added once per CTA and bin at the end
 #pragma unroll
-            for (int b = 2; b < kNumBins; b++) cnt[b] += bin == b;
+            for (int b = 1; b < kNumBins; b++) cnt[b] += bin == b;
             continue;
         }
         // fill pass: positions claimed once per CTA and bin, warps ranked in shared memory
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_bin(int64_t k, const int32_t
         __syncthreads();
         int rank = 0;
 #pragma unroll
-        for (int b = 2; b < kNumBins; b++) {
+        for (int b = 1; b < kNumBins; b++) {
             const unsigned mask = __ballot_sync(0xffffffffu, bin == b);
             if (!mask) continue;
             const int leader = __ffs(mask) - 1;
@@ -126,14 +126,14 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_bin(int64_t k, const int32_t
         if (threadIdx.x < kNumBins)
             s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]) : 0;
         __syncthreads();
-        if (bin >= 2) ba.list[ba.off[bin] + s_base[bin] + rank] = (int32_t)a;
+        if (bin >= 1) ba.list[ba.off[bin] + s_base[bin] + rank] = (int32_t)a;
         __syncthreads();  // s_cnt / s_base read before the next round resets them
     }
     if (!FILL) {
         if (threadIdx.x < kNumBins) s_cnt[threadIdx.x] = 0;
         __syncthreads();
 #pragma unroll
-        for (int b = 2; b < kNumBins; b++) {
+        for (int b = 1; b < kNumBins; b++) {
             const int c = sum_reduce(cnt[b], 32);
             if (lane == 0 && c) atomicAdd(&s_cnt[b], c);
         }
@@ -202,12 +202,13 @@ __device__ __forceinline__ void flat_entry(const CoarsenArgs<WT> &A, int32_t &p,
     wv = (i64)A.w[kk];
 }
 
-// One warp per community with few entries: 256-slot shared table per warp.
-template <typename WT, typename VT>
+// G lanes per community with few entries (8 for at most 32 entries, a warp for at most
+// 128): a 2^LOG2CAP-slot shared table per group.
+template <int G, int LOG2CAP, typename WT, typename VT>
 __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, const int32_t *clist,
                                                           int ncl)
 {
-    constexpr int LOG2CAP = 8, CAP = 1 << LOG2CAP, NG = kBlock / 32;
+    constexpr int CAP = 1 << LOG2CAP, NG = kBlock / G;
     __shared__ int s_keys[NG * CAP];
     __shared__ VT s_vals[NG * CAP];
     __shared__ int s_list[NG * CAP];
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
     }
     if (threadIdx.x < NG) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
     int *keys = s_keys + g * CAP;
     VT *vals = s_vals + g * CAP;
     int *list = s_list + g * CAP;
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
             te = A.mpre[pe];
         }
         int32_t p = pb;
-        for (int64_t t = tb + lane; t < te; t += 32) {
+        for (int64_t t = tb + lane; t < te; t += G) {
             int32_t key;
             i64 wv;
             flat_entry(A, p, pe, t, key, wv);
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
         }
         __syncwarp();
         const int m = valid ? *(volatile int *)cnt : 0;
-        for (int q = lane; q < m; q += 32) {
+        for (int q = lane; q < m; q += G) {
             const int s = list[q];
             A.tmp_col[tb + q] = keys[s];
             ((VT *)A.tmp_w)[tb + q] = vals[s];
@@ -579,18 +580,23 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_compact(int64_t k, int64_t n
     for (int64_t o0 = warp * kCompactSlice; o0 < nnz_next; o0 += nwarps * kCompactSlice) {
         const int64_t o1 = min(nnz_next, o0 + kCompactSlice);
         int64_t a = row_of(rp_next, 0, k, o0);
+        // the lane's current row: its end and the shift from output to source index, reloaded
+        // only when the lane's entry crosses into a later row
+        int64_t end = rp_next[a + 1];
+        int64_t shift = mpre[moff[a]] - rp_next[a];
         for (int64_t o = o0 + lane; o < o1; o += 32) {
-            if (rp_next[a + 1] <= o) {  // gallop from the next row, then bisect
+            if (end <= o) {  // gallop from the next row, then bisect
                 int64_t lo = a + 1, step = 1;
                 while (lo + step < k && rp_next[lo + step] <= o) {
                     lo += step;
                     step <<= 1;
                 }
                 a = row_of(rp_next, lo, lo + step < k ? lo + step : k, o);
+                end = rp_next[a + 1];
+                shift = mpre[moff[a]] - rp_next[a];
             }
-            const int64_t src = mpre[moff[a]] + (o - rp_next[a]);
-            col_next[o] = tmp_col[src];
-            w_next[o] = (WO)tmp_w[src];
+            col_next[o] = tmp_col[o + shift];
+            w_next[o] = (WO)tmp_w[o + shift];
         }
     }
 }
@@ -716,15 +722,20 @@ static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *n
     CoarsenArgs<WT> A{g.rp,    g.col,   (const WT *)g.w, st.Cnext,   new_id,   cb.moff,
                       cb.mrow, cb.mpre, cb.ccnt,         cb.tmp_col, cb.tmp_w, err};
     int launched = 1;
-    for (int bin = 2; bin < kNumBins; bin++) {
+    for (int bin = 1; bin < kNumBins; bin++) {
         const BinSpec sp = kBinSpec[bin];
         const int nr = bins.nlist[bin];
         const int32_t *rows = bins.rows(bin);
         if (nr == 0 && sp.kind != BIN_CHUNKED) continue;
-        if (sp.kind == BIN_WARP) {
-            k_coarsen_group<WT, VT><<<grid_for(nr, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(
+        if (sp.kind == BIN_GROUP8) {
+            k_coarsen_group<8, 6, WT, VT><<<grid_for(nr, kBlock / 8, lc.max_blocks), kBlock, 0, s>>>(
                 A, rows, nr);
-            note_launch("k_coarsen_group");
+            note_launch("k_coarsen_group<8>");
+            launched++;
+        } else if (sp.kind == BIN_WARP) {
+            k_coarsen_group<32, 8, WT, VT><<<grid_for(nr, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(
+                A, rows, nr);
+            note_launch("k_coarsen_group<32>");
             launched++;
         } else if (sp.kind == BIN_CTA) {
             const int l2 = cta_log2cap(bins, bin);
