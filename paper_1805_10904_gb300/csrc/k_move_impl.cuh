@@ -366,11 +366,24 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
             dl = A.delta[i];
         }
         i64 loop = 0;
-        for (int64_t k = rb + lane; k < re; k += G) {
-            const int32_t j = A.col[k];
-            const i64 x = (i64)A.w[k];
-            if (j == i) loop += x;
-            else tbl_insert<false, VT>(keys, vals, list, cnt, LOG2CAP, A.C[j], (VT)x, A.err);
+        // kUnroll entries per lane in flight: columns and weights, then their labels
+        for (int64_t k0 = rb + lane; k0 < re; k0 += (int64_t)G * kUnroll) {
+            int32_t j[kUnroll], c[kUnroll];
+            i64 x[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const int64_t k = k0 + (int64_t)G * u;
+                j[u] = k < re ? A.col[k] : -1;
+                x[u] = k < re ? (i64)A.w[k] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (j[u] == i) loop += x[u];
+                else if (c[u] >= 0)
+                    tbl_insert<false, VT>(keys, vals, list, cnt, LOG2CAP, c[u], (VT)x[u], A.err);
+            }
         }
         __syncwarp();
         const int m = valid ? *(volatile int *)cnt : 0;
@@ -1020,16 +1033,25 @@ __global__ void __launch_bounds__(kBlock) k_move_group_first(MoveArgs<WT> A, con
         u64 cnt = 0;
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
-#pragma unroll 2
-        for (int64_t k = rb + lane; k < re; k += G) {
-            const int32_t j = A.col[k];
-            const i64 x = (i64)A.w[k];
-            if (j == i) {
-                loop += x;
-                continue;
+        for (int64_t k0 = rb + lane; k0 < re; k0 += (int64_t)G * kUnroll) {
+            int32_t j[kUnroll], c[kUnroll];
+            i64 x[kUnroll], dc[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const int64_t k = k0 + (int64_t)G * u;
+                j[u] = k < re ? A.col[k] : -1;
+                x[u] = k < re ? (i64)A.w[k] : 0;
             }
-            const int32_t c = A.C[j];
-            first_entry<GT>(c, x, c == a ? 0 : A.deg[c], a, dl, tw, gbest, best, e_a, cnt);
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) dc[u] = (c[u] >= 0 && c[u] != a) ? A.deg[c[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (j[u] == i) loop += x[u];
+                else if (c[u] >= 0)
+                    first_entry<GT>(c[u], x[u], dc[u], a, dl, tw, gbest, best, e_a, cnt);
+            }
         }
         argmax_reduce(gbest, best, G);
         e_a = sum_reduce(e_a, G);
