@@ -300,6 +300,12 @@ int64_t louvain_result_num_vertices(const louvain_result *r);
 int louvain_result_labels(const louvain_result *r, int level, const int32_t **labels,
                           int64_t *ncomm);
 
+/* Same labels copied into the caller's host buffer dst (n int32 values, any host memory;
+ * the copy goes through a pinned staging buffer of the library, two 8 MB halves so the
+ * transfer of one overlaps the host copy of the other).  Returns when dst is filled.
+ * Errors: INVALID_ARG (bad level, dst NULL with n > 0), CUDA. */
+int louvain_result_labels_into(const louvain_result *r, int level, int32_t *dst);
+
 /* Same labels in device memory owned by r (no copy). */
 int louvain_result_labels_device(const louvain_result *r, int level, const int32_t **labels);
 

@@ -1965,6 +1965,87 @@ struct RunCtx {
 
 }  // namespace
 
+// ------------------------------------------------------------ device -> host label copies
+// A process-wide pinned staging buffer (two halves) and a stream of its own: a copy into
+// ordinary host memory moves each chunk into pinned memory by DMA, then copies it on the host
+// while the next chunk is in flight.
+struct PinnedStage {
+    std::mutex mu;
+    int device = -1;
+    char *buf = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    static constexpr size_t kHalf = (size_t)8 << 20;
+
+    void release()
+    {
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+        if (s) cudaStreamDestroy(s);
+        if (buf) cudaFreeHost(buf);
+        ev[0] = ev[1] = nullptr;
+        s = nullptr;
+        buf = nullptr;
+        device = -1;
+    }
+    bool ready(int dev)
+    {
+        if (device == dev && buf) return true;
+        release();
+        if (cudaMallocHost((void **)&buf, 2 * kHalf) != cudaSuccess) {
+            buf = nullptr;
+            return false;
+        }
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
+            release();
+            return false;
+        }
+        device = dev;
+        return true;
+    }
+};
+
+PinnedStage &pinned_stage()
+{
+    static PinnedStage st;  // lives until the process exits (pinned memory is released then)
+    return st;
+}
+
+bool copy_d2h_staged(int device, void *dst, const void *src, size_t bytes)
+{
+    PinnedStage &st = pinned_stage();
+    std::lock_guard<std::mutex> lock(st.mu);
+    if (cudaSetDevice(device) != cudaSuccess || !st.ready(device)) return false;
+    const char *from = (const char *)src;
+    char *to = (char *)dst;
+    size_t pend_off[2] = {0, 0}, pend_len[2] = {0, 0};
+    bool pend[2] = {false, false};
+    int next = 0;
+    auto drain = [&](int hb) {
+        if (!pend[hb]) return true;
+        if (cudaEventSynchronize(st.ev[hb]) != cudaSuccess) return false;
+        memcpy(to + pend_off[hb], st.buf + hb * PinnedStage::kHalf, pend_len[hb]);
+        pend[hb] = false;
+        return true;
+    };
+    for (size_t off = 0; off < bytes; off += PinnedStage::kHalf) {
+        const size_t len = std::min(PinnedStage::kHalf, bytes - off);
+        const int hb = next;
+        next ^= 1;
+        if (!drain(hb)) return false;
+        if (cudaMemcpyAsync(st.buf + hb * PinnedStage::kHalf, from + off, len,
+                            cudaMemcpyDeviceToHost, st.s) != cudaSuccess ||
+            cudaEventRecord(st.ev[hb], st.s) != cudaSuccess)
+            return false;
+        pend[hb] = true;
+        pend_off[hb] = off;
+        pend_len[hb] = len;
+    }
+    return drain(next) && drain(next ^ 1);  // the older half first
+}
+
 // ====================================================================== C ABI
 
 extern "C" {
@@ -2710,9 +2791,8 @@ int louvain_result_labels(const louvain_result *r, int level, const int32_t **la
     std::vector<int32_t> &hl = r->host_labels[level];
     if (hl.size() != (size_t)r->n0) {
         hl.resize(r->n0);
-        if (cudaSetDevice(r->device) != cudaSuccess ||
-            cudaMemcpy(hl.data(), r->levels[level].d_labels, sizeof(int32_t) * (size_t)r->n0,
-                       cudaMemcpyDeviceToHost) != cudaSuccess) {
+        if (!copy_d2h_staged(r->device, hl.data(), r->levels[level].d_labels,
+                             sizeof(int32_t) * (size_t)r->n0)) {
             cudaGetLastError();
             hl.clear();
             return LOUVAIN_ERR_CUDA;
@@ -2720,6 +2800,19 @@ int louvain_result_labels(const louvain_result *r, int level, const int32_t **la
     }
     *labels = hl.data();
     if (ncomm) *ncomm = r->levels[level].ncomm;
+    return LOUVAIN_OK;
+}
+
+int louvain_result_labels_into(const louvain_result *r, int level, int32_t *dst)
+{
+    if (!r || level < 0 || level >= (int)r->levels.size() || (!dst && r->n0 > 0))
+        return LOUVAIN_ERR_INVALID_ARG;
+    if (r->n0 == 0) return LOUVAIN_OK;
+    if (!copy_d2h_staged(r->device, dst, r->levels[level].d_labels,
+                         sizeof(int32_t) * (size_t)r->n0)) {
+        cudaGetLastError();
+        return LOUVAIN_ERR_CUDA;
+    }
     return LOUVAIN_OK;
 }
 

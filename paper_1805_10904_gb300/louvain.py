@@ -108,6 +108,7 @@ def load():
     lib.louvain_result_num_vertices.restype = i64
     lib.louvain_result_labels.argtypes = [P, ctypes.c_int, ctypes.POINTER(P), P]
     lib.louvain_result_labels_device.argtypes = [P, ctypes.c_int, ctypes.POINTER(P)]
+    lib.louvain_result_labels_into.argtypes = [P, ctypes.c_int, P]
     lib.louvain_result_modularity.argtypes = [P, ctypes.c_int, P, P, P, P]
     lib.louvain_result_level_info.argtypes = [P, ctypes.c_int, P, P, P, P, P]
     lib.louvain_result_trace.argtypes = [P, P, P, P, P, P]
@@ -188,13 +189,13 @@ class Result:
         return self._lib.louvain_result_num_vertices(self._p)
 
     def labels(self, level: int) -> np.ndarray:
-        p = ctypes.c_void_p()
-        rc = self._lib.louvain_result_labels(self._p, level, ctypes.byref(p), None)
+        """Labels of the input vertices after `level`, copied into a new array."""
+        out = np.empty(self.n, np.int32)
+        rc = self._lib.louvain_result_labels_into(self._p, level,
+                                                  out.ctypes.data if self.n else None)
         if rc != OK:
-            raise LouvainError(rc, "louvain_result_labels")
-        n = self.n
-        return np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ctypes.c_int32)),
-                                     shape=(n,)).copy() if n else np.zeros(0, np.int32)
+            raise LouvainError(rc, "louvain_result_labels_into")
+        return out
 
     def labels_device_ptr(self, level: int) -> int:
         p = ctypes.c_void_p()
