@@ -54,7 +54,6 @@ constexpr BinSpec kBinSpec[kNumBins] = {
     {BIN_CHUNKED, 512, 1},   // 10: CTA chunks merged in a global-memory table
 };
 constexpr int kChunkedBin = kNumBins - 1;
-constexpr int kHugeSlice = 4096;  // candidate-list entries per CTA when deciding a long row
 // Partitioned aggregation of rows spanning several chunks (table sweeps): a row's distinct
 // keys are split by hash over P = 2^plog2 partitions, P the smallest power of two that keeps
 // the expected keys per partition at or below the configured part_keys (default kPartKeys,

@@ -92,6 +92,8 @@ def test_null_handle_calls_are_safe(lib):
     assert lib.louvain_serve_close(None) == 1
     assert lib.louvain_csr_from_edges(None, 0, 0, None, None, None, 0, None, None, None, None,
                                       None) == 1
+    assert lib.louvain_result_labels_into(None, 0, None) == 1
+    assert lib.louvain_result_bin_stats(None, 0, None, None, None, None, None) == 1
 
 
 def test_stack_graphs_builds_block_diagonal_csr():
