@@ -2013,6 +2013,32 @@ PinnedStage &pinned_stage()
     return st;
 }
 
+// Host copy of one staged chunk, split over a few threads: the destination is usually fresh
+// pageable memory whose first touch (page faults) dominates a single-threaded copy.
+void parallel_memcpy(char *to, const char *from, size_t len)
+{
+    constexpr size_t kMinPart = (size_t)1 << 20;
+    constexpr int kMaxThreads = 4;
+    int parts = (int)std::min<size_t>(kMaxThreads, std::max<size_t>(1, len / kMinPart));
+    if (parts <= 1) {
+        memcpy(to, from, len);
+        return;
+    }
+    const size_t step = (len + parts - 1) / parts;
+    std::vector<std::thread> workers;
+    for (int t = 1; t < parts; t++) {
+        const size_t b = (size_t)t * step, e = std::min(len, b + step);
+        if (b >= e) continue;
+        try {
+            workers.emplace_back([=] { memcpy(to + b, from + b, e - b); });
+        } catch (...) {  // no thread to spare: copy this part here
+            memcpy(to + b, from + b, e - b);
+        }
+    }
+    memcpy(to, from, std::min(len, step));
+    for (auto &w : workers) w.join();
+}
+
 bool copy_d2h_staged(int device, void *dst, const void *src, size_t bytes)
 {
     PinnedStage &st = pinned_stage();
@@ -2026,7 +2052,7 @@ bool copy_d2h_staged(int device, void *dst, const void *src, size_t bytes)
     auto drain = [&](int hb) {
         if (!pend[hb]) return true;
         if (cudaEventSynchronize(st.ev[hb]) != cudaSuccess) return false;
-        memcpy(to + pend_off[hb], st.buf + hb * PinnedStage::kHalf, pend_len[hb]);
+        parallel_memcpy(to + pend_off[hb], st.buf + hb * PinnedStage::kHalf, pend_len[hb]);
         pend[hb] = false;
         return true;
     };
