@@ -21,8 +21,11 @@
 //   bin 6-9  a thread-block cluster of 2-16 CTAs per row; the table is partitioned over the
 //            cluster's distributed shared memory by key hash (inserts are DSMEM atomics),
 //            each CTA scans its own part, and rank 0 combines the partial argmaxes,
-//   bin 10   CTA-sized chunks of a row; a row spanning several chunks merges its chunk
-//            tables into a global-memory table and the last chunk to finish decides.
+//   bin 10   CTA-sized chunks of a row, each aggregated in shared memory; a row spanning
+//            several chunks has its chunks' distinct (community, weight) pairs grouped by a
+//            hash partition, every partition merged in shared memory by a work item of its
+//            own, and the partial argmaxes combined by the item finishing the row last.
+// The first sweep of a phase (FIRST) scores entries without tables (see below).
 // Table values are 32-bit when 2W < 2^32 (every e_{i->c} <= delta_i <= 2W fits), else 64-bit.
 #pragma once
 #include <algorithm>
