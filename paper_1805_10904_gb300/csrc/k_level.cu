@@ -597,8 +597,9 @@ int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg 
     return 1;
 }
 
-// Chunked rows: chunk counts and, for multi-chunk rows, a global table of 2^k >= 2*min(d, n)
-// slots (distinct neighbour labels <= min(d, n) < slots, so it never fills).
+// Chunked rows: chunk counts and, for multi-chunk rows, the number of hash partitions of the
+// row's keys (a power of two keeping the expected distinct keys per partition, at most
+// min(d, n) in all, at or below part_keys; 2^kMaxPartLog2 at most).
 __global__ void k_big_prep(int nb, const int32_t *bverts, const int64_t *rp, int64_t n, int chunk,
                            int part_keys, int32_t *nch, int32_t *plog2)
 {

@@ -1394,7 +1394,8 @@ static int launch_huge_first(const MoveArgs<WT> &A, const Bins &b, cudaStream_t 
     return 1;
 }
 
-// Bin 10: chunk tables, then the slice-parallel decision for rows spanning several chunks.
+// Bin 10: chunk tables, then the per-partition merge and decision of rows spanning several
+// chunks.
 template <typename WT, typename GT, typename VT, bool BT>
 static int launch_huge(const MoveArgs<WT> &A, const Bins &b, cudaStream_t bs, const LaunchCfg &lc)
 {
