@@ -2043,6 +2043,20 @@ bool copy_d2h_staged(int device, void *dst, const void *src, size_t bytes)
 {
     PinnedStage &st = pinned_stage();
     std::lock_guard<std::mutex> lock(st.mu);
+    struct KeepDevice {  // the caller's current device is restored on return
+        int prev = -1;
+        KeepDevice()
+        {
+            if (cudaGetDevice(&prev) != cudaSuccess) {
+                cudaGetLastError();
+                prev = -1;
+            }
+        }
+        ~KeepDevice()
+        {
+            if (prev >= 0) cudaSetDevice(prev);
+        }
+    } keep;
     if (cudaSetDevice(device) != cudaSuccess || !st.ready(device)) return false;
     const char *from = (const char *)src;
     char *to = (char *)dst;
