@@ -49,3 +49,23 @@ def test_single_rank_is_identity():
     import bench
     assert bench.reduce_max(3.5, 1) == 3.5
     assert bench.reduce_sum(2.0, 1) == 2.0
+
+
+def test_roofline_traffic_only_for_the_captured_kernel_and_bins():
+    """bench.py reports the committed DRAM-traffic figure only while the kernel source and
+    the bin layout match the capture; anything else gives None (no stale number)."""
+    import json
+    import bench
+    with open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")) as f:
+        rec = json.load(f)["kernels"]["k_move_cta<1024>"]
+    import hashlib
+    src = os.path.join(os.path.dirname(bench.__file__), "paper_1805_10904_gb300", "csrc",
+                       "k_move_impl.cuh")
+    with open(src, "rb") as f:
+        same_source = hashlib.sha256(f.read()).hexdigest() == rec["source_sha256"]
+    bins, chunk = rec["bins"], rec["chunk_entries"]
+    expected = rec["dram_bytes_per_launch_full"] if same_source else None
+    assert bench.kernel_traffic("k_move_cta<1024>", bins, chunk) == expected
+    assert bench.kernel_traffic("k_move_cta<1024>", bins[:-1] + [bins[-1] // 2], chunk) is None
+    assert bench.kernel_traffic("k_move_cta<1024>", bins, chunk // 2) is None
+    assert bench.kernel_traffic("k_move_cta<256>", bins, chunk) is None
