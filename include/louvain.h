@@ -79,7 +79,9 @@ typedef struct {
      *   d <= 2/4/8/16 * bin_cta3 -> a thread-block cluster of 2/4/8/16 such CTAs per
      *                     vertex, the table spread over the cluster's shared memory
      *                     (sizes the device cannot host are skipped)
-     *   larger         -> CTA chunks of chunk_entries entries merged in a global table.
+     *   larger         -> CTA chunks of chunk_entries entries, merged by hash partition
+     *                     of the neighbouring communities (graph induction: one global
+     *                     table per long community).
      * Thresholds must not decrease.  All zero selects the defaults 8, 32, 128, 512, 2048,
      * 12288.  The same thresholds bin the communities (by entries) when coarsening. */
     int32_t bin_small;
