@@ -4,13 +4,15 @@
 // whose GPU memory is entirely reserved up front by another framework's allocator, or code
 // that must not trigger the device-wide synchronisation that cudaMalloc / cudaFree imply.
 // Everything this entry point needs beyond the caller's inputs lives in one file-scope
-// device array, reserved when the library is loaded and held until the process exits on
-// every GPU that loads the library.
+// device array.  CUDA loads a library's GPU code lazily by default, so the array is reserved
+// on a device when this file's code is first used there -- by the first call on that
+// device -- and is held until the process exits.
 //
 // The computation is the library's exact modularity (Eq. 3 of the method, kept as the
 // integer Qn = (2W)^2 * Q): per vertex the weighted degree and the weight of its entries
 // whose column shares its label, per community the sum of its members' degrees, then
 // Qn = 2W * sum_i e_{i->C(i)} - sum_c deg_c^2.
+#include <atomic>
 #include <cstring>
 
 #include "../../include/louvain.h"
@@ -25,7 +27,13 @@ constexpr int64_t kAccWords = 8;
 static __device__ __align__(256) u64 g_noalloc_scratch[LOUVAIN_NOALLOC_MAX_VERTICES + kAccWords];
 
 constexpr int kMaxDevices = 64;
-static u64 *g_scratch_ptr[kMaxDevices];  // device address of g_noalloc_scratch per device
+// device address of g_noalloc_scratch per device; host threads may race on the first
+// lookup, and every one of them stores the same address
+static std::atomic<u64 *> g_scratch_ptr[kMaxDevices];
+
+// Sums of weights build up in 64-bit words: with weights below 2^31, fewer than 2^33
+// entries cannot wrap them, and larger sums than 2^62 are rejected after the sum.
+constexpr int64_t kMaxEntries = (int64_t)1 << 33;
 
 __global__ void k_na_clear(u64 *scratch, int64_t n)
 {
@@ -111,6 +119,8 @@ extern "C" int louvain_modularity_noalloc(int64_t n, const int64_t *row_ptr,
 {
     if (n < 0 || (n > 0 && (!row_ptr || !labels))) return LOUVAIN_ERR_INVALID_ARG;
     if (n > LOUVAIN_NOALLOC_MAX_VERTICES) return LOUVAIN_ERR_TOO_LARGE;
+    // an error the caller's earlier work left pending is theirs: report it, do not clear it
+    if (cudaPeekAtLastError() != cudaSuccess) return LOUVAIN_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
@@ -118,15 +128,16 @@ extern "C" int louvain_modularity_noalloc(int64_t n, const int64_t *row_ptr,
     }
     // first call on this device: look up the array's device address (host code cannot use
     // the symbol itself as a pointer)
-    if (!g_scratch_ptr[dev]) {
+    u64 *deg = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!deg) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return LOUVAIN_ERR_CUDA;
         }
-        g_scratch_ptr[dev] = (u64 *)p;
+        deg = (u64 *)p;
+        g_scratch_ptr[dev].store(deg, std::memory_order_release);
     }
-    u64 *deg = g_scratch_ptr[dev];
     u64 *acc = deg + LOUVAIN_NOALLOC_MAX_VERTICES;
     cudaStream_t s = (cudaStream_t)stream;
     const int grid = 152 * 4;
@@ -136,21 +147,19 @@ extern "C" int louvain_modularity_noalloc(int64_t n, const int64_t *row_ptr,
     if (n > 0) {
         k_na_rowptr<<<grid, kBlock, 0, s>>>(row_ptr, n, acc);
         u64 host_acc[kAccWords];
-        if (cudaMemcpyAsync(host_acc, acc, sizeof(host_acc), cudaMemcpyDeviceToHost, s) !=
+        int64_t nnz = 0;
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(host_acc, acc, sizeof(host_acc), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(nnz), cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             cudaGetLastError();
             return LOUVAIN_ERR_CUDA;
         }
         if (host_acc[4]) return LOUVAIN_ERR_INDEX_RANGE;  // row offsets unusable: stop here
-        if (!col_idx) {
-            int64_t nnz = 0;
-            if (cudaMemcpy(&nnz, row_ptr + n, sizeof(nnz), cudaMemcpyDeviceToHost) != cudaSuccess) {
-                cudaGetLastError();
-                return LOUVAIN_ERR_CUDA;
-            }
-            if (nnz > 0) return LOUVAIN_ERR_INVALID_ARG;
-        }
+        if (!col_idx && nnz > 0) return LOUVAIN_ERR_INVALID_ARG;
+        if (weights && nnz >= kMaxEntries) return LOUVAIN_ERR_TOO_LARGE;
         k_na_rows<<<grid, kBlock, 0, s>>>(n, row_ptr, col_idx, weights, labels, deg, acc);
         k_na_squares<<<grid, kBlock, 0, s>>>(n, deg, acc);
     }

@@ -4,8 +4,10 @@ or code that must avoid the synchronisation of cudaMalloc/cudaFree).
 
 The entry point is called through the C ABI twice in a row on the same device; both calls
 must reproduce, exactly, the modularity that louvain_run reports for each recorded level
-(so the second call proves the shared scratch array is cleared between calls).  Kept in a
-file of its own, collected last.
+(so the second call proves the shared scratch array is cleared between calls), and the
+oracle's Eq. 3 on random partitions that leave labels unused, with and without weights.
+A call after the first one on a device must leave the device's free memory unchanged.
+Kept in a file of its own, collected last.
 """
 import ctypes
 
@@ -13,6 +15,7 @@ import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -94,3 +97,51 @@ def test_noalloc_singletons_and_limits():
     rc = f(4194305, rp.data_ptr(), col.data_ptr(), w.data_ptr(), singletons.data_ptr(),
            None, None, None, None)
     assert rc == 12
+
+
+@pytest.mark.parametrize("weighted", [True, False])
+def test_noalloc_matches_oracle_on_random_partitions(weighted):
+    """Random labels drawn from [0, n) leave many labels unused; NULL weights mean 1."""
+    torch = pytest.importorskip("torch")
+    import paper_1805_10904_gb300 as lv
+    f = _noalloc(lv.load())
+    g = gg.rmat(12, 16, seed=7)
+    dev = torch.device("cuda:0")
+    rp = torch.from_numpy(g.rp).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    w = torch.from_numpy(g.w).to(dev) if weighted else None
+    rng = np.random.default_rng(11)
+    for ncomm in (1, 7, 300, g.n):
+        labels = rng.integers(0, ncomm, size=g.n).astype(np.int32)
+        # spread the used labels over [0, n) so that most labels stay unused
+        labels = (labels * (g.n // ncomm)).astype(np.int32)
+        ref_qn, ref_tw = oracle.modularity(g.rp, g.col, g.w if weighted else None, labels)
+        d_labels = torch.from_numpy(labels).to(dev)
+        for _ in range(2):
+            rc, qn, tw, q = _call(f, torch, g.n, rp, col, w, d_labels)
+            assert rc == 0
+            assert qn == ref_qn and tw == ref_tw
+            ref_q = float(ref_qn) / float(ref_tw * ref_tw)
+            assert abs(q - ref_q) <= Q_RTOL * max(1.0, abs(ref_q))
+
+
+def test_noalloc_later_calls_allocate_nothing():
+    torch = pytest.importorskip("torch")
+    import paper_1805_10904_gb300 as lv
+    f = _noalloc(lv.load())
+    g = gg.sbm(2048, 64, 0.2, 0.005, 1, 4, seed=3)
+    dev = torch.device("cuda:0")
+    rp = torch.from_numpy(g.rp).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    w = torch.from_numpy(g.w).to(dev)
+    labels = torch.from_numpy((np.arange(g.n) // 64).astype(np.int32)).to(dev)
+    rc, first, _, _ = _call(f, torch, g.n, rp, col, w, labels)  # the set-up call
+    assert rc == 0
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info(dev)
+    for _ in range(2):
+        rc, qn, _, _ = _call(f, torch, g.n, rp, col, w, labels)
+        assert rc == 0 and qn == first
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info(dev)
+    assert free_after == free_before
