@@ -41,7 +41,7 @@ extern "C" {
 #define LOUVAIN_ERR_INDEX_RANGE 5  /* row_ptr not monotone from 0, or a column outside [0,n) */
 #define LOUVAIN_ERR_OOM 6          /* device or host allocation failed                      */
 #define LOUVAIN_ERR_CUDA 7         /* a CUDA runtime call failed (message has the CUDA text) */
-#define LOUVAIN_ERR_TIMEOUT 8      /* a bounded device wait gave up                          */
+#define LOUVAIN_ERR_TIMEOUT 8      /* reserved: no call returns it (no device wait spins)    */
 #define LOUVAIN_ERR_INTERNAL 9     /* a device-side consistency check failed                */
 #define LOUVAIN_PENDING 10         /* serving: the ticket has not finished                   */
 #define LOUVAIN_ERR_REJECTED 11    /* serving: request larger than the memory budget         */
@@ -67,8 +67,12 @@ typedef struct {
     int32_t vf_all_levels;     /* 1: also before every later level; default 0            */
     int32_t checks;            /* 1 (default): index and weight checks; 2: also symmetry,
                                   sortedness and duplicates; 0 is treated as 1             */
-    int32_t force_int128;      /* 1: take the int128 gain path even when int64 suffices  */
-    int32_t wide_sums;         /* 1: 64-bit hash-table sums even when 2W < 2^32 allows 32 */
+    /* Widths, chosen per level from its largest weighted degree d_max and 2W: sweep gains
+     * are int64 when d_max * 2W <= 2^62 (|gain of i| <= 2W * delta_i), else int128; sweep
+     * table sums are 32-bit when d_max < 2^32 (e_{i->c} <= delta_i), induction sums when
+     * 2W < 2^32 (a community's sum <= 2W); all exact.  The flags force the wide forms. */
+    int32_t force_int128;      /* 1: int128 gains even when int64 is exact               */
+    int32_t wide_sums;         /* 1: 64-bit table sums even when 32 bits are exact        */
     /* degree-bin thresholds on the row length d (entries stored in the row):
      *   d <= bin_small -> one thread per vertex            (0 <= bin_small <= 8)
      *   d <= bin_mid1  -> 8 lanes per vertex               (bin_mid1 <= 32)
@@ -369,6 +373,23 @@ int louvain_result_bin_stats(const louvain_result *r, int bin, double *time_ms,
                              int64_t *launches, int64_t *alg_bytes, int64_t *rows,
                              int64_t *entries);
 
+/* Graph induction (Sec. 5.1.2 "Inducing new graph": the coarse graph of the communities,
+ * A'_ab = sum of A_uv over C(u) = a, C(v) = b) summed over the run's levels:
+ *   *inductions  coarse graphs built
+ *   *alg_bytes   algorithmic bytes: per induction
+ *                nnz * (4 column + s_w weight + 4 label of the target)
+ *                + n * (8 row offset + 4 label of the member)
+ *                + nnz' * (4 column + s_w' weight) + (n' + 1) * 8 new row offsets,
+ *                for a fine graph of n vertices and nnz entries (s_w = 4 or 8) and a coarse
+ *                graph of n' vertices and nnz' entries (s_w' = 4 when 2W < 2^31, else 8);
+ *                the library's own temporaries are not counted.  In a batch these are the
+ *                totals of every level step the graph took part in.
+ *   *time_ms     device time from the first to the last induction kernel (profile = 1
+ *                only, else 0)
+ * Any out pointer may be NULL.  Errors: INVALID_ARG (r NULL). */
+int louvain_result_coarsen_stats(const louvain_result *r, int64_t *inductions,
+                                 int64_t *alg_bytes, double *time_ms);
+
 /* How the result's level steps ran: info[0] sweeps run inside CUDA graphs (device-side
  * loop, cuda_graphs = 1), [1] sweeps run with one host round trip each (with cuda_graphs = 1
  * only the table-free first sweeps, see louvain_result_bin_stats), [2] engine level
@@ -390,7 +411,7 @@ void louvain_result_free(louvain_result *r);
  * partition, like louvain_result_modularity reports it for the levels of a run, without
  * allocating anything: its scratch (one degree per community plus a few accumulators) is a
  * static device array of LOUVAIN_NOALLOC_MAX_VERTICES + 8 64-bit words (32 MiB + 64 bytes),
- * reserved on every GPU that loads the library and held until the process exits.
+ * reserved on a GPU by the first call there (see below) and held until the process exits.
  *   n         vertices, 0 <= n <= LOUVAIN_NOALLOC_MAX_VERTICES, else LOUVAIN_ERR_TOO_LARGE
  *             (checked before any device work)
  *   row_ptr, col_idx, weights
@@ -399,11 +420,18 @@ void louvain_result_free(louvain_result *r);
  *   stream    stream the work is ordered on; the call returns after it completes
  *   qn, tw, q host outputs: Qn = (2W)^2 Q as int128 limbs {high, low}, 2W, and
  *             Q = (double)Qn / (double)(2W)^2 (0 when 2W = 0); any may be NULL
- * Errors: INVALID_ARG, TOO_LARGE, INDEX_RANGE (row offsets, a column or a label out of
- * range), BAD_WEIGHT, CUDA.  The first call on each device looks up the array's device
- * address with cudaGetSymbolAddress (the current device must be the one the graph lives
- * on); make that first call before any stream capture.  Every call on a device uses the same
- * array and clears the part it needs at its start, so calls whose GPU work overlaps (on
+ * Errors: INVALID_ARG, TOO_LARGE (also 2^33 or more weighted entries, whose 64-bit sums
+ * could wrap), INDEX_RANGE (row offsets, a column or a label out of range), BAD_WEIGHT,
+ * CUDA (also when an error of the caller's earlier work is still pending on entry; it is
+ * left pending).
+ * First call on each device: it is the set-up.  CUDA loads this library's GPU code lazily,
+ * so that call loads the code that holds the array -- which reserves the array's 32 MiB on
+ * the device -- and looks up the array's device address with cudaGetSymbolAddress (the
+ * current device must be the one the graph lives on).  A caller that reserves all of its
+ * device memory up front must make this first call before doing so, and the first call
+ * should come before any stream capture; every later call allocates nothing.  The call
+ * synchronises its stream before it returns.  Every call on a device uses the same array
+ * and clears the part it needs at its start, so calls whose GPU work overlaps (on
  * different streams or from different host threads) race and give wrong results. */
 #define LOUVAIN_NOALLOC_MAX_VERTICES 4194304
 int louvain_modularity_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,

@@ -140,6 +140,7 @@ struct Scalars {
     unsigned err;
     int32_t ndone;  // phase controllers that have stopped
     u64 tw;
+    u64 dmax;       // largest weighted degree of the level's graph
     SweepStats st;
     LevelCtl ctl;
     int32_t bin_counts[40];
@@ -242,6 +243,8 @@ struct louvain_result {
     // graph sweeps, host-loop sweeps, steps, captures, autotuning trials, tuned-bins cache hit
     int64_t exec_info[6] = {0, 0, 0, 0, 0, 0};
     double acc_alg_bytes = 0.0, acc_coarsen_ms = 0.0, acc_step_ms = 0.0;
+    double acc_coarsen_bytes = 0.0;  // algorithmic bytes of the graph inductions
+    int64_t acc_inductions = 0;
     int64_t tw = 0;
     int device = 0;
     std::vector<LevelRec> levels;
@@ -922,10 +925,16 @@ void Engine::step(std::vector<Member *> &retired)
         if ((u64)h_tw[m] > tw_max) tw_max = (u64)h_tw[m];
     }
     if (batch) upload(d_tw, (const u64 *)h_tw.data(), M);
-    // gains in int128 when some graph's (2W)^2 leaves int64; 32-bit table sums when every
-    // graph's 2W fits (a table sum never exceeds its graph's 2W)
-    const bool wide = cfg.force_int128 || (u128)tw_max * tw_max > (u128)INT64_MAX;
-    const bool narrow = !cfg.wide_sums && tw_max < ((u64)1 << 32);
+    // Exact widths of the level's sweeps from its largest weighted degree: a table sum
+    // e_{i->c} never exceeds delta_i, so 32-bit sums are exact when every delta_i < 2^32;
+    // a gain of vertex i is at most 2W * delta_i in magnitude (both of its products are),
+    // so int64 gains are exact when max delta * 2W <= 2^62, else int128.  The induction's
+    // sums reach a community's degree, up to 2W: its width follows 2W.
+    kernels += launch_max_delta(delta.p, n, &d_sc->dmax, s, lc);
+    const u64 dmax = read_one(&d_sc->dmax);
+    const bool wide = cfg.force_int128 || (u128)dmax * tw_max > ((u128)1 << 62);
+    const bool narrow = !cfg.wide_sums && dmax < ((u64)1 << 32);
+    const bool narrow_c = !cfg.wide_sums && tw_max < ((u64)1 << 32);
     const i64 TW = h_tw[0];  // one graph: its 2W (a batch reads 2W per graph on the device)
 
     PhaseState st;
@@ -1157,7 +1166,7 @@ void Engine::step(std::vector<Member *> &retired)
     // finished: no new level), then the outer test of Algorithm 2
     std::vector<int32_t> rec(M, 0), keep(M, 0);
     int nrec = 0, nkeep = 0;
-    int64_t k_next = 0, n_keep = 0, n0_all = 0;
+    int64_t k_next = 0, n_keep = 0, nnz_keep = 0, n0_all = 0;
     bool all_kept = true;
     for (int m = 0; m < M; m++) {
         Member *mb = mem[m];
@@ -1191,6 +1200,7 @@ void Engine::step(std::vector<Member *> &retired)
             nkeep++;
             k_next += kg;
             n_keep += mb->nv;
+            nnz_keep += mb->nnz;
         }
     }
     // labels of the input vertices of every recorded graph (one array for this step, shared
@@ -1229,7 +1239,7 @@ void Engine::step(std::vector<Member *> &retired)
 
     proc.phase("induce");
     // ---------------- induce the next graph of the kept graphs (Sec. 5.1.2)
-    double t_coarsen = 0.0;
+    double t_coarsen = 0.0, coarsen_bytes = 0.0;
     std::vector<int64_t> gptr_next(M + 1, 0), gnnz_next(M + 1, 0);
     if (nkeep > 0) {
         ensure(c_csize, n);
@@ -1255,7 +1265,7 @@ void Engine::step(std::vector<Member *> &retired)
         cb.scratch32 = scratch32.p;
         cb.scratch64 = scratch64.p;
         if (tm.on) CK(cudaEventRecord(coarsen_ev[0], s));
-        Bins cbins = proto;
+        Bins cbins = narrow_c == narrow ? proto : make_proto(narrow_c);  // table widths of the induction
         cbins.nch = b_nch.p;
         cbins.chunk_first = b_chunk_first.p;
         cbins.gloop = b_gloop.p;
@@ -1280,7 +1290,7 @@ void Engine::step(std::vector<Member *> &retired)
         }
         kernels += launch_coarsen_binfill(k, cb, cbins, s, lc);
         prep_huge(cbins, true, k, &cb);
-        kernels += launch_coarsen_stage2(G, st, nid2, k, cb, cbins, narrow, &d_sc->err, s, lc);
+        kernels += launch_coarsen_stage2(G, st, nid2, k, cb, cbins, narrow_c, &d_sc->err, s, lc);
         DBuf<int64_t> rp_next;
         rp_next.reset(&A, (size_t)k + 1);
         kernels += launch_coarsen_rowptr(k, cb, rp_next.p, s);
@@ -1292,7 +1302,10 @@ void Engine::step(std::vector<Member *> &retired)
         col_next.reset(&A, (size_t)nnz_next);
         w_next.reset(&A, (size_t)nnz_next * wb_next);
         kernels += launch_coarsen_compact(k, nnz_next, cb, rp_next.p, col_next.p, w_next.p,
-                                          wb_next, narrow, s, lc);
+                                          wb_next, narrow_c, s, lc);
+        // algorithmic bytes of the induction (louvain_result_coarsen_stats)
+        coarsen_bytes = (double)nnz_keep * (4 + G.wbytes + 4) + (double)n_keep * (8 + 4) +
+                        (double)nnz_next * (4 + wb_next) + (double)(k + 1) * 8;
         if (tm.on) {
             CK(cudaEventRecord(coarsen_ev[1], s));
             CK(cudaEventSynchronize(coarsen_ev[1]));
@@ -1369,6 +1382,8 @@ void Engine::step(std::vector<Member *> &retired)
         r->acc_cand += (int64_t)cand_all;
         r->acc_kernels += step_kernels;
         r->acc_coarsen_ms += t_coarsen;
+        r->acc_coarsen_bytes += coarsen_bytes;
+        r->acc_inductions += nkeep > 0;
         r->acc_step_ms += wall;
         r->exec_info[0] += graph_sweeps;
         r->exec_info[1] += sweeps - graph_sweeps;
@@ -2936,6 +2951,16 @@ int louvain_result_bin_stats(const louvain_result *r, int bin, double *time_ms,
     if (alg_bytes) *alg_bytes = (int64_t)r->bin_bytes[bin];
     if (rows) *rows = r->bin_rows[bin];
     if (entries) *entries = r->bin_entries[bin];
+    return LOUVAIN_OK;
+}
+
+int louvain_result_coarsen_stats(const louvain_result *r, int64_t *inductions,
+                                 int64_t *alg_bytes, double *time_ms)
+{
+    if (!r) return LOUVAIN_ERR_INVALID_ARG;
+    if (inductions) *inductions = r->acc_inductions;
+    if (alg_bytes) *alg_bytes = (int64_t)r->acc_coarsen_bytes;
+    if (time_ms) *time_ms = r->acc_coarsen_ms;
     return LOUVAIN_OK;
 }
 

@@ -85,6 +85,28 @@ int launch_fill_ones(int32_t *w, int64_t nnz, cudaStream_t s, const LaunchCfg &l
     return 1;
 }
 
+// Largest weighted degree of the level: every table sum e_{i->c} of a sweep is at most
+// delta_i, and every gain of vertex i is at most 2W * delta_i in magnitude, so this bound
+// picks the narrowest exact sum and gain widths of the level's sweeps.
+__global__ void __launch_bounds__(kBlock) k_max_delta(const i64 *delta, int64_t n, u64 *out)
+{
+    u64 m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (u64)delta[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax((unsigned long long *)out, (unsigned long long)m);
+}
+
+int launch_max_delta(const i64 *delta, int64_t n, u64 *out, cudaStream_t s, const LaunchCfg &lc)
+{
+    cudaMemsetAsync(out, 0, sizeof(u64), s);
+    if (n == 0) return 0;
+    k_max_delta<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(delta, n, out);
+    return 1;
+}
+
 // delta_i = sum of row i's weights (loop once), 2W = sum delta; columns and weights are
 // checked on the way.  Rows of bin 0 take one thread each (dense kernel), rows of bins 1-4
 // one warp each, longer rows one CTA each, so a hub row never serialises on one warp.

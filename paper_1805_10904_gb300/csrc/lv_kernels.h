@@ -158,6 +158,8 @@ size_t shared_table_bytes(int log2cap, bool narrow);
 int launch_validate_rowptr(const int64_t *rp, int64_t n, unsigned *err, cudaStream_t s,
                            const LaunchCfg &lc);
 int launch_fill_ones(int32_t *w, int64_t nnz, cudaStream_t s, const LaunchCfg &lc);
+// *out = max_i delta[i] over n vertices (0 when n = 0)
+int launch_max_delta(const i64 *delta, int64_t n, u64 *out, cudaStream_t s, const LaunchCfg &lc);
 // Columns in [0, n) and weights >= 1 of one graph (w NULL: all 1), *tw += its 2W.
 int launch_check_rows(int64_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
                       unsigned *err, u64 *tw, cudaStream_t s, const LaunchCfg &lc);

@@ -122,6 +122,7 @@ def load():
     lib.louvain_resume.argtypes = [P, i32, P, i64, P, P, P, i32, ctypes.c_int, P,
                                    ctypes.POINTER(P)]
     lib.louvain_result_bin_stats.argtypes = [P, ctypes.c_int, P, P, P, P, P]
+    lib.louvain_result_coarsen_stats.argtypes = [P, P, P, P]
     lib.louvain_result_free.argtypes = [P]
     lib.louvain_result_free.restype = None
     _lib = lib
@@ -280,6 +281,16 @@ class Result:
         if rc != OK:
             raise LouvainError(rc, "louvain_result_coarse_copy")
         return rp, col[:nnz.value], w[:nnz.value]
+
+    def coarsen_stats(self):
+        """(coarse graphs built, their algorithmic bytes, induction device ms (profile
+        runs only)) -- louvain_result_coarsen_stats."""
+        k, b, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        rc = self._lib.louvain_result_coarsen_stats(self._p, ctypes.addressof(k),
+                                                    ctypes.addressof(b), ctypes.addressof(t))
+        if rc != OK:
+            raise LouvainError(rc, "louvain_result_coarsen_stats")
+        return k.value, b.value, t.value
 
     def exec_info(self):
         """(sweeps in CUDA graphs, host-loop sweeps, level steps, graph captures, autotuning

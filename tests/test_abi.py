@@ -83,6 +83,7 @@ def test_null_handle_calls_are_safe(lib):
     lib.louvain_destroy(None)
     lib.louvain_result_free(None)
     assert lib.louvain_result_num_levels(None) == 0
+    assert lib.louvain_result_coarsen_stats(None, None, None, None) == 1
     assert lib.louvain_run(None, 0, None, None, None, 0, None, None) == 1
     assert lib.louvain_run_batch(None, 1, None, None, None, None, None, 0, None, None) == 1
     assert lib.louvain_serve_open(None, ctypes.c_uint64(1), 1) == 1

@@ -298,3 +298,28 @@ def test_post_merge_mode(torch, lv, kw, kind):
         g = gg.from_edges(3, [(0, 1, 1), (1, 2, 1)])
     res, ref = run_both(torch, lv, g, post_merge=True, **kw)
     assert_parity(res, ref)
+
+
+# Heavy weights put 2W far above 2^32 while every weighted degree stays small or large:
+# the level's widths follow its largest weighted degree d_max (32-bit table sums when
+# d_max < 2^32, int64 gains when d_max * 2W <= 2^62), so these graphs run the width
+# combinations that 2W alone would never pick.
+HEAVY = [
+    # (weights, expected: d_max < 2^32, d_max * 2W <= 2^62)
+    ((1 << 16, 1 << 20), (True, True)),        # 2W ~ 2^35: int64 gains, 32-bit sums
+    ((1 << 25, 1 << 26), (True, False)),       # int128 gains, 32-bit sums
+    ((1 << 29, (1 << 31) - 1), (False, False)),  # int128 gains, 64-bit sums
+]
+
+
+@pytest.mark.parametrize("weights,expect", HEAVY)
+@pytest.mark.parametrize("cfg", [{}, {"bins": (1, 2, 3, 4, 5, 6), "chunk_entries": 32}])
+def test_heavy_weights_per_level_widths(torch, lv, weights, expect, cfg):
+    g = gg.sbm(4096, 128, 0.10, 0.002, weights[0], weights[1], seed=9)
+    rows = np.repeat(np.arange(g.n), np.diff(g.rp))
+    dmax = int(np.bincount(rows, weights=g.w.astype(np.float64)).max())
+    tw = int(g.w.astype(np.int64).sum())
+    assert tw > 2 ** 32
+    assert (dmax < 2 ** 32, dmax * tw <= 2 ** 62) == expect
+    res, ref = run_both(torch, lv, g, **cfg)
+    assert_parity(res, ref)
