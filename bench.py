@@ -1,9 +1,11 @@
-"""Benchmark: multi-level synchronous Louvain on an R-MAT scale-22 graph.
+"""Benchmark: multi-level synchronous Louvain on the largest single graph, R-MAT scale 26.
 
 One step = one full multi-level run (every local-moving sweep, renumbering and graph
 induction of every level) of the library on the same synthetic graph:
-R-MAT scale 22 (4,194,304 vertices, 16 * 2^22 sampled pairs, a=0.57 b=0.19 c=0.19),
-symmetrised, loops and duplicates dropped, int32 weights uniform in [1, 16], seed 22.
+R-MAT scale 26 (67,108,864 vertices, 16 * 2^26 sampled pairs, a=0.57 b=0.19 c=0.19),
+symmetrised, loops and duplicates dropped, int32 weights uniform in [1, 16], seed 26
+(2.1e9 stored entries; 2W above 2^32, so int128 gains and 64-bit table sums).
+`--scale 22` runs the R-MAT scale-22 graph instead.
 
 Metric: local-move edge-visits/s = sum over phases of (sweeps applied) * (stored
 entries of that phase's graph), divided by the device time of the run.
@@ -11,7 +13,8 @@ entries of that phase's graph), divided by the device time of the run.
 Prints one JSON line.  With torchrun (N > 1) every rank runs its own replica on its
 own GPU (no data-path collective; weak scaling) and rank 0 reports the max time.
 `--impl reference` times the CPU oracle (single thread) on a bounded sample of the
-same workload instead.
+same workload instead: the full multi-level run on the subgraph induced by one aligned
+block of vertices (rows and columns in [r0, r0 + 2^block_bits)).
 """
 from __future__ import annotations
 
@@ -55,9 +58,10 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["native", "reference"], default="native")
-    p.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 is the workload)")
+    p.add_argument("--scale", type=int, default=26, help="R-MAT scale (26 is the workload)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample-sweeps", type=int, default=2)
+    p.add_argument("--sample-bits", type=int, default=20,
+                   help="CPU sample: vertex block of 2^bits vertices (induced subgraph)")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer arm (profiling)")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the default degree bins instead of tuning them (profiling)")
@@ -66,13 +70,15 @@ def parse_args(argv=None):
                         "one graph at a time (0: skip)")
     p.add_argument("--batch-only", action="store_true",
                    help="time only the batch workload (its own JSON line)")
-    p.add_argument("--serve-requests", type=int, default=400,
+    p.add_argument("--serve-requests", type=int, default=2000,
                    help="also run the serving workload with this many requests (0: skip)")
     p.add_argument("--serve-only", action="store_true",
                    help="run only the serving workload (its own JSON line)")
     p.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
     p.add_argument("--no-edges", action="store_true",
                    help="skip timing the edge-list to CSR conversion")
+    p.add_argument("--edges-scale", type=int, default=22,
+                   help="R-MAT scale of the edge-list conversion leg")
     p.add_argument("--serve-budget-gb", type=float, default=120.0)
     p.add_argument("--serve-slots", type=int, default=256)
     return p.parse_args(argv)
@@ -216,6 +222,24 @@ def kernel_traffic(kernel_name: str, bins=None, chunk=None):
     return entry.get("dram_bytes_per_launch_full")
 
 
+def host_cpu():
+    """Host CPU model (from /proc/cpuinfo) and logical core count."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(),
+            "arch": platform.machine(), "logical_cores": os.cpu_count()}
+
+
 def make_graph(scale: int):
     import graphgen as gg
     return gg.rmat(scale, 16, 0.57, 0.19, 0.19, 1, 16, seed=scale)
@@ -223,14 +247,55 @@ def make_graph(scale: int):
 
 # ---------------------------------------------------------------- CPU oracle timing
 
-def time_oracle(g, sweeps: int):
-    """Single-threaded oracle on level 0 of the workload, `sweeps` sweeps."""
+def sample_block(scale: int, bits: int):
+    """First vertex of the CPU sample's block: the aligned block of 2^bits vertices whose
+    index is the top bit of the vertex id (vertices [2^(scale-1), 2^(scale-1) + 2^bits)),
+    a block of typical density (one R-MAT level in the (1,1) quadrant)."""
+    return 1 << (scale - 1) if bits < scale else 0
+
+
+def induced_block(g, r0: int, bits: int):
+    """Subgraph induced by vertices [r0, r0 + 2^bits) of g, renumbered from 0: the rows of
+    the block with the entries whose column lies in the block (symmetric, rows sorted)."""
+    import numpy as np
+    import graphgen as gg
+    r1 = min(g.n, r0 + (1 << bits))
+    e0, e1 = int(g.rp[r0]), int(g.rp[r1])
+    col = np.asarray(g.col[e0:e1])
+    keep = (col >= r0) & (col < r1)
+    rows = np.repeat(np.arange(r1 - r0, dtype=np.int64), np.diff(g.rp[r0:r1 + 1]))
+    rp = np.zeros(r1 - r0 + 1, np.int64)
+    np.add.at(rp, rows[keep] + 1, 1)
+    np.cumsum(rp, out=rp)
+    return gg.Graph(rp, (col[keep] - r0).astype(np.int32),
+                    np.ascontiguousarray(np.asarray(g.w[e0:e1])[keep]), f"block{r0}")
+
+
+def time_oracle(sample):
+    """Single-threaded oracle: the full multi-level run on the sample graph."""
     import oracle
     t0 = time.perf_counter()
-    r = oracle.louvain(g.rp, g.col, g.w, max_iters=sweeps, max_levels=1)
+    r = oracle.louvain(sample.rp, sample.col, sample.w)
     dt = time.perf_counter() - t0
     visits = r.edge_visits
     return visits / dt, dt, visits
+
+
+def time_omp(sample, threads: int):
+    """The OpenMP CPU Louvain (cpu_omp) on the sample graph with `threads` threads; its
+    result is checked equal to the oracle's in tests/test_cpu_omp.py."""
+    import cpu_omp
+    t0 = time.perf_counter()
+    r = cpu_omp.louvain(sample.rp, sample.col, sample.w, threads=threads)
+    dt = time.perf_counter() - t0
+    return r.edge_visits / dt, dt, r.edge_visits
+
+
+def sample_text(scale, bits, sample):
+    r0 = sample_block(scale, bits)
+    return (f"full multi-level oracle run (defaults as the GPU run) on the subgraph of the "
+            f"workload graph induced by vertices [{r0:,}, {r0 + (1 << bits):,}) "
+            f"({sample.n:,} vertices, {sample.nnz:,} entries), single thread, per step")
 
 
 def run_reference(args):
@@ -238,13 +303,14 @@ def run_reference(args):
     if rank != 0:
         return 0
     g = make_graph(args.scale)
-    sample = (f"level 0 of the workload graph, first {args.cpu_sample_sweeps} sweeps "
-              "(max_iters and max_levels capped), single thread, per step")
+    sample_g = induced_block(g, sample_block(args.scale, args.sample_bits), args.sample_bits)
+    del g
+    sample = sample_text(args.scale, args.sample_bits, sample_g)
     for _ in range(args.warmup):
-        time_oracle(g, args.cpu_sample_sweeps)
+        time_oracle(sample_g)
     times, visits_total = [], 0
     for _ in range(args.steps):
-        _, dt, v = time_oracle(g, args.cpu_sample_sweeps)
+        _, dt, v = time_oracle(sample_g)
         times.append(dt)
         visits_total += v
     value = visits_total / sum(times)
@@ -253,10 +319,11 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": workload(args.scale), "graph_n": g.n, "graph_nnz": g.nnz,
+        "config": {"workload": workload(args.scale), "graph_n": 1 << args.scale,
+                   "sample_n": sample_g.n, "sample_nnz": sample_g.nnz,
                    "parallelism": "single host thread"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host_cpu": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -265,14 +332,15 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- native arm
 
-def run_e2e(args, g, lv, local, stream, world, dev):
+def run_e2e(args, g, lv, local, stream, world, dev, bins, chunk):
     """Same metric through the C ABI with pinned host buffers: the H2D copy of the graph
-    and the D2H copy of every level's labels are inside the timed region."""
+    and the D2H copy of every level's labels are inside the timed region.  The handle uses
+    the bins the timed runs' autotuner chose (the choice it would cache)."""
     import torch
     rp_h = torch.from_numpy(g.rp).pin_memory()
     col_h = torch.from_numpy(g.col).pin_memory()
     w_h = torch.from_numpy(g.w).pin_memory()
-    h2 = lv.Louvain(local, profile=False, autotune=not args.no_autotune)
+    h2 = lv.Louvain(local, profile=False, bins=bins, chunk_entries=chunk)
     for _ in range(max(1, args.warmup)):
         r = h2.run(rp_h, col_h, w_h, stream=stream.cuda_stream)
         for l in range(r.num_levels):
@@ -288,6 +356,8 @@ def run_e2e(args, g, lv, local, stream, world, dev):
         e2e_visits += int(r.counters()[0][0])
         d2h = sum(a.nbytes for a in out)
         r.close()
+    h2.close()
+    del rp_h, col_h, w_h
     e2e_max = reduce_max(e2e_s, world, dev)
     e2e_all = reduce_sum(float(e2e_visits), world, dev)
     h2d = g.rp.nbytes + g.col.nbytes + g.w.nbytes
@@ -582,6 +652,7 @@ def run_native(args):
         launches += int(c[4])
         if levels is None:
             levels = [(l.n, l.nnz, l.iters, l.ncomm, round(l.q, 6)) for l in res.levels()]
+            run_bytes = {"local_move": int(c[2]), "coarsen": int(res.coarsen_stats()[1])}
         res.close()
     torch.cuda.synchronize(dev)
     barrier(world)
@@ -597,7 +668,7 @@ def run_native(args):
     hp.run(rp, col, w, stream=stream.cuda_stream).close()
     prof_steps = 3
     dom = {"time_ms": 0.0, "bytes": 0, "launches": 0, "id": None}
-    bins_acc, coarsen_ms, prof_ms = {}, 0.0, 0.0
+    bins_acc, coarsen_ms, coarsen_bytes, prof_ms = {}, 0.0, 0, 0.0
     for _ in range(prof_steps):
         flush.fill_(1)
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -613,18 +684,51 @@ def run_native(args):
         dom["launches"] += int(c[5])
         dom["id"] = int(c[7])
         coarsen_ms += float(t[1])
+        coarsen_bytes += int(res.coarsen_stats()[1])
         for b, st in enumerate(res.bin_stats()):
             agg = bins_acc.setdefault(b, {"time_ms": 0.0, "launches": 0, "alg_bytes": 0})
             for key in agg:
                 agg[key] += st[key]
         res.close()
 
+    hp.close()
+    h.close()
+    del rp, col, w, flush
+    torch.cuda.empty_cache()
     # end-to-end through the C ABI with pinned host buffers: H2D inside, labels D2H inside
-    e2e = run_e2e(args, g, lv, local, stream, world, dev) if not args.no_e2e else None
+    e2e = (run_e2e(args, g, lv, local, stream, world, dev, tuned_bins, tuned_chunk)
+           if not args.no_e2e else None)
+    torch.cuda.empty_cache()
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        # the oracle on a bounded sample of the workload graph, one host thread
+        sample_g = induced_block(g, sample_block(args.scale, args.sample_bits), args.sample_bits)
+        v, dt, vis = time_oracle(sample_g)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": sample_text(args.scale, args.sample_bits, sample_g) +
+                         f": {vis:,} edge visits in {dt:.1f} s",
+               "host_cpu": host_cpu()}
+        # this project's OpenMP synchronous Louvain on the same sample (same results as the
+        # oracle), at 8 threads as in the paper's CPU comparison and at every host core
+        omp = {}
+        for th in sorted({8, os.cpu_count() or 1}):
+            v2, dt2, _ = time_omp(sample_g, th)
+            omp[f"threads_{th}"] = {"value": v2, "unit": UNIT, "cores": th,
+                                    "seconds": round(dt2, 3)}
+        cpu["omp"] = omp
+    graph_n, graph_nnz = g.n, g.nnz
+    del g
     batch = (run_batch_workload(args, lv, dev, stream, 2, 1) if args.batch_graphs > 0
              else None)
+    torch.cuda.empty_cache()
     serve = run_serve_workload(args, lv, dev) if args.serve_requests > 0 else None
-    edges = None if args.no_edges else run_edges_workload(lv, g, dev, stream)
+    torch.cuda.empty_cache()
+    edges = None
+    if not args.no_edges:
+        ge = make_graph(args.edges_scale)
+        edges = run_edges_workload(lv, ge, dev, stream)
+        edges["workload"] = f"R-MAT scale {args.edges_scale} (seed {args.edges_scale})"
+        del ge
 
     if rank != 0:
         if world > 1:
@@ -643,25 +747,39 @@ def run_native(args):
                     "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
                     "avg_launch_ms": dom["time_ms"] / dom["launches"]}
 
-    cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        cores = 1
-        v, dt, vis = time_oracle(g, args.cpu_sample_sweeps)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"level 0 of the workload graph, first {args.cpu_sample_sweeps} sweeps "
-                         f"(max_iters/max_levels capped): {vis} edge visits in {dt:.1f} s, "
-                         f"one thread; host has {os.cpu_count()} cores"}
-
     value = all_visits / (max_ms / 1000.0)
+    ms_step = max_ms / args.steps
+    roofline_coarsen = None
+    if coarsen_ms > 0:
+        ach = coarsen_bytes / (coarsen_ms / 1000.0) / 1e9
+        roofline_coarsen = {"bound": "hbm", "achieved": ach, "peak": peak, "peak_kind": peak_kind,
+                            "unit": "GB/s", "frac": ach / peak,
+                            "bytes_per_step": coarsen_bytes // prof_steps,
+                            "ms_per_step": coarsen_ms / prof_steps,
+                            "note": "graph induction of all levels: algorithmic bytes "
+                                    "(louvain_result_coarsen_stats) over its device time in the "
+                                    "profiled runs"}
+    step_bytes = run_bytes["local_move"] + run_bytes["coarsen"]
+    roofline_step = {"bound": "hbm", "bytes_local_move": run_bytes["local_move"],
+                     "bytes_coarsen": run_bytes["coarsen"], "ms_per_step": ms_step,
+                     "achieved": step_bytes / (ms_step / 1000.0) / 1e9,
+                     "achieved_local_move": run_bytes["local_move"] / (ms_step / 1000.0) / 1e9,
+                     "peak": peak, "unit": "GB/s",
+                     "frac": step_bytes / (ms_step / 1000.0) / 1e9 / peak,
+                     "note": "whole run: algorithmic bytes of every sweep and induction over "
+                             "the timed step (includes binning, renumbering and host syncs)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": workload(args.scale), "graph_n": g.n, "graph_nnz": g.nnz,
+        "config": {"workload": workload(args.scale), "graph_n": graph_n,
+                   "graph_nnz": graph_nnz,
                    "levels": levels, "parallelism": "replicas" if world > 1 else "single",
                    "bins": list(tuned_bins), "chunk_entries": tuned_chunk,
-                   "l2": "L2 flushed between timed steps (258 MB write); CSR of 1 GB > L2"},
-        "roofline": roofline, "cpu_baseline": cpu,
+                   "l2": "L2 flushed between timed steps (258 MB write); CSR "
+                         f"{(graph_nnz * 8 + graph_n * 8) / 1e9:.1f} GB > L2"},
+        "roofline": roofline, "roofline_step": roofline_step,
+        "roofline_coarsen": roofline_coarsen, "cpu_baseline": cpu,
         "kernels_ms_per_step": {
             KERNEL_NAMES[b]: {"ms": round(a["time_ms"] / prof_steps, 4),
                               "launches": a["launches"] // prof_steps,
