@@ -740,6 +740,8 @@ def run_native(args):
     if dom["time_ms"] > 0 and dom["launches"] > 0:
         achieved = dom["bytes"] / (dom["time_ms"] / 1000.0) / 1e9
         name = KERNEL_NAMES[dom["id"]]
+        if dom["id"] == 5 and tuned_bins[5] <= 6144:
+            name = "k_move_cta<512>"  # bin 5 with an 8K-slot table (1024 threads if 64-bit)
         traffic = kernel_traffic(name, tuned_bins, tuned_chunk)
         roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -781,7 +783,7 @@ def run_native(args):
         "roofline": roofline, "roofline_step": roofline_step,
         "roofline_coarsen": roofline_coarsen, "cpu_baseline": cpu,
         "kernels_ms_per_step": {
-            KERNEL_NAMES[b]: {"ms": round(a["time_ms"] / prof_steps, 4),
+            (KERNEL_NAMES[b] if b != 5 or tuned_bins[5] > 6144 else "k_move_cta<512>"): {"ms": round(a["time_ms"] / prof_steps, 4),
                               "launches": a["launches"] // prof_steps,
                               "GB/s": round(a["alg_bytes"] / (a["time_ms"] / 1000.0) / 1e9, 1)
                               if a["time_ms"] > 0 else None}

@@ -1948,7 +1948,7 @@ void tuned_bins(louvain_handle *h, cudaStream_t s, DevAlloc &A, int64_t n, const
         return best;
     };
     static const int32_t cand[7][3] = {{0, 4, 8},       {16, 32, 32},       {64, 128, 128},
-                                       {256, 512, 1024}, {1024, 2048, 4096}, {4096, 8192, 12288},
+                                       {256, 512, 1024}, {1024, 2048, 4096}, {4096, 6144, 12288},
                                        {1024, 2048, 4096}};
     int32_t cur[7];
     get_bins(h->cfg, cur);

@@ -40,6 +40,9 @@ namespace lv {
 
 constexpr int kSmallMax = 8;  // register slots of the thread-per-vertex kernel
 constexpr int kUnroll = 4;    // independent row entries in flight per thread
+// bin 5 runs 512-thread CTAs when its table has at most 2^kHalfCtaLog2 slots (rows of at
+// most 6,144 entries) with 32-bit sums (two such tables fit an SM), else 1024-thread CTAs
+constexpr int kHalfCtaLog2 = 13;
 
 template <typename WT>
 struct MoveArgs {
@@ -463,8 +466,8 @@ __device__ __forceinline__ void gather_chunk(const MoveArgs<WT> &A, int32_t i,
 // argmax), the next row's vertex id, entry range, first chunk of columns / weights and its
 // label gathers are already in flight, issued stage by stage so no load waits on another.
 template <int BLOCK, typename WT, typename GT, typename VT, bool BT>
-__global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_t *verts,
-                                                    int nverts, int log2cap, int slot)
+__global__ void __launch_bounds__(BLOCK, BLOCK == 512 ? 2 : 1)
+    k_move_cta(MoveArgs<WT> A, const int32_t *verts, int nverts, int log2cap, int slot)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int cap = 1 << log2cap;
@@ -478,8 +481,13 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
     }
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    auto ins = [&](int32_t key, VT val) {
-        tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, val, A.err);
+    // the kUnroll entries of a thread go into the table together (tbl_insert_batch); the
+    // loops around it are uniform across each warp
+    auto ins = [&](const int32_t (&key)[kUnroll], const i64 (&x)[kUnroll]) {
+        VT v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) v[u] = (VT)x[u];
+        tbl_insert_batch<kUnroll, VT>(keys, vals, list, &s_cnt, log2cap, key, v, A.err);
     };
     u64 internal = 0, moved = 0, cand = 0;
     // prologue: the first row completely prefetched
@@ -508,12 +516,11 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
         const bool fz = frozen<BT>(A, gr);  // a frozen row inserts nothing and stays
         // the prefetched first chunk, then the rest of the row
         i64 loop = 0;
-        if (!fz) {
+        if (!fz) {  // fz is the same for the whole CTA (one row)
 #pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
+            for (int u = 0; u < kUnroll; u++)
                 if (nj[u] == i) loop += nw[u];
-                chunk_insert<VT>(nc[u], nw[u], ins);
-            }
+            ins(nc, nw);
         }
         for (int64_t k0 = rb + threadIdx.x + (int64_t)kUnroll * BLOCK;
              !fz && __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * BLOCK) {
@@ -522,10 +529,9 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta(MoveArgs<WT> A, const int32_
             load_chunk<BLOCK>(A, k0, re, j, x);
             gather_chunk(A, i, j, c);
 #pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
+            for (int u = 0; u < kUnroll; u++)
                 if (j[u] == i) loop += x[u];
-                chunk_insert<VT>(c[u], x[u], ins);
-            }
+            ins(c, x);
         }
         // stage 2: next row's entry range; this row's community degree and size
         int64_t rb_next = 0, re_next = 0;
@@ -620,9 +626,6 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
         const bool fz = frozen<BT>(A, gr);  // a frozen row inserts nothing and stays
         const int64_t rb = A.rp[i], re = fz ? rb : A.rp[i + 1];
         i64 loop = 0;
-        auto cins = [&](int32_t key, VT val) {
-            cluster_insert<VT>(cluster, keys, vals, LOG2CL, log2cap, key, val, A.err);
-        };
         for (int64_t k0 = rb + (int64_t)rank * BLOCK + threadIdx.x;
              __any_sync(0xffffffffu, k0 < re); k0 += (int64_t)kUnroll * stride) {
             int32_t j[kUnroll];
@@ -638,13 +641,16 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
                 }
             }
             int32_t c[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+            VT cv[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) {
-                if (j[u] == i) loop += x[u];
-                chunk_insert<VT>(c[u], x[u], cins);
+                c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
+                cv[u] = (VT)x[u];
             }
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++)
+                if (j[u] == i) loop += x[u];
+            cluster_insert_batch<kUnroll, VT>(cluster, keys, vals, LOG2CL, log2cap, c, cv, A.err);
         }
         cluster.sync();  // every insert of this row has landed
         const int32_t a = A.C[i];
@@ -1324,6 +1330,12 @@ static int launch_bin_table(const MoveArgs<WT> &A, const Bins &b, const BinSpec 
             const int grid = launch_cta_kernel(k_move_cta<256, WT, GT, VT, BT>, 256, smem, nr, bs,
                                                lc, "k_move_cta<256>");
             k_move_cta<256, WT, GT, VT, BT><<<grid, 256, smem, bs>>>(A, rows, nr, l2, bin);
+        } else if (l2 <= kHalfCtaLog2 && sizeof(VT) == 4) {
+            // rows of at most 6,144 entries: 512 threads and an 8K-slot table, so that two
+            // rows are in flight on an SM where the 16K-slot table leaves room for one
+            const int grid = launch_cta_kernel(k_move_cta<512, WT, GT, VT, BT>, 512, smem, nr,
+                                               bs, lc, "k_move_cta<512>");
+            k_move_cta<512, WT, GT, VT, BT><<<grid, 512, smem, bs>>>(A, rows, nr, l2, bin);
         } else {
             const int grid = launch_cta_kernel(k_move_cta<1024, WT, GT, VT, BT>, 1024, smem, nr,
                                                bs, lc, "k_move_cta<1024>");

@@ -286,6 +286,54 @@ __device__ __forceinline__ void warp_append(bool claimed, int slot, int *list, i
     if (claimed) list[base + __popc(m & ((1u << lane) - 1u))] = slot;
 }
 
+// Insert-or-add of U entries of one thread at once (key < 0: nothing to insert).  The
+// claims of all U keys are issued before any result is needed: one CAS per key at its
+// home slot (a key already present there returns itself), so a thread has U shared-memory
+// round trips in flight instead of one chain per entry; a key whose home slot holds
+// another key probes on (tbl_insert_claim).  New slots are appended to `list` once per
+// warp (every lane of the warp must call this with the same U), and the sums are added
+// with atomics whose results are not used.
+template <int U, typename VT>
+__device__ __forceinline__ void tbl_insert_batch(int *keys, VT *vals, int *list, int *cnt,
+                                                 int log2cap, const int32_t (&key)[U],
+                                                 const VT (&val)[U], unsigned *err)
+{
+    unsigned h[U];
+    int old[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        h[u] = key[u] >= 0 ? hash_slot(key[u], log2cap) : 0u;
+        old[u] = key[u] >= 0 ? atomicCAS(&keys[h[u]], -1, key[u]) : key[u];
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        bool claimed = key[u] >= 0 && old[u] == -1;
+        int slot = (int)h[u];
+        if (key[u] >= 0 && old[u] != -1 && old[u] != key[u]) {  // home slot taken: probe on
+            const unsigned mask = (1u << log2cap) - 1u;
+            unsigned hh = (h[u] + 1u) & mask;
+            bool done = false;
+#pragma unroll 1
+            for (unsigned probe = 1; probe <= mask && !done; probe++) {
+                const int o = atomicCAS(&keys[hh], -1, key[u]);
+                if (o == -1 || o == key[u]) {
+                    claimed = o == -1;
+                    slot = (int)hh;
+                    done = true;
+                } else {
+                    hh = (hh + 1u) & mask;
+                }
+            }
+            if (!done) {
+                atomicOr(err, ERRF_HASH_FULL);
+                slot = -1;
+            }
+        }
+        warp_append(claimed, slot, list, cnt);
+        if (key[u] >= 0 && slot >= 0) atomicAdd(&vals[slot], val[u]);
+    }
+}
+
 // Mixing hash of a key (multiply, xor-shift, multiply, xor-shift; the constants of
 // MurmurHash3's 32-bit finaliser), a bijection of 32-bit values independent of the
 // multiplicative hash that indexes the shared tables.  Its top bits choose a key's
@@ -428,11 +476,13 @@ __device__ __forceinline__ void merge_partition(int *keys, VT *vals, int *list, 
 // arrays; each segment's list records the local slots claimed in it.
 template <typename VT, typename Cluster>
 __device__ __forceinline__ void cluster_insert(Cluster &cluster, int *keys, VT *vals, int log2cl,
-                                               int log2cap, int key, VT val, unsigned *err)
+                                               int log2cap, int key, VT val, unsigned *err,
+                                               unsigned start = ~0u)
 {
     const unsigned total_mask = (1u << (log2cl + log2cap)) - 1u;
     const unsigned local_mask = (1u << log2cap) - 1u;
-    unsigned v = ((unsigned)key * 2654435761u) >> (32 - (log2cl + log2cap));
+    unsigned v = start != ~0u ? start
+                              : ((unsigned)key * 2654435761u) >> (32 - (log2cl + log2cap));
     unsigned owner = v >> log2cap;
     int *rk = cluster.map_shared_rank(keys, owner);
 #pragma unroll 1
@@ -457,6 +507,39 @@ __device__ __forceinline__ void cluster_insert(Cluster &cluster, int *keys, VT *
         }
     }
     atomicOr(err, ERRF_HASH_FULL);
+}
+
+// U entries of one thread into the cluster-wide table at once: one remote CAS per key at
+// its home slot issued before any result is needed, probing on only for keys whose home
+// slot holds another key, and sums added with atomics whose results are not used.
+template <int U, typename VT, typename Cluster>
+__device__ __forceinline__ void cluster_insert_batch(Cluster &cluster, int *keys, VT *vals,
+                                                     int log2cl, int log2cap,
+                                                     const int32_t (&key)[U], const VT (&val)[U],
+                                                     unsigned *err)
+{
+    const unsigned local_mask = (1u << log2cap) - 1u;
+    unsigned v[U];
+    int old[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        v[u] = key[u] >= 0 ? ((unsigned)key[u] * 2654435761u) >> (32 - (log2cl + log2cap)) : 0u;
+        old[u] = key[u] >= 0
+                     ? atomicCAS(cluster.map_shared_rank(keys, v[u] >> log2cap) + (v[u] & local_mask),
+                                 -1, key[u])
+                     : key[u];
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        if (key[u] < 0) continue;
+        if (old[u] == -1 || old[u] == key[u]) {
+            atomicAdd(cluster.map_shared_rank(vals, v[u] >> log2cap) + (v[u] & local_mask), val[u]);
+        } else {  // home slot taken: probe on from the next virtual slot
+            const unsigned total_mask = (1u << (log2cl + log2cap)) - 1u;
+            cluster_insert<VT>(cluster, keys, vals, log2cl, log2cap, key[u], val[u], err,
+                               (v[u] + 1u) & total_mask);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- launch helpers
