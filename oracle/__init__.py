@@ -15,7 +15,13 @@ Parity status of each exported function (what pins it to the paper, in tests/):
   renumber        -- pinned: order-preserving compaction checked against numpy.unique.
   coarsen         -- pinned: dense P^T A P (numpy matmul) on small graphs.
   louvain         -- pinned: Q <= brute-force optimum (n <= 12), planted cliques
-                     recovered, Theorem 1 and TW / Q preservation across levels.
+                     recovered, Theorem 1 and TW / Q preservation across levels; the
+                     outer stop of Algorithm 2 against exact fractions.
+  color           -- pinned: proper colouring equal to the sequential greedy colouring
+                     in decreasing priority order.
+  louvain(coloring=True) -- pinned: with one vertex per colour class it is sequential
+                     local moving (textbook Blondel gain with removal first); hand-worked
+                     two-colour case; Q <= brute force; planted cliques; Theorem 1.
 """
 from __future__ import annotations
 
@@ -58,7 +64,9 @@ def _load():
     lib.oracle_run.restype = P
     lib.oracle_run.argtypes = [i64, P, P, P, i64, i64, i32, i32, i32, i32, P]
     lib.oracle_run_ex.restype = P
-    lib.oracle_run_ex.argtypes = [i64, P, P, P, i64, i64, i32, i32, i32, i32, i32, i32, P]
+    lib.oracle_run_ex.argtypes = [i64, P, P, P, i64, i64, i32, i32, i32, i32, i32, i32, i32, P]
+    lib.oracle_color.restype = i32
+    lib.oracle_color.argtypes = [i64, P, P, P]
     lib.oracle_res_num_levels.restype = i32
     lib.oracle_res_num_levels.argtypes = [P]
     lib.oracle_res_tw.restype = i64
@@ -152,10 +160,12 @@ class OracleResult:
 
 def louvain(rp, col, w=None, theta=(1, 1_000_000), max_iters=1000, max_levels=64,
             vertex_following=True, vf_all_levels=False, threshold_mode=0,
-            post_merge=False) -> OracleResult:
+            post_merge=False, coloring=False) -> OracleResult:
     """Full multi-level synchronous Louvain (Algorithm 2 around Algorithm 1).
     threshold_mode 0: absolute phase test; 1: the relative test printed in Algorithm 1.
-    post_merge: the post-phase merge of single-neighbour-community vertices (Sec. 5.1.2)."""
+    post_merge: the post-phase merge of single-neighbour-community vertices (Sec. 5.1.2).
+    coloring: sweeps take the colour classes of a distance-1 colouring one after the other
+    (Lu et al.'s colouring heuristic, reading R17)."""
     lib = _load()
     rp, col, w = _csr(rp, col, w, np.int32)
     n = len(rp) - 1
@@ -163,7 +173,7 @@ def louvain(rp, col, w=None, theta=(1, 1_000_000), max_iters=1000, max_levels=64
     h = lib.oracle_run_ex(n, _ptr(rp), _ptr(col), _ptr(w), int(theta[0]), int(theta[1]),
                           int(max_iters), int(max_levels), int(bool(vertex_following)),
                           int(bool(vf_all_levels)), int(threshold_mode), int(bool(post_merge)),
-                          ctypes.addressof(st))
+                          int(bool(coloring)), ctypes.addressof(st))
     if not h:
         raise OracleError(f"oracle_run failed with status {st.value}")
     try:
@@ -195,6 +205,17 @@ def louvain(rp, col, w=None, theta=(1, 1_000_000), max_iters=1000, max_levels=64
                             lib.oracle_res_sweeps(h), bool(lib.oracle_res_hit_iter_cap(h)))
     finally:
         lib.oracle_res_free(h)
+
+
+def color(rp, col):
+    """Distance-1 colouring of reading R17: (colour of every vertex, number of colours)."""
+    lib = _load()
+    rp, col, _ = _csr(rp, col)
+    out = np.empty(len(rp) - 1, np.int32)
+    k = lib.oracle_color(len(rp) - 1, _ptr(rp), _ptr(col), _ptr(out))
+    if k < 0:
+        raise OracleError("bad input")
+    return out, int(k)
 
 
 def modularity(rp, col, w, C):

@@ -61,6 +61,15 @@
  *       pair (each the other's only neighbour) joins min(i, j).
  *   R12 zero-degree vertices stay singletons at every level.
  *   R13 a graph without vertices runs no phase (no sweep, no level).
+ *   R17 coloring (a variant; Lu et al.'s colouring heuristic, which Sec. 7 names among the
+ *       "other heuristics" without defining it): at every level the graph's vertices get a
+ *       distance-1 colouring (Jones-Plassmann rounds: an uncoloured vertex whose priority
+ *       exceeds that of every uncoloured non-loop neighbour takes the smallest colour
+ *       unused by its coloured neighbours; priority = SplitMix64 output function of the
+ *       vertex id).  A sweep takes the colour classes in increasing colour: the vertices of
+ *       a class decide together on the current state (the rule of R5/R6), their moves are
+ *       applied and deg/size rebuilt before the next class.  Stop tests, trace and levels
+ *       are per sweep as without colouring.
  *
  * Arithmetic: weights, degrees and sums in int64; every product of two of them in
  * __int128.  Nothing here is floating point except the reported Q = (double)Qn / (double)TW^2
@@ -228,12 +237,17 @@ static void vertex_following(const og_graph *g, int32_t *C)
  * zero on entry and is all zero again on return. */
 static int64_t local_move_sweep(const og_graph *g, const int32_t *C, const int64_t *deg,
                                 const int32_t *size, const int64_t *delta, int64_t TW,
-                                int32_t *Cnext, int64_t *e, int64_t *seen, int32_t *touched)
+                                int32_t *Cnext, int64_t *e, int64_t *seen, int32_t *touched,
+                                const int32_t *color, int32_t cls)
 {
     int64_t moved = 0;
     for (int64_t i = 0; i < g->n; i++) {
         int32_t a = C[i];
         int64_t m = 0;
+        if (color && color[i] != cls) { /* another colour class: stays this time (R17) */
+            Cnext[i] = a;
+            continue;
+        }
         /* Eq. 1 over the neighbours' communities, loop excluded (R4) */
         for (int64_t k = g->rp[i]; k < g->rp[i + 1]; k++) {
             int32_t j = g->col[k];
@@ -274,6 +288,75 @@ static int64_t local_move_sweep(const og_graph *g, const int32_t *C, const int64
         moved += 1;
     }
     return moved;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Distance-1 colouring for the colouring variant (R17).                     */
+/* ------------------------------------------------------------------------- */
+
+/* Priority of vertex v: the output function of SplitMix64 (Steele, Lea, Flood 2014) applied
+ * to v, a bijection of 64-bit values, so no two vertices tie. */
+static uint64_t color_priority(int64_t v)
+{
+    uint64_t z = (uint64_t)v + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Jones-Plassmann rounds: every uncoloured vertex whose priority is above that of each of
+ * its uncoloured non-loop neighbours takes the smallest colour none of its coloured
+ * neighbours has; the vertices chosen in one round are pairwise non-adjacent, so the
+ * order within a round does not matter.  Returns the number of colours, -1 on OOM. */
+static int32_t color_graph(const og_graph *g, int32_t *color)
+{
+    int64_t n = g->n;
+    uint8_t *pick = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    uint8_t *used = NULL;
+    int64_t used_cap = 0;
+    if (!pick) return -1;
+    for (int64_t v = 0; v < n; v++) color[v] = -1;
+    int64_t left = n;
+    int32_t ncolors = 0;
+    while (left > 0) {
+        for (int64_t v = 0; v < n; v++) {
+            pick[v] = 0;
+            if (color[v] >= 0) continue;
+            uint64_t pv = color_priority(v);
+            int top = 1;
+            for (int64_t k = g->rp[v]; k < g->rp[v + 1] && top; k++) {
+                int32_t u = g->col[k];
+                if (u != v && color[u] < 0 && color_priority(u) > pv) top = 0;
+            }
+            pick[v] = (uint8_t)top;
+        }
+        for (int64_t v = 0; v < n; v++) {
+            if (!pick[v]) continue;
+            int64_t d = g->rp[v + 1] - g->rp[v];
+            if (d + 1 > used_cap) {
+                free(used);
+                used_cap = d + 1;
+                used = (uint8_t *)malloc((size_t)used_cap);
+                if (!used) {
+                    free(pick);
+                    return -1;
+                }
+            }
+            memset(used, 0, (size_t)(d + 1));
+            for (int64_t k = g->rp[v]; k < g->rp[v + 1]; k++) {
+                int32_t cu = color[g->col[k]];
+                if (g->col[k] != v && cu >= 0 && cu <= d) used[cu] = 1;
+            }
+            int32_t c = 0;
+            while (used[c]) c++; /* at most d colours are taken: c <= d */
+            color[v] = c;
+            if (c + 1 > ncolors) ncolors = c + 1;
+            left--;
+        }
+    }
+    free(pick);
+    free(used);
+    return ncolors;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -508,7 +591,7 @@ static int below_threshold_rel(i128 qn_new, i128 qn_old, int64_t num, int64_t de
 
 static int louvain_run_impl(const og_graph *g0, int64_t theta_num, int64_t theta_den,
                             int32_t max_iters, int32_t max_levels, int32_t vf, int32_t vf_all,
-                            int32_t rel, int32_t merge, og_result *r)
+                            int32_t rel, int32_t merge, int32_t coloring, og_result *r)
 {
     int64_t n0 = g0->n;
     og_graph g = {0, 0, NULL, NULL, NULL};
@@ -527,8 +610,9 @@ static int louvain_run_impl(const og_graph *g0, int64_t theta_num, int64_t theta
     int64_t *deg_tmp = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
     int64_t *e = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
     int64_t *seen = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    int32_t *color = coloring ? (int32_t *)malloc(sizeof(int32_t) * (size_t)N) : NULL;
     if (!map0 || !C || !Cnext || !new_id || !size || !size_tmp || !touched || !delta || !deg ||
-        !deg_tmp || !e || !seen) {
+        !deg_tmp || !e || !seen || (coloring && !color)) {
         rc = ORACLE_ERR_OOM;
         goto done;
     }
@@ -567,15 +651,26 @@ static int louvain_run_impl(const og_graph *g0, int64_t theta_num, int64_t theta
         i128 qn_init = modularity_qn(&g, C, delta, TW, deg_tmp, size_tmp);
         i128 qn_prev = qn_init, qn_new = qn_init;
         int32_t iters = 0;
+        int32_t ncolors = 1;
+        if (coloring && (ncolors = color_graph(&g, color)) < 0) {
+            rc = ORACLE_ERR_OOM;
+            goto done;
+        }
         for (;;) {
-            int64_t moved = local_move_sweep(&g, C, deg, size, delta, TW, Cnext, e, seen, touched);
+            /* one sweep: every vertex at once, or (R17) the colour classes one after the
+             * other, each deciding on the state its predecessors left */
+            int64_t moved = 0;
+            for (int32_t cls = 0; cls < ncolors; cls++) {
+                moved += local_move_sweep(&g, C, deg, size, delta, TW, Cnext, e, seen, touched,
+                                          coloring ? color : NULL, cls);
+                int32_t *t = C;
+                C = Cnext;
+                Cnext = t;
+                community_degrees(n, C, delta, deg, size);
+            }
             iters += 1;
             r->edge_visits += g.nnz;
             r->sweeps_total += 1;
-            int32_t *t = C;
-            C = Cnext;
-            Cnext = t;
-            community_degrees(n, C, delta, deg, size);
             qn_new = modularity_qn(&g, C, delta, TW, deg_tmp, size_tmp);
             if ((rc = trace_push(r, level, iters, moved, qn_new)) != ORACLE_OK) goto done;
             if (moved == 0) break;
@@ -642,6 +737,7 @@ done:
     free(deg_tmp);
     free(e);
     free(seen);
+    free(color);
     return rc;
 }
 
@@ -664,7 +760,7 @@ int32_t oracle_abi_version(void) { return 1; }
 void *oracle_run_ex(int64_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
                     int64_t theta_num, int64_t theta_den, int32_t max_iters, int32_t max_levels,
                     int32_t vertex_following_on, int32_t vf_all_levels, int32_t threshold_mode,
-                    int32_t post_merge_on, int32_t *status)
+                    int32_t post_merge_on, int32_t coloring, int32_t *status)
 {
     if (threshold_mode != 0 && threshold_mode != 1) {
         if (status) *status = ORACLE_ERR_INVALID;
@@ -703,7 +799,7 @@ void *oracle_run_ex(int64_t n, const int64_t *rp, const int32_t *col, const int3
         return NULL;
     }
     rc = louvain_run_impl(&g, theta_num, theta_den, max_iters, max_levels, vertex_following_on,
-                          vf_all_levels, threshold_mode, post_merge_on, r);
+                          vf_all_levels, threshold_mode, post_merge_on, coloring != 0, r);
     graph_free(&g);
     if (rc != ORACLE_OK) {
         result_free(r);
@@ -718,7 +814,7 @@ void *oracle_run(int64_t n, const int64_t *rp, const int32_t *col, const int32_t
                  int32_t vertex_following_on, int32_t vf_all_levels, int32_t *status)
 {
     return oracle_run_ex(n, rp, col, w, theta_num, theta_den, max_iters, max_levels,
-                         vertex_following_on, vf_all_levels, 0, 0, status);
+                         vertex_following_on, vf_all_levels, 0, 0, 0, status);
 }
 
 int32_t oracle_res_num_levels(const void *h) { return ((const og_result *)h)->num_levels; }
@@ -765,6 +861,17 @@ void oracle_res_trace(const void *h, int32_t *level, int32_t *iter, int64_t *mov
 void oracle_res_free(void *h) { result_free((og_result *)h); }
 
 /* ---- single steps, exposed so the tests can pin each against the paper ---- */
+
+/* Colouring of reading R17 for graph (n, rp, col): colour of every vertex into color_out;
+ * returns the number of colours, or -1 on bad input. */
+int32_t oracle_color(int64_t n, const int64_t *rp, const int32_t *col, int32_t *color_out)
+{
+    og_graph g = {0, 0, NULL, NULL, NULL};
+    if (graph_from_input(&g, n, rp, col, NULL, NULL) != ORACLE_OK) return -1;
+    int32_t k = color_graph(&g, color_out);
+    graph_free(&g);
+    return k;
+}
 
 /* Eq. 3 times TW^2 for labels C (values in [0, n)).  Returns TW, or -1 on bad input. */
 int64_t oracle_modularity(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
@@ -842,7 +949,8 @@ int64_t oracle_sweep(int64_t n, const int64_t *rp, const int32_t *col, const int
     int64_t TW = 0;
     for (int64_t v = 0; v < n; v++) TW += delta[v];
     for (int64_t v = 0; v < n; v++) seen[v] = 0;
-    int64_t moved = local_move_sweep(&g, C, deg, size, delta, TW, Cnext, e, seen, touched);
+    int64_t moved = local_move_sweep(&g, C, deg, size, delta, TW, Cnext, e, seen, touched,
+                                     NULL, 0);
     free(delta);
     free(deg);
     free(size);
