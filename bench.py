@@ -235,6 +235,15 @@ def host_cpu():
                         break
     except OSError:
         pass
+    if not model or model.startswith("0x"):  # Arm: /proc/cpuinfo gives only a part code
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name:"):
+                    model = line.split(":", 1)[1].strip() or model
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
     import platform
     return {"model": model or platform.processor() or platform.machine(),
             "arch": platform.machine(), "logical_cores": os.cpu_count()}
