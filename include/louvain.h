@@ -120,6 +120,14 @@ typedef struct {
     int32_t part_keys;         /* rows spanning several chunks are merged by partition: the */
                                /* expected distinct keys per partition (64 .. 2^30; 0 or */
                                /* the default 2048); larger means fewer partitions      */
+    int32_t coloring;          /* 1: Lu et al.'s colouring heuristic, which Sec. 7 names    */
+                               /* among the parallel heuristics it builds on: each level's */
+                               /* graph gets a distance-1 colouring (Jones-Plassmann      */
+                               /* rounds, priorities from SplitMix64's output function of */
+                               /* the vertex id, smallest free colour) and a sweep takes  */
+                               /* the colour classes in increasing colour, each deciding  */
+                               /* on the state its predecessors left (louvain_run and     */
+                               /* louvain_resume only); 0 (default): synchronous sweeps   */
     /* device memory: both NULL means stream-ordered cudaMallocAsync/cudaFreeAsync */
     louvain_alloc_fn alloc;
     louvain_free_fn free;

@@ -9,6 +9,7 @@
 // per level; every step of the method runs in the kernels of k_level.cu, k_move.cu and
 // k_coarsen.cu.
 #include <algorithm>
+#include <functional>
 #include <array>
 #include <chrono>
 #include <climits>
@@ -141,6 +142,10 @@ struct Scalars {
     int32_t ndone;  // phase controllers that have stopped
     u64 tw;
     u64 dmax;       // largest weighted degree of the level's graph
+    u64 ccounts2[2];  // colouring round: uncoloured vertices, picks
+    u64 cmoved;       // colouring variant: vertices moved by the classes of a sweep
+    int32_t ncolors;  // colouring variant: colours of the level's graph
+    int32_t pad2_;
     SweepStats st;
     LevelCtl ctl;
     int32_t bin_counts[40];
@@ -152,19 +157,34 @@ struct Scalars {
     int32_t tail[8];
 };
 
-bool host_below_threshold(i128 qn_new, i128 qn_old, i64 tw, i64 num, i64 den)
+// x * a < y * b for unsigned 128-bit x, y and 64-bit a, b, compared in 192 bits
+bool host_less_192(u128 x, u64 a, u128 y, u64 b)
 {
-    const i128 diff = qn_new - qn_old;
-    if (diff < 0) return true;
-    const u128 tw2 = (u128)(u64)tw * (u64)tw;
-    const u128 x = (u128)diff;
-    const u128 xl = (u128)(u64)x * (u64)den, xh = (u128)(u64)(x >> 64) * (u64)den;
-    const u128 yl = (u128)(u64)tw2 * (u64)num, yh = (u128)(u64)(tw2 >> 64) * (u64)num;
+    const u128 xl = (u128)(u64)x * a, xh = (u128)(u64)(x >> 64) * a;
+    const u128 yl = (u128)(u64)y * b, yh = (u128)(u64)(y >> 64) * b;
     const u128 xmid = (xl >> 64) + (u64)xh, ymid = (yl >> 64) + (u64)yh;
     const u64 x2 = (u64)(xh >> 64) + (u64)(xmid >> 64), y2 = (u64)(yh >> 64) + (u64)(ymid >> 64);
     if (x2 != y2) return x2 < y2;
     if ((u64)xmid != (u64)ymid) return (u64)xmid < (u64)ymid;
     return (u64)xl < (u64)yl;
+}
+
+bool host_below_threshold(i128 qn_new, i128 qn_old, i64 tw, i64 num, i64 den)
+{
+    const i128 diff = qn_new - qn_old;
+    if (diff < 0) return true;
+    const u128 tw2 = (u128)(u64)tw * (u64)tw;
+    return host_less_192((u128)diff, (u64)den, tw2, (u64)num);
+}
+
+// relative phase test of Algorithm 1 (reading R14): |qn_new - qn_old| * den < num * |qn_old|;
+// qn_old = 0 stops only on an unchanged Qn
+bool host_below_threshold_rel(i128 qn_new, i128 qn_old, i64 num, i64 den)
+{
+    const i128 diff = qn_new - qn_old;
+    const u128 ad = (u128)(diff < 0 ? -diff : diff), ao = (u128)(qn_old < 0 ? -qn_old : qn_old);
+    if (ao == 0) return ad == 0;
+    return host_less_192(ad, (u64)den, ao, (u64)num);
 }
 
 i128 limbs_to_i128(const i64 v[2]) { return (i128)(((u128)(u64)v[0] << 64) | (u128)(u64)v[1]); }
@@ -361,13 +381,18 @@ struct Engine {
     // per-vertex state, sized for the largest stacked graph so far
     DBuf<i64> delta, delta_next, deg;
     DBuf<int32_t> C, Cnext, size, new_id, new_id2, lists, vg;
-    DBuf<int32_t> b_nch, b_chunk_first, b_plog2, b_glog2, b_gcnt, b_gdone;
+    DBuf<int32_t> colorb, pickb;  // colouring variant: colour of every vertex, round picks
+    DBuf<int32_t> b_nch, b_chunk_first, b_plog2, b_glog2;
     DBuf<int64_t> b_hoff, b_gcap, b_goff;
     DBuf<u64> b_gloop;
     DBuf<int32_t> scratch32;
     DBuf<int64_t> scratch64;
-    DBuf<int32_t> chunk_b, gkeys, glist, hp_best, hp_sdone, hp_slice_row;
-    DBuf<u64> gvals;
+    DBuf<int32_t> chunk_b, hp_best, hp_sdone, hp_slice_row;
+    // induction of multi-chunk communities: pairs per partition, offsets, cursors, the
+    // partition's community, pairs per chunk, the pairs grouped by partition
+    DBuf<int32_t> c_pcnt, c_pcur, c_partb, c_chm, c_pk;
+    DBuf<int64_t> c_poff, c_pscr;
+    DBuf<u64> c_pv;
     DBuf<int64_t> hp_soff;
     DBuf<i64> hp_ea;
     DBuf<u64> hp_cnt;
@@ -506,7 +531,13 @@ struct Engine {
 
     Bins make_proto(bool narrow_sums) const;
     Bins make_bins(const DevGraph &gr, const Bins &pr, const int32_t *vgp = nullptr,
-                   const LevelCtl *gctl = nullptr);
+                   const LevelCtl *gctl = nullptr, const int32_t *color = nullptr,
+                   int32_t cls = 0);
+    int color_level(int64_t n);
+    void colored_phase(const PhaseState &st, const Bins &proto, i64 TW, bool wide, bool narrow,
+                       SweepStats *st_dev, BatchCtx &bc, SweepTimers &tm, int &sweeps,
+                       double *t_kernel, int64_t *launches_kernel,
+                       const std::function<void(const Bins &, int)> &account);
     void prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *cbp);
     void join();
     void step(std::vector<Member *> &retired);
@@ -633,7 +664,7 @@ Bins Engine::make_proto(bool narrow_sums) const
 // degree bins of graph gr: count, then fill the list grouped by bin (rows of graphs whose
 // phase stopped are left out when gctl is given)
 Bins Engine::make_bins(const DevGraph &gr, const Bins &pr, const int32_t *vgp,
-                       const LevelCtl *gctl)
+                       const LevelCtl *gctl, const int32_t *color, int32_t cls)
 {
     Bins bins = pr;
     bins.list = lists.p;
@@ -643,7 +674,7 @@ Bins Engine::make_bins(const DevGraph &gr, const Bins &pr, const int32_t *vgp,
     bins.gloop = b_gloop.p;
     bins.plog2 = b_plog2.p;
     bins.hoff = b_hoff.p;
-    kernels += launch_bin_count(gr, bins, s, lc, vgp, gctl);
+    kernels += launch_bin_count(gr, bins, s, lc, vgp, gctl, color, cls);
     sync_scalars();
     bins.off[0] = bins.off[1] = 0;
     for (int b = 0; b < kNumBins; b++) {
@@ -651,8 +682,119 @@ Bins Engine::make_bins(const DevGraph &gr, const Bins &pr, const int32_t *vgp,
         memcpy(&bins.entries[b], &h->pinned->bin_counts[16 + 2 * b], sizeof(int64_t));
         if (b >= 1) bins.off[b + 1] = bins.off[b] + bins.nlist[b];
     }
-    kernels += launch_bin_fill(gr, bins, s, lc, vgp, gctl);
+    kernels += launch_bin_fill(gr, bins, s, lc, vgp, gctl, color, cls);
     return bins;
+}
+
+// Colouring variant: Jones-Plassmann rounds over the level's graph into colorb; returns the
+// number of colours.  Every round colours at least the highest-priority uncoloured vertex,
+// so n rounds always suffice.
+int Engine::color_level(int64_t n)
+{
+    ensure(colorb, n);
+    ensure(pickb, n);
+    CK(cudaMemsetAsync(colorb.p, 0xFF, sizeof(int32_t) * (size_t)n, s));  // -1: uncoloured
+    CK(cudaMemsetAsync(&d_sc->ncolors, 0, sizeof(int32_t), s));
+    for (int64_t round = 0;; round++) {
+        kernels += launch_color_pick(G, colorb.p, pickb.p, &d_sc->ccounts2[0], s, lc);
+        kernels += launch_color_assign(G, colorb.p, pickb.p, &d_sc->ncolors, s, lc);
+        sync_scalars();
+        const u64 unc = h->pinned->ccounts2[0], picked = h->pinned->ccounts2[1];
+        if (unc == picked) break;
+        if (picked == 0 || round > n) throw LvErr{LOUVAIN_ERR_INTERNAL, "colouring did not finish"};
+    }
+    return h->pinned->ncolors;
+}
+
+// Colouring variant of one phase (one graph): every sweep takes the colour classes in
+// increasing colour; the class's vertices decide on the current state (the sweep kernels
+// over the class's rows), their moves are applied, then the next class.  After each sweep the
+// exact Qn of the new state decides the stop as without colouring (nothing moved, the theta
+// test, the sweep cap).  The device controller, trace and candidate totals are left as the
+// synchronous phase leaves them.
+void Engine::colored_phase(const PhaseState &st, const Bins &proto, i64 TW, bool wide,
+                           bool narrow, SweepStats *st_dev, BatchCtx &bc, SweepTimers &tm,
+                           int &sweeps, double *t_kernel, int64_t *launches_kernel,
+                           const std::function<void(const Bins &, int)> &account)
+{
+    const int64_t n = G.n;
+    const int K = color_level(n);
+    CK(cudaMemsetAsync(st_dev, 0, sizeof(SweepStats), s));
+    kernels += launch_qn_one(G, st, st_dev, &d_sc->ctl, s, lc);
+    sync_scalars();
+    const i128 qn_init = limbs_to_i128(h->pinned->ctl.qn_final);
+    i128 qn_prev = qn_init, qn = qn_init;
+    std::vector<i64> tr_m, tr_q;
+    u64 cand[16] = {};
+    int iters = 0;
+    bool cap = false;
+    for (;;) {
+        CK(cudaMemsetAsync(&d_sc->cmoved, 0, sizeof(u64), s));
+        for (int c = 0; c < K; c++) {
+            PhaseState sc = st;
+            sc.color = colorb.p;
+            sc.cls = c;
+            Bins cb = make_bins(G, proto, nullptr, nullptr, colorb.p, c);
+            prep_huge(cb, false, 0, nullptr);
+            kernels += launch_sweep(G, sc, cb, TW, wide, narrow, false, st_dev, &d_sc->err, s,
+                                    lc, &tm, bc);
+            kernels += launch_apply_class(n, sc, &d_sc->cmoved, s, lc);
+            account(cb, 0);
+            for (int b = 0; b < kNumBins; b++)
+                launches_kernel[b] +=
+                    b == 0 ? 1 : (b == kChunkedBin ? cb.nchunks > 0 : cb.nlist[b] > 0);
+            if (tm.on) {
+                CK(cudaStreamSynchronize(s));
+                for (int b = 0; b < kNumBins; b++) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, tm.ev[2 * b], tm.ev[2 * b + 1]));
+                    t_kernel[b] += ms;
+                }
+            }
+        }
+        sync_scalars();
+        const u64 moved = h->pinned->cmoved;
+        for (int b = 0; b < 16; b++) cand[b] += h->pinned->st.cand[b];
+        // exact Qn of the state after the sweep (the sweep kernels' statistics are not used)
+        CK(cudaMemsetAsync(st_dev, 0, sizeof(SweepStats), s));
+        kernels += launch_qn_one(G, st, st_dev, &d_sc->ctl, s, lc);
+        sync_scalars();
+        qn = limbs_to_i128(h->pinned->ctl.qn_final);
+        iters++;
+        sweeps++;
+        tr_m.push_back((i64)moved);
+        tr_q.push_back((i64)(qn >> 64));
+        tr_q.push_back((i64)(u64)qn);
+        if (moved == 0) break;
+        const bool below = cfg.threshold_mode == 1
+                               ? host_below_threshold_rel(qn, qn_prev, cfg.theta_num, cfg.theta_den)
+                               : host_below_threshold(qn, qn_prev, TW, cfg.theta_num, cfg.theta_den);
+        if (below) break;
+        if (iters >= cfg.max_iters) {
+            cap = true;
+            break;
+        }
+        qn_prev = qn;
+    }
+    // leave the controller, trace and candidate totals where the synchronous phase leaves them
+    LevelCtl cc = h->pinned->ctl;
+    cc.iters = iters;
+    cc.sweep = iters;
+    cc.hit_cap = cap;
+    cc.done = 1;
+    cc.qn_init[0] = (i64)(qn_init >> 64);
+    cc.qn_init[1] = (i64)(u64)qn_init;
+    cc.qn_final[0] = (i64)(qn >> 64);
+    cc.qn_final[1] = (i64)(u64)qn;
+    cc.qn_prev[0] = (i64)(qn_prev >> 64);
+    cc.qn_prev[1] = (i64)(u64)qn_prev;
+    h->pinned->ctl = cc;
+    CK(cudaMemcpyAsync(&d_sc->ctl, &h->pinned->ctl, sizeof(LevelCtl), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(tr_moved.p, tr_m.data(), sizeof(i64) * tr_m.size(), cudaMemcpyHostToDevice,
+                       s));
+    CK(cudaMemcpyAsync(tr_qn.p, tr_q.data(), sizeof(i64) * tr_q.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(&d_sc->cand_total[0], cand, sizeof(cand), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
 }
 
 // chunk lists and global tables of the chunked bin (after its size is known)
@@ -669,20 +811,31 @@ void Engine::prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *
     chunk_b.reset(&A, b.nchunks);
     b.chunk_b = chunk_b.p;
     kernels += launch_big_fill(b, s, lc);
-    if (coarsen_side) {  // one global table per multi-chunk community
-        b.gslots = read_one(b_goff.p + nb);
-        if (b.gslots > 0) {
-            gkeys.reset(&A, b.gslots);
-            gvals.reset(&A, b.gslots);  // 8 bytes per slot covers both sum widths
-            glist.reset(&A, b.gslots);
-            CK(cudaMemsetAsync(gkeys.p, 0xFF, sizeof(int32_t) * b.gslots, s));
-            CK(cudaMemsetAsync(gvals.p, 0, sizeof(u64) * b.gslots, s));
+    if (coarsen_side) {  // partitioned merge of the multi-chunk communities
+        const int64_t np = read_one(b_goff.p + nb);
+        b.gslots = np;
+        if (np > 0) {
+            ensure(c_pcnt, (size_t)np + 1);
+            ensure(c_poff, (size_t)np + 1);
+            ensure(c_pcur, (size_t)np);
+            ensure(c_partb, (size_t)np);
+            ensure(c_pscr, (size_t)scan_scratch_elems(np + 1) + 64);
+            // a chunk's distinct pairs never outnumber its entries
+            ensure(c_pk, (size_t)b.nchunks * b.chunk);
+            ensure(c_pv, (size_t)b.nchunks * b.chunk);  // 8 bytes covers both sum widths
+            CK(cudaMemsetAsync(c_pcnt.p, 0, sizeof(int32_t) * (np + 1), s));
+            CK(cudaMemsetAsync(c_pcur.p, 0, sizeof(int32_t) * np, s));
         }
-        b.gkeys = gkeys.p;
-        b.gvals = gvals.p;
-        b.glist = glist.p;
-        CK(cudaMemsetAsync(b_gcnt.p, 0, sizeof(int32_t) * nb, s));
-        CK(cudaMemsetAsync(b_gdone.p, 0, sizeof(int32_t) * nb, s));
+        ensure(c_chm, (size_t)std::max(b.nchunks, 1));
+        b.cpcnt = c_pcnt.p;
+        b.cpoff = c_poff.p;
+        b.cpcur = c_pcur.p;
+        b.cpartb = c_partb.p;
+        b.cchm = c_chm.p;
+        b.cpk = c_pk.p;
+        b.cpv = c_pv.p;
+        b.cpscr = c_pscr.p;
+        if (np > 0) kernels += launch_coarsen_partfill(b, s, lc);
         return;
     }
     if (b.nchunks > nb) {  // some rows span several chunks
@@ -825,8 +978,6 @@ void Engine::join()
 
     ensure(b_plog2, n);
     ensure(b_glog2, n);
-    ensure(b_gcnt, n);
-    ensure(b_gdone, n);
     ensure(b_gcap, n);
     ensure(b_goff, (size_t)n + 1);
     ensure(b_hoff, (size_t)n + 1);
@@ -929,12 +1080,11 @@ void Engine::step(std::vector<Member *> &retired)
     // e_{i->c} never exceeds delta_i, so 32-bit sums are exact when every delta_i < 2^32;
     // a gain of vertex i is at most 2W * delta_i in magnitude (both of its products are),
     // so int64 gains are exact when max delta * 2W <= 2^62, else int128.  The induction's
-    // sums reach a community's degree, up to 2W: its width follows 2W.
+    // widths follow the largest community degree (below).
     kernels += launch_max_delta(delta.p, n, &d_sc->dmax, s, lc);
     const u64 dmax = read_one(&d_sc->dmax);
     const bool wide = cfg.force_int128 || (u128)dmax * tw_max > ((u128)1 << 62);
     const bool narrow = !cfg.wide_sums && dmax < ((u64)1 << 32);
-    const bool narrow_c = !cfg.wide_sums && tw_max < ((u64)1 << 32);
     const i64 TW = h_tw[0];  // one graph: its 2W (a batch reads 2W per graph on the device)
 
     PhaseState st;
@@ -1044,7 +1194,12 @@ void Engine::step(std::vector<Member *> &retired)
     // host round trip per sweep
     bool use_graph = cfg.cuda_graphs && !tm.on;
     SweepGraph sg;
-    for (;;) {
+    if (cfg.coloring) {
+        colored_phase(st, proto, TW, wide, narrow, st_dev, bc, tm, sweeps, t_kernel,
+                      launches_kernel, account_sweep);
+        ndone = M;
+    }
+    for (; !cfg.coloring;) {
         int ran = 0, per_sweep = 0;
         const bool fs = first;  // this round is the table-free first sweep
         first = false;
@@ -1242,6 +1397,13 @@ void Engine::step(std::vector<Member *> &retired)
     double t_coarsen = 0.0, coarsen_bytes = 0.0;
     std::vector<int64_t> gptr_next(M + 1, 0), gnnz_next(M + 1, 0);
     if (nkeep > 0) {
+        // Exact widths of the induction from the largest community degree: an induced weight
+        // A'_ab and every sum of the induction's tables are at most deg_a (Eq. 2), so the
+        // tables take 32-bit sums when every deg_a < 2^32 and the next graph keeps int32
+        // weights when every deg_a < 2^31.
+        kernels += launch_max_delta(deg.p, n, &d_sc->dmax, s, lc);
+        const u64 cmax = read_one(&d_sc->dmax);
+        const bool narrow_c = !cfg.wide_sums && cmax < ((u64)1 << 32);
         ensure(c_csize, n);
         ensure(c_moff, (size_t)n + 1);
         ensure(c_cursor, n);
@@ -1272,8 +1434,6 @@ void Engine::step(std::vector<Member *> &retired)
         cbins.gcap = b_gcap.p;
         cbins.goff = b_goff.p;
         cbins.glog2 = b_glog2.p;
-        cbins.gcnt = b_gcnt.p;
-        cbins.gdone = b_gdone.p;
         cbins.plog2 = b_plog2.p;
         cbins.hoff = b_hoff.p;
         const int64_t k = k_next;
@@ -1296,7 +1456,7 @@ void Engine::step(std::vector<Member *> &retired)
         kernels += launch_coarsen_rowptr(k, cb, rp_next.p, s);
         sync_scalars();
         const int64_t nnz_next = read_one(rp_next.p + k);
-        const int wb_next = tw_max <= (u64)INT32_MAX ? 4 : 8;
+        const int wb_next = cmax <= (u64)INT32_MAX ? 4 : 8;
         DBuf<int32_t> col_next;
         DBuf<unsigned char> w_next;
         col_next.reset(&A, (size_t)nnz_next);
@@ -2189,6 +2349,10 @@ static int check_config(louvain_config &c, std::string &msg)
         msg = "chunk_entries must be a power of two in [32, 4096]";
         return LOUVAIN_ERR_INVALID_ARG;
     }
+    if (c.coloring != 0 && c.coloring != 1) {
+        msg = "coloring must be 0 or 1";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
     if (c.part_keys == 0) c.part_keys = kPartKeys;
     if (c.part_keys < 64 || c.part_keys > (1 << 30)) {
         msg = "part_keys must be in [64, 2^30]";
@@ -2570,6 +2734,10 @@ int louvain_run_batch(louvain_handle *h, int32_t num_graphs, const int64_t *grap
         h->err = "the handle is serving: use louvain_submit / louvain_poll";
         return LOUVAIN_ERR_INVALID_ARG;
     }
+    if (h->cfg.coloring) {
+        h->err = "the colouring variant runs one graph at a time (louvain_run)";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
     if (num_graphs > LOUVAIN_MAX_BATCH_GRAPHS) {
         h->err = "more graphs than LOUVAIN_MAX_BATCH_GRAPHS";
         return LOUVAIN_ERR_TOO_LARGE;
@@ -2642,6 +2810,10 @@ int louvain_serve_open(louvain_handle *h, uint64_t hbm_budget_bytes, int max_slo
     }
     if (max_slots < 1 || hbm_budget_bytes == 0) {
         h->err = "max_slots must be >= 1 and the budget above 0";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (h->cfg.coloring) {
+        h->err = "the colouring variant runs one graph at a time (louvain_run)";
         return LOUVAIN_ERR_INVALID_ARG;
     }
     Server *S = new (std::nothrow) Server();

@@ -9,8 +9,10 @@
 // aggregated directly in a hash table keyed by the target community:
 //   1. community sizes and next-level delta (= deg of the old community),
 //   2. member lists by counting sort, flattened entry offsets of each community,
-//   3. per community: a warp with a shared-memory table (few entries) or CTA chunks with
-//      a shared table merged into a global table (many entries),
+//   3. per community: a warp, a CTA or a cluster with a shared-memory table, or (the
+//      communities with the most entries) CTA chunks each aggregated in shared memory whose
+//      distinct (target, sum) pairs are then grouped by a hash partition of the target and
+//      merged partition by partition in shared memory,
 //   4. row offsets by prefix sum, then compaction into the next CSR.
 // Rows of the induced graph are not sorted; nothing downstream depends on their order.
 #include <climits>
@@ -143,6 +145,12 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_bin(int64_t k, const int32_t
     }
 }
 
+// A multi-chunk community's pairs are split over 2^l hash partitions of the target, 2^l the
+// smallest power of two leaving at most kCPartPairs of its entries per partition on average
+// (its pairs never outnumber its entries), at most 2^kCMaxPartLog2.
+constexpr int64_t kCPartPairs = 4096;
+constexpr int kCMaxPartLog2 = 20;
+
 __global__ void k_cbig_prep(int nb, const int32_t *blist, const int32_t *moff, const int64_t *mpre,
                             int64_t k, int chunk, int32_t *nch, int64_t *gcap, int32_t *glog2)
 {
@@ -150,17 +158,22 @@ __global__ void k_cbig_prep(int nb, const int32_t *blist, const int32_t *moff, c
         const int64_t e = comm_entries(moff, mpre, blist[b]);
         const int64_t c = (e + chunk - 1) / chunk;
         nch[b] = (int32_t)c;
-        if (c > 1) {
-            const int64_t need = 2 * (e < k ? e : k);
-            int l = 1;
-            while (((int64_t)1 << l) < need) l++;
-            gcap[b] = (int64_t)1 << l;
-            glog2[b] = l;
-        } else {
-            gcap[b] = 0;
-            glog2[b] = 0;
-        }
+        int l = 0;
+        if (c > 1)
+            while (l < kCMaxPartLog2 && (kCPartPairs << l) < e) l++;
+        gcap[b] = c > 1 ? (int64_t)1 << l : 0;
+        glog2[b] = l;
     }
+}
+
+// Community of every partition: warp b fills partitions goff[b] .. goff[b + 1].
+__global__ void k_cpart_fill(int nb, const int64_t *goff, int32_t *partb)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = warp; b < nb; b += nwarps)
+        for (int64_t q = goff[b] + lane; q < goff[b + 1]; q += 32) partb[q] = (int32_t)b;
 }
 
 template <typename WT>
@@ -252,6 +265,7 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
             keys[s] = -1;
             vals[s] = 0;
         }
+        __syncwarp();  // every lane has read the count before it is reset
         if (lane == 0) {
             if (valid) A.ccnt[a] = m;
             *cnt = 0;
@@ -435,22 +449,26 @@ struct CBigArgs {
     const int32_t *chunk_b;
     const int32_t *chunk_first;
     const int32_t *nch;
-    const int64_t *goff;
-    const int32_t *glog2;
-    int32_t *gcnt;
-    int32_t *gdone;
-    int32_t *gkeys;
-    void *gvals;
-    int32_t *glist;
+    const int64_t *pbase;   // first partition of every community (goff)
+    const int32_t *plog2;   // log2 of its partition count
+    int32_t *pcnt;          // pairs per partition
+    const int64_t *poff;    // exclusive scan of pcnt
+    int32_t *pcur;          // scatter cursor per partition
+    const int32_t *partb;   // community of every partition
+    int64_t nparts;
+    int32_t *chm;           // distinct pairs of every chunk
+    int32_t *pk;            // pairs grouped by partition
+    void *pv;
     int chunk;
     int nchunks;
 };
 
 constexpr int kCHugeBlock = 512;
 
-// Communities with the most entries: CTA chunks of `chunk` flattened entries merged in a
-// global table (a single-chunk community writes its row directly); k_coarsen_huge_extract
-// then writes the rows of multi-chunk communities, every chunk CTA taking a slice.
+// Communities with the most entries, phase A: CTA chunks of `chunk` flattened entries, each
+// aggregated in a shared table.  A one-chunk community writes its row directly.  A chunk of
+// a multi-chunk community leaves its distinct (target, sum) pairs in its own slice of the
+// community's temporary row and counts them per hash partition of the target.
 template <typename WT, typename VT>
 __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A, CBigArgs B)
 {
@@ -477,6 +495,7 @@ __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A,
         const int64_t cb = tb + (int64_t)q * B.chunk;
         const int64_t ce = min(te, cb + (int64_t)B.chunk);
         int32_t p = pb;
+        if (cb > tb) p = find_member(A.mpre, pb, pe, cb);  // the member holding entry cb
         for (int64_t t = cb + threadIdx.x; t < ce; t += kCHugeBlock) {
             int32_t key;
             i64 wv;
@@ -485,67 +504,99 @@ __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A,
         }
         __syncthreads();
         const int m = s_cnt;
-        if (nch == 1) {
-            for (int r = threadIdx.x; r < m; r += kCHugeBlock) {
-                const int s = list[r];
-                A.tmp_col[tb + r] = keys[s];
-                ((VT *)A.tmp_w)[tb + r] = vals[s];
-                keys[s] = -1;
-                vals[s] = 0;
-            }
-            if (threadIdx.x == 0) A.ccnt[a] = m;
-        } else {
-            const int64_t off = B.goff[b];
-            const int l2 = B.glog2[b];
-            int32_t *gk = B.gkeys + off;
-            VT *gv = (VT *)B.gvals + off;
-            int32_t *gl = B.glist + off;
-            // claims appended a warp at a time (warp-uniform loop): one list counter per
-            // community takes every distinct key
-            for (int r0 = threadIdx.x & ~31; r0 < m; r0 += kCHugeBlock) {
-                const int r = r0 + (threadIdx.x & 31);
-                bool claimed = false;
-                int gs = 0;
-                if (r < m) {
-                    const int s = list[r];
-                    const int32_t key = keys[s];
-                    const VT v = vals[s];
-                    keys[s] = -1;
-                    vals[s] = 0;
-                    claimed = tbl_insert_claim<VT>(gk, gv, l2, key, v, A.err, gs);
-                }
-                warp_append(claimed, gs, gl, &B.gcnt[b]);
-            }
+        const int64_t out = nch == 1 ? tb : cb;  // a one-chunk community: its row
+        const int pl = B.plog2[b];
+        int32_t *pc = nch == 1 ? nullptr : B.pcnt + B.pbase[b];
+        for (int r = threadIdx.x; r < m; r += kCHugeBlock) {
+            const int s = list[r];
+            const int32_t key = keys[s];
+            A.tmp_col[out + r] = key;
+            ((VT *)A.tmp_w)[out + r] = vals[s];
+            keys[s] = -1;
+            vals[s] = 0;
+            if (pc) atomicAdd(&pc[part_of(key, pl)], 1);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();  // every thread has read the count before it is reset
+        if (threadIdx.x == 0) {
+            if (nch == 1) A.ccnt[a] = m;
+            else B.chm[c] = m;
+            if (nch > 1 && q == 0) A.ccnt[a] = 0;  // phase C counts the merged row
+            s_cnt = 0;
+        }
         __syncthreads();
     }
 }
 
-// Rows of multi-chunk communities: chunk q of community b writes list positions
-// [q * chunk, (q + 1) * chunk) of its global table (the list order is the row order).
+// Phase B: every chunk's pairs to their partition's place in (pk, pv).
 template <typename VT>
-__global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge_extract(
-    CBigArgs B, const int32_t *moff, const int64_t *mpre, int32_t *ccnt, int32_t *tmp_col,
-    void *tmp_w)
+__global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge_scatter(CBigArgs B,
+                                                                      const int32_t *moff,
+                                                                      const int64_t *mpre,
+                                                                      const int32_t *tmp_col,
+                                                                      const void *tmp_w)
 {
     for (int c = blockIdx.x; c < B.nchunks; c += gridDim.x) {
         const int b = B.chunk_b[c];
         if (B.nch[b] == 1) continue;
         const int32_t a = B.blist[b];
         const int q = c - B.chunk_first[b];
-        const int64_t tb = mpre[moff[a]];
-        const int64_t off = B.goff[b];
-        const int gm = B.gcnt[b];
-        const int64_t pb = (int64_t)q * B.chunk;
-        const int64_t pe = min((int64_t)gm, pb + B.chunk);
-        for (int64_t p = pb + threadIdx.x; p < pe; p += kCHugeBlock) {
-            const int s = B.glist[off + p];
-            tmp_col[tb + p] = B.gkeys[off + s];
-            ((VT *)tmp_w)[tb + p] = ((const VT *)B.gvals)[off + s];
+        const int64_t cb = mpre[moff[a]] + (int64_t)q * B.chunk;
+        const int m = B.chm[c];
+        const int pl = B.plog2[b];
+        const int64_t base = B.pbase[b];
+        for (int r = threadIdx.x; r < m; r += kCHugeBlock) {
+            const int32_t key = tmp_col[cb + r];
+            const int64_t part = base + part_of(key, pl);
+            const int64_t pos = B.poff[part] + atomicAdd(&B.pcur[part], 1);
+            B.pk[pos] = key;
+            ((VT *)B.pv)[pos] = ((const VT *)tmp_w)[cb + r];
         }
-        if (q == 0 && threadIdx.x == 0) ccnt[a] = gm;
+    }
+}
+
+// Phase C: one CTA per partition merges its pairs in a shared table (merge_partition splits a
+// crowded partition into residue classes) and appends the distinct targets with their sums to
+// its community's row; the order of a row's entries is left open.
+template <typename WT, typename VT>
+__global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge_merge(CoarsenArgs<WT> A, CBigArgs B)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int log2cap = kPartTableLog2;
+    constexpr int cap = 1 << log2cap;
+    constexpr int thresh = cap - 2 * kCHugeBlock;
+    VT *vals = (VT *)smem;
+    int *keys = (int *)(vals + cap);
+    int *list = keys + cap;
+    __shared__ int s_base;
+    for (int s = threadIdx.x; s < cap; s += kCHugeBlock) {
+        keys[s] = -1;
+        vals[s] = 0;
+    }
+    __syncthreads();
+    for (int64_t q = blockIdx.x; q < B.nparts; q += gridDim.x) {
+        const int64_t lo = B.poff[q], hi = B.poff[q + 1];
+        if (lo == hi) continue;
+        const int32_t a = B.blist[B.partb[q]];
+        const int64_t tb = A.mpre[A.moff[a]];
+        auto for_pairs = [&](auto f) {
+            for (int64_t r = lo + threadIdx.x; r < hi; r += kCHugeBlock)
+                f(B.pk[r], ((const VT *)B.pv)[r]);
+        };
+        auto emit = [&](int m) {
+            if (threadIdx.x == 0) s_base = atomicAdd(&A.ccnt[a], m);
+            __syncthreads();
+            const int64_t o = tb + s_base;
+            for (int r = threadIdx.x; r < m; r += kCHugeBlock) {
+                const int s = list[r];
+                A.tmp_col[o + r] = keys[s];
+                ((VT *)A.tmp_w)[o + r] = vals[s];
+                keys[s] = -1;
+                vals[s] = 0;
+            }
+            __syncthreads();  // s_base is read before the next class sets it
+        };
+        merge_partition<kCHugeBlock, VT>(keys, vals, list, log2cap, thresh, A.err, for_pairs,
+                                         emit);
     }
 }
 
@@ -774,19 +825,31 @@ static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *n
                 break;
             }
         } else if (sp.kind == BIN_CHUNKED && bins.nchunks > 0) {
-            CBigArgs B{rows,       bins.chunk_b, bins.chunk_first, bins.nch,   bins.goff,
-                       bins.glog2, bins.gcnt,    bins.gdone,       bins.gkeys, bins.gvals,
-                       bins.glist, bins.chunk,   bins.nchunks};
+            CBigArgs B{rows,        bins.chunk_b, bins.chunk_first, bins.nch,
+                       bins.goff,   bins.glog2,   bins.cpcnt,       bins.cpoff,
+                       bins.cpcur,  bins.cpartb,  bins.gslots,      bins.cchm,
+                       bins.cpk,    bins.cpv,     bins.chunk,       bins.nchunks};
             const int l2 = 31 - __builtin_clz(2 * bins.chunk);
             const size_t smem = ctable_bytes<VT>(l2, true);
             const int grid = cta_grid(k_coarsen_huge<WT, VT>, kCHugeBlock, smem, bins.nchunks, lc,
                                       "k_coarsen_huge");
             k_coarsen_huge<WT, VT><<<grid, kCHugeBlock, smem, s>>>(A, B);
             note_launch("k_coarsen_huge");
-            k_coarsen_huge_extract<VT><<<grid, kCHugeBlock, 0, s>>>(B, cb.moff, cb.mpre, cb.ccnt,
-                                                                   cb.tmp_col, cb.tmp_w);
-            note_launch("k_coarsen_huge_extract");
-            launched += 2;
+            launched++;
+            if (bins.gslots > 0) {  // multi-chunk communities: scatter by partition, merge
+                launched += exclusive_scan<int64_t>(I32AsI64In{bins.cpcnt}, bins.gslots, bins.cpoff,
+                                                    bins.cpscr, s);
+                k_coarsen_huge_scatter<VT><<<grid, kCHugeBlock, 0, s>>>(B, cb.moff, cb.mpre,
+                                                                       cb.tmp_col, cb.tmp_w);
+                note_launch("k_coarsen_huge_scatter");
+                const size_t msmem = ctable_bytes<VT>(kPartTableLog2, true);
+                const int64_t mgrid_want = bins.gslots < (int64_t)INT32_MAX ? bins.gslots : INT32_MAX;
+                const int mgrid = cta_grid(k_coarsen_huge_merge<WT, VT>, kCHugeBlock, msmem,
+                                           (int)mgrid_want, lc, "k_coarsen_huge_merge");
+                k_coarsen_huge_merge<WT, VT><<<mgrid, kCHugeBlock, msmem, s>>>(A, B);
+                note_launch("k_coarsen_huge_merge");
+                launched += 2;
+            }
         }
     }
     return launched;
@@ -817,6 +880,15 @@ int launch_coarsen_bigprep(int64_t k, CoarsenBufs &cb, Bins &bins, cudaStream_t 
                                         cb.scratch32, s);
     launched += exclusive_scan<int64_t>(ArrayIn<int64_t>{bins.gcap}, nb, bins.goff, cb.scratch64, s);
     return launched;
+}
+
+int launch_coarsen_partfill(Bins &bins, cudaStream_t s, const LaunchCfg &lc)
+{
+    const int nb = bins.nlist[kChunkedBin];
+    if (nb == 0 || bins.gslots == 0) return 0;
+    k_cpart_fill<<<grid_for(nb, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(nb, bins.goff,
+                                                                             bins.cpartb);
+    return 1;
 }
 
 int launch_coarsen_rowptr(int64_t k, CoarsenBufs &cb, int64_t *rp_next, cudaStream_t s)

@@ -504,6 +504,8 @@ struct BinArgs {
     int32_t *list;
     const int32_t *vg;      // batch: graph of every vertex (nullptr for one graph)
     const LevelCtl *gctl;   // batch: rows of graphs whose phase stopped are left out
+    const int32_t *color;   // colouring variant: only vertices of colour cls are binned
+    int32_t cls;
 };
 
 __device__ __forceinline__ int bin_of(int64_t d, const int64_t *upper)
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, Bi
         const int64_t i = i0 + threadIdx.x;
         int bin = -1;
         int64_t d = 0;
-        if (i < n && !(ba.vg && ba.gctl[ba.vg[i]].done)) {
+        if (i < n && !(ba.vg && ba.gctl[ba.vg[i]].done) && !(ba.color && ba.color[i] != ba.cls)) {
             d = rp[i + 1] - rp[i];
             bin = bin_of(d, ba.upper);
         }
@@ -588,11 +590,14 @@ __global__ void __launch_bounds__(kBlock) k_bin(int64_t n, const int64_t *rp, Bi
     }
 }
 
-static BinArgs bin_args(const Bins &b, const int32_t *vg, const LevelCtl *gctl)
+static BinArgs bin_args(const Bins &b, const int32_t *vg, const LevelCtl *gctl,
+                        const int32_t *color, int32_t cls)
 {
     BinArgs ba;
     ba.vg = vg;
     ba.gctl = gctl;
+    ba.color = color;
+    ba.cls = cls;
     for (int t = 0; t < kNumBins - 1; t++) ba.upper[t] = b.upper[t];
     for (int t = 0; t <= kNumBins; t++) ba.off[t] = b.off[t];
     ba.list = b.list;
@@ -600,22 +605,22 @@ static BinArgs bin_args(const Bins &b, const int32_t *vg, const LevelCtl *gctl)
 }
 
 int launch_bin_count(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc,
-                     const int32_t *vg, const LevelCtl *gctl)
+                     const int32_t *vg, const LevelCtl *gctl, const int32_t *color, int32_t cls)
 {
     cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * (16 + 2 * kNumBins), s);
     if (g.n == 0) return 0;
     k_bin<false><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        g.n, g.rp, bin_args(b, vg, gctl), b.counts);
+        g.n, g.rp, bin_args(b, vg, gctl, color, cls), b.counts);
     return 1;
 }
 
 int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc,
-                    const int32_t *vg, const LevelCtl *gctl)
+                    const int32_t *vg, const LevelCtl *gctl, const int32_t *color, int32_t cls)
 {
     cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * 16, s);
     if (g.n == 0) return 0;
     k_bin<true><<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        g.n, g.rp, bin_args(b, vg, gctl), b.counts);
+        g.n, g.rp, bin_args(b, vg, gctl, color, cls), b.counts);
     return 1;
 }
 
@@ -1016,6 +1021,161 @@ static int post_merge_impl(const DevGraph &g, const PhaseState &st, const int32_
     k_qn_squares<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(g.n, st.deg, vg, stats);
     k_qn_finalize<<<(G + 127) / 128, 128, 0, s>>>(G, stats, ctl);
     return k + 3;
+}
+
+// ------------------------------------------------------------------ colouring variant
+// Lu et al.'s colouring heuristic (named, not defined, in Sec. 7 of the paper): a
+// distance-1 colouring by Jones-Plassmann rounds, then sweeps that take the colour classes
+// one after the other.  The priority of vertex v is the output function of SplitMix64
+// (Steele, Lea and Flood 2014) applied to v, a bijection of 64-bit values, so no two
+// vertices tie.
+__device__ __forceinline__ u64 color_priority(int64_t v)
+{
+    u64 z = (u64)v + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// One warp per uncoloured vertex: picked when no uncoloured non-loop neighbour has a higher
+// priority.  Picks of one round are pairwise non-adjacent, so assigning their colours in the
+// next kernel reads only colours of earlier rounds.
+__global__ void __launch_bounds__(kBlock) k_color_pick(int64_t n, const int64_t *rp,
+                                                       const int32_t *col, const int32_t *color,
+                                                       int32_t *pick, u64 *counts)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    u64 unc = 0, picked = 0;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        if (color[v] >= 0) {
+            if (lane == 0) pick[v] = 0;
+            continue;
+        }
+        const u64 pv = color_priority(v);
+        bool beaten = false;
+        for (int64_t k = rp[v] + lane; k < rp[v + 1] && !beaten; k += 32) {
+            const int32_t u = col[k];
+            beaten = u != (int32_t)v && color[u] < 0 && color_priority(u) > pv;
+        }
+        const bool top = !__any_sync(0xffffffffu, beaten);
+        if (lane == 0) {
+            pick[v] = top;
+            unc += 1;
+            picked += top;
+        }
+    }
+    if (lane == 0) {
+        if (unc) atomicAdd(&counts[0], unc);
+        if (picked) atomicAdd(&counts[1], picked);
+    }
+}
+
+// One warp per picked vertex: the smallest colour missing among its neighbours, found 64
+// colours at a time (a vertex of d entries needs at most d + 1 colours).
+__global__ void __launch_bounds__(kBlock) k_color_assign(int64_t n, const int64_t *rp,
+                                                         const int32_t *col, int32_t *color,
+                                                         const int32_t *pick, int32_t *ncolors)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int top = 0;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        if (!pick[v]) continue;
+        for (int base = 0;; base += 64) {
+            u64 used = 0;
+            for (int64_t k = rp[v] + lane; k < rp[v + 1]; k += 32) {
+                const int32_t u = col[k];
+                const int c = u != (int32_t)v ? color[u] - base : -1;
+                if (c >= 0 && c < 64) used |= (u64)1 << c;
+            }
+            const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)used);
+            const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(used >> 32));
+            const u64 all = ((u64)hi << 32) | lo;
+            if (all != ~(u64)0) {
+                const int c = base + __ffsll((long long)~all) - 1;
+                if (lane == 0) color[v] = c;
+                top = max(top, c + 1);
+                break;
+            }
+        }
+    }
+    if (lane == 0 && top) atomicMax(ncolors, top);
+}
+
+int launch_color_pick(const DevGraph &g, const int32_t *color, int32_t *pick, u64 *counts,
+                      cudaStream_t s, const LaunchCfg &lc)
+{
+    cudaMemsetAsync(counts, 0, 2 * sizeof(u64), s);
+    if (g.n == 0) return 0;
+    k_color_pick<<<grid_for(g.n, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(g.n, g.rp, g.col,
+                                                                             color, pick, counts);
+    return 1;
+}
+
+int launch_color_assign(const DevGraph &g, int32_t *color, const int32_t *pick, int32_t *ncolors,
+                        cudaStream_t s, const LaunchCfg &lc)
+{
+    if (g.n == 0) return 0;
+    k_color_assign<<<grid_for(g.n, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(
+        g.n, g.rp, g.col, color, pick, ncolors);
+    return 1;
+}
+
+// Moves of the vertices of one colour class: deg / size follow (remove / insert with
+// atomics), then C <- C_next for them.
+__global__ void __launch_bounds__(kBlock) k_apply_class(int64_t n, int32_t *C, const int32_t *Cnext,
+                                                        i64 *deg, int32_t *size, const i64 *delta,
+                                                        const int32_t *color, int32_t cls,
+                                                        u64 *moved)
+{
+    u64 mv = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (color[i] != cls) continue;
+        const int32_t a = C[i], b = Cnext[i];
+        if (a == b) continue;
+        const i64 d = delta[i];
+        atomicAdd((u64 *)&deg[b], (u64)d);
+        atomicAdd((u64 *)&deg[a], (u64)(-d));
+        atomicAdd(&size[b], 1);
+        atomicSub(&size[a], 1);
+        C[i] = b;
+        mv++;
+    }
+    mv = sum_reduce(mv, 32);
+    if ((threadIdx.x & 31) == 0 && mv) atomicAdd(moved, mv);
+}
+
+int launch_apply_class(int64_t n, const PhaseState &st, u64 *moved, cudaStream_t s,
+                       const LaunchCfg &lc)
+{
+    if (n == 0) return 0;
+    k_apply_class<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+        n, st.C, st.Cnext, st.deg, st.size, st.delta, st.color, st.cls, moved);
+    return 1;
+}
+
+template <typename WT>
+static int qn_one_impl(const DevGraph &g, const PhaseState &st, SweepStats *stats, LevelCtl *ctl,
+                       cudaStream_t s, const LaunchCfg &lc)
+{
+    k_qn_rows<WT><<<grid_for(g.n, kBlock / 32, lc.max_blocks), kBlock, 0, s>>>(
+        g.n, g.rp, g.col, (const WT *)g.w, st.C, nullptr, stats);
+    k_qn_squares<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(g.n, st.deg, nullptr,
+                                                                         stats);
+    k_qn_finalize<<<1, 128, 0, s>>>(1, stats, ctl);
+    return 3;
+}
+
+int launch_qn_one(const DevGraph &g, const PhaseState &st, SweepStats *stats, LevelCtl *ctl,
+                  cudaStream_t s, const LaunchCfg &lc)
+{
+    if (g.n == 0) return 0;
+    if (g.wbytes == 4) return qn_one_impl<int32_t>(g, st, stats, ctl, s, lc);
+    return qn_one_impl<i64>(g, st, stats, ctl, s, lc);
 }
 
 int launch_post_merge(const DevGraph &g, const PhaseState &st, const int32_t *vg, const i64 *gtw,

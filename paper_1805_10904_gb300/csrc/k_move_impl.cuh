@@ -61,6 +61,8 @@ struct MoveArgs {
     const int32_t *vg;    // graph of every vertex in a batch of graphs, nullptr for one graph
     const i64 *gtw;       // 2W of every graph of the batch
     const LevelCtl *gctl; // phase controller of every graph; rows of finished graphs are frozen
+    const int32_t *color = nullptr;  // colouring variant: only colour `cls` decides
+    int32_t cls = 0;
 };
 
 // Graph context of vertex i: its graph, that graph's 2W, and whether its phase has stopped.
@@ -236,7 +238,8 @@ __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small
             v_sq = (u128)(u64)dg * (u64)dg;
             const int64_t rb = A.rp[i];
             const int64_t d = A.rp[i + 1] - rb;
-            const bool fz = frozen<BT>(A, g);
+            // frozen graph, or a vertex of another colour class: it keeps its label
+            const bool fz = frozen<BT>(A, g) || (A.color && A.color[i] != A.cls);
             if (d <= small_max && !fz) {
                 const i64 tw = tw_of<BT>(A, g);
                 const int32_t a = A.C[i];
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small
                 v_int = (u64)(e_a + loop);
                 cand += (u64)m;
             } else if (d <= small_max) {
-                A.Cnext[i] = A.C[i];  // frozen graph: nothing moves
+                A.Cnext[i] = A.C[i];  // frozen graph or other class: nothing moves
             }
         }
         if constexpr (!BT) {
@@ -465,8 +468,11 @@ __device__ __forceinline__ void gather_chunk(const MoveArgs<WT> &A, int32_t i,
 // Software pipeline over the CTA's rows: while row v finishes (barrier, candidate scan,
 // argmax), the next row's vertex id, entry range, first chunk of columns / weights and its
 // label gathers are already in flight, issued stage by stage so no load waits on another.
+// At most 64 registers a thread for every block size: 128- and 256-thread CTAs then keep 8
+// and 4 rows in flight on an SM (register-limited to 6 and 3 otherwise), and two
+// 512-thread CTAs fit.
 template <int BLOCK, typename WT, typename GT, typename VT, bool BT>
-__global__ void __launch_bounds__(BLOCK, BLOCK == 512 ? 2 : 1)
+__global__ void __launch_bounds__(BLOCK, 2048 / BLOCK >= 2 ? 2048 / BLOCK / 2 : 1)
     k_move_cta(MoveArgs<WT> A, const int32_t *verts, int nverts, int log2cap, int slot)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1441,6 +1447,8 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
     MoveArgs<WT> A{g.n,   g.rp,     g.col,  (const WT *)g.w, st.C,  st.deg,  st.size,
                    st.delta, tw,    st.Cnext, stats,         err,   bc.vg,   bc.gtw,
                    bc.gctl};
+    A.color = st.color;
+    A.cls = st.cls;
     const bool timed = tm && tm->on;
     int launched = 0;
     // the bins read the same snapshot and write disjoint rows: with a stream set they run

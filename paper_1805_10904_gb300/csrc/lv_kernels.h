@@ -29,6 +29,9 @@ struct PhaseState {
     i64 *deg = nullptr;        // deg_c (Eq. 2)
     int32_t *size = nullptr;   // members of c
     i64 *delta = nullptr;      // weighted degree of each vertex
+    // colouring variant: only the vertices of colour `cls` decide in this launch
+    const int32_t *color = nullptr;
+    int32_t cls = 0;
 };
 
 // Degree bins of one phase.  Bin b holds the rows (vertices, or communities when coarsening)
@@ -79,16 +82,21 @@ struct Bins {
     int32_t *chunk_b = nullptr;      // chunked-list index of every chunk
     int nchunks = 0;
     u64 *gloop = nullptr;      // loop weight of every multi-chunk row
-    // graph induction: one global hash table per multi-chunk community
-    int64_t *gcap = nullptr;   // slots (0 for single-chunk communities)
-    int64_t *goff = nullptr;   // exclusive scan of gcap (nb + 1)
+    // graph induction: a multi-chunk community merges its chunks' distinct (target, sum)
+    // pairs by hash partition of the target: gcap[b] partitions (0 for one chunk), goff
+    // their exclusive scan (first partition of each community), glog2 = log2 gcap
+    int64_t *gcap = nullptr;
+    int64_t *goff = nullptr;
     int32_t *glog2 = nullptr;
-    int32_t *gcnt = nullptr;
-    int32_t *gdone = nullptr;
-    int32_t *gkeys = nullptr;
-    void *gvals = nullptr;     // u32 or u64 per slot
-    int32_t *glist = nullptr;
-    int64_t gslots = 0;
+    int64_t gslots = 0;        // partitions in all
+    int32_t *cpcnt = nullptr;  // pairs per partition
+    int64_t *cpoff = nullptr;  // their exclusive scan (gslots + 1)
+    int32_t *cpcur = nullptr;  // scatter cursor per partition
+    int32_t *cpartb = nullptr; // community (chunked-list index) of every partition
+    int32_t *cchm = nullptr;   // distinct pairs of every chunk
+    int32_t *cpk = nullptr;    // pairs grouped by partition: targets
+    void *cpv = nullptr;       //                              sums (u32 or u64)
+    int64_t *cpscr = nullptr;  // scan scratch for the partition offsets
     // decision of multi-chunk rows, one work item ("slice") per partition of a row's keys:
     // partial argmax (gain, label, e_{i->C(i)}) and distinct keys of every slice; in the
     // first sweep of a phase one partial per chunk instead, pcnt then holding the chunk's
@@ -182,10 +190,13 @@ int launch_vertex_following(const DevGraph &g, const PhaseState &st, cudaStream_
 // Two passes: count rows and entries per bin (then the host reads counts and sets off[]),
 // fill the list grouped by bin.  In a batch (vg, gctl given) rows of graphs whose phase has
 // stopped are left out of every bin.
+// color (optional): only the vertices of colour cls are binned
 int launch_bin_count(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc,
-                     const int32_t *vg = nullptr, const LevelCtl *gctl = nullptr);
+                     const int32_t *vg = nullptr, const LevelCtl *gctl = nullptr,
+                     const int32_t *color = nullptr, int32_t cls = 0);
 int launch_bin_fill(const DevGraph &g, Bins &b, cudaStream_t s, const LaunchCfg &lc,
-                    const int32_t *vg = nullptr, const LevelCtl *gctl = nullptr);
+                    const int32_t *vg = nullptr, const LevelCtl *gctl = nullptr,
+                    const int32_t *color = nullptr, int32_t cls = 0);
 int launch_big_prep(const DevGraph &g, Bins &b, int64_t *scratch64, int32_t *scratch32,
                     cudaStream_t s, const LaunchCfg &lc);
 int launch_big_fill(Bins &b, cudaStream_t s, const LaunchCfg &lc);
@@ -204,6 +215,22 @@ int launch_apply(int64_t n, const PhaseState &st, const LevelCtl *ctl, const int
 // community joins it when the move's gain is positive), applied to every vertex of g, then
 // the exact Qn of the merged state into ctl[g].qn_final for all G controllers.  stats must
 // be zero on entry and are zero on return.
+// Colouring variant (one graph).  One Jones-Plassmann round: pick marks every uncoloured
+// vertex whose priority is above that of each uncoloured non-loop neighbour, counting the
+// uncoloured vertices (counts[0]) and the picks (counts[1]); assign gives every pick the
+// smallest colour none of its neighbours has and raises *ncolors to cover it.
+int launch_color_pick(const DevGraph &g, const int32_t *color, int32_t *pick, u64 *counts,
+                      cudaStream_t s, const LaunchCfg &lc);
+int launch_color_assign(const DevGraph &g, int32_t *color, const int32_t *pick, int32_t *ncolors,
+                        cudaStream_t s, const LaunchCfg &lc);
+// Apply the proposals of the vertices of colour st.cls (deg / size follow), adding the number
+// that moved to *moved.
+int launch_apply_class(int64_t n, const PhaseState &st, u64 *moved, cudaStream_t s,
+                       const LaunchCfg &lc);
+// Exact Qn of the current state of one graph into ctl->qn_final (stats must be zero on entry
+// and are zero again on return).
+int launch_qn_one(const DevGraph &g, const PhaseState &st, SweepStats *stats, LevelCtl *ctl,
+                  cudaStream_t s, const LaunchCfg &lc);
 int launch_post_merge(const DevGraph &g, const PhaseState &st, const int32_t *vg, const i64 *gtw,
                       i64 tw, bool wide, SweepStats *stats, LevelCtl *ctl, int G, cudaStream_t s,
                       const LaunchCfg &lc);
@@ -305,6 +332,8 @@ int launch_coarsen_stage1(const DevGraph &g, const PhaseState &st, const int32_t
 int launch_coarsen_binfill(int64_t k, CoarsenBufs &cb, Bins &bins, cudaStream_t s,
                            const LaunchCfg &lc);
 // Chunk counts and global-table sizes of the communities of the chunked bin.
+// community of every partition of the multi-chunk communities (bins.cpartb)
+int launch_coarsen_partfill(Bins &bins, cudaStream_t s, const LaunchCfg &lc);
 int launch_coarsen_bigprep(int64_t k, CoarsenBufs &cb, Bins &bins, cudaStream_t s,
                            const LaunchCfg &lc);
 // Stage 2 (after the host read the bin counts): aggregate every community's entries.

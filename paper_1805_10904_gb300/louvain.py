@@ -64,6 +64,7 @@ class Config(ctypes.Structure):
         ("keep_coarse", ctypes.c_int32),
         ("sweep_streams", ctypes.c_int32),
         ("part_keys", ctypes.c_int32),
+        ("coloring", ctypes.c_int32),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
@@ -321,7 +322,7 @@ class Louvain:
                  profile: bool = False, torch_alloc: bool = True, cuda_graphs: bool = True,
                  autotune: bool = False, threshold_mode: int = 0, post_merge: bool = False,
                  alloc_hook=None, keep_coarse: bool = False, sweep_streams: int = 4,
-                 part_keys: int = 0):
+                 part_keys: int = 0, coloring: bool = False):
         lib = load()
         self._lib = lib
         cfg = Config()
@@ -348,6 +349,7 @@ class Louvain:
         cfg.sweep_streams = int(sweep_streams)
         if part_keys:
             cfg.part_keys = int(part_keys)
+        cfg.coloring = int(coloring)
         self.device = device
         # alloc_hook(bytes) -> bool may refuse an allocation (failure-injection tests)
         self.alloc_hook = alloc_hook

@@ -61,9 +61,10 @@ def test_resume_reproduces_later_levels(lv):
 
 
 def test_resume_with_int64_coarse_weights(lv):
-    """2W above 2^31 - 1 makes the induced graphs carry int64 weights."""
+    """Community degrees above 2^31 - 1 make the induced graphs carry int64 weights (every
+    vertex's weighted degree is near 2^29 here, so a community of four already needs them)."""
     b = gg.sbm(3000, 60, 0.1, 0.004, 1, 4, seed=2)
-    heavy = gg.Graph(b.rp, b.col, (b.w.astype(np.int64) * (1 << 20)).astype(np.int32), "heavy")
+    heavy = gg.Graph(b.rp, b.col, (b.w.astype(np.int64) * (1 << 24)).astype(np.int32), "heavy")
     import torch
     full = lv.Louvain(0, keep_coarse=True).run(*[torch.from_numpy(a).cuda()
                                                   for a in (heavy.rp, heavy.col, heavy.w)])
