@@ -61,8 +61,8 @@ struct MoveArgs {
     const int32_t *vg;    // graph of every vertex in a batch of graphs, nullptr for one graph
     const i64 *gtw;       // 2W of every graph of the batch
     const LevelCtl *gctl; // phase controller of every graph; rows of finished graphs are frozen
-    const int32_t *color = nullptr;  // colouring variant: only colour `cls` decides
-    int32_t cls = 0;
+    const int32_t *color;  // colouring variant: only colour `cls` decides (nullptr: all)
+    int32_t cls;
 };
 
 // Graph context of vertex i: its graph, that graph's 2W, and whether its phase has stopped.
@@ -468,11 +468,11 @@ __device__ __forceinline__ void gather_chunk(const MoveArgs<WT> &A, int32_t i,
 // Software pipeline over the CTA's rows: while row v finishes (barrier, candidate scan,
 // argmax), the next row's vertex id, entry range, first chunk of columns / weights and its
 // label gathers are already in flight, issued stage by stage so no load waits on another.
-// At most 64 registers a thread for every block size: 128- and 256-thread CTAs then keep 8
-// and 4 rows in flight on an SM (register-limited to 6 and 3 otherwise), and two
-// 512-thread CTAs fit.
+// 128-thread CTAs are held to 64 registers a thread, so 8 rows are in flight on an SM (6
+// otherwise; 12% faster at R-MAT 26); two 512-thread CTAs fit.  The same cap on 256-thread
+// CTAs (4 rows instead of 3) made them twice as slow at R-MAT 26 and is not applied.
 template <int BLOCK, typename WT, typename GT, typename VT, bool BT>
-__global__ void __launch_bounds__(BLOCK, 2048 / BLOCK >= 2 ? 2048 / BLOCK / 2 : 1)
+__global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 8 : (BLOCK == 512 ? 2 : 1))
     k_move_cta(MoveArgs<WT> A, const int32_t *verts, int nverts, int log2cap, int slot)
 {
     extern __shared__ __align__(16) unsigned char smem[];

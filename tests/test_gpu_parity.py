@@ -323,3 +323,23 @@ def test_heavy_weights_per_level_widths(torch, lv, weights, expect, cfg):
     assert (dmax < 2 ** 32, dmax * tw <= 2 ** 62) == expect
     res, ref = run_both(torch, lv, g, **cfg)
     assert_parity(res, ref)
+
+
+@pytest.mark.parametrize("shift", [(1, 0), (0, 3), (2, 1)])
+def test_unaligned_column_and_weight_arrays(torch, lv, shift):
+    """Column and weight arrays that start 4, 8 or 12 bytes past a 16-byte boundary (views
+    into larger buffers) give the same result in every kernel path."""
+    g = gg.rmat(14, 16, seed=31)
+    d = torch.device("cuda:0")
+
+    def view(a, s):
+        buf = torch.zeros(a.size + s, dtype=torch.int32, device=d)
+        buf[s:] = torch.from_numpy(a).to(d)
+        return buf[s:]
+
+    rp = torch.from_numpy(g.rp).to(d)
+    col, w = view(g.col, shift[0]), view(g.w, shift[1])
+    assert col.data_ptr() % 16 or w.data_ptr() % 16
+    ref = oracle.louvain(g.rp, g.col, g.w)
+    for cfg in ({}, {"bins": (0, 0, 0, 0, 0, 12288)}, {"sweep_streams": 0, "cuda_graphs": False}):
+        assert_parity(lv.Louvain(0, **cfg).run(rp, col, w), ref)
