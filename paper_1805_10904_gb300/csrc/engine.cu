@@ -1428,9 +1428,10 @@ void Engine::step(std::vector<Member *> &retired)
         cb.scratch64 = scratch64.p;
         if (tm.on) CK(cudaEventRecord(coarsen_ev[0], s));
         Bins cbins = narrow_c == narrow ? proto : make_proto(narrow_c);  // table widths of the induction
-        // no cluster bins in the induction: communities above the bin-5 bound take the chunked
-        // bin's partitioned merge, which is faster there (R-MAT 26: 174.7 -> 163.8 ms of
-        // induction per run; the sweeps keep their cluster bins)
+        // no cluster bins in the induction (the community binning folds bins 6-9 into 10):
+        // communities above the bin-5 bound take the chunked bin's partitioned merge, which
+        // is faster there (R-MAT 26: 174.7 -> 163.8 ms of induction per run; the sweeps keep
+        // their cluster bins)
         for (int t = 0; t < 4; t++) cbins.upper[6 + t] = cbins.upper[5];
         cbins.nch = b_nch.p;
         cbins.chunk_first = b_chunk_first.p;

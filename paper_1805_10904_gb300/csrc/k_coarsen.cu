@@ -9,15 +9,14 @@
 // aggregated directly in a hash table keyed by the target community:
 //   1. community sizes and next-level delta (= deg of the old community),
 //   2. member lists by counting sort, flattened entry offsets of each community,
-//   3. per community: a warp, a CTA or a cluster with a shared-memory table, or (the
-//      communities with the most entries) CTA chunks each aggregated in shared memory whose
+//   3. per community: a warp or a CTA with a shared-memory table, or (communities above
+//      the largest CTA table, which take no thread-block clusters here) CTA chunks each
+//      aggregated in shared memory whose
 //      distinct (target, sum) pairs are then grouped by a hash partition of the target and
 //      merged partition by partition in shared memory,
 //   4. row offsets by prefix sum, then compaction into the next CSR.
 // Rows of the induced graph are not sorted; nothing downstream depends on their order.
 #include <climits>
-
-#include <cooperative_groups.h>
 
 #include "lv_common.cuh"
 #include "lv_kernels.h"
@@ -274,59 +273,6 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
     }
 }
 
-// Exclusive prefix sum over the threads of a CTA of BLOCK threads; *total gets the sum.
-template <int BLOCK>
-__device__ __forceinline__ int cta_excl_scan(int v, int *total)
-{
-    __shared__ int s_w[32];
-    __shared__ int s_total;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = v;
-    for (int off = 1; off < 32; off <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += u;
-    }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const int x = lane < BLOCK / 32 ? s_w[lane] : 0;
-        int xi = x;
-        for (int off = 1; off < 32; off <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, xi, off);
-            if (lane >= off) xi += u;
-        }
-        if (lane < BLOCK / 32) s_w[lane] = xi - x;
-        if (lane == 31) s_total = xi;  // lanes >= BLOCK/32 add nothing
-    }
-    __syncthreads();
-    const int res = s_w[warp] + incl - v;
-    *total = s_total;
-    __syncthreads();
-    return res;
-}
-
-// Write the occupied slots of a table of `cap` slots to out[base + ...] in slot order of a
-// CTA-strided walk, clearing them; returns this CTA's count (valid in every thread).
-template <int BLOCK, typename VT>
-__device__ __forceinline__ int drain_table(int *keys, VT *vals, int cap, int32_t *out_col,
-                                           VT *out_w, int64_t base, int rank_off)
-{
-    int mine = 0;
-    for (int s = threadIdx.x; s < cap; s += BLOCK) mine += keys[s] >= 0;
-    int total;
-    int off = cta_excl_scan<BLOCK>(mine, &total) + rank_off;
-    for (int s = threadIdx.x; s < cap; s += BLOCK) {
-        const int key = keys[s];
-        if (key < 0) continue;
-        out_col[base + off] = key;
-        out_w[base + off] = vals[s];
-        off++;
-        keys[s] = -1;
-        vals[s] = 0;
-    }
-    return total;
-}
-
 // One CTA per community with a 2^log2cap-slot table in dynamic shared memory.
 template <int BLOCK, typename WT, typename VT>
 __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const int32_t *clist,
@@ -370,77 +316,6 @@ __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const 
             s_cnt = 0;
         }
         __syncthreads();
-    }
-}
-
-namespace cg = cooperative_groups;
-
-template <int CL>
-struct CLog2 {
-    static constexpr int v = CL <= 1 ? 0 : 1 + CLog2<CL / 2>::v;
-};
-template <>
-struct CLog2<1> {
-    static constexpr int v = 0;
-};
-
-// Large communities: one thread-block cluster per community, the table partitioned over
-// the cluster's distributed shared memory; each CTA writes the occupied slots of its segment
-// after the segments of lower ranks.
-template <int CL, typename WT, typename VT>
-__global__ void __launch_bounds__(1024) k_coarsen_cluster(CoarsenArgs<WT> A, const int32_t *clist,
-                                                          int ncl, int log2cap)
-{
-    constexpr int BLOCK = 1024;
-    constexpr int LOG2CL = CLog2<CL>::v;
-    cg::cluster_group cluster = cg::this_cluster();
-    const unsigned rank = cluster.block_rank();
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int cap = 1 << log2cap;
-    VT *vals = (VT *)smem;
-    int *keys = (int *)(vals + cap);
-    __shared__ int s_cnt;
-    __shared__ int s_off, s_tot;
-    for (int s = threadIdx.x; s < cap; s += BLOCK) {
-        keys[s] = -1;
-        vals[s] = 0;
-    }
-    cluster.sync();
-    const int cid = blockIdx.x / CL, nclu = gridDim.x / CL;
-    const int64_t stride = (int64_t)CL * BLOCK;
-    for (int v = cid; v < ncl; v += nclu) {
-        const int32_t a = clist[v];
-        const int32_t pb = A.moff[a], pe = A.moff[a + 1];
-        const int64_t tb = A.mpre[pb], te = A.mpre[pe];
-        int32_t p = pb;
-        for (int64_t t = tb + (int64_t)rank * BLOCK + threadIdx.x; t < te; t += stride) {
-            int32_t key;
-            i64 wv;
-            flat_entry(A, p, pe, t, key, wv);
-            cluster_insert<VT>(cluster, keys, vals, LOG2CL, log2cap, key, (VT)wv, A.err);
-        }
-        cluster.sync();  // every insert has landed
-        int mine = 0;
-        for (int s = threadIdx.x; s < cap; s += BLOCK) mine += keys[s] >= 0;
-        int total;
-        cta_excl_scan<BLOCK>(mine, &total);
-        if (threadIdx.x == 0) s_cnt = total;
-        cluster.sync();  // every segment's count published
-        if (threadIdx.x == 0) {
-            int off = 0, tot = 0;
-#pragma unroll 1
-            for (int r = 0; r < CL; r++) {
-                const int c = *cluster.map_shared_rank(&s_cnt, r);
-                if (r < (int)rank) off += c;
-                tot += c;
-            }
-            s_off = off;
-            s_tot = tot;
-        }
-        __syncthreads();
-        drain_table<BLOCK, VT>(keys, vals, cap, A.tmp_col, (VT *)A.tmp_w, tb, s_off);
-        if (threadIdx.x == 0 && rank == 0) A.ccnt[a] = s_tot;
-        cluster.sync();  // counts read and tables cleared before the next community
     }
 }
 
@@ -662,7 +537,8 @@ struct I32AsI64In {
 static CBinArgs cbin_args(const Bins &b)
 {
     CBinArgs ba;
-    for (int t = 0; t < kNumBins - 1; t++) ba.upper[t] = b.upper[t];
+    // no cluster bins in the induction: a community above the bin-5 bound goes to bin 10
+    for (int t = 0; t < kNumBins - 1; t++) ba.upper[t] = b.upper[t < 5 ? t : 5];
     for (int t = 0; t <= kNumBins; t++) ba.off[t] = b.off[t];
     ba.list = b.list;
     return ba;
@@ -721,37 +597,6 @@ static int cta_grid(K kernel, int block, size_t smem, int nrows, const LaunchCfg
     return nrows < maxg ? nrows : maxg;
 }
 
-template <int CL, typename K, typename... Args>
-static int cluster_launch(K kernel, size_t smem, int nrows, cudaStream_t s, const char *name,
-                          Args... args)
-{
-    set_dyn_smem(kernel, smem, name);
-    if (CL > 8) cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(1024, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3(CL, 1, 1);
-    int maxc = 0;
-    if (cudaOccupancyMaxActiveClusters(&maxc, kernel, &cfg) != cudaSuccess || maxc < 1) {
-        cudaGetLastError();
-        if (!launch_site()) launch_site() = name;
-        return 0;
-    }
-    const int nclusters = nrows < maxc ? nrows : maxc;
-    cfg.gridDim = dim3((unsigned)(nclusters * CL), 1, 1);
-    cudaLaunchKernelEx(&cfg, kernel, args...);
-    note_launch(name);
-    return 1;
-}
-
 // cn[v] = new_id[C[v]]: the next-level vertex of every vertex, so that the aggregation
 // gathers one label per entry instead of two in a row
 __global__ void k_renumbered_labels(int64_t n, const int32_t *C, const int32_t *new_id,
@@ -803,27 +648,6 @@ static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *n
             }
             note_launch("k_coarsen_cta");
             launched++;
-        } else if (sp.kind == BIN_CLUSTER) {
-            const int l2 = cta_log2cap(bins, bin);
-            const size_t smem = ctable_bytes<VT>(l2);
-            switch (sp.cluster) {
-            case 2:
-                launched += cluster_launch<2>(k_coarsen_cluster<2, WT, VT>, smem, nr, s,
-                                              "k_coarsen_cluster<2>", A, rows, nr, l2);
-                break;
-            case 4:
-                launched += cluster_launch<4>(k_coarsen_cluster<4, WT, VT>, smem, nr, s,
-                                              "k_coarsen_cluster<4>", A, rows, nr, l2);
-                break;
-            case 8:
-                launched += cluster_launch<8>(k_coarsen_cluster<8, WT, VT>, smem, nr, s,
-                                              "k_coarsen_cluster<8>", A, rows, nr, l2);
-                break;
-            default:
-                launched += cluster_launch<16>(k_coarsen_cluster<16, WT, VT>, smem, nr, s,
-                                               "k_coarsen_cluster<16>", A, rows, nr, l2);
-                break;
-            }
         } else if (sp.kind == BIN_CHUNKED && bins.nchunks > 0) {
             CBigArgs B{rows,        bins.chunk_b, bins.chunk_first, bins.nch,
                        bins.goff,   bins.glog2,   bins.cpcnt,       bins.cpoff,

@@ -57,15 +57,19 @@ def test_roofline_traffic_only_for_the_captured_kernel_and_bins():
     import json
     import bench
     with open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")) as f:
-        rec = json.load(f)["kernels"]["k_move_cta<1024>"]
+        kernels = json.load(f)["kernels"]
+    assert kernels
     import hashlib
     src = os.path.join(os.path.dirname(bench.__file__), "paper_1805_10904_gb300", "csrc",
                        "k_move_impl.cuh")
     with open(src, "rb") as f:
-        same_source = hashlib.sha256(f.read()).hexdigest() == rec["source_sha256"]
-    bins, chunk = rec["bins"], rec["chunk_entries"]
-    expected = rec["dram_bytes_per_launch_full"] if same_source else None
-    assert bench.kernel_traffic("k_move_cta<1024>", bins, chunk) == expected
-    assert bench.kernel_traffic("k_move_cta<1024>", bins[:-1] + [bins[-1] // 2], chunk) is None
-    assert bench.kernel_traffic("k_move_cta<1024>", bins, chunk // 2) is None
-    assert bench.kernel_traffic("k_move_cta<256>", bins, chunk) is None
+        sha = hashlib.sha256(f.read()).hexdigest()
+    for name, rec in kernels.items():
+        bins, chunk = rec["bins"], rec["chunk_entries"]
+        expected = rec["dram_bytes_per_launch_full"] if sha == rec["source_sha256"] else None
+        assert bench.kernel_traffic(name, bins, chunk) == expected
+        assert bench.kernel_traffic(name, bins[:-1] + [bins[-1] // 2], chunk) is None
+        assert bench.kernel_traffic(name, bins, chunk // 2) is None
+    other = next(k for k in ("k_move_cta<128>", "k_move_cta<256>", "k_move_cta<1024>")
+                 if k not in kernels)
+    assert bench.kernel_traffic(other, bins, chunk) is None
