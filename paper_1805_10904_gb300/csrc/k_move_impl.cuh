@@ -123,6 +123,88 @@ __device__ __forceinline__ void consider(int32_t c, i64 e, int32_t a, i64 dl, i6
     }
 }
 
+// consider() with the community degree dc = deg[c] already read (unused for c == a).
+template <typename GT>
+__device__ __forceinline__ void consider_deg(int32_t c, i64 e, i64 dc, int32_t a, i64 dl, i64 tw,
+                                             GT &gbest, int32_t &best, i64 &e_a)
+{
+    if (c == a) {
+        e_a = e;
+        return;
+    }
+    const GT g = (GT)tw * (GT)e - (GT)dl * (GT)dc;
+    if (better(g, c, gbest, best)) {
+        gbest = g;
+        best = c;
+    }
+}
+
+// Candidate scan of a row's claim list: list positions first, first + step, ... below m,
+// scored and cleared.  kScanBatch candidates are read at a time and their community degrees
+// gathered together before any is scored, so those random reads overlap instead of each
+// waiting for the previous one.
+constexpr int kScanBatch = 4;
+
+template <typename GT, typename VT>
+__device__ __forceinline__ void scan_list(int *keys, VT *vals, const int *list, int m, int first,
+                                          int step, int32_t a, i64 dl, i64 tw, const i64 *deg,
+                                          GT &gbest, int32_t &best, i64 &e_a)
+{
+    for (int p0 = first; p0 < m; p0 += kScanBatch * step) {
+        int sl[kScanBatch];
+        int32_t cc[kScanBatch];
+        i64 dc[kScanBatch];
+#pragma unroll
+        for (int u = 0; u < kScanBatch; u++) {
+            const int p = p0 + u * step;
+            sl[u] = p < m ? list[p] : -1;
+            cc[u] = sl[u] >= 0 ? keys[sl[u]] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kScanBatch; u++) dc[u] = (cc[u] >= 0 && cc[u] != a) ? deg[cc[u]] : 0;
+#pragma unroll
+        for (int u = 0; u < kScanBatch; u++) {
+            if (sl[u] < 0) continue;
+            const i64 e = (i64)vals[sl[u]];
+            keys[sl[u]] = -1;
+            vals[sl[u]] = 0;
+            consider_deg<GT>(cc[u], e, dc[u], a, dl, tw, gbest, best, e_a);
+        }
+    }
+}
+
+// The same over a whole table segment of cap slots (tables without a claim list): slots
+// first, first + step, ...; returns the occupied slots this thread saw.
+template <typename GT, typename VT>
+__device__ __forceinline__ i64 scan_slots(int *keys, VT *vals, int cap, int first, int step,
+                                          int32_t a, i64 dl, i64 tw, const i64 *deg, GT &gbest,
+                                          int32_t &best, i64 &e_a)
+{
+    i64 seen = 0;
+    for (int s0 = first; s0 < cap; s0 += kScanBatch * step) {
+        int32_t cc[kScanBatch];
+        i64 dc[kScanBatch];
+#pragma unroll
+        for (int u = 0; u < kScanBatch; u++) {
+            const int sl = s0 + u * step;
+            cc[u] = sl < cap ? keys[sl] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kScanBatch; u++) dc[u] = (cc[u] >= 0 && cc[u] != a) ? deg[cc[u]] : 0;
+#pragma unroll
+        for (int u = 0; u < kScanBatch; u++) {
+            if (cc[u] < 0) continue;
+            const int sl = s0 + u * step;
+            const i64 e = (i64)vals[sl];
+            keys[sl] = -1;
+            vals[sl] = 0;
+            seen++;
+            consider_deg<GT>(cc[u], e, dc[u], a, dl, tw, gbest, best, e_a);
+        }
+    }
+    return seen;
+}
+
 // Helpers of the first sweep of a phase (kernels and the reason they hold below).
 __device__ __forceinline__ u64 first_cand(u64 cnt)
 {
@@ -399,14 +481,7 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
         i64 e_a = 0;
-        for (int p = lane; p < m; p += G) {
-            const int s = list[p];
-            const int32_t c = keys[s];
-            const i64 e = (i64)vals[s];
-            keys[s] = -1;
-            vals[s] = 0;
-            consider<GT>(c, e, a, dl, tw, A.deg, gbest, best, e_a);
-        }
+        scan_list<GT, VT>(keys, vals, list, m, lane, G, a, dl, tw, A.deg, gbest, best, e_a);
         argmax_reduce(gbest, best, G);
         e_a = sum_reduce(e_a, G);
         loop = sum_reduce(loop, G);
@@ -554,6 +629,9 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 8 : (BLOCK == 512 ? 2 : 
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
         i64 e_a = 0;
+        // one candidate at a time here: the batched scan (scan_list) needs registers that the
+        // next row's prefetched chunk holds, and made bins 3-4 slower (R-MAT 26: 93.7 -> 113.3
+        // ms per run for 256-thread CTAs) while it speeds up the group and cluster kernels
         for (int p = threadIdx.x; p < m; p += BLOCK) {
             const int s = list[p];
             const int32_t cc = keys[s];
@@ -663,16 +741,9 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
         const i64 dl = A.delta[i];
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
-        i64 e_a = 0, mloc = 0;
-        for (int s = threadIdx.x; s < cap; s += BLOCK) {
-            const int32_t cc = keys[s];
-            if (cc < 0) continue;
-            const i64 e = (i64)vals[s];
-            keys[s] = -1;
-            vals[s] = 0;
-            mloc++;
-            consider<GT>(cc, e, a, dl, tw, A.deg, gbest, best, e_a);
-        }
+        i64 e_a = 0;
+        i64 mloc = scan_slots<GT, VT>(keys, vals, cap, threadIdx.x, BLOCK, a, dl, tw, A.deg, gbest,
+                                      best, e_a);
         mloc = sum_reduce(mloc, 32);  // per-warp count, folded into the CTA sum below
         block_argmax(gbest, best, e_a, loop);
         __shared__ i64 s_mw[32];
