@@ -128,6 +128,14 @@ typedef struct {
                                /* the colour classes in increasing colour, each deciding  */
                                /* on the state its predecessors left (louvain_run and     */
                                /* louvain_resume only); 0 (default): synchronous sweeps   */
+    int32_t host_labels;       /* 1: each recorded level's labels are copied to pinned host */
+                               /* memory on a copy stream while the later levels run (the */
+                               /* pinned blocks are kept by the handle for its next runs, */
+                               /* and outlive it while a result uses them); the run returns */
+                               /* with every copy done, louvain_result_labels returns that */
+                               /* memory and louvain_result_labels_into copies from it on  */
+                               /* the host; 0 (default): labels stay on the device until  */
+                               /* first asked for                                          */
     /* device memory: both NULL means stream-ordered cudaMallocAsync/cudaFreeAsync */
     louvain_alloc_fn alloc;
     louvain_free_fn free;
@@ -309,8 +317,9 @@ int64_t louvain_result_num_vertices(const louvain_result *r);
 
 /* Labels of the original vertices after level `level`, compacted to 0..ncomm-1 in the
  * order of the level's community labels (Sec. 5.1.2 renumbering).  *labels points to
- * n int32 values in host memory owned by r (copied from the device on first access).
- * ncomm may be NULL. */
+ * n int32 values in host memory owned by r (copied from the device on first access, or
+ * during the run with config.host_labels = 1), valid until r is destroyed.  ncomm may be
+ * NULL. */
 int louvain_result_labels(const louvain_result *r, int level, const int32_t **labels,
                           int64_t *ncomm);
 

@@ -210,6 +210,7 @@ struct LevelRec {
     int64_t n = 0, nnz = 0;
     int32_t hit_cap = 0;
     int32_t *d_labels = nullptr;
+    const int32_t *h_labels = nullptr;  // pinned host copy made during the run (host_labels)
 };
 
 struct TraceRec {
@@ -218,8 +219,65 @@ struct TraceRec {
     i128 qn;
 };
 
+// Pinned host blocks for labels copied during a run (config.host_labels).  A block goes back
+// to the pool when the last result using it is destroyed and is reused by later runs; at most
+// kKeep bytes stay cached.  Shared by the handle and the label stores, so it outlives a
+// handle whose results are still open.
+struct PinnedPool {
+    std::mutex mu;
+    std::vector<std::pair<size_t, void *>> free_blocks;
+    size_t cached = 0;
+    static constexpr size_t kKeep = (size_t)16 << 30;
+    static constexpr size_t kGrain = (size_t)2 << 20;
+
+    // a block of at least `bytes` (its size in *got), or nullptr when none can be pinned
+    void *get(size_t bytes, size_t *got)
+    {
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            int best = -1;
+            for (int i = 0; i < (int)free_blocks.size(); i++) {
+                const size_t b = free_blocks[i].first;
+                if (b >= bytes && b <= 2 * bytes + kGrain &&
+                    (best < 0 || b < free_blocks[best].first))
+                    best = i;
+            }
+            if (best >= 0) {
+                const auto blk = free_blocks[best];
+                free_blocks.erase(free_blocks.begin() + best);
+                cached -= blk.first;
+                *got = blk.first;
+                return blk.second;
+            }
+        }
+        const size_t sz = (bytes + kGrain - 1) / kGrain * kGrain;
+        void *p = nullptr;
+        if (cudaMallocHost(&p, sz) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        *got = sz;
+        return p;
+    }
+    void put(void *p, size_t bytes)
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (cached + bytes > kKeep) {
+            cudaFreeHost(p);
+            return;
+        }
+        free_blocks.push_back({bytes, p});
+        cached += bytes;
+    }
+    ~PinnedPool()
+    {
+        for (auto &b : free_blocks) cudaFreeHost(b.second);
+    }
+};
+
 struct louvain_handle {
     louvain_config cfg;
+    std::shared_ptr<PinnedPool> pool = std::make_shared<PinnedPool>();
     int device = 0;
     std::string err;
     LaunchCfg lc;
@@ -236,6 +294,10 @@ struct LabelStore {
     louvain_free_fn ff = nullptr;
     void *ctx = nullptr;
     int device = 0;
+    // pinned host copy of the labels (host_labels), returned to its pool
+    std::shared_ptr<PinnedPool> pool;
+    void *pinned = nullptr;
+    size_t pinned_bytes = 0;
     ~LabelStore()
     {
         cudaSetDevice(device);
@@ -243,6 +305,7 @@ struct LabelStore {
             if (ff) ff(p, ctx, nullptr);
             else cudaFreeAsync(p, nullptr);
         }
+        if (pinned) pool->put(pinned, pinned_bytes);
     }
 };
 
@@ -416,6 +479,8 @@ struct Engine {
     SweepTimers tm;
     cudaEvent_t coarsen_ev[2] = {nullptr, nullptr};
     cudaStream_t cap = nullptr;  // stream the sweep graphs are captured on (never runs work)
+    cudaStream_t lab_s = nullptr;  // host_labels: copies of recorded labels to pinned memory
+    cudaEvent_t lab_ev = nullptr;
     SweepStreams ss;             // streams the bins of a sweep run on side by side
 
     Engine(louvain_handle *h_, cudaStream_t s_, DevAlloc &A_, bool batch_,
@@ -433,6 +498,10 @@ struct Engine {
             ss.k = q + 1;
         }
         if (ss.k) CK(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+        if (cfg.host_labels) {
+            CK(cudaStreamCreateWithFlags(&lab_s, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&lab_ev, cudaEventDisableTiming));
+        }
         if (cfg.profile) {
             for (auto &e : tm.ev) CK(cudaEventCreate(&e));
             CK(cudaEventCreate(&coarsen_ev[0]));
@@ -454,6 +523,11 @@ struct Engine {
             cudaEventDestroy(ss.join[q]);
         }
         if (ss.fork) cudaEventDestroy(ss.fork);
+        if (lab_s) {
+            cudaStreamSynchronize(lab_s);  // a failed step may leave a copy in flight
+            cudaStreamDestroy(lab_s);
+            cudaEventDestroy(lab_ev);
+        }
     }
     Engine(const Engine &) = delete;
     Engine &operator=(const Engine &) = delete;
@@ -1389,6 +1463,21 @@ void Engine::step(std::vector<Member *> &retired)
         }
         kernels += launch_compose(n0_all, M, d_off.p, d_maps.p, d_rec.p, d_keep.p, st.C, new_id.p,
                                   d_base1.p, nid2, out, s, lc);
+        if (lab_s) {  // the labels go to pinned host memory while the induction runs
+            size_t got = 0;
+            void *hb = h->pool->get(sizeof(int32_t) * (size_t)n0_all, &got);
+            if (hb) {  // no pinned memory to be had: the labels are copied when asked for
+                store->pool = h->pool;
+                store->pinned = hb;
+                store->pinned_bytes = got;
+                CK(cudaEventRecord(lab_ev, s));
+                CK(cudaStreamWaitEvent(lab_s, lab_ev, 0));
+                CK(cudaMemcpyAsync(hb, out, sizeof(int32_t) * (size_t)n0_all,
+                                   cudaMemcpyDeviceToHost, lab_s));
+                for (int m = 0; m < M; m++)
+                    if (rec[m]) mem[m]->res->levels.back().h_labels = (int32_t *)hb + off[m];
+            }
+        }
         CK(cudaStreamSynchronize(s));  // host vectors above are uploaded before they go
     }
 
@@ -1538,6 +1627,9 @@ void Engine::step(std::vector<Member *> &retired)
     // step totals go to every graph of the step; the kept graphs move on, the rest leave
     const double wall = now_ms() - wall0;
     const int64_t step_kernels = kernels - k_start;
+    // this step's label copies (overlapped with its induction) are done before any result
+    // leaves the engine
+    if (lab_s) CK(cudaStreamSynchronize(lab_s));
     std::vector<Member *> next;
     for (int m = 0; m < M; m++) {
         Member *mb = mem[m];
@@ -2195,11 +2287,10 @@ PinnedStage &pinned_stage()
 
 // Host copy of one staged chunk, split over a few threads: the destination is usually fresh
 // pageable memory whose first touch (page faults) dominates a single-threaded copy.
-void parallel_memcpy(char *to, const char *from, size_t len)
+void parallel_memcpy(char *to, const char *from, size_t len, int max_threads = 4)
 {
     constexpr size_t kMinPart = (size_t)1 << 20;
-    constexpr int kMaxThreads = 4;
-    int parts = (int)std::min<size_t>(kMaxThreads, std::max<size_t>(1, len / kMinPart));
+    int parts = (int)std::min<size_t>((size_t)max_threads, std::max<size_t>(1, len / kMinPart));
     if (parts <= 1) {
         memcpy(to, from, len);
         return;
@@ -2356,6 +2447,10 @@ static int check_config(louvain_config &c, std::string &msg)
     }
     if (c.coloring != 0 && c.coloring != 1) {
         msg = "coloring must be 0 or 1";
+        return LOUVAIN_ERR_INVALID_ARG;
+    }
+    if (c.host_labels != 0 && c.host_labels != 1) {
+        msg = "host_labels must be 0 or 1";
         return LOUVAIN_ERR_INVALID_ARG;
     }
     if (c.part_keys == 0) c.part_keys = kPartKeys;
@@ -3019,6 +3114,11 @@ int louvain_result_labels(const louvain_result *r, int level, const int32_t **la
 {
     if (!r || level < 0 || level >= (int)r->levels.size() || !labels)
         return LOUVAIN_ERR_INVALID_ARG;
+    if (r->levels[level].h_labels) {  // copied during the run (host_labels)
+        *labels = r->levels[level].h_labels;
+        if (ncomm) *ncomm = r->levels[level].ncomm;
+        return LOUVAIN_OK;
+    }
     if (r->host_labels.size() != r->levels.size()) r->host_labels.resize(r->levels.size());
     std::vector<int32_t> &hl = r->host_labels[level];
     if (hl.size() != (size_t)r->n0) {
@@ -3040,6 +3140,11 @@ int louvain_result_labels_into(const louvain_result *r, int level, int32_t *dst)
     if (!r || level < 0 || level >= (int)r->levels.size() || (!dst && r->n0 > 0))
         return LOUVAIN_ERR_INVALID_ARG;
     if (r->n0 == 0) return LOUVAIN_OK;
+    if (r->levels[level].h_labels) {  // copied during the run (host_labels): a host copy
+        parallel_memcpy((char *)dst, (const char *)r->levels[level].h_labels,
+                        sizeof(int32_t) * (size_t)r->n0, 8);
+        return LOUVAIN_OK;
+    }
     if (!copy_d2h_staged(r->device, dst, r->levels[level].d_labels,
                          sizeof(int32_t) * (size_t)r->n0)) {
         cudaGetLastError();

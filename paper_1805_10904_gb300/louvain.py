@@ -65,6 +65,7 @@ class Config(ctypes.Structure):
         ("sweep_streams", ctypes.c_int32),
         ("part_keys", ctypes.c_int32),
         ("coloring", ctypes.c_int32),
+        ("host_labels", ctypes.c_int32),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
@@ -190,8 +191,23 @@ class Result:
     def n(self) -> int:
         return self._lib.louvain_result_num_vertices(self._p)
 
-    def labels(self, level: int) -> np.ndarray:
-        """Labels of the input vertices after `level`, copied into a new array."""
+    def labels(self, level: int, copy: bool = True) -> np.ndarray:
+        """Labels of the input vertices after `level`.  copy=True: a new array.  copy=False:
+        a read-only view of the result's own host copy (made during the run when the handle
+        has host_labels=True, else on this first access); the view keeps the result alive
+        and is valid until close()."""
+        if not copy:
+            p = ctypes.c_void_p()
+            rc = self._lib.louvain_result_labels(self._p, level, ctypes.byref(p), None)
+            if rc != OK:
+                raise LouvainError(rc, "louvain_result_labels")
+            if self.n == 0:
+                return np.empty(0, np.int32)
+            buf = (ctypes.c_int32 * self.n).from_address(p.value)
+            buf._owner = self  # the result outlives the view
+            view = np.frombuffer(buf, dtype=np.int32)
+            view.flags.writeable = False
+            return view
         out = np.empty(self.n, np.int32)
         rc = self._lib.louvain_result_labels_into(self._p, level,
                                                   out.ctypes.data if self.n else None)
@@ -322,7 +338,7 @@ class Louvain:
                  profile: bool = False, torch_alloc: bool = True, cuda_graphs: bool = True,
                  autotune: bool = False, threshold_mode: int = 0, post_merge: bool = False,
                  alloc_hook=None, keep_coarse: bool = False, sweep_streams: int = 4,
-                 part_keys: int = 0, coloring: bool = False):
+                 part_keys: int = 0, coloring: bool = False, host_labels: bool = False):
         lib = load()
         self._lib = lib
         cfg = Config()
@@ -350,6 +366,7 @@ class Louvain:
         if part_keys:
             cfg.part_keys = int(part_keys)
         cfg.coloring = int(coloring)
+        cfg.host_labels = int(host_labels)
         self.device = device
         # alloc_hook(bytes) -> bool may refuse an allocation (failure-injection tests)
         self.alloc_hook = alloc_hook

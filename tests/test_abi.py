@@ -70,7 +70,8 @@ def test_invalid_config_rejected_before_any_device_call(lib):
     bad.bin_small = 9
     assert lib.louvain_create(ctypes.byref(bad), 0, ctypes.byref(h)) == 1
     for field, value in (("sweep_streams", 5), ("threshold_mode", 2), ("post_merge", 3),
-                         ("keep_coarse", -1), ("part_keys", 63), ("part_keys", -5)):
+                         ("keep_coarse", -1), ("part_keys", 63), ("part_keys", -5),
+                         ("coloring", 2), ("host_labels", 2), ("host_labels", -1)):
         bad = Config.from_buffer_copy(cfg)
         setattr(bad, field, value)
         assert lib.louvain_create(ctypes.byref(bad), 0, ctypes.byref(h)) == 1
