@@ -210,8 +210,8 @@ __device__ __forceinline__ void flat_entry(const CoarsenArgs<WT> &A, int32_t &p,
 {
     if (A.mpre[p + 1] <= t) p = find_member(A.mpre, p + 1, pe, t);
     const int64_t kk = A.mrow[p] + (t - A.mpre[p]);
-    key = A.C[A.col[kk]];  // A.C holds the renumbered labels new_id[C[v]]
-    wv = (i64)A.w[kk];
+    key = A.C[ld_stream(A.col + kk)];  // A.C holds the renumbered labels new_id[C[v]]
+    wv = (i64)ld_stream(A.w + kk);
 }
 
 // G lanes per community with few entries (8 for at most 32 entries, a warp for at most

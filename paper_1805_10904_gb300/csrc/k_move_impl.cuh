@@ -332,8 +332,8 @@ __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small
                     lab[t] = -1;
                     wt[t] = 0;
                     if (t < d) {
-                        lab[t] = A.col[rb + t];
-                        wt[t] = (i64)A.w[rb + t];
+                        lab[t] = ld_stream(A.col + rb + t);
+                        wt[t] = (i64)ld_stream(A.w + rb + t);
                     }
                 }
                 i64 loop = 0;
@@ -464,8 +464,8 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) {
                 const int64_t k = k0 + (int64_t)G * u;
-                j[u] = k < re ? A.col[k] : -1;
-                x[u] = k < re ? (i64)A.w[k] : 0;
+                j[u] = k < re ? ld_stream(A.col + k) : -1;
+                x[u] = k < re ? (i64)ld_stream(A.w + k) : 0;
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
@@ -524,8 +524,8 @@ __device__ __forceinline__ void load_chunk(const MoveArgs<WT> &A, int64_t base, 
         j[u] = -1;
         x[u] = 0;
         if (k < re) {
-            j[u] = A.col[k];
-            x[u] = (i64)A.w[k];
+            j[u] = ld_stream(A.col + k);
+            x[u] = (i64)ld_stream(A.w + k);
         }
     }
 }
@@ -720,8 +720,8 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
                 j[u] = -1;
                 x[u] = 0;
                 if (k < re) {
-                    j[u] = A.col[k];
-                    x[u] = (i64)A.w[k];
+                    j[u] = ld_stream(A.col + k);
+                    x[u] = (i64)ld_stream(A.w + k);
                 }
             }
             int32_t c[kUnroll];
@@ -888,8 +888,8 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
                 j[u] = -1;
                 x[u] = 0;
                 if (k < ce) {
-                    j[u] = A.col[k];
-                    x[u] = (i64)A.w[k];
+                    j[u] = ld_stream(A.col + k);
+                    x[u] = (i64)ld_stream(A.w + k);
                 }
             }
             int32_t cc[kUnroll];
@@ -1125,8 +1125,8 @@ __global__ void __launch_bounds__(kBlock) k_move_group_first(MoveArgs<WT> A, con
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) {
                 const int64_t k = k0 + (int64_t)G * u;
-                j[u] = k < re ? A.col[k] : -1;
-                x[u] = k < re ? (i64)A.w[k] : 0;
+                j[u] = k < re ? ld_stream(A.col + k) : -1;
+                x[u] = k < re ? (i64)ld_stream(A.w + k) : 0;
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;

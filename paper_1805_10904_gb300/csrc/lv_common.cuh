@@ -192,6 +192,15 @@ __device__ __forceinline__ unsigned hash_slot(int key, int log2cap)
     return log2cap == 0 ? 0u : ((unsigned)key * 2654435761u) >> (32 - log2cap);
 }
 
+// Read-once data (a sweep's or an induction's columns and weights): loaded with the
+// evict-first hint, so the streamed rows do not push the gathered labels and community
+// degrees out of L2.
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T *p)
+{
+    return __ldcs(p);
+}
+
 // Open-addressing insert-or-add of (key, val) into a table of 2^log2cap slots.  `list`
 // records the slot of every key the first time it is claimed (count in *cnt), so the table
 // can be walked and cleared in O(distinct keys).  A table with more slots than distinct
