@@ -259,8 +259,8 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
         const int m = valid ? *(volatile int *)cnt : 0;
         for (int q = lane; q < m; q += G) {
             const int s = list[q];
-            A.tmp_col[tb + q] = keys[s];
-            ((VT *)A.tmp_w)[tb + q] = vals[s];
+            st_stream(A.tmp_col + tb + q, keys[s]);
+            st_stream((VT *)A.tmp_w + tb + q, vals[s]);
             keys[s] = -1;
             vals[s] = 0;
         }
@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const 
         const int m = s_cnt;
         for (int q = threadIdx.x; q < m; q += BLOCK) {
             const int s = list[q];
-            A.tmp_col[tb + q] = keys[s];
-            ((VT *)A.tmp_w)[tb + q] = vals[s];
+            st_stream(A.tmp_col + tb + q, keys[s]);
+            st_stream((VT *)A.tmp_w + tb + q, vals[s]);
             keys[s] = -1;
             vals[s] = 0;
         }
@@ -463,8 +463,8 @@ __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge_merge(CoarsenArgs<
             const int64_t o = tb + s_base;
             for (int r = threadIdx.x; r < m; r += kCHugeBlock) {
                 const int s = list[r];
-                A.tmp_col[o + r] = keys[s];
-                ((VT *)A.tmp_w)[o + r] = vals[s];
+                st_stream(A.tmp_col + o + r, keys[s]);
+                st_stream((VT *)A.tmp_w + o + r, vals[s]);
                 keys[s] = -1;
                 vals[s] = 0;
             }
@@ -521,8 +521,8 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_compact(int64_t k, int64_t n
                 end = rp_next[a + 1];
                 shift = mpre[moff[a]] - rp_next[a];
             }
-            col_next[o] = tmp_col[o + shift];
-            w_next[o] = (WO)tmp_w[o + shift];
+            st_stream(col_next + o, ld_stream(tmp_col + o + shift));
+            st_stream(w_next + o, (WO)ld_stream(tmp_w + o + shift));
         }
     }
 }

@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(kBlock) k_row_sums_thread(RowCtx R, const int6
         i64 x[kMax];
 #pragma unroll
         for (int t = 0; t < kMax; t++) {
-            j[t] = t < d ? col[b + t] : 0;
-            x[t] = t < d ? (i64)w[b + t] : 1;
+            j[t] = t < d ? ld_stream(col + b + t) : 0;
+            x[t] = t < d ? (i64)ld_stream(w + b + t) : 1;
         }
         const int g = R.graph(i);
         int64_t lo, hi;
@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(kBlock) k_row_sums_warp(RowCtx R, const int64_
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int64_t k = k0 + 32 * u;
-                j[u] = k < e ? col[k] : INT_MAX;
-                x[u] = k < e ? (i64)w[k] : 0;
+                j[u] = k < e ? ld_stream(col + k) : INT_MAX;
+                x[u] = k < e ? (i64)ld_stream(w + k) : 0;
             }
 #pragma unroll
             for (int u = 0; u < U; u++) {
@@ -302,8 +302,8 @@ __global__ void __launch_bounds__(kBlock) k_row_sums_cta(RowCtx R, const int64_t
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int64_t k = k0 + (int64_t)kBlock * u;
-                j[u] = k < e ? col[k] : INT_MAX;
-                x[u] = k < e ? (i64)w[k] : 0;
+                j[u] = k < e ? ld_stream(col + k) : INT_MAX;
+                x[u] = k < e ? (i64)ld_stream(w + k) : 0;
             }
 #pragma unroll
             for (int u = 0; u < U; u++) {

@@ -201,6 +201,14 @@ __device__ __forceinline__ T ld_stream(const T *p)
     return __ldcs(p);
 }
 
+// Write-once data that is read back much later (an induction's rows): stored with the
+// streaming hint.
+template <typename T>
+__device__ __forceinline__ void st_stream(T *p, T v)
+{
+    __stcs(p, v);
+}
+
 // Open-addressing insert-or-add of (key, val) into a table of 2^log2cap slots.  `list`
 // records the slot of every key the first time it is claimed (count in *cnt), so the table
 // can be walked and cleared in O(distinct keys).  A table with more slots than distinct
