@@ -208,7 +208,20 @@ template <typename WT>
 __device__ __forceinline__ void flat_entry(const CoarsenArgs<WT> &A, int32_t &p, int32_t pe,
                                            int64_t t, int32_t &key, i64 &wv)
 {
-    if (A.mpre[p + 1] <= t) p = find_member(A.mpre, p + 1, pe, t);
+    if (A.mpre[p + 1] <= t) {
+        // the member holding t lies a few members on: gallop (p + 2, p + 4, p + 8, ...) to a
+        // member past it, then bisect that span, instead of bisecting all members up to pe
+        int32_t lo = p + 1, hi = pe;
+#pragma unroll 1
+        for (int32_t step = 1; lo + step < pe; step <<= 1) {
+            if (A.mpre[lo + step] > t) {
+                hi = lo + step;
+                break;
+            }
+            lo += step;
+        }
+        p = find_member(A.mpre, lo, hi, t);
+    }
     const int64_t kk = A.mrow[p] + (t - A.mpre[p]);
     key = A.C[ld_stream(A.col + kk)];  // A.C holds the renumbered labels new_id[C[v]]
     wv = (i64)ld_stream(A.w + kk);
