@@ -453,7 +453,7 @@ struct Engine {
     DBuf<int32_t> chunk_b, hp_best, hp_sdone, hp_slice_row;
     // induction of multi-chunk communities: pairs per partition, offsets, cursors, the
     // partition's community, pairs per chunk, the pairs grouped by partition
-    DBuf<int32_t> c_pcnt, c_pcur, c_partb, c_chm, c_pk;
+    DBuf<int32_t> c_pcnt, c_pcur, c_partb, c_chm, c_pk, c_mem0;
     DBuf<int64_t> c_poff, c_pscr;
     DBuf<u64> c_pv;
     DBuf<int64_t> hp_soff;
@@ -901,6 +901,8 @@ void Engine::prep_huge(Bins &b, bool coarsen_side, int64_t k_comm, CoarsenBufs *
             CK(cudaMemsetAsync(c_pcur.p, 0, sizeof(int32_t) * np, s));
         }
         ensure(c_chm, (size_t)std::max(b.nchunks, 1));
+        ensure(c_mem0, (size_t)std::max(b.nchunks, 1));
+        b.cmem0 = c_mem0.p;
         b.cpcnt = c_pcnt.p;
         b.cpoff = c_poff.p;
         b.cpcur = c_pcur.p;

@@ -349,9 +349,29 @@ struct CBigArgs {
     void *pv;
     int chunk;
     int nchunks;
+    const int32_t *mem0;    // member holding the first entry of every chunk
 };
 
 constexpr int kCHugeBlock = 512;
+
+// The member holding the first entry of every chunk, found for all chunks at once (one
+// thread per chunk) instead of by a search over the community's members at the start of
+// each chunk's CTA.
+__global__ void __launch_bounds__(kBlock) k_chunk_member0(int nchunks, const int32_t *chunk_b,
+                                                          const int32_t *chunk_first,
+                                                          const int32_t *blist, const int32_t *moff,
+                                                          const int64_t *mpre, int chunk,
+                                                          int32_t *mem0)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x) {
+        const int b = chunk_b[c];
+        const int32_t a = blist[b];
+        const int32_t pb = moff[a], pe = moff[a + 1];
+        const int64_t tb = mpre[pb];
+        const int64_t cb = tb + (int64_t)(c - chunk_first[b]) * chunk;
+        mem0[c] = cb > tb ? find_member(mpre, pb, pe, cb) : pb;
+    }
+}
 
 // Communities with the most entries, phase A: CTA chunks of `chunk` flattened entries, each
 // aggregated in a shared table.  A one-chunk community writes its row directly.  A chunk of
@@ -382,8 +402,7 @@ __global__ void __launch_bounds__(kCHugeBlock) k_coarsen_huge(CoarsenArgs<WT> A,
         const int64_t tb = A.mpre[pb], te = A.mpre[pe];
         const int64_t cb = tb + (int64_t)q * B.chunk;
         const int64_t ce = min(te, cb + (int64_t)B.chunk);
-        int32_t p = pb;
-        if (cb > tb) p = find_member(A.mpre, pb, pe, cb);  // the member holding entry cb
+        int32_t p = B.mem0[c];  // the member holding entry cb
         for (int64_t t = cb + threadIdx.x; t < ce; t += kCHugeBlock) {
             int32_t key;
             i64 wv;
@@ -665,7 +684,13 @@ static int stage2_impl(const DevGraph &g, const PhaseState &st, const int32_t *n
             CBigArgs B{rows,        bins.chunk_b, bins.chunk_first, bins.nch,
                        bins.goff,   bins.glog2,   bins.cpcnt,       bins.cpoff,
                        bins.cpcur,  bins.cpartb,  bins.gslots,      bins.cchm,
-                       bins.cpk,    bins.cpv,     bins.chunk,       bins.nchunks};
+                       bins.cpk,    bins.cpv,     bins.chunk,       bins.nchunks,
+                       bins.cmem0};
+            k_chunk_member0<<<grid_for(bins.nchunks, kBlock, lc.max_blocks), kBlock, 0, s>>>(
+                bins.nchunks, bins.chunk_b, bins.chunk_first, rows, cb.moff, cb.mpre, bins.chunk,
+                bins.cmem0);
+            note_launch("k_chunk_member0");
+            launched++;
             const int l2 = 31 - __builtin_clz(2 * bins.chunk);
             const size_t smem = ctable_bytes<VT>(l2, true);
             const int grid = cta_grid(k_coarsen_huge<WT, VT>, kCHugeBlock, smem, bins.nchunks, lc,

@@ -94,6 +94,7 @@ struct Bins {
     int32_t *cpcur = nullptr;  // scatter cursor per partition
     int32_t *cpartb = nullptr; // community (chunked-list index) of every partition
     int32_t *cchm = nullptr;   // distinct pairs of every chunk
+    int32_t *cmem0 = nullptr;  // member holding the first entry of every chunk
     int32_t *cpk = nullptr;    // pairs grouped by partition: targets
     void *cpv = nullptr;       //                              sums (u32 or u64)
     int64_t *cpscr = nullptr;  // scan scratch for the partition offsets
