@@ -249,18 +249,25 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
     VT *vals = s_vals + g * CAP;
     int *list = s_list + g * CAP;
     int *cnt = &s_cnt[g];
-    for (int base = blockIdx.x * NG; base < ncl; base += gridDim.x * NG) {
-        const int vi = base + g;
-        const bool valid = vi < ncl;
-        int32_t a = 0, pb = 0, pe = 0;
-        int64_t tb = 0, te = 0;
-        if (valid) {
-            a = clist[vi];
-            pb = A.moff[a];
-            pe = A.moff[a + 1];
-            tb = A.mpre[pb];
-            te = A.mpre[pe];
-        }
+    // the next community's list entry, member range and entry range are loaded stage by stage
+    // while the current one is merged, so no load of that chain waits at the loop's top
+    const int step = gridDim.x * NG;
+    int base = blockIdx.x * NG;
+    int32_t na = 0, npb = 0, npe = 0;
+    int64_t ntb = 0, nte = 0;
+    if (base + g < ncl) {
+        na = clist[base + g];
+        npb = A.moff[na];
+        npe = A.moff[na + 1];
+        ntb = A.mpre[npb];
+        nte = A.mpre[npe];
+    }
+    for (; base < ncl; base += step) {
+        const bool valid = base + g < ncl;
+        const int32_t a = na, pb = npb, pe = npe;
+        const int64_t tb = ntb, te = nte;
+        const bool next = base + step + g < ncl;
+        if (next) na = clist[base + step + g];
         int32_t p = pb;
         for (int64_t t = tb + lane; t < te; t += G) {
             int32_t key;
@@ -268,8 +275,19 @@ __global__ void __launch_bounds__(kBlock) k_coarsen_group(CoarsenArgs<WT> A, con
             flat_entry(A, p, pe, t, key, wv);
             tbl_insert<false, VT>(keys, vals, list, cnt, LOG2CAP, key, (VT)wv, A.err);
         }
+        if (next) {
+            npb = A.moff[na];
+            npe = A.moff[na + 1];
+        }
         __syncwarp();
         const int m = valid ? *(volatile int *)cnt : 0;
+        if (next) {
+            ntb = A.mpre[npb];
+            nte = A.mpre[npe];
+        } else {  // this group has no community in the next round: an empty range
+            npb = npe = 0;
+            ntb = nte = 0;
+        }
         for (int q = lane; q < m; q += G) {
             const int s = list[q];
             st_stream(A.tmp_col + tb + q, keys[s]);
@@ -303,10 +321,23 @@ __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const 
     }
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    for (int v = blockIdx.x; v < ncl; v += gridDim.x) {
-        const int32_t a = clist[v];
-        const int32_t pb = A.moff[a], pe = A.moff[a + 1];
-        const int64_t tb = A.mpre[pb], te = A.mpre[pe];
+    // the next community's list entry, member range and entry range are loaded stage by stage
+    // while the current one is merged, so no load of that chain waits at the loop's top
+    int v = blockIdx.x;
+    int32_t na = 0, npb = 0, npe = 0;
+    int64_t ntb = 0, nte = 0;
+    if (v < ncl) {
+        na = clist[v];
+        npb = A.moff[na];
+        npe = A.moff[na + 1];
+        ntb = A.mpre[npb];
+        nte = A.mpre[npe];
+    }
+    for (; v < ncl; v += gridDim.x) {
+        const int32_t a = na, pb = npb, pe = npe;
+        const int64_t tb = ntb, te = nte;
+        const bool next = v + (int)gridDim.x < ncl;
+        if (next) na = clist[v + gridDim.x];
         int32_t p = pb;
         for (int64_t t = tb + threadIdx.x; t < te; t += BLOCK) {
             int32_t key;
@@ -314,8 +345,16 @@ __global__ void __launch_bounds__(BLOCK) k_coarsen_cta(CoarsenArgs<WT> A, const 
             flat_entry(A, p, pe, t, key, wv);
             tbl_insert<false, VT>(keys, vals, list, &s_cnt, log2cap, key, (VT)wv, A.err);
         }
+        if (next) {
+            npb = A.moff[na];
+            npe = A.moff[na + 1];
+        }
         __syncthreads();
         const int m = s_cnt;
+        if (next) {
+            ntb = A.mpre[npb];
+            nte = A.mpre[npe];
+        }
         for (int q = threadIdx.x; q < m; q += BLOCK) {
             const int s = list[q];
             st_stream(A.tmp_col + tb + q, keys[s]);
