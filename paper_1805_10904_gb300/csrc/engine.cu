@@ -153,7 +153,7 @@ struct Scalars {
     u64 cand_total[16];
     LoopCtl loop;
     unsigned unsorted;  // one graph: a row without strictly increasing columns was seen
-    int32_t pad_;
+    unsigned deg32_bad;  // a community degree reached 2^32: the sweeps read the 64-bit deg
     int32_t tail[8];
 };
 
@@ -443,6 +443,7 @@ struct Engine {
 
     // per-vertex state, sized for the largest stacked graph so far
     DBuf<i64> delta, delta_next, deg;
+    DBuf<unsigned> deg32;  // 32-bit copy of deg for the candidate scans
     DBuf<int32_t> C, Cnext, size, new_id, new_id2, lists, vg;
     DBuf<int32_t> colorb, pickb;  // colouring variant: colour of every vertex, round picks
     DBuf<int32_t> b_nch, b_chunk_first, b_plog2, b_glog2;
@@ -1169,6 +1170,10 @@ void Engine::step(std::vector<Member *> &retired)
     st.deg = deg.p;
     st.size = size.p;
     st.delta = delta.p;
+    ensure(deg32, n);
+    st.deg32 = deg32.p;
+    st.deg32_bad = &d_sc->deg32_bad;
+    CK(cudaMemsetAsync(&d_sc->deg32_bad, 0, sizeof(unsigned), s));
     kernels += launch_init_state(n, st, s, lc);
     // vertex following: level 0 of each graph (every level with vf_all_levels)
     if (cfg.vertex_following) {

@@ -416,13 +416,34 @@ int launch_check_symmetry(const DevGraph &g, unsigned *err, cudaStream_t s, cons
 
 // ------------------------------------------------------------------ phase state
 
-__global__ void k_init_state(int64_t n, int32_t *C, i64 *deg, int32_t *size, const i64 *delta)
+// Weight d of a vertex moves from community a to community b: deg and its 32-bit copy follow
+// (the copy modulo 2^32), and the flag is raised when b's degree reaches 2^32, after which
+// the copy is not read.  Degrees change only here, so a final degree of 2^32 or more is always
+// seen by the increment that reached it.
+__device__ __forceinline__ void move_degree(i64 *deg, unsigned *deg32, unsigned *bad, int32_t a,
+                                            int32_t b, i64 d)
+{
+    const u64 ob = atomicAdd((u64 *)&deg[b], (u64)d);
+    atomicAdd((u64 *)&deg[a], (u64)(-d));
+    if (deg32) {
+        atomicAdd(&deg32[b], (unsigned)d);
+        atomicSub(&deg32[a], (unsigned)d);
+        if ((ob + (u64)d) >> 32) *bad = 1u;
+    }
+}
+
+__global__ void k_init_state(int64_t n, int32_t *C, i64 *deg, int32_t *size, const i64 *delta,
+                             unsigned *deg32, unsigned *bad)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         C[i] = (int32_t)i;
         deg[i] = delta[i];
         size[i] = 1;
+        if (deg32) {
+            deg32[i] = (unsigned)delta[i];
+            if ((u64)delta[i] >> 32) *bad = 1u;
+        }
     }
 }
 
@@ -430,7 +451,8 @@ int launch_init_state(int64_t n, const PhaseState &st, cudaStream_t s, const Lau
 {
     if (n == 0) return 0;
     k_init_state<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(n, st.C, st.deg, st.size,
-                                                                      st.delta);
+                                                                      st.delta, st.deg32,
+                                                                      st.deg32_bad);
     return 1;
 }
 
@@ -466,7 +488,8 @@ __device__ __forceinline__ int sole_neighbour(const int64_t *rp, const int32_t *
 // the deg/size updates below commute.  Runs right after k_init_state.
 __global__ void k_vertex_following(int64_t n, const int64_t *rp, const int32_t *col,
                                    const i64 *delta, int32_t *C, i64 *deg, int32_t *size,
-                                   const int32_t *vg, const int32_t *vf_on)
+                                   const int32_t *vg, const int32_t *vf_on, unsigned *deg32,
+                                   unsigned *bad)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -478,8 +501,7 @@ __global__ void k_vertex_following(int64_t n, const int64_t *rp, const int32_t *
         if (t == (int32_t)i) continue;
         const i64 d = delta[i];
         C[i] = t;
-        atomicAdd((u64 *)&deg[t], (u64)d);
-        atomicAdd((u64 *)&deg[i], (u64)(-d));
+        move_degree(deg, deg32, bad, (int32_t)i, t, d);
         atomicAdd(&size[t], 1);
         atomicSub(&size[i], 1);
     }
@@ -490,7 +512,7 @@ int launch_vertex_following(const DevGraph &g, const PhaseState &st, cudaStream_
 {
     if (g.n == 0) return 0;
     k_vertex_following<<<grid_for(g.n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        g.n, g.rp, g.col, st.delta, st.C, st.deg, st.size, vg, vf_on);
+        g.n, g.rp, g.col, st.delta, st.C, st.deg, st.size, vg, vf_on, st.deg32, st.deg32_bad);
     return 1;
 }
 
@@ -871,7 +893,8 @@ int launch_loop_ctl(cudaGraphConditionalHandle handle, LoopCtl *lc, const int *n
 // atomics), then C <- C_next.
 __global__ void __launch_bounds__(kBlock) k_apply(int64_t n, int32_t *C, const int32_t *Cnext,
                                                   i64 *deg, int32_t *size, const i64 *delta,
-                                                  const LevelCtl *ctl, const int32_t *vg)
+                                                  const LevelCtl *ctl, const int32_t *vg,
+                                                  unsigned *deg32, unsigned *bad)
 {
     if (!vg && ctl && *(volatile const int *)&ctl->done) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -879,9 +902,7 @@ __global__ void __launch_bounds__(kBlock) k_apply(int64_t n, int32_t *C, const i
         const int32_t a = C[i], b = Cnext[i];
         if (a == b) continue;
         if (vg && ctl && ctl[vg[i]].done) continue;
-        const i64 d = delta[i];
-        atomicAdd((u64 *)&deg[b], (u64)d);
-        atomicAdd((u64 *)&deg[a], (u64)(-d));
+        move_degree(deg, deg32, bad, a, b, delta[i]);
         atomicAdd(&size[b], 1);
         atomicSub(&size[a], 1);
         C[i] = b;
@@ -893,7 +914,8 @@ int launch_apply(int64_t n, const PhaseState &st, const LevelCtl *ctl, const int
 {
     if (n == 0) return 0;
     k_apply<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(n, st.C, st.Cnext, st.deg,
-                                                                 st.size, st.delta, ctl, vg);
+                                                                 st.size, st.delta, ctl, vg,
+                                                                 st.deg32, st.deg32_bad);
     return 1;
 }
 
@@ -1129,7 +1151,7 @@ int launch_color_assign(const DevGraph &g, int32_t *color, const int32_t *pick, 
 __global__ void __launch_bounds__(kBlock) k_apply_class(int64_t n, int32_t *C, const int32_t *Cnext,
                                                         i64 *deg, int32_t *size, const i64 *delta,
                                                         const int32_t *color, int32_t cls,
-                                                        u64 *moved)
+                                                        u64 *moved, unsigned *deg32, unsigned *bad)
 {
     u64 mv = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -1137,9 +1159,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_class(int64_t n, int32_t *C, c
         if (color[i] != cls) continue;
         const int32_t a = C[i], b = Cnext[i];
         if (a == b) continue;
-        const i64 d = delta[i];
-        atomicAdd((u64 *)&deg[b], (u64)d);
-        atomicAdd((u64 *)&deg[a], (u64)(-d));
+        move_degree(deg, deg32, bad, a, b, delta[i]);
         atomicAdd(&size[b], 1);
         atomicSub(&size[a], 1);
         C[i] = b;
@@ -1154,7 +1174,8 @@ int launch_apply_class(int64_t n, const PhaseState &st, u64 *moved, cudaStream_t
 {
     if (n == 0) return 0;
     k_apply_class<<<grid_for(n, kBlock, lc.max_blocks), kBlock, 0, s>>>(
-        n, st.C, st.Cnext, st.deg, st.size, st.delta, st.color, st.cls, moved);
+        n, st.C, st.Cnext, st.deg, st.size, st.delta, st.color, st.cls, moved, st.deg32,
+        st.deg32_bad);
     return 1;
 }
 

@@ -63,7 +63,28 @@ struct MoveArgs {
     const LevelCtl *gctl; // phase controller of every graph; rows of finished graphs are frozen
     const int32_t *color;  // colouring variant: only colour `cls` decides (nullptr: all)
     int32_t cls;
+    const unsigned *deg32;      // 32-bit copy of deg (nullptr: none)
+    const unsigned *deg32_bad;  // nonzero once a community degree reached 2^32
 };
+
+// Community degrees as the candidate scans read them: the 32-bit copy (half the bytes, so
+// more of it stays in L2) while every community degree fits it, else the 64-bit deg.  The
+// stay gain and the sums of squares always read deg.
+struct DegRead {
+    const i64 *d64;
+    const unsigned *d32;
+    __device__ __forceinline__ i64 operator[](int32_t c) const
+    {
+        return d32 ? (i64)d32[c] : d64[c];
+    }
+};
+
+template <typename WT>
+__device__ __forceinline__ DegRead deg_read(const MoveArgs<WT> &A)
+{
+    const bool ok = A.deg32 && *(volatile const unsigned *)A.deg32_bad == 0;
+    return DegRead{A.deg, ok ? A.deg32 : nullptr};
+}
 
 // Graph context of vertex i: its graph, that graph's 2W, and whether its phase has stopped.
 // BT (a batch) is a template flag, so the one-graph kernels carry none of this.
@@ -110,7 +131,7 @@ __device__ __forceinline__ int32_t choose_target(int32_t a, int32_t best, GT gbe
 // or records e_{i->a}.
 template <typename GT>
 __device__ __forceinline__ void consider(int32_t c, i64 e, int32_t a, i64 dl, i64 tw,
-                                         const i64 *deg, GT &gbest, int32_t &best, i64 &e_a)
+                                         DegRead deg, GT &gbest, int32_t &best, i64 &e_a)
 {
     if (c == a) {
         e_a = e;
@@ -147,7 +168,7 @@ constexpr int kScanBatch = 4;
 
 template <typename GT, typename VT>
 __device__ __forceinline__ void scan_list(int *keys, VT *vals, const int *list, int m, int first,
-                                          int step, int32_t a, i64 dl, i64 tw, const i64 *deg,
+                                          int step, int32_t a, i64 dl, i64 tw, DegRead deg,
                                           GT &gbest, int32_t &best, i64 &e_a)
 {
     for (int p0 = first; p0 < m; p0 += kScanBatch * step) {
@@ -177,7 +198,7 @@ __device__ __forceinline__ void scan_list(int *keys, VT *vals, const int *list, 
 // first, first + step, ...; returns the occupied slots this thread saw.
 template <typename GT, typename VT>
 __device__ __forceinline__ i64 scan_slots(int *keys, VT *vals, int cap, int first, int step,
-                                          int32_t a, i64 dl, i64 tw, const i64 *deg, GT &gbest,
+                                          int32_t a, i64 dl, i64 tw, DegRead deg, GT &gbest,
                                           int32_t &best, i64 &e_a)
 {
     i64 seen = 0;
@@ -307,6 +328,7 @@ template <typename WT, typename GT, bool BT, bool FIRST>
 __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small_max)
 {
     u64 internal = 0, moved = 0, cand = 0;
+    const DegRead dg = deg_read(A);
     u128 sq = 0;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < A.n;
          i0 += (int64_t)gridDim.x * blockDim.x) {
@@ -316,8 +338,8 @@ __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small
         int g = -1;
         if (i < A.n) {
             g = graph_of<BT>(A, i);
-            const i64 dg = A.deg[i];
-            v_sq = (u128)(u64)dg * (u64)dg;
+            const i64 di = A.deg[i];
+            v_sq = (u128)(u64)di * (u64)di;
             const int64_t rb = A.rp[i];
             const int64_t d = A.rp[i + 1] - rb;
             // frozen graph, or a vertex of another colour class: it keeps its label
@@ -359,7 +381,7 @@ __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small
                     for (int t = 0; t < kSmallMax; t++) {
                         const int32_t c = lab[t];
                         if (c >= 0)
-                            first_entry<GT>(c, wt[t], c == a ? 0 : A.deg[c], a, dl, tw, gbest,
+                            first_entry<GT>(c, wt[t], c == a ? 0 : dg[c], a, dl, tw, gbest,
                                             best, e_a, cnt);
                     }
                     m = (int)first_cand(cnt);
@@ -375,7 +397,7 @@ __global__ void __launch_bounds__(kBlock) k_move_small(MoveArgs<WT> A, int small
 #pragma unroll
                             for (int u = t; u < kSmallMax; u++) e += (lab[u] == c) ? wt[u] : 0;
                             m++;
-                            consider<GT>(c, e, a, dl, tw, A.deg, gbest, best, e_a);
+                            consider<GT>(c, e, a, dl, tw, dg, gbest, best, e_a);
                         }
                     }
                 }
@@ -438,6 +460,7 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
     int *list = s_list + g * CAP;
     int *cnt = &s_cnt[g];
     u64 internal = 0, moved = 0, cand = 0;
+    const DegRead dg = deg_read(A);
     for (int base = blockIdx.x * NG; base < nverts; base += gridDim.x * NG) {
         const int vi = base + g;
         const bool valid = vi < nverts;
@@ -481,7 +504,7 @@ __global__ void __launch_bounds__(kBlock) k_move_group(MoveArgs<WT> A, const int
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
         i64 e_a = 0;
-        scan_list<GT, VT>(keys, vals, list, m, lane, G, a, dl, tw, A.deg, gbest, best, e_a);
+        scan_list<GT, VT>(keys, vals, list, m, lane, G, a, dl, tw, dg, gbest, best, e_a);
         argmax_reduce(gbest, best, G);
         e_a = sum_reduce(e_a, G);
         loop = sum_reduce(loop, G);
@@ -571,6 +594,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 8 : (BLOCK == 512 ? 2 : 
         tbl_insert_batch<kUnroll, VT>(keys, vals, list, &s_cnt, log2cap, key, v, A.err);
     };
     u64 internal = 0, moved = 0, cand = 0;
+    const DegRead dg = deg_read(A);
     // prologue: the first row completely prefetched
     int v = blockIdx.x;
     int32_t nx_i = -1;
@@ -638,7 +662,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 8 : (BLOCK == 512 ? 2 : 
             const i64 e = (i64)vals[s];
             keys[s] = -1;
             vals[s] = 0;
-            consider<GT>(cc, e, a, dl, tw, A.deg, gbest, best, e_a);
+            consider<GT>(cc, e, a, dl, tw, dg, gbest, best, e_a);
         }
         // stage 4: next row's label gathers
         gather_chunk(A, i_next, nj, nc);
@@ -703,6 +727,9 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
     const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
     const int64_t stride = (int64_t)CL * BLOCK;
     u64 internal = 0, moved = 0, cand = 0;
+    // the 64-bit degrees here: these kernels are bound by their remote atomics, and reading the
+    // 32-bit copy made them slower (R-MAT 26: clusters of 2 and 8, 52.3 -> 54.8, 42.9 -> 44.1 ms)
+    const DegRead dg{A.deg, nullptr};
     for (int v = cid; v < nverts; v += ncl) {
         const int32_t i = verts[v];
         const int gr = graph_of<BT>(A, i);
@@ -742,7 +769,7 @@ __global__ void __launch_bounds__(1024) k_move_cluster(MoveArgs<WT> A, const int
         GT gbest = gain_min<GT>();
         int32_t best = INT_MAX;
         i64 e_a = 0;
-        i64 mloc = scan_slots<GT, VT>(keys, vals, cap, threadIdx.x, BLOCK, a, dl, tw, A.deg, gbest,
+        i64 mloc = scan_slots<GT, VT>(keys, vals, cap, threadIdx.x, BLOCK, a, dl, tw, dg, gbest,
                                       best, e_a);
         mloc = sum_reduce(mloc, 32);  // per-warp count, folded into the CTA sum below
         block_argmax(gbest, best, e_a, loop);
@@ -862,6 +889,7 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     u64 internal = 0, moved = 0, cand = 0;
+    const DegRead dg = deg_read(A);
     for (int c = blockIdx.x; c < B.nchunks; c += gridDim.x) {
         const int b = B.chunk_b[c];
         const int32_t i = B.bverts[b];
@@ -914,7 +942,7 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge(MoveArgs<WT> A, BigArg
                 const i64 e = (i64)vals[s];
                 keys[s] = -1;
                 vals[s] = 0;
-                consider<GT>(k2, e, a, dl, tw, A.deg, gbest, best, e_a);
+                consider<GT>(k2, e, a, dl, tw, dg, gbest, best, e_a);
             }
             block_argmax(gbest, best, e_a, loop);
             if (threadIdx.x == 0) {
@@ -990,6 +1018,7 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge_decide(MoveArgs<WT> A,
     GT *pg = (GT *)B.pgain;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     u64 internal = 0, moved = 0, cand = 0;
+    const DegRead dg = deg_read(A);
     for (int64_t q = blockIdx.x; q < B.nslices; q += gridDim.x) {
         const int b = B.slice_row[q];
         const int32_t i = B.bverts[b];
@@ -1026,7 +1055,7 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge_decide(MoveArgs<WT> A,
                 const i64 e = (i64)vals[s];
                 keys[s] = -1;
                 vals[s] = 0;
-                consider<GT>(k2, e, a, dl, tw, A.deg, gbest, best, e_a);
+                consider<GT>(k2, e, a, dl, tw, dg, gbest, best, e_a);
             }
             if (threadIdx.x == 0) mm += (u64)m;
         };
@@ -1097,6 +1126,7 @@ __global__ void __launch_bounds__(kBlock) k_move_group_first(MoveArgs<WT> A, con
     constexpr int NG = kBlock / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     u64 internal = 0, moved = 0, cand = 0;
+    const DegRead dg = deg_read(A);
     for (int base = blockIdx.x * NG; base < nverts; base += gridDim.x * NG) {
         const int vi = base + g;
         const bool valid = vi < nverts;
@@ -1131,7 +1161,7 @@ __global__ void __launch_bounds__(kBlock) k_move_group_first(MoveArgs<WT> A, con
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) c[u] = (j[u] >= 0 && j[u] != i) ? A.C[j[u]] : -1;
 #pragma unroll
-            for (int u = 0; u < kUnroll; u++) dc[u] = (c[u] >= 0 && c[u] != a) ? A.deg[c[u]] : 0;
+            for (int u = 0; u < kUnroll; u++) dc[u] = (c[u] >= 0 && c[u] != a) ? dg[c[u]] : 0;
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) {
                 if (j[u] == i) loop += x[u];
@@ -1165,6 +1195,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta_first(MoveArgs<WT> A, const 
                                                           int nverts, int slot)
 {
     u64 internal = 0, moved = 0, cand = 0;
+    const DegRead dg = deg_read(A);
     for (int v = blockIdx.x; v < nverts; v += gridDim.x) {
         const int32_t i = verts[v];
         const int gr = graph_of<BT>(A, i);
@@ -1184,7 +1215,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_cta_first(MoveArgs<WT> A, const 
             load_chunk<BLOCK>(A, k0, re, j, x);
             gather_chunk(A, i, j, c);
 #pragma unroll
-            for (int u = 0; u < kUnroll; u++) dc[u] = (c[u] >= 0 && c[u] != a) ? A.deg[c[u]] : 0;
+            for (int u = 0; u < kUnroll; u++) dc[u] = (c[u] >= 0 && c[u] != a) ? dg[c[u]] : 0;
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) {
                 if (j[u] == i) loop += x[u];
@@ -1216,6 +1247,7 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge_first(MoveArgs<WT> A, 
     __shared__ int s_last;
     GT *pg = (GT *)B.pgain;
     u64 internal = 0, moved = 0, cand = 0;
+    const DegRead dg = deg_read(A);
     for (int c = blockIdx.x; c < B.nchunks; c += gridDim.x) {
         const int b = B.chunk_b[c];
         const int32_t i = B.bverts[b];
@@ -1244,7 +1276,7 @@ __global__ void __launch_bounds__(kHugeBlock) k_move_huge_first(MoveArgs<WT> A, 
             gather_chunk(A, i, j, cc);
 #pragma unroll
             for (int u = 0; u < kUnroll; u++)
-                dc[u] = (cc[u] >= 0 && cc[u] != a) ? A.deg[cc[u]] : 0;
+                dc[u] = (cc[u] >= 0 && cc[u] != a) ? dg[cc[u]] : 0;
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) {
                 if (j[u] == i) loop += x[u];
@@ -1520,6 +1552,8 @@ static int sweep_impl(const DevGraph &g, const PhaseState &st, const Bins &b, i6
                    bc.gctl};
     A.color = st.color;
     A.cls = st.cls;
+    A.deg32 = st.deg32;
+    A.deg32_bad = st.deg32_bad;
     const bool timed = tm && tm->on;
     int launched = 0;
     // the bins read the same snapshot and write disjoint rows: with a stream set they run

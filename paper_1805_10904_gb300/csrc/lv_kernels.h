@@ -29,6 +29,10 @@ struct PhaseState {
     i64 *deg = nullptr;        // deg_c (Eq. 2)
     int32_t *size = nullptr;   // members of c
     i64 *delta = nullptr;      // weighted degree of each vertex
+    // 32-bit copy of deg, read by the sweeps' candidate scans while *deg32_bad is 0 (every
+    // community degree below 2^32); the writers of deg keep it and raise the flag
+    unsigned *deg32 = nullptr;
+    unsigned *deg32_bad = nullptr;
     // colouring variant: only the vertices of colour `cls` decide in this launch
     const int32_t *color = nullptr;
     int32_t cls = 0;
